@@ -1,0 +1,424 @@
+"""Seeded synthetic inputs: procedural interiors, cameras, probe grids and
+synthetic per-pixel buffers.
+
+This module holds only input data.  It builds triangle soups, per-triangle
+albedo and emission, camera frames and probe-grid placements from a seed, and
+random buffers shaped like the per-pixel G-buffer and reservoirs.  It performs
+none of the rendering method's arithmetic (no ray casting, no probe update, no
+resampling); both the CPU oracle and the CUDA path consume what it produces.
+
+Workloads (stand-ins for the paper's third-party scenes of Sec. 4, which are
+not available):
+
+* ``tiny_room``   -- 2 m closed box, 24 triangles, one emissive ceiling quad
+                     (radiance 10), 128x128 camera, 4x4x4 probes, 64 rays.
+* ``apartment``   -- 4-room apartment (walls with doors, 400 furniture boxes),
+                     about 64k triangles, 1024 emissive ceiling triangles with
+                     radiance log-uniform in [1, 100], 1920x1080 camera path
+                     translating 5 cm per frame, 16x8x16 probes, 256 rays.
+* ``tiny_room_1080p`` -- the tiny room rendered at 1920x1080 (learned-target
+                     workload).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+
+__all__ = [
+    "Scene", "Camera", "ProbeGrid", "Settings",
+    "tiny_room", "tiny_room_1080p", "apartment", "make_scene",
+    "synthetic_gbuffer", "synthetic_reservoirs", "synthetic_irradiance_interior",
+    "synthetic_depth_interior",
+]
+
+
+# ---------------------------------------------------------------------------
+# containers
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Camera:
+    """Pinhole camera frame.  ``right``/``up``/``fwd`` are orthonormal."""
+    pos: np.ndarray
+    fwd: np.ndarray
+    right: np.ndarray
+    up: np.ndarray
+    tan_half_fovy: float
+    width: int
+    height: int
+
+    def as_array(self) -> np.ndarray:
+        """Packed float32[16]: pos, fwd, right, up (xyz each), tan, w, h, pad."""
+        a = np.zeros(16, np.float32)
+        a[0:3] = self.pos
+        a[3:6] = self.fwd
+        a[6:9] = self.right
+        a[9:12] = self.up
+        a[12] = self.tan_half_fovy
+        a[13] = self.width
+        a[14] = self.height
+        return a
+
+
+@dataclasses.dataclass
+class ProbeGrid:
+    origin: np.ndarray   # float32[3], position of probe (0,0,0)
+    spacing: np.ndarray  # float32[3]
+    counts: np.ndarray   # int32[3]
+
+    @property
+    def num_probes(self) -> int:
+        return int(np.prod(self.counts))
+
+
+@dataclasses.dataclass
+class Settings:
+    """Method parameters of one workload (readings listed in the design notes)."""
+    rays_per_probe: int = 64
+    irr_texels: int = 8
+    depth_texels: int = 16
+    hysteresis: float = 0.97
+    le_attenuation: float = 1.0      # slider s; 0 disables the attenuation
+    depth_sharpness: float = 50.0
+    num_light_candidates: int = 31
+    num_bsdf_candidates: int = 1
+    temporal_mcap: float = 20.0
+    spatial_passes: int = 1
+    spatial_neighbours: int = 5
+    spatial_radius: int = 30
+    normal_reject_cos: float = 0.9
+    depth_reject_frac: float = 0.1
+    seed: int = 1
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    verts: np.ndarray      # float32[T, 3, 3]
+    albedo: np.ndarray     # float32[T, 3]
+    emission: np.ndarray   # float32[T, 3]
+    grid: ProbeGrid
+    cameras: List[Camera]
+    settings: Settings
+
+    @property
+    def num_tris(self) -> int:
+        return int(self.verts.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# geometry helpers (triangle soups with a winding that fixes the facing side)
+# ---------------------------------------------------------------------------
+
+def _quad(c, a, b, facing, nu=1, nv=1):
+    """Quad centred at ``c`` with half-extent vectors ``a`` and ``b``, wound so
+    that cross(v1 - v0, v2 - v0) points along ``facing``; split into
+    ``nu x nv`` sub-quads (2 triangles each)."""
+    c = np.asarray(c, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if np.dot(np.cross(a, b), facing) < 0:
+        a, b = b, a
+        nu, nv = nv, nu
+    tris = []
+    for i in range(nu):
+        for j in range(nv):
+            s0, s1 = -1 + 2 * i / nu, -1 + 2 * (i + 1) / nu
+            t0, t1 = -1 + 2 * j / nv, -1 + 2 * (j + 1) / nv
+            p0 = c + s0 * a + t0 * b
+            p1 = c + s1 * a + t0 * b
+            p2 = c + s1 * a + t1 * b
+            p3 = c + s0 * a + t1 * b
+            tris.append([p0, p1, p2])
+            tris.append([p0, p2, p3])
+    return tris
+
+
+_AXES = np.eye(3)
+
+
+def _box_faces(lo, hi, inward=False, tess=(1, 1, 1)):
+    """The 6 faces of an axis-aligned box as lists of triangles.  ``tess[k]``
+    is the number of subdivisions along axis k.  Normals point out of the solid
+    (``inward=False``) or into the enclosed room (``inward=True``)."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    c = 0.5 * (lo + hi)
+    h = 0.5 * (hi - lo)
+    faces = []
+    for ax in range(3):
+        u, v = [k for k in range(3) if k != ax]
+        for sgn in (-1.0, 1.0):
+            fc = c.copy()
+            fc[ax] += sgn * h[ax]
+            facing = _AXES[ax] * (sgn if not inward else -sgn)
+            faces.append(_quad(fc, _AXES[u] * h[u], _AXES[v] * h[v], facing,
+                               tess[u], tess[v]))
+    return faces
+
+
+def _look_camera(pos, target, width, height, vfov_deg=90.0) -> Camera:
+    pos = np.asarray(pos, np.float64)
+    fwd = np.asarray(target, np.float64) - pos
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, [0.0, 1.0, 0.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    return Camera(pos.astype(np.float32), fwd.astype(np.float32),
+                  right.astype(np.float32), up.astype(np.float32),
+                  float(math.tan(math.radians(vfov_deg) / 2)), width, height)
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def tiny_room(seed: int = 1, width: int = 128, height: int = 128,
+              frames: int = 16, name: str = "tiny_room") -> Scene:
+    """2 m closed box [-1,1]^3: each of the 6 walls is split into 2 quads
+    (12 quads, 24 triangles).  The x<0 half of the ceiling is the emitter
+    (radiance 10, albedo 0); every other quad has an albedo uniform in
+    [0.2, 0.8]^3.  The camera sits at the room centre looking down -z with a
+    90 degree vertical field of view; the probe grid is 4x4x4."""
+    rng = np.random.default_rng(seed)
+    tris, alb, emi = [], [], []
+    c = np.zeros(3)
+    for ax in range(3):
+        u, v = [k for k in range(3) if k != ax]
+        for sgn in (-1.0, 1.0):
+            facing = -_AXES[ax] * sgn          # into the room
+            for half in (-1.0, 1.0):           # split along axis u
+                qc = c.copy()
+                qc[ax] = sgn
+                qc[u] = 0.5 * half
+                q = _quad(qc, _AXES[u] * 0.5, _AXES[v] * 1.0, facing)
+                is_emitter = (ax == 1 and sgn > 0 and u == 0 and half < 0)
+                a = np.zeros(3) if is_emitter else rng.uniform(0.2, 0.8, 3)
+                e = np.full(3, 10.0) if is_emitter else np.zeros(3)
+                for t in q:
+                    tris.append(t)
+                    alb.append(a)
+                    emi.append(e)
+    verts = np.asarray(tris, np.float32)
+    grid = ProbeGrid(np.full(3, -0.75, np.float32), np.full(3, 0.5, np.float32),
+                     np.array([4, 4, 4], np.int32))
+    cams = [_look_camera([0, 0, 0], [0, 0, -1], width, height) for _ in range(frames)]
+    st = Settings(rays_per_probe=64, spatial_passes=1, seed=seed)
+    return Scene(name, verts, np.asarray(alb, np.float32), np.asarray(emi, np.float32),
+                 grid, cams, st)
+
+
+def tiny_room_1080p(seed: int = 1, frames: int = 32) -> Scene:
+    """The tiny room rendered at 1920x1080 (learned-target workload)."""
+    return tiny_room(seed, 1920, 1080, frames, name="tiny_room_1080p")
+
+
+def apartment(seed: int = 7, width: int = 1920, height: int = 1080,
+              frames: int = 16, target_tris: int = 65536) -> Scene:
+    """Procedural 4-room apartment, 16 m x 12 m x 3 m.
+
+    * shell: floor, ceiling and 4 outer walls facing into the apartment,
+      tessellated so that the whole scene has about ``target_tris`` triangles;
+    * two interior walls (0.2 m thick solids) at x = 8 and z = 6, each with two
+      door openings 1 m wide and 2.1 m high;
+    * 400 furniture boxes (solids) with random sizes and positions, kept out
+      of the camera corridor;
+    * 512 ceiling light panels (0.3 m x 0.3 m, 2 cm below the ceiling, facing
+      down): 1024 emissive triangles whose radiance is log-uniform in
+      [1, 100], albedo 0;
+    * camera starting in the first room at (2, 1.6, 3) looking along +x and
+      slightly toward +z, translating 5 cm per frame along +x;
+    * 16x8x16 probes spanning the apartment.
+    """
+    rng = np.random.default_rng(seed)
+    tris, alb, emi = [], [], []
+
+    def add(tri_list, a, e=(0.0, 0.0, 0.0)):
+        for t in tri_list:
+            tris.append(t)
+            alb.append(np.asarray(a, np.float64))
+            emi.append(np.asarray(e, np.float64))
+
+    X, Y, Z = 16.0, 3.0, 12.0
+    # interior walls with door gaps: list of solid boxes (lo, hi)
+    walls = []
+    t = 0.1
+    # wall at x = 8 along z, doors at z in [2.5,3.5] and [8.5,9.5]
+    for z0, z1 in ((0.0, 2.5), (3.5, 8.5), (9.5, Z)):
+        walls.append(((8 - t, 0, z0), (8 + t, Y, z1)))
+    for z0, z1 in ((2.5, 3.5), (8.5, 9.5)):
+        walls.append(((8 - t, 2.1, z0), (8 + t, Y, z1)))
+    # wall at z = 6 along x, doors at x in [3.5,4.5] and [11.5,12.5]
+    for x0, x1 in ((0.0, 3.5), (4.5, 8 - t), (8 + t, 11.5), (12.5, X)):
+        walls.append(((x0, 0, 6 - t), (x1, Y, 6 + t)))
+    for x0, x1 in ((3.5, 4.5), (11.5, 12.5)):
+        walls.append(((x0, 2.1, 6 - t), (x1, Y, 6 + t)))
+    for lo, hi in walls:
+        a = rng.uniform(0.5, 0.8, 3)
+        for f in _box_faces(lo, hi):
+            add(f, a)
+
+    # furniture: 400 boxes away from the camera corridor (z in [2.2, 3.8])
+    nbox = 0
+    while nbox < 400:
+        sx, sz = rng.uniform(0.3, 1.5, 2)
+        sy = rng.uniform(0.3, 2.0)
+        cx = rng.uniform(0.3 + sx / 2, X - 0.3 - sx / 2)
+        cz = rng.uniform(0.3 + sz / 2, Z - 0.3 - sz / 2)
+        if cz + sz / 2 > 2.2 and cz - sz / 2 < 3.8:
+            continue
+        lo = (cx - sx / 2, 0.0, cz - sz / 2)
+        hi = (cx + sx / 2, sy, cz + sz / 2)
+        a = rng.uniform(0.2, 0.8, 3)
+        for f in _box_faces(lo, hi):
+            add(f, a)
+        nbox += 1
+
+    # ceiling lights: 32 x 16 panels
+    for i in range(32):
+        for j in range(16):
+            cx = (i + 0.5) * X / 32
+            cz = (j + 0.5) * Z / 16
+            q = _quad((cx, Y - 0.02, cz), (0.15, 0, 0), (0, 0, 0.15), (0, -1, 0))
+            for tri in q:
+                le = math.exp(rng.uniform(math.log(1.0), math.log(100.0)))
+                add([tri], (0, 0, 0), (le, le, le))
+
+    # shell: tessellate to reach target_tris
+    remaining = max(target_tris - len(tris), 12)
+    # area-proportional split; faces: floor/ceiling (X*Z each), walls 2*(X*Y) + 2*(Z*Y)
+    total_area = 2 * X * Z + 2 * X * Y + 2 * Z * Y
+    cell = math.sqrt(total_area * 2 / remaining)
+    nx, ny, nz = max(1, int(X / cell)), max(1, int(Y / cell)), max(1, int(Z / cell))
+    shell_alb = [rng.uniform(0.3, 0.8, 3) for _ in range(6)]
+    for k, f in enumerate(_box_faces((0, 0, 0), (X, Y, Z), inward=True, tess=(nx, ny, nz))):
+        add(f, shell_alb[k])
+
+    verts = np.asarray(tris, np.float32)
+    counts = np.array([16, 8, 16], np.int32)
+    spacing = np.array([X / 16, Y / 8, Z / 16], np.float32)
+    grid = ProbeGrid((spacing * 0.5).astype(np.float32), spacing, counts)
+    cams = []
+    for f in range(frames):
+        p = np.array([2.0 + 0.05 * f, 1.6, 3.0])
+        cams.append(_look_camera(p, p + np.array([1.0, -0.15, 0.35]), width, height))
+    st = Settings(rays_per_probe=256, spatial_passes=2, seed=seed)
+    return Scene("apartment", verts, np.asarray(alb, np.float32),
+                 np.asarray(emi, np.float32), grid, cams, st)
+
+
+def make_scene(name: str, **kw) -> Scene:
+    return {"tiny_room": tiny_room, "tiny_room_1080p": tiny_room_1080p,
+            "apartment": apartment}[name](**kw)
+
+
+# ---------------------------------------------------------------------------
+# synthetic per-pixel buffers for pass-isolated tests
+# ---------------------------------------------------------------------------
+
+def _random_surface_points(scene: Scene, n: int, rng, emissive_frac=0.02):
+    """Random triangles and uniform barycentric coordinates (b1, b2)."""
+    emissive = np.flatnonzero(scene.emission.max(axis=1) > 0)
+    plain = np.flatnonzero(scene.emission.max(axis=1) <= 0)
+    use_e = rng.random(n) < emissive_frac if len(emissive) else np.zeros(n, bool)
+    tri = np.where(use_e, rng.choice(emissive, n) if len(emissive) else 0,
+                   rng.choice(plain, n)).astype(np.int64)
+    b1 = rng.random(n)
+    b2 = rng.random(n)
+    flip = b1 + b2 > 1
+    b1[flip], b2[flip] = 1 - b1[flip], 1 - b2[flip]
+    v = scene.verts[tri].astype(np.float64)
+    # keep points strictly inside the triangle
+    b1 = 0.02 + 0.96 * b1
+    b2 = 0.02 + 0.96 * b2
+    s = b1 + b2
+    over = s > 0.98
+    b1[over] *= 0.98 / s[over]
+    b2[over] *= 0.98 / s[over]
+    p = v[:, 0] + b1[:, None] * (v[:, 1] - v[:, 0]) + b2[:, None] * (v[:, 2] - v[:, 0])
+    return tri, p
+
+
+def synthetic_gbuffer(scene: Scene, width: int, height: int, seed: int,
+                      invalid_frac: float = 0.03, motion_frac: float = 0.9):
+    """Random G-buffer planes shaped like the primary-visibility output.
+
+    Every valid pixel holds a point on a random triangle, that triangle's
+    facing normal (the winding normal, passed in as data) and albedo, a
+    camera distance uniform in [0.5, 10] and a previous-frame pixel a few
+    pixels away (or -1).  Returns three float32 arrays of shape [H*W, 4]
+    (pos+dist, normal+tri bits, albedo+prev-pixel bits)."""
+    rng = np.random.default_rng(seed)
+    n = width * height
+    tri, p = _random_surface_points(scene, n, rng)
+    v = scene.verts[tri].astype(np.float64)
+    nrm = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    g0 = np.zeros((n, 4), np.float32)
+    g1 = np.zeros((n, 4), np.float32)
+    g2 = np.zeros((n, 4), np.float32)
+    g0[:, :3] = p
+    g0[:, 3] = rng.uniform(0.5, 10.0, n)
+    g1[:, :3] = nrm
+    tri_u = tri.astype(np.uint32)
+    invalid = rng.random(n) < invalid_frac
+    tri_u[invalid] = 0xFFFFFFFF
+    g1[:, 3] = tri_u.view(np.float32)
+    g2[:, :3] = scene.albedo[tri]
+    px = np.arange(n) % width
+    py = np.arange(n) // width
+    qx = px + rng.integers(-2, 3, n)
+    qy = py + rng.integers(-2, 3, n)
+    ok = (qx >= 0) & (qx < width) & (qy >= 0) & (qy < height) & (rng.random(n) < motion_frac)
+    prev = np.where(ok, qy * width + qx, -1).astype(np.int32)
+    g2[:, 3] = prev.view(np.float32)
+    return g0, g1, g2
+
+
+def synthetic_reservoirs(scene: Scene, n: int, seed: int, empty_frac: float = 0.05):
+    """Random reservoirs: a point y on a random triangle, W log-normal, M in
+    [1, 40], a cached radiance uniform in [0, 5]^3 and a random tag.  Returns
+    (r0 float32[n,4] = y.xyz,W; r1 float32[n,4] = L.rgb,M; r2 uint32[n,2] =
+    y-triangle, tag)."""
+    rng = np.random.default_rng(seed)
+    tri, p = _random_surface_points(scene, n, rng, emissive_frac=0.3)
+    r0 = np.zeros((n, 4), np.float32)
+    r1 = np.zeros((n, 4), np.float32)
+    r2 = np.zeros((n, 2), np.uint32)
+    r0[:, :3] = p
+    r0[:, 3] = np.exp(rng.normal(0.0, 1.0, n))
+    r1[:, :3] = rng.uniform(0.0, 5.0, (n, 3))
+    r1[:, 3] = rng.integers(1, 41, n)
+    r2[:, 0] = tri
+    r2[:, 1] = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    empty = rng.random(n) < empty_frac
+    r0[empty] = 0
+    r1[empty] = 0
+    r2[empty, 0] = 0xFFFFFFFF
+    r2[empty, 1] = 0
+    return r0, r1, r2
+
+
+def synthetic_irradiance_interior(grid: ProbeGrid, n: int, seed: int):
+    """Random positive irradiance for the n x n interior texels of every probe:
+    float32[P, n, n, 3] (row-major: [probe, row, column, rgb])."""
+    rng = np.random.default_rng(seed)
+    P = grid.num_probes
+    base = rng.uniform(0.2, 3.0, (P, 1, 1, 3))
+    var = rng.uniform(0.5, 1.5, (P, n, n, 3))
+    return (base * var).astype(np.float32)
+
+
+def synthetic_depth_interior(grid: ProbeGrid, n: int, seed: int):
+    """Random mean / mean-square distances for the n x n interior depth texels
+    of every probe: float32[P, n, n, 2] with mean in [0.05, 1.5] x max spacing
+    and a non-negative variance."""
+    rng = np.random.default_rng(seed)
+    P = grid.num_probes
+    s = float(np.max(grid.spacing))
+    mu = rng.uniform(0.05, 1.5, (P, n, n)) * s
+    var = rng.uniform(0.0, 0.1, (P, n, n)) * s * s
+    return np.stack([mu, mu * mu + var], axis=-1).astype(np.float32)

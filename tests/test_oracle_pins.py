@@ -1,0 +1,608 @@
+"""Pins of the CPU oracle to facts other than itself (no GPU needed).
+
+Each test checks the oracle against a closed form, an invariant, a textbook
+special case or an independent brute-force computation, so that a plausible
+mistake in the oracle (a dropped term, a wrong sign or index, a transposed
+operand) fails at least one of them.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import scenegen
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def _custom_scene(base, albedo=None, emission=None, settings=None, verts=None, grid=None):
+    return scenegen.Scene(base.name,
+                          base.verts if verts is None else np.asarray(verts, np.float32),
+                          base.albedo if albedo is None else np.asarray(albedo, np.float32),
+                          base.emission if emission is None else np.asarray(emission, np.float32),
+                          base.grid if grid is None else grid,
+                          base.cameras,
+                          settings or base.settings)
+
+
+def _icosphere(r, subdiv=4):
+    """Triangulated sphere of radius r with normals pointing inward."""
+    t = (1 + 5 ** 0.5) / 2
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t),
+         (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    v = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    tris = [[v[a], v[b], v[c]] for a, b, c in f]
+    for _ in range(subdiv):
+        nt = []
+        for a, b, c in tris:
+            ab, bc, ca = [(p + q) / np.linalg.norm(p + q) for p, q in ((a, b), (b, c), (c, a))]
+            nt += [[a, ab, ca], [b, bc, ab], [c, ca, bc], [ab, bc, ca]]
+        tris = nt
+    tris = np.asarray(tris) * r
+    # icosahedron faces above are outward-wound; flip to face the centre
+    return tris[:, [0, 2, 1], :]
+
+
+def _rect_form_factor(x0, x1, z0, z1, c):
+    """Form factor from a differential area to a parallel rectangle
+    [x0,x1] x [z0,z1] at height c above it (signed superposition of the
+    corner-rectangle formula, Howell's catalogue)."""
+    def corner(a, b):
+        A, B = a / c, b / c
+        sa, sb = math.sqrt(1 + A * A), math.sqrt(1 + B * B)
+        return (A / sa * math.atan(B / sa) + B / sb * math.atan(A / sb)) / (2 * math.pi)
+    return corner(x1, z1) - corner(x0, z1) - corner(x1, z0) + corner(x0, z0)
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+
+def test_pcg_hash_is_a_permutation_and_uniform(oracle_lib):
+    o = oracle_lib
+    vals = np.array([o.pcg(i) for i in range(1 << 17)], np.uint64)
+    assert len(np.unique(vals)) == len(vals)          # bijection on uint32
+    # chi-square of the top 8 bits of the chained key over many pixels
+    h = np.array([o.rng_u32(1, p, 3, 0, 5, 2) >> 24 for p in range(1 << 16)])
+    cnt = np.bincount(h, minlength=256)
+    exp = len(h) / 256
+    chi2 = ((cnt - exp) ** 2 / exp).sum()
+    assert chi2 < 255 + 5 * math.sqrt(2 * 255)
+    u = np.array([o.rng(7, p, 0, 1, 2, 3) for p in range(4096)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert np.all(np.round(u * 2 ** 24) == u * 2 ** 24)   # 24-bit grid
+
+
+# ---------------------------------------------------------------------------
+# ray casting
+# ---------------------------------------------------------------------------
+
+def test_intersection_axis_rays_hit_walls_at_unit_distance(oracle_lib):
+    o = oracle_lib
+    sc = o.Scene(scenegen.tiny_room())
+    dirs = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1.]])
+    dirs = dirs + 1e-3 * np.array([0.3, 0.2, 0.1])   # stay off the quad seams
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    tri, t = o.intersect(sc, np.zeros((6, 3)), dirs)
+    assert np.all(tri >= 0)
+    ax = np.argmax(np.abs(dirs), axis=1)
+    np.testing.assert_allclose(t, 1.0 / np.abs(dirs[np.arange(6), ax]), rtol=1e-12)
+    n = sc.normals[tri]
+    assert np.all(np.einsum("ij,ij->i", n, dirs) < 0)   # room walls face inward
+
+
+def _numpy_closest_hit(verts, o, d, tmin=1e-4):
+    """Independent closest hit: plane intersection + same-side edge tests."""
+    v0, v1, v2 = verts[:, 0], verts[:, 1], verts[:, 2]
+    N = np.cross(v1 - v0, v2 - v0)
+    best_t = np.full(len(o), np.inf)
+    best_i = np.full(len(o), -1)
+    margin = np.zeros(len(o))
+    for k in range(len(o)):
+        dn = N @ d[k]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.einsum("ij,ij->i", v0 - o[k], N) / dn
+        p = o[k] + t[:, None] * d[k]
+        s0 = np.einsum("ij,ij->i", np.cross(v1 - v0, p - v0), N)
+        s1 = np.einsum("ij,ij->i", np.cross(v2 - v1, p - v1), N)
+        s2 = np.einsum("ij,ij->i", np.cross(v0 - v2, p - v2), N)
+        nn = np.einsum("ij,ij->i", N, N)
+        inside = (s0 >= 0) & (s1 >= 0) & (s2 >= 0) & np.isfinite(t) & (t > tmin)
+        if inside.any():
+            i = np.flatnonzero(inside)[np.argmin(t[inside])]
+            best_t[k], best_i[k] = t[i], i
+            margin[k] = min(s0[i], s1[i], s2[i]) / nn[i]
+    return best_i, best_t, margin
+
+
+def test_intersection_matches_independent_brute_force(oracle_lib):
+    o = oracle_lib
+    ap = scenegen.apartment(width=8, height=8, frames=1)
+    sc = o.Scene(ap)
+    rng = np.random.default_rng(3)
+    n = 96
+    org = np.column_stack([rng.uniform(0.5, 15.5, n), rng.uniform(0.2, 2.8, n), rng.uniform(0.5, 11.5, n)])
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tri, t = o.intersect(sc, org, d)
+    bi, bt, margin = _numpy_closest_hit(ap.verts.astype(np.float64), org, d)
+    clear = margin > 1e-9
+    assert clear.mean() > 0.9
+    np.testing.assert_array_equal(tri[clear], bi[clear])
+    np.testing.assert_allclose(t[clear], bt[clear], rtol=1e-9)
+
+
+def test_emitter_sampling_is_area_proportional(oracle_lib):
+    o = oracle_lib
+    ap = scenegen.apartment(width=8, height=8, frames=1)
+    # scale the panel triangles unevenly so the areas differ
+    v = ap.verts.astype(np.float64).copy()
+    em = np.flatnonzero(ap.emission.max(1) > 0)
+    rng = np.random.default_rng(0)
+    for i in em:
+        c = v[i].mean(0)
+        v[i] = c + (v[i] - c) * rng.uniform(0.5, 1.5)
+    v = v.astype(np.float32).astype(np.float64)
+    sc = o.Scene(_custom_scene(ap, verts=v))
+    area = 0.5 * np.linalg.norm(np.cross(v[em, 1] - v[em, 0], v[em, 2] - v[em, 0]), axis=1)
+    assert sc.area_total == pytest.approx(area.sum(), rel=1e-12)
+    picks = np.array([o.sample_emitter(sc, o.rng(1, k, 0, 0, 0, 0)) for k in range(1 << 18)])
+    assert np.all(np.isin(picks, em))
+    cnt = np.array([(picks == i).sum() for i in em])
+    exp = area / area.sum() * len(picks)
+    chi2 = ((cnt - exp) ** 2 / exp).sum()
+    dof = len(em) - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+# ---------------------------------------------------------------------------
+# probe representation
+# ---------------------------------------------------------------------------
+
+def test_octahedral_round_trip(oracle_lib):
+    o = oracle_lib
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(20000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d[:4] = [[0, 0, 1], [0, 0, -1], [1, 0, 0], [0, -1, 0]]
+    for k in range(len(d)):
+        uv = o.oct_encode(d[k])
+        assert abs(uv[0]) <= 1 and abs(uv[1]) <= 1
+        assert abs(uv[0]) + abs(uv[1]) <= 1 + 1e-12 or d[k, 2] < 0
+        back = o.oct_decode(uv)
+        assert np.linalg.norm(back - d[k]) < 1e-12
+
+
+def test_texel_centres_round_trip(oracle_lib):
+    o = oracle_lib
+    for n in (8, 16):
+        for j in range(n):
+            for i in range(n):
+                d = o.texel_dir(i, j, n)
+                assert abs(np.linalg.norm(d) - 1) < 1e-14
+                uv = o.oct_encode(d)
+                np.testing.assert_allclose(uv, [2 * (i + .5) / n - 1, 2 * (j + .5) / n - 1], atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_border_makes_bilinear_lookup_continuous(oracle_lib, n):
+    """A map holding its own texel directions must reproduce any direction by
+    bilinear lookup within the discretisation error -- also next to the
+    octahedral fold, which only works if the border repeats the right texel."""
+    o = oracle_lib
+    tile = np.zeros((n + 2, n + 2, 3))
+    for j in range(n):
+        for i in range(n):
+            tile[j + 1, i + 1] = o.texel_dir(i, j, n)
+    tile = o.gutter(tile, n)
+    rng = np.random.default_rng(2)
+    d = rng.normal(size=(5000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    err = np.array([np.linalg.norm(o.bilinear(tile, n, x) - x) for x in d])
+    near_fold = np.array([max(abs(o.oct_encode(x))) > 1 - 1.0 / n for x in d])
+    bound = 0.6 * (2.0 / n) ** 1 * 1.2
+    assert err.max() < bound
+    assert err[near_fold].max() < 2 * max(err[~near_fold].max(), 1e-3)
+
+
+def test_spherical_fibonacci_and_rotation(oracle_lib):
+    o = oracle_lib
+    for n in (64, 256):
+        d = np.array([o.sf_dir(i, n) for i in range(n)])
+        np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1, atol=1e-14)
+        np.testing.assert_allclose(d[:, 2], 1 - (2 * np.arange(n) + 1) / n, atol=1e-14)
+        assert np.linalg.norm(d.mean(0)) < 2.0 / n
+    Rs = np.array([o.probe_rotation(1, f) for f in range(4096)])
+    for R in Rs[:64]:
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-12)
+    assert np.abs(Rs.mean(0)).max() < 0.04   # uniform rotations average to 0
+
+
+def test_orthonormal_basis(oracle_lib):
+    o = oracle_lib
+    rng = np.random.default_rng(4)
+    ns = rng.normal(size=(200, 3))
+    ns /= np.linalg.norm(ns, axis=1, keepdims=True)
+    ns[:3] = [[0, 0, 1], [0, 0, -1], [0, 1, 0]]
+    for n in ns:
+        t = o.onb_local_to_world(n, [1, 0, 0])
+        b = o.onb_local_to_world(n, [0, 1, 0])
+        z = o.onb_local_to_world(n, [0, 0, 1])
+        B = np.array([t, b, z])
+        np.testing.assert_allclose(B @ B.T, np.eye(3), atol=1e-12)
+        np.testing.assert_allclose(z, n, atol=1e-14)
+        assert np.linalg.det(B) == pytest.approx(1.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# probe update (Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def _enclosure(L, attenuation=0.0, rays=64):
+    base = scenegen.tiny_room()
+    T = base.num_tris
+    st = dataclasses.replace(base.settings, le_attenuation=attenuation, rays_per_probe=rays)
+    return _custom_scene(base, albedo=np.zeros((T, 3)), emission=np.tile(L, (T, 1)), settings=st)
+
+
+def test_uniform_enclosure_gives_pi_L_after_first_update(oracle_lib):
+    o = oracle_lib
+    L = np.array([1.0, 2.0, 3.0])
+    sc = _enclosure(L)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    o.probe_update(S, vol, 0)
+    inner = vol.irr[:, 1:9, 1:9]
+    np.testing.assert_allclose(inner, np.broadcast_to(np.pi * L, inner.shape), rtol=1e-12)
+    np.testing.assert_allclose(vol.irr, np.broadcast_to(np.pi * L, vol.irr.shape), rtol=1e-12)
+
+
+def test_hysteresis_step_response_closed_form(oracle_lib):
+    o = oracle_lib
+    L1, L2 = np.array([1.0, 1.0, 1.0]), np.array([4.0, 0.5, 2.0])
+    sc1, sc2 = _enclosure(L1), _enclosure(L2)
+    S1, S2 = o.Scene(sc1), o.Scene(sc2)
+    vol = o.Volume(sc1.grid)
+    a = sc1.settings.hysteresis
+    for u in range(10):
+        o.probe_update(S1 if u < 3 else S2, vol, u)
+        exp = np.pi * L1 if u < 3 else np.pi * L2 + (np.pi * L1 - np.pi * L2) * a ** (u - 2)
+        np.testing.assert_allclose(vol.irr[:, 1:9, 1:9], np.broadcast_to(exp, (64, 8, 8, 3)), rtol=1e-12)
+
+
+def _sphere_scene(r, L, attenuation):
+    base = scenegen.tiny_room()
+    v = _icosphere(r)
+    T = len(v)
+    grid = scenegen.ProbeGrid(np.zeros(3, np.float32), np.ones(3, np.float32), np.ones(3, np.int32))
+    st = dataclasses.replace(base.settings, le_attenuation=attenuation, rays_per_probe=256)
+    return _custom_scene(base, verts=v, albedo=np.zeros((T, 3)), emission=np.tile(L, (T, 1)),
+                         settings=st, grid=grid)
+
+
+def test_depth_moments_at_sphere_centre(oracle_lib):
+    o = oracle_lib
+    r = 1.2
+    sc = _sphere_scene(r, np.ones(3), 0.0)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    o.probe_update(S, vol, 0)
+    mu = vol.depth[0, 1:17, 1:17, 0]
+    mu2 = vol.depth[0, 1:17, 1:17, 1]
+    v = sc.verts.astype(np.float64)
+    nrm = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    r_in = np.min(np.abs(np.einsum("ij,ij->i", nrm, v[:, 0])) / np.linalg.norm(nrm, axis=1))
+    r_out = np.linalg.norm(v, axis=2).max()
+    assert r_in > 0.99 * r
+    assert mu.min() >= r_in - 1e-12 and mu.max() <= r_out + 1e-12
+    assert np.abs(mu2 - mu * mu).max() < 1e-3 * r * r
+
+
+def test_le_attenuation_closed_form_in_sphere(oracle_lib):
+    """Second update inside a sphere of radius 1.2 around a probe of unit
+    cell: the backward mean distance (about 1.2) is clipped to the cell
+    boundary 0.5 / max|w|, so each ray's Le is scaled by (t / (t + d))^2."""
+    o = oracle_lib
+    r, L = 1.2, np.array([2.0, 1.0, 0.5])
+    sc = _sphere_scene(r, L, 1.0)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    o.probe_update(S, vol, 0)
+    np.testing.assert_allclose(vol.irr[0, 1:9, 1:9], np.broadcast_to(np.pi * L, (8, 8, 3)), rtol=1e-12)
+    o.probe_update(S, vol, 1)
+    R = 256
+    w = o.probe_ray_dirs(sc.settings.seed, 1, R)
+    _, t = o.intersect(S, np.zeros((R, 3)), w)
+    d = 0.5 / np.abs(w).max(axis=1)
+    att = (t / (t + d)) ** 2
+    a = sc.settings.hysteresis
+    for j in range(8):
+        for i in range(8):
+            dt = o.texel_dir(i, j, 8)
+            c = np.maximum(w @ dt, 0)
+            est = np.pi * L * (c * att).sum() / c.sum()
+            np.testing.assert_allclose(vol.irr[0, j + 1, i + 1], a * np.pi * L + (1 - a) * est, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# probe query (DDGI volume + view-path bias)
+# ---------------------------------------------------------------------------
+
+def test_query_of_constant_field_is_that_constant(oracle_lib):
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    vol = o.Volume(sc.grid)
+    rng = np.random.default_rng(5)
+    E0 = np.array([0.7, 1.3, 2.1])
+    irr = np.broadcast_to(E0, (64, 8, 8, 3))
+    depth = scenegen.synthetic_depth_interior(sc.grid, 16, 3).astype(np.float64)
+    vol.set_interior(irr, depth)
+    for _ in range(300):
+        q = rng.uniform(-1.2, 1.2, 3)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        E, sw = o.ddgi_query(vol, q, n)
+        assert sw > 0
+        np.testing.assert_allclose(E, E0, rtol=1e-12)
+
+
+def test_query_at_a_probe_returns_its_texels(oracle_lib):
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    vol = o.Volume(sc.grid)
+    vol.set_interior(scenegen.synthetic_irradiance_interior(sc.grid, 8, 1),
+                     scenegen.synthetic_depth_interior(sc.grid, 16, 2))
+    rng = np.random.default_rng(6)
+    for p in [0, 21, 42, 63]:
+        i, j, k = p % 4, (p // 4) % 4, p // 16
+        P = sc.grid.origin.astype(np.float64) + sc.grid.spacing * np.array([i, j, k])
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        E, _ = o.ddgi_query(vol, P, n)
+        np.testing.assert_allclose(E, o.bilinear(vol.irr[p], 8, n), rtol=1e-12)
+
+
+def test_chebyshev_weight_is_one_inside_the_mean_distance(oracle_lib):
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    irr = scenegen.synthetic_irradiance_interior(sc.grid, 8, 1)
+    rng = np.random.default_rng(7)
+    big = np.zeros((64, 16, 16, 2))
+    big[..., 0] = 10.0
+    v1, v2 = o.Volume(sc.grid), o.Volume(sc.grid)
+    b2 = big.copy()
+    b2[..., 1] = rng.uniform(0, 50, (64, 16, 16))   # any second moment
+    v1.set_interior(irr, big)
+    v2.set_interior(irr, b2)
+    for _ in range(100):
+        q = rng.uniform(-0.9, 0.9, 3)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        np.testing.assert_array_equal(o.ddgi_query(v1, q, n)[0], o.ddgi_query(v2, q, n)[0])
+
+
+def test_probes_on_the_normal_side_dominate(oracle_lib):
+    """Probes the surface faces must outweigh probes behind it: with the
+    upper probe layer at E = 1 and the lower at E = 100, an upward-facing
+    query halfway between them must stay much closer to 1."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    irr = np.ones((64, 8, 8, 3))
+    for p in range(64):
+        if (p // 4) % 4 == 1:       # layer j = 1 (y = -0.25) is below the query
+            irr[p] = 100.0
+    depth = np.zeros((64, 16, 16, 2))
+    depth[..., 0], depth[..., 1] = 10.0, 100.0
+    v = o.Volume(sc.grid)
+    v.set_interior(irr, depth)
+    up = o.ddgi_query(v, np.array([0.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]))[0][0]
+    down = o.ddgi_query(v, np.array([0.0, 0.0, 0.0]), np.array([0.0, -1.0, 0.0]))[0][0]
+    assert up < 30.0 and down > 70.0
+
+
+def test_occluded_probe_is_suppressed(oracle_lib):
+    """A probe whose distance map says every surface is 1 cm away (zero
+    variance) must contribute almost nothing to a query 25 cm away."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    irr = np.ones((64, 8, 8, 3))
+    irr[0] = 100.0
+    depth = np.zeros((64, 16, 16, 2))
+    depth[..., 0], depth[..., 1] = 10.0, 100.0
+    depth_occ = depth.copy()
+    depth_occ[0, ..., 0], depth_occ[0, ..., 1] = 0.01, 1e-4
+    q = np.array([-0.5, -0.5, -0.5])
+    n = np.array([0.0, 1.0, 0.0])
+    v_open, v_occ = o.Volume(sc.grid), o.Volume(sc.grid)
+    v_open.set_interior(irr, depth)
+    v_occ.set_interior(irr, depth_occ)
+    assert o.ddgi_query(v_open, q, n)[0][0] > 5.0
+    assert o.ddgi_query(v_occ, q, n)[0][0] < 1.0 + 1e-6
+
+
+# ---------------------------------------------------------------------------
+# primary visibility
+# ---------------------------------------------------------------------------
+
+def test_gbuffer_closed_form_in_tiny_room(oracle_lib):
+    o = oracle_lib
+    sc = scenegen.tiny_room(width=32, height=32)
+    S = o.Scene(sc)
+    cam = sc.cameras[0]
+    g = o.gbuffer(S, cam, cam)
+    W = H = 32
+    i, j = np.arange(W * H) % W, np.arange(W * H) // W
+    sx = 2 * (i + 0.5) / W - 1
+    sy = 1 - 2 * (j + 0.5) / H
+    assert np.all(g.tri >= 0)
+    np.testing.assert_allclose(g.pos[:, 2], -1.0, atol=1e-12)
+    np.testing.assert_allclose(g.dist, np.sqrt(1 + sx ** 2 + sy ** 2), rtol=1e-12)
+    np.testing.assert_allclose(g.pos[:, 0], sx, atol=1e-12)
+    np.testing.assert_allclose(g.nrm, np.broadcast_to([0, 0, 1.0], g.nrm.shape), atol=1e-12)
+    np.testing.assert_array_equal(g.prev, np.arange(W * H))
+
+
+# ---------------------------------------------------------------------------
+# resampling estimator (Sec. 3.1, 3.5, 3.6, Eq. Algorithm)
+# ---------------------------------------------------------------------------
+
+def _point_gbuffer(o, S, pts, nrm, rho, cam_pos, width=None):
+    n = len(pts)
+    width = width or n
+    g = o.GBuffer(n, width, n // width)
+    tri, t = o.intersect(S, pts + 1e-3 * nrm, -nrm)
+    assert np.all(tri >= 0)
+    g.pos[:] = pts
+    g.nrm[:] = nrm
+    g.alb[:] = rho
+    g.tri[:] = tri
+    g.dist[:] = np.linalg.norm(pts - cam_pos, axis=1)
+    g.prev[:] = np.arange(n)
+    return g
+
+
+@pytest.mark.slow
+def test_direct_light_estimate_matches_form_factor(oracle_lib):
+    """With empty probes, the estimator (candidates + selection + shadow ray)
+    must average to the reflected direct light rho * Le * F, F the closed-form
+    point-to-rectangle form factor of the ceiling emitter."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    pts = np.array([[x, -1.0, z] for x in (-0.8, -0.3, 0.4) for z in (-0.6, 0.1, 0.7)])
+    nrm = np.tile([0.0, 1.0, 0.0], (len(pts), 1))
+    rho = np.tile([0.5, 0.6, 0.7], (len(pts), 1))
+    g = _point_gbuffer(o, S, pts, nrm, rho, np.zeros(3))
+    F = np.array([_rect_form_factor(-1 - p[0], -p[0], -1 - p[2], 1 - p[2], 2.0) for p in pts])
+    exp = rho * 10.0 * F[:, None]
+    N = 3000
+    acc = np.zeros((N, len(pts), 3))
+    for f in range(N):
+        res, resid = o.restir_initial(S, vol, g, f)
+        acc[f] = o.shade(S, vol, g, res, resid)
+    mean, sd = acc.mean(0), acc.std(0) / math.sqrt(N)
+    assert np.all(np.abs(mean - exp) <= 4 * sd + 1e-9), (mean, exp, sd)
+
+
+def test_form_factor_formula_against_quadrature():
+    """The textbook formula used above, checked by midpoint quadrature."""
+    x0, x1, z0, z1, c = -0.7, 0.3, -1.4, 0.6, 2.0
+    n = 1500
+    xs = x0 + (np.arange(n) + 0.5) * (x1 - x0) / n
+    zs = z0 + (np.arange(n) + 0.5) * (z1 - z0) / n
+    X, Z = np.meshgrid(xs, zs)
+    r2 = X ** 2 + Z ** 2 + c * c
+    F = (c * c / (np.pi * r2 ** 2)).sum() * (x1 - x0) * (z1 - z0) / n / n
+    assert _rect_form_factor(x0, x1, z0, z1, c) == pytest.approx(F, rel=1e-5)
+
+
+@pytest.mark.slow
+def test_bounded_plus_residual_matches_bsdf_sampling_near_emitter(oracle_lib):
+    """Points on a side wall just under the emitter see it at G >> 1: the
+    bounded resampled term plus the residual must average to the plain
+    cosine-sampled estimate of the same (probe-augmented) transport."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    for f in range(4):
+        o.probe_update(S, vol, f)
+    pts = np.array([[-1.0, 0.97, -0.5], [-1.0, 0.9, 0.2], [-1.0, 0.8, 0.6]])
+    nrm = np.tile([1.0, 0.0, 0.0], (3, 1))
+    rho = np.tile([0.6, 0.5, 0.4], (3, 1))
+    g = _point_gbuffer(o, S, pts, nrm, rho, np.zeros(3))
+    # brute force: cosine-distributed directions, rho * L(y) per sample
+    rng = np.random.default_rng(9)
+    K = 1 << 17
+    ref = []
+    for p in range(3):
+        u0, u1 = rng.random(K), rng.random(K)
+        r, ph = np.sqrt(u0), 2 * np.pi * u1
+        loc = np.column_stack([r * np.cos(ph), r * np.sin(ph), np.sqrt(1 - u0)])
+        w = np.array([o.onb_local_to_world(nrm[p], l) for l in loc])
+        tri, t = o.intersect(S, np.tile(pts[p], (K, 1)), w)
+        y = pts[p] + t[:, None] * w
+        L = o.radiance(S, vol, y, tri, np.tile(pts[p], (K, 1)))
+        L[tri < 0] = 0
+        v = rho[p] * L
+        ref.append((v.mean(0), v.std(0) / math.sqrt(K)))
+    N = 3000
+    acc = np.zeros((N, 3, 3))
+    for f in range(N):
+        res, resid = o.restir_initial(S, vol, g, 100 + f)
+        acc[f] = o.shade(S, vol, g, res, resid)
+    mean, sd = acc.mean(0), acc.std(0) / math.sqrt(N)
+    for p in range(3):
+        tol = 4 * np.sqrt(sd[p] ** 2 + ref[p][1] ** 2)
+        assert np.all(np.abs(mean[p] - ref[p][0]) <= tol), (p, mean[p], ref[p])
+
+
+@pytest.mark.slow
+def test_temporal_and_spatial_reuse_keep_the_estimate_unbiased(oracle_lib):
+    """An 8x8 image whose pixels all see the same floor point: with equal
+    target functions, merging reservoirs across pixels and frames must not
+    change the expectation (still rho * Le * F)."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    p = np.array([-0.3, -1.0, 0.2])
+    n = 64
+    cam = np.array([-0.3, 1.0, 0.2])
+    g = _point_gbuffer(o, S, np.tile(p, (n, 1)), np.tile([0, 1.0, 0], (n, 1)),
+                       np.tile([0.5, 0.5, 0.5], (n, 1)), cam, width=8)
+    F = _rect_form_factor(-1 - p[0], -p[0], -1 - p[2], 1 - p[2], 2.0)
+    exp = 0.5 * 10.0 * F
+    T = 700
+    acc = np.zeros((T, 3))
+    for k in range(T):
+        f0, f1 = 2 * k, 2 * k + 1
+        prev, _ = o.restir_initial(S, vol, g, f0)
+        prev.M[:] = 5000.0                         # exercises the M cap
+        cur, resid = o.restir_initial(S, vol, g, f1)
+        tmp = o.restir_temporal(S, g, g, cam, cur, prev, f1)
+        assert np.all(tmp.M <= cur.M * (1 + sc.settings.temporal_mcap) + 1e-9)
+        res = o.restir_spatial(S, g, tmp, f1, 0)
+        acc[k] = o.shade(S, vol, g, res, resid).mean(0)
+    mean, sd = acc.mean(0), acc.std(0) / math.sqrt(T)
+    assert np.all(np.abs(mean - exp) <= 4 * sd), (mean, exp, sd)
+
+
+def test_reservoir_merge_special_case(oracle_lib):
+    """Two reservoirs with equal target: the merged W equals the M-weighted
+    mean of the input W (target cancels), and M adds up (no cap hit)."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    pts = np.array([[0.0, -1.0, 0.0]] * 2)
+    g = _point_gbuffer(o, S, pts, np.tile([0, 1.0, 0], (2, 1)), np.tile([0.5] * 3, (2, 1)),
+                       np.array([0.0, 1.0, 0.0]), width=2)
+    cur = o.Reservoirs(2)
+    prev = o.Reservoirs(2)
+    ytri, _ = o.intersect(S, np.array([[-0.5, 0.5, 0.0]]), np.array([[0, 1.0, 0]]))
+    for r, W, M in ((cur, 0.8, 32.0), (prev, 2.0, 100.0)):
+        r.y[:] = [-0.5, 1.0, 0.0]
+        r.L[:] = 10.0
+        r.tri[:] = ytri[0]
+        r.W[:] = W
+        r.M[:] = M
+        r.tag[:] = 7 if r is cur else 9
+    out = o.restir_temporal(S, g, g, np.array([0.0, 1.0, 0.0]), cur, prev, 3)
+    np.testing.assert_allclose(out.M, 132.0)
+    np.testing.assert_allclose(out.W, (0.8 * 32 + 2.0 * 100) / 132.0, rtol=1e-12)
+
+
+def test_mape_definition():
+    import oracle
+    ref = np.array([0.0, 1.0, 2.0])
+    v = np.array([0.01, 1.5, 1.0])
+    assert oracle.mape(v, ref) == pytest.approx((0.01 / 0.01 + 0.5 / 1.01 + 1.0 / 2.01) / 3)
+    assert oracle.mse(v, ref) == pytest.approx((1e-4 + 0.25 + 1.0) / 3)
