@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Benchmark of one frame of DDGI resampling (probe update + initial +
+temporal + spatial passes + shade) at 1920x1080 on the 64k-triangle
+apartment, timed on the device with CUDA events.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (fp64 brute force, one thread) on a
+bounded sample of the same workload and extrapolates to ms per frame.
+With N > 1 (torchrun) every rank renders its own replica of the workload;
+there is no data exchange between ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("apartment-1080p: 65,180 triangles (400 boxes, walls with doors), 1024 emissive "
+            "triangles, 1920x1080, 16x8x16 probes x 256 rays, 8x8 irradiance / 16x16 distance "
+            "texels, 31 emitter + 1 BSDF candidates, temporal (M cap 20) + 2 spatial passes x 5 "
+            "neighbours (30 px)")
+METRIC = "ms/frame 1080p ReSTIR+DDGI (% HBM roofline); MSE at equal time, MLP vs probes"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames", type=int, default=16)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2108_05263_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
+            return float(parts[2])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per pixel of each pass (compulsory HBM traffic)
+# ---------------------------------------------------------------------------
+# G-buffer 48 B/px (3 x 16 B), reservoir 40 B/px (16 + 16 + 8), residual and
+# radiance 16 B/px.  Neighbour reads of the spatial pass and BVH / probe-map
+# reads are cache traffic (the scene, BVH and maps are ~12 MB, L2-resident).
+BYTES_PER_PX = {
+    "restir_initial": 48 + 40 + 16,            # G in; reservoir + residual out
+    "restir_temporal": 40 + 48 + 32 + 40 + 40,  # cur res, G, prev G (g0,g1), prev res; out
+    "restir_spatial": 40 + 48 + 40,            # own res, G; out
+    "ddgi_shade": 48 + 24 + 16 + 16,           # G, res (r0, r2), residual; radiance out
+}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import scenegen
+    from paper_2108_05263_gb300 import build, ddgi
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    ddgi.load()
+    sc = scenegen.apartment(frames=args.frames)
+    st = sc.settings
+    ctx = ddgi.Context.from_scene(sc)
+    W, H = 1920, 1080
+    N = W * H
+    stream = torch.cuda.current_stream(dev)
+    # primary visibility for every camera of the path (support pass, outside the timed frame)
+    gbufs = []
+    prev = None
+    for f in range(args.frames):
+        g = ddgi.GBuffer(W, H, dev)
+        ctx.gbuffer(sc.cameras[f], prev, g, stream)
+        prev = sc.cameras[f]
+        gbufs.append(g)
+    gb_ms = None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gtmp = ddgi.GBuffer(W, H, dev)
+    ev0.record(stream)
+    for f in range(4):
+        ctx.gbuffer(sc.cameras[f + 1], sc.cameras[f], gtmp, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gb_ms = ev0.elapsed_time(ev1) / 4
+
+    fr = ddgi.Frame(ctx, W, H, st.spatial_passes, dev)
+    passes = ["probe_update", "restir_initial", "restir_temporal"] + \
+             [f"restir_spatial{i}" for i in range(st.spatial_passes)] + ["ddgi_shade"]
+
+    def step(k, evs=None):
+        f = k
+        cam = sc.cameras[f % args.frames]
+        g = gbufs[f % args.frames]
+        # one frame, pass by pass (same calls as Frame.render, with events between passes)
+        e = iter(evs) if evs else None
+
+        def mark():
+            if e is not None:
+                next(e).record(stream)
+
+        mark()
+        ctx.probe_update(f, stream)
+        mark()
+        init, tmp = fr._free_pair()
+        ctx.restir_initial(g, init, fr.resid, f, stream)
+        mark()
+        res = init
+        if fr.prev_final is not None:
+            ctx.restir_temporal(g, fr._prev_g, fr.prev_cam.pos, init, fr.prev_final, tmp, f, stream)
+            res = tmp
+        mark()
+        for i in range(st.spatial_passes):
+            nxt = fr._other(res)
+            ctx.restir_spatial(g, res, nxt, f, i, stream)
+            res = nxt
+            mark()
+        ctx.shade(g, res, fr.resid, fr.radiance, stream)
+        mark()
+        fr.prev_final, fr._prev_g, fr.prev_cam = res, g, cam
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)] for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    for k in range(K):
+        step(args.warmup + k, evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = t0.elapsed_time(t1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per_pass = {p: 0.0 for p in passes}
+    for k in range(K):
+        for i, p in enumerate(passes):
+            per_pass[p] += evs[k][i].elapsed_time(evs[k][i + 1]) / K
+    status = ctx.get_status(stream)
+
+    hbm, peak_kind = peaks()
+    pass_report = {}
+    for p, ms in per_pass.items():
+        key = "restir_spatial" if p.startswith("restir_spatial") else p
+        entry = {"ms": round(ms, 4)}
+        if key in BYTES_PER_PX:
+            gbs = BYTES_PER_PX[key] * N / (ms * 1e-3) / 1e9
+            entry.update({"bytes": BYTES_PER_PX[key] * N, "gbs": round(gbs, 1),
+                          "hbm_frac": round(gbs / hbm, 4)})
+        pass_report[p] = entry
+    # roofline of the dominant kernel
+    dom = max(per_pass, key=per_pass.get)
+    dom_key = "restir_spatial" if dom.startswith("restir_spatial") else dom
+    if dom_key in BYTES_PER_PX:
+        achieved = BYTES_PER_PX[dom_key] * N / (per_pass[dom] * 1e-3) / 1e9
+        kernel = {"restir_initial": "k_restir_initial", "restir_temporal": "k_restir_temporal",
+                  "restir_spatial": "k_restir_spatial", "ddgi_shade": "k_shade"}[dom_key]
+        roof = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": ncu_traffic(kernel),
+                "note": "algorithmic bytes = compulsory per-pixel plane traffic; ray traversal of "
+                        "this kernel is L2/latency-bound, see the per-pass list"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None}
+
+    ms_frame = total_ms / K
+    value = total_ms / (K * ws)
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": ws,
+           "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_frame, 4),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded procedural apartment standing in for the paper's scenes)",
+           "config": {"workload": WORKLOAD, "l2": "inputs larger than L2: 16 distinct 1080p "
+                      "G-buffers (0.8 GB) cycled; ~0.8 GB of per-pixel planes touched per frame",
+                      "parallelism": "replicas" if ws > 1 else "single GPU",
+                      "gbuffer_ms_untimed": round(gb_ms, 4)},
+           "passes": pass_report, "roofline": roof, "clocks": clocks,
+           "gpu_launches": K * (len(passes) + 1), "device_status": int(status)}
+
+    # end to end through the public API: host G-buffer in, radiance out
+    if not args.no_e2e:
+        host = [[t.cpu().pin_memory() for t in (g.g0, g.g1, g.g2)] for g in gbufs]
+        dg = ddgi.GBuffer(W, H, dev)
+        out_host = torch.empty((N, 4), dtype=torch.float32).pin_memory()
+        fr2 = ddgi.Frame(ctx, W, H, st.spatial_passes, dev)
+
+        def e2e_step(k):
+            f = k % args.frames
+            for d, h in zip((dg.g0, dg.g1, dg.g2), host[f]):
+                d.copy_(h, non_blocking=True)
+            rad = fr2.render(k, sc.cameras[f], gbuf=dg, stream=stream)
+            out_host.copy_(rad, non_blocking=True)
+
+        for k in range(3):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        Ke = max(10, min(K, 50))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(Ke):
+            e2e_step(3 + k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out["e2e"] = {"value": round(a.elapsed_time(b) / Ke, 4), "unit": "ms/frame",
+                      "h2d_bytes_per_step": 48 * N, "d2h_bytes_per_step": 16 * N,
+                      "path": "Frame.render through the C ABI, pinned host G-buffer in, radiance out"}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(sc, budget_s=12.0)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+class OracleSample:
+    """The oracle (fp64 brute force, one thread) on bounded samples of the
+    1080p frame: per-pixel time of initial + temporal + spatial passes +
+    shade on random pixels of a synthetic G-buffer, per-probe time of trace +
+    blend on random probes; extrapolated to a whole frame."""
+
+    def __init__(self, sc):
+        import oracle
+        import scenegen
+        oracle.build()
+        self.o, self.sc = oracle, sc
+        self.S = oracle.Scene(sc)
+        self.W, self.H = 1920, 1080
+        self.rng = np.random.default_rng(5)
+        vol = oracle.Volume(sc.grid)
+        vol.set_interior(scenegen.synthetic_irradiance_interior(sc.grid, 8, 5),
+                         scenegen.synthetic_depth_interior(sc.grid, 16, 6))
+        vol.updates = 3
+        self.vol = vol
+        gp = scenegen.synthetic_gbuffer(sc, self.W, self.H, 21)
+        self.g = oracle.GBuffer.from_planes(*gp, self.W, self.H)
+        self.res = oracle.Reservoirs.from_planes(*scenegen.synthetic_reservoirs(sc, self.W * self.H, 31))
+        self.zero_resid = np.zeros((self.W * self.H, 3))
+
+    def pixels(self, npix):
+        o, S, g, res = self.o, self.S, self.g, self.res
+        pix = self.rng.choice(self.W * self.H, npix, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        o.restir_initial(S, self.vol, g, 1, pix=pix)
+        o.restir_temporal(S, g, g, np.array([4.0, 1.5, 6.0]), res, res, 1, pix=pix)
+        for i in range(self.sc.settings.spatial_passes):
+            o.restir_spatial(S, g, res, 1, i, pix=pix)
+        o.shade(S, self.vol, g, res, self.zero_resid, pix=pix)
+        return (time.perf_counter() - t0) / npix
+
+    def probes(self, nprobes):
+        o = self.o
+        probes = self.rng.choice(self.sc.grid.num_probes, nprobes, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        rays = o.probe_trace(self.S, self.vol, 1, probes=probes)
+        v2 = self.vol.copy()
+        o.probe_blend(v2, rays, 1, self.S.settings, probes=probes)
+        return (time.perf_counter() - t0) / nprobes
+
+    def frame_ms(self, t_px, t_pr):
+        return (t_px * self.W * self.H + t_pr * self.sc.grid.num_probes) * 1e3
+
+
+def cpu_baseline(sc, budget_s=12.0):
+    s = OracleSample(sc)
+    est = s.pixels(8)
+    npix = int(max(16, min(4096, 0.6 * budget_s / max(est, 1e-6))))
+    t_px = s.pixels(npix)
+    nprobes = int(max(1, min(16, 0.3 * budget_s / max(256 * est / 2, 1e-6))))
+    t_pr = s.probes(nprobes)
+    return {"value": round(s.frame_ms(t_px, t_pr), 1), "unit": "ms/frame", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{npix} random pixels of a synthetic 1080p G-buffer (initial + temporal + "
+                      f"{sc.settings.spatial_passes} spatial + shade) and {nprobes} probes (trace + "
+                      f"blend) of the apartment, extrapolated to 2,073,600 pixels + "
+                      f"{sc.grid.num_probes} probes",
+            "per_pixel_ms": round(t_px * 1e3, 4), "per_probe_ms": round(t_pr * 1e3, 3)}
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: every step is a bounded sample of the
+    frame (32 pixels + 1 probe), extrapolated to ms per 1080p frame."""
+    if rank != 0:
+        return
+    import scenegen
+    sc = scenegen.apartment(frames=1)
+    s = OracleSample(sc)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v = s.frame_ms(s.pixels(32), s.probes(1))
+        if k >= args.warmup:
+            vals.append(v)
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms/frame",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": round(v, 1), "unit": "ms/frame", "cores": 1, "kind": "oracle",
+                            "sample": "per step: 32 random pixels (initial + temporal + spatial + "
+                                      "shade) and 1 probe (trace + blend), extrapolated to a frame"},
+           "e2e": {"value": round(v, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

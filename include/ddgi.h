@@ -1,0 +1,197 @@
+/* ddgi.h -- C ABI of the GB300 DDGI-resampling library (libddgi.so).
+ *
+ * The library implements, as CUDA kernels for sm_103a, the per-frame path of
+ * "Dynamic Diffuse Global Illumination Resampling" (Majercik et al., arXiv
+ * 2108.05263): the augmented probe update of Sec. 3.2, the unified candidate
+ * generation and reservoir resampling of Sec. 3.1 (with the bounded geometry
+ * term and residual of Sec. 3.5 and the cached probe queries of Sec. 3.6),
+ * and the shading estimator of Eq. Algorithm.
+ *
+ * General rules
+ *  - Every function returns a ddgi_status (0 = success, negative = error).
+ *  - Pointers marked "device" must be CUDA device (or managed) memory owned by
+ *    the caller; "host" pointers are ordinary host memory.  The library never
+ *    frees caller memory.
+ *  - Per-pixel planes are arrays of 4-float (16-byte) records, one per pixel
+ *    in row-major order (pixel = y * width + x), 16-byte aligned; the
+ *    reservoir index plane r2 holds 2 uint32 per pixel, 8-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work and return without synchronising, except
+ *    ddgi_get_status and the *_get functions, which synchronise `stream`.
+ *  - Argument errors (NULL, misalignment, size mismatch, out-of-range
+ *    configuration) are detected on the host before anything is enqueued and
+ *    return DDGI_ERR_INVALID_ARG.  Launch failures return DDGI_ERR_CUDA with
+ *    the CUDA message available from ddgi_last_error.  Device-side limits
+ *    (traversal iteration cap, traversal stack overflow) set an error word
+ *    that ddgi_get_status reports; a kernel that hits one returns "no hit"
+ *    for that ray and the frame continues.
+ *  - A context is not thread-safe; use one per host thread or serialise.
+ */
+#ifndef DDGI_H
+#define DDGI_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ddgi_status;
+#define DDGI_OK 0
+#define DDGI_ERR_INVALID_ARG (-1)
+#define DDGI_ERR_CUDA (-2)
+#define DDGI_ERR_NOT_READY (-3)
+#define DDGI_ERR_TRAVERSAL_LIMIT (-4)
+#define DDGI_ERR_BOUNDS (-5)
+#define DDGI_ERR_OOM (-6)
+
+typedef struct ddgi_ctx ddgi_ctx;
+
+/* Scene: a triangle soup (host memory, copied at ddgi_create).  The facing
+ * side of triangle i is the side its winding normal cross(v1-v0, v2-v0)
+ * points to; emission is one-sided (Sec. 3.1 treats every surface as a light
+ * source; emitters here are pure emitters with albedo 0). */
+typedef struct {
+    uint32_t num_tris;
+    const float* vertices;   /* host [num_tris][3][3] */
+    const float* albedo;     /* host [num_tris][3]  diffuse albedo rho */
+    const float* emission;   /* host [num_tris][3]  emitted radiance Le */
+} ddgi_scene;
+
+/* Method parameters.  Probe volume: a counts[0] x counts[1] x counts[2] grid,
+ * probe (i,j,k) at origin + spacing * (i,j,k) + its relocation offset. */
+typedef struct {
+    float origin[3];
+    float spacing[3];
+    int32_t counts[3];
+    uint32_t rays_per_probe;      /* 1..1024 (Sec. 3.2 update rays) */
+    uint32_t irr_texels;          /* octahedral irradiance map side, 2..32 */
+    uint32_t depth_texels;        /* octahedral distance-moment map side, 2..32 */
+    float hysteresis;             /* blend weight of the old value, [0, 1) */
+    float le_attenuation;         /* slider s of Sec. 3.2; 0 disables */
+    float depth_sharpness;        /* cosine exponent of the distance blend */
+    uint32_t num_light_candidates;/* emitter candidates per pixel (Sec. 3.1) */
+    uint32_t num_bsdf_candidates; /* BSDF candidates per pixel; sum <= 64 */
+    float temporal_mcap;          /* temporal M cap, multiple of current M */
+    uint32_t spatial_neighbours;  /* neighbours per spatial pass, <= 32 */
+    uint32_t spatial_radius;      /* pixels, 1..255 */
+    float normal_reject_cos;      /* reuse only if dot(n, n') > this */
+    float depth_reject_frac;      /* ... and |d - d'| <= this * d */
+    uint32_t seed;
+} ddgi_config;
+
+/* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */
+typedef struct {
+    float pos[3], fwd[3], right[3], up[3];
+    float tan_half_fovy;
+    uint32_t width, height;
+} ddgi_camera;
+
+/* G-buffer planes (device): g0 = position.xyz, distance to camera;
+ * g1 = normal.xyz, triangle index (uint32 bits, 0xFFFFFFFF = no valid
+ * front-facing hit); g2 = albedo.rgb, previous-frame pixel (int32 bits, -1 =
+ * none). */
+typedef struct {
+    float* g0;
+    float* g1;
+    float* g2;
+    uint32_t width, height;
+} ddgi_gbuf;
+
+/* Reservoirs (device): r0 = y.xyz, W; r1 = cached radiance L(y).rgb, M;
+ * r2 = triangle of y (0xFFFFFFFF = empty), tag (origin pixel * 64 +
+ * candidate index). */
+typedef struct {
+    float* r0;
+    float* r1;
+    uint32_t* r2;
+    uint32_t num_pixels;
+} ddgi_reservoirs;
+
+typedef struct {
+    uint32_t num_tris, num_emitters, num_probes, rays_per_probe;
+    uint32_t irr_tile, depth_tile;   /* padded map side (texels + 2) */
+    uint32_t bvh_nodes, bvh_depth;
+    uint32_t updates;                /* completed probe updates */
+    uint64_t device_bytes;           /* device memory held by the context */
+} ddgi_info;
+
+/* Build the context: copies the scene, builds a 4-wide BVH on the host
+ * (binned SAH) and uploads it, builds the emitter area table, allocates the
+ * probe maps (zero) and the probe ray buffer.  Synchronous. */
+ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ctx** out);
+ddgi_status ddgi_destroy(ddgi_ctx* ctx);
+ddgi_status ddgi_get_info(ddgi_ctx* ctx, ddgi_info* out);
+
+/* Sec. 3.2, Eq. probeUpdate: trace rays_per_probe rays from every probe
+ * (spherical Fibonacci set under a per-frame random rotation), radiance at the
+ * hit = Le attenuated by (t / (t + s d_back))^2 + rho / pi * E at the
+ * view-path-biased hit point (previous maps); then blend irradiance and
+ * distance moments per texel with hysteresis and refresh the map borders.
+ * ddgi_probe_update = ddgi_probe_trace + ddgi_probe_blend. */
+ddgi_status ddgi_probe_update(ddgi_ctx* ctx, uint32_t frame, void* stream);
+ddgi_status ddgi_probe_trace(ddgi_ctx* ctx, uint32_t frame, void* stream);
+ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream);
+
+/* Probe state transfer (host or device pointers; synchronises the stream):
+ * irr [P][irr_tile^2][4] floats (rgb, 0), depth [P][depth_tile^2][2],
+ * offsets [P][4] (xyz, 0), rays [P][rays_per_probe][4] (L.rgb, signed
+ * distance: +t front hit, -t back hit, 1e30 miss).  NULL skips a buffer. */
+ddgi_status ddgi_probe_state_get(ddgi_ctx* ctx, float* irr, float* depth, float* offsets,
+                                 uint32_t* updates, void* stream);
+ddgi_status ddgi_probe_state_set(ddgi_ctx* ctx, const float* irr, const float* depth,
+                                 const float* offsets, uint32_t updates, void* stream);
+ddgi_status ddgi_probe_rays_get(ddgi_ctx* ctx, float* rays, void* stream);
+ddgi_status ddgi_probe_rays_set(ddgi_ctx* ctx, const float* rays, void* stream);
+
+/* Primary visibility (support pass, the paper rasterises it): one pinhole
+ * ray per pixel centre; prev_cam (nullable) gives the previous-frame pixel of
+ * each hit.  out->width/height must equal cam->width/height. */
+ddgi_status ddgi_gbuffer(ddgi_ctx* ctx, const ddgi_camera* cam, const ddgi_camera* prev_cam,
+                         const ddgi_gbuf* out, void* stream);
+
+/* Sec. 3.1 steps 1-2 and Sec. 3.5: per valid pixel x, num_light_candidates
+ * area-uniform emitter points and num_bsdf_candidates cosine-distributed rays
+ * (the BSDF hit's radiance (Le + L_DDGI+) is queried once and cached in the
+ * reservoir), weighted by target / mixture density in area measure; one is
+ * kept by weighted reservoir sampling, W = w_sum / (M target(y)).  residual
+ * (device [N][4]) receives the BSDF-ray estimate rho_x L(y) max(0, 1 - 1/G)
+ * of the residual transport. */
+ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* out,
+                           float* residual, uint32_t frame, void* stream);
+
+/* Sec. 3.1 step 2 (temporal): merge each pixel's reservoir with that of its
+ * previous-frame pixel if the normals (cos > normal_reject_cos) and the
+ * distances (within depth_reject_frac) agree; the previous M is capped at
+ * temporal_mcap times the current M; targets use the cached radiance
+ * (Sec. 3.6).  prev_cam_pos: host float[3], the previous camera position.
+ * out must not alias cur or prev. */
+ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_gbuf* g_prev,
+                            const float* prev_cam_pos, const ddgi_reservoirs* cur,
+                            const ddgi_reservoirs* prev, const ddgi_reservoirs* out,
+                            uint32_t frame, void* stream);
+
+/* Sec. 3.1 step 2 (spatial): merge with spatial_neighbours reservoirs drawn in
+ * a disk of spatial_radius pixels, with the same rejection and cached
+ * radiance.  `pass` (0-based) keys the random numbers.  out must not alias
+ * in. */
+ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* in,
+                           const ddgi_reservoirs* out, uint32_t frame, uint32_t pass,
+                           void* stream);
+
+/* Sec. 3.1 steps 3-4, Eq. Algorithm: radiance (device [N][4], rgb, 1) = Le(x)
+ * + residual + (if the shadow ray to y is clear) rho_x / pi (Le +
+ * L_DDGI+)(y) min(G, 1) W, with a fresh probe query at y. */
+ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* r,
+                       const float* residual, float* radiance, void* stream);
+
+/* Synchronise `stream`, return (and clear) the device error word:
+ * DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded the node-visit cap or the
+ * traversal stack, else DDGI_OK. */
+ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream);
+const char* ddgi_last_error(ddgi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

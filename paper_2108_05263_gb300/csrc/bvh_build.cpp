@@ -1,0 +1,276 @@
+// Host BVH construction: binned surface-area-heuristic binary BVH, collapsed
+// into 4-wide nodes whose children boxes are stored as SoA float4 rows so
+// that one node is eight 16-byte loads on the device.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bvh.h"
+
+namespace {
+
+struct Box {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX};
+    float hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    void grow(const float* p) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], p[a]);
+            hi[a] = std::max(hi[a], p[a]);
+        }
+    }
+    void grow(const Box& b) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], b.lo[a]);
+            hi[a] = std::max(hi[a], b.hi[a]);
+        }
+    }
+    float area() const {
+        float d[3];
+        for (int a = 0; a < 3; ++a) d[a] = std::max(hi[a] - lo[a], 0.f);
+        return 2.f * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0]);
+    }
+    bool valid() const { return lo[0] <= hi[0]; }
+};
+
+struct BNode {
+    Box box;
+    int left = -1, right = -1;   // children (binary), -1 for leaves
+    int first = 0, count = 0;    // leaf range in the index array
+};
+
+constexpr int kBins = 16;
+constexpr int kMaxLeaf = 4;
+
+struct Builder {
+    const float* verts;
+    std::vector<Box> tbox;
+    std::vector<float> cent;     // 3 per triangle
+    std::vector<int> idx;
+    std::vector<BNode> nodes;
+
+    int make_leaf(int first, int count, const Box& b) {
+        BNode n;
+        n.box = b;
+        n.first = first;
+        n.count = count;
+        nodes.push_back(n);
+        return (int)nodes.size() - 1;
+    }
+
+    // iterative top-down build; returns root index
+    int build(int T) {
+        struct Item {
+            int first, count, parent, side;
+        };
+        std::vector<Item> work;
+        work.push_back({0, T, -1, 0});
+        int root = -1;
+        while (!work.empty()) {
+            Item it = work.back();
+            work.pop_back();
+            Box b, cb;
+            for (int k = it.first; k < it.first + it.count; ++k) {
+                b.grow(tbox[idx[k]]);
+                cb.grow(&cent[3 * idx[k]]);
+            }
+            int self;
+            int split_axis = -1, split_bin = -1;
+            if (it.count > 2) {
+                float best = FLT_MAX;
+                for (int a = 0; a < 3; ++a) {
+                    float ext = cb.hi[a] - cb.lo[a];
+                    if (!(ext > 0.f)) continue;
+                    Box bb[kBins];
+                    int bc[kBins] = {0};
+                    float scale = kBins / ext;
+                    for (int k = it.first; k < it.first + it.count; ++k) {
+                        int t = idx[k];
+                        int bi = std::min(kBins - 1, (int)((cent[3 * t + a] - cb.lo[a]) * scale));
+                        bc[bi]++;
+                        bb[bi].grow(tbox[t]);
+                    }
+                    float la[kBins], ra[kBins];
+                    int lc[kBins], rc[kBins];
+                    Box acc;
+                    int n = 0;
+                    for (int i = 0; i < kBins; ++i) {
+                        acc.grow(bb[i]);
+                        n += bc[i];
+                        la[i] = acc.area();
+                        lc[i] = n;
+                    }
+                    acc = Box();
+                    n = 0;
+                    for (int i = kBins - 1; i >= 0; --i) {
+                        acc.grow(bb[i]);
+                        n += bc[i];
+                        ra[i] = acc.area();
+                        rc[i] = n;
+                    }
+                    for (int i = 0; i < kBins - 1; ++i) {
+                        if (lc[i] == 0 || rc[i + 1] == 0) continue;
+                        float c = la[i] * lc[i] + ra[i + 1] * rc[i + 1];
+                        if (c < best) {
+                            best = c;
+                            split_axis = a;
+                            split_bin = i;
+                        }
+                    }
+                }
+                float leaf_cost = b.area() * it.count;
+                float sah = 0.5f * b.area() + best;   // traversal cost of one node
+                if (split_axis >= 0 && it.count <= kMaxLeaf && sah >= leaf_cost) split_axis = -1;
+            }
+            int mid = -1;
+            if (split_axis >= 0) {
+                float ext = cb.hi[split_axis] - cb.lo[split_axis];
+                float scale = kBins / ext;
+                auto beg = idx.begin() + it.first, end = beg + it.count;
+                auto m = std::partition(beg, end, [&](int t) {
+                    int bi = std::min(kBins - 1, (int)((cent[3 * t + split_axis] - cb.lo[split_axis]) * scale));
+                    return bi <= split_bin;
+                });
+                mid = (int)(m - idx.begin());
+            } else if (it.count > kMaxLeaf) {
+                mid = it.first + it.count / 2;   // degenerate centroids: split by position
+            }
+            if (mid < 0) {
+                self = make_leaf(it.first, it.count, b);
+            } else {
+                BNode n;
+                n.box = b;
+                nodes.push_back(n);
+                self = (int)nodes.size() - 1;
+                work.push_back({mid, it.first + it.count - mid, self, 1});
+                work.push_back({it.first, mid - it.first, self, 0});
+            }
+            if (it.parent < 0)
+                root = self;
+            else if (it.side == 0)
+                nodes[it.parent].left = self;
+            else
+                nodes[it.parent].right = self;
+        }
+        return root;
+    }
+};
+
+}  // namespace
+
+void build_bvh4(const float* verts, uint32_t num_tris, Bvh4* out) {
+    Builder b;
+    b.verts = verts;
+    int T = (int)num_tris;
+    b.tbox.resize(T);
+    b.cent.resize(3 * (size_t)T);
+    b.idx.resize(T);
+    for (int t = 0; t < T; ++t) {
+        const float* v = verts + 9 * (size_t)t;
+        for (int k = 0; k < 3; ++k) b.tbox[t].grow(v + 3 * k);
+        for (int a = 0; a < 3; ++a) b.cent[3 * t + a] = (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
+        b.idx[t] = t;
+    }
+    b.nodes.reserve(2 * (size_t)T + 1);
+    int root = T > 0 ? b.build(T) : -1;
+
+    // triangles in leaf order (the index array is already leaf-ordered)
+    out->tris.assign(12 * (size_t)T, 0.f);
+    for (int k = 0; k < T; ++k) {
+        int t = b.idx[k];
+        const float* v = verts + 9 * (size_t)t;
+        float* o = &out->tris[12 * (size_t)k];
+        uint32_t tid = (uint32_t)t;
+        o[0] = v[0]; o[1] = v[1]; o[2] = v[2];
+        std::memcpy(&o[3], &tid, 4);
+        for (int a = 0; a < 3; ++a) {
+            o[4 + a] = v[3 + a] - v[a];
+            o[8 + a] = v[6 + a] - v[a];
+        }
+    }
+
+    // collapse to 4-wide nodes, breadth-first
+    out->nodes.clear();
+    struct Q {
+        int bnode;   // binary node whose children become this node's slots
+        int depth;
+    };
+    std::vector<Q> queue;
+    std::vector<std::vector<int>> slots;
+    if (root < 0) {
+        out->nodes.assign(32, 0.f);
+        float* n = out->nodes.data();
+        int neg1 = -1;
+        for (int c = 0; c < 4; ++c) std::memcpy(&n[24 + c], &neg1, 4);
+        out->num_nodes = 1;
+        out->depth = 1;
+        return;
+    }
+    queue.push_back({root, 1});
+    uint32_t max_depth = 1;
+    for (size_t qi = 0; qi < queue.size(); ++qi) {
+        int bn = queue[qi].bnode;
+        std::vector<int> ch;
+        if (b.nodes[bn].left < 0) {
+            ch.push_back(bn);   // a leaf root: one leaf slot
+        } else {
+            ch.push_back(b.nodes[bn].left);
+            ch.push_back(b.nodes[bn].right);
+            while (ch.size() < 4) {
+                int best = -1;
+                float ba = -1.f;
+                for (int i = 0; i < (int)ch.size(); ++i) {
+                    const BNode& c = b.nodes[ch[i]];
+                    if (c.left >= 0 && c.box.area() > ba) {
+                        ba = c.box.area();
+                        best = i;
+                    }
+                }
+                if (best < 0) break;
+                int x = ch[best];
+                ch[best] = b.nodes[x].left;
+                ch.push_back(b.nodes[x].right);
+            }
+        }
+        slots.push_back(ch);
+        for (int c : ch)
+            if (b.nodes[c].left >= 0) queue.push_back({c, queue[qi].depth + 1});
+        max_depth = std::max(max_depth, (uint32_t)queue[qi].depth);
+    }
+    // queue order is node order; assign indices of inner children
+    size_t N = queue.size();
+    out->nodes.assign(32 * N, 0.f);
+    size_t next = 1;
+    for (size_t qi = 0; qi < N; ++qi) {
+        float* n = &out->nodes[32 * qi];
+        const std::vector<int>& ch = slots[qi];
+        for (int c = 0; c < 4; ++c) {
+            int child_bits = -1, count = 0;
+            float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+            if (c < (int)ch.size()) {
+                const BNode& cn = b.nodes[ch[c]];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = cn.box.lo[a];
+                    hi[a] = cn.box.hi[a];
+                }
+                if (cn.left < 0) {
+                    child_bits = ~cn.first;
+                    count = cn.count;
+                } else {
+                    child_bits = (int)next++;
+                }
+            }
+            n[0 + c] = lo[0];
+            n[4 + c] = hi[0];
+            n[8 + c] = lo[1];
+            n[12 + c] = hi[1];
+            n[16 + c] = lo[2];
+            n[20 + c] = hi[2];
+            std::memcpy(&n[24 + c], &child_bits, 4);
+            std::memcpy(&n[28 + c], &count, 4);
+        }
+    }
+    out->num_nodes = (uint32_t)N;
+    out->depth = max_depth;
+}

@@ -1,0 +1,558 @@
+// C ABI of libddgi.so: context lifetime, argument validation and kernel
+// launches.  Every call validates on the host, enqueues on the caller's
+// stream and returns without synchronising (except the documented getters).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct ddgi_ctx {
+    ddgi_config cfg{};
+    uint32_t T = 0, E = 0, P = 0;
+    float4* nodes = nullptr;
+    float4* tris = nullptr;
+    float4* nrm = nullptr;
+    float4* alb = nullptr;
+    float4* emi = nullptr;
+    float4* evert = nullptr;
+    float* cdf = nullptr;
+    uint32_t* etri = nullptr;
+    float area_total = 0.f;
+    float4* irr = nullptr;
+    float2* depth = nullptr;
+    float4* offset = nullptr;
+    float4* rays = nullptr;
+    float4* sf = nullptr;
+    uint32_t* err = nullptr;
+    uint32_t updates = 0;
+    uint32_t bvh_nodes = 0, bvh_depth = 0;
+    uint64_t device_bytes = 0;
+    std::vector<void*> allocs;
+    std::string last_error;
+};
+
+namespace {
+
+ddgi_status fail(ddgi_ctx* c, ddgi_status code, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+ddgi_status cuda_fail(ddgi_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, DDGI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(ddgi_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    size_t bytes = sizeof(T) * count;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(*p);
+        ctx->device_bytes += bytes;
+    }
+    return e;
+}
+
+// PCG hash (Jarzynski & Olano 2020), host copy for the per-frame rotation
+uint32_t pcg_h(uint32_t v) {
+    uint32_t state = v * 747796405u + 2891336453u;
+    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+double rng_h(uint32_t seed, uint32_t pixel, uint32_t frame, uint32_t pass, uint32_t cand, uint32_t dim) {
+    uint32_t h = pcg_h(seed);
+    h = pcg_h(h + pixel);
+    h = pcg_h(h + frame);
+    h = pcg_h(h + pass);
+    h = pcg_h(h + cand);
+    h = pcg_h(h + dim);
+    return (double)(h >> 8) * (1.0 / 16777216.0);
+}
+
+// uniform random rotation from a unit quaternion (Shoemake's method)
+void frame_rotation(uint32_t seed, uint32_t frame, float R[9]) {
+    const double PI = 3.14159265358979323846;
+    double u0 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 0);
+    double u1 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 1);
+    double u2 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 2);
+    double a = std::sqrt(1.0 - u0), b = std::sqrt(u0);
+    double x = a * std::sin(2 * PI * u1), y = a * std::cos(2 * PI * u1);
+    double z = b * std::sin(2 * PI * u2), w = b * std::cos(2 * PI * u2);
+    double M[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w),
+                   2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w),
+                   2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)};
+    for (int i = 0; i < 9; ++i) R[i] = (float)M[i];
+}
+
+SceneView scene_view(ddgi_ctx* c) {
+    SceneView s;
+    s.nodes = c->nodes;
+    s.tris = c->tris;
+    s.nrm = c->nrm;
+    s.alb = c->alb;
+    s.emi = c->emi;
+    s.cdf = c->cdf;
+    s.etri = c->etri;
+    s.evert = c->evert;
+    s.num_emitters = c->E;
+    s.area_total = c->area_total;
+    s.err = c->err;
+    return s;
+}
+
+VolumeView volume_view(ddgi_ctx* c) {
+    VolumeView v;
+    v.irr = c->irr;
+    v.depth = c->depth;
+    v.offset = c->offset;
+    v.origin = make_float3(c->cfg.origin[0], c->cfg.origin[1], c->cfg.origin[2]);
+    v.spacing = make_float3(c->cfg.spacing[0], c->cfg.spacing[1], c->cfg.spacing[2]);
+    v.counts = make_int3(c->cfg.counts[0], c->cfg.counts[1], c->cfg.counts[2]);
+    v.irr_n = (int)c->cfg.irr_texels;
+    v.depth_n = (int)c->cfg.depth_texels;
+    v.min_spacing = std::fmin(std::fmin(c->cfg.spacing[0], c->cfg.spacing[1]), c->cfg.spacing[2]);
+    v.max_spacing = std::fmax(std::fmax(c->cfg.spacing[0], c->cfg.spacing[1]), c->cfg.spacing[2]);
+    return v;
+}
+
+RestirParams restir_params(ddgi_ctx* c) {
+    RestirParams r;
+    r.seed = c->cfg.seed;
+    r.n_light = c->cfg.num_light_candidates;
+    r.n_bsdf = c->cfg.num_bsdf_candidates;
+    r.temporal_mcap = c->cfg.temporal_mcap;
+    r.spatial_neighbours = c->cfg.spatial_neighbours;
+    r.spatial_radius = c->cfg.spatial_radius;
+    r.normal_reject_cos = c->cfg.normal_reject_cos;
+    r.depth_reject_frac = c->cfg.depth_reject_frac;
+    return r;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+const uint32_t kMaxPixels = 1u << 26;   // tag = pixel * 64 + candidate fits 32 bits
+
+ddgi_status check_gbuf(ddgi_ctx* ctx, const ddgi_gbuf* g, GBufView* out) {
+    if (!g) return fail(ctx, DDGI_ERR_INVALID_ARG, "gbuffer is NULL");
+    uint64_t n = (uint64_t)g->width * g->height;
+    if (n > kMaxPixels) return fail(ctx, DDGI_ERR_INVALID_ARG, "gbuffer larger than 2^26 pixels");
+    if (n > 0 && (!g->g0 || !g->g1 || !g->g2))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "gbuffer plane is NULL");
+    if (!aligned(g->g0, 16) || !aligned(g->g1, 16) || !aligned(g->g2, 16))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "gbuffer plane not 16-byte aligned");
+    out->g0 = reinterpret_cast<float4*>(g->g0);
+    out->g1 = reinterpret_cast<float4*>(g->g1);
+    out->g2 = reinterpret_cast<float4*>(g->g2);
+    out->width = (int)g->width;
+    out->height = (int)g->height;
+    return DDGI_OK;
+}
+
+ddgi_status check_res(ddgi_ctx* ctx, const ddgi_reservoirs* r, uint64_t npix, ResView* out) {
+    if (!r) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoirs is NULL");
+    if (r->num_pixels != npix) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir size != gbuffer size");
+    if (npix > 0 && (!r->r0 || !r->r1 || !r->r2))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir plane is NULL");
+    if (!aligned(r->r0, 16) || !aligned(r->r1, 16) || !aligned(r->r2, 8))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir plane misaligned");
+    out->r0 = reinterpret_cast<float4*>(r->r0);
+    out->r1 = reinterpret_cast<float4*>(r->r1);
+    out->r2 = reinterpret_cast<uint2*>(r->r2);
+    return DDGI_OK;
+}
+
+bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+ddgi_status check_config(const ddgi_config* c, std::string* why) {
+    for (int a = 0; a < 3; ++a) {
+        if (c->counts[a] < 1 || c->counts[a] > 4096) { *why = "probe counts out of range"; return DDGI_ERR_INVALID_ARG; }
+        if (!(c->spacing[a] > 0.f) || !std::isfinite(c->spacing[a])) { *why = "probe spacing must be > 0"; return DDGI_ERR_INVALID_ARG; }
+    }
+    if (!finite3(c->origin)) { *why = "probe origin not finite"; return DDGI_ERR_INVALID_ARG; }
+    if ((uint64_t)c->counts[0] * c->counts[1] * c->counts[2] > (1u << 22)) { *why = "too many probes"; return DDGI_ERR_INVALID_ARG; }
+    if (c->rays_per_probe < 1 || c->rays_per_probe > 1024) { *why = "rays_per_probe must be 1..1024"; return DDGI_ERR_INVALID_ARG; }
+    if (c->irr_texels < 2 || c->irr_texels > 32 || c->depth_texels < 2 || c->depth_texels > 32) {
+        *why = "texel counts must be 2..32"; return DDGI_ERR_INVALID_ARG;
+    }
+    if (!(c->hysteresis >= 0.f && c->hysteresis < 1.f)) { *why = "hysteresis must be in [0,1)"; return DDGI_ERR_INVALID_ARG; }
+    if (!(c->le_attenuation >= 0.f) || !std::isfinite(c->le_attenuation)) { *why = "le_attenuation must be >= 0"; return DDGI_ERR_INVALID_ARG; }
+    if (!(c->depth_sharpness > 0.f) || !std::isfinite(c->depth_sharpness)) { *why = "depth_sharpness must be > 0"; return DDGI_ERR_INVALID_ARG; }
+    uint32_t M = c->num_light_candidates + c->num_bsdf_candidates;
+    if (c->num_bsdf_candidates < 1 || M > 64) { *why = "need 1..64 candidates with at least one BSDF candidate"; return DDGI_ERR_INVALID_ARG; }
+    if (!(c->temporal_mcap >= 0.f) || !std::isfinite(c->temporal_mcap)) { *why = "temporal_mcap must be >= 0"; return DDGI_ERR_INVALID_ARG; }
+    if (c->spatial_neighbours > 32) { *why = "spatial_neighbours must be <= 32"; return DDGI_ERR_INVALID_ARG; }
+    if (c->spatial_radius < 1 || c->spatial_radius > 255) { *why = "spatial_radius must be 1..255"; return DDGI_ERR_INVALID_ARG; }
+    if (!std::isfinite(c->normal_reject_cos) || !(c->depth_reject_frac >= 0.f)) { *why = "bad rejection thresholds"; return DDGI_ERR_INVALID_ARG; }
+    return DDGI_OK;
+}
+
+CamView cam_view(const ddgi_camera* c) {
+    CamView v;
+    v.pos = make_float3(c->pos[0], c->pos[1], c->pos[2]);
+    v.fwd = make_float3(c->fwd[0], c->fwd[1], c->fwd[2]);
+    v.right = make_float3(c->right[0], c->right[1], c->right[2]);
+    v.up = make_float3(c->up[0], c->up[1], c->up[2]);
+    v.tan_half_fovy = c->tan_half_fovy;
+    v.width = (int)c->width;
+    v.height = (int)c->height;
+    return v;
+}
+
+ddgi_status probe_params(ddgi_ctx* c, uint32_t frame, ProbeParams* p) {
+    p->sf = c->sf;
+    p->rays = c->cfg.rays_per_probe;
+    frame_rotation(c->cfg.seed, frame, p->R);
+    p->hysteresis = c->updates == 0 ? 0.f : c->cfg.hysteresis;
+    p->le_attenuation = c->cfg.le_attenuation;
+    p->depth_sharpness = c->cfg.depth_sharpness;
+    p->depth_tmax = 1.5f * std::fmax(std::fmax(c->cfg.spacing[0], c->cfg.spacing[1]), c->cfg.spacing[2]);
+    return DDGI_OK;
+}
+
+void release(ddgi_ctx* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ctx** out) {
+    if (!out) return DDGI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!scene || !cfg) return DDGI_ERR_INVALID_ARG;
+    if (scene->num_tris > 0 && (!scene->vertices || !scene->albedo || !scene->emission))
+        return DDGI_ERR_INVALID_ARG;
+    if (scene->num_tris > (1u << 28)) return DDGI_ERR_INVALID_ARG;
+    std::string why;
+    if (check_config(cfg, &why) != DDGI_OK) return DDGI_ERR_INVALID_ARG;
+    for (uint64_t i = 0; i < 9ull * scene->num_tris; ++i)
+        if (!std::isfinite(scene->vertices[i])) return DDGI_ERR_INVALID_ARG;
+    for (uint64_t i = 0; i < 3ull * scene->num_tris; ++i)
+        if (!(scene->albedo[i] >= 0.f && scene->albedo[i] <= 1.f) ||
+            !(scene->emission[i] >= 0.f) || !std::isfinite(scene->emission[i]))
+            return DDGI_ERR_INVALID_ARG;
+
+    ddgi_ctx* ctx = new (std::nothrow) ddgi_ctx;
+    if (!ctx) return DDGI_ERR_OOM;
+    ctx->cfg = *cfg;
+    const uint32_t T = scene->num_tris;
+    ctx->T = T;
+    ctx->P = (uint32_t)(cfg->counts[0] * cfg->counts[1] * cfg->counts[2]);
+
+    // scene tables (host), fp64 geometry for normals / areas
+    Bvh4 bvh;
+    build_bvh4(scene->vertices, T, &bvh);
+    ctx->bvh_nodes = bvh.num_nodes;
+    ctx->bvh_depth = bvh.depth;
+    std::vector<float4> nrm(T), alb(T), emi(T);
+    std::vector<float4> evert;
+    std::vector<float> cdf;
+    std::vector<uint32_t> etri;
+    double acc = 0.0;
+    for (uint32_t i = 0; i < T; ++i) {
+        const float* v = scene->vertices + 9ull * i;
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = (double)v[3 + a] - (double)v[a];
+            e2[a] = (double)v[6 + a] - (double)v[a];
+        }
+        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                       e1[0] * e2[1] - e1[1] * e2[0]};
+        double l = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        nrm[i] = l > 0 ? make_float4((float)(c[0] / l), (float)(c[1] / l), (float)(c[2] / l), 0.f)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* a = scene->albedo + 3ull * i;
+        const float* e = scene->emission + 3ull * i;
+        bool emissive = e[0] > 0.f || e[1] > 0.f || e[2] > 0.f;
+        alb[i] = make_float4(a[0], a[1], a[2], 0.f);
+        emi[i] = make_float4(e[0], e[1], e[2], emissive ? 1.f : 0.f);
+        if (emissive) {
+            acc += 0.5 * l;
+            cdf.push_back((float)acc);
+            etri.push_back(i);
+            evert.push_back(make_float4(v[0], v[1], v[2], 0.f));
+            evert.push_back(make_float4(v[3] - v[0], v[4] - v[1], v[5] - v[2], 0.f));
+            evert.push_back(make_float4(v[6] - v[0], v[7] - v[1], v[8] - v[2], 0.f));
+        }
+    }
+    ctx->E = (uint32_t)etri.size();
+    ctx->area_total = (float)acc;
+    if (ctx->E > 0 && !(acc > 0.0)) {
+        delete ctx;
+        return DDGI_ERR_INVALID_ARG;   // emissive triangles of zero area
+    }
+    // spherical Fibonacci directions (fp64 on the host)
+    const uint32_t R = cfg->rays_per_probe;
+    std::vector<float4> sf(R);
+    for (uint32_t i = 0; i < R; ++i) {
+        double z = 1.0 - (2.0 * i + 1.0) / R;
+        double r = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+        double ph = i * 0.6180339887498949;
+        ph = 2.0 * 3.14159265358979323846 * (ph - std::floor(ph));
+        sf[i] = make_float4((float)(r * std::cos(ph)), (float)(r * std::sin(ph)), (float)z, 0.f);
+    }
+
+    const size_t ti = cfg->irr_texels + 2, td = cfg->depth_texels + 2;
+    const size_t P = ctx->P;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n)                                 \
+    if (e == cudaSuccess) e = dalloc(ctx, &ctx->ptr, (n));
+    ALLOC(nodes, 8ull * bvh.num_nodes)
+    ALLOC(tris, 3ull * T)
+    ALLOC(nrm, T)
+    ALLOC(alb, T)
+    ALLOC(emi, T)
+    ALLOC(evert, 3ull * ctx->E)
+    ALLOC(cdf, ctx->E)
+    ALLOC(etri, ctx->E)
+    ALLOC(irr, P * ti * ti)
+    ALLOC(depth, P * td * td)
+    ALLOC(offset, P)
+    ALLOC(rays, P * R)
+    ALLOC(sf, R)
+    ALLOC(err, 4)
+#undef ALLOC
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(ctx->nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float));
+    up(ctx->tris, bvh.tris.data(), bvh.tris.size() * sizeof(float));
+    up(ctx->nrm, nrm.data(), T * sizeof(float4));
+    up(ctx->alb, alb.data(), T * sizeof(float4));
+    up(ctx->emi, emi.data(), T * sizeof(float4));
+    up(ctx->evert, evert.data(), evert.size() * sizeof(float4));
+    up(ctx->cdf, cdf.data(), cdf.size() * sizeof(float));
+    up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
+    up(ctx->sf, sf.data(), R * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(ctx->depth, 0, P * td * td * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(ctx->offset, 0, P * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(ctx->rays, 0, P * R * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        VolumeView v = volume_view(ctx);
+        if (probe_blend_smem(v, R) > 200 * 1024) e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) {
+        release(ctx);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? DDGI_ERR_OOM : DDGI_ERR_CUDA;
+    }
+    *out = ctx;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_destroy(ddgi_ctx* ctx) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    release(ctx);
+    delete ctx;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_get_info(ddgi_ctx* ctx, ddgi_info* out) {
+    if (!ctx || !out) return DDGI_ERR_INVALID_ARG;
+    out->num_tris = ctx->T;
+    out->num_emitters = ctx->E;
+    out->num_probes = ctx->P;
+    out->rays_per_probe = ctx->cfg.rays_per_probe;
+    out->irr_tile = ctx->cfg.irr_texels + 2;
+    out->depth_tile = ctx->cfg.depth_texels + 2;
+    out->bvh_nodes = ctx->bvh_nodes;
+    out->bvh_depth = ctx->bvh_depth;
+    out->updates = ctx->updates;
+    out->device_bytes = ctx->device_bytes;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_trace(ddgi_ctx* ctx, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    ProbeParams p;
+    probe_params(ctx, frame, &p);
+    CK(launch_probe_trace(scene_view(ctx), volume_view(ctx), p, ctx->rays, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    ProbeParams p;
+    probe_params(ctx, frame, &p);
+    CK(launch_probe_blend(volume_view(ctx), p, ctx->rays, (cudaStream_t)stream));
+    ctx->updates++;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_update(ddgi_ctx* ctx, uint32_t frame, void* stream) {
+    ddgi_status s = ddgi_probe_trace(ctx, frame, stream);
+    if (s != DDGI_OK) return s;
+    return ddgi_probe_blend(ctx, frame, stream);
+}
+
+ddgi_status ddgi_probe_state_get(ddgi_ctx* ctx, float* irr, float* depth, float* offsets,
+                                 uint32_t* updates, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = ctx->P, ti = ctx->cfg.irr_texels + 2, td = ctx->cfg.depth_texels + 2;
+    if (irr) CK(cudaMemcpyAsync(irr, ctx->irr, P * ti * ti * sizeof(float4), cudaMemcpyDefault, st));
+    if (depth) CK(cudaMemcpyAsync(depth, ctx->depth, P * td * td * sizeof(float2), cudaMemcpyDefault, st));
+    if (offsets) CK(cudaMemcpyAsync(offsets, ctx->offset, P * sizeof(float4), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    if (updates) *updates = ctx->updates;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_state_set(ddgi_ctx* ctx, const float* irr, const float* depth,
+                                 const float* offsets, uint32_t updates, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = ctx->P, ti = ctx->cfg.irr_texels + 2, td = ctx->cfg.depth_texels + 2;
+    if (irr) CK(cudaMemcpyAsync(ctx->irr, irr, P * ti * ti * sizeof(float4), cudaMemcpyDefault, st));
+    if (depth) CK(cudaMemcpyAsync(ctx->depth, depth, P * td * td * sizeof(float2), cudaMemcpyDefault, st));
+    if (offsets) CK(cudaMemcpyAsync(ctx->offset, offsets, P * sizeof(float4), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->updates = updates;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_rays_get(ddgi_ctx* ctx, float* rays, void* stream) {
+    if (!ctx || !rays) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(rays, ctx->rays, (size_t)ctx->P * ctx->cfg.rays_per_probe * sizeof(float4),
+                       cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_probe_rays_set(ddgi_ctx* ctx, const float* rays, void* stream) {
+    if (!ctx || !rays) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->rays, rays, (size_t)ctx->P * ctx->cfg.rays_per_probe * sizeof(float4),
+                       cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_gbuffer(ddgi_ctx* ctx, const ddgi_camera* cam, const ddgi_camera* prev_cam,
+                         const ddgi_gbuf* out, void* stream) {
+    if (!ctx || !cam) return fail(ctx, DDGI_ERR_INVALID_ARG, "NULL argument");
+    GBufView g;
+    ddgi_status s = check_gbuf(ctx, out, &g);
+    if (s != DDGI_OK) return s;
+    if (cam->width != out->width || cam->height != out->height)
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "camera size != gbuffer size");
+    if (!(cam->tan_half_fovy > 0.f) || (prev_cam && !(prev_cam->tan_half_fovy > 0.f)))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "field of view must be > 0");
+    if (prev_cam && (prev_cam->width != cam->width || prev_cam->height != cam->height))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "previous camera size differs");
+    CamView c = cam_view(cam), pc;
+    if (prev_cam) pc = cam_view(prev_cam);
+    CK(launch_gbuffer(scene_view(ctx), c, prev_cam ? &pc : nullptr, g, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* out,
+                           float* residual, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    GBufView g;
+    ResView r;
+    ddgi_status s = check_gbuf(ctx, gb, &g);
+    if (s != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height;
+    if ((s = check_res(ctx, out, n, &r)) != DDGI_OK) return s;
+    if (n > 0 && (!residual || !aligned(residual, 16)))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "residual NULL or misaligned");
+    CK(launch_restir_initial(scene_view(ctx), volume_view(ctx), restir_params(ctx), g, r,
+                             reinterpret_cast<float4*>(residual), frame, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_gbuf* gbp,
+                            const float* prev_cam_pos, const ddgi_reservoirs* cur,
+                            const ddgi_reservoirs* prev, const ddgi_reservoirs* out,
+                            uint32_t frame, void* stream) {
+    if (!ctx || !prev_cam_pos) return fail(ctx, DDGI_ERR_INVALID_ARG, "NULL argument");
+    GBufView g, gp;
+    ResView rc, rpv, ro;
+    ddgi_status s;
+    if ((s = check_gbuf(ctx, gb, &g)) != DDGI_OK) return s;
+    if ((s = check_gbuf(ctx, gbp, &gp)) != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height, np = (uint64_t)gp.width * gp.height;
+    if ((s = check_res(ctx, cur, n, &rc)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, prev, np, &rpv)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, out, n, &ro)) != DDGI_OK) return s;
+    if (n > 0 && (ro.r0 == rc.r0 || ro.r0 == rpv.r0 || ro.r2 == rc.r2 || ro.r2 == rpv.r2))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "output reservoirs alias an input");
+    if (!finite3(prev_cam_pos)) return fail(ctx, DDGI_ERR_INVALID_ARG, "camera position not finite");
+    CK(launch_restir_temporal(scene_view(ctx), restir_params(ctx), g, gp,
+                              make_float3(prev_cam_pos[0], prev_cam_pos[1], prev_cam_pos[2]), rc, rpv,
+                              ro, frame, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* in,
+                           const ddgi_reservoirs* out, uint32_t frame, uint32_t pass,
+                           void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    GBufView g;
+    ResView ri, ro;
+    ddgi_status s;
+    if ((s = check_gbuf(ctx, gb, &g)) != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height;
+    if ((s = check_res(ctx, in, n, &ri)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, out, n, &ro)) != DDGI_OK) return s;
+    if (n > 0 && (ro.r0 == ri.r0 || ro.r1 == ri.r1 || ro.r2 == ri.r2))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "output reservoirs alias the input");
+    if (pass > 3) return fail(ctx, DDGI_ERR_INVALID_ARG, "spatial pass index must be 0..3");
+    CK(launch_restir_spatial(scene_view(ctx), restir_params(ctx), g, ri, ro, frame, pass,
+                             (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* res,
+                       const float* residual, float* radiance, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    GBufView g;
+    ResView r;
+    ddgi_status s;
+    if ((s = check_gbuf(ctx, gb, &g)) != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height;
+    if ((s = check_res(ctx, res, n, &r)) != DDGI_OK) return s;
+    if (n > 0 && (!residual || !radiance || !aligned(residual, 16) || !aligned(radiance, 16)))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "residual / radiance NULL or misaligned");
+    CK(launch_shade(scene_view(ctx), volume_view(ctx), g, r, reinterpret_cast<const float4*>(residual),
+                    reinterpret_cast<float4*>(radiance), (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t w[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(w, ctx->err, sizeof(w), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(ctx->err, 0, sizeof(w), st));
+    CK(cudaStreamSynchronize(st));
+    if (w[0] & (ERRBIT_TRAVERSAL | ERRBIT_STACK)) {
+        ctx->last_error = (w[0] & ERRBIT_STACK) ? "traversal stack overflow" : "traversal visit limit";
+        return DDGI_ERR_TRAVERSAL_LIMIT;
+    }
+    return DDGI_OK;
+}
+
+const char* ddgi_last_error(ddgi_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "NULL context"; }
+
+}  // extern "C"

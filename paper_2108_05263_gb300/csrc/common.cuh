@@ -1,0 +1,274 @@
+// Device-side building blocks shared by the kernels: vector math, the
+// counter-based random numbers, octahedral probe maps and the views of the
+// scene / probe volume that kernels receive by value.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DDGI_PI 3.14159265358979323846f
+#define DDGI_T_EPS 1e-4f
+#define DDGI_MISS_T 1e30f
+#define DDGI_NONE 0xFFFFFFFFu
+
+// random-number pass ids (keys of the hash chain)
+#define PASS_INITIAL 0u
+#define PASS_SPATIAL0 1u
+#define PASS_TEMPORAL 5u
+#define PASS_PROBE_ROT 7u
+
+// device error word bits
+#define ERRBIT_TRAVERSAL 1u
+#define ERRBIT_STACK 2u
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 xyz(float4 a) { return {a.x, a.y, a.z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ f3 mul(f3 a, f3 b) { return {a.x * b.x, a.y * b.y, a.z * b.z}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float length(f3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float luminance(f3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
+__device__ __forceinline__ bool any_pos(f3 c) { return c.x > 0.f || c.y > 0.f || c.z > 0.f; }
+
+// ---------------------------------------------------------------------------
+// PCG hash (Jarzynski & Olano, JCGT 2020) chained over the key tuple
+// (seed, pixel, frame, pass, candidate, dimension).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+    uint32_t state = v * 747796405u + 2891336453u;
+    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+// prefix of the chain up to the pass id; candidate and dimension follow
+__device__ __forceinline__ uint32_t rng_prefix(uint32_t seed, uint32_t pixel, uint32_t frame,
+                                               uint32_t pass) {
+    uint32_t h = pcg_hash(seed);
+    h = pcg_hash(h + pixel);
+    h = pcg_hash(h + frame);
+    return pcg_hash(h + pass);
+}
+__device__ __forceinline__ uint32_t rng_cand(uint32_t prefix, uint32_t cand) {
+    return pcg_hash(prefix + cand);
+}
+__device__ __forceinline__ uint32_t rng_u32_dim(uint32_t cprefix, uint32_t dim) {
+    return pcg_hash(cprefix + dim);
+}
+__device__ __forceinline__ float u01(uint32_t h) { return (float)(h >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// views passed to kernels by value
+// ---------------------------------------------------------------------------
+struct SceneView {
+    const float4* nodes;     // BVH4 nodes, 8 float4 each
+    const float4* tris;      // BVH-ordered triangles: (v0, orig idx bits), e1, e2
+    const float4* nrm;       // per original triangle: unit normal, 0
+    const float4* alb;       // albedo rgb, 0
+    const float4* emi;       // emission rgb, emissive flag (1/0)
+    const float* cdf;        // cumulative emitter area (float), [num_emitters]
+    const uint32_t* etri;    // emitter triangle ids
+    const float4* evert;     // per emitter: v0, e1 = v1 - v0, e2 = v2 - v0
+    uint32_t num_emitters;
+    float area_total;
+    uint32_t* err;           // device error word
+};
+
+struct VolumeView {
+    float4* irr;             // [P][ti*ti] rgb, 0
+    float2* depth;           // [P][td*td] mean, mean square
+    const float4* offset;    // [P] xyz, 0
+    float3 origin, spacing;
+    int3 counts;
+    int irr_n, depth_n;      // interior texels per side
+    float min_spacing, max_spacing;
+};
+
+// ---------------------------------------------------------------------------
+// octahedral maps with a one-texel border
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float signnz(float x) { return x >= 0.f ? 1.f : -1.f; }
+
+__device__ __forceinline__ float2 oct_encode(f3 d) {
+    float s = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
+    float u = d.x / s, v = d.y / s;
+    if (d.z < 0.f) {
+        float fu = (1.f - fabsf(v)) * signnz(u);
+        float fv = (1.f - fabsf(u)) * signnz(v);
+        u = fu;
+        v = fv;
+    }
+    return make_float2(u, v);
+}
+
+__device__ __forceinline__ f3 oct_decode(float u, float v) {
+    float z = 1.f - fabsf(u) - fabsf(v);
+    float x = u, y = v;
+    if (z < 0.f) {
+        x = (1.f - fabsf(v)) * signnz(u);
+        y = (1.f - fabsf(u)) * signnz(v);
+    }
+    float l = rsqrtf(x * x + y * y + z * z);
+    return {x * l, y * l, z * l};
+}
+
+__device__ __forceinline__ f3 texel_dir(int i, int j, int n) {
+    return oct_decode(2.f * (i + 0.5f) / n - 1.f, 2.f * (j + 0.5f) / n - 1.f);
+}
+
+// bilinear taps of a padded (n+2)^2 tile in direction d
+struct Taps {
+    int i00;   // index of the top-left tap within the tile
+    float ax, ay;
+};
+__device__ __forceinline__ Taps oct_taps(f3 d, int n) {
+    float2 uv = oct_encode(d);
+    float fx = (uv.x + 1.f) * 0.5f * n + 0.5f;
+    float fy = (uv.y + 1.f) * 0.5f * n + 0.5f;
+    float x0f = floorf(fx), y0f = floorf(fy);
+    Taps t;
+    t.ax = fx - x0f;
+    t.ay = fy - y0f;
+    int x0 = (int)x0f, y0 = (int)y0f;
+    if (x0 < 0) { x0 = 0; t.ax = 0.f; }
+    if (y0 < 0) { y0 = 0; t.ay = 0.f; }
+    if (x0 > n) { x0 = n; t.ax = 1.f; }
+    if (y0 > n) { y0 = n; t.ay = 1.f; }
+    t.i00 = y0 * (n + 2) + x0;
+    return t;
+}
+
+__device__ __forceinline__ f3 sample_irr(const float4* tile, int n, f3 d) {
+    Taps t = oct_taps(d, n);
+    int w = n + 2;
+    float4 a = __ldg(tile + t.i00), b = __ldg(tile + t.i00 + 1);
+    float4 c = __ldg(tile + t.i00 + w), e = __ldg(tile + t.i00 + w + 1);
+    float w00 = (1.f - t.ax) * (1.f - t.ay), w10 = t.ax * (1.f - t.ay);
+    float w01 = (1.f - t.ax) * t.ay, w11 = t.ax * t.ay;
+    return {w00 * a.x + w10 * b.x + w01 * c.x + w11 * e.x,
+            w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y,
+            w00 * a.z + w10 * b.z + w01 * c.z + w11 * e.z};
+}
+
+__device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) {
+    Taps t = oct_taps(d, n);
+    int w = n + 2;
+    float2 a = __ldg(tile + t.i00), b = __ldg(tile + t.i00 + 1);
+    float2 c = __ldg(tile + t.i00 + w), e = __ldg(tile + t.i00 + w + 1);
+    float w00 = (1.f - t.ax) * (1.f - t.ay), w10 = t.ax * (1.f - t.ay);
+    float w01 = (1.f - t.ax) * t.ay, w11 = t.ax * t.ay;
+    return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * e.x,
+                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y);
+}
+
+__device__ __forceinline__ f3 probe_pos(const VolumeView& v, int i, int j, int k, int p) {
+    float4 o = __ldg(v.offset + p);
+    return {v.origin.x + v.spacing.x * i + o.x, v.origin.y + v.spacing.y * j + o.y,
+            v.origin.z + v.spacing.z * k + o.z};
+}
+
+// ---------------------------------------------------------------------------
+// probe query: irradiance E(q, n) blended from the 8 surrounding probes
+// (trilinear x wrap shading x cubed Chebyshev visibility, crushed below 0.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
+    float g[3] = {(q.x - v.origin.x) / v.spacing.x, (q.y - v.origin.y) / v.spacing.y,
+                  (q.z - v.origin.z) / v.spacing.z};
+    int cnt[3] = {v.counts.x, v.counts.y, v.counts.z};
+    int base[3];
+    float al[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int hi = max(cnt[a] - 2, 0);
+        float f = floorf(g[a]);
+        int b = f < 0.f ? 0 : (f > (float)hi ? hi : (int)f);
+        base[a] = b;
+        al[a] = cnt[a] > 1 ? fminf(fmaxf(g[a] - (float)b, 0.f), 1.f) : 0.f;
+    }
+    const int ti = v.irr_n + 2, td = v.depth_n + 2;
+    float sw = 0.f;
+    f3 se = {0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int c = 0; c < 8; ++c) {
+        int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+        int gi = min(base[0] + ox, cnt[0] - 1);
+        int gj = min(base[1] + oy, cnt[1] - 1);
+        int gk = min(base[2] + oz, cnt[2] - 1);
+        float tri = (ox ? al[0] : 1.f - al[0]) * (oy ? al[1] : 1.f - al[1]) *
+                    (oz ? al[2] : 1.f - al[2]);
+        int p = gi + cnt[0] * (gj + cnt[1] * gk);
+        f3 P = probe_pos(v, gi, gj, gk, p);
+        f3 dir = P - q;
+        float r = length(dir);
+        dir = r > 0.f ? dir * (1.f / r) : n;
+        float wrap = 0.5f * (dot(dir, n) + 1.f);
+        float w = wrap * wrap + 0.2f;
+        float2 mom = sample_depth(v.depth + (size_t)p * td * td, v.depth_n, -dir);
+        if (r > mom.x) {
+            float var = fabsf(mom.y - mom.x * mom.x);
+            float dd = r - mom.x;
+            float ch = var / (var + dd * dd);
+            w *= ch * ch * ch;
+        }
+        w = fmaxf(w, 1e-6f);
+        if (w < 0.2f) w = w * w * w * 25.f;
+        w *= tri;
+        f3 e = sample_irr(v.irr + (size_t)p * ti * ti, v.irr_n, n);
+        se = se + e * w;
+        sw += w;
+    }
+    return sw > 0.f ? se * (1.f / sw) : f3{0.f, 0.f, 0.f};
+}
+
+// view-path bias (Sec. 3.4): move from y toward the previous vertex `from`
+__device__ __forceinline__ f3 ddgi_irradiance_biased(const VolumeView& v, f3 y, f3 n, f3 from) {
+    f3 d = from - y;
+    float l = length(d);
+    f3 q = y;
+    if (l > 0.f) {
+        float dv = fminf(0.2f * v.min_spacing, 0.5f * l);
+        q = y + d * (dv / l);
+    }
+    return ddgi_irradiance(v, q, n);
+}
+
+// outgoing radiance (Le + L_DDGI+)(y, y -> from) of a triangle point
+__device__ __forceinline__ f3 radiance_at(const SceneView& s, const VolumeView& v, f3 y,
+                                          uint32_t tri, f3 from) {
+    f3 n = xyz(__ldg(s.nrm + tri));
+    if (dot(n, from - y) <= 0.f) return {0.f, 0.f, 0.f};
+    f3 le = xyz(__ldg(s.emi + tri));
+    f3 rho = xyz(__ldg(s.alb + tri));
+    if (any_pos(rho)) {
+        f3 E = ddgi_irradiance_biased(v, y, n, from);
+        le = le + mul(rho, E) * (1.f / DDGI_PI);
+    }
+    return le;
+}
+
+// target function: luminance of rho_x / pi * L * min(G, 1)
+__device__ __forceinline__ float target_fn(const SceneView& s, f3 x, f3 nx, f3 rho, f3 y,
+                                           uint32_t tri, f3 L) {
+    if (tri == DDGI_NONE) return 0.f;
+    f3 d = y - x;
+    float d2 = dot(d, d);
+    if (d2 <= 0.f) return 0.f;
+    float inv = rsqrtf(d2);
+    f3 w = d * inv;
+    float cx = dot(nx, w);
+    if (cx <= 0.f) return 0.f;
+    float cy = fabsf(dot(xyz(__ldg(s.nrm + tri)), w));
+    float G = cx * cy / d2;
+    float Gb = fminf(G, 1.f);
+    return luminance(mul(rho, L)) * (Gb * (1.f / DDGI_PI));
+}

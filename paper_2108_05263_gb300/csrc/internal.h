@@ -1,0 +1,74 @@
+// Internal host-side declarations shared by the C-ABI layer and the kernel
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ddgi.h"
+#include "bvh.h"
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// per-launch parameter blocks
+// ---------------------------------------------------------------------------
+struct GBufView {
+    float4* g0;
+    float4* g1;
+    float4* g2;
+    int width, height;
+};
+
+struct ResView {
+    float4* r0;
+    float4* r1;
+    uint2* r2;
+};
+
+struct CamView {
+    float3 pos, fwd, right, up;
+    float tan_half_fovy;
+    int width, height;
+};
+
+struct RestirParams {
+    uint32_t seed;
+    uint32_t n_light, n_bsdf;
+    float temporal_mcap;
+    uint32_t spatial_neighbours, spatial_radius;
+    float normal_reject_cos, depth_reject_frac;
+};
+
+struct ProbeParams {
+    const float4* sf;    // spherical Fibonacci directions, [rays]
+    uint32_t rays;
+    float R[9];          // per-frame rotation of the ray set
+    float hysteresis;    // effective (0 on the first update)
+    float le_attenuation;
+    float depth_sharpness;
+    float depth_tmax;
+};
+
+// kernel launchers (return the launch error)
+cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
+                               float4* rays, cudaStream_t st);
+size_t probe_blend_smem(const VolumeView& v, uint32_t rays);
+cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays,
+                               cudaStream_t st);
+cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
+                           const GBufView& g, cudaStream_t st);
+cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
+                                  const GBufView& g, const ResView& out, float4* resid,
+                                  uint32_t frame, cudaStream_t st);
+cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
+                                   const GBufView& gp, float3 prev_cam, const ResView& cur,
+                                   const ResView& prev, const ResView& out, uint32_t frame,
+                                   cudaStream_t st);
+cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, const GBufView& g,
+                                  const ResView& in, const ResView& out, uint32_t frame,
+                                  uint32_t pass, cudaStream_t st);
+cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
+                         const ResView& r, const float4* resid, float4* radiance,
+                         cudaStream_t st);

@@ -1,0 +1,113 @@
+// Primary visibility (support pass) and the shading estimator of Sec. 3.1
+// steps 3-4 / Eq. Algorithm: Le at x + residual + the resampled bounded term
+// behind one shadow ray, with a fresh probe query at the selected point.
+#include "internal.h"
+#include "trace.cuh"
+
+namespace {
+
+__global__ void __launch_bounds__(128) k_gbuffer(SceneView s, CamView cam, CamView pc, int has_prev,
+                                                 GBufView g) {
+    int px = blockIdx.x * blockDim.x + threadIdx.x;
+    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    if (px >= g.width || py >= g.height) return;
+    uint32_t pix = (uint32_t)py * g.width + px;
+    const float W = (float)cam.width, H = (float)cam.height;
+    const float aspect = W / H;
+    float sx = (2.f * (px + 0.5f) / W - 1.f) * cam.tan_half_fovy * aspect;
+    float sy = (1.f - 2.f * (py + 0.5f) / H) * cam.tan_half_fovy;
+    f3 fwd = {cam.fwd.x, cam.fwd.y, cam.fwd.z}, right = {cam.right.x, cam.right.y, cam.right.z};
+    f3 up = {cam.up.x, cam.up.y, cam.up.z}, o = {cam.pos.x, cam.pos.y, cam.pos.z};
+    f3 d = fwd + right * sx + up * sy;
+    d = d * rsqrtf(dot(d, d));
+    Hit h = trace_bvh<false>(s, Ray{o, d, DDGI_T_EPS, DDGI_MISS_T});
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 0.f, __uint_as_float(DDGI_NONE));
+    float4 g2 = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    if (h.tri != DDGI_NONE) {
+        f3 n = xyz(__ldg(s.nrm + h.tri));
+        if (dot(n, d) <= 0.f) {
+            f3 p = o + d * h.t;
+            f3 a = xyz(__ldg(s.alb + h.tri));
+            int prev = -1;
+            if (has_prev) {
+                f3 v = p - f3{pc.pos.x, pc.pos.y, pc.pos.z};
+                float z = dot(v, f3{pc.fwd.x, pc.fwd.y, pc.fwd.z});
+                if (z > 0.f) {
+                    float qx = dot(v, f3{pc.right.x, pc.right.y, pc.right.z}) / z / (pc.tan_half_fovy * aspect);
+                    float qy = dot(v, f3{pc.up.x, pc.up.y, pc.up.z}) / z / pc.tan_half_fovy;
+                    float fx = (qx + 1.f) * 0.5f * W, fy = (1.f - qy) * 0.5f * H;
+                    if (fx >= 0.f && fy >= 0.f && fx < W && fy < H)
+                        prev = (int)floorf(fy) * cam.width + (int)floorf(fx);
+                }
+            }
+            g0 = make_float4(p.x, p.y, p.z, h.t);
+            g1 = make_float4(n.x, n.y, n.z, __uint_as_float(h.tri));
+            g2 = make_float4(a.x, a.y, a.z, __int_as_float(prev));
+        }
+    }
+    g.g0[pix] = g0;
+    g.g1[pix] = g1;
+    g.g2[pix] = g2;
+}
+
+__global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
+                                               const float4* __restrict__ resid,
+                                               float4* __restrict__ radiance) {
+    int px = blockIdx.x * blockDim.x + threadIdx.x;
+    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    if (px >= g.width || py >= g.height) return;
+    uint32_t pix = (uint32_t)py * g.width + px;
+    float4 g1 = g.g1[pix];
+    uint32_t xtri = __float_as_uint(g1.w);
+    if (xtri == DDGI_NONE) {
+        radiance[pix] = make_float4(0.f, 0.f, 0.f, 1.f);
+        return;
+    }
+    float4 g0 = g.g0[pix], g2 = g.g2[pix];
+    const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
+    f3 out = xyz(__ldg(s.emi + xtri)) + xyz(resid[pix]);
+    float4 r0 = r.r0[pix];
+    uint2 r2 = r.r2[pix];
+    uint32_t ty = r2.x;
+    if (ty != DDGI_NONE && r0.w > 0.f) {
+        f3 y = xyz(r0);
+        f3 d = y - x;
+        float d2 = dot(d, d);
+        if (d2 > 0.f) {
+            float l = sqrtf(d2);
+            f3 w = d * (1.f / l);
+            float cx = dot(nx, w);
+            if (cx > 0.f) {
+                Hit h = trace_bvh<true>(s, Ray{x, w, DDGI_T_EPS, (1.f - 1e-4f) * l});
+                if (h.tri == DDGI_NONE) {
+                    f3 L = radiance_at(s, v, y, ty, x);
+                    float cy = fabsf(dot(xyz(__ldg(s.nrm + ty)), w));
+                    float G = cx * cy / d2;
+                    out = out + mul(rho, L) * (fminf(G, 1.f) * r0.w * (1.f / DDGI_PI));
+                }
+            }
+        }
+    }
+    radiance[pix] = make_float4(out.x, out.y, out.z, 1.f);
+}
+
+inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
+
+}  // namespace
+
+cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
+                           const GBufView& g, cudaStream_t st) {
+    if (g.width == 0 || g.height == 0) return cudaSuccess;
+    dim3 b(16, 8);
+    k_gbuffer<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, cam, prev ? *prev : cam, prev != nullptr, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
+                         const ResView& r, const float4* resid, float4* radiance,
+                         cudaStream_t st) {
+    if (g.width == 0 || g.height == 0) return cudaSuccess;
+    dim3 b(16, 8);
+    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance);
+    return cudaGetLastError();
+}

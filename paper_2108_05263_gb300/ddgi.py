@@ -1,0 +1,376 @@
+"""ctypes binding of libddgi.so (``include/ddgi.h``): the same entry points,
+argument marshalling only.  Every step of the frame runs in the library's
+CUDA kernels; there is no CPU path.  Buffers are torch CUDA tensors; streams
+are torch CUDA streams (default: the current stream).
+
+Raises ``RuntimeError`` at load time if the library has not been built, and
+``DDGIError`` whenever an entry point returns a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_NOT_READY = -3
+ERR_TRAVERSAL_LIMIT = -4
+ERR_BOUNDS = -5
+ERR_OOM = -6
+
+_f3 = C.c_float * 3
+_i3 = C.c_int32 * 3
+
+
+class Scene(C.Structure):
+    _fields_ = [("num_tris", C.c_uint32), ("vertices", C.c_void_p), ("albedo", C.c_void_p),
+                ("emission", C.c_void_p)]
+
+
+class Config(C.Structure):
+    _fields_ = [("origin", _f3), ("spacing", _f3), ("counts", _i3), ("rays_per_probe", C.c_uint32),
+                ("irr_texels", C.c_uint32), ("depth_texels", C.c_uint32), ("hysteresis", C.c_float),
+                ("le_attenuation", C.c_float), ("depth_sharpness", C.c_float),
+                ("num_light_candidates", C.c_uint32), ("num_bsdf_candidates", C.c_uint32),
+                ("temporal_mcap", C.c_float), ("spatial_neighbours", C.c_uint32),
+                ("spatial_radius", C.c_uint32), ("normal_reject_cos", C.c_float),
+                ("depth_reject_frac", C.c_float), ("seed", C.c_uint32)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", _f3), ("fwd", _f3), ("right", _f3), ("up", _f3),
+                ("tan_half_fovy", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class GBuf(C.Structure):
+    _fields_ = [("g0", C.c_void_p), ("g1", C.c_void_p), ("g2", C.c_void_p),
+                ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class Res(C.Structure):
+    _fields_ = [("r0", C.c_void_p), ("r1", C.c_void_p), ("r2", C.c_void_p),
+                ("num_pixels", C.c_uint32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("num_tris", C.c_uint32), ("num_emitters", C.c_uint32), ("num_probes", C.c_uint32),
+                ("rays_per_probe", C.c_uint32), ("irr_tile", C.c_uint32), ("depth_tile", C.c_uint32),
+                ("bvh_nodes", C.c_uint32), ("bvh_depth", C.c_uint32), ("updates", C.c_uint32),
+                ("device_bytes", C.c_uint64)]
+
+
+class DDGIError(RuntimeError):
+    def __init__(self, fn, code, msg=""):
+        super().__init__(f"{fn} returned {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# entry points declared in include/ddgi.h (all return ddgi_status except the last)
+EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
+           "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
+           "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
+           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_get_status",
+           "ddgi_last_error"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libddgi.so (fails loudly if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libddgi.so not built ({p}); run paper_2108_05263_gb300.build.build()")
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    st = C.c_int32
+    L.ddgi_create.argtypes = [C.POINTER(Scene), C.POINTER(Config), C.POINTER(vp)]
+    L.ddgi_destroy.argtypes = [vp]
+    L.ddgi_get_info.argtypes = [vp, C.POINTER(Info)]
+    for fn in ("ddgi_probe_update", "ddgi_probe_trace", "ddgi_probe_blend"):
+        getattr(L, fn).argtypes = [vp, C.c_uint32, vp]
+    L.ddgi_probe_state_get.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_uint32), vp]
+    L.ddgi_probe_state_set.argtypes = [vp, vp, vp, vp, C.c_uint32, vp]
+    L.ddgi_probe_rays_get.argtypes = [vp, vp, vp]
+    L.ddgi_probe_rays_set.argtypes = [vp, vp, vp]
+    L.ddgi_gbuffer.argtypes = [vp, C.POINTER(Camera), C.POINTER(Camera), C.POINTER(GBuf), vp]
+    L.restir_initial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, C.c_uint32, vp]
+    L.restir_temporal.argtypes = [vp, C.POINTER(GBuf), C.POINTER(GBuf), C.POINTER(C.c_float),
+                                  C.POINTER(Res), C.POINTER(Res), C.POINTER(Res), C.c_uint32, vp]
+    L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
+                                 C.c_uint32, vp]
+    L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
+    L.ddgi_get_status.argtypes = [vp, vp]
+    L.ddgi_last_error.argtypes = [vp]
+    L.ddgi_last_error.restype = C.c_char_p
+    for fn in EXPORTS[:-1]:
+        getattr(L, fn).restype = st
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# buffers
+# ---------------------------------------------------------------------------
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class GBuffer:
+    """Three [N, 4] float32 planes (see ddgi_gbuf)."""
+
+    def __init__(self, width: int, height: int, device="cuda", planes=None):
+        self.width, self.height = width, height
+        n = width * height
+        if planes is None:
+            planes = [torch.empty((n, 4), dtype=torch.float32, device=device) for _ in range(3)]
+        self.g0, self.g1, self.g2 = planes
+
+    def c(self) -> GBuf:
+        return GBuf(self.g0.data_ptr(), self.g1.data_ptr(), self.g2.data_ptr(), self.width, self.height)
+
+    def numpy(self):
+        return tuple(t.cpu().numpy() for t in (self.g0, self.g1, self.g2))
+
+
+class Reservoirs:
+    """r0, r1: [N, 4] float32; r2: [N, 2] int32 holding uint32 bits."""
+
+    def __init__(self, n: int, device="cuda", planes=None):
+        self.n = n
+        if planes is None:
+            planes = (torch.empty((n, 4), dtype=torch.float32, device=device),
+                      torch.empty((n, 4), dtype=torch.float32, device=device),
+                      torch.empty((n, 2), dtype=torch.int32, device=device))
+        self.r0, self.r1, self.r2 = planes
+
+    def c(self) -> Res:
+        return Res(self.r0.data_ptr(), self.r1.data_ptr(), self.r2.data_ptr(), self.n)
+
+    def numpy(self):
+        return (self.r0.cpu().numpy(), self.r1.cpu().numpy(),
+                self.r2.cpu().numpy().view(np.uint32))
+
+
+def camera(cam) -> Camera:
+    """From any object with pos/fwd/right/up/tan_half_fovy/width/height."""
+    return Camera(_f3(*map(float, cam.pos)), _f3(*map(float, cam.fwd)), _f3(*map(float, cam.right)),
+                  _f3(*map(float, cam.up)), float(cam.tan_half_fovy), int(cam.width), int(cam.height))
+
+
+def config_from(grid, settings) -> Config:
+    """From a probe grid (origin/spacing/counts) and method settings."""
+    c = Config()
+    c.origin = _f3(*map(float, grid.origin))
+    c.spacing = _f3(*map(float, grid.spacing))
+    c.counts = _i3(*map(int, grid.counts))
+    c.rays_per_probe = settings.rays_per_probe
+    c.irr_texels = settings.irr_texels
+    c.depth_texels = settings.depth_texels
+    c.hysteresis = settings.hysteresis
+    c.le_attenuation = settings.le_attenuation
+    c.depth_sharpness = settings.depth_sharpness
+    c.num_light_candidates = settings.num_light_candidates
+    c.num_bsdf_candidates = settings.num_bsdf_candidates
+    c.temporal_mcap = settings.temporal_mcap
+    c.spatial_neighbours = settings.spatial_neighbours
+    c.spatial_radius = settings.spatial_radius
+    c.normal_reject_cos = settings.normal_reject_cos
+    c.depth_reject_frac = settings.depth_reject_frac
+    c.seed = settings.seed
+    return c
+
+
+class Context:
+    """Owns a ddgi_ctx (scene BVH, emitter table, probe maps, probe rays)."""
+
+    def __init__(self, verts, albedo, emission, grid, settings):
+        L = load()
+        self.L = L
+        self._v = np.ascontiguousarray(verts, np.float32)
+        self._a = np.ascontiguousarray(albedo, np.float32)
+        self._e = np.ascontiguousarray(emission, np.float32)
+        sc = Scene(self._v.shape[0], self._v.ctypes.data, self._a.ctypes.data, self._e.ctypes.data)
+        self.cfg = config_from(grid, settings)
+        self.settings = settings
+        h = C.c_void_p()
+        rc = L.ddgi_create(C.byref(sc), C.byref(self.cfg), C.byref(h))
+        if rc != OK:
+            raise DDGIError("ddgi_create", rc)
+        self.h = h
+        self.info = self.get_info()
+
+    @staticmethod
+    def from_scene(sc, settings=None) -> "Context":
+        return Context(sc.verts, sc.albedo, sc.emission, sc.grid, settings or sc.settings)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ddgi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, fn, rc):
+        if rc != OK:
+            raise DDGIError(fn, rc, self.L.ddgi_last_error(self.h).decode())
+
+    def get_info(self) -> Info:
+        i = Info()
+        self._check("ddgi_get_info", self.L.ddgi_get_info(self.h, C.byref(i)))
+        return i
+
+    # --- probe update (Sec. 3.2) ---
+    def probe_update(self, frame, stream=None):
+        self._check("ddgi_probe_update", self.L.ddgi_probe_update(self.h, frame, _stream(stream)))
+
+    def probe_trace(self, frame, stream=None):
+        self._check("ddgi_probe_trace", self.L.ddgi_probe_trace(self.h, frame, _stream(stream)))
+
+    def probe_blend(self, frame, stream=None):
+        self._check("ddgi_probe_blend", self.L.ddgi_probe_blend(self.h, frame, _stream(stream)))
+
+    def probe_state_get(self, stream=None):
+        i = self.info
+        P = i.num_probes
+        irr = np.zeros((P, i.irr_tile, i.irr_tile, 4), np.float32)
+        dep = np.zeros((P, i.depth_tile, i.depth_tile, 2), np.float32)
+        off = np.zeros((P, 4), np.float32)
+        upd = C.c_uint32()
+        self._check("ddgi_probe_state_get",
+                    self.L.ddgi_probe_state_get(self.h, irr.ctypes.data, dep.ctypes.data,
+                                                off.ctypes.data, C.byref(upd), _stream(stream)))
+        return irr, dep, off, upd.value
+
+    def probe_state_set(self, irr=None, depth=None, offsets=None, updates=0, stream=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float32) for a in (irr, depth, offsets)]
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        self._check("ddgi_probe_state_set",
+                    self.L.ddgi_probe_state_set(self.h, ptrs[0], ptrs[1], ptrs[2], updates,
+                                                _stream(stream)))
+
+    def probe_rays_get(self, stream=None):
+        i = self.info
+        out = np.zeros((i.num_probes, i.rays_per_probe, 4), np.float32)
+        self._check("ddgi_probe_rays_get", self.L.ddgi_probe_rays_get(self.h, out.ctypes.data, _stream(stream)))
+        return out
+
+    def probe_rays_set(self, rays, stream=None):
+        a = np.ascontiguousarray(rays, np.float32)
+        self._check("ddgi_probe_rays_set", self.L.ddgi_probe_rays_set(self.h, a.ctypes.data, _stream(stream)))
+
+    # --- per-frame passes ---
+    def gbuffer(self, cam, prev_cam, out: GBuffer, stream=None):
+        c = camera(cam)
+        pc = camera(prev_cam) if prev_cam is not None else None
+        g = out.c()
+        self._check("ddgi_gbuffer", self.L.ddgi_gbuffer(self.h, C.byref(c), C.byref(pc) if pc else None,
+                                                        C.byref(g), _stream(stream)))
+
+    def restir_initial(self, g: GBuffer, out: Reservoirs, residual: torch.Tensor, frame, stream=None):
+        gc, oc = g.c(), out.c()
+        self._check("restir_initial", self.L.restir_initial(self.h, C.byref(gc), C.byref(oc),
+                                                            _ptr(residual), frame, _stream(stream)))
+
+    def restir_temporal(self, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Reservoirs,
+                        prev: Reservoirs, out: Reservoirs, frame, stream=None):
+        gc, gpc, cc, pc, oc = g.c(), gp.c(), cur.c(), prev.c(), out.c()
+        cp = _f3(*map(float, prev_cam_pos))
+        self._check("restir_temporal",
+                    self.L.restir_temporal(self.h, C.byref(gc), C.byref(gpc), cp, C.byref(cc),
+                                           C.byref(pc), C.byref(oc), frame, _stream(stream)))
+
+    def restir_spatial(self, g: GBuffer, src: Reservoirs, out: Reservoirs, frame, pass_idx,
+                       stream=None):
+        gc, ic, oc = g.c(), src.c(), out.c()
+        self._check("restir_spatial", self.L.restir_spatial(self.h, C.byref(gc), C.byref(ic),
+                                                            C.byref(oc), frame, pass_idx,
+                                                            _stream(stream)))
+
+    def shade(self, g: GBuffer, res: Reservoirs, residual: torch.Tensor, radiance: torch.Tensor,
+              stream=None):
+        gc, rc = g.c(), res.c()
+        self._check("ddgi_shade", self.L.ddgi_shade(self.h, C.byref(gc), C.byref(rc), _ptr(residual),
+                                                    _ptr(radiance), _stream(stream)))
+
+    def get_status(self, stream=None) -> int:
+        return self.L.ddgi_get_status(self.h, _stream(stream))
+
+
+class Frame:
+    """Per-frame buffers of one resolution and a driver for the whole path
+    (probe update, initial, temporal, spatial passes, shade) on one stream;
+    ping-pongs the G-buffer and the final reservoirs between frames."""
+
+    def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda"):
+        n = width * height
+        self.ctx, self.width, self.height, self.n = ctx, width, height, n
+        self.spatial_passes = spatial_passes
+        self.g = [GBuffer(width, height, device), GBuffer(width, height, device)]
+        self.res = [Reservoirs(n, device) for _ in range(4)]
+        self.resid = torch.empty((n, 4), dtype=torch.float32, device=device)
+        self.radiance = torch.empty((n, 4), dtype=torch.float32, device=device)
+        self.prev_final: Optional[Reservoirs] = None
+        self.prev_cam = None
+        self.cur = 0
+
+    def render(self, frame: int, cam, gbuf: Optional[GBuffer] = None, stream=None,
+               probe_update=True):
+        """One frame.  If ``gbuf`` is given it is used as this frame's
+        G-buffer (the primary-visibility pass is skipped)."""
+        ctx = self.ctx
+        if probe_update:
+            ctx.probe_update(frame, stream)
+        g = gbuf
+        if g is None:
+            g = self.g[self.cur]
+            ctx.gbuffer(cam, self.prev_cam, g, stream)
+        init, tmp = self._free_pair()
+        ctx.restir_initial(g, init, self.resid, frame, stream)
+        res = init
+        if self.prev_final is not None:
+            ctx.restir_temporal(g, self._prev_g, self.prev_cam.pos, init, self.prev_final, tmp, frame, stream)
+            res = tmp
+        for i in range(self.spatial_passes):
+            nxt = self._other(res)
+            ctx.restir_spatial(g, res, nxt, frame, i, stream)
+            res = nxt
+        ctx.shade(g, res, self.resid, self.radiance, stream)
+        self.prev_final, self._prev_g, self.prev_cam = res, g, cam
+        self.cur ^= 1
+        return self.radiance
+
+    def _free_pair(self):
+        free = [r for r in self.res if r is not self.prev_final]
+        self._free = free
+        return free[0], free[1]
+
+    def _other(self, r):
+        for c in self._free:
+            if c is not r:
+                return c
+        raise AssertionError

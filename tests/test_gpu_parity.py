@@ -1,0 +1,440 @@
+"""GPU <-> oracle parity of every pass, through the C ABI.
+
+Pass-isolated tests feed the CUDA pass exactly the inputs the oracle pass
+receives (oracle upstream outputs, or seeded synthetic buffers) and compare
+element by element.  Chain tests run the whole frame on both sides.
+
+Tolerances (float32 kernels vs the fp64 oracle):
+* hit triangles, reservoir triangles / tags: identical wherever no floating
+  point tie decides; >= 99.9 % identical overall;
+* radiance, W, cached radiance, residual, probe maps: |gpu - ref| <=
+  1e-4 |ref| + ABS per value, on >= 99.9 % of the values (ABS is a small
+  absolute floor stated per quantity: values at the float32 resolution of
+  their neighbours).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_05263_gb300 import build
+    build.build()
+    from paper_2108_05263_gb300 import ddgi
+    ddgi.load()
+    return ddgi
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _t(a, dtype=None):
+    import torch
+    a = np.ascontiguousarray(a)
+    t = torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a)
+    return t.cuda()
+
+
+def _gbuf_to_gpu(dd, g):
+    g0, g1, g2 = g.planes()
+    return dd.GBuffer(g.width, g.height, planes=[_t(g0), _t(g1), _t(g2)])
+
+
+def _res_to_gpu(dd, r):
+    r0, r1, r2 = r.planes()
+    return dd.Reservoirs(r0.shape[0], planes=(_t(r0), _t(r1), _t(r2)))
+
+
+def _vol_to_gpu(ctx, vol):
+    P = vol.P
+    irr = np.zeros(vol.irr.shape[:-1] + (4,), np.float32)
+    irr[..., :3] = vol.irr
+    off = np.zeros((P, 4), np.float32)
+    off[:, :3] = vol.offset
+    ctx.probe_state_set(irr, vol.depth.astype(np.float32), off, vol.updates)
+
+
+def _close(gpu, ref, abs_floor, rel=REL):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.abs(gpu - ref) <= rel * np.abs(ref) + abs_floor
+
+
+def _frac(mask):
+    return float(np.mean(mask)) if mask.size else 1.0
+
+
+def _res_compare(gr, orr, w_abs=1e-6, l_abs=1e-5, what=""):
+    """GPU reservoir planes vs oracle Reservoirs; returns tag agreement."""
+    r0, r1, r2 = gr
+    tri = r2[:, 0].view(np.int32)
+    same = (tri == orr.tri) & (r2[:, 1] == orr.tag)
+    agree = _frac(same)
+    assert agree >= 0.999, f"{what}: selections agree on {agree:.5f}"
+    np.testing.assert_array_equal(r1[:, 3], orr.M.astype(np.float32))
+    ok = same & (orr.tri >= 0)
+    assert _frac(_close(r0[ok, 3], orr.W[ok], w_abs)) >= 0.999, what
+    assert _frac(_close(r1[ok, :3], orr.L[ok], l_abs).all(axis=1)) >= 0.999, what
+    assert _frac(_close(r0[ok, :3], orr.y[ok], 1e-5).all(axis=1)) >= 0.999, what
+    return agree
+
+
+# ---------------------------------------------------------------------------
+# tiny room: every pass in isolation, all pixels
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny(dd, orc):
+    """Oracle run of the tiny room for two frames (the GPU inputs)."""
+    sc = scenegen.tiny_room()
+    R = orc.Renderer(sc)
+    frames = [R.frame(f) for f in range(2)]
+    vol_after = R.vol.copy()
+    return sc, R, frames, vol_after
+
+
+def test_gbuffer_parity(dd, orc, tiny):
+    sc, R, _, _ = tiny
+    ctx = dd.Context.from_scene(sc)
+    cam, pc = sc.cameras[1], sc.cameras[0]
+    g = dd.GBuffer(cam.width, cam.height)
+    ctx.gbuffer(cam, pc, g)
+    g0, g1, g2 = g.numpy()
+    ref = orc.gbuffer(orc.Scene(sc), cam, pc)
+    tri = g1[:, 3].view(np.int32)
+    assert _frac(tri == ref.tri) >= 0.999
+    ok = tri == ref.tri
+    assert _frac(_close(g0[ok, :3], ref.pos[ok], 1e-5).all(1)) == 1.0
+    assert _frac(_close(g0[ok, 3], ref.dist[ok], 1e-6)) == 1.0
+    np.testing.assert_allclose(g1[ok, :3], ref.nrm[ok], atol=1e-6)
+    np.testing.assert_array_equal(g2[ok, 3].view(np.int32), ref.prev[ok])
+    assert ctx.get_status() == dd.OK
+
+
+def test_probe_trace_and_blend_parity(dd, orc, tiny):
+    sc, _, _, _ = tiny
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    for f in range(3):
+        orc.probe_update(S, vol, f)
+    ctx = dd.Context.from_scene(sc)
+    _vol_to_gpu(ctx, vol)
+    # trace, isolated: same maps in, rays out
+    ctx.probe_trace(3)
+    rays = ctx.probe_rays_get()
+    ref = orc.probe_trace(S, vol, 3)
+    hit_same = np.sign(rays[..., 3]) == np.sign(ref[..., 3])
+    assert _frac(hit_same) >= 0.999
+    assert _frac(_close(np.abs(rays[..., 3])[hit_same], np.abs(ref[..., 3])[hit_same], 1e-6)) >= 0.999
+    assert _frac(_close(rays[..., :3][hit_same], ref[..., :3][hit_same], 1e-5).all(-1)) >= 0.999
+    # blend, isolated: oracle rays in, maps out
+    ctx.probe_rays_set(ref.astype(np.float32))
+    ctx.probe_blend(3)
+    orc.probe_blend(vol, ref, 3, S.settings)
+    irr, dep, _, upd = ctx.probe_state_get()
+    assert upd == 4
+    assert _frac(_close(irr[..., :3], vol.irr, 1e-5)) >= 0.9999
+    assert _frac(_close(dep, vol.depth, 1e-5)) >= 0.9999
+    assert ctx.get_status() == dd.OK
+
+
+def test_probe_update_chain_parity(dd, orc, tiny):
+    sc, _, _, _ = tiny
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    ctx = dd.Context.from_scene(sc)
+    for f in range(6):
+        orc.probe_update(S, vol, f)
+        ctx.probe_update(f)
+    irr, dep, _, _ = ctx.probe_state_get()
+    assert _frac(_close(irr[..., :3], vol.irr, 1e-4, rel=1e-3)) >= 0.999
+    assert _frac(_close(dep, vol.depth, 1e-4, rel=1e-3)) >= 0.999
+    assert np.abs(irr[..., :3] - vol.irr).max() <= 1e-3 * np.abs(vol.irr).max()
+
+
+def test_initial_parity(dd, orc, tiny):
+    import torch
+    sc, R, frames, _ = tiny
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    for f in range(3):
+        orc.probe_update(S, vol, f)
+    g = frames[1]["gbuffer"]
+    ref, resid = orc.restir_initial(S, vol, g, 7)
+    ctx = dd.Context.from_scene(sc)
+    _vol_to_gpu(ctx, vol)
+    gg = _gbuf_to_gpu(dd, g)
+    out = dd.Reservoirs(g.tri.shape[0])
+    rr = torch.empty((g.tri.shape[0], 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(gg, out, rr, 7)
+    _res_compare(out.numpy(), ref, what="initial")
+    assert _frac(_close(rr.cpu().numpy()[:, :3], resid, 1e-5).all(1)) >= 0.999
+    assert ctx.get_status() == dd.OK
+
+
+def test_temporal_parity(dd, orc, tiny):
+    sc, R, frames, _ = tiny
+    S = orc.Scene(sc)
+    f0, f1 = frames
+    ref = orc.restir_temporal(S, f1["gbuffer"], f0["gbuffer"], sc.cameras[0].pos, f1["initial"], f0["final"], 1)
+    ctx = dd.Context.from_scene(sc)
+    out = dd.Reservoirs(ref.W.shape[0])
+    ctx.restir_temporal(_gbuf_to_gpu(dd, f1["gbuffer"]), _gbuf_to_gpu(dd, f0["gbuffer"]), sc.cameras[0].pos,
+                        _res_to_gpu(dd, f1["initial"]), _res_to_gpu(dd, f0["final"]), out, 1)
+    _res_compare(out.numpy(), ref, what="temporal")
+
+
+def test_spatial_parity(dd, orc, tiny):
+    sc, R, frames, _ = tiny
+    S = orc.Scene(sc)
+    f1 = frames[1]
+    ref = orc.restir_spatial(S, f1["gbuffer"], f1["temporal"], 1, 0)
+    ctx = dd.Context.from_scene(sc)
+    out = dd.Reservoirs(ref.W.shape[0])
+    ctx.restir_spatial(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["temporal"]), out, 1, 0)
+    _res_compare(out.numpy(), ref, what="spatial")
+
+
+def test_shade_parity(dd, orc, tiny):
+    import torch
+    sc, R, frames, vol_after = tiny
+    S = orc.Scene(sc)
+    f1 = frames[1]
+    ref = orc.shade(S, vol_after, f1["gbuffer"], f1["final"], f1["resid"])
+    ctx = dd.Context.from_scene(sc)
+    _vol_to_gpu(ctx, vol_after)
+    n = ref.shape[0]
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    resid = np.zeros((n, 4), np.float32)
+    resid[:, :3] = f1["resid"]
+    ctx.shade(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["final"]), _t(resid), rad)
+    out = rad.cpu().numpy()
+    assert _frac(_close(out[:, :3], ref, 1e-5).all(1)) >= 0.999
+    assert ctx.get_status() == dd.OK
+
+
+# ---------------------------------------------------------------------------
+# whole frames on both sides
+# ---------------------------------------------------------------------------
+
+def _chain(dd, orc, sc, nframes):
+    R = orc.Renderer(sc)
+    ctx = dd.Context.from_scene(sc)
+    cam0 = sc.cameras[0]
+    fr = dd.Frame(ctx, cam0.width, cam0.height, sc.settings.spatial_passes)
+    stats = []
+    for f in range(nframes):
+        cam = sc.cameras[f % len(sc.cameras)]
+        ref = R.frame(f, cam)
+        rad = fr.render(f, cam).cpu().numpy()[:, :3]
+        r2 = fr.prev_final.r2.cpu().numpy().view(np.uint32)
+        tag_ok = (r2[:, 0].view(np.int32) == ref["final"].tri) & (r2[:, 1] == ref["final"].tag)
+        close = _close(rad, ref["radiance"], 1e-5).all(1)
+        stats.append((_frac(tag_ok), _frac(close)))
+    assert ctx.get_status() == dd.OK
+    return stats
+
+
+def test_whole_frame_chain_tiny_room(dd, orc):
+    stats = _chain(dd, orc, scenegen.tiny_room(), 6)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
+def test_whole_frame_chain_ragged_image(dd, orc):
+    """100 x 75 pixels (not a multiple of the 16 x 8 tiles), camera turned
+    toward a corner so that every wall and the emitter are in view."""
+    sc = scenegen.tiny_room(width=100, height=75, frames=3)
+    sc.cameras = [scenegen._look_camera([0.1, -0.2, 0.3], [-1, 0.6, -0.8], 100, 75, 100.0)] * 3
+    stats = _chain(dd, orc, sc, 3)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
+# ---------------------------------------------------------------------------
+# full-size apartment: sampled outputs with synthetic inputs
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def apt(dd, orc):
+    sc = scenegen.apartment()
+    ctx = dd.Context.from_scene(sc)
+    S = orc.Scene(sc)
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(1920 * 1080, 384, replace=False)).astype(np.int32)
+    return sc, ctx, S, sample
+
+
+def test_apartment_gbuffer_sampled(dd, orc, apt):
+    sc, ctx, S, sample = apt
+    cam, pc = sc.cameras[3], sc.cameras[2]
+    g = dd.GBuffer(cam.width, cam.height)
+    ctx.gbuffer(cam, pc, g)
+    g0, g1, g2 = g.numpy()
+    ref = orc.gbuffer(S, cam, pc, pix=sample)
+    tri = g1[sample, 3].view(np.int32)
+    same = tri == ref.tri
+    assert _frac(same) >= 0.99
+    assert _frac(_close(g0[sample][same, 3], ref.dist[same], 1e-5)) >= 0.99
+    prev_same = g2[sample, 3].view(np.int32) == ref.prev
+    assert _frac(prev_same[same]) >= 0.99
+
+
+def test_apartment_probe_trace_sampled(dd, orc, apt):
+    sc, ctx, S, _ = apt
+    vol = orc.Volume(sc.grid)
+    vol.set_interior(scenegen.synthetic_irradiance_interior(sc.grid, 8, 5),
+                     scenegen.synthetic_depth_interior(sc.grid, 16, 6))
+    vol.updates = 3
+    _vol_to_gpu(ctx, vol)
+    ctx.probe_trace(9)
+    rays = ctx.probe_rays_get()
+    probes = np.array([0, 77, 500, 1023, 1500, 2047], np.int32)
+    ref = orc.probe_trace(S, vol, 9, probes=probes)
+    got = rays[probes]
+    same = np.sign(got[..., 3]) == np.sign(ref[..., 3])
+    assert _frac(same) >= 0.99
+    assert _frac(_close(got[..., :3][same], ref[..., :3][same], 1e-4).all(-1)) >= 0.99
+
+
+def test_apartment_resampling_passes_sampled(dd, orc, apt):
+    """initial / temporal / spatial / shade at 1920x1080 on synthetic
+    G-buffers, reservoirs and probe maps, compared on sampled pixels."""
+    import torch
+    sc, ctx, S, sample = apt
+    W, H = 1920, 1080
+    n = W * H
+    vol = orc.Volume(sc.grid)
+    vol.set_interior(scenegen.synthetic_irradiance_interior(sc.grid, 8, 5),
+                     scenegen.synthetic_depth_interior(sc.grid, 16, 6))
+    vol.updates = 3
+    _vol_to_gpu(ctx, vol)
+    gp = scenegen.synthetic_gbuffer(sc, W, H, 21)
+    gq = scenegen.synthetic_gbuffer(sc, W, H, 22)
+    og = orc.GBuffer.from_planes(*gp, W, H)
+    oq = orc.GBuffer.from_planes(*gq, W, H)
+    gg = dd.GBuffer(W, H, planes=[_t(a) for a in gp])
+    gq_gpu = dd.GBuffer(W, H, planes=[_t(a) for a in gq])
+    # initial
+    out = dd.Reservoirs(n)
+    resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(gg, out, resid, 5)
+    ref, rref = orc.restir_initial(S, vol, og, 5, pix=sample)
+    r0, r1, r2 = out.numpy()
+    _res_compare((r0[sample], r1[sample], r2[sample]), ref, what="initial@1080p")
+    assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-4).all(1)) >= 0.99
+    # temporal / spatial on synthetic reservoirs
+    rc = scenegen.synthetic_reservoirs(sc, n, 31)
+    rp = scenegen.synthetic_reservoirs(sc, n, 32)
+    oc, op = orc.Reservoirs.from_planes(*rc), orc.Reservoirs.from_planes(*rp)
+    cam_prev = np.array([4.0, 1.5, 6.0])
+    tout = dd.Reservoirs(n)
+    ctx.restir_temporal(gg, gq_gpu, cam_prev, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)),
+                        dd.Reservoirs(n, planes=tuple(_t(a) for a in rp)), tout, 5)
+    tref = orc.restir_temporal(S, og, oq, cam_prev, oc, op, 5, pix=sample)
+    t0, t1, t2 = tout.numpy()
+    _res_compare((t0[sample], t1[sample], t2[sample]), tref, what="temporal@1080p")
+    sout = dd.Reservoirs(n)
+    ctx.restir_spatial(gg, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)), sout, 5, 1)
+    sref = orc.restir_spatial(S, og, oc, 5, 1, pix=sample)
+    s0, s1, s2 = sout.numpy()
+    _res_compare((s0[sample], s1[sample], s2[sample]), sref, what="spatial@1080p")
+    # shade
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    rs = np.zeros((n, 4), np.float32)
+    rs[:, :3] = np.random.default_rng(3).uniform(0, 0.1, (n, 3))
+    ctx.shade(gg, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)), _t(rs), rad)
+    shref = orc.shade(S, vol, og, oc, rs[:, :3].astype(np.float64), pix=sample)
+    assert _frac(_close(rad.cpu().numpy()[sample, :3], shref, 1e-4).all(1)) >= 0.99
+    assert ctx.get_status() == dd.OK
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_image_is_a_no_op(dd):
+    import torch
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    g = dd.GBuffer(0, 0)
+    r = dd.Reservoirs(0)
+    z = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(g, r, z, 0)
+    ctx.restir_spatial(g, r, dd.Reservoirs(0), 0, 0)
+    ctx.shade(g, r, z, z)
+    assert ctx.get_status() == dd.OK
+
+
+def test_invalid_pixels_give_empty_reservoirs_and_black(dd):
+    import torch
+    sc = scenegen.tiny_room(width=16, height=16)
+    ctx = dd.Context.from_scene(sc)
+    n = 256
+    g = dd.GBuffer(16, 16)
+    g.g0.zero_()
+    g.g2.zero_()
+    g.g1.zero_()
+    g.g1.view(torch.int32)[:, 3] = -1
+    r = dd.Reservoirs(n)
+    resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(g, r, resid, 0)
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.shade(g, r, resid, rad)
+    r0, r1, r2 = r.numpy()
+    assert np.all(r2[:, 0] == 0xFFFFFFFF) and np.all(r1[:, 3] == 0)
+    assert np.all(rad.cpu().numpy()[:, :3] == 0)
+
+
+def test_argument_errors(dd):
+    import torch
+    sc = scenegen.tiny_room(width=16, height=16)
+    ctx = dd.Context.from_scene(sc)
+    g = dd.GBuffer(16, 16)
+    short = dd.Reservoirs(100)
+    resid = torch.empty((256, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(dd.DDGIError) as e:
+        ctx.restir_initial(g, short, resid, 0)
+    assert e.value.code == dd.ERR_INVALID_ARG
+    r = dd.Reservoirs(256)
+    with pytest.raises(dd.DDGIError):
+        ctx.restir_spatial(g, r, r, 0, 0)            # aliasing
+    bad = torch.empty((257 * 4 + 1,), dtype=torch.float32, device="cuda")[1:].view(257, 4)[:256]
+    with pytest.raises(dd.DDGIError):
+        ctx.shade(g, r, bad, resid)                  # misaligned residual
+    assert ctx.get_status() == dd.OK
+
+
+def test_scene_without_emitters(dd, orc):
+    """No emissive triangle: no light candidates, M = number of BSDF rays."""
+    import torch
+    sc = scenegen.tiny_room(width=32, height=32)
+    sc.emission = np.zeros_like(sc.emission)
+    ctx = dd.Context.from_scene(sc)
+    assert ctx.info.num_emitters == 0
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    vol.set_interior(np.ones((64, 8, 8, 3)), np.full((64, 16, 16, 2), 5.0))
+    _vol_to_gpu(ctx, vol)
+    og = orc.gbuffer(S, sc.cameras[0])
+    ref, _ = orc.restir_initial(S, vol, og, 2)
+    out = dd.Reservoirs(1024)
+    rr = torch.empty((1024, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(_gbuf_to_gpu(dd, og), out, rr, 2)
+    _res_compare(out.numpy(), ref, what="no-emitter initial")
+    assert np.all(out.numpy()[1][:, 3] == 1.0)
