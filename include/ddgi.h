@@ -185,6 +185,17 @@ ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservo
 ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* r,
                        const float* residual, float* radiance, void* stream);
 
+/* Error metrics of Sec. 4 between a rendered image and a reference: out[0] =
+ * mean squared error, out[1] = mean absolute percentage error
+ * mean(|v - ref| / (ref + 0.01)), both over the 3 colour values of every
+ * pixel, accumulated in fp64 (0 for n = 0).  img, ref: device [n][4] floats
+ * (rgb, ignored), 16-byte aligned; out: device double[2]; scratch: device
+ * memory of at least scratch_doubles doubles for per-block partial sums
+ * (2048 always suffice), 8-byte aligned, owned by the caller and overwritten.
+ * Does not depend on a context. */
+ddgi_status ddgi_image_metrics(const float* img, const float* ref, uint32_t n, double* scratch,
+                               uint32_t scratch_doubles, double* out, void* stream);
+
 /* Synchronise `stream`, return (and clear) the device error word:
  * DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded the node-visit cap or the
  * traversal stack, else DDGI_OK. */

@@ -69,6 +69,12 @@ cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, c
 cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                   const ResView& in, const ResView& out, uint32_t frame,
                                   uint32_t pass, cudaStream_t st);
+// image metrics: per-block fp64 partials in `scratch` (2 doubles per block)
+constexpr uint32_t kMetricMaxBlocks = 1024;
+uint32_t metric_blocks(uint32_t n);
+cudaError_t launch_metrics(const float4* img, const float4* ref, uint32_t n, double* scratch,
+                           double* out, cudaStream_t st);
+
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
                          const ResView& r, const float4* resid, float4* radiance,
                          cudaStream_t st);

@@ -78,8 +78,8 @@ _lib = None
 EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
            "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
-           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_get_status",
-           "ddgi_last_error"]
+           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_image_metrics",
+           "ddgi_get_status", "ddgi_last_error"]
 
 
 def lib_path() -> str:
@@ -113,6 +113,7 @@ def load(path: Optional[str] = None):
     L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
                                  C.c_uint32, vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
+    L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
     L.ddgi_get_status.argtypes = [vp, vp]
     L.ddgi_last_error.argtypes = [vp]
     L.ddgi_last_error.restype = C.c_char_p
@@ -170,6 +171,25 @@ class Reservoirs:
     def numpy(self):
         return (self.r0.cpu().numpy(), self.r1.cpu().numpy(),
                 self.r2.cpu().numpy().view(np.uint32))
+
+
+METRIC_SCRATCH_DOUBLES = 2048
+
+
+def image_metrics(img: torch.Tensor, ref: torch.Tensor, scratch: Optional[torch.Tensor] = None,
+                  out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """(MSE, MAPE) of [n, 4] float32 CUDA images as a float64 CUDA tensor [2]."""
+    L = load()
+    n = img.shape[0]
+    if scratch is None:
+        scratch = torch.empty(METRIC_SCRATCH_DOUBLES, dtype=torch.float64, device=img.device)
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=img.device)
+    rc = L.ddgi_image_metrics(_ptr(img), _ptr(ref), n, _ptr(scratch), scratch.numel(), _ptr(out),
+                              _stream(stream))
+    if rc != OK:
+        raise DDGIError("ddgi_image_metrics", rc)
+    return out
 
 
 def camera(cam) -> Camera:

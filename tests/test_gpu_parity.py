@@ -438,3 +438,29 @@ def test_scene_without_emitters(dd, orc):
     ctx.restir_initial(_gbuf_to_gpu(dd, og), out, rr, 2)
     _res_compare(out.numpy(), ref, what="no-emitter initial")
     assert np.all(out.numpy()[1][:, 3] == 1.0)
+
+
+# ---------------------------------------------------------------------------
+# image metrics (Sec. 4): MSE and MAPE in fp64
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 1920 * 1080 + 7])
+def test_image_metrics_match_the_oracle(dd, orc, n):
+    import torch
+    rng = np.random.default_rng(n)
+    img = rng.exponential(1.0, (n, 4)).astype(np.float32)
+    ref = rng.exponential(1.0, (n, 4)).astype(np.float32)
+    ref[: n // 3, :3] = 0.0                          # black reference pixels: epsilon matters
+    out = dd.image_metrics(_t(img), _t(ref)).cpu().numpy()
+    if n == 0:
+        np.testing.assert_array_equal(out, [0.0, 0.0])
+        return
+    exp = [orc.mse(img[:, :3], ref[:, :3]), orc.mape(img[:, :3], ref[:, :3])]
+    np.testing.assert_allclose(out, exp, rtol=1e-12)
+
+
+def test_image_metrics_rejects_short_scratch(dd):
+    import torch
+    img = torch.zeros((4096 * 1024, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(dd.DDGIError):
+        dd.image_metrics(img, img, scratch=torch.empty(16, dtype=torch.float64, device="cuda"))
