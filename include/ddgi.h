@@ -196,6 +196,24 @@ ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs*
 ddgi_status ddgi_image_metrics(const float* img, const float* ref, uint32_t n, double* scratch,
                                uint32_t scratch_doubles, double* out, void* stream);
 
+/* Allocation-free form of ddgi_image_metrics (the paper has no counterpart:
+ * this exists for callers that must not call cudaMalloc, e.g. a plug-in whose
+ * host application owns all device memory, or a real-time thread where an
+ * allocation and its implicit device synchronisation are not allowed).
+ * Same inputs, output and result as ddgi_image_metrics, but the partial sums
+ * live in a 16 KiB array inside the library that every GPU which loads the
+ * library keeps until the process exits; nothing is allocated.
+ *  - n must be <= 2^26 pixels; larger n returns DDGI_ERR_INVALID_ARG.
+ *  - The first call on each device looks up that array's device address (with
+ *    the device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (different
+ *    streams, or different host threads) race and may return wrong values;
+ *    serialise them.  Each call writes every partial sum it reads, so what an
+ *    earlier call left behind does not matter. */
+ddgi_status ddgi_image_metrics_static(const float* img, const float* ref, uint32_t n,
+                                      double* out, void* stream);
+
 /* Synchronise `stream`, return (and clear) the device error word:
  * DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded the node-visit cap or the
  * traversal stack, else DDGI_OK. */

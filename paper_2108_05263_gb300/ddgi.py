@@ -79,7 +79,7 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_image_metrics",
-           "ddgi_get_status", "ddgi_last_error"]
+           "ddgi_image_metrics_static", "ddgi_get_status", "ddgi_last_error"]
 
 
 def lib_path() -> str:
@@ -114,6 +114,7 @@ def load(path: Optional[str] = None):
                                  C.c_uint32, vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
     L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
+    L.ddgi_image_metrics_static.argtypes = [vp, vp, C.c_uint32, vp, vp]
     L.ddgi_get_status.argtypes = [vp, vp]
     L.ddgi_last_error.argtypes = [vp]
     L.ddgi_last_error.restype = C.c_char_p
