@@ -23,6 +23,9 @@ struct ddgi_ctx {
     float4* evert = nullptr;
     float* cdf = nullptr;
     uint32_t* etri = nullptr;
+    uint32_t* guide = nullptr;
+    uint32_t G = 0;
+    uint32_t emitters_reflect = 0;
     float area_total = 0.f;
     float4* irr = nullptr;
     float2* depth = nullptr;
@@ -108,6 +111,9 @@ SceneView scene_view(ddgi_ctx* c) {
     s.cdf = c->cdf;
     s.etri = c->etri;
     s.evert = c->evert;
+    s.guide = c->guide;
+    s.guide_size = c->G;
+    s.emitters_reflect = c->emitters_reflect;
     s.num_emitters = c->E;
     s.area_total = c->area_total;
     s.err = c->err;
@@ -286,9 +292,15 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
             acc += 0.5 * l;
             cdf.push_back((float)acc);
             etri.push_back(i);
-            evert.push_back(make_float4(v[0], v[1], v[2], 0.f));
-            evert.push_back(make_float4(v[3] - v[0], v[4] - v[1], v[5] - v[2], 0.f));
-            evert.push_back(make_float4(v[6] - v[0], v[7] - v[1], v[8] - v[2], 0.f));
+            // packed record: v0 + triangle id, e1 + Le.r, e2 + Le.g, normal + Le.b
+            uint32_t tid = i;
+            float tbits;
+            std::memcpy(&tbits, &tid, 4);
+            evert.push_back(make_float4(v[0], v[1], v[2], tbits));
+            evert.push_back(make_float4(v[3] - v[0], v[4] - v[1], v[5] - v[2], e[0]));
+            evert.push_back(make_float4(v[6] - v[0], v[7] - v[1], v[8] - v[2], e[1]));
+            evert.push_back(make_float4(nrm[i].x, nrm[i].y, nrm[i].z, e[2]));
+            if (a[0] > 0.f || a[1] > 0.f || a[2] > 0.f) ctx->emitters_reflect = 1;
         }
     }
     ctx->E = (uint32_t)etri.size();
@@ -297,6 +309,24 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
         delete ctx;
         return DDGI_ERR_INVALID_ARG;   // emissive triangles of zero area
     }
+    // guide table for the emitter search: guide[j] = first emitter whose
+    // cumulative area exceeds (j / G) * total, evaluated in float exactly as
+    // the kernel forms its search target, so a scan from guide[floor(u G)]
+    // ends on the same emitter as a search over the whole table
+    std::vector<uint32_t> guide;
+    if (ctx->E > 0) {
+        uint32_t G = 1;
+        while (G < ctx->E && G < (1u << 16)) G <<= 1;
+        guide.resize(G);
+        const float total = cdf.back();
+        uint32_t i = 0;
+        for (uint32_t j = 0; j < G; ++j) {
+            float Tj = ((float)j / (float)G) * total;
+            while (i < ctx->E - 1 && !(Tj < cdf[i])) ++i;
+            guide[j] = i;
+        }
+    }
+    ctx->G = (uint32_t)guide.size();
     // spherical Fibonacci directions (fp64 on the host)
     const uint32_t R = cfg->rays_per_probe;
     std::vector<float4> sf(R);
@@ -318,7 +348,8 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(nrm, T)
     ALLOC(alb, T)
     ALLOC(emi, T)
-    ALLOC(evert, 3ull * ctx->E)
+    ALLOC(evert, 4ull * ctx->E)
+    ALLOC(guide, ctx->G)
     ALLOC(cdf, ctx->E)
     ALLOC(etri, ctx->E)
     ALLOC(irr, P * ti * ti)
@@ -339,6 +370,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     up(ctx->evert, evert.data(), evert.size() * sizeof(float4));
     up(ctx->cdf, cdf.data(), cdf.size() * sizeof(float));
     up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
+    up(ctx->guide, guide.data(), guide.size() * sizeof(uint32_t));
     up(ctx->sf, sf.data(), R * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->depth, 0, P * td * td * sizeof(float2));

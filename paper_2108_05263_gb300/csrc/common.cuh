@@ -78,7 +78,10 @@ struct SceneView {
     const float4* emi;       // emission rgb, emissive flag (1/0)
     const float* cdf;        // cumulative emitter area (float), [num_emitters]
     const uint32_t* etri;    // emitter triangle ids
-    const float4* evert;     // per emitter: v0, e1 = v1 - v0, e2 = v2 - v0
+    const float4* evert;     // per emitter: (v0, tri), (e1, Le.r), (e2, Le.g), (n, Le.b)
+    const uint32_t* guide;   // emitter search start per 1/guide_size of the area
+    uint32_t guide_size;
+    uint32_t emitters_reflect;   // some emitter has albedo > 0
     uint32_t num_emitters;
     float area_total;
     uint32_t* err;           // device error word

@@ -15,18 +15,14 @@ struct Sel {
 };
 
 __device__ __forceinline__ uint32_t sample_emitter(const SceneView& s, float u) {
-    // first emitter whose cumulative area exceeds u * total (binary search)
-    uint32_t E = s.num_emitters;
-    float target = u * __ldg(s.cdf + E - 1);
-    uint32_t lo = 0, hi = E - 1;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (target < __ldg(s.cdf + mid))
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
+    // first emitter whose cumulative area exceeds u * total: start at the
+    // guide entry of u (never past the answer) and scan forward
+    const uint32_t E = s.num_emitters;
+    const float target = u * __ldg(s.cdf + E - 1);
+    uint32_t j = min((uint32_t)(u * (float)s.guide_size), s.guide_size - 1);
+    uint32_t i = __ldg(s.guide + j);
+    while (i < E - 1 && !(target < __ldg(s.cdf + i))) ++i;
+    return i;
 }
 
 // orthonormal basis around n (Duff et al., JCGT 2017)
@@ -73,25 +69,33 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     for (uint32_t c = 0; c < M; ++c) {
         const uint32_t cp = rng_cand(prefix, c);
         f3 y, L;
-        float d2, cx, cy;
+        float d2, cx, cy, pL;
         uint32_t tri;
         if (c < NL) {
+            pL = inv_area;
             float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
             float u2 = u01(rng_u32_dim(cp, 2));
             uint32_t e = sample_emitter(s, u0);
-            tri = __ldg(s.etri + e);
-            f3 v0 = xyz(__ldg(s.evert + 3 * e)), e1 = xyz(__ldg(s.evert + 3 * e + 1));
-            f3 e2 = xyz(__ldg(s.evert + 3 * e + 2));
+            const float4* rec = s.evert + 4 * (size_t)e;
+            float4 q0 = __ldg(rec), q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3);
+            tri = __float_as_uint(q0.w);
             float sq = sqrtf(u1);
             float b1 = sq * (1.f - u2), b2 = sq * u2;
-            y = v0 + e1 * b1 + e2 * b2;
+            y = xyz(q0) + xyz(q1) * b1 + xyz(q2) * b2;
             f3 d = y - x;
             d2 = dot(d, d);
             if (d2 <= 0.f) continue;
             f3 w = d * rsqrtf(d2);
             cx = dot(nx, w);
-            cy = fabsf(dot(xyz(__ldg(s.nrm + tri)), w));
-            L = radiance_at(s, v, y, tri, x);
+            f3 ny = xyz(q3);
+            float cyn = dot(ny, w);
+            cy = fabsf(cyn);
+            if (s.emitters_reflect) {
+                L = radiance_at(s, v, y, tri, x);
+            } else {
+                // pure emitter: one-sided Le toward x
+                L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
+            }
         } else {
             float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
             float r = sqrtf(u0);
@@ -102,6 +106,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             Hit h = trace_bvh<false>(s, ray);
             if (h.tri == DDGI_NONE) continue;
             tri = h.tri;
+            pL = __ldg(s.emi + tri).w > 0.f ? inv_area : 0.f;
             y = x + w * h.t;
             d2 = h.t * h.t;
             cx = dot(nx, w);
@@ -114,7 +119,6 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         }
         if (cx <= 0.f) continue;
         float pB = cx * (1.f / DDGI_PI) * cy / d2;
-        float pL = __ldg(s.emi + tri).w > 0.f ? inv_area : 0.f;
         float pmix = ((float)NL * pL + (float)NB * pB) * invM;
         float G = cx * cy / d2;
         float ph = luminance(mul(rho, L)) * (fminf(G, 1.f) * (1.f / DDGI_PI));
