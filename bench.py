@@ -146,14 +146,16 @@ def ncu_traffic(kernel: str):
 # ---------------------------------------------------------------------------
 # algorithmic bytes per pixel of each pass (compulsory HBM traffic)
 # ---------------------------------------------------------------------------
-# G-buffer 48 B/px (3 x 16 B), reservoir 40 B/px (16 + 16 + 8), residual and
-# radiance 16 B/px.  Neighbour reads of the spatial pass and BVH / probe-map
-# reads are cache traffic (the scene, BVH and maps are ~12 MB, L2-resident).
+# G-buffer planes 16 B each (position+distance, normal+triangle, albedo+
+# previous pixel), reservoir record 64 B (it carries its pixel's normal and
+# distance), residual and radiance 16 B/px.  Neighbour reads of the spatial
+# pass and BVH / probe-map reads are cache traffic (scene, BVH and maps are
+# ~12 MB, L2-resident) and are not counted.
 BYTES_PER_PX = {
-    "restir_initial": 48 + 40 + 16,            # G in; reservoir + residual out
-    "restir_temporal": 40 + 48 + 32 + 40 + 40,  # cur res, G, prev G (g0,g1), prev res; out
-    "restir_spatial": 40 + 48 + 40,            # own res, G; out
-    "ddgi_shade": 48 + 24 + 16 + 16,           # G, res (r0, r2), residual; radiance out
+    "restir_initial": 48 + 64 + 16,             # G in; record + residual out
+    "restir_temporal": 64 + 32 + 64 + 64,       # cur record, G (pos, albedo+prev), prev record; out
+    "restir_spatial": 64 + 32 + 64,             # own record, G (pos, albedo); out
+    "ddgi_shade": 48 + 64 + 16 + 16,            # G, record, residual; radiance out
 }
 
 
@@ -217,7 +219,7 @@ def run_ours(args, ws, rank, local):
         mark()
         res = init
         if fr.prev_final is not None:
-            ctx.restir_temporal(g, fr._prev_g, fr.prev_cam.pos, init, fr.prev_final, tmp, f, stream)
+            ctx.restir_temporal(g, fr.prev_cam.pos, init, fr.prev_final, tmp, f, stream)
             res = tmp
         mark()
         for i in range(st.spatial_passes):
@@ -227,7 +229,7 @@ def run_ours(args, ws, rank, local):
             mark()
         ctx.shade(g, res, fr.resid, fr.radiance, stream)
         mark()
-        fr.prev_final, fr._prev_g, fr.prev_cam = res, g, cam
+        fr.prev_final, fr.prev_cam = res, cam
 
     for k in range(args.warmup):
         step(k)

@@ -98,13 +98,18 @@ typedef struct {
     uint32_t width, height;
 } ddgi_gbuf;
 
-/* Reservoirs (device): r0 = y.xyz, W; r1 = cached radiance L(y).rgb, M;
- * r2 = triangle of y (0xFFFFFFFF = empty), tag (origin pixel * 64 +
- * candidate index). */
+/* Reservoirs (device): one 64-byte record per pixel, 64-byte aligned, as
+ * 16 floats:
+ *   [0..3]   y.xyz (selected point), W (unbiased contribution weight)
+ *   [4..7]   cached radiance L(y).rgb leaving y toward its pixel, M
+ *   [8..11]  the owning pixel's normal.xyz and distance to the camera
+ *   [12..15] uint32 bits: triangle of y (0xFFFFFFFF = empty), tag (origin
+ *            pixel * 64 + candidate index), 1 if the owning pixel has a valid
+ *            G-buffer hit else 0, 0.
+ * Words 8..11 and 14 repeat the owning pixel's G-buffer so that neighbour and
+ * previous-frame reuse read one record (two 32-byte sectors) per candidate. */
 typedef struct {
-    float* r0;
-    float* r1;
-    uint32_t* r2;
+    float* rec;
     uint32_t num_pixels;
 } ddgi_reservoirs;
 
@@ -164,9 +169,11 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservo
  * previous-frame pixel if the normals (cos > normal_reject_cos) and the
  * distances (within depth_reject_frac) agree; the previous M is capped at
  * temporal_mcap times the current M; targets use the cached radiance
- * (Sec. 3.6).  prev_cam_pos: host float[3], the previous camera position.
- * out must not alias cur or prev. */
-ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_gbuf* g_prev,
+ * (Sec. 3.6).  The previous pixel's normal, distance and validity come from
+ * its reservoir record (words 8..11, 14); prev may hold a different number of
+ * pixels than cur.  prev_cam_pos: host float[3], the previous camera
+ * position.  out must not alias cur or prev. */
+ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g,
                             const float* prev_cam_pos, const ddgi_reservoirs* cur,
                             const ddgi_reservoirs* prev, const ddgi_reservoirs* out,
                             uint32_t frame, void* stream);

@@ -145,6 +145,8 @@ RestirParams restir_params(ddgi_ctx* c) {
     r.spatial_radius = c->cfg.spatial_radius;
     r.normal_reject_cos = c->cfg.normal_reject_cos;
     r.depth_reject_frac = c->cfg.depth_reject_frac;
+    const uint64_t span = 2ull * c->cfg.spatial_radius + 1ull;
+    r.span_magic = (uint32_t)(((1ull << 32) + span - 1) / span);
     return r;
 }
 
@@ -170,14 +172,13 @@ ddgi_status check_gbuf(ddgi_ctx* ctx, const ddgi_gbuf* g, GBufView* out) {
 
 ddgi_status check_res(ddgi_ctx* ctx, const ddgi_reservoirs* r, uint64_t npix, ResView* out) {
     if (!r) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoirs is NULL");
-    if (r->num_pixels != npix) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir size != gbuffer size");
-    if (npix > 0 && (!r->r0 || !r->r1 || !r->r2))
-        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir plane is NULL");
-    if (!aligned(r->r0, 16) || !aligned(r->r1, 16) || !aligned(r->r2, 8))
-        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir plane misaligned");
-    out->r0 = reinterpret_cast<float4*>(r->r0);
-    out->r1 = reinterpret_cast<float4*>(r->r1);
-    out->r2 = reinterpret_cast<uint2*>(r->r2);
+    if (npix != UINT64_MAX && r->num_pixels != npix)
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir size != gbuffer size");
+    if (npix == UINT64_MAX) npix = r->num_pixels;
+    if (npix > 0 && !r->rec) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir records are NULL");
+    if (!aligned(r->rec, 64)) return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir records not 64-byte aligned");
+    out->rec = reinterpret_cast<float4*>(r->rec);
+    out->n = (uint32_t)npix;
     return DDGI_OK;
 }
 
@@ -513,24 +514,22 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     return DDGI_OK;
 }
 
-ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_gbuf* gbp,
-                            const float* prev_cam_pos, const ddgi_reservoirs* cur,
-                            const ddgi_reservoirs* prev, const ddgi_reservoirs* out,
-                            uint32_t frame, void* stream) {
+ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* gb, const float* prev_cam_pos,
+                            const ddgi_reservoirs* cur, const ddgi_reservoirs* prev,
+                            const ddgi_reservoirs* out, uint32_t frame, void* stream) {
     if (!ctx || !prev_cam_pos) return fail(ctx, DDGI_ERR_INVALID_ARG, "NULL argument");
-    GBufView g, gp;
+    GBufView g;
     ResView rc, rpv, ro;
     ddgi_status s;
     if ((s = check_gbuf(ctx, gb, &g)) != DDGI_OK) return s;
-    if ((s = check_gbuf(ctx, gbp, &gp)) != DDGI_OK) return s;
-    uint64_t n = (uint64_t)g.width * g.height, np = (uint64_t)gp.width * gp.height;
+    uint64_t n = (uint64_t)g.width * g.height;
     if ((s = check_res(ctx, cur, n, &rc)) != DDGI_OK) return s;
-    if ((s = check_res(ctx, prev, np, &rpv)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, prev, UINT64_MAX, &rpv)) != DDGI_OK) return s;
     if ((s = check_res(ctx, out, n, &ro)) != DDGI_OK) return s;
-    if (n > 0 && (ro.r0 == rc.r0 || ro.r0 == rpv.r0 || ro.r2 == rc.r2 || ro.r2 == rpv.r2))
+    if (n > 0 && (ro.rec == rc.rec || ro.rec == rpv.rec))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "output reservoirs alias an input");
     if (!finite3(prev_cam_pos)) return fail(ctx, DDGI_ERR_INVALID_ARG, "camera position not finite");
-    CK(launch_restir_temporal(scene_view(ctx), restir_params(ctx), g, gp,
+    CK(launch_restir_temporal(scene_view(ctx), restir_params(ctx), g,
                               make_float3(prev_cam_pos[0], prev_cam_pos[1], prev_cam_pos[2]), rc, rpv,
                               ro, frame, (cudaStream_t)stream));
     return DDGI_OK;
@@ -547,7 +546,7 @@ ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     uint64_t n = (uint64_t)g.width * g.height;
     if ((s = check_res(ctx, in, n, &ri)) != DDGI_OK) return s;
     if ((s = check_res(ctx, out, n, &ro)) != DDGI_OK) return s;
-    if (n > 0 && (ro.r0 == ri.r0 || ro.r1 == ri.r1 || ro.r2 == ri.r2))
+    if (n > 0 && ro.rec == ri.rec)
         return fail(ctx, DDGI_ERR_INVALID_ARG, "output reservoirs alias the input");
     if (pass > 3) return fail(ctx, DDGI_ERR_INVALID_ARG, "spatial pass index must be 0..3");
     CK(launch_restir_spatial(scene_view(ctx), restir_params(ctx), g, ri, ro, frame, pass,

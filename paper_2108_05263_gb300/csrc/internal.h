@@ -21,10 +21,10 @@ struct GBufView {
     int width, height;
 };
 
+// reservoir records: 4 float4 per pixel (see ddgi_reservoirs)
 struct ResView {
-    float4* r0;
-    float4* r1;
-    uint2* r2;
+    float4* rec;
+    uint32_t n;   // number of records
 };
 
 struct CamView {
@@ -39,6 +39,7 @@ struct RestirParams {
     float temporal_mcap;
     uint32_t spatial_neighbours, spatial_radius;
     float normal_reject_cos, depth_reject_frac;
+    uint32_t span_magic;   // ceil(2^32 / (2 radius + 1)): x / span = mulhi(x, magic) for x < 2^16
 };
 
 struct ProbeParams {
@@ -63,7 +64,7 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, cudaStream_t st);
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
-                                   const GBufView& gp, float3 prev_cam, const ResView& cur,
+                                   float3 prev_cam, const ResView& cur,
                                    const ResView& prev, const ResView& out, uint32_t frame,
                                    cudaStream_t st);
 cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, const GBufView& g,

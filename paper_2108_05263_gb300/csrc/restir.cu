@@ -35,6 +35,49 @@ __device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
     return t * lx + bt * ly + n * lz;
 }
 
+// reservoir record: q0 = (y, W), q1 = (L, M), q2 = (owner normal, owner
+// distance), q3 = (triangle of y, tag, owner valid, 0)
+struct Rec {
+    float4 q0, q1, q2, q3;
+};
+
+// 32-byte (256-bit) accesses: one L1 sector access per record half
+__device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+__device__ __forceinline__ void st32(float4* p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
+                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void store_rec(float4* p, float4 q0, float4 q1, float4 q2, uint32_t tri,
+                                          uint32_t tag, uint32_t valid) {
+    st32(p, q0, q1);
+    st32(p + 2, q2, make_float4(__uint_as_float(tri), __uint_as_float(tag), __uint_as_float(valid), 0.f));
+}
+
+__device__ __forceinline__ void copy_rec(float4* p, const Rec& r) {
+    st32(p, r.q0, r.q1);
+    st32(p + 2, r.q2, r.q3);
+}
+
+__device__ __forceinline__ Rec load_rec(const float4* p) {
+    Rec r;
+    ld32(p, r.q0, r.q1);
+    ld32(p + 2, r.q2, r.q3);
+    return r;
+}
+
+__device__ __forceinline__ uint32_t rec_tri(const Rec& r) { return __float_as_uint(r.q3.x); }
+
+__device__ __forceinline__ float rec_target(const SceneView& s, f3 x, f3 nx, f3 rho, const Rec& r) {
+    return target_fn(s, x, nx, rho, xyz(r.q0), rec_tri(r), xyz(r.q1));
+}
+
 __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
                                                         float4* __restrict__ resid, uint32_t frame) {
@@ -47,14 +90,15 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     const uint32_t NL = s.num_emitters > 0 ? rp.n_light : 0u;
     const uint32_t NB = rp.n_bsdf;
     const uint32_t M = NL + NB;
+    float4* rec = out.rec + 4 * (size_t)pix;
     if (xtri == DDGI_NONE) {
-        out.r0[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.r1[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.r2[pix] = make_uint2(DDGI_NONE, 0u);
+        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                  make_float4(0.f, 0.f, 0.f, 0.f), DDGI_NONE, 0u, 0u);
         resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
+    const float4 geo = make_float4(g1.x, g1.y, g1.z, g0.w);
     const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
     const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
     const float inv_area = 1.f / s.area_total;
@@ -135,83 +179,72 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     }
     resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
     if (sel.tri == DDGI_NONE) {
-        out.r0[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.r1[pix] = make_float4(0.f, 0.f, 0.f, (float)M);
-        out.r2[pix] = make_uint2(DDGI_NONE, 0u);
+        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
+                  DDGI_NONE, 0u, 1u);
         return;
     }
     float W = sel.p > 0.f ? wsum / ((float)M * sel.p) : 0.f;
-    out.r0[pix] = make_float4(sel.y.x, sel.y.y, sel.y.z, W);
-    out.r1[pix] = make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M);
-    out.r2[pix] = make_uint2(sel.tri, sel.tag);
-}
-
-__device__ __forceinline__ float res_target(const SceneView& s, f3 x, f3 nx, f3 rho, float4 r0,
-                                            float4 r1, uint32_t tri) {
-    return target_fn(s, x, nx, rho, xyz(r0), tri, xyz(r1));
+    store_rec(rec, make_float4(sel.y.x, sel.y.y, sel.y.z, W),
+              make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo, sel.tri, sel.tag, 1u);
 }
 
 __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirParams rp, GBufView g,
-                                                         GBufView gp, float3 cam_prev, ResView cur,
-                                                         ResView prev, ResView out, uint32_t frame) {
+                                                         float3 cam_prev, ResView cur, ResView prev,
+                                                         ResView out, uint32_t frame) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
-    float4 c0 = cur.r0[pix], c1 = cur.r1[pix];
-    uint2 c2 = cur.r2[pix];
-    float4 g1 = g.g1[pix];
+    Rec c = load_rec(cur.rec + 4 * (size_t)pix);
+    float4* o = out.rec + 4 * (size_t)pix;
     float4 g2 = g.g2[pix];
     int pq = __float_as_int(g2.w);
-    bool merge = __float_as_uint(g1.w) != DDGI_NONE && pq >= 0 &&
-                 pq < gp.width * gp.height;
-    float4 p0, p1;
-    uint2 p2;
+    // the owner validity of the current record is this pixel's G-buffer validity
+    bool merge = __float_as_uint(c.q3.z) != 0u && pq >= 0 && (uint32_t)pq < prev.n;
+    Rec p;
     float4 g0;
     if (merge) {
-        float4 h1 = gp.g1[pq];
+        p = load_rec(prev.rec + 4 * (size_t)pq);
         g0 = g.g0[pix];
-        merge = __float_as_uint(h1.w) != DDGI_NONE &&
-                dot(xyz(g1), xyz(h1)) > rp.normal_reject_cos;
+        merge = __float_as_uint(p.q3.z) != 0u && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
         if (merge) {
-            f3 dv = xyz(g0) - f3{cam_prev.x, cam_prev.y, cam_prev.z};
-            float de = length(dv);
-            float dp = gp.g0[pq].w;
-            merge = fabsf(de - dp) <= rp.depth_reject_frac * de;
+            float de = length(xyz(g0) - f3{cam_prev.x, cam_prev.y, cam_prev.z});
+            merge = fabsf(de - p.q2.w) <= rp.depth_reject_frac * de;
         }
     }
     if (!merge) {
-        out.r0[pix] = c0;
-        out.r1[pix] = c1;
-        out.r2[pix] = c2;
+        copy_rec(o, c);
         return;
     }
-    p0 = prev.r0[pq];
-    p1 = prev.r1[pq];
-    p2 = prev.r2[pq];
-    const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
-    float Mc = c1.w;
-    float Mp = fminf(p1.w, rp.temporal_mcap * Mc);
-    float pc = res_target(s, x, nx, rho, c0, c1, c2.x);
-    float wsum = pc * c0.w * Mc;
-    float pp = res_target(s, x, nx, rho, p0, p1, p2.x);
-    float wp = pp * p0.w * Mp;
+    const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
+    float Mc = c.q1.w;
+    float Mp = fminf(p.q1.w, rp.temporal_mcap * Mc);
+    float pc = rec_target(s, x, nx, rho, c);
+    float wsum = pc * c.q0.w * Mc;
+    float pp = rec_target(s, x, nx, rho, p);
+    float wp = pp * p.q0.w * Mp;
     wsum += wp;
     uint32_t h = rng_u32_dim(rng_cand(rng_prefix(rp.seed, pix, frame, PASS_TEMPORAL), 0u), 0u);
     float u = u01(h);
+    float4 q0 = c.q0, q1 = c.q1;
+    uint32_t tri = rec_tri(c), tag = __float_as_uint(c.q3.y);
     float psel = pc;
     if (wp > 0.f && u * wsum < wp) {
-        c0 = p0;
-        c1 = p1;
-        c2 = p2;
+        q0 = p.q0;
+        q1 = p.q1;
+        tri = rec_tri(p);
+        tag = __float_as_uint(p.q3.y);
         psel = pp;
     }
     float Mo = Mc + Mp;
-    c0.w = psel > 0.f ? wsum / (Mo * psel) : 0.f;
-    c1.w = Mo;
-    out.r0[pix] = c0;
-    out.r1[pix] = c1;
-    out.r2[pix] = c2;
+    q0.w = psel > 0.f ? wsum / (Mo * psel) : 0.f;
+    q1.w = Mo;
+    store_rec(o, q0, q1, c.q2, tri, tag, 1u);
+}
+
+// x mod span for x < 2^16 via a multiply-high reciprocal (exact in that range)
+__device__ __forceinline__ uint32_t mod_span(uint32_t x, uint32_t span, uint32_t magic) {
+    return x - __umulhi(x, magic) * span;
 }
 
 __global__ void __launch_bounds__(128) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
@@ -221,66 +254,63 @@ __global__ void __launch_bounds__(128) k_restir_spatial(SceneView s, RestirParam
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
-    float4 s0 = in.r0[pix], s1 = in.r1[pix];
-    uint2 s2 = in.r2[pix];
-    float4 g1 = g.g1[pix];
-    if (__float_as_uint(g1.w) == DDGI_NONE) {
-        out.r0[pix] = s0;
-        out.r1[pix] = s1;
-        out.r2[pix] = s2;
+    Rec c = load_rec(in.rec + 4 * (size_t)pix);
+    float4* o = out.rec + 4 * (size_t)pix;
+    if (__float_as_uint(c.q3.z) == 0u) {
+        copy_rec(o, c);
         return;
     }
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
-    const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
-    const float dist = g0.w;
-    float psel = res_target(s, x, nx, rho, s0, s1, s2.x);
-    float wsum = psel * s0.w * s1.w;
-    float M = s1.w;
+    const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
+    const float dist = c.q2.w;
+    float psel = rec_target(s, x, nx, rho, c);
+    float wsum = psel * c.q0.w * c.q1.w;
+    float M = c.q1.w;
+    float4 q0 = c.q0, q1 = c.q1;
+    uint32_t tri = rec_tri(c), tag = __float_as_uint(c.q3.y);
     const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_SPATIAL0 + pass);
     const int R = (int)rp.spatial_radius;
     const uint32_t span = 2u * rp.spatial_radius + 1u;
     for (uint32_t j = 0; j < rp.spatial_neighbours; ++j) {
         const uint32_t cp = rng_cand(prefix, j);
-        int dx = 0, dy = 0;
-        bool ok = false;
+        int nq = -1;
         for (uint32_t a = 0; a < 8u; ++a) {
             uint32_t h = rng_u32_dim(cp, a);
-            int ox = (int)((h & 0xFFFFu) % span) - R;
-            int oy = (int)((h >> 16) % span) - R;
+            int ox = (int)mod_span(h & 0xFFFFu, span, rp.span_magic) - R;
+            int oy = (int)mod_span(h >> 16, span, rp.span_magic) - R;
             if ((ox != 0 || oy != 0) && ox * ox + oy * oy <= R * R) {
-                dx = ox;
-                dy = oy;
-                ok = true;
+                int qx = px + ox, qy = py + oy;
+                if (qx >= 0 && qy >= 0 && qx < g.width && qy < g.height) nq = qy * g.width + qx;
                 break;
             }
         }
-        if (!ok) continue;
-        int qx = px + dx, qy = py + dy;
-        if (qx < 0 || qy < 0 || qx >= g.width || qy >= g.height) continue;
-        uint32_t q = (uint32_t)qy * g.width + qx;
-        float4 h1 = g.g1[q];
-        if (__float_as_uint(h1.w) == DDGI_NONE) continue;
-        if (dot(nx, xyz(h1)) <= rp.normal_reject_cos) continue;
-        if (fabsf(dist - g.g0[q].w) > rp.depth_reject_frac * dist) continue;
-        float4 n0 = in.r0[q], n1 = in.r1[q];
-        uint2 n2 = in.r2[q];
-        float pn = res_target(s, x, nx, rho, n0, n1, n2.x);
+        if (nq < 0) continue;
+        const float4* nr = in.rec + 4 * (size_t)nq;
+        // geometry half of the neighbour record first: rejection needs only it
+        float4 n2, n3;
+        ld32(nr + 2, n2, n3);
+        if (__float_as_uint(n3.z) == 0u) continue;
+        if (dot(nx, xyz(n2)) <= rp.normal_reject_cos) continue;
+        if (fabsf(dist - n2.w) > rp.depth_reject_frac * dist) continue;
+        float4 n0, n1;
+        ld32(nr, n0, n1);
+        uint32_t ntri = __float_as_uint(n3.x);
+        float pn = target_fn(s, x, nx, rho, xyz(n0), ntri, xyz(n1));
         float wn = pn * n0.w * n1.w;
         wsum += wn;
         M += n1.w;
         float u = u01(rng_u32_dim(cp, 8u));
         if (wn > 0.f && u * wsum < wn) {
-            s0 = n0;
-            s1 = n1;
-            s2 = n2;
+            q0 = n0;
+            q1 = n1;
+            tri = ntri;
+            tag = __float_as_uint(n3.y);
             psel = pn;
         }
     }
-    s0.w = psel > 0.f ? wsum / (M * psel) : 0.f;
-    s1.w = M;
-    out.r0[pix] = s0;
-    out.r1[pix] = s1;
-    out.r2[pix] = s2;
+    q0.w = psel > 0.f ? wsum / (M * psel) : 0.f;
+    q1.w = M;
+    store_rec(o, q0, q1, c.q2, tri, tag, 1u);
 }
 
 inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
@@ -297,13 +327,12 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
 }
 
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
-                                   const GBufView& gp, float3 prev_cam, const ResView& cur,
-                                   const ResView& prev, const ResView& out, uint32_t frame,
-                                   cudaStream_t st) {
+                                   float3 prev_cam, const ResView& cur, const ResView& prev,
+                                   const ResView& out, uint32_t frame, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     dim3 b(32, 8);
-    k_restir_temporal<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, gp, prev_cam, cur,
-                                                                      prev, out, frame);
+    k_restir_temporal<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, prev_cam, cur, prev,
+                                                                      out, frame);
     return cudaGetLastError();
 }
 

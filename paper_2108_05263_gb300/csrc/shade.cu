@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
     const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
     f3 out = xyz(__ldg(s.emi + xtri)) + xyz(resid[pix]);
-    float4 r0 = r.r0[pix];
-    uint2 r2 = r.r2[pix];
-    uint32_t ty = r2.x;
+    const float4* rec = r.rec + 4 * (size_t)pix;
+    float4 r0 = __ldg(rec);
+    uint32_t ty = __float_as_uint(__ldg(rec + 3).x);
     if (ty != DDGI_NONE && r0.w > 0.f) {
         f3 y = xyz(r0);
         f3 d = y - x;

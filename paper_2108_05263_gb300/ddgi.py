@@ -55,8 +55,7 @@ class GBuf(C.Structure):
 
 
 class Res(C.Structure):
-    _fields_ = [("r0", C.c_void_p), ("r1", C.c_void_p), ("r2", C.c_void_p),
-                ("num_pixels", C.c_uint32)]
+    _fields_ = [("rec", C.c_void_p), ("num_pixels", C.c_uint32)]
 
 
 class Info(C.Structure):
@@ -108,8 +107,8 @@ def load(path: Optional[str] = None):
     L.ddgi_probe_rays_set.argtypes = [vp, vp, vp]
     L.ddgi_gbuffer.argtypes = [vp, C.POINTER(Camera), C.POINTER(Camera), C.POINTER(GBuf), vp]
     L.restir_initial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, C.c_uint32, vp]
-    L.restir_temporal.argtypes = [vp, C.POINTER(GBuf), C.POINTER(GBuf), C.POINTER(C.c_float),
-                                  C.POINTER(Res), C.POINTER(Res), C.POINTER(Res), C.c_uint32, vp]
+    L.restir_temporal.argtypes = [vp, C.POINTER(GBuf), C.POINTER(C.c_float), C.POINTER(Res),
+                                  C.POINTER(Res), C.POINTER(Res), C.c_uint32, vp]
     L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
                                  C.c_uint32, vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
@@ -156,22 +155,27 @@ class GBuffer:
 
 
 class Reservoirs:
-    """r0, r1: [N, 4] float32; r2: [N, 2] int32 holding uint32 bits."""
+    """One 64-byte record per pixel: a [N, 16] float32 tensor (see
+    ddgi_reservoirs): y.xyz, W | L.rgb, M | owner normal.xyz, owner distance |
+    uint32 bits of (triangle of y, tag, owner valid, 0)."""
 
-    def __init__(self, n: int, device="cuda", planes=None):
+    def __init__(self, n: int, device="cuda", rec: Optional[torch.Tensor] = None):
         self.n = n
-        if planes is None:
-            planes = (torch.empty((n, 4), dtype=torch.float32, device=device),
-                      torch.empty((n, 4), dtype=torch.float32, device=device),
-                      torch.empty((n, 2), dtype=torch.int32, device=device))
-        self.r0, self.r1, self.r2 = planes
+        self.rec = rec if rec is not None else torch.empty((n, 16), dtype=torch.float32, device=device)
 
     def c(self) -> Res:
-        return Res(self.r0.data_ptr(), self.r1.data_ptr(), self.r2.data_ptr(), self.n)
+        return Res(self.rec.data_ptr(), self.n)
 
-    def numpy(self):
-        return (self.r0.cpu().numpy(), self.r1.cpu().numpy(),
-                self.r2.cpu().numpy().view(np.uint32))
+    def numpy(self) -> np.ndarray:
+        return self.rec.cpu().numpy()
+
+    @staticmethod
+    def fields(rec: np.ndarray) -> dict:
+        """Named views of a [N, 16] record array."""
+        bits = np.ascontiguousarray(rec[:, 12:16]).view(np.uint32)
+        return {"y": rec[:, 0:3], "W": rec[:, 3], "L": rec[:, 4:7], "M": rec[:, 7],
+                "n": rec[:, 8:11], "dist": rec[:, 11], "tri": bits[:, 0].view(np.int32),
+                "tag": bits[:, 1], "valid": bits[:, 2]}
 
 
 METRIC_SCRATCH_DOUBLES = 2048
@@ -317,13 +321,13 @@ class Context:
         self._check("restir_initial", self.L.restir_initial(self.h, C.byref(gc), C.byref(oc),
                                                             _ptr(residual), frame, _stream(stream)))
 
-    def restir_temporal(self, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Reservoirs,
-                        prev: Reservoirs, out: Reservoirs, frame, stream=None):
-        gc, gpc, cc, pc, oc = g.c(), gp.c(), cur.c(), prev.c(), out.c()
+    def restir_temporal(self, g: GBuffer, prev_cam_pos, cur: Reservoirs, prev: Reservoirs,
+                        out: Reservoirs, frame, stream=None):
+        gc, cc, pc, oc = g.c(), cur.c(), prev.c(), out.c()
         cp = _f3(*map(float, prev_cam_pos))
         self._check("restir_temporal",
-                    self.L.restir_temporal(self.h, C.byref(gc), C.byref(gpc), cp, C.byref(cc),
-                                           C.byref(pc), C.byref(oc), frame, _stream(stream)))
+                    self.L.restir_temporal(self.h, C.byref(gc), cp, C.byref(cc), C.byref(pc),
+                                           C.byref(oc), frame, _stream(stream)))
 
     def restir_spatial(self, g: GBuffer, src: Reservoirs, out: Reservoirs, frame, pass_idx,
                        stream=None):
@@ -374,14 +378,14 @@ class Frame:
         ctx.restir_initial(g, init, self.resid, frame, stream)
         res = init
         if self.prev_final is not None:
-            ctx.restir_temporal(g, self._prev_g, self.prev_cam.pos, init, self.prev_final, tmp, frame, stream)
+            ctx.restir_temporal(g, self.prev_cam.pos, init, self.prev_final, tmp, frame, stream)
             res = tmp
         for i in range(self.spatial_passes):
             nxt = self._other(res)
             ctx.restir_spatial(g, res, nxt, frame, i, stream)
             res = nxt
         ctx.shade(g, res, self.resid, self.radiance, stream)
-        self.prev_final, self._prev_g, self.prev_cam = res, g, cam
+        self.prev_final, self.prev_cam = res, cam
         self.cur ^= 1
         return self.radiance
 

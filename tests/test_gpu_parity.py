@@ -55,9 +55,34 @@ def _gbuf_to_gpu(dd, g):
     return dd.GBuffer(g.width, g.height, planes=[_t(g0), _t(g1), _t(g2)])
 
 
-def _res_to_gpu(dd, r):
-    r0, r1, r2 = r.planes()
-    return dd.Reservoirs(r0.shape[0], planes=(_t(r0), _t(r1), _t(r2)))
+def _pack(y, W, L, M, tri, tag, nrm, dist, valid):
+    """Reservoir records in the library's layout (the owning pixel's normal,
+    distance and validity come from its G-buffer)."""
+    n = len(W)
+    rec = np.zeros((n, 16), np.float32)
+    rec[:, 0:3], rec[:, 3] = y, W
+    rec[:, 4:7], rec[:, 7] = L, M
+    rec[:, 8:11], rec[:, 11] = nrm, dist
+    bits = np.zeros((n, 4), np.uint32)
+    bits[:, 0] = np.asarray(tri).astype(np.int64).astype(np.uint32)
+    bits[:, 1] = tag
+    bits[:, 2] = valid
+    rec[:, 12:16] = bits.view(np.float32)
+    return rec
+
+
+def _res_to_gpu(dd, r, g):
+    rec = _pack(r.y, r.W, r.L, r.M, r.tri, r.tag, g.nrm, g.dist, (g.tri >= 0).astype(np.uint32))
+    return dd.Reservoirs(rec.shape[0], rec=_t(rec))
+
+
+def _synthetic_res_to_gpu(dd, res, gplanes):
+    r0, r1, r2 = res
+    g0, g1, _ = gplanes
+    valid = (np.ascontiguousarray(g1[:, 3]).view(np.uint32) != 0xFFFFFFFF).astype(np.uint32)
+    rec = _pack(r0[:, :3], r0[:, 3], r1[:, :3], r1[:, 3], r2[:, 0].view(np.int32), r2[:, 1],
+                g1[:, :3], g0[:, 3], valid)
+    return dd.Reservoirs(rec.shape[0], rec=_t(rec))
 
 
 def _vol_to_gpu(ctx, vol):
@@ -79,18 +104,18 @@ def _frac(mask):
     return float(np.mean(mask)) if mask.size else 1.0
 
 
-def _res_compare(gr, orr, w_abs=1e-6, l_abs=1e-5, what=""):
-    """GPU reservoir planes vs oracle Reservoirs; returns tag agreement."""
-    r0, r1, r2 = gr
-    tri = r2[:, 0].view(np.int32)
-    same = (tri == orr.tri) & (r2[:, 1] == orr.tag)
+def _res_compare(rec, orr, w_abs=1e-6, l_abs=1e-5, what=""):
+    """GPU reservoir records vs oracle Reservoirs; returns tag agreement."""
+    from paper_2108_05263_gb300 import ddgi
+    f = ddgi.Reservoirs.fields(rec)
+    same = (f["tri"] == orr.tri) & (f["tag"] == orr.tag)
     agree = _frac(same)
     assert agree >= 0.999, f"{what}: selections agree on {agree:.5f}"
-    np.testing.assert_array_equal(r1[:, 3], orr.M.astype(np.float32))
+    np.testing.assert_array_equal(f["M"], orr.M.astype(np.float32))
     ok = same & (orr.tri >= 0)
-    assert _frac(_close(r0[ok, 3], orr.W[ok], w_abs)) >= 0.999, what
-    assert _frac(_close(r1[ok, :3], orr.L[ok], l_abs).all(axis=1)) >= 0.999, what
-    assert _frac(_close(r0[ok, :3], orr.y[ok], 1e-5).all(axis=1)) >= 0.999, what
+    assert _frac(_close(f["W"][ok], orr.W[ok], w_abs)) >= 0.999, what
+    assert _frac(_close(f["L"][ok], orr.L[ok], l_abs).all(axis=1)) >= 0.999, what
+    assert _frac(_close(f["y"][ok], orr.y[ok], 1e-5).all(axis=1)) >= 0.999, what
     return agree
 
 
@@ -183,6 +208,13 @@ def test_initial_parity(dd, orc, tiny):
     rr = torch.empty((g.tri.shape[0], 4), dtype=torch.float32, device="cuda")
     ctx.restir_initial(gg, out, rr, 7)
     _res_compare(out.numpy(), ref, what="initial")
+    # the record carries its pixel's G-buffer geometry verbatim
+    f = dd.Reservoirs.fields(out.numpy())
+    g0, g1, _ = g.planes()
+    valid = g.tri >= 0
+    np.testing.assert_array_equal(f["valid"], valid.astype(np.uint32))
+    np.testing.assert_array_equal(f["n"][valid], g1[valid, :3])
+    np.testing.assert_array_equal(f["dist"][valid], g0[valid, 3])
     assert _frac(_close(rr.cpu().numpy()[:, :3], resid, 1e-5).all(1)) >= 0.999
     assert ctx.get_status() == dd.OK
 
@@ -194,8 +226,9 @@ def test_temporal_parity(dd, orc, tiny):
     ref = orc.restir_temporal(S, f1["gbuffer"], f0["gbuffer"], sc.cameras[0].pos, f1["initial"], f0["final"], 1)
     ctx = dd.Context.from_scene(sc)
     out = dd.Reservoirs(ref.W.shape[0])
-    ctx.restir_temporal(_gbuf_to_gpu(dd, f1["gbuffer"]), _gbuf_to_gpu(dd, f0["gbuffer"]), sc.cameras[0].pos,
-                        _res_to_gpu(dd, f1["initial"]), _res_to_gpu(dd, f0["final"]), out, 1)
+    ctx.restir_temporal(_gbuf_to_gpu(dd, f1["gbuffer"]), sc.cameras[0].pos,
+                        _res_to_gpu(dd, f1["initial"], f1["gbuffer"]),
+                        _res_to_gpu(dd, f0["final"], f0["gbuffer"]), out, 1)
     _res_compare(out.numpy(), ref, what="temporal")
 
 
@@ -206,7 +239,8 @@ def test_spatial_parity(dd, orc, tiny):
     ref = orc.restir_spatial(S, f1["gbuffer"], f1["temporal"], 1, 0)
     ctx = dd.Context.from_scene(sc)
     out = dd.Reservoirs(ref.W.shape[0])
-    ctx.restir_spatial(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["temporal"]), out, 1, 0)
+    ctx.restir_spatial(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["temporal"], f1["gbuffer"]),
+                       out, 1, 0)
     _res_compare(out.numpy(), ref, what="spatial")
 
 
@@ -222,7 +256,7 @@ def test_shade_parity(dd, orc, tiny):
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     resid = np.zeros((n, 4), np.float32)
     resid[:, :3] = f1["resid"]
-    ctx.shade(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["final"]), _t(resid), rad)
+    ctx.shade(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["final"], f1["gbuffer"]), _t(resid), rad)
     out = rad.cpu().numpy()
     assert _frac(_close(out[:, :3], ref, 1e-5).all(1)) >= 0.999
     assert ctx.get_status() == dd.OK
@@ -242,8 +276,8 @@ def _chain(dd, orc, sc, nframes):
         cam = sc.cameras[f % len(sc.cameras)]
         ref = R.frame(f, cam)
         rad = fr.render(f, cam).cpu().numpy()[:, :3]
-        r2 = fr.prev_final.r2.cpu().numpy().view(np.uint32)
-        tag_ok = (r2[:, 0].view(np.int32) == ref["final"].tri) & (r2[:, 1] == ref["final"].tag)
+        fl = dd.Reservoirs.fields(fr.prev_final.numpy())
+        tag_ok = (fl["tri"] == ref["final"].tri) & (fl["tag"] == ref["final"].tag)
         close = _close(rad, ref["radiance"], 1e-5).all(1)
         stats.append((_frac(tag_ok), _frac(close)))
     assert ctx.get_status() == dd.OK
@@ -335,8 +369,7 @@ def test_apartment_resampling_passes_sampled(dd, orc, apt):
     resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     ctx.restir_initial(gg, out, resid, 5)
     ref, rref = orc.restir_initial(S, vol, og, 5, pix=sample)
-    r0, r1, r2 = out.numpy()
-    _res_compare((r0[sample], r1[sample], r2[sample]), ref, what="initial@1080p")
+    _res_compare(out.numpy()[sample], ref, what="initial@1080p")
     assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-4).all(1)) >= 0.99
     # temporal / spatial on synthetic reservoirs
     rc = scenegen.synthetic_reservoirs(sc, n, 31)
@@ -344,21 +377,19 @@ def test_apartment_resampling_passes_sampled(dd, orc, apt):
     oc, op = orc.Reservoirs.from_planes(*rc), orc.Reservoirs.from_planes(*rp)
     cam_prev = np.array([4.0, 1.5, 6.0])
     tout = dd.Reservoirs(n)
-    ctx.restir_temporal(gg, gq_gpu, cam_prev, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)),
-                        dd.Reservoirs(n, planes=tuple(_t(a) for a in rp)), tout, 5)
+    ctx.restir_temporal(gg, cam_prev, _synthetic_res_to_gpu(dd, rc, gp),
+                        _synthetic_res_to_gpu(dd, rp, gq), tout, 5)
     tref = orc.restir_temporal(S, og, oq, cam_prev, oc, op, 5, pix=sample)
-    t0, t1, t2 = tout.numpy()
-    _res_compare((t0[sample], t1[sample], t2[sample]), tref, what="temporal@1080p")
+    _res_compare(tout.numpy()[sample], tref, what="temporal@1080p")
     sout = dd.Reservoirs(n)
-    ctx.restir_spatial(gg, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)), sout, 5, 1)
+    ctx.restir_spatial(gg, _synthetic_res_to_gpu(dd, rc, gp), sout, 5, 1)
     sref = orc.restir_spatial(S, og, oc, 5, 1, pix=sample)
-    s0, s1, s2 = sout.numpy()
-    _res_compare((s0[sample], s1[sample], s2[sample]), sref, what="spatial@1080p")
+    _res_compare(sout.numpy()[sample], sref, what="spatial@1080p")
     # shade
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     rs = np.zeros((n, 4), np.float32)
     rs[:, :3] = np.random.default_rng(3).uniform(0, 0.1, (n, 3))
-    ctx.shade(gg, dd.Reservoirs(n, planes=tuple(_t(a) for a in rc)), _t(rs), rad)
+    ctx.shade(gg, _synthetic_res_to_gpu(dd, rc, gp), _t(rs), rad)
     shref = orc.shade(S, vol, og, oc, rs[:, :3].astype(np.float64), pix=sample)
     assert _frac(_close(rad.cpu().numpy()[sample, :3], shref, 1e-4).all(1)) >= 0.99
     assert ctx.get_status() == dd.OK
@@ -396,8 +427,8 @@ def test_invalid_pixels_give_empty_reservoirs_and_black(dd):
     ctx.restir_initial(g, r, resid, 0)
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     ctx.shade(g, r, resid, rad)
-    r0, r1, r2 = r.numpy()
-    assert np.all(r2[:, 0] == 0xFFFFFFFF) and np.all(r1[:, 3] == 0)
+    f = dd.Reservoirs.fields(r.numpy())
+    assert np.all(f["tri"] == -1) and np.all(f["M"] == 0) and np.all(f["valid"] == 0)
     assert np.all(rad.cpu().numpy()[:, :3] == 0)
 
 
@@ -437,7 +468,7 @@ def test_scene_without_emitters(dd, orc):
     rr = torch.empty((1024, 4), dtype=torch.float32, device="cuda")
     ctx.restir_initial(_gbuf_to_gpu(dd, og), out, rr, 2)
     _res_compare(out.numpy(), ref, what="no-emitter initial")
-    assert np.all(out.numpy()[1][:, 3] == 1.0)
+    assert np.all(dd.Reservoirs.fields(out.numpy())["M"][og.tri >= 0] == 1.0)
 
 
 # ---------------------------------------------------------------------------
