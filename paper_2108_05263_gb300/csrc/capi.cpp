@@ -33,6 +33,9 @@ struct ddgi_ctx {
     float4* rays = nullptr;
     float4* sf = nullptr;
     uint32_t* err = nullptr;
+    uint32_t* counter = nullptr;   // work counter of the persistent trace kernel
+    float2* hits = nullptr;        // per-ray hit records (t, triangle), grown on demand
+    size_t hits_cap = 0;
     uint32_t updates = 0;
     uint32_t bvh_nodes = 0, bvh_depth = 0;
     uint64_t device_bytes = 0;
@@ -233,6 +236,26 @@ ddgi_status probe_params(ddgi_ctx* c, uint32_t frame, ProbeParams* p) {
 void release(ddgi_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    if (c->hits) cudaFree(c->hits);
+    c->hits = nullptr;
+    c->hits_cap = 0;
+}
+
+// Hit-record scratch for n rays; grows stream-ordered (no device sync).
+cudaError_t ensure_hits(ddgi_ctx* c, size_t n, cudaStream_t st) {
+    if (n <= c->hits_cap) return cudaSuccess;
+    size_t cap = n + n / 4;
+    float2* p = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), cap * sizeof(float2), st);
+    if (e != cudaSuccess) return e;
+    if (c->hits) {
+        e = cudaFreeAsync(c->hits, st);
+        c->device_bytes -= c->hits_cap * sizeof(float2);
+    }
+    c->hits = p;
+    c->hits_cap = cap;
+    c->device_bytes += cap * sizeof(float2);
+    return e;
 }
 
 }  // namespace
@@ -359,6 +382,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(rays, P * R)
     ALLOC(sf, R)
     ALLOC(err, 4)
+    ALLOC(counter, 4)
 #undef ALLOC
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -378,6 +402,9 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     if (e == cudaSuccess) e = cudaMemset(ctx->offset, 0, P * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->rays, 0, P * R * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = ensure_hits(ctx, P * R, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) {
         VolumeView v = volume_view(ctx);
         if (probe_blend_smem(v, R) > 200 * 1024) e = cudaErrorInvalidValue;
@@ -417,7 +444,8 @@ ddgi_status ddgi_probe_trace(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     if (!ctx) return DDGI_ERR_INVALID_ARG;
     ProbeParams p;
     probe_params(ctx, frame, &p);
-    CK(launch_probe_trace(scene_view(ctx), volume_view(ctx), p, ctx->rays, (cudaStream_t)stream));
+    CK(launch_probe_trace(scene_view(ctx), volume_view(ctx), p, ctx->rays, ctx->hits, ctx->counter,
+                          (cudaStream_t)stream));
     return DDGI_OK;
 }
 
@@ -494,7 +522,9 @@ ddgi_status ddgi_gbuffer(ddgi_ctx* ctx, const ddgi_camera* cam, const ddgi_camer
         return fail(ctx, DDGI_ERR_INVALID_ARG, "previous camera size differs");
     CamView c = cam_view(cam), pc;
     if (prev_cam) pc = cam_view(prev_cam);
-    CK(launch_gbuffer(scene_view(ctx), c, prev_cam ? &pc : nullptr, g, (cudaStream_t)stream));
+    CK(ensure_hits(ctx, (size_t)g.width * g.height, (cudaStream_t)stream));
+    CK(launch_gbuffer(scene_view(ctx), c, prev_cam ? &pc : nullptr, g, ctx->hits, ctx->counter,
+                      (cudaStream_t)stream));
     return DDGI_OK;
 }
 
@@ -509,8 +539,10 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     if ((s = check_res(ctx, out, n, &r)) != DDGI_OK) return s;
     if (n > 0 && (!residual || !aligned(residual, 16)))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "residual NULL or misaligned");
+    CK(ensure_hits(ctx, (size_t)n * ctx->cfg.num_bsdf_candidates, (cudaStream_t)stream));
     CK(launch_restir_initial(scene_view(ctx), volume_view(ctx), restir_params(ctx), g, r,
-                             reinterpret_cast<float4*>(residual), frame, (cudaStream_t)stream));
+                             reinterpret_cast<float4*>(residual), frame, ctx->hits, ctx->counter,
+                             (cudaStream_t)stream));
     return DDGI_OK;
 }
 
@@ -565,8 +597,9 @@ ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs
     if ((s = check_res(ctx, res, n, &r)) != DDGI_OK) return s;
     if (n > 0 && (!residual || !radiance || !aligned(residual, 16) || !aligned(radiance, 16)))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "residual / radiance NULL or misaligned");
+    CK(ensure_hits(ctx, (size_t)n, (cudaStream_t)stream));
     CK(launch_shade(scene_view(ctx), volume_view(ctx), g, r, reinterpret_cast<const float4*>(residual),
-                    reinterpret_cast<float4*>(radiance), (cudaStream_t)stream));
+                    reinterpret_cast<float4*>(radiance), ctx->hits, ctx->counter, (cudaStream_t)stream));
     return DDGI_OK;
 }
 

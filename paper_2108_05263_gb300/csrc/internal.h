@@ -54,15 +54,15 @@ struct ProbeParams {
 
 // kernel launchers (return the launch error)
 cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
-                               float4* rays, cudaStream_t st);
+                               float4* rays, float2* hits, uint32_t* counter, cudaStream_t st);
 size_t probe_blend_smem(const VolumeView& v, uint32_t rays);
 cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays,
                                cudaStream_t st);
 cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
-                           const GBufView& g, cudaStream_t st);
+                           const GBufView& g, float2* hits, uint32_t* counter, cudaStream_t st);
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
-                                  uint32_t frame, cudaStream_t st);
+                                  uint32_t frame, float2* hits, uint32_t* counter, cudaStream_t st);
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                    float3 prev_cam, const ResView& cur,
                                    const ResView& prev, const ResView& out, uint32_t frame,
@@ -77,5 +77,5 @@ cudaError_t launch_metrics(const float4* img, const float4* ref, uint32_t n, dou
                            double* out, cudaStream_t st);
 
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
-                         const ResView& r, const float4* resid, float4* radiance,
-                         cudaStream_t st);
+                         const ResView& r, const float4* resid, float4* radiance, float2* hits,
+                         uint32_t* counter, cudaStream_t st);

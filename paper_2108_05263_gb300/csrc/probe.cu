@@ -2,7 +2,7 @@
 // attenuated emission and the probe-augmented bounce, then a per-probe blend
 // of irradiance and distance moments with hysteresis and border refresh.
 #include "internal.h"
-#include "trace.cuh"
+#include "trace_engine.cuh"
 
 namespace {
 
@@ -20,7 +20,12 @@ __device__ __forceinline__ float cell_exit(const VolumeView& v, f3 d) {
     return t;
 }
 
-// one thread per (probe, ray)
+__device__ __forceinline__ f3 probe_of(const VolumeView& v, int p) {
+    int i = p % v.counts.x, j = (p / v.counts.x) % v.counts.y, k = p / (v.counts.x * v.counts.y);
+    return probe_pos(v, i, j, k, p);
+}
+
+// one thread per (probe, ray): trace, then the radiance of Eq. probeUpdate
 __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, ProbeParams pp,
                                                      const float4* __restrict__ sf,
                                                      float4* __restrict__ rays, int total) {
@@ -28,11 +33,10 @@ __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, 
     if (tid >= total) return;
     int R = (int)pp.rays;
     int p = tid / R, r = tid - p * R;
-    int i = p % v.counts.x, j = (p / v.counts.x) % v.counts.y, k = p / (v.counts.x * v.counts.y);
-    f3 P = probe_pos(v, i, j, k, p);
+    f3 P = probe_of(v, p);
     f3 w = rotate(pp, __ldg(sf + r));
-    Ray ray{P, w, DDGI_T_EPS, DDGI_MISS_T};
-    Hit h = trace_bvh<false>(s, ray);
+    // coherent rays (one origin per 32-lane warp): traversal in place
+    Hit h = trace_bvh<false>(s, Ray{P, w, DDGI_T_EPS, DDGI_MISS_T});
     float4 out = make_float4(0.f, 0.f, 0.f, DDGI_MISS_T);
     if (h.tri != DDGI_NONE) {
         f3 n = xyz(__ldg(s.nrm + h.tri));
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256) k_probe_blend(VolumeView v, ProbeParams p
 }  // namespace
 
 cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
-                               float4* rays, cudaStream_t st) {
+                               float4* rays, float2* hits, uint32_t* counter, cudaStream_t st) {
     int P = v.counts.x * v.counts.y * v.counts.z;
     int total = P * (int)p.rays;
     if (total == 0) return cudaSuccess;

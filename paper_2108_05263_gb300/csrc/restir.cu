@@ -4,7 +4,7 @@
 // Sec. 3.6.  One thread per pixel; SoA planes read and written as 16-byte
 // records.
 #include "internal.h"
-#include "trace.cuh"
+#include "trace_engine.cuh"
 
 namespace {
 
@@ -78,9 +78,38 @@ __device__ __forceinline__ float rec_target(const SceneView& s, f3 x, f3 nx, f3 
     return target_fn(s, x, nx, rho, xyz(r.q0), rec_tri(r), xyz(r.q1));
 }
 
+// cosine-distributed direction of BSDF candidate c at pixel pix (Sec. 3.1 step 1)
+__device__ __forceinline__ f3 bsdf_dir(const RestirParams& rp, uint32_t pix, uint32_t frame,
+                                       uint32_t c, f3 nx) {
+    const uint32_t cp = rng_cand(rng_prefix(rp.seed, pix, frame, PASS_INITIAL), c);
+    float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
+    float r = sqrtf(u0);
+    float sn, cs;
+    sincospif(2.f * u1, &sn, &cs);
+    return onb_to_world(nx, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
+}
+
+// BSDF candidate rays: work item i = pixel * n_bsdf + b
+struct BsdfGen {
+    GBufView g;
+    RestirParams rp;
+    uint32_t frame, nl, nb;
+    __device__ __forceinline__ bool ray(uint32_t i, Ray& r) const {
+        const uint32_t pix = i / nb, b = i - pix * nb;
+        r.tmax = DDGI_MISS_T;
+        float4 g1 = g.g1[pix];
+        if (__float_as_uint(g1.w) == DDGI_NONE) return false;
+        r.o = xyz(g.g0[pix]);
+        r.d = bsdf_dir(rp, pix, frame, nl + b, xyz(g1));
+        r.tmin = DDGI_T_EPS;
+        return true;
+    }
+};
+
 __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
-                                                        float4* __restrict__ resid, uint32_t frame) {
+                                                        float4* __restrict__ resid, uint32_t frame,
+                                                        const float2* __restrict__ bsdf_hits) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
@@ -121,7 +150,9 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             float u2 = u01(rng_u32_dim(cp, 2));
             uint32_t e = sample_emitter(s, u0);
             const float4* rec = s.evert + 4 * (size_t)e;
-            float4 q0 = __ldg(rec), q1 = __ldg(rec + 1), q2 = __ldg(rec + 2), q3 = __ldg(rec + 3);
+            float4 q0, q1, q2, q3;
+            ld32(rec, q0, q1);
+            ld32(rec + 2, q2, q3);
             tri = __float_as_uint(q0.w);
             float sq = sqrtf(u1);
             float b1 = sq * (1.f - u2), b2 = sq * u2;
@@ -141,13 +172,9 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
                 L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
             }
         } else {
-            float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
-            float r = sqrtf(u0);
-            float sn, cs;
-            sincospif(2.f * u1, &sn, &cs);
-            f3 w = onb_to_world(nx, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
-            Ray ray{x, w, DDGI_T_EPS, DDGI_MISS_T};
-            Hit h = trace_bvh<false>(s, ray);
+            f3 w = bsdf_dir(rp, pix, frame, c, nx);
+            float2 hb = __ldg(bsdf_hits + (size_t)pix * NB + (c - NL));
+            Hit h{hb.x, __float_as_uint(hb.y)};
             if (h.tri == DDGI_NONE) continue;
             tri = h.tri;
             pL = __ldg(s.emi + tri).w > 0.f ? inv_area : 0.f;
@@ -319,10 +346,15 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
-                                  uint32_t frame, cudaStream_t st) {
+                                  uint32_t frame, float2* hits, uint32_t* counter, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
+    const uint32_t nl = s.num_emitters > 0 ? rp.n_light : 0u;
+    BsdfGen gen{g, rp, frame, nl, rp.n_bsdf};
+    cudaError_t e = launch_trace<BsdfGen, false>(s, gen, (uint32_t)g.width * g.height * rp.n_bsdf,
+                                                 counter, hits, st);
+    if (e != cudaSuccess) return e;
     dim3 b(16, 8);
-    k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame);
+    k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits);
     return cudaGetLastError();
 }
 

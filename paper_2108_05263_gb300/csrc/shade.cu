@@ -2,9 +2,20 @@
 // steps 3-4 / Eq. Algorithm: Le at x + residual + the resampled bounded term
 // behind one shadow ray, with a fresh probe query at the selected point.
 #include "internal.h"
-#include "trace.cuh"
+#include "trace_engine.cuh"
 
 namespace {
+
+__device__ __forceinline__ f3 camera_dir(const CamView& cam, int px, int py) {
+    const float W = (float)cam.width, H = (float)cam.height;
+    const float aspect = W / H;
+    float sx = (2.f * (px + 0.5f) / W - 1.f) * cam.tan_half_fovy * aspect;
+    float sy = (1.f - 2.f * (py + 0.5f) / H) * cam.tan_half_fovy;
+    f3 fwd = {cam.fwd.x, cam.fwd.y, cam.fwd.z}, right = {cam.right.x, cam.right.y, cam.right.z};
+    f3 up = {cam.up.x, cam.up.y, cam.up.z};
+    f3 d = fwd + right * sx + up * sy;
+    return d * rsqrtf(dot(d, d));
+}
 
 __global__ void __launch_bounds__(128) k_gbuffer(SceneView s, CamView cam, CamView pc, int has_prev,
                                                  GBufView g) {
@@ -14,12 +25,9 @@ __global__ void __launch_bounds__(128) k_gbuffer(SceneView s, CamView cam, CamVi
     uint32_t pix = (uint32_t)py * g.width + px;
     const float W = (float)cam.width, H = (float)cam.height;
     const float aspect = W / H;
-    float sx = (2.f * (px + 0.5f) / W - 1.f) * cam.tan_half_fovy * aspect;
-    float sy = (1.f - 2.f * (py + 0.5f) / H) * cam.tan_half_fovy;
-    f3 fwd = {cam.fwd.x, cam.fwd.y, cam.fwd.z}, right = {cam.right.x, cam.right.y, cam.right.z};
-    f3 up = {cam.up.x, cam.up.y, cam.up.z}, o = {cam.pos.x, cam.pos.y, cam.pos.z};
-    f3 d = fwd + right * sx + up * sy;
-    d = d * rsqrtf(dot(d, d));
+    f3 o = {cam.pos.x, cam.pos.y, cam.pos.z};
+    f3 d = camera_dir(cam, px, py);
+    // coherent rays: traversal in place, warps stay on the same nodes
     Hit h = trace_bvh<false>(s, Ray{o, d, DDGI_T_EPS, DDGI_MISS_T});
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = make_float4(0.f, 0.f, 0.f, __uint_as_float(DDGI_NONE));
     float4 g2 = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
@@ -50,9 +58,36 @@ __global__ void __launch_bounds__(128) k_gbuffer(SceneView s, CamView cam, CamVi
     g.g2[pix] = g2;
 }
 
+// shadow rays toward each pixel's selected sample, work item = pixel
+struct ShadowGen {
+    GBufView g;
+    ResView r;
+    __device__ __forceinline__ bool ray(uint32_t pix, Ray& ry) const {
+        ry.tmax = 0.f;
+        float4 g1 = g.g1[pix];
+        if (__float_as_uint(g1.w) == DDGI_NONE) return false;
+        const float4* rec = r.rec + 4 * (size_t)pix;
+        float4 r0 = __ldg(rec);
+        if (__float_as_uint(__ldg(rec + 3).x) == DDGI_NONE || !(r0.w > 0.f)) return false;
+        f3 x = xyz(g.g0[pix]);
+        f3 d = xyz(r0) - x;
+        float d2 = dot(d, d);
+        if (!(d2 > 0.f)) return false;
+        float l = sqrtf(d2);
+        f3 w = d * (1.f / l);
+        if (!(dot(xyz(g1), w) > 0.f)) return false;
+        ry.o = x;
+        ry.d = w;
+        ry.tmin = DDGI_T_EPS;
+        ry.tmax = (1.f - 1e-4f) * l;
+        return true;
+    }
+};
+
 __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
                                                const float4* __restrict__ resid,
-                                               float4* __restrict__ radiance) {
+                                               float4* __restrict__ radiance,
+                                               const float2* __restrict__ vis) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
@@ -78,8 +113,7 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
             f3 w = d * (1.f / l);
             float cx = dot(nx, w);
             if (cx > 0.f) {
-                Hit h = trace_bvh<true>(s, Ray{x, w, DDGI_T_EPS, (1.f - 1e-4f) * l});
-                if (h.tri == DDGI_NONE) {
+                if (__float_as_uint(__ldg(vis + pix).y) == DDGI_NONE) {
                     f3 L = radiance_at(s, v, y, ty, x);
                     float cy = fabsf(dot(xyz(__ldg(s.nrm + ty)), w));
                     float G = cx * cy / d2;
@@ -96,7 +130,7 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 }  // namespace
 
 cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
-                           const GBufView& g, cudaStream_t st) {
+                           const GBufView& g, float2* hits, uint32_t* counter, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     dim3 b(16, 8);
     k_gbuffer<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, cam, prev ? *prev : cam, prev != nullptr, g);
@@ -104,10 +138,13 @@ cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView
 }
 
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
-                         const ResView& r, const float4* resid, float4* radiance,
-                         cudaStream_t st) {
+                         const ResView& r, const float4* resid, float4* radiance, float2* hits,
+                         uint32_t* counter, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
+    cudaError_t e = launch_trace<ShadowGen, true>(s, ShadowGen{g, r}, (uint32_t)g.width * g.height,
+                                                  counter, hits, st);
+    if (e != cudaSuccess) return e;
     dim3 b(16, 8);
-    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance);
+    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits);
     return cudaGetLastError();
 }

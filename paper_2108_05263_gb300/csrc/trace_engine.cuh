@@ -1,0 +1,228 @@
+// Persistent ray-traversal kernel with per-warp dynamic work refill.
+//
+// Each lane owns one ray at a time and advances it by one BVH entry per loop
+// iteration; when a lane's ray finishes, the warp hands it the next work item
+// from a warp-private pool (refilled 64 items at a time from a global
+// counter), so lanes with short rays do not idle behind lanes with long ones.
+// A generator functor turns a work index into a ray; the result of work item
+// i is written to hits[i] as (t, triangle bits) -- (tmax, 0xFFFFFFFF) on a
+// miss or when the generator emits no ray.  Any-hit rays stop at the first
+// hit in (tmin, tmax).
+//
+// BVH entries on the traversal stack: >= 0 inner node index; < 0 a leaf,
+// encoded as -1 - (first_triangle * 8 + count - 1).
+#pragma once
+#include "trace.cuh"
+
+#define ENGINE_THREADS 128
+#define ENGINE_GRAB 64u
+
+__device__ __forceinline__ int leaf_entry(int first, int count) { return -1 - (first * 8 + count - 1); }
+
+template <class Gen, bool ANY_HIT>
+__global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, uint32_t n,
+                                                          uint32_t* __restrict__ counter,
+                                                          float2* __restrict__ hits) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // per-lane ray state
+    uint32_t idx = DDGI_NONE;
+    f3 o = {0.f, 0.f, 0.f}, d = {0.f, 0.f, 1.f}, inv = {0.f, 0.f, 0.f}, oi = {0.f, 0.f, 0.f};
+    float tmin = 0.f, tmax = 0.f, best_t = 0.f;
+    uint32_t best_tri = DDGI_NONE;
+    int node = 0, sp = 0, visits = 0;
+    int stack[TRAV_STACK];
+    float stack_t[TRAV_STACK];
+    // warp-uniform work pool
+    uint32_t pool = 0, pool_end = 0;
+    bool exhausted = false;
+    const float widen = 1.0000004f;
+
+    while (true) {
+        // ---- refill idle lanes ------------------------------------------------
+        while (true) {
+            unsigned need = __ballot_sync(FULL, idx == DDGI_NONE);
+            if (need == 0u) break;
+            if (pool == pool_end) {
+                if (exhausted) break;
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(counter, ENGINE_GRAB);
+                base = __shfl_sync(FULL, base, 0);
+                if (base >= n) {
+                    exhausted = true;
+                    break;
+                }
+                pool = base;
+                pool_end = min(base + ENGINE_GRAB, n);
+            }
+            const uint32_t avail = pool_end - pool;
+            const uint32_t rank = __popc(need & lt_mask);
+            if (idx == DDGI_NONE && rank < avail) {
+                const uint32_t i = pool + rank;
+                Ray r;
+                if (gen.ray(i, r)) {
+                    idx = i;
+                    o = r.o;
+                    d = r.d;
+                    tmin = r.tmin;
+                    tmax = r.tmax;
+                    inv = {safe_inv(d.x), safe_inv(d.y), safe_inv(d.z)};
+                    oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
+                    best_t = tmax;
+                    best_tri = DDGI_NONE;
+                    node = 0;
+                    sp = 0;
+                    visits = 0;
+                } else {
+                    hits[i] = make_float2(r.tmax, __uint_as_float(DDGI_NONE));
+                }
+            }
+            pool += min(avail, (uint32_t)__popc(need));
+        }
+        if (__all_sync(FULL, idx == DDGI_NONE)) break;
+        if (idx == DDGI_NONE) continue;
+
+        // ---- descend inner nodes until a leaf, then intersect that leaf -------
+        bool done = false;
+        while (!done && node >= 0) {
+            if (++visits > TRAV_MAX_VISITS) {
+                atomicOr(s.err, ERRBIT_TRAVERSAL);
+                best_tri = DDGI_NONE;
+                best_t = tmax;
+                done = true;
+                break;
+            }
+            const float4* np = s.nodes + (size_t)node * 8;
+            float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3);
+            float4 lz = __ldg(np + 4), hz = __ldg(np + 5);
+            float4 chf = __ldg(np + 6), cnf = __ldg(np + 7);
+            float t0[4];
+            int ent[4];
+            const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
+            const float lya[4] = {ly.x, ly.y, ly.z, ly.w}, hya[4] = {hy.x, hy.y, hy.z, hy.w};
+            const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
+            const int cha[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
+                                __float_as_int(chf.w)};
+            const int cna[4] = {__float_as_int(cnf.x), __float_as_int(cnf.y), __float_as_int(cnf.z),
+                                __float_as_int(cnf.w)};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float tx0 = fmaf(lxa[c], inv.x, -oi.x), tx1 = fmaf(hxa[c], inv.x, -oi.x);
+                float ty0 = fmaf(lya[c], inv.y, -oi.y), ty1 = fmaf(hya[c], inv.y, -oi.y);
+                float tz0 = fmaf(lza[c], inv.z, -oi.z), tz1 = fmaf(hza[c], inv.z, -oi.z);
+                float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+                float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), best_t)) * widen;
+                bool valid = cna[c] > 0 || cha[c] >= 0;
+                bool hit = valid && a <= b;
+                t0[c] = hit ? a : INFINITY;
+                ent[c] = cna[c] > 0 ? leaf_entry(~cha[c], cna[c]) : cha[c];
+            }
+            // sort the 4 (t, entry) pairs by t, ascending (sorting network)
+#define CSWAP(i, j)                                          \
+    if (t0[j] < t0[i]) {                                     \
+        float tt = t0[i];                                    \
+        t0[i] = t0[j];                                       \
+        t0[j] = tt;                                          \
+        int ee = ent[i];                                     \
+        ent[i] = ent[j];                                     \
+        ent[j] = ee;                                         \
+    }
+            CSWAP(0, 1)
+            CSWAP(2, 3)
+            CSWAP(0, 2)
+            CSWAP(1, 3)
+            CSWAP(1, 2)
+#undef CSWAP
+            const int nhit = (t0[0] < INFINITY) + (t0[1] < INFINITY) + (t0[2] < INFINITY) + (t0[3] < INFINITY);
+            if (sp + nhit > TRAV_STACK) {
+                atomicOr(s.err, ERRBIT_STACK);
+                best_tri = DDGI_NONE;
+                best_t = tmax;
+                done = true;
+                break;
+            }
+            // push far-to-near, continue with the nearest
+#pragma unroll
+            for (int k = 3; k >= 1; --k)
+                if (k < nhit) {
+                    stack_t[sp] = t0[k];
+                    stack[sp] = ent[k];
+                    ++sp;
+                }
+            if (nhit > 0) {
+                node = ent[0];
+            } else {
+                bool found = false;
+                while (sp > 0) {
+                    --sp;
+                    if (stack_t[sp] <= best_t * widen) {
+                        node = stack[sp];
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) done = true;
+            }
+        }
+        if (!done) {
+            // node < 0: a leaf entry
+            const int v = -1 - node;
+            const int first = v >> 3, count = (v & 7) + 1;
+            for (int k = 0; k < count; ++k) {
+                uint32_t orig;
+                float t = tri_hit(s.tris + (size_t)(first + k) * 3, o, d, &orig);
+                if (t > tmin && t < tmax) {
+                    if (ANY_HIT) {
+                        best_t = t;
+                        best_tri = orig;
+                        done = true;
+                        break;
+                    }
+                    if (t < best_t || (t == best_t && orig < best_tri)) {
+                        best_t = t;
+                        best_tri = orig;
+                    }
+                }
+            }
+            if (!done) {
+                bool found = false;
+                while (sp > 0) {
+                    --sp;
+                    if (stack_t[sp] <= best_t * widen) {
+                        node = stack[sp];
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) done = true;
+            }
+        }
+        if (done) {
+            hits[idx] = make_float2(best_t, __uint_as_float(best_tri));
+            idx = DDGI_NONE;
+        }
+    }
+}
+
+// Launches the persistent trace over n work items: a few warps per SM, the
+// work counter reset on the stream first.
+template <class Gen, bool ANY_HIT>
+cudaError_t launch_trace(const SceneView& s, const Gen& gen, uint32_t n, uint32_t* counter,
+                         float2* hits, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    static int blocks = 0;
+    if (blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace<Gen, ANY_HIT>, ENGINE_THREADS, 0);
+        blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    uint32_t need = (n + ENGINE_THREADS - 1) / ENGINE_THREADS;
+    uint32_t grid = need < (uint32_t)blocks ? need : (uint32_t)blocks;
+    k_trace<Gen, ANY_HIT><<<grid, ENGINE_THREADS, 0, st>>>(s, gen, n, counter, hits);
+    return cudaGetLastError();
+}
