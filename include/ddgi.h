@@ -13,8 +13,8 @@
  *    the caller; "host" pointers are ordinary host memory.  The library never
  *    frees caller memory.
  *  - Per-pixel planes are arrays of 4-float (16-byte) records, one per pixel
- *    in row-major order (pixel = y * width + x), 16-byte aligned; the
- *    reservoir index plane r2 holds 2 uint32 per pixel, 8-byte aligned.
+ *    in row-major order (pixel = y * width + x), 16-byte aligned; reservoirs
+ *    are 64-byte records, 64-byte aligned.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls enqueue work and return without synchronising, except
  *    ddgi_get_status and the *_get functions, which synchronise `stream`.
@@ -25,7 +25,8 @@
  *    (traversal iteration cap, traversal stack overflow) set an error word
  *    that ddgi_get_status reports; a kernel that hits one returns "no hit"
  *    for that ray and the frame continues.
- *  - A context is not thread-safe; use one per host thread or serialise.
+ *  - A context is not thread-safe, and calls on one context share its scratch
+ *    buffers: issue them on one stream (or order the streams).
  */
 #ifndef DDGI_H
 #define DDGI_H
@@ -78,6 +79,15 @@ typedef struct {
     float normal_reject_cos;      /* reuse only if dot(n, n') > this */
     float depth_reject_frac;      /* ... and |d - d'| <= this * d */
     uint32_t seed;
+    /* learned target form: a network stands in for the probe lookup (the
+     * paper names neural radiance caches as interchangeable with the probes,
+     * Sec. 2 and Sec. 5) */
+    uint32_t learned_target;      /* 1: resampling and shading query the network while
+                                   * its held-out error is not above the probes' */
+    uint32_t train_samples;       /* self-training samples per ddgi_mlp_train call; a
+                                   * multiple of 16 and of the probe count (0 = none) */
+    float train_lr;               /* Adam learning rate */
+    uint32_t mlp_seed;            /* seed of the weight initialisation */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */
@@ -220,6 +230,54 @@ ddgi_status ddgi_image_metrics(const float* img, const float* ref, uint32_t n, d
  *    earlier call left behind does not matter. */
 ddgi_status ddgi_image_metrics_static(const float* img, const float* ref, uint32_t n,
                                       double* out, void* stream);
+
+/* ---- learned target form ------------------------------------------------
+ * Network: input = sin / cos(2^k pi p'_a) for k = 0..11 and the 3 axes of the
+ * position normalised to the scene box (p' = (p - box_lo) / max box extent),
+ * the normal, 5 zeros (80 values); 4 hidden layers of 64 ReLU units; linear
+ * 3-channel output f ~ E / pi, so the reflected indirect radiance at y is
+ * rho(y) max(f, 0).  Weights and activations fp16, tensor-core accumulation
+ * fp32, fp32 master weights, Adam (beta 0.9 / 0.99, eps 1e-8), relative-L2
+ * loss with dynamic loss scaling.  Parameters: MLP_NPARAM = 18184 floats:
+ * W1 [64][80] at 0, W2..W4 [64][64] at 5120 / 9216 / 13312, W5 [8][64] at
+ * 17408 (rows 3..7 zero), b1..b4 [64] at 17920 + 64 l, b5 [8] at 18176. */
+#define DDGI_MLP_NPARAM 18184
+
+/* One self-training step: train_samples rays from the probe centres
+ * (spherical Fibonacci set per probe, per-frame random rotation) hit y; a
+ * cosine-distributed bounce from y hits z; target = Le(z) + rho(z) max(f(z),
+ * 0).  Samples 16 j + 15 are held out and judge the updated network against
+ * the probe lookup (relative squared error); the verdict decides for the
+ * following resampling / shading calls whether the network or the probes
+ * serve the queries.  Requires train_samples > 0. */
+ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream);
+
+/* Evaluate the network: queries (device [n][8] floats: p.xyz, valid, n.xyz,
+ * 0), out (device [n][4]: f.rgb, valid). */
+ddgi_status ddgi_mlp_infer(ddgi_ctx* ctx, const float* queries, float* out, uint32_t n, void* stream);
+
+/* Gradient of the mean relative-L2 loss over caller samples (host or device
+ * [n][12] floats: y.xyz, _, n.xyz, _, target.rgb, weight; weight 0 excludes
+ * a sample) at the current weights, without updating them; grad: host or
+ * device [DDGI_MLP_NPARAM].  Synchronises the stream. */
+ddgi_status ddgi_mlp_grad(ddgi_ctx* ctx, const float* samples, uint32_t n, float* grad, void* stream);
+
+/* One Adam step on caller samples (same layout as ddgi_mlp_grad). */
+ddgi_status ddgi_mlp_step(ddgi_ctx* ctx, const float* samples, uint32_t n, void* stream);
+
+/* fp32 master parameters (host or device [DDGI_MLP_NPARAM]); set also resets
+ * the Adam moments and step count.  Both synchronise the stream. */
+ddgi_status ddgi_mlp_params_get(ddgi_ctx* ctx, float* params, void* stream);
+ddgi_status ddgi_mlp_params_set(ddgi_ctx* ctx, const float* params, void* stream);
+
+/* The last ddgi_mlp_train call's samples (host or device [train_samples][12]
+ * floats: y.xyz, valid, n.xyz, 0, target.rgb, weight).  Synchronises. */
+ddgi_status ddgi_mlp_samples_get(ddgi_ctx* ctx, float* out, void* stream);
+
+/* Optimiser / judge state (host double[8]): loss scale, last step overflowed,
+ * training samples of the last step, held-out error of the network, of the
+ * probes, held-out count, network serving (1/0), Adam steps.  Synchronises. */
+ddgi_status ddgi_mlp_status(ddgi_ctx* ctx, double* out, void* stream);
 
 /* Synchronise `stream`, return (and clear) the device error word:
  * DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded the node-visit cap or the

@@ -3,6 +3,7 @@
 // stream and returns without synchronising (except the documented getters).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -36,6 +37,24 @@ struct ddgi_ctx {
     uint32_t* counter = nullptr;   // work counter of the persistent trace kernel
     float2* hits = nullptr;        // per-ray hit records (t, triangle), grown on demand
     size_t hits_cap = 0;
+    float4* ind = nullptr;         // per-query network radiance, grown on demand
+    size_t ind_cap = 0;
+    // learned target form
+    float* mlp_params = nullptr;   // fp32 master [MLP_NPARAM]
+    float* mlp_grad = nullptr;
+    float* mlp_m = nullptr;
+    float* mlp_v = nullptr;
+    __half* mlp_w16 = nullptr;     // fp16 weights [MLP_NW]
+    MLPState* mlp_state = nullptr;
+    float4* train_smp = nullptr;   // [train_samples][3]
+    float4* train_sf = nullptr;    // [train_per]
+    uint32_t train_per = 0;
+    uint32_t mlp_step = 0;
+    float mlp_lo[3] = {0.f, 0.f, 0.f};
+    float mlp_scale = 1.f;
+    float4* tmp_smp = nullptr;     // caller samples staged on the device
+    size_t tmp_cap = 0;
+    float* tmp_grad = nullptr;
     uint32_t updates = 0;
     uint32_t bvh_nodes = 0, bvh_depth = 0;
     uint64_t device_bytes = 0;
@@ -90,11 +109,11 @@ double rng_h(uint32_t seed, uint32_t pixel, uint32_t frame, uint32_t pass, uint3
 }
 
 // uniform random rotation from a unit quaternion (Shoemake's method)
-void frame_rotation(uint32_t seed, uint32_t frame, float R[9]) {
+void frame_rotation(uint32_t seed, uint32_t frame, float R[9], uint32_t pass = PASS_PROBE_ROT) {
     const double PI = 3.14159265358979323846;
-    double u0 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 0);
-    double u1 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 1);
-    double u2 = rng_h(seed, 0, frame, PASS_PROBE_ROT, 0, 2);
+    double u0 = rng_h(seed, 0, frame, pass, 0, 0);
+    double u1 = rng_h(seed, 0, frame, pass, 0, 1);
+    double u2 = rng_h(seed, 0, frame, pass, 0, 2);
     double a = std::sqrt(1.0 - u0), b = std::sqrt(u0);
     double x = a * std::sin(2 * PI * u1), y = a * std::cos(2 * PI * u1);
     double z = b * std::sin(2 * PI * u2), w = b * std::cos(2 * PI * u2);
@@ -207,6 +226,13 @@ ddgi_status check_config(const ddgi_config* c, std::string* why) {
     if (c->spatial_neighbours > 32) { *why = "spatial_neighbours must be <= 32"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_radius < 1 || c->spatial_radius > 255) { *why = "spatial_radius must be 1..255"; return DDGI_ERR_INVALID_ARG; }
     if (!std::isfinite(c->normal_reject_cos) || !(c->depth_reject_frac >= 0.f)) { *why = "bad rejection thresholds"; return DDGI_ERR_INVALID_ARG; }
+    const uint64_t P = (uint64_t)c->counts[0] * c->counts[1] * c->counts[2];
+    if (c->train_samples > 0 && (c->train_samples % 16 != 0 || c->train_samples % P != 0 ||
+                                 c->train_samples / P > 65536 || c->train_samples > (1u << 24))) {
+        *why = "train_samples must be a multiple of 16 and of the probe count"; return DDGI_ERR_INVALID_ARG;
+    }
+    if (c->learned_target && c->train_samples == 0) { *why = "learned target needs train_samples"; return DDGI_ERR_INVALID_ARG; }
+    if (c->train_samples > 0 && !(c->train_lr > 0.f && c->train_lr < 1.f)) { *why = "train_lr must be in (0, 1)"; return DDGI_ERR_INVALID_ARG; }
     return DDGI_OK;
 }
 
@@ -239,6 +265,66 @@ void release(ddgi_ctx* c) {
     if (c->hits) cudaFree(c->hits);
     c->hits = nullptr;
     c->hits_cap = 0;
+    if (c->ind) cudaFree(c->ind);
+    c->ind = nullptr;
+    c->ind_cap = 0;
+    if (c->tmp_smp) cudaFree(c->tmp_smp);
+    c->tmp_smp = nullptr;
+    c->tmp_cap = 0;
+}
+
+// stream-ordered growth of a scratch buffer of T
+template <class T>
+cudaError_t grow(ddgi_ctx* c, T** buf, size_t* cap, size_t n, cudaStream_t st) {
+    if (n <= *cap) return cudaSuccess;
+    size_t nc = n + n / 4;
+    T* p = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), nc * sizeof(T), st);
+    if (e != cudaSuccess) return e;
+    if (*buf) {
+        e = cudaFreeAsync(*buf, st);
+        c->device_bytes -= *cap * sizeof(T);
+    }
+    *buf = p;
+    *cap = nc;
+    c->device_bytes += nc * sizeof(T);
+    return e;
+}
+
+MLPView mlp_view(ddgi_ctx* c) {
+    MLPView m;
+    m.w16 = c->mlp_w16;
+    m.params = c->mlp_params;
+    for (int a = 0; a < 3; ++a) m.lo[a] = c->mlp_lo[a];
+    m.scale = c->mlp_scale;
+    return m;
+}
+
+// He-uniform initialisation from the PCG hash: w = (2u - 1) sqrt(6 / fan_in)
+void mlp_init(uint32_t seed, std::vector<float>& p) {
+    p.assign(MLP_NPARAM, 0.f);
+    for (int l = 0; l < 5; ++l) {
+        const int in = mlp_in(l), out = l == 4 ? 3 : 64;
+        const double bound = std::sqrt(6.0 / in);
+        for (int o = 0; o < out; ++o)
+            for (int i = 0; i < in; ++i) {
+                const uint32_t idx = (uint32_t)(mlp_off_w(l) + o * in + i);
+                const double u = rng_h(seed, idx, 0, 11, 0, 0);
+                p[idx] = (float)((2.0 * u - 1.0) * bound);
+            }
+    }
+}
+
+cudaError_t mlp_upload(ddgi_ctx* c, const float* host_params) {
+    std::vector<__half> h(MLP_NW);
+    for (int i = 0; i < MLP_NW; ++i) h[i] = __float2half_rn(host_params[i]);
+    cudaError_t e = cudaMemcpy(c->mlp_params, host_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16, h.data(), MLP_NW * sizeof(__half), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->mlp_m, 0, MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->mlp_v, 0, MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, MLP_NPARAM * sizeof(float));
+    c->mlp_step = 0;
+    return e;
 }
 
 // Hit-record scratch for n rays; grows stream-ordered (no device sync).
@@ -383,6 +469,15 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(sf, R)
     ALLOC(err, 4)
     ALLOC(counter, 4)
+    ALLOC(mlp_params, MLP_NPARAM)
+    ALLOC(mlp_grad, MLP_NPARAM)
+    ALLOC(mlp_m, MLP_NPARAM)
+    ALLOC(mlp_v, MLP_NPARAM)
+    ALLOC(tmp_grad, MLP_NPARAM)
+    ALLOC(mlp_w16, MLP_NW)
+    ALLOC(mlp_state, 1)
+    ALLOC(train_smp, 3ull * cfg->train_samples)
+    ALLOC(train_sf, cfg->train_samples ? cfg->train_samples / P : 0)
 #undef ALLOC
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -403,7 +498,41 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     if (e == cudaSuccess) e = cudaMemset(ctx->rays, 0, P * R * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, 4 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 4 * sizeof(uint32_t));
-    if (e == cudaSuccess) e = ensure_hits(ctx, P * R, 0);
+    if (e == cudaSuccess) e = ensure_hits(ctx, std::max<size_t>(P * R, cfg->train_samples), 0);
+    if (e == cudaSuccess) {
+        // network: scene box for the input normalisation, initial weights, state
+        float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+        for (uint64_t i = 0; i < 3ull * T; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::fmin(lo[a], scene->vertices[3 * i + a]);
+                hi[a] = std::fmax(hi[a], scene->vertices[3 * i + a]);
+            }
+        float ext = 0.f;
+        for (int a = 0; a < 3; ++a) {
+            ctx->mlp_lo[a] = T ? lo[a] : 0.f;
+            ext = std::fmax(ext, hi[a] - lo[a]);
+        }
+        ctx->mlp_scale = ext > 0.f ? 1.f / ext : 1.f;
+        std::vector<float> p0;
+        mlp_init(cfg->mlp_seed, p0);
+        e = mlp_upload(ctx, p0.data());
+        MLPState st0{};
+        st0.loss_scale = 1.f;
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->mlp_state, &st0, sizeof(st0), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && cfg->train_samples) {
+            const uint32_t per = (uint32_t)(cfg->train_samples / P);
+            ctx->train_per = per;
+            std::vector<float4> tsf(per);
+            for (uint32_t i = 0; i < per; ++i) {
+                double z = 1.0 - (2.0 * i + 1.0) / per;
+                double r = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+                double ph = i * 0.6180339887498949;
+                ph = 2.0 * 3.14159265358979323846 * (ph - std::floor(ph));
+                tsf[i] = make_float4((float)(r * std::cos(ph)), (float)(r * std::sin(ph)), (float)z, 0.f);
+            }
+            e = cudaMemcpy(ctx->train_sf, tsf.data(), per * sizeof(float4), cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) {
         VolumeView v = volume_view(ctx);
@@ -540,8 +669,12 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     if (n > 0 && (!residual || !aligned(residual, 16)))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "residual NULL or misaligned");
     CK(ensure_hits(ctx, (size_t)n * ctx->cfg.num_bsdf_candidates, (cudaStream_t)stream));
+    MLPView mv = mlp_view(ctx);
+    if (ctx->cfg.learned_target)
+        CK(grow(ctx, &ctx->ind, &ctx->ind_cap, (size_t)n * ctx->cfg.num_bsdf_candidates, (cudaStream_t)stream));
     CK(launch_restir_initial(scene_view(ctx), volume_view(ctx), restir_params(ctx), g, r,
                              reinterpret_cast<float4*>(residual), frame, ctx->hits, ctx->counter,
+                             ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind,
                              (cudaStream_t)stream));
     return DDGI_OK;
 }
@@ -598,8 +731,109 @@ ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs
     if (n > 0 && (!residual || !radiance || !aligned(residual, 16) || !aligned(radiance, 16)))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "residual / radiance NULL or misaligned");
     CK(ensure_hits(ctx, (size_t)n, (cudaStream_t)stream));
+    MLPView mv = mlp_view(ctx);
+    if (ctx->cfg.learned_target) CK(grow(ctx, &ctx->ind, &ctx->ind_cap, (size_t)n, (cudaStream_t)stream));
     CK(launch_shade(scene_view(ctx), volume_view(ctx), g, r, reinterpret_cast<const float4*>(residual),
-                    reinterpret_cast<float4*>(radiance), ctx->hits, ctx->counter, (cudaStream_t)stream));
+                    reinterpret_cast<float4*>(radiance), ctx->hits, ctx->counter,
+                    ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    if (ctx->cfg.train_samples == 0) return fail(ctx, DDGI_ERR_INVALID_ARG, "train_samples is 0");
+    TrainParams tp;
+    frame_rotation(ctx->cfg.seed, frame, tp.R, PASS_TRAIN_ROT);
+    tp.sf = ctx->train_sf;
+    tp.per = ctx->train_per;
+    tp.samples = ctx->cfg.train_samples;
+    tp.seed = ctx->cfg.seed;
+    tp.frame = frame;
+    CK(launch_mlp_train_frame(scene_view(ctx), volume_view(ctx), mlp_view(ctx), tp, ctx->train_smp, ctx->hits,
+                              ctx->counter, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad, ctx->mlp_m,
+                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ++ctx->mlp_step,
+                              (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_infer(ddgi_ctx* ctx, const float* queries, float* out, uint32_t n, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    if (n > 0 && (!queries || !out || !aligned(queries, 16) || !aligned(out, 16)))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "queries / out NULL or misaligned");
+    CK(launch_mlp_infer_buffer(mlp_view(ctx), queries, out, n, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+static ddgi_status stage_samples(ddgi_ctx* ctx, const float* samples, uint32_t n, cudaStream_t st) {
+    if (n == 0 || !samples) return fail(ctx, DDGI_ERR_INVALID_ARG, "no samples");
+    CK(grow(ctx, &ctx->tmp_smp, &ctx->tmp_cap, 3ull * n, st));
+    CK(cudaMemcpyAsync(ctx->tmp_smp, samples, 3ull * n * sizeof(float4), cudaMemcpyDefault, st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_grad(ddgi_ctx* ctx, const float* samples, uint32_t n, float* grad, void* stream) {
+    if (!ctx || !grad) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ddgi_status s = stage_samples(ctx, samples, n, st);
+    if (s != DDGI_OK) return s;
+    CK(launch_mlp_grad_only(mlp_view(ctx), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_grad, ctx->tmp_grad, st));
+    CK(cudaMemcpyAsync(grad, ctx->tmp_grad, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_step(ddgi_ctx* ctx, const float* samples, uint32_t n, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ddgi_status s = stage_samples(ctx, samples, n, st);
+    if (s != DDGI_OK) return s;
+    CK(launch_mlp_step(mlp_view(ctx), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad,
+                       ctx->mlp_m, ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr > 0.f ? ctx->cfg.train_lr : 1e-3f,
+                       ++ctx->mlp_step, st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_params_get(ddgi_ctx* ctx, float* params, void* stream) {
+    if (!ctx || !params) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(params, ctx->mlp_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_params_set(ddgi_ctx* ctx, const float* params, void* stream) {
+    if (!ctx || !params) return DDGI_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<float> h(MLP_NPARAM);
+    CK(cudaMemcpy(h.data(), params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault));
+    for (float v : h)
+        if (!std::isfinite(v)) return fail(ctx, DDGI_ERR_INVALID_ARG, "non-finite parameter");
+    CK(mlp_upload(ctx, h.data()));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_samples_get(ddgi_ctx* ctx, float* out, void* stream) {
+    if (!ctx || !out || ctx->cfg.train_samples == 0) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, ctx->train_smp, 3ull * ctx->cfg.train_samples * sizeof(float4), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_status(ddgi_ctx* ctx, double* out, void* stream) {
+    if (!ctx || !out) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    MLPState h;
+    CK(cudaMemcpyAsync(&h, ctx->mlp_state, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out[0] = h.loss_scale;
+    out[1] = h.overflow;
+    out[2] = h.count;
+    out[3] = h.judge_mlp;
+    out[4] = h.judge_probe;
+    out[5] = h.judge_n;
+    out[6] = h.use_mlp;
+    out[7] = ctx->mlp_step;
     return DDGI_OK;
 }
 

@@ -62,7 +62,8 @@ cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView
                            const GBufView& g, float2* hits, uint32_t* counter, cudaStream_t st);
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
-                                  uint32_t frame, float2* hits, uint32_t* counter, cudaStream_t st);
+                                  uint32_t frame, float2* hits, uint32_t* counter, const struct MLPView* mlp,
+                                  struct MLPState* mst, float4* ind, cudaStream_t st);
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                    float3 prev_cam, const ResView& cur,
                                    const ResView& prev, const ResView& out, uint32_t frame,
@@ -70,6 +71,33 @@ cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, c
 cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                   const ResView& in, const ResView& out, uint32_t frame,
                                   uint32_t pass, cudaStream_t st);
+// learned target form (mlp.cu)
+#include "mlp.cuh"
+#define PASS_TRAIN_ROT 9u
+#define PASS_TRAIN_BOUNCE 10u
+struct TrainParams {
+    float R[9];           // per-frame rotation of the training ray set
+    const float4* sf;     // spherical Fibonacci directions, [per]
+    uint32_t per;         // training rays per probe
+    uint32_t samples;     // probes * per
+    uint32_t seed, frame;
+};
+cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, float* out, uint32_t n,
+                                    cudaStream_t st);
+cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const TrainParams& tp,
+                                   float4* smp, float2* hits, uint32_t* counter, MLPState* state, float* params,
+                                   float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
+                                   cudaStream_t st);
+cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
+                                 float* out, cudaStream_t st);
+cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* params,
+                            float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
+                            cudaStream_t st);
+cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
+                            cudaStream_t st);
+cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, __half* w16, MLPState* state,
+                            float lr, uint32_t step, cudaStream_t st);
+
 // image metrics: per-block fp64 partials in `scratch` (2 doubles per block)
 constexpr uint32_t kMetricMaxBlocks = 1024;
 uint32_t metric_blocks(uint32_t n);
@@ -78,4 +106,5 @@ cudaError_t launch_metrics(const float4* img, const float4* ref, uint32_t n, dou
 
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
                          const ResView& r, const float4* resid, float4* radiance, float2* hits,
-                         uint32_t* counter, cudaStream_t st);
+                         uint32_t* counter, const struct MLPView* mlp, struct MLPState* mst, float4* ind,
+                         cudaStream_t st);

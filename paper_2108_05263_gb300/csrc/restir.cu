@@ -106,10 +106,44 @@ struct BsdfGen {
     }
 };
 
+// network query at each BSDF hit (learned target form): rho(y) max(f(y), 0)
+struct BsdfHitQuery {
+    SceneView s;
+    GBufView g;
+    RestirParams rp;
+    uint32_t frame, nl, nb;
+    const float2* hits;
+    float4* ind;
+    __device__ bool query(uint32_t i, f3& p, f3& n) const {
+        const uint32_t pix = i / nb, b = i - pix * nb;
+        float4 g1 = g.g1[pix];
+        if (__float_as_uint(g1.w) == DDGI_NONE) return false;
+        float2 hv = hits[i];
+        uint32_t tri = __float_as_uint(hv.y);
+        if (tri == DDGI_NONE) return false;
+        f3 w = bsdf_dir(rp, pix, frame, nl + b, xyz(g1));
+        f3 ny = xyz(__ldg(s.nrm + tri));
+        if (!(dot(ny, w) < 0.f) || !any_pos(xyz(__ldg(s.alb + tri)))) return false;
+        p = xyz(g.g0[pix]) + w * hv.x;
+        n = ny;
+        return true;
+    }
+    __device__ void store(uint32_t i, bool valid, f3 f) const {
+        if (!valid) {
+            ind[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
+        f3 rho = xyz(__ldg(s.alb + __float_as_uint(hits[i].y)));
+        ind[i] = make_float4(rho.x * fmaxf(f.x, 0.f), rho.y * fmaxf(f.y, 0.f), rho.z * fmaxf(f.z, 0.f), 1.f);
+    }
+};
+
 __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
                                                         float4* __restrict__ resid, uint32_t frame,
-                                                        const float2* __restrict__ bsdf_hits) {
+                                                        const float2* __restrict__ bsdf_hits,
+                                                        const float4* __restrict__ ind,
+                                                        const MLPState* __restrict__ mst) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
@@ -181,8 +215,15 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             y = x + w * h.t;
             d2 = h.t * h.t;
             cx = dot(nx, w);
-            cy = fabsf(dot(xyz(__ldg(s.nrm + tri)), w));
-            L = radiance_at(s, v, y, tri, x);
+            float cyn = dot(xyz(__ldg(s.nrm + tri)), w);
+            cy = fabsf(cyn);
+            if (mst != nullptr && mst->use_mlp) {
+                // learned target: Le + the network's rho max(f, 0), front faces only
+                const uint32_t qi = pix * NB + (c - NL);
+                L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
+            } else {
+                L = radiance_at(s, v, y, tri, x);
+            }
             if (cx > 0.f) {
                 float G = cx * cy / d2;
                 if (G > 1.f) res = res + mul(rho, L) * ((1.f - 1.f / G) / (float)NB);
@@ -346,15 +387,22 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
-                                  uint32_t frame, float2* hits, uint32_t* counter, cudaStream_t st) {
+                                  uint32_t frame, float2* hits, uint32_t* counter, const MLPView* mlp,
+                                  MLPState* mst, float4* ind, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     const uint32_t nl = s.num_emitters > 0 ? rp.n_light : 0u;
     BsdfGen gen{g, rp, frame, nl, rp.n_bsdf};
     cudaError_t e = launch_trace<BsdfGen, false>(s, gen, (uint32_t)g.width * g.height * rp.n_bsdf,
                                                  counter, hits, st);
     if (e != cudaSuccess) return e;
+    if (mlp) {
+        e = launch_mlp_infer(*mlp, BsdfHitQuery{s, g, rp, frame, nl, rp.n_bsdf, hits, ind},
+                             (uint32_t)g.width * g.height * rp.n_bsdf, st);
+        if (e != cudaSuccess) return e;
+    }
     dim3 b(16, 8);
-    k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits);
+    k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind,
+                                                                     mlp ? mst : nullptr);
     return cudaGetLastError();
 }
 

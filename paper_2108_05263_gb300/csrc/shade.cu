@@ -84,10 +84,42 @@ struct ShadowGen {
     }
 };
 
+// network query at each visible selected sample (learned target form)
+struct ShadeQuery {
+    SceneView s;
+    GBufView g;
+    ResView r;
+    const float2* vis;
+    float4* ind;
+    __device__ bool query(uint32_t pix, f3& p, f3& n) const {
+        if (__float_as_uint(g.g1[pix].w) == DDGI_NONE) return false;
+        const float4* rec = r.rec + 4 * (size_t)pix;
+        float4 r0 = __ldg(rec);
+        uint32_t ty = __float_as_uint(__ldg(rec + 3).x);
+        if (ty == DDGI_NONE || !(r0.w > 0.f)) return false;
+        if (__float_as_uint(vis[pix].y) != DDGI_NONE) return false;
+        f3 ny = xyz(__ldg(s.nrm + ty));
+        if (!(dot(ny, xyz(g.g0[pix]) - xyz(r0)) > 0.f) || !any_pos(xyz(__ldg(s.alb + ty)))) return false;
+        p = xyz(r0);
+        n = ny;
+        return true;
+    }
+    __device__ void store(uint32_t pix, bool valid, f3 f) const {
+        if (!valid) {
+            ind[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
+        f3 rho = xyz(__ldg(s.alb + __float_as_uint(__ldg(r.rec + 4 * (size_t)pix + 3).x)));
+        ind[pix] = make_float4(rho.x * fmaxf(f.x, 0.f), rho.y * fmaxf(f.y, 0.f), rho.z * fmaxf(f.z, 0.f), 1.f);
+    }
+};
+
 __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
                                                const float4* __restrict__ resid,
                                                float4* __restrict__ radiance,
-                                               const float2* __restrict__ vis) {
+                                               const float2* __restrict__ vis,
+                                               const float4* __restrict__ ind,
+                                               const MLPState* __restrict__ mst) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
@@ -114,7 +146,13 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
             float cx = dot(nx, w);
             if (cx > 0.f) {
                 if (__float_as_uint(__ldg(vis + pix).y) == DDGI_NONE) {
-                    f3 L = radiance_at(s, v, y, ty, x);
+                    f3 L;
+                    if (mst != nullptr && mst->use_mlp) {
+                        bool front = dot(xyz(__ldg(s.nrm + ty)), x - y) > 0.f;
+                        L = front ? xyz(__ldg(s.emi + ty)) + xyz(__ldg(ind + pix)) : f3{0.f, 0.f, 0.f};
+                    } else {
+                        L = radiance_at(s, v, y, ty, x);
+                    }
                     float cy = fabsf(dot(xyz(__ldg(s.nrm + ty)), w));
                     float G = cx * cy / d2;
                     out = out + mul(rho, L) * (fminf(G, 1.f) * r0.w * (1.f / DDGI_PI));
@@ -139,12 +177,18 @@ cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView
 
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
                          const ResView& r, const float4* resid, float4* radiance, float2* hits,
-                         uint32_t* counter, cudaStream_t st) {
+                         uint32_t* counter, const MLPView* mlp, MLPState* mst, float4* ind,
+                         cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     cudaError_t e = launch_trace<ShadowGen, true>(s, ShadowGen{g, r}, (uint32_t)g.width * g.height,
                                                   counter, hits, st);
     if (e != cudaSuccess) return e;
+    if (mlp) {
+        e = launch_mlp_infer(*mlp, ShadeQuery{s, g, r, hits, ind}, (uint32_t)g.width * g.height, st);
+        if (e != cudaSuccess) return e;
+    }
     dim3 b(16, 8);
-    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits);
+    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
+                                                           mlp ? mst : nullptr);
     return cudaGetLastError();
 }

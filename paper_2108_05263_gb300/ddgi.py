@@ -41,7 +41,9 @@ class Config(C.Structure):
                 ("num_light_candidates", C.c_uint32), ("num_bsdf_candidates", C.c_uint32),
                 ("temporal_mcap", C.c_float), ("spatial_neighbours", C.c_uint32),
                 ("spatial_radius", C.c_uint32), ("normal_reject_cos", C.c_float),
-                ("depth_reject_frac", C.c_float), ("seed", C.c_uint32)]
+                ("depth_reject_frac", C.c_float), ("seed", C.c_uint32),
+                ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
+                ("mlp_seed", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -78,7 +80,11 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_image_metrics",
-           "ddgi_image_metrics_static", "ddgi_get_status", "ddgi_last_error"]
+           "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
+           "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_set", "ddgi_mlp_samples_get",
+           "ddgi_mlp_status", "ddgi_get_status", "ddgi_last_error"]
+
+MLP_NPARAM = 18184
 
 
 def lib_path() -> str:
@@ -114,6 +120,14 @@ def load(path: Optional[str] = None):
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
     L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
     L.ddgi_image_metrics_static.argtypes = [vp, vp, C.c_uint32, vp, vp]
+    L.ddgi_mlp_train.argtypes = [vp, C.c_uint32, vp]
+    L.ddgi_mlp_infer.argtypes = [vp, vp, vp, C.c_uint32, vp]
+    L.ddgi_mlp_grad.argtypes = [vp, vp, C.c_uint32, vp, vp]
+    L.ddgi_mlp_step.argtypes = [vp, vp, C.c_uint32, vp]
+    L.ddgi_mlp_params_get.argtypes = [vp, vp, vp]
+    L.ddgi_mlp_params_set.argtypes = [vp, vp, vp]
+    L.ddgi_mlp_samples_get.argtypes = [vp, vp, vp]
+    L.ddgi_mlp_status.argtypes = [vp, vp, vp]
     L.ddgi_get_status.argtypes = [vp, vp]
     L.ddgi_last_error.argtypes = [vp]
     L.ddgi_last_error.restype = C.c_char_p
@@ -223,6 +237,10 @@ def config_from(grid, settings) -> Config:
     c.normal_reject_cos = settings.normal_reject_cos
     c.depth_reject_frac = settings.depth_reject_frac
     c.seed = settings.seed
+    c.learned_target = int(getattr(settings, "learned_target", 0))
+    c.train_samples = int(getattr(settings, "train_samples", 0))
+    c.train_lr = float(getattr(settings, "train_lr", 1e-3))
+    c.mlp_seed = int(getattr(settings, "mlp_seed", 1))
     return c
 
 
@@ -341,6 +359,47 @@ class Context:
         gc, rc = g.c(), res.c()
         self._check("ddgi_shade", self.L.ddgi_shade(self.h, C.byref(gc), C.byref(rc), _ptr(residual),
                                                     _ptr(radiance), _stream(stream)))
+
+    # --- learned target form ---
+    def mlp_train(self, frame, stream=None):
+        self._check("ddgi_mlp_train", self.L.ddgi_mlp_train(self.h, frame, _stream(stream)))
+
+    def mlp_infer(self, queries: torch.Tensor, out: torch.Tensor, stream=None):
+        self._check("ddgi_mlp_infer", self.L.ddgi_mlp_infer(self.h, _ptr(queries), _ptr(out),
+                                                            queries.shape[0], _stream(stream)))
+
+    def mlp_grad(self, samples, stream=None) -> np.ndarray:
+        a = np.ascontiguousarray(samples, np.float32)
+        g = np.zeros(MLP_NPARAM, np.float32)
+        self._check("ddgi_mlp_grad", self.L.ddgi_mlp_grad(self.h, a.ctypes.data, a.shape[0], g.ctypes.data,
+                                                          _stream(stream)))
+        return g
+
+    def mlp_step(self, samples, stream=None):
+        a = np.ascontiguousarray(samples, np.float32)
+        self._check("ddgi_mlp_step", self.L.ddgi_mlp_step(self.h, a.ctypes.data, a.shape[0], _stream(stream)))
+        torch.cuda.current_stream().synchronize()
+
+    def mlp_params(self, stream=None) -> np.ndarray:
+        p = np.zeros(MLP_NPARAM, np.float32)
+        self._check("ddgi_mlp_params_get", self.L.ddgi_mlp_params_get(self.h, p.ctypes.data, _stream(stream)))
+        return p
+
+    def mlp_set_params(self, params, stream=None):
+        a = np.ascontiguousarray(params, np.float32)
+        self._check("ddgi_mlp_params_set", self.L.ddgi_mlp_params_set(self.h, a.ctypes.data, _stream(stream)))
+
+    def mlp_samples(self, stream=None) -> np.ndarray:
+        n = self.cfg.train_samples
+        out = np.zeros((n, 12), np.float32)
+        self._check("ddgi_mlp_samples_get", self.L.ddgi_mlp_samples_get(self.h, out.ctypes.data, _stream(stream)))
+        return out
+
+    def mlp_status(self, stream=None) -> dict:
+        o = np.zeros(8, np.float64)
+        self._check("ddgi_mlp_status", self.L.ddgi_mlp_status(self.h, o.ctypes.data, _stream(stream)))
+        keys = ["loss_scale", "overflow", "count", "judge_mlp", "judge_probe", "judge_n", "use_mlp", "step"]
+        return dict(zip(keys, o.tolist()))
 
     def get_status(self, stream=None) -> int:
         return self.L.ddgi_get_status(self.h, _stream(stream))

@@ -92,6 +92,10 @@ class Settings:
     normal_reject_cos: float = 0.9
     depth_reject_frac: float = 0.1
     seed: int = 1
+    learned_target: int = 0      # 1: the network serves p-hat / termination queries
+    train_samples: int = 0       # self-training samples per frame
+    train_lr: float = 1e-3
+    mlp_seed: int = 1
 
 
 @dataclasses.dataclass
@@ -211,9 +215,12 @@ def tiny_room(seed: int = 1, width: int = 128, height: int = 128,
                  grid, cams, st)
 
 
-def tiny_room_1080p(seed: int = 1, frames: int = 32) -> Scene:
-    """The tiny room rendered at 1920x1080 (learned-target workload)."""
-    return tiny_room(seed, 1920, 1080, frames, name="tiny_room_1080p")
+def tiny_room_1080p(seed: int = 1, frames: int = 32, learned: bool = True) -> Scene:
+    """The tiny room rendered at 1920x1080 with the learned target: 65,536
+    self-training samples per frame, Adam lr 1e-3."""
+    sc = tiny_room(seed, 1920, 1080, frames, name="tiny_room_1080p")
+    sc.settings = dataclasses.replace(sc.settings, learned_target=int(learned), train_samples=65536)
+    return sc
 
 
 def apartment(seed: int = 7, width: int = 1920, height: int = 1080,

@@ -1,0 +1,188 @@
+"""GPU <-> oracle parity of the learned target form, through the C ABI.
+
+The GPU network computes with fp16 weights and activations and fp32
+accumulation; the oracle repeats the computation in fp64 on the same
+fp16-rounded weights.  Tolerances follow from fp16 activations (11-bit
+significand, 5 layers): outputs within 1e-2 relative (+1e-2 of the mean
+magnitude), gradients within 3e-2 relative L2 per layer."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_05263_gb300 import build
+    build.build()
+    from paper_2108_05263_gb300 import ddgi
+    ddgi.load()
+    return ddgi
+
+
+@pytest.fixture(scope="module")
+def M():
+    import oracle
+    oracle.build()
+    from oracle import mlp
+    return mlp
+
+
+def _to_oracle(flat, M, round16=True):
+    """GPU parameter layout -> oracle [(W, b)] (weights rounded to fp16 as the
+    kernels use them; biases stay fp32)."""
+    flat = np.asarray(flat, np.float32)
+    offs_w = [0, 5120, 9216, 13312, 17408]
+    out = []
+    for l, (o, i) in enumerate(M.layer_shapes()):
+        W = flat[offs_w[l]:offs_w[l] + o * i].reshape(o, i)
+        if round16:
+            W = W.astype(np.float16)
+        b = flat[17920 + 64 * l:17920 + 64 * l + o]
+        out.append((W.astype(np.float64), b.astype(np.float64)))
+    return out
+
+
+def _flat(grads):
+    """oracle gradients -> GPU layout (W5 padded to 8 rows)."""
+    flat = np.zeros(18184)
+    offs_w = [0, 5120, 9216, 13312, 17408]
+    for l, (gW, gb) in enumerate(grads):
+        flat[offs_w[l]:offs_w[l] + gW.size] = gW.reshape(-1)
+        flat[17920 + 64 * l:17920 + 64 * l + gb.size] = gb
+    return flat
+
+
+def _samples(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-1, 1, (n, 3))
+    nn = rng.normal(size=(n, 3))
+    nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+    t = rng.uniform(0, 3, (n, 3))
+    w = (rng.random(n) > 0.1).astype(np.float32)
+    s = np.zeros((n, 12), np.float32)
+    s[:, 0:3], s[:, 3] = y, 1.0
+    s[:, 4:7] = nn
+    s[:, 8:11], s[:, 11] = t, w
+    return s
+
+
+def _close_frac(a, b, rel, absf):
+    return float(np.mean(np.abs(a - b) <= rel * np.abs(b) + absf))
+
+
+def test_inference_matches_oracle(dd, M):
+    import torch
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    params = _to_oracle(ctx.mlp_params(), M)
+    lo, scale = M.scene_box(sc.verts)
+    rng = np.random.default_rng(3)
+    n = 5000
+    p = rng.uniform(-1, 1, (n, 3))
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    q = np.zeros((n, 8), np.float32)
+    q[:, 0:3], q[:, 3], q[:, 4:7] = p, 1.0, nrm
+    q[::7, 3] = 0.0                                    # invalid queries
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.mlp_infer(torch.from_numpy(q).cuda(), out)
+    got = out.cpu().numpy()
+    ref, _ = M.forward(params, M.encode(p, nrm, lo, scale))
+    np.testing.assert_array_equal(got[:, 3], q[:, 3])
+    ok = q[:, 3] > 0
+    assert _close_frac(got[ok, :3], ref[ok], 1e-2, 1e-2 * np.abs(ref).mean()) >= 0.99
+
+
+def test_gradients_match_oracle(dd, M):
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    params = _to_oracle(ctx.mlp_params(), M)
+    lo, scale = M.scene_box(sc.verts)
+    s = _samples(sc, 4096, 5)
+    g = ctx.mlp_grad(s)
+    x = M.encode(s[:, 0:3].astype(np.float64), s[:, 4:7].astype(np.float64), lo, scale)
+    out, cache = M.forward(params, x)
+    _, dout = M.rel_l2(out, s[:, 8:11].astype(np.float64), s[:, 11] > 0)
+    ref = _flat(M.backward(params, cache, dout))
+    offs = [0, 5120, 9216, 13312, 17408, 17920, 18184]
+    for a, b in zip(offs[:-1], offs[1:]):
+        err = np.linalg.norm(g[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
+        assert err < 3e-2, (a, b, err)
+
+
+def test_adam_step_matches_oracle(dd, M):
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    p0 = ctx.mlp_params()
+    params16 = _to_oracle(p0, M)
+    lo, scale = M.scene_box(sc.verts)
+    s = _samples(sc, 4096, 6)
+    ctx.mlp_step(s)
+    p1 = ctx.mlp_params()
+    x = M.encode(s[:, 0:3].astype(np.float64), s[:, 4:7].astype(np.float64), lo, scale)
+    out, cache = M.forward(params16, x)
+    _, dout = M.rel_l2(out, s[:, 8:11].astype(np.float64), s[:, 11] > 0)
+    grads = M.backward(params16, cache, dout)
+    master = _to_oracle(p0, M, round16=False)
+    opt = M.Adam(master)
+    ref = _flat(opt.step(master, grads))
+    d_gpu, d_ref = p1 - p0, ref - p0
+    live = np.abs(_flat(grads)) > 0
+    assert _close_frac(d_gpu[live], d_ref[live], 0.0, 1e-4) >= 0.95
+    assert np.abs(d_gpu - d_ref).max() <= 2.1e-3          # at most 2 lr apart (sign of a ~0 gradient)
+    np.testing.assert_array_equal(p1[17408 + 3 * 64:17920], 0.0)   # padded output rows stay 0
+
+
+def test_training_samples_match_oracle(dd, M):
+    import oracle
+    sc = scenegen.tiny_room()
+    sc.settings = dataclasses.replace(sc.settings, train_samples=4096)
+    ctx = dd.Context.from_scene(sc)
+    S = oracle.Scene(sc)
+    for f in range(2):
+        ctx.probe_update(f)
+    p0 = ctx.mlp_params()
+    ctx.mlp_train(7)
+    got = ctx.mlp_samples()
+    params = _to_oracle(p0, M)
+    lo, scale = M.scene_box(sc.verts)
+    y, ny, target, valid = M.training_samples(oracle, S, sc, params, 7, 4096, sc.settings.seed, lo, scale)
+    gv = got[:, 3] > 0
+    assert np.mean(gv == valid) >= 0.999
+    both = gv & valid
+    assert _close_frac(got[both, 0:3], y[both], 1e-5, 1e-5) >= 0.999
+    np.testing.assert_allclose(got[both, 4:7], ny[both], atol=1e-6)
+    assert _close_frac(got[both, 8:11], target[both], 1e-2, 1e-2) >= 0.99
+    w = both & (np.arange(4096) % 16 != 15)
+    np.testing.assert_array_equal(got[:, 11] > 0, w)
+    st = ctx.mlp_status()
+    assert st["count"] == w.sum() and st["step"] == 1 and st["overflow"] == 0
+    assert st["judge_n"] == (valid & (np.arange(4096) % 16 == 15)).sum()
+    assert st["use_mlp"] in (0.0, 1.0)
+
+
+def test_learned_frame_runs_and_trains(dd, M):
+    """Learned target on the tiny room: training lowers the held-out error
+    of the network, and frames rendered with it stay finite and error-free."""
+    sc = scenegen.tiny_room(frames=24)
+    sc.settings = dataclasses.replace(sc.settings, learned_target=1, train_samples=8192)
+    ctx = dd.Context.from_scene(sc)
+    fr = dd.Frame(ctx, 128, 128, sc.settings.spatial_passes)
+    errs = []
+    for f in range(24):
+        ctx.probe_update(f)
+        ctx.mlp_train(f)
+        st = ctx.mlp_status()
+        errs.append(st["judge_mlp"] / max(st["judge_n"], 1))
+        rad = fr.render(f, sc.cameras[f], probe_update=False).cpu().numpy()
+        assert np.all(np.isfinite(rad))
+    assert np.mean(errs[-4:]) < 0.5 * np.mean(errs[:2])
+    assert ctx.get_status() == dd.OK
