@@ -270,6 +270,11 @@ ddgi_status ddgi_mlp_step(ddgi_ctx* ctx, const float* samples, uint32_t n, void*
 ddgi_status ddgi_mlp_params_get(ddgi_ctx* ctx, float* params, void* stream);
 ddgi_status ddgi_mlp_params_set(ddgi_ctx* ctx, const float* params, void* stream);
 
+/* Who serves the queries of a learned-target context: 0 = the judge of the
+ * last ddgi_mlp_train call (default), 1 = always the network, 2 = always the
+ * probes.  Takes effect for the calls enqueued after it. */
+ddgi_status ddgi_mlp_serve(ddgi_ctx* ctx, int32_t mode, void* stream);
+
 /* The last ddgi_mlp_train call's samples (host or device [train_samples][12]
  * floats: y.xyz, valid, n.xyz, 0, target.rgb, weight).  Synchronises. */
 ddgi_status ddgi_mlp_samples_get(ddgi_ctx* ctx, float* out, void* stream);

@@ -70,7 +70,8 @@ class _Settings(C.Structure):
 class _Volume(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("counts", C.c_int32 * 3),
                 ("irr_n", C.c_int32), ("depth_n", C.c_int32), ("irr", _dp), ("depth", _dp),
-                ("offset", _dp), ("updates", C.c_int32)]
+                ("offset", _dp), ("updates", C.c_int32), ("mlp", _dp), ("mlp_lo", C.c_double * 3),
+                ("mlp_scale", C.c_double), ("use_mlp", C.c_int32)]
 
 
 class _Camera(C.Structure):
@@ -203,6 +204,14 @@ class Volume:
     def updates(self, n):
         self.v.updates = n
 
+    def set_mlp(self, flat_params, lo, scale, use=True):
+        """Serve (Le + L_DDGI+) from the network (library parameter layout)."""
+        self._mlp = np.ascontiguousarray(flat_params, np.float64)
+        self.v.mlp = _p(self._mlp)
+        self.v.mlp_lo = _v3(lo)
+        self.v.mlp_scale = float(scale)
+        self.v.use_mlp = 1 if use else 0
+
     def set_interior(self, irr_int, depth_int):
         """Fill the interior texels and rebuild the borders."""
         n, m = self.irr_n, self.depth_n
@@ -217,6 +226,8 @@ class Volume:
         o.v = _Volume()
         C.pointer(o.v)[0] = self.v
         o._bind()
+        if getattr(self, "_mlp", None) is not None:
+            o._mlp = self._mlp
         return o
 
 
@@ -502,6 +513,15 @@ def radiance(scene: Scene, vol: Volume, y, tri, frm):
     lib().or_radiance_batch(C.byref(scene.s), C.byref(vol.v), C.c_int32(y.shape[0]), _p(y),
                             _p(tri, _ip), _p(frm), _p(L))
     return L
+
+
+def mlp_eval(vol: Volume, p, n):
+    p = np.ascontiguousarray(p, np.float64).reshape(-1, 3)
+    n = np.ascontiguousarray(n, np.float64).reshape(-1, 3)
+    out = np.zeros_like(p)
+    for k in range(p.shape[0]):
+        lib().or_mlp_eval(C.byref(vol.v), _p(p[k]), _p(n[k]), _p(out[k]))
+    return out
 
 
 def target(scene: Scene, x, nx, rho, y, tri, L) -> float:

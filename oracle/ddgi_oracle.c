@@ -590,8 +590,46 @@ void or_onb_local_to_world(const double n[3], const double l[3], double w[3]) {
     for (int k = 0; k < 3; ++k) w[k] = l[0] * t[k] + l[1] * bt[k] + l[2] * n[k];
 }
 
+/* Network of the learned target form: frequency-encoded position (12
+ * frequencies, 3 axes, sin and cos), normal, 5 zeros; 4 ReLU layers of 64; a
+ * linear 3-channel output.  Parameters in the library's documented layout. */
+void or_mlp_eval(const or_volume* v, const double p[3], const double n[3], double out[3]) {
+    static const int off_w[5] = {0, 5120, 9216, 13312, 17408};
+    double x[80], h[64], g[64];
+    for (int a = 0; a < 3; ++a) {
+        double q = (p[a] - v->mlp_lo[a]) * v->mlp_scale;
+        for (int k = 0; k < 12; ++k) {
+            double arg = ldexp(1.0, k) * PI * q;
+            x[24 * a + 2 * k] = sin(arg);
+            x[24 * a + 2 * k + 1] = cos(arg);
+        }
+    }
+    x[72] = n[0]; x[73] = n[1]; x[74] = n[2];
+    for (int i = 75; i < 80; ++i) x[i] = 0.0;
+    const double* w = v->mlp;
+    for (int o = 0; o < 64; ++o) {
+        double acc = w[17920 + o];
+        for (int i = 0; i < 80; ++i) acc += w[off_w[0] + o * 80 + i] * x[i];
+        h[o] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int l = 1; l < 4; ++l) {
+        for (int o = 0; o < 64; ++o) {
+            double acc = w[17920 + 64 * l + o];
+            for (int i = 0; i < 64; ++i) acc += w[off_w[l] + o * 64 + i] * h[i];
+            g[o] = acc > 0.0 ? acc : 0.0;
+        }
+        memcpy(h, g, sizeof(h));
+    }
+    for (int o = 0; o < 3; ++o) {
+        double acc = w[17920 + 256 + o];
+        for (int i = 0; i < 64; ++i) acc += w[off_w[4] + o * 64 + i] * h[i];
+        out[o] = acc;
+    }
+}
+
 /* outgoing radiance (Le + L_DDGI+)(y, y -> x): emission is one-sided, back
- * faces carry nothing, the probe term is queried with the view-path bias */
+ * faces carry nothing, the probe term is queried with the view-path bias (or
+ * the network is evaluated at y in the learned target form) */
 static void radiance_at(const or_scene* s, const or_volume* v, const double y[3], int32_t tri,
                         const double x[3], double L[3]) {
     const double* n = s->normal + 3 * tri;
@@ -601,8 +639,18 @@ static void radiance_at(const or_scene* s, const or_volume* v, const double y[3]
     if (dot3(n, d) <= 0.0) return;
     const double* le = s->emission + 3 * tri;
     const double* rho = s->albedo + 3 * tri;
+    if (!(rho[0] > 0 || rho[1] > 0 || rho[2] > 0)) {
+        for (int c = 0; c < 3; ++c) L[c] = le[c];
+        return;
+    }
+    if (v->use_mlp && v->mlp) {
+        double f[3];
+        or_mlp_eval(v, y, n, f);
+        for (int c = 0; c < 3; ++c) L[c] = le[c] + rho[c] * (f[c] > 0.0 ? f[c] : 0.0);
+        return;
+    }
     double E[3] = {0, 0, 0};
-    if (rho[0] > 0 || rho[1] > 0 || rho[2] > 0) or_biased_query(v, y, n, x, E);
+    or_biased_query(v, y, n, x, E);
     for (int c = 0; c < 3; ++c) L[c] = le[c] + rho[c] / PI * E[c];
 }
 

@@ -53,6 +53,11 @@ typedef struct {
     double* depth;   /* [P][depth_n+2][depth_n+2][2] (mean, mean square) */
     double* offset;  /* [P][3] relocation offsets */
     int32_t updates; /* number of completed probe updates */
+    /* learned target form: when use_mlp, (Le + L_DDGI+)(y) uses the network
+     * rho(y) max(f(y), 0) in place of the probe query */
+    const double* mlp;   /* [18184] parameters in the library's layout */
+    double mlp_lo[3], mlp_scale;
+    int32_t use_mlp;
 } or_volume;
 
 typedef struct {
@@ -142,6 +147,7 @@ int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_r
              const double* resid, const int32_t* pix, int32_t npix, double* radiance);
 void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const double* y,
                        const int32_t* tri, const double* from, double* L);
+void or_mlp_eval(const or_volume* v, const double p[3], const double n[3], double out[3]);
 double or_target(const or_scene* s, const double x[3], const double nx[3],
                  const double rho[3], const double y[3], int32_t tri, const double L[3]);
 #ifdef __cplusplus

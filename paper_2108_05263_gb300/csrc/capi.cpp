@@ -50,6 +50,7 @@ struct ddgi_ctx {
     float4* train_sf = nullptr;    // [train_per]
     uint32_t train_per = 0;
     uint32_t mlp_step = 0;
+    int serve = 0;                 // 0 judge, 1 network, 2 probes
     float mlp_lo[3] = {0.f, 0.f, 0.f};
     float mlp_scale = 1.f;
     float4* tmp_smp = nullptr;     // caller samples staged on the device
@@ -751,7 +752,7 @@ ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     tp.frame = frame;
     CK(launch_mlp_train_frame(scene_view(ctx), volume_view(ctx), mlp_view(ctx), tp, ctx->train_smp, ctx->hits,
                               ctx->counter, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad, ctx->mlp_m,
-                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ++ctx->mlp_step,
+                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ++ctx->mlp_step, ctx->serve,
                               (cudaStream_t)stream));
     return DDGI_OK;
 }
@@ -809,6 +810,13 @@ ddgi_status ddgi_mlp_params_set(ddgi_ctx* ctx, const float* params, void* stream
     for (float v : h)
         if (!std::isfinite(v)) return fail(ctx, DDGI_ERR_INVALID_ARG, "non-finite parameter");
     CK(mlp_upload(ctx, h.data()));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_serve(ddgi_ctx* ctx, int32_t mode, void* stream) {
+    if (!ctx || mode < 0 || mode > 2) return DDGI_ERR_INVALID_ARG;
+    ctx->serve = mode;
+    CK(launch_mlp_serve(ctx->mlp_state, mode, (cudaStream_t)stream));
     return DDGI_OK;
 }
 

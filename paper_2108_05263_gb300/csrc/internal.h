@@ -87,7 +87,8 @@ cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, floa
 cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const TrainParams& tp,
                                    float4* smp, float2* hits, uint32_t* counter, MLPState* state, float* params,
                                    float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
-                                   cudaStream_t st);
+                                   int serve, cudaStream_t st);
+cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st);
 cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                                  float* out, cudaStream_t st);
 cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* params,

@@ -467,8 +467,14 @@ __global__ void k_mlp_begin(MLPState* st) {
     st->judge_n = 0;
 }
 
-__global__ void k_mlp_judge(MLPState* st) {
-    st->use_mlp = (st->judge_n > 0 && st->judge_mlp <= st->judge_probe) ? 1u : 0u;
+// serve: 0 = the judge decides, 1 = always the network, 2 = always the probes
+__global__ void k_mlp_judge(MLPState* st, int serve) {
+    if (serve == 1)
+        st->use_mlp = 1u;
+    else if (serve == 2)
+        st->use_mlp = 0u;
+    else
+        st->use_mlp = (st->judge_n > 0 && st->judge_mlp <= st->judge_probe) ? 1u : 0u;
 }
 
 // gradient of the mean loss (unscaled) into out
@@ -519,7 +525,7 @@ cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, 
 cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const TrainParams& tp,
                                    float4* smp, float2* hits, uint32_t* counter, MLPState* state, float* params,
                                    float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
-                                   cudaStream_t st) {
+                                   int serve, cudaStream_t st) {
     k_mlp_begin<<<1, 1, 0, st>>>(state);
     k_train_primary<<<(tp.samples + 127) / 128, 128, 0, st>>>(s, v, tp, smp);
     cudaError_t e = cudaGetLastError();
@@ -535,7 +541,12 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
     // the judge compares the updated network with the probes on held-out samples
     e = launch_mlp_infer(m, JudgeQuery{v, tp, smp, state}, tp.samples / 16, st);
     if (e != cudaSuccess) return e;
-    k_mlp_judge<<<1, 1, 0, st>>>(state);
+    k_mlp_judge<<<1, 1, 0, st>>>(state, serve);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st) {
+    k_mlp_judge<<<1, 1, 0, st>>>(state, serve);
     return cudaGetLastError();
 }
 

@@ -81,7 +81,7 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
-           "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_set", "ddgi_mlp_samples_get",
+           "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
            "ddgi_mlp_status", "ddgi_get_status", "ddgi_last_error"]
 
 MLP_NPARAM = 18184
@@ -127,6 +127,7 @@ def load(path: Optional[str] = None):
     L.ddgi_mlp_params_get.argtypes = [vp, vp, vp]
     L.ddgi_mlp_params_set.argtypes = [vp, vp, vp]
     L.ddgi_mlp_samples_get.argtypes = [vp, vp, vp]
+    L.ddgi_mlp_serve.argtypes = [vp, C.c_int32, vp]
     L.ddgi_mlp_status.argtypes = [vp, vp, vp]
     L.ddgi_get_status.argtypes = [vp, vp]
     L.ddgi_last_error.argtypes = [vp]
@@ -388,6 +389,10 @@ class Context:
     def mlp_set_params(self, params, stream=None):
         a = np.ascontiguousarray(params, np.float32)
         self._check("ddgi_mlp_params_set", self.L.ddgi_mlp_params_set(self.h, a.ctypes.data, _stream(stream)))
+
+    def mlp_serve(self, mode: int, stream=None):
+        """0: judge decides, 1: always the network, 2: always the probes."""
+        self._check("ddgi_mlp_serve", self.L.ddgi_mlp_serve(self.h, mode, _stream(stream)))
 
     def mlp_samples(self, stream=None) -> np.ndarray:
         n = self.cfg.train_samples

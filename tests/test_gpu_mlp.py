@@ -186,3 +186,74 @@ def test_learned_frame_runs_and_trains(dd, M):
         assert np.all(np.isfinite(rad))
     assert np.mean(errs[-4:]) < 0.5 * np.mean(errs[:2])
     assert ctx.get_status() == dd.OK
+
+
+def _learned_setup(dd, M):
+    import oracle
+    sc = scenegen.tiny_room()
+    sc.settings = dataclasses.replace(sc.settings, learned_target=1, train_samples=4096)
+    ctx = dd.Context.from_scene(sc)
+    S = oracle.Scene(sc)
+    vol = oracle.Volume(sc.grid)
+    for f in range(3):
+        oracle.probe_update(S, vol, f)
+    irr = np.zeros(vol.irr.shape[:-1] + (4,), np.float32)
+    irr[..., :3] = vol.irr
+    ctx.probe_state_set(irr, vol.depth.astype(np.float32), np.zeros((vol.P, 4), np.float32), vol.updates)
+    # a network with visible output: oracle init with positive output biases
+    params = M.init_params(31)
+    W5, b5 = params[4]
+    params[4] = (W5, b5 + 0.5)
+    flat = np.zeros(18184, np.float32)
+    offs = [0, 5120, 9216, 13312, 17408]
+    for l, (W, b) in enumerate(params):
+        flat[offs[l]:offs[l] + W.size] = W.reshape(-1)
+        flat[17920 + 64 * l:17920 + 64 * l + b.size] = b
+    ctx.mlp_set_params(flat)
+    ctx.mlp_serve(1)
+    f16 = flat.copy()
+    f16[:17920] = flat[:17920].astype(np.float16).astype(np.float32)
+    lo, scale = M.scene_box(sc.verts)
+    vol.set_mlp(f16.astype(np.float64), lo, scale)
+    return sc, ctx, S, vol
+
+
+def _rec_fields(dd, out):
+    return dd.Reservoirs.fields(out.numpy())
+
+
+def test_learned_initial_and_shade_match_oracle(dd, M):
+    import oracle
+    import torch
+    sc, ctx, S, vol = _learned_setup(dd, M)
+    cam = sc.cameras[0]
+    g = oracle.gbuffer(S, cam)
+    ref, resid = oracle.restir_initial(S, vol, g, 4)
+    g0, g1, g2 = g.planes()
+    gg = dd.GBuffer(g.width, g.height, planes=[torch.from_numpy(a).cuda() for a in (g0, g1, g2)])
+    n = g.tri.shape[0]
+    out = dd.Reservoirs(n)
+    rr = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(gg, out, rr, 4)
+    f = _rec_fields(dd, out)
+    same = (f["tri"] == ref.tri) & (f["tag"] == ref.tag)
+    assert same.mean() >= 0.99
+    ok = same & (ref.tri >= 0)
+    assert _close_frac(f["L"][ok], ref.L[ok], 2e-2, 1e-3) >= 0.99
+    assert _close_frac(f["W"][ok], ref.W[ok], 2e-2, 1e-6) >= 0.99
+    # shade the oracle's reservoirs with the network's fresh query
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    rec = np.zeros((n, 16), np.float32)
+    rec[:, 0:3], rec[:, 3], rec[:, 4:7], rec[:, 7] = ref.y, ref.W, ref.L, ref.M
+    rec[:, 8:11], rec[:, 11] = g.nrm, g.dist
+    bits = np.zeros((n, 4), np.uint32)
+    bits[:, 0] = ref.tri.astype(np.int64).astype(np.uint32)
+    bits[:, 1] = ref.tag
+    bits[:, 2] = (g.tri >= 0)
+    rec[:, 12:16] = bits.view(np.float32)
+    res4 = np.zeros((n, 4), np.float32)
+    res4[:, :3] = resid
+    ctx.shade(gg, dd.Reservoirs(n, rec=torch.from_numpy(rec).cuda()), torch.from_numpy(res4).cuda(), rad)
+    sref = oracle.shade(S, vol, g, ref, resid)
+    assert _close_frac(rad.cpu().numpy()[:, :3], sref, 2e-2, 1e-3) >= 0.99
+    assert ctx.get_status() == dd.OK

@@ -168,3 +168,28 @@ def test_training_targets_without_network_are_emission(M):
     vals = np.unique(np.round(target[valid], 9))
     assert set(vals.tolist()) <= {0.0, 10.0}
     assert 0.0 < (target[valid, 0] > 0).mean() < 0.5
+
+
+def test_c_network_matches_numpy_network(M):
+    """The C oracle's network (used inside its radiance lookup in the learned
+    form) agrees with the numpy network pinned to torch above."""
+    import oracle
+    import scenegen
+    sc = scenegen.tiny_room()
+    params = M.init_params(21)
+    rng = np.random.default_rng(2)
+    for W, b in params:
+        b += rng.normal(0, 0.2, b.shape)
+    flat = np.zeros(18184)
+    offs = [0, 5120, 9216, 13312, 17408]
+    for l, (W, b) in enumerate(params):
+        flat[offs[l]:offs[l] + W.size] = W.reshape(-1)
+        flat[17920 + 64 * l:17920 + 64 * l + b.size] = b
+    vol = oracle.Volume(sc.grid)
+    lo, scale = M.scene_box(sc.verts)
+    vol.set_mlp(flat, lo, scale)
+    p = rng.uniform(-1, 1, (200, 3))
+    n = rng.normal(size=(200, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    ref, _ = M.forward(params, M.encode(p, n, lo, scale))
+    np.testing.assert_allclose(oracle.mlp_eval(vol, p, n), ref, rtol=1e-11, atol=1e-12)
