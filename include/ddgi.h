@@ -202,6 +202,16 @@ ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservo
 ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* r,
                        const float* residual, float* radiance, void* stream);
 
+/* Path-traced reference of Sec. 4 ("Reference" images for MAPE): unbiased
+ * path tracing with next-event estimation toward area-sampled emitters,
+ * cosine continuation, Russian roulette from the 4th vertex, at most 64
+ * vertices, one path per pixel centre and sample.  Adds samples sample0 ..
+ * sample0 + spp - 1 to accum (device [N][4] doubles: rgb sums, sample count;
+ * zero it before the first call) and, if mean (device [N][4] floats) is not
+ * NULL, writes the running mean there. */
+ddgi_status ddgi_reference_accumulate(ddgi_ctx* ctx, const ddgi_camera* cam, uint32_t sample0, uint32_t spp,
+                                      double* accum, float* mean, void* stream);
+
 /* Error metrics of Sec. 4 between a rendered image and a reference: out[0] =
  * mean squared error, out[1] = mean absolute percentage error
  * mean(|v - ref| / (ref + 0.01)), both over the 3 colour values of every
@@ -246,7 +256,8 @@ ddgi_status ddgi_image_metrics_static(const float* img, const float* ref, uint32
 /* One self-training step: train_samples rays from the probe centres
  * (spherical Fibonacci set per probe, per-frame random rotation) hit y; a
  * cosine-distributed bounce from y hits z; target = Le(z) + rho(z) max(f(z),
- * 0).  Samples 16 j + 15 are held out and judge the updated network against
+ * 0).  The samples train in minibatches of 16,384, one Adam step each.
+ * Samples 16 j + 15 are held out and judge the updated network against
  * the probe lookup (relative squared error); the verdict decides for the
  * following resampling / shading calls whether the network or the probes
  * serve the queries.  Requires train_samples > 0. */

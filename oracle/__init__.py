@@ -515,6 +515,17 @@ def radiance(scene: Scene, vol: Volume, y, tri, frm):
     return L
 
 
+def pt_reference(scene: Scene, cam, pix, seed, sample0, spp):
+    """Sum of spp path-traced samples for each listed pixel ([n, 3])."""
+    pix = np.ascontiguousarray(pix, np.int32)
+    out = np.zeros((len(pix), 3))
+    c = camera(cam)
+    for k, q in enumerate(pix):
+        lib().or_pt_pixel(C.byref(scene.s), C.byref(c), C.c_int32(int(q)), C.c_uint32(seed),
+                          C.c_uint32(sample0), C.c_uint32(spp), _p(out[k]))
+    return out
+
+
 def mlp_eval(vol: Volume, p, n):
     p = np.ascontiguousarray(p, np.float64).reshape(-1, 3)
     n = np.ascontiguousarray(n, np.float64).reshape(-1, 3)

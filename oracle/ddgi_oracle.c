@@ -892,3 +892,76 @@ int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_r
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* path-traced reference (Sec. 4): next-event estimation toward an emitter  */
+/* point uniform in area, cosine continuation, Russian roulette from the    */
+/* 4th vertex, at most 64 vertices; keys (seed, pixel, sample, pass 8,      */
+/* vertex, dimension)                                                       */
+/* ------------------------------------------------------------------------ */
+
+void or_pt_pixel(const or_scene* s, const or_camera* cam, int32_t pix, uint32_t seed, uint32_t sample0,
+                 uint32_t spp, double out[3]) {
+    int32_t W = cam->width, H = cam->height;
+    int32_t i = pix % W, j = pix / W;
+    double aspect = (double)W / H;
+    double sx = (2.0 * (i + 0.5) / W - 1.0) * cam->tan_half_fovy * aspect;
+    double sy = (1.0 - 2.0 * (j + 0.5) / H) * cam->tan_half_fovy;
+    double d0[3];
+    for (int a = 0; a < 3; ++a) d0[a] = cam->fwd[a] + sx * cam->right[a] + sy * cam->up[a];
+    double l0 = len3(d0);
+    for (int a = 0; a < 3; ++a) d0[a] /= l0;
+    out[0] = out[1] = out[2] = 0.0;
+    for (uint32_t k = 0; k < spp; ++k) {
+        uint32_t smp = sample0 + k;
+        double o[3] = {cam->pos[0], cam->pos[1], cam->pos[2]}, d[3] = {d0[0], d0[1], d0[2]};
+        double beta[3] = {1, 1, 1}, L[3] = {0, 0, 0};
+        int32_t tri;
+        double t;
+        int hit = or_intersect(s, o, d, T_EPS, MISS_T, &tri, &t);
+        for (uint32_t depth = 1; depth <= 64; ++depth) {
+            if (!hit) break;
+            const double* n = s->normal + 3 * tri;
+            if (!(dot3(n, d) < 0.0)) break;
+            double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+            if (depth == 1)
+                for (int c = 0; c < 3; ++c) L[c] += s->emission[3 * tri + c];
+            const double* rho = s->albedo + 3 * tri;
+            if (!(rho[0] > 0 || rho[1] > 0 || rho[2] > 0)) break;
+            if (s->num_emitters > 0) {
+                double u0 = or_rng(seed, pix, smp, 8, depth, 0);
+                double u1 = or_rng(seed, pix, smp, 8, depth, 1);
+                double u2 = or_rng(seed, pix, smp, 8, depth, 2);
+                int32_t et = or_sample_emitter(s, u0);
+                const double* tv = s->verts + 9 * et;
+                double sq = sqrt(u1), b1 = sq * (1.0 - u2), b2 = sq * u2, y[3], dv[3];
+                for (int a = 0; a < 3; ++a) y[a] = tv[a] + b1 * (tv[3 + a] - tv[a]) + b2 * (tv[6 + a] - tv[a]);
+                sub3(y, x, dv);
+                double d2 = dot3(dv, dv);
+                if (d2 > 0.0) {
+                    double l = sqrt(d2), w[3] = {dv[0] / l, dv[1] / l, dv[2] / l};
+                    double cx = dot3(n, w), cy = -dot3(s->normal + 3 * et, w);
+                    if (cx > 0.0 && cy > 0.0 && !occluded(s, x, w, T_EPS, (1.0 - 1e-4) * l)) {
+                        double gf = cx * cy / d2 * s->area_total / PI;
+                        for (int c = 0; c < 3; ++c) L[c] += beta[c] * rho[c] * s->emission[3 * et + c] * gf;
+                    }
+                }
+            }
+            double u3 = or_rng(seed, pix, smp, 8, depth, 3), u4 = or_rng(seed, pix, smp, 8, depth, 4);
+            double r = sqrt(u3), ph = 2.0 * PI * u4;
+            double lc[3] = {r * cos(ph), r * sin(ph), sqrt(fmax(0.0, 1.0 - u3))}, w[3];
+            or_onb_local_to_world(n, lc, w);
+            for (int c = 0; c < 3; ++c) beta[c] *= rho[c];
+            if (depth >= 4) {
+                double q = beta[0] > beta[1] ? beta[0] : beta[1];
+                if (beta[2] > q) q = beta[2];
+                if (q > 0.95) q = 0.95;
+                if ((float)or_rng(seed, pix, smp, 8, depth, 5) >= (float)q) break;
+                for (int c = 0; c < 3; ++c) beta[c] /= q;
+            }
+            for (int a = 0; a < 3; ++a) { o[a] = x[a]; d[a] = w[a]; }
+            hit = or_intersect(s, o, d, T_EPS, MISS_T, &tri, &t);
+        }
+        for (int c = 0; c < 3; ++c) out[c] += L[c];
+    }
+}

@@ -147,6 +147,8 @@ int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_r
              const double* resid, const int32_t* pix, int32_t npix, double* radiance);
 void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const double* y,
                        const int32_t* tri, const double* from, double* L);
+void or_pt_pixel(const or_scene* s, const or_camera* cam, int32_t pix, uint32_t seed, uint32_t sample0,
+                 uint32_t spp, double out[3]);
 void or_mlp_eval(const or_volume* v, const double p[3], const double n[3], double out[3]);
 double or_target(const or_scene* s, const double x[3], const double nx[3],
                  const double rho[3], const double y[3], int32_t tri, const double L[3]);

@@ -14,7 +14,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libddgi.so")
 SOURCES = ["capi.cpp", "bvh_build.cpp", "probe.cu", "restir.cu", "shade.cu", "metrics.cu",
-           "metrics_static.cu", "mlp.cu"]
+           "metrics_static.cu", "mlp.cu",
+           "reference.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "--ftz=true", "--prec-div=false",
            "--prec-sqrt=false", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE]

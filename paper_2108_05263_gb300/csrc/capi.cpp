@@ -740,6 +740,18 @@ ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs
     return DDGI_OK;
 }
 
+ddgi_status ddgi_reference_accumulate(ddgi_ctx* ctx, const ddgi_camera* cam, uint32_t sample0, uint32_t spp,
+                                      double* accum, float* mean, void* stream) {
+    if (!ctx || !cam) return DDGI_ERR_INVALID_ARG;
+    uint64_t n = (uint64_t)cam->width * cam->height;
+    if (n > kMaxPixels || (n > 0 && !accum) || !aligned(accum, 16) || (mean && !aligned(mean, 16)))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "accum / mean NULL, misaligned or too large");
+    if (!(cam->tan_half_fovy > 0.f)) return fail(ctx, DDGI_ERR_INVALID_ARG, "field of view must be > 0");
+    CK(launch_reference(scene_view(ctx), cam_view(cam), ctx->cfg.seed, sample0, spp, 64, accum,
+                        reinterpret_cast<float4*>(mean), (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     if (!ctx) return DDGI_ERR_INVALID_ARG;
     if (ctx->cfg.train_samples == 0) return fail(ctx, DDGI_ERR_INVALID_ARG, "train_samples is 0");
@@ -752,8 +764,9 @@ ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     tp.frame = frame;
     CK(launch_mlp_train_frame(scene_view(ctx), volume_view(ctx), mlp_view(ctx), tp, ctx->train_smp, ctx->hits,
                               ctx->counter, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad, ctx->mlp_m,
-                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ++ctx->mlp_step, ctx->serve,
+                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ctx->mlp_step + 1, ctx->serve,
                               (cudaStream_t)stream));
+    ctx->mlp_step += (ctx->cfg.train_samples + MLP_BATCH - 1) / MLP_BATCH;
     return DDGI_OK;
 }
 

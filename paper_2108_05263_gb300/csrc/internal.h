@@ -99,6 +99,9 @@ cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLP
 cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, __half* w16, MLPState* state,
                             float lr, uint32_t step, cudaStream_t st);
 
+cudaError_t launch_reference(const SceneView& s, const CamView& cam, uint32_t seed, uint32_t sample0,
+                             uint32_t spp, uint32_t max_depth, double* accum, float4* mean, cudaStream_t st);
+
 // image metrics: per-block fp64 partials in `scratch` (2 doubles per block)
 constexpr uint32_t kMetricMaxBlocks = 1024;
 uint32_t metric_blocks(uint32_t n);

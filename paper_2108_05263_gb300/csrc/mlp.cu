@@ -334,21 +334,12 @@ __device__ __forceinline__ f3 train_ray_dir(const TrainParams& tp, uint32_t r) {
             tp.R[6] * q.x + tp.R[7] * q.y + tp.R[8] * q.z};
 }
 
-__device__ __forceinline__ f3 onb_world(f3 n, float lx, float ly, float lz) {
-    float sign = n.z >= 0.f ? 1.f : -1.f;
-    float a = -1.f / (sign + n.z);
-    float b = n.x * n.y * a;
-    f3 t = {1.f + sign * n.x * n.x * a, sign * b, -sign * n.x};
-    f3 bt = {b, sign + n.y * n.y * a, -n.y};
-    return t * lx + bt * ly + n * lz;
-}
-
 __device__ __forceinline__ f3 bounce_dir(const TrainParams& tp, uint32_t s, f3 n) {
     const uint32_t cp = rng_cand(rng_prefix(tp.seed, s, tp.frame, PASS_TRAIN_BOUNCE), 0u);
     float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
     float r = sqrtf(u0), sn, cs;
     sincospif(2.f * u1, &sn, &cs);
-    return onb_world(n, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
+    return onb_to_world(n, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
 }
 
 __global__ void __launch_bounds__(128) k_train_primary(SceneView s, VolumeView v, TrainParams tp, float4* smp) {
@@ -468,6 +459,8 @@ __global__ void k_mlp_begin(MLPState* st) {
 }
 
 // serve: 0 = the judge decides, 1 = always the network, 2 = always the probes
+__global__ void k_mlp_count_reset(MLPState* st) { st->count = 0; }
+
 __global__ void k_mlp_judge(MLPState* st, int serve) {
     if (serve == 1)
         st->use_mlp = 1u;
@@ -534,10 +527,15 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
     if (e != cudaSuccess) return e;
     e = launch_mlp_infer(m, TargetQuery{s, tp, smp, hits}, tp.samples, st);
     if (e != cudaSuccess) return e;
-    e = launch_mlp_grad(m, smp, tp.samples, state, grad, st);
-    if (e != cudaSuccess) return e;
-    e = launch_mlp_adam(params, grad, mom, vel, w16, state, lr, step, st);
-    if (e != cudaSuccess) return e;
+    // minibatches of MLP_BATCH samples, one Adam step each
+    for (uint32_t b0 = 0, k = 0; b0 < tp.samples; b0 += MLP_BATCH, ++k) {
+        const uint32_t nb = min(MLP_BATCH, tp.samples - b0);
+        k_mlp_count_reset<<<1, 1, 0, st>>>(state);
+        e = launch_mlp_grad(m, smp + 3 * (size_t)b0, nb, state, grad, st);
+        if (e != cudaSuccess) return e;
+        e = launch_mlp_adam(params, grad, mom, vel, w16, state, lr, step + k, st);
+        if (e != cudaSuccess) return e;
+    }
     // the judge compares the updated network with the probes on held-out samples
     e = launch_mlp_infer(m, JudgeQuery{v, tp, smp, state}, tp.samples / 16, st);
     if (e != cudaSuccess) return e;

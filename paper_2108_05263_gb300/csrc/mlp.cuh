@@ -17,6 +17,7 @@
 #define MLP_OUTP 8
 #define MLP_NPARAM 18184
 #define MLP_NW 17920
+#define MLP_BATCH 16384u   // training samples per Adam step
 #define MLP_LD_IN 88
 #define MLP_LD_H 72
 #define MLP_SW_HALVES (64 * 88 + 3 * 64 * 72 + 8 * 72)   // 20032

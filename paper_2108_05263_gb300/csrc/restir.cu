@@ -14,70 +14,6 @@ struct Sel {
     float p;   // target at the owning pixel
 };
 
-__device__ __forceinline__ uint32_t sample_emitter(const SceneView& s, float u) {
-    // first emitter whose cumulative area exceeds u * total: start at the
-    // guide entry of u (never past the answer) and scan forward
-    const uint32_t E = s.num_emitters;
-    const float target = u * __ldg(s.cdf + E - 1);
-    uint32_t j = min((uint32_t)(u * (float)s.guide_size), s.guide_size - 1);
-    uint32_t i = __ldg(s.guide + j);
-    while (i < E - 1 && !(target < __ldg(s.cdf + i))) ++i;
-    return i;
-}
-
-// orthonormal basis around n (Duff et al., JCGT 2017)
-__device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
-    float sign = n.z >= 0.f ? 1.f : -1.f;
-    float a = -1.f / (sign + n.z);
-    float b = n.x * n.y * a;
-    f3 t = {1.f + sign * n.x * n.x * a, sign * b, -sign * n.x};
-    f3 bt = {b, sign + n.y * n.y * a, -n.y};
-    return t * lx + bt * ly + n * lz;
-}
-
-// reservoir record: q0 = (y, W), q1 = (L, M), q2 = (owner normal, owner
-// distance), q3 = (triangle of y, tag, owner valid, 0)
-struct Rec {
-    float4 q0, q1, q2, q3;
-};
-
-// 32-byte (256-bit) accesses: one L1 sector access per record half
-__device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-}
-
-__device__ __forceinline__ void st32(float4* p, float4 a, float4 b) {
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
-                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void store_rec(float4* p, float4 q0, float4 q1, float4 q2, uint32_t tri,
-                                          uint32_t tag, uint32_t valid) {
-    st32(p, q0, q1);
-    st32(p + 2, q2, make_float4(__uint_as_float(tri), __uint_as_float(tag), __uint_as_float(valid), 0.f));
-}
-
-__device__ __forceinline__ void copy_rec(float4* p, const Rec& r) {
-    st32(p, r.q0, r.q1);
-    st32(p + 2, r.q2, r.q3);
-}
-
-__device__ __forceinline__ Rec load_rec(const float4* p) {
-    Rec r;
-    ld32(p, r.q0, r.q1);
-    ld32(p + 2, r.q2, r.q3);
-    return r;
-}
-
-__device__ __forceinline__ uint32_t rec_tri(const Rec& r) { return __float_as_uint(r.q3.x); }
-
-__device__ __forceinline__ float rec_target(const SceneView& s, f3 x, f3 nx, f3 rho, const Rec& r) {
-    return target_fn(s, x, nx, rho, xyz(r.q0), rec_tri(r), xyz(r.q1));
-}
-
 // cosine-distributed direction of BSDF candidate c at pixel pix (Sec. 3.1 step 1)
 __device__ __forceinline__ f3 bsdf_dir(const RestirParams& rp, uint32_t pix, uint32_t frame,
                                        uint32_t c, f3 nx) {

@@ -79,7 +79,7 @@ _lib = None
 EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
            "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
-           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_image_metrics",
+           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
            "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
            "ddgi_mlp_status", "ddgi_get_status", "ddgi_last_error"]
@@ -118,6 +118,7 @@ def load(path: Optional[str] = None):
     L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
                                  C.c_uint32, vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
+    L.ddgi_reference_accumulate.argtypes = [vp, C.POINTER(Camera), C.c_uint32, C.c_uint32, vp, vp, vp]
     L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
     L.ddgi_image_metrics_static.argtypes = [vp, vp, C.c_uint32, vp, vp]
     L.ddgi_mlp_train.argtypes = [vp, C.c_uint32, vp]
@@ -360,6 +361,13 @@ class Context:
         gc, rc = g.c(), res.c()
         self._check("ddgi_shade", self.L.ddgi_shade(self.h, C.byref(gc), C.byref(rc), _ptr(residual),
                                                     _ptr(radiance), _stream(stream)))
+
+    def reference_accumulate(self, cam, sample0: int, spp: int, accum: torch.Tensor,
+                             mean: Optional[torch.Tensor] = None, stream=None):
+        c = camera(cam)
+        self._check("ddgi_reference_accumulate",
+                    self.L.ddgi_reference_accumulate(self.h, C.byref(c), sample0, spp, _ptr(accum), _ptr(mean),
+                                                     _stream(stream)))
 
     # --- learned target form ---
     def mlp_train(self, frame, stream=None):

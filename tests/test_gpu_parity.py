@@ -495,3 +495,28 @@ def test_image_metrics_rejects_short_scratch(dd):
     img = torch.zeros((4096 * 1024, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(dd.DDGIError):
         dd.image_metrics(img, img, scratch=torch.empty(16, dtype=torch.float64, device="cuda"))
+
+
+# ---------------------------------------------------------------------------
+# path-traced reference (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def test_reference_matches_oracle_paths(dd, orc):
+    """Same random-number keys on both sides: the per-pixel sums of 32 paths
+    agree up to rounding (a rare path that diverges at an edge aside)."""
+    import torch
+    sc = scenegen.tiny_room(width=48, height=40)
+    ctx = dd.Context.from_scene(sc)
+    cam = sc.cameras[0]
+    n = 48 * 40
+    acc = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    mean = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.reference_accumulate(cam, 0, 16, acc, mean)
+    ctx.reference_accumulate(cam, 16, 16, acc, mean)
+    a = acc.cpu().numpy()
+    np.testing.assert_array_equal(a[:, 3], 32.0)
+    pix = np.arange(0, n, 13)
+    ref = orc.pt_reference(orc.Scene(sc), cam, pix, sc.settings.seed, 0, 32)
+    assert _frac(_close(a[pix, :3], ref, 1e-3, 1e-4).all(1)) >= 0.97
+    np.testing.assert_allclose(mean.cpu().numpy()[:, :3], a[:, :3] / 32.0, rtol=1e-6)
+    assert ctx.get_status() == dd.OK

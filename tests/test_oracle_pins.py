@@ -606,3 +606,46 @@ def test_mape_definition():
     v = np.array([0.01, 1.5, 1.0])
     assert oracle.mape(v, ref) == pytest.approx((0.01 / 0.01 + 0.5 / 1.01 + 1.0 / 2.01) / 3)
     assert oracle.mse(v, ref) == pytest.approx((1e-4 + 0.25 + 1.0) / 3)
+
+
+# ---------------------------------------------------------------------------
+# path-traced reference (Sec. 4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_reference_furnace(oracle_lib):
+    """Closed box where every surface emits Le = 1 and has albedo 0.5: the
+    radiance is Le / (1 - rho) = 2 everywhere."""
+    o = oracle_lib
+    base = scenegen.tiny_room(width=8, height=8)
+    T = base.num_tris
+    sc = _custom_scene(base, albedo=np.full((T, 3), 0.5), emission=np.ones((T, 3)))
+    S = o.Scene(sc)
+    spp = 20000
+    # pixels in the middle of the back wall (next-event estimation from points
+    # near the box's creases has a heavy tail)
+    est = o.pt_reference(S, sc.cameras[0], [18, 21, 27, 36, 42, 45], 3, 0, spp) / spp
+    np.testing.assert_allclose(est, 2.0, rtol=0.02)
+
+
+@pytest.mark.slow
+def test_reference_direct_light_form_factor(oracle_lib):
+    """Only the floor reflects (albedo 0.5): a floor pixel's reference is
+    rho * Le * F with F the point-to-rectangle form factor of the emitter."""
+    o = oracle_lib
+    base = scenegen.tiny_room(width=16, height=16)
+    alb = np.zeros_like(base.albedo)
+    S0 = o.Scene(base)
+    floor = np.flatnonzero(S0.normals[:, 1] > 0.9)
+    alb[floor] = 0.5
+    sc = _custom_scene(base, albedo=alb)
+    cam = scenegen._look_camera([0.05, 0.5, 0.02], [0.05, -1.0, 0.0], 16, 16, 60.0)
+    S = o.Scene(sc)
+    g = o.gbuffer(S, cam)
+    pix = np.flatnonzero(g.tri >= 0)[::9]
+    spp = 1500
+    est = o.pt_reference(S, cam, pix, 5, 0, spp) / spp
+    for k, q in enumerate(pix):
+        px = g.pos[q]
+        F = _rect_form_factor(-1 - px[0], -px[0], -1 - px[2], 1 - px[2], 2.0)
+        assert est[k, 0] == pytest.approx(0.5 * 10.0 * F, rel=0.06), (q, est[k], F)
