@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=16)
     ap.add_argument("--res", default="1920x1080",
                     help="frame size WxH; other sizes are profiling cases, not the metric")
+    ap.add_argument("--no-equal-time", action="store_true",
+                    help="skip the equal-time MSE comparison of the learned and probe forms")
+    ap.add_argument("--equal-time-frames", type=int, default=256)
     return ap.parse_args()
 
 
@@ -331,11 +334,109 @@ def run_ours(args, ws, rank, local):
                       "path": "Frame.render through the C ABI, pinned host G-buffer in, radiance out"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=12.0)
+    if rank == 0 and not args.no_equal_time and ws == 1:
+        out["equal_time_mse"] = equal_time_mse(dev, args.equal_time_frames)
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
     if rank == 0:
         print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# equal-time error of the learned form against the probe form
+# ---------------------------------------------------------------------------
+
+PROBE_SWEEP = [(31, 1), (31, 2), (47, 1), (47, 2), (63, 1), (63, 2), (63, 3)]
+
+
+def _form_run(ddgi, torch, sc, cam, g, ref, frames, measure, learned):
+    """Render `frames` frames of a static view; per-frame MSE / MAPE against
+    the reference, frame time (probe update [+ training] + resampling +
+    shade, CUDA events) and the error of the mean of the measured frames."""
+    N = ref.shape[0]
+    ctx = ddgi.Context.from_scene(sc)
+    fr = ddgi.Frame(ctx, cam.width, cam.height, sc.settings.spatial_passes, ref.device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mses, mapes, ms, served = [], [], [], []
+    mean = torch.zeros((N, 4), dtype=torch.float64, device=ref.device)
+    for f in range(frames):
+        a.record()
+        ctx.probe_update(f)
+        if learned:
+            ctx.mlp_train(f)
+        rad = fr.render(f, cam, gbuf=g, probe_update=False)
+        b.record()
+        torch.cuda.synchronize()
+        if f >= frames - measure:
+            m = ddgi.image_metrics(rad, ref).cpu().numpy()
+            mses.append(float(m[0]))
+            mapes.append(float(m[1]))
+            ms.append(a.elapsed_time(b))
+            mean += rad.double()
+            if learned:
+                served.append(ctx.mlp_status()["use_mlp"])
+    mm = ddgi.image_metrics((mean / measure).float().contiguous(), ref).cpu().numpy()
+    r = {"ms": round(statistics.median(ms), 4), "mse": round(float(np.mean(mses)), 5),
+         "mape": round(float(np.mean(mapes)), 5), "mse_of_mean": round(float(mm[0]), 5),
+         "mape_of_mean": round(float(mm[1]), 5)}
+    if learned:
+        r["network_served_frac"] = round(float(np.mean(served)), 3)
+    if ctx.get_status() != ddgi.OK:
+        r["device_status"] = int(ctx.get_status())
+    return r
+
+
+def equal_time_mse(dev, frames=256, measure=32, ref_spp=4096):
+    """MSE and MAPE at equal GPU time per 1080p frame: the learned form
+    (65,536 self-training samples per frame, network judged against the
+    probes) against the probe form on the 24-triangle box at 1920x1080,
+    static view, both against the path-traced fp64 reference.  The probe
+    form is swept over candidate counts and spatial passes; its error at
+    equal time is the best one among the settings whose frame time is
+    within 5% above the learned form's (or below it).  Errors are averaged
+    over the last `measure` of `frames` frames, after the probe hysteresis
+    and the network have settled; the MSE of the mean of those frames
+    isolates the bias."""
+    import dataclasses
+
+    import torch
+
+    import scenegen
+    from paper_2108_05263_gb300 import ddgi
+
+    W, H = 1920, 1080
+    base = scenegen.tiny_room(width=W, height=H, frames=1)
+    cam = base.cameras[0]
+    ctx0 = ddgi.Context.from_scene(base)
+    acc = torch.zeros((W * H, 4), dtype=torch.float64, device=dev)
+    ref = torch.empty((W * H, 4), dtype=torch.float32, device=dev)
+    t0 = time.time()
+    for k in range(0, ref_spp, 64):
+        ctx0.reference_accumulate(cam, k, 64, acc, ref)
+    torch.cuda.synchronize()
+    ref_s = time.time() - t0
+    g = ddgi.GBuffer(W, H, dev)
+    ctx0.gbuffer(cam, None, g)
+    s0 = base.settings
+    learned = _form_run(ddgi, torch, dataclasses.replace(base, settings=dataclasses.replace(
+        s0, learned_target=1, train_samples=65536)), cam, g, ref, frames, measure, True)
+    sweep = []
+    for nl, sp in PROBE_SWEEP:
+        st = dataclasses.replace(s0, num_light_candidates=nl, spatial_passes=sp)
+        r = _form_run(ddgi, torch, dataclasses.replace(base, settings=st), cam, g, ref, frames, measure,
+                      False)
+        r.update({"candidates": nl + s0.num_bsdf_candidates, "spatial_passes": sp})
+        sweep.append(r)
+    within = [r for r in sweep if r["ms"] <= 1.05 * learned["ms"]]
+    best = min(within, key=lambda r: r["mse"]) if within else None
+    return {"scene": "24-triangle box (emitter Le 10), 1920x1080, static view, 4x4x4 probes x 64 rays",
+            "reference": f"path-traced, {ref_spp} spp, fp64 accumulation ({ref_s:.1f} s)",
+            "frames": frames, "measured_frames": measure,
+            "learned": learned, "probe_sweep": sweep,
+            "probe_at_equal_time": best,
+            "mse_ratio_learned_over_probe": round(learned["mse"] / best["mse"], 4) if best else None,
+            "mape_ratio_learned_over_probe": round(learned["mape"] / best["mape"], 4) if best else None}
 
 
 class OracleSample:

@@ -88,6 +88,11 @@ typedef struct {
                                    * multiple of 16 and of the probe count (0 = none) */
     float train_lr;               /* Adam learning rate */
     uint32_t mlp_seed;            /* seed of the weight initialisation */
+    float train_ema;              /* the network that serves queries is an exponential
+                                   * moving average of the trained weights, blended
+                                   * once per ddgi_mlp_train call with this weight on
+                                   * the old average (the probes' hysteresis 0.97 is
+                                   * the default); 0 serves the trained weights */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */
@@ -256,15 +261,18 @@ ddgi_status ddgi_image_metrics_static(const float* img, const float* ref, uint32
 /* One self-training step: train_samples rays from the probe centres
  * (spherical Fibonacci set per probe, per-frame random rotation) hit y; a
  * cosine-distributed bounce from y hits z; target = Le(z) + rho(z) max(f(z),
- * 0).  The samples train in minibatches of 16,384, one Adam step each.
- * Samples 16 j + 15 are held out and judge the updated network against
- * the probe lookup (relative squared error); the verdict decides for the
- * following resampling / shading calls whether the network or the probes
- * serve the queries.  Requires train_samples > 0. */
+ * 0), f the served network.  The samples train in minibatches of 16,384,
+ * one Adam step each; then the served network is blended toward the trained
+ * weights (train_ema).  Samples 16 j + 15 are held out and judge the served
+ * network against the probe lookup (squared error relative to the mean of
+ * the two predictions squared plus 0.01, so that the target's noise weighs
+ * both equally); the verdict decides for the following resampling / shading
+ * calls whether the network or the probes serve the queries.  Requires
+ * train_samples > 0. */
 ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream);
 
-/* Evaluate the network: queries (device [n][8] floats: p.xyz, valid, n.xyz,
- * 0), out (device [n][4]: f.rgb, valid). */
+/* Evaluate the served network: queries (device [n][8] floats: p.xyz,
+ * valid, n.xyz, 0), out (device [n][4]: f.rgb, valid). */
 ddgi_status ddgi_mlp_infer(ddgi_ctx* ctx, const float* queries, float* out, uint32_t n, void* stream);
 
 /* Gradient of the mean relative-L2 loss over caller samples (host or device
@@ -277,8 +285,14 @@ ddgi_status ddgi_mlp_grad(ddgi_ctx* ctx, const float* samples, uint32_t n, float
 ddgi_status ddgi_mlp_step(ddgi_ctx* ctx, const float* samples, uint32_t n, void* stream);
 
 /* fp32 master parameters (host or device [DDGI_MLP_NPARAM]); set also resets
- * the Adam moments and step count.  Both synchronise the stream. */
+ * the Adam moments and step count and makes the served network equal to
+ * the given one.  Both synchronise the stream. */
 ddgi_status ddgi_mlp_params_get(ddgi_ctx* ctx, float* params, void* stream);
+
+/* fp32 parameters of the served network (the moving average of the trained
+ * weights; host or device [DDGI_MLP_NPARAM]).  Its weights serve queries
+ * rounded to fp16.  Synchronises the stream. */
+ddgi_status ddgi_mlp_params_served_get(ddgi_ctx* ctx, float* params, void* stream);
 ddgi_status ddgi_mlp_params_set(ddgi_ctx* ctx, const float* params, void* stream);
 
 /* Who serves the queries of a learned-target context: 0 = the judge of the

@@ -45,6 +45,8 @@ struct ddgi_ctx {
     float* mlp_m = nullptr;
     float* mlp_v = nullptr;
     __half* mlp_w16 = nullptr;     // fp16 weights [MLP_NW]
+    float* mlp_ema = nullptr;      // served network: moving average of the master weights
+    __half* mlp_w16s = nullptr;    // its fp16 weights
     MLPState* mlp_state = nullptr;
     float4* train_smp = nullptr;   // [train_samples][3]
     float4* train_sf = nullptr;    // [train_per]
@@ -234,6 +236,7 @@ ddgi_status check_config(const ddgi_config* c, std::string* why) {
     }
     if (c->learned_target && c->train_samples == 0) { *why = "learned target needs train_samples"; return DDGI_ERR_INVALID_ARG; }
     if (c->train_samples > 0 && !(c->train_lr > 0.f && c->train_lr < 1.f)) { *why = "train_lr must be in (0, 1)"; return DDGI_ERR_INVALID_ARG; }
+    if (!(c->train_ema >= 0.f && c->train_ema < 1.f)) { *why = "train_ema must be in [0, 1)"; return DDGI_ERR_INVALID_ARG; }
     return DDGI_OK;
 }
 
@@ -292,10 +295,12 @@ cudaError_t grow(ddgi_ctx* c, T** buf, size_t* cap, size_t n, cudaStream_t st) {
     return e;
 }
 
-MLPView mlp_view(ddgi_ctx* c) {
+// served: the moving-average network that answers queries; else the
+// network being trained
+MLPView mlp_view(ddgi_ctx* c, bool served = true) {
     MLPView m;
-    m.w16 = c->mlp_w16;
-    m.params = c->mlp_params;
+    m.w16 = served ? c->mlp_w16s : c->mlp_w16;
+    m.params = served ? c->mlp_ema : c->mlp_params;
     for (int a = 0; a < 3; ++a) m.lo[a] = c->mlp_lo[a];
     m.scale = c->mlp_scale;
     return m;
@@ -321,6 +326,8 @@ cudaError_t mlp_upload(ddgi_ctx* c, const float* host_params) {
     for (int i = 0; i < MLP_NW; ++i) h[i] = __float2half_rn(host_params[i]);
     cudaError_t e = cudaMemcpy(c->mlp_params, host_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault);
     if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16, h.data(), MLP_NW * sizeof(__half), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_ema, host_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16s, h.data(), MLP_NW * sizeof(__half), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->mlp_m, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_v, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, MLP_NPARAM * sizeof(float));
@@ -476,6 +483,8 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(mlp_v, MLP_NPARAM)
     ALLOC(tmp_grad, MLP_NPARAM)
     ALLOC(mlp_w16, MLP_NW)
+    ALLOC(mlp_ema, MLP_NPARAM)
+    ALLOC(mlp_w16s, MLP_NW)
     ALLOC(mlp_state, 1)
     ALLOC(train_smp, 3ull * cfg->train_samples)
     ALLOC(train_sf, cfg->train_samples ? cfg->train_samples / P : 0)
@@ -762,9 +771,10 @@ ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     tp.samples = ctx->cfg.train_samples;
     tp.seed = ctx->cfg.seed;
     tp.frame = frame;
-    CK(launch_mlp_train_frame(scene_view(ctx), volume_view(ctx), mlp_view(ctx), tp, ctx->train_smp, ctx->hits,
-                              ctx->counter, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad, ctx->mlp_m,
-                              ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr, ctx->mlp_step + 1, ctx->serve,
+    CK(launch_mlp_train_frame(scene_view(ctx), volume_view(ctx), mlp_view(ctx, false), mlp_view(ctx, true), tp,
+                              ctx->train_smp, ctx->hits, ctx->counter, ctx->mlp_state, ctx->mlp_params,
+                              ctx->mlp_grad, ctx->mlp_m, ctx->mlp_v, ctx->mlp_w16, ctx->mlp_ema, ctx->mlp_w16s,
+                              ctx->cfg.train_ema, ctx->cfg.train_lr, ctx->mlp_step + 1, ctx->serve,
                               (cudaStream_t)stream));
     ctx->mlp_step += (ctx->cfg.train_samples + MLP_BATCH - 1) / MLP_BATCH;
     return DDGI_OK;
@@ -790,7 +800,7 @@ ddgi_status ddgi_mlp_grad(ddgi_ctx* ctx, const float* samples, uint32_t n, float
     cudaStream_t st = (cudaStream_t)stream;
     ddgi_status s = stage_samples(ctx, samples, n, st);
     if (s != DDGI_OK) return s;
-    CK(launch_mlp_grad_only(mlp_view(ctx), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_grad, ctx->tmp_grad, st));
+    CK(launch_mlp_grad_only(mlp_view(ctx, false), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_grad, ctx->tmp_grad, st));
     CK(cudaMemcpyAsync(grad, ctx->tmp_grad, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     return DDGI_OK;
@@ -801,7 +811,7 @@ ddgi_status ddgi_mlp_step(ddgi_ctx* ctx, const float* samples, uint32_t n, void*
     cudaStream_t st = (cudaStream_t)stream;
     ddgi_status s = stage_samples(ctx, samples, n, st);
     if (s != DDGI_OK) return s;
-    CK(launch_mlp_step(mlp_view(ctx), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad,
+    CK(launch_mlp_step(mlp_view(ctx, false), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_params, ctx->mlp_grad,
                        ctx->mlp_m, ctx->mlp_v, ctx->mlp_w16, ctx->cfg.train_lr > 0.f ? ctx->cfg.train_lr : 1e-3f,
                        ++ctx->mlp_step, st));
     return DDGI_OK;
@@ -811,6 +821,14 @@ ddgi_status ddgi_mlp_params_get(ddgi_ctx* ctx, float* params, void* stream) {
     if (!ctx || !params) return DDGI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(params, ctx->mlp_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_mlp_params_served_get(ddgi_ctx* ctx, float* params, void* stream) {
+    if (!ctx || !params) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(params, ctx->mlp_ema, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     return DDGI_OK;
 }

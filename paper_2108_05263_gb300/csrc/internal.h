@@ -84,10 +84,13 @@ struct TrainParams {
 };
 cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, float* out, uint32_t n,
                                     cudaStream_t st);
-cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const TrainParams& tp,
-                                   float4* smp, float2* hits, uint32_t* counter, MLPState* state, float* params,
-                                   float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
-                                   int serve, cudaStream_t st);
+// m: the trained network (master weights), ms: the served network (moving
+// average, blended with weight ema_a on the old average after the steps)
+cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const MLPView& ms,
+                                   const TrainParams& tp, float4* smp, float2* hits, uint32_t* counter,
+                                   MLPState* state, float* params, float* grad, float* mom, float* vel, __half* w16,
+                                   float* ema, __half* w16s, float ema_a, float lr, uint32_t step, int serve,
+                                   cudaStream_t st);
 cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st);
 cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                                  float* out, cudaStream_t st);

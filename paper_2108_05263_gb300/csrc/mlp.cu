@@ -415,7 +415,11 @@ struct TargetQuery {
 };
 
 // held-out samples (index 16 j + 15): relative squared error of the network
-// and of the probe lookup against the one-bounce target
+// and of the probe lookup against the one-bounce target.  The denominator,
+// the mean of the two predictions squared plus 0.01, is common to both and
+// independent of the target: the target's noise then adds the same amount to
+// both sums, so their difference weighs only the two predictions' biases (a
+// target-based denominator would reward predictions biased toward zero).
 struct JudgeQuery {
     VolumeView v;
     TrainParams tp;
@@ -441,7 +445,7 @@ struct JudgeQuery {
         const float tv[3] = {tg.x, tg.y, tg.z}, mv[3] = {fm.x, fm.y, fm.z}, pv[3] = {E.x, E.y, E.z};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float den = tv[c] * tv[c] + 0.01f;
+            const float den = 0.5f * (mv[c] * mv[c] + pv[c] * pv[c]) + 0.01f;
             em += (mv[c] - tv[c]) * (mv[c] - tv[c]) / den;
             ep += (pv[c] - tv[c]) * (pv[c] - tv[c]) / den;
         }
@@ -468,6 +472,17 @@ __global__ void k_mlp_judge(MLPState* st, int serve) {
         st->use_mlp = 0u;
     else
         st->use_mlp = (st->judge_n > 0 && st->judge_mlp <= st->judge_probe) ? 1u : 0u;
+}
+
+// served network: ema <- a ema + (1 - a) params, fp16 copy of its weights
+__global__ void k_mlp_ema(const float* __restrict__ params, float* __restrict__ ema, __half* __restrict__ w16s,
+                          float a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < MLP_NPARAM) {
+        const float e = a * ema[i] + (1.f - a) * params[i];
+        ema[i] = e;
+        if (i < MLP_NW) w16s[i] = __float2half_rn(e);
+    }
 }
 
 // gradient of the mean loss (unscaled) into out
@@ -515,17 +530,18 @@ cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const TrainParams& tp,
-                                   float4* smp, float2* hits, uint32_t* counter, MLPState* state, float* params,
-                                   float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
-                                   int serve, cudaStream_t st) {
+cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const MLPView& ms,
+                                   const TrainParams& tp, float4* smp, float2* hits, uint32_t* counter,
+                                   MLPState* state, float* params, float* grad, float* mom, float* vel, __half* w16,
+                                   float* ema, __half* w16s, float ema_a, float lr, uint32_t step, int serve,
+                                   cudaStream_t st) {
     k_mlp_begin<<<1, 1, 0, st>>>(state);
     k_train_primary<<<(tp.samples + 127) / 128, 128, 0, st>>>(s, v, tp, smp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_trace<BounceGen, false>(s, BounceGen{smp, tp}, tp.samples, counter, hits, st);
     if (e != cudaSuccess) return e;
-    e = launch_mlp_infer(m, TargetQuery{s, tp, smp, hits}, tp.samples, st);
+    e = launch_mlp_infer(ms, TargetQuery{s, tp, smp, hits}, tp.samples, st);
     if (e != cudaSuccess) return e;
     // minibatches of MLP_BATCH samples, one Adam step each
     for (uint32_t b0 = 0, k = 0; b0 < tp.samples; b0 += MLP_BATCH, ++k) {
@@ -536,8 +552,11 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
         e = launch_mlp_adam(params, grad, mom, vel, w16, state, lr, step + k, st);
         if (e != cudaSuccess) return e;
     }
-    // the judge compares the updated network with the probes on held-out samples
-    e = launch_mlp_infer(m, JudgeQuery{v, tp, smp, state}, tp.samples / 16, st);
+    k_mlp_ema<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, ema, w16s, ema_a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the judge compares the served network with the probes on held-out samples
+    e = launch_mlp_infer(ms, JudgeQuery{v, tp, smp, state}, tp.samples / 16, st);
     if (e != cudaSuccess) return e;
     k_mlp_judge<<<1, 1, 0, st>>>(state, serve);
     return cudaGetLastError();

@@ -43,7 +43,7 @@ class Config(C.Structure):
                 ("spatial_radius", C.c_uint32), ("normal_reject_cos", C.c_float),
                 ("depth_reject_frac", C.c_float), ("seed", C.c_uint32),
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
-                ("mlp_seed", C.c_uint32)]
+                ("mlp_seed", C.c_uint32), ("train_ema", C.c_float)]
 
 
 class Camera(C.Structure):
@@ -81,7 +81,8 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
-           "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
+           "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_served_get",
+           "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
            "ddgi_mlp_status", "ddgi_get_status", "ddgi_last_error"]
 
 MLP_NPARAM = 18184
@@ -126,6 +127,7 @@ def load(path: Optional[str] = None):
     L.ddgi_mlp_grad.argtypes = [vp, vp, C.c_uint32, vp, vp]
     L.ddgi_mlp_step.argtypes = [vp, vp, C.c_uint32, vp]
     L.ddgi_mlp_params_get.argtypes = [vp, vp, vp]
+    L.ddgi_mlp_params_served_get.argtypes = [vp, vp, vp]
     L.ddgi_mlp_params_set.argtypes = [vp, vp, vp]
     L.ddgi_mlp_samples_get.argtypes = [vp, vp, vp]
     L.ddgi_mlp_serve.argtypes = [vp, C.c_int32, vp]
@@ -243,6 +245,7 @@ def config_from(grid, settings) -> Config:
     c.train_samples = int(getattr(settings, "train_samples", 0))
     c.train_lr = float(getattr(settings, "train_lr", 1e-3))
     c.mlp_seed = int(getattr(settings, "mlp_seed", 1))
+    c.train_ema = float(getattr(settings, "train_ema", 0.97))
     return c
 
 
@@ -392,6 +395,13 @@ class Context:
     def mlp_params(self, stream=None) -> np.ndarray:
         p = np.zeros(MLP_NPARAM, np.float32)
         self._check("ddgi_mlp_params_get", self.L.ddgi_mlp_params_get(self.h, p.ctypes.data, _stream(stream)))
+        return p
+
+    def mlp_params_served(self, stream=None) -> np.ndarray:
+        """The served network: moving average of the trained weights."""
+        p = np.zeros(MLP_NPARAM, np.float32)
+        self._check("ddgi_mlp_params_served_get",
+                    self.L.ddgi_mlp_params_served_get(self.h, p.ctypes.data, _stream(stream)))
         return p
 
     def mlp_set_params(self, params, stream=None):

@@ -96,6 +96,7 @@ class Settings:
     train_samples: int = 0       # self-training samples per frame
     train_lr: float = 1e-3
     mlp_seed: int = 1
+    train_ema: float = 0.97      # served network: moving average of the trained weights
 
 
 @dataclasses.dataclass
