@@ -64,7 +64,7 @@ class _Settings(C.Structure):
                 ("depth_sharpness", C.c_double), ("n_light", C.c_int32), ("n_bsdf", C.c_int32),
                 ("temporal_mcap", C.c_double), ("spatial_neighbours", C.c_int32),
                 ("spatial_radius", C.c_int32), ("normal_reject_cos", C.c_double),
-                ("depth_reject_frac", C.c_double), ("seed", C.c_uint32)]
+                ("depth_reject_frac", C.c_double), ("seed", C.c_uint32), ("relocate", C.c_int32)]
 
 
 class _Volume(C.Structure):
@@ -173,6 +173,7 @@ def settings_of(st) -> _Settings:
     o.normal_reject_cos = st.normal_reject_cos
     o.depth_reject_frac = st.depth_reject_frac
     o.seed = st.seed
+    o.relocate = int(getattr(st, "probe_relocation", 0))
     return o
 
 
@@ -433,6 +434,15 @@ def probe_blend(vol: Volume, rays, frame: int, settings, probes=None):
     rays = np.ascontiguousarray(rays, np.float64)
     lib().or_probe_blend(C.byref(vol.v), C.byref(settings), C.c_uint32(frame), pp,
                          C.c_int32(n), _p(rays))
+
+
+def probe_relocate(vol: Volume, rays, frame: int, settings, probes=None):
+    """Probe relocation from one frame's rays (offsets updated in place)."""
+    pr, pp = _pixarg(probes)
+    n = vol.P if probes is None else len(pr)
+    rays = np.ascontiguousarray(rays, np.float64)
+    lib().or_probe_relocate(C.byref(vol.v), C.byref(settings), C.c_uint32(frame), pp,
+                            C.c_int32(n), _p(rays))
 
 
 def probe_update(scene: Scene, vol: Volume, frame: int, settings=None):

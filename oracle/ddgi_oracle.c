@@ -493,13 +493,69 @@ int or_probe_blend(or_volume* v, const or_settings* st, uint32_t frame,
     return 0;
 }
 
-/* one full update: trace every probe against the previous maps, then blend */
+/* Probe relocation (the paper cites it for its probe volume, Sec. 2; the
+ * method is that of Majercik et al. 2021): from this frame's rays of a probe,
+ * with delta = 0.1 * min spacing the smallest distance a probe keeps from a
+ * front face:
+ *   - more than a quarter of the rays hit back faces (the probe sits inside
+ *     geometry): move along the direction of the closest back-face hit by its
+ *     distance + delta / 2, through that face;
+ *   - else if the closest front-face hit is nearer than delta: move away from
+ *     it by the shortfall;
+ * then clamp every axis of the offset to +-0.45 of the grid spacing, so a
+ * probe never leaves its cell's inner region.  Misses count as neither. */
+int or_probe_relocate(or_volume* v, const or_settings* st, uint32_t frame,
+                      const int32_t* probes, int32_t nprobes, const double* rays) {
+    int32_t R = st->rays_per_probe;
+    double Rf[9];
+    or_probe_rotation(st->seed, frame, Rf);
+    double delta = v->spacing[0];
+    for (int a = 1; a < 3; ++a)
+        if (v->spacing[a] < delta) delta = v->spacing[a];
+    delta *= 0.1;
+    for (int32_t k = 0; k < nprobes; ++k) {
+        int32_t p = probes ? probes[k] : k;
+        const double* ray = rays + (size_t)k * R * 4;
+        int32_t nback = 0, rb = -1, rf = -1;
+        double tb = MISS_T, tf = MISS_T;
+        for (int32_t r = 0; r < R; ++r) {
+            double t = ray[4 * r + 3];
+            if (t >= MISS_T) continue;
+            if (t < 0.0) {
+                ++nback;
+                if (-t < tb) { tb = -t; rb = r; }
+            } else if (t < tf) {
+                tf = t;
+                rf = r;
+            }
+        }
+        double* off = v->offset + 3 * (size_t)p;
+        double d[3];
+        if (4 * nback > R && rb >= 0) {
+            or_probe_ray_dir(Rf, rb, R, d);
+            for (int a = 0; a < 3; ++a) off[a] += d[a] * (tb + 0.5 * delta);
+        } else if (rf >= 0 && tf < delta) {
+            or_probe_ray_dir(Rf, rf, R, d);
+            for (int a = 0; a < 3; ++a) off[a] -= d[a] * (delta - tf);
+        }
+        for (int a = 0; a < 3; ++a) {
+            double lim = 0.45 * v->spacing[a];
+            if (off[a] > lim) off[a] = lim;
+            if (off[a] < -lim) off[a] = -lim;
+        }
+    }
+    return 0;
+}
+
+/* one full update: trace every probe against the previous maps, blend, and
+ * (when enabled) relocate */
 int or_probe_update(const or_scene* s, or_volume* v, const or_settings* st, uint32_t frame) {
     int32_t P = v->counts[0] * v->counts[1] * v->counts[2];
     double* rays = (double*)malloc(sizeof(double) * 4 * (size_t)P * st->rays_per_probe);
     if (!rays) return -1;
     or_probe_trace(s, v, st, frame, NULL, P, rays);
     int rc = or_probe_blend(v, st, frame, NULL, P, rays);
+    if (rc == 0 && st->relocate) rc = or_probe_relocate(v, st, frame, NULL, P, rays);
     v->updates++;
     free(rays);
     return rc;

@@ -43,6 +43,7 @@ typedef struct {
     int32_t spatial_neighbours, spatial_radius;
     double normal_reject_cos, depth_reject_frac;
     uint32_t seed;
+    int32_t relocate;        /* probe relocation after each blend (1) or not */
 } or_settings;
 
 typedef struct {
@@ -129,6 +130,8 @@ int or_probe_trace(const or_scene* s, const or_volume* v, const or_settings* st,
                    uint32_t frame, const int32_t* probes, int32_t nprobes, double* rays);
 int or_probe_blend(or_volume* v, const or_settings* st, uint32_t frame,
                    const int32_t* probes, int32_t nprobes, const double* rays);
+int or_probe_relocate(or_volume* v, const or_settings* st, uint32_t frame,
+                      const int32_t* probes, int32_t nprobes, const double* rays);
 int or_probe_update(const or_scene* s, or_volume* v, const or_settings* st, uint32_t frame);
 
 int or_gbuffer(const or_scene* s, const or_camera* cam, const or_camera* prev_cam,

@@ -92,6 +92,7 @@ class Settings:
     normal_reject_cos: float = 0.9
     depth_reject_frac: float = 0.1
     seed: int = 1
+    probe_relocation: int = 0    # 1: relocate probes after each update
     learned_target: int = 0      # 1: the network serves p-hat / termination queries
     train_samples: int = 0       # self-training samples per frame
     train_lr: float = 1e-3

@@ -649,3 +649,116 @@ def test_reference_direct_light_form_factor(oracle_lib):
         px = g.pos[q]
         F = _rect_form_factor(-1 - px[0], -px[0], -1 - px[2], 1 - px[2], 2.0)
         assert est[k, 0] == pytest.approx(0.5 * 10.0 * F, rel=0.06), (q, est[k], F)
+
+
+# ---------------------------------------------------------------------------
+# probe relocation (cited probe volume, Sec. 2; Majercik et al. 2021)
+# ---------------------------------------------------------------------------
+
+def _cube(c, h, outward=True):
+    """12 triangles of an axis-aligned cube of half-size h around c, with
+    normals pointing out of (or into) the cube."""
+    c = np.asarray(c, float)
+    tris = []
+    for ax in range(3):
+        u, v = [k for k in range(3) if k != ax]
+        for sgn in (-1.0, 1.0):
+            qc = c.copy()
+            qc[ax] += sgn * h
+            a, b = np.zeros(3), np.zeros(3)
+            a[u], b[v] = h, h
+            facing = np.zeros(3)
+            facing[ax] = sgn if outward else -sgn
+            tris += scenegen._quad(qc, a, b, facing)
+    return np.asarray(tris)
+
+
+def _reloc_setup(tris, grid):
+    import oracle
+    base = scenegen.tiny_room()
+    T = len(tris)
+    sc = _custom_scene(base, albedo=np.full((T, 3), 0.5), emission=np.zeros((T, 3)), verts=tris, grid=grid)
+    st = dataclasses.replace(base.settings, rays_per_probe=256, probe_relocation=1)
+    S = oracle.Scene(dataclasses.replace(sc, settings=st))
+    return oracle, S, st, oracle.settings_of(st)
+
+
+def test_relocation_moves_a_probe_out_of_a_box_it_sits_in(oracle_lib):
+    """A probe 0.03 m off the centre of a closed, outward-facing cube of
+    half-size 0.1 sees only back faces: it moves along its ray closest to the
+    near (-x) face, by that ray's exit distance + delta/2, and lands outside
+    the cube within delta/2 of the face plane.  The exit distances are
+    recomputed here from the slab formula, not with the oracle's intersector."""
+    grid = scenegen.ProbeGrid(np.zeros(3, np.float32), np.full(3, 1.0, np.float32), np.array([1, 1, 1], np.int32))
+    c, h = np.array([0.03, 0.0, 0.0]), 0.1
+    oracle, S, st, cs = _reloc_setup(_cube(c, h), grid)
+    vol = oracle.Volume(grid)
+    rays = oracle.probe_trace(S, vol, 3, settings=cs)
+    assert np.all(rays[0, :, 3] < 0)                       # every hit is a back face
+    dirs = oracle.probe_ray_dirs(st.seed, 3, st.rays_per_probe)
+    hi = (c + h).astype(np.float32).astype(float)         # the scene stores float32 vertices
+    lo = (c - h).astype(np.float32).astype(float)
+    with np.errstate(divide="ignore"):
+        slab = np.where(dirs > 0, hi / dirs, np.where(dirs < 0, lo / dirs, np.inf))
+    t_exit = slab.min(axis=1)
+    np.testing.assert_allclose(-rays[0, :, 3], t_exit, rtol=1e-9)
+    rb = int(np.argmin(t_exit))
+    delta = 0.1
+    oracle.probe_relocate(vol, rays, 3, cs)
+    want = dirs[rb] * (t_exit[rb] + 0.5 * delta)
+    np.testing.assert_allclose(vol.offset[0], want, rtol=1e-12, atol=1e-15)
+    P = vol.offset[0]
+    assert P[0] < lo[0] and P[0] > lo[0] - 0.5 * delta - 1e-12
+    assert np.all(np.abs(P[1:] - c[1:]) < h)
+
+
+def test_relocation_pushes_a_probe_off_a_near_front_face(oracle_lib):
+    """0.3 delta above an upward-facing floor (no back faces): the probe moves
+    against its closest front hit by delta - t_f; a probe 0.2 m above the
+    floor (> delta) and one in empty space stay put."""
+    grid = scenegen.ProbeGrid(np.zeros(3, np.float32), np.full(3, 1.0, np.float32), np.array([1, 1, 1], np.int32))
+    delta = 0.1
+    for height, moves in ((0.3 * delta, True), (0.2, False)):
+        floor = np.asarray(scenegen._quad([0, -height, 0], [5, 0, 0], [0, 0, 5], [0, 1, 0]))
+        oracle, S, st, cs = _reloc_setup(floor, grid)
+        vol = oracle.Volume(grid)
+        rays = oracle.probe_trace(S, vol, 0, settings=cs)
+        dirs = oracle.probe_ray_dirs(st.seed, 0, st.rays_per_probe)
+        down = dirs[:, 1] < 0
+        hf = float(np.float32(height))
+        t_plane = np.where(down, hf / np.where(down, -dirs[:, 1], 1.0), np.inf)
+        steep = dirs[:, 1] < -0.1                          # hit points well inside the 10 m floor
+        np.testing.assert_allclose(rays[0, steep, 3], t_plane[steep], rtol=1e-9)
+        assert np.all((rays[0, :, 3] > 0) | (rays[0, :, 3] >= 1e30))
+        oracle.probe_relocate(vol, rays, 0, cs)
+        if moves:
+            rf = int(np.argmin(t_plane))
+            np.testing.assert_allclose(vol.offset[0], -dirs[rf] * (delta - t_plane[rf]), rtol=1e-12)
+            assert vol.offset[0][1] > 0
+        else:
+            np.testing.assert_array_equal(vol.offset[0], 0.0)
+
+
+def test_relocation_threshold_and_clamp(oracle_lib):
+    """Synthetic ray records: 16 of 64 back faces (exactly a quarter) do not
+    move a probe, 17 do; a far back face moves it only to the 0.45 x spacing
+    clamp on each axis."""
+    import oracle
+    grid = scenegen.ProbeGrid(np.zeros(3, np.float32), np.array([1.0, 0.5, 2.0], np.float32),
+                              np.array([1, 1, 1], np.int32))
+    st = dataclasses.replace(scenegen.tiny_room().settings, rays_per_probe=64, probe_relocation=1)
+    cs = oracle.settings_of(st)
+    dirs = oracle.probe_ray_dirs(st.seed, 2, 64)
+    for nback, moved in ((16, False), (17, True)):
+        vol = oracle.Volume(grid)
+        rays = np.zeros((1, 64, 4))
+        rays[0, :, 3] = 1e30
+        rays[0, :nback, 3] = -np.linspace(5.0, 6.0, nback)   # closest back face: ray 0 at 5 m
+        oracle.probe_relocate(vol, rays, 2, cs)
+        if moved:
+            lim = 0.45 * grid.spacing.astype(float)
+            want = np.clip(dirs[0] * (5.0 + 0.5 * 0.05), -lim, lim)
+            np.testing.assert_allclose(vol.offset[0], want, rtol=1e-12)
+            np.testing.assert_array_equal(np.abs(vol.offset[0]), lim)
+        else:
+            np.testing.assert_array_equal(vol.offset[0], 0.0)
