@@ -93,6 +93,7 @@ typedef struct {
                                    * once per ddgi_mlp_train call with this weight on
                                    * the old average (the probes' hysteresis 0.97 is
                                    * the default); 0 serves the trained weights */
+    uint32_t probe_relocation;    /* 1: ddgi_probe_update ends with ddgi_probe_relocate */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */
@@ -152,6 +153,16 @@ ddgi_status ddgi_get_info(ddgi_ctx* ctx, ddgi_info* out);
 ddgi_status ddgi_probe_update(ddgi_ctx* ctx, uint32_t frame, void* stream);
 ddgi_status ddgi_probe_trace(ddgi_ctx* ctx, uint32_t frame, void* stream);
 ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream);
+
+/* Probe relocation from the rays of the last ddgi_probe_trace of `frame`
+ * (the paper's probe volume, Sec. 2, cites it; the rule is that of Majercik
+ * et al. 2021).  delta = 0.1 x the smallest grid spacing.  A probe with more
+ * than a quarter of its rays on back faces moves along its closest back-face
+ * ray by that distance + delta / 2 (out of the geometry it sits in); else a
+ * front face nearer than delta pushes it back along that ray by the
+ * shortfall.  Each offset axis is clamped to +-0.45 x its spacing.  Offsets
+ * persist and move the probe for every later trace and query. */
+ddgi_status ddgi_probe_relocate(ddgi_ctx* ctx, uint32_t frame, void* stream);
 
 /* Probe state transfer (host or device pointers; synchronises the stream):
  * irr [P][irr_tile^2][4] floats (rgb, 0), depth [P][depth_tile^2][2],

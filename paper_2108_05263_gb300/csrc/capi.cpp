@@ -597,10 +597,20 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     return DDGI_OK;
 }
 
+ddgi_status ddgi_probe_relocate(ddgi_ctx* ctx, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    ProbeParams p;
+    probe_params(ctx, frame, &p);
+    CK(launch_probe_relocate(volume_view(ctx), p, ctx->rays, ctx->offset, (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
 ddgi_status ddgi_probe_update(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     ddgi_status s = ddgi_probe_trace(ctx, frame, stream);
     if (s != DDGI_OK) return s;
-    return ddgi_probe_blend(ctx, frame, stream);
+    s = ddgi_probe_blend(ctx, frame, stream);
+    if (s != DDGI_OK || !ctx->cfg.probe_relocation) return s;
+    return ddgi_probe_relocate(ctx, frame, stream);
 }
 
 ddgi_status ddgi_probe_state_get(ddgi_ctx* ctx, float* irr, float* depth, float* offsets,

@@ -55,6 +55,8 @@ struct ProbeParams {
 // kernel launchers (return the launch error)
 cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
                                float4* rays, float2* hits, uint32_t* counter, cudaStream_t st);
+cudaError_t launch_probe_relocate(const VolumeView& v, const ProbeParams& p, const float4* rays, float4* offset,
+                                  cudaStream_t st);
 size_t probe_blend_smem(const VolumeView& v, uint32_t rays);
 cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays,
                                cudaStream_t st);

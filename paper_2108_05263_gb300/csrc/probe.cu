@@ -170,7 +170,81 @@ __global__ void __launch_bounds__(256) k_probe_blend(VolumeView v, ProbeParams p
     }
 }
 
+// lexicographic minimum of (t, ray index) across the warp
+__device__ __forceinline__ void warp_min_idx(float& t, int& r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float t2 = __shfl_xor_sync(0xffffffffu, t, o);
+        int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+        if (t2 < t || (t2 == t && r2 < r)) {
+            t = t2;
+            r = r2;
+        }
+    }
+}
+
+// Probe relocation (cited probe volume; Majercik et al. 2021), one warp per
+// probe over this frame's rays: more than a quarter back-face hits moves the
+// probe through the closest back face by its distance + delta / 2; else a
+// front face nearer than delta pushes it away by the shortfall; every axis of
+// the offset is then clamped to +-0.45 spacing.
+__global__ void __launch_bounds__(128) k_probe_relocate(ProbeParams pp, const float4* __restrict__ rays,
+                                                        float4* __restrict__ offset, float3 spacing, float delta,
+                                                        int P) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (p >= P) return;
+    const int R = (int)pp.rays;
+    int nback = 0, rb = INT_MAX, rf = INT_MAX;
+    float tb = DDGI_MISS_T, tf = DDGI_MISS_T;
+    for (int r = lane; r < R; r += 32) {
+        const float t = __ldg(rays + (size_t)p * R + r).w;
+        if (t >= DDGI_MISS_T) continue;
+        if (t < 0.f) {
+            ++nback;
+            if (-t < tb) {
+                tb = -t;
+                rb = r;
+            }
+        } else if (t < tf) {
+            tf = t;
+            rf = r;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nback += __shfl_xor_sync(0xffffffffu, nback, o);
+    warp_min_idx(tb, rb);
+    warp_min_idx(tf, rf);
+    if (lane != 0) return;
+    float4 off = offset[p];
+    if (4 * nback > R && rb != INT_MAX) {
+        const f3 d = rotate(pp, __ldg(pp.sf + rb));
+        const float s = tb + 0.5f * delta;
+        off.x += d.x * s;
+        off.y += d.y * s;
+        off.z += d.z * s;
+    } else if (rf != INT_MAX && tf < delta) {
+        const f3 d = rotate(pp, __ldg(pp.sf + rf));
+        const float s = delta - tf;
+        off.x -= d.x * s;
+        off.y -= d.y * s;
+        off.z -= d.z * s;
+    }
+    off.x = fminf(fmaxf(off.x, -0.45f * spacing.x), 0.45f * spacing.x);
+    off.y = fminf(fmaxf(off.y, -0.45f * spacing.y), 0.45f * spacing.y);
+    off.z = fminf(fmaxf(off.z, -0.45f * spacing.z), 0.45f * spacing.z);
+    offset[p] = off;
+}
+
 }  // namespace
+
+cudaError_t launch_probe_relocate(const VolumeView& v, const ProbeParams& p, const float4* rays, float4* offset,
+                                  cudaStream_t st) {
+    int P = v.counts.x * v.counts.y * v.counts.z;
+    if (P == 0) return cudaSuccess;
+    k_probe_relocate<<<(P + 3) / 4, 128, 0, st>>>(p, rays, offset, v.spacing, 0.1f * v.min_spacing, P);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
                                float4* rays, float2* hits, uint32_t* counter, cudaStream_t st) {

@@ -43,7 +43,7 @@ class Config(C.Structure):
                 ("spatial_radius", C.c_uint32), ("normal_reject_cos", C.c_float),
                 ("depth_reject_frac", C.c_float), ("seed", C.c_uint32),
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
-                ("mlp_seed", C.c_uint32), ("train_ema", C.c_float)]
+                ("mlp_seed", C.c_uint32), ("train_ema", C.c_float), ("probe_relocation", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -77,7 +77,7 @@ _lib = None
 
 # entry points declared in include/ddgi.h (all return ddgi_status except the last)
 EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
-           "ddgi_probe_blend", "ddgi_probe_state_get", "ddgi_probe_state_set",
+           "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
@@ -106,7 +106,7 @@ def load(path: Optional[str] = None):
     L.ddgi_create.argtypes = [C.POINTER(Scene), C.POINTER(Config), C.POINTER(vp)]
     L.ddgi_destroy.argtypes = [vp]
     L.ddgi_get_info.argtypes = [vp, C.POINTER(Info)]
-    for fn in ("ddgi_probe_update", "ddgi_probe_trace", "ddgi_probe_blend"):
+    for fn in ("ddgi_probe_update", "ddgi_probe_trace", "ddgi_probe_blend", "ddgi_probe_relocate"):
         getattr(L, fn).argtypes = [vp, C.c_uint32, vp]
     L.ddgi_probe_state_get.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_uint32), vp]
     L.ddgi_probe_state_set.argtypes = [vp, vp, vp, vp, C.c_uint32, vp]
@@ -246,6 +246,7 @@ def config_from(grid, settings) -> Config:
     c.train_lr = float(getattr(settings, "train_lr", 1e-3))
     c.mlp_seed = int(getattr(settings, "mlp_seed", 1))
     c.train_ema = float(getattr(settings, "train_ema", 0.97))
+    c.probe_relocation = int(getattr(settings, "probe_relocation", 0))
     return c
 
 
@@ -301,6 +302,9 @@ class Context:
 
     def probe_blend(self, frame, stream=None):
         self._check("ddgi_probe_blend", self.L.ddgi_probe_blend(self.h, frame, _stream(stream)))
+
+    def probe_relocate(self, frame, stream=None):
+        self._check("ddgi_probe_relocate", self.L.ddgi_probe_relocate(self.h, frame, _stream(stream)))
 
     def probe_state_get(self, stream=None):
         i = self.info

@@ -520,3 +520,72 @@ def test_reference_matches_oracle_paths(dd, orc):
     assert _frac(_close(a[pix, :3], ref, 1e-3, 1e-4).all(1)) >= 0.97
     np.testing.assert_allclose(mean.cpu().numpy()[:, :3], a[:, :3] / 32.0, rtol=1e-6)
     assert ctx.get_status() == dd.OK
+
+
+# ---------------------------------------------------------------------------
+# probe relocation
+# ---------------------------------------------------------------------------
+
+def test_probe_relocation_parity_synthetic_rays(dd, orc):
+    """The same seeded ray records on both sides (back-face fractions around
+    the 1/4 threshold, near front faces, misses, far faces that hit the
+    clamp), two relocation steps: offsets agree to float32 rounding."""
+    import dataclasses
+    sc = scenegen.apartment(frames=1)
+    sc.settings = dataclasses.replace(sc.settings, probe_relocation=1)
+    ctx = dd.Context.from_scene(sc)
+    P, R = ctx.info.num_probes, ctx.info.rays_per_probe
+    vol = orc.Volume(sc.grid)
+    cs = orc.settings_of(sc.settings)
+    rng = np.random.default_rng(17)
+    for frame in (3, 4):
+        rays = np.zeros((P, R, 4), np.float32)
+        frac_back = rng.uniform(0.0, 0.5, P)
+        lo = np.where(rng.random(P) < 0.5, 0.01, 0.2)          # half the probes have no near face
+        t = rng.uniform(lo[:, None], 3.0, (P, R)).astype(np.float32)
+        back = rng.random((P, R)) < frac_back[:, None]
+        miss = rng.random((P, R)) < 0.2
+        t = np.where(back, -t, t)
+        t = np.where(miss & ~back, np.float32(1e30), t)
+        rays[:, :, 3] = t
+        ctx.probe_rays_set(rays)
+        ctx.probe_relocate(frame)
+        orc.probe_relocate(vol, rays.astype(np.float64), frame, cs)
+        off = ctx.probe_state_get()[2][:, :3]
+        np.testing.assert_allclose(off, vol.offset, rtol=1e-5, atol=2e-6)
+    moved = np.abs(vol.offset).max(axis=1) > 0
+    clamped = np.isclose(np.abs(vol.offset), 0.45 * sc.grid.spacing.astype(float)).any(axis=1)
+    assert 0.2 < moved.mean() < 0.95 and clamped.any()
+    assert ctx.get_status() == dd.OK
+
+
+def test_probe_relocation_chain_parity_tiny_room(dd, orc):
+    """A grid that reaches past the walls of the box: the probes outside one
+    wall see its back face in half of their directions and move inside.  Three traced updates with
+    relocation on both sides agree (offsets, irradiance)."""
+    import dataclasses
+    sc = scenegen.tiny_room()
+    grid = scenegen.ProbeGrid(np.full(3, -1.05, np.float32), np.full(3, 0.7, np.float32),
+                              np.array([4, 4, 4], np.int32))
+    sc = dataclasses.replace(sc, grid=grid, settings=dataclasses.replace(sc.settings, probe_relocation=1))
+    ctx = dd.Context.from_scene(sc)
+    S = orc.Scene(sc)
+    vol = orc.Volume(grid)
+    for f in range(3):
+        ctx.probe_update(f)
+        orc.probe_update(S, vol, f)
+    irr, _, off, _ = ctx.probe_state_get()
+    np.testing.assert_allclose(off[:, :3], vol.offset, rtol=1e-4, atol=1e-5)
+    home = grid.origin + grid.spacing * _probe_ijk(grid)
+    face = (np.abs(home) > 1.0).sum(axis=1) == 1          # half of their rays hit a wall's back
+    inside = np.all(np.abs(home + vol.offset) < 1.0, axis=1)
+    assert face.sum() == 24 and inside[face].all()
+    ok = np.abs(irr[..., :3] - vol.irr) <= 1e-3 * np.abs(vol.irr) + 1e-4
+    assert ok.mean() >= 0.999
+    assert ctx.get_status() == dd.OK
+
+
+def _probe_ijk(grid):
+    c = grid.counts
+    p = np.arange(int(np.prod(c)))
+    return np.stack([p % c[0], (p // c[0]) % c[1], p // (c[0] * c[1])], 1)
