@@ -54,8 +54,10 @@ _fp = C.POINTER(C.c_float)
 
 class _Scene(C.Structure):
     _fields_ = [("num_tris", C.c_int32), ("verts", _dp), ("albedo", _dp), ("emission", _dp),
+                ("tri_instance", _ip), ("num_instances", C.c_int32), ("object_verts", _dp),
                 ("normal", _dp), ("area", _dp), ("num_emitters", C.c_int32),
-                ("emitter_tri", _ip), ("emitter_cdf", _fp), ("area_total", C.c_double)]
+                ("emitter_tri", _ip), ("emitter_of", _ip), ("emitter_cdf", _fp), ("area_total", C.c_double),
+                ("inst_cur", _dp), ("inst_prev", _dp)]
 
 
 class _Settings(C.Structure):
@@ -138,9 +140,27 @@ class Scene:
         self.s = _Scene()
         self.s.num_tris = sc.num_tris
         self.s.verts, self.s.albedo, self.s.emission = _p(self.verts), _p(self.albedo), _p(self.emission)
+        inst = getattr(sc, "tri_instance", None)
+        if inst is not None:
+            self.tri_instance = np.ascontiguousarray(inst, np.int32)
+            self.object_verts = self.verts.copy()
+            self.s.tri_instance = _p(self.tri_instance, _ip)
+            self.s.num_instances = int(self.tri_instance.max(initial=-1)) + 1
+            self.s.object_verts = _p(self.object_verts)
         if lib().or_scene_init(C.byref(self.s)) != 0:
             raise MemoryError("or_scene_init")
         self.settings = settings_of(sc.settings)
+
+    def update(self, xf=None, emitter_radiance=None):
+        """Move the instances to the poses xf ([I][12] row-major 3x4, relative
+        to the identity pose) and / or set the emitters' radiance ([E][3])."""
+        a = None if xf is None else np.ascontiguousarray(xf, np.float64).reshape(-1, 12)
+        b = None if emitter_radiance is None else np.ascontiguousarray(emitter_radiance, np.float64)
+        n = 0 if a is None else a.shape[0]
+        rc = lib().or_scene_update(C.byref(self.s), None if a is None else _p(a), C.c_int32(n),
+                                   None if b is None else _p(b))
+        if rc != 0:
+            raise ValueError("or_scene_update: transform count differs from the instance count")
 
     def __del__(self):
         try:
@@ -155,6 +175,9 @@ class Scene:
     @property
     def area_total(self):
         return self.s.area_total
+
+    def area(self):
+        return np.ctypeslib.as_array(self.s.area, (self.s.num_tris,)).copy()
 
 
 def settings_of(st) -> _Settings:
@@ -346,6 +369,14 @@ def intersect(scene: Scene, o, d, tmin=1e-4, tmax=1e30):
     lib().or_trace_batch(C.byref(scene.s), C.c_int32(n), _p(o), _p(d), C.c_double(tmin),
                          C.c_double(tmax), _p(tri, _ip), _p(t))
     return tri, t
+
+
+def prev_position(scene: Scene, tri: int, x):
+    """Position of point x on triangle tri one scene update earlier."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.zeros(3)
+    lib().or_prev_position(C.byref(scene.s), C.c_int32(tri), _p(x), _p(out))
+    return out
 
 
 def sample_emitter(scene: Scene, u: float) -> int:

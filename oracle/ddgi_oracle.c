@@ -33,27 +33,46 @@ static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x >
 /* scene                                                                    */
 /* ------------------------------------------------------------------------ */
 
+static void tri_geometry(or_scene* s, int32_t i) {
+    const double* v = s->verts + 9 * i;
+    double e1[3], e2[3], c[3];
+    sub3(v + 3, v, e1);
+    sub3(v + 6, v, e2);
+    cross3(e1, e2, c);
+    double l = len3(c);
+    s->area[i] = 0.5 * l;
+    for (int k = 0; k < 3; ++k) s->normal[3 * i + k] = l > 0 ? c[k] / l : 0.0;
+}
+
+static void identity34(double* m) {
+    for (int k = 0; k < 12; ++k) m[k] = (k == 0 || k == 5 || k == 10) ? 1.0 : 0.0;
+}
+
 int or_scene_init(or_scene* s) {
-    int32_t T = s->num_tris;
+    int32_t T = s->num_tris, I = s->tri_instance ? s->num_instances : 0;
     s->normal = (double*)malloc(sizeof(double) * 3 * (T > 0 ? T : 1));
     s->area = (double*)malloc(sizeof(double) * (T > 0 ? T : 1));
     s->emitter_tri = (int32_t*)malloc(sizeof(int32_t) * (T > 0 ? T : 1));
+    s->emitter_of = (int32_t*)malloc(sizeof(int32_t) * (T > 0 ? T : 1));
     s->emitter_cdf = (float*)malloc(sizeof(float) * (T > 0 ? T : 1));
-    if (!s->normal || !s->area || !s->emitter_tri || !s->emitter_cdf) return -1;
+    s->inst_cur = (double*)malloc(sizeof(double) * 12 * (I > 0 ? I : 1));
+    s->inst_prev = (double*)malloc(sizeof(double) * 12 * (I > 0 ? I : 1));
+    if (!s->normal || !s->area || !s->emitter_tri || !s->emitter_of || !s->emitter_cdf || !s->inst_cur ||
+        !s->inst_prev)
+        return -1;
+    for (int32_t k = 0; k < I; ++k) {
+        identity34(s->inst_cur + 12 * k);
+        identity34(s->inst_prev + 12 * k);
+    }
     s->num_emitters = 0;
     double acc = 0.0;
     for (int32_t i = 0; i < T; ++i) {
-        const double* v = s->verts + 9 * i;
-        double e1[3], e2[3], c[3];
-        sub3(v + 3, v, e1);
-        sub3(v + 6, v, e2);
-        cross3(e1, e2, c);
-        double l = len3(c);
-        s->area[i] = 0.5 * l;
-        for (int k = 0; k < 3; ++k) s->normal[3 * i + k] = l > 0 ? c[k] / l : 0.0;
+        tri_geometry(s, i);
+        s->emitter_of[i] = -1;
         const double* e = s->emission + 3 * i;
         if (e[0] > 0 || e[1] > 0 || e[2] > 0) {
             acc += s->area[i];
+            s->emitter_of[i] = s->num_emitters;
             s->emitter_tri[s->num_emitters] = i;
             s->emitter_cdf[s->num_emitters] = (float)acc;
             s->num_emitters++;
@@ -64,8 +83,59 @@ int or_scene_init(or_scene* s) {
 }
 
 void or_scene_free(or_scene* s) {
-    free(s->normal); free(s->area); free(s->emitter_tri); free(s->emitter_cdf);
-    s->normal = NULL; s->area = NULL; s->emitter_tri = NULL; s->emitter_cdf = NULL;
+    free(s->normal); free(s->area); free(s->emitter_tri); free(s->emitter_of); free(s->emitter_cdf);
+    free(s->inst_cur); free(s->inst_prev);
+    s->normal = NULL; s->area = NULL; s->emitter_tri = NULL; s->emitter_of = NULL; s->emitter_cdf = NULL;
+    s->inst_cur = NULL; s->inst_prev = NULL;
+}
+
+/* y = M x for a row-major 3x4 affine transform */
+static void xform(const double* m, const double x[3], double y[3]) {
+    for (int r = 0; r < 3; ++r) y[r] = m[4 * r] * x[0] + m[4 * r + 1] * x[1] + m[4 * r + 2] * x[2] + m[4 * r + 3];
+}
+
+/* Scene dynamics (the dynamic scenes the method is built for, Sec. 1 and
+ * Sec. 4): instanced triangles take positions M_i p0 from their identity-pose
+ * positions p0 (xf: [n][12] row-major 3x4, n = num_instances; the old
+ * transforms are kept for reprojection), and the emitters take new radiance
+ * (emitter_radiance: [E][3] in emitter-list order).  Either may be NULL.  The
+ * emitter list and its area distribution stay those of the first scene. */
+int or_scene_update(or_scene* s, const double* xf, int32_t n, const double* emitter_radiance) {
+    if (xf) {
+        if (!s->tri_instance || n != s->num_instances) return -1;
+        memcpy(s->inst_prev, s->inst_cur, sizeof(double) * 12 * (size_t)n);
+        memcpy(s->inst_cur, xf, sizeof(double) * 12 * (size_t)n);
+        for (int32_t i = 0; i < s->num_tris; ++i) {
+            int32_t k = s->tri_instance[i];
+            if (k < 0) continue;
+            for (int c = 0; c < 3; ++c) xform(s->inst_cur + 12 * k, s->object_verts + 9 * i + 3 * c, s->verts + 9 * i + 3 * c);
+            tri_geometry(s, i);
+        }
+    }
+    if (emitter_radiance)
+        for (int32_t e = 0; e < s->num_emitters; ++e)
+            for (int c = 0; c < 3; ++c) s->emission[3 * s->emitter_tri[e] + c] = emitter_radiance[3 * e + c];
+    return 0;
+}
+
+/* Where a point x on triangle tri was one update earlier: an instanced
+ * triangle moved with its instance, x_prev = M_prev M_cur^-1 x (the 3x3 part
+ * inverted by cofactors); a static one stayed. */
+void or_prev_position(const or_scene* s, int32_t tri, const double x[3], double xp[3]) {
+    int32_t k = (s->tri_instance && tri >= 0) ? s->tri_instance[tri] : -1;
+    if (k < 0) {
+        for (int a = 0; a < 3; ++a) xp[a] = x[a];
+        return;
+    }
+    const double* m = s->inst_cur + 12 * k;
+    double A[9] = {m[0], m[1], m[2], m[4], m[5], m[6], m[8], m[9], m[10]};
+    double C[9] = {A[4] * A[8] - A[5] * A[7], A[2] * A[7] - A[1] * A[8], A[1] * A[5] - A[2] * A[4],
+                   A[5] * A[6] - A[3] * A[8], A[0] * A[8] - A[2] * A[6], A[2] * A[3] - A[0] * A[5],
+                   A[3] * A[7] - A[4] * A[6], A[1] * A[6] - A[0] * A[7], A[0] * A[4] - A[1] * A[3]};
+    double det = A[0] * C[0] + A[1] * C[3] + A[2] * C[6];
+    double d[3] = {x[0] - m[3], x[1] - m[7], x[2] - m[11]}, p0[3];
+    for (int r = 0; r < 3; ++r) p0[r] = (C[3 * r] * d[0] + C[3 * r + 1] * d[1] + C[3 * r + 2] * d[2]) / det;
+    xform(s->inst_prev + 12 * k, p0, xp);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -595,8 +665,9 @@ int or_gbuffer(const or_scene* s, const or_camera* cam, const or_camera* pc,
             g->alb[3 * k + a] = s->albedo[3 * tri + a];
         }
         if (pc) {
-            double vv[3];
-            sub3(g->pos + 3 * k, pc->pos, vv);
+            double vv[3], xp[3];
+            or_prev_position(s, tri, g->pos + 3 * k, xp);
+            sub3(xp, pc->pos, vv);
             double z = dot3(vv, pc->fwd);
             if (z > 0.0) {
                 double px = dot3(vv, pc->right) / z / (pc->tan_half_fovy * aspect);
@@ -799,7 +870,7 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
             if (cx <= 0.0) continue;
             pB = cx / PI * cy / dist2;
             const double* le = s->emission + 3 * tri;
-            pL = (le[0] > 0 || le[1] > 0 || le[2] > 0) ? 1.0 / s->area_total : 0.0;
+            pL = s->emitter_of[tri] >= 0 ? 1.0 / s->area_total : 0.0;
             double pmix = (NL * pL + NB * pB) / M;
             double ph = or_target(s, x, nx, rho, y, tri, L);
             double wc = pmix > 0.0 ? ph / pmix : 0.0;
@@ -840,8 +911,9 @@ int or_restir_temporal(const or_scene* s, const or_settings* st, const or_gbuf* 
         int32_t pq = g->prev[q];
         if (pq < 0 || gp->tri[pq] < 0) continue;
         if (dot3(g->nrm + 3 * q, gp->nrm + 3 * pq) <= st->normal_reject_cos) continue;
-        double dv[3];
-        sub3(g->pos + 3 * q, cpos, dv);
+        double dv[3], xp[3];
+        or_prev_position(s, g->tri[q], g->pos + 3 * q, xp);
+        sub3(xp, cpos, dv);
         double de = len3(dv);
         if (fabs(de - gp->dist[pq]) > st->depth_reject_frac * de) continue;
         double Mc = cur->M[q];

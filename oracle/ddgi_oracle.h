@@ -23,16 +23,23 @@
 
 typedef struct {
     int32_t num_tris;
-    const double* verts;     /* [T][3][3] */
+    double* verts;           /* [T][3][3] current positions (or_scene_update moves instances) */
     const double* albedo;    /* [T][3] */
-    const double* emission;  /* [T][3] */
+    double* emission;        /* [T][3] (or_scene_update sets the emitters' radiance) */
+    /* scene dynamics (tri_instance NULL: a static scene) */
+    const int32_t* tri_instance;  /* [T] rigid instance of each triangle, -1 = static */
+    int32_t num_instances;
+    const double* object_verts;   /* [T][3][3] positions at the identity pose */
     /* derived by or_scene_init */
     double* normal;          /* [T][3] winding normal cross(v1-v0, v2-v0), unit */
     double* area;            /* [T] */
     int32_t num_emitters;
     int32_t* emitter_tri;    /* [E] emissive triangles in increasing index */
+    int32_t* emitter_of;     /* [T] position in the emitter list, -1 = not an emitter */
     float* emitter_cdf;      /* [E] cumulative emitter area, rounded to float */
     double area_total;       /* total emissive area (fp64) */
+    double* inst_cur;        /* [I][12] current instance transforms (row-major 3x4) */
+    double* inst_prev;       /* [I][12] the transforms of the previous update */
 } or_scene;
 
 typedef struct {
@@ -97,6 +104,8 @@ extern "C" {
 #endif
 int or_scene_init(or_scene* s);
 void or_scene_free(or_scene* s);
+int or_scene_update(or_scene* s, const double* xf, int32_t n, const double* emitter_radiance);
+void or_prev_position(const or_scene* s, int32_t tri, const double x[3], double xp[3]);
 
 uint32_t or_pcg(uint32_t v);
 uint32_t or_rng_u32(uint32_t seed, uint32_t pixel, uint32_t frame, uint32_t pass,

@@ -18,6 +18,11 @@ not available):
                      translating 5 cm per frame, 16x8x16 probes, 256 rays.
 * ``tiny_room_1080p`` -- the tiny room rendered at 1920x1080 (learned-target
                      workload).
+* ``apartment_dynamic`` -- the apartment plus 200 boxes in sinusoidal rigid
+                     motion, emitter halves swapping every 8 frames, probe
+                     relocation on, 64 frames.
+* ``tiny_room_dynamic`` -- the box with 3 moving boxes and toggling emitters
+                     (small full-image case of the dynamics).
 """
 from __future__ import annotations
 
@@ -28,8 +33,8 @@ from typing import Dict, List, Optional
 import numpy as np
 
 __all__ = [
-    "Scene", "Camera", "ProbeGrid", "Settings",
-    "tiny_room", "tiny_room_1080p", "apartment", "make_scene",
+    "Scene", "Camera", "ProbeGrid", "Settings", "Motion",
+    "tiny_room", "tiny_room_1080p", "apartment", "apartment_dynamic", "tiny_room_dynamic", "make_scene",
     "synthetic_gbuffer", "synthetic_reservoirs", "synthetic_irradiance_interior",
     "synthetic_depth_interior",
 ]
@@ -101,6 +106,33 @@ class Settings:
 
 
 @dataclasses.dataclass
+class Motion:
+    """Rigid sinusoidal motion of instances about their identity pose: at
+    frame f instance i is turned by spin_i (sin(2 pi f / T_i + phi_i) -
+    sin(phi_i)) radians about the vertical axis through its centre and
+    shifted by amp_i (same bracket) along its horizontal axis, so that frame
+    0 is the identity."""
+    center: np.ndarray     # float64[I, 3]
+    axis: np.ndarray       # float64[I, 3] unit, horizontal
+    amp: np.ndarray        # float64[I] metres
+    spin: np.ndarray       # float64[I] radians
+    period: np.ndarray     # float64[I] frames
+    phase: np.ndarray      # float64[I]
+
+    def transforms(self, frame: int) -> np.ndarray:
+        """float32[I, 12]: row-major 3x4 transforms [R | t]."""
+        s = np.sin(2 * np.pi * frame / self.period + self.phase) - np.sin(self.phase)
+        th = self.spin * s
+        c, n = np.cos(th), np.sin(th)
+        I = len(self.amp)
+        R = np.zeros((I, 3, 3))
+        R[:, 0, 0], R[:, 0, 2], R[:, 1, 1], R[:, 2, 0], R[:, 2, 2] = c, n, 1.0, -n, c
+        t = self.center - np.einsum("ijk,ik->ij", R, self.center) + self.axis * (self.amp * s)[:, None]
+        M = np.concatenate([R, t[:, :, None]], axis=2)
+        return M.reshape(I, 12).astype(np.float32)
+
+
+@dataclasses.dataclass
 class Scene:
     name: str
     verts: np.ndarray      # float32[T, 3, 3]
@@ -109,10 +141,36 @@ class Scene:
     grid: ProbeGrid
     cameras: List[Camera]
     settings: Settings
+    # dynamics (None: static): rigid instance of each triangle (-1 static),
+    # its motion, and the period (frames) after which the two halves of the
+    # emitters (even / odd position in the emitter list) swap on and off
+    tri_instance: Optional[np.ndarray] = None     # int32[T]
+    motion: Optional[Motion] = None
+    emitter_toggle: int = 0
 
     @property
     def num_tris(self) -> int:
         return int(self.verts.shape[0])
+
+    @property
+    def num_instances(self) -> int:
+        return 0 if self.tri_instance is None else int(self.tri_instance.max(initial=-1)) + 1
+
+    def instance_transforms(self, frame: int) -> Optional[np.ndarray]:
+        return None if self.motion is None else self.motion.transforms(frame)
+
+    def emitter_radiance(self, frame: int) -> Optional[np.ndarray]:
+        """float32[E, 3] radiance of the emitters (emissive triangles in
+        increasing index) at this frame: the even half is on during the first
+        `emitter_toggle` frames of every 2 x `emitter_toggle`, the odd half
+        during the others."""
+        if not self.emitter_toggle:
+            return None
+        le = self.emission[self.emission.max(axis=1) > 0]
+        on_even = (frame // self.emitter_toggle) % 2 == 0
+        odd = (np.arange(len(le)) % 2) == 1
+        lit = odd != on_even
+        return np.where(lit[:, None], le, 0.0).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------
@@ -319,9 +377,66 @@ def apartment(seed: int = 7, width: int = 1920, height: int = 1080,
                  np.asarray(emi, np.float32), grid, cams, st)
 
 
+def _moving_boxes(rng, n, lo, hi, size, keep_out=None):
+    """n random solid boxes inside [lo, hi] (a box's triangles, its centre)
+    with sinusoidal motion parameters."""
+    tris, centers = [], []
+    while len(centers) < n:
+        s = rng.uniform(size[0], size[1], 3)
+        c = np.array([rng.uniform(lo[a] + s[a] / 2, hi[a] - s[a] / 2) for a in range(3)])
+        if keep_out is not None and keep_out(c, s):
+            continue
+        tris.append([t for f in _box_faces(c - s / 2, c + s / 2) for t in f])
+        centers.append(c)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    axis = np.stack([np.cos(ang), np.zeros(n), np.sin(ang)], 1)
+    motion = Motion(np.asarray(centers), axis, rng.uniform(0.2, 0.6, n), rng.uniform(0.1, 0.5, n),
+                    rng.uniform(32, 128, n), rng.uniform(0, 2 * np.pi, n))
+    return tris, motion
+
+
+def _with_instances(sc: Scene, box_tris, motion, rng, toggle, name) -> Scene:
+    """Scene plus moving boxes (instances 0..n-1, appended after the static
+    triangles) and emitter toggling."""
+    extra = [t for b in box_tris for t in b]
+    inst = np.concatenate([np.full(sc.num_tris, -1, np.int32),
+                           np.repeat(np.arange(len(box_tris), dtype=np.int32), [len(b) for b in box_tris])])
+    alb = np.repeat(rng.uniform(0.2, 0.8, (len(box_tris), 3)), [len(b) for b in box_tris], axis=0)
+    return Scene(name, np.concatenate([sc.verts, np.asarray(extra, np.float32)]),
+                 np.concatenate([sc.albedo, alb.astype(np.float32)]),
+                 np.concatenate([sc.emission, np.zeros((len(extra), 3), np.float32)]),
+                 sc.grid, sc.cameras, dataclasses.replace(sc.settings, probe_relocation=1),
+                 inst, motion, toggle)
+
+
+def apartment_dynamic(seed: int = 7, width: int = 1920, height: int = 1080, frames: int = 64,
+                      moving_boxes: int = 200) -> Scene:
+    """The apartment plus 200 boxes (0.2 to 0.6 m, anywhere in the volume
+    outside the camera corridor) moving sinusoidally (shift 0.2 to 0.6 m,
+    turn 0.1 to 0.5 rad, periods 32 to 128 frames); the two halves of the
+    1024 emitters swap on and off every 8 frames; probe relocation on."""
+    sc = apartment(seed, width, height, frames)
+    rng = np.random.default_rng([seed, 0x6D6F74])      # the "motion" stream
+    boxes, motion = _moving_boxes(rng, moving_boxes, (0.3, 0.1, 0.3), (15.7, 2.8, 11.7), (0.2, 0.6),
+                                  keep_out=lambda c, s: c[2] + s[2] / 2 > 2.2 and c[2] - s[2] / 2 < 3.8)
+    return _with_instances(sc, boxes, motion, rng, 8, "apartment_dynamic")
+
+
+def tiny_room_dynamic(seed: int = 1, width: int = 64, height: int = 48, frames: int = 8) -> Scene:
+    """The box with 3 floating boxes in motion and its two emitter triangles
+    swapping every 2 frames (a small full-image case of the dynamics)."""
+    sc = tiny_room(seed, width, height, frames)
+    rng = np.random.default_rng([seed, 0x6D6F74])
+    boxes, motion = _moving_boxes(rng, 3, (-0.9, -0.9, -0.9), (0.9, 0.6, 0.9), (0.15, 0.4),
+                                  keep_out=lambda c, s: np.linalg.norm(c[[0, 2]]) < 0.35)
+    motion.period[:] = rng.uniform(4, 8, 3)
+    return _with_instances(sc, boxes, motion, rng, 2, "tiny_room_dynamic")
+
+
 def make_scene(name: str, **kw) -> Scene:
     return {"tiny_room": tiny_room, "tiny_room_1080p": tiny_room_1080p,
-            "apartment": apartment}[name](**kw)
+            "apartment": apartment, "apartment_dynamic": apartment_dynamic,
+            "tiny_room_dynamic": tiny_room_dynamic}[name](**kw)
 
 
 # ---------------------------------------------------------------------------

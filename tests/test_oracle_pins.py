@@ -762,3 +762,102 @@ def test_relocation_threshold_and_clamp(oracle_lib):
             np.testing.assert_array_equal(np.abs(vol.offset[0]), lim)
         else:
             np.testing.assert_array_equal(vol.offset[0], 0.0)
+
+
+# ---------------------------------------------------------------------------
+# scene dynamics: rigid instances, emitter toggling, reprojection
+# ---------------------------------------------------------------------------
+
+def _translation(I, t):
+    M = np.tile(np.eye(3, 4), (I, 1, 1))
+    M[:, :, 3] = t
+    return M.reshape(I, 12)
+
+
+def test_moved_instance_is_hit_where_it_moved(oracle_lib):
+    """A ray toward a box translated by d along its axis hits it d closer
+    (the static walls do not move); areas are unchanged by a rotation."""
+    O = oracle_lib
+    sc = scenegen.tiny_room_dynamic()
+    S = O.Scene(sc)
+    c = sc.motion.center[0]
+    o = np.array([c[0], c[1], -0.999])
+    d = np.array([0.0, 0.0, 1.0])
+    tri0, t0 = O.intersect(S, o, d)
+    assert sc.tri_instance[tri0] == 0
+    shift = np.zeros((3, 3))
+    shift[0, 2] = -0.05
+    S.update(_translation(3, shift))
+    tri1, t1 = O.intersect(S, o, d)
+    assert sc.tri_instance[tri1] == 0
+    assert t1 == pytest.approx(t0 - 0.05, abs=1e-9)
+    area0 = S.area().copy()
+    S.update(sc.instance_transforms(3))
+    np.testing.assert_allclose(S.area(), area0, rtol=1e-6)
+    moved = sc.tri_instance >= 0
+    assert np.abs(S.verts.reshape(-1, 3, 3)[moved] - sc.verts[moved]).max() > 1e-3
+    np.testing.assert_array_equal(S.verts.reshape(-1, 3, 3)[~moved], sc.verts[~moved].astype(float))
+
+
+def test_previous_position_follows_the_instance(oracle_lib):
+    """x_prev of a point on a moved triangle has the same barycentric
+    coordinates on the triangle's previous pose; static points stay."""
+    O = oracle_lib
+    sc = scenegen.tiny_room_dynamic()
+    S = O.Scene(sc)
+    S.update(sc.instance_transforms(1))
+    before = S.verts.reshape(-1, 3, 3).copy()
+    S.update(sc.instance_transforms(2))
+    after = S.verts.reshape(-1, 3, 3)
+    rng = np.random.default_rng(4)
+    for tri in list(np.flatnonzero(sc.tri_instance >= 0)[::5]) + [0, 7]:
+        b = rng.dirichlet([1, 1, 1])
+        x = b @ after[tri]
+        xp = O.prev_position(S, int(tri), x)
+        np.testing.assert_allclose(xp, b @ before[tri], atol=1e-12)
+
+
+def test_emitter_toggle_keeps_the_emitter_list(oracle_lib):
+    """Switching emitters off changes their radiance only: the emitter list
+    and its area distribution, and so the choice of emitter for a given u,
+    stay the same."""
+    O = oracle_lib
+    sc = scenegen.apartment_dynamic(frames=1)
+    S = O.Scene(sc)
+    us = np.random.default_rng(3).random(200)
+    before = [O.sample_emitter(S, u) for u in us]
+    le = sc.emitter_radiance(8)
+    S.update(emitter_radiance=le)
+    assert [O.sample_emitter(S, u) for u in us] == before
+    em = np.flatnonzero(sc.emission.max(axis=1) > 0)
+    np.testing.assert_array_equal(S.emission.reshape(-1, 3)[em], le.astype(float))
+    assert (le.max(axis=1) > 0).sum() == len(em) // 2
+
+
+def test_gbuffer_reprojects_a_moving_box(oracle_lib):
+    """Static camera, box translated along the camera's right axis by d at
+    depth z: its pixels' previous pixel is d / (z tan(fov/2) aspect) x W/2
+    columns to the left (exact up to the pixel grid)."""
+    O = oracle_lib
+    sc = scenegen.tiny_room_dynamic(width=96, height=72)
+    S = O.Scene(sc)
+    cam = sc.cameras[0]
+    S.update(_translation(3, np.zeros((3, 3))))
+    shift = np.zeros((3, 3))
+    shift[:, 0] = 0.06                                    # camera right is +x (looking down -z)
+    S.update(_translation(3, shift))
+    g = O.gbuffer(S, cam, cam)
+    W, H = cam.width, cam.height
+    on_box = np.flatnonzero((g.tri >= 0) & (sc.tri_instance[np.maximum(g.tri, 0)] >= 0))
+    assert len(on_box) > 50
+    z = -g.pos[on_box, 2]                                 # depth along the view axis (camera at the origin)
+    dcol = 0.06 / (z * cam.tan_half_fovy * W / H) * W / 2
+    i = on_box % W
+    pq = g.prev[on_box]
+    ok = pq >= 0
+    pcol = pq[ok] % W
+    exp = np.floor((i[ok] + 0.5) - dcol[ok])
+    assert np.mean(np.abs(pcol - exp) <= 1) == 1.0
+    assert np.mean(pcol == exp) > 0.95
+    static = np.flatnonzero((g.tri >= 0) & (sc.tri_instance[np.maximum(g.tri, 0)] < 0))
+    np.testing.assert_array_equal(g.prev[static], static)
