@@ -57,6 +57,11 @@ typedef struct {
     const float* vertices;   /* host [num_tris][3][3] */
     const float* albedo;     /* host [num_tris][3]  diffuse albedo rho */
     const float* emission;   /* host [num_tris][3]  emitted radiance Le */
+    /* dynamics (NULL / 0: a static scene): the rigid instance of each
+     * triangle, -1 = static; instance ids < num_instances; the vertices above
+     * are the instances' identity pose; instanced triangles may not emit */
+    const int32_t* tri_instance;   /* host [num_tris] or NULL */
+    uint32_t num_instances;        /* <= 2^20 */
 } ddgi_scene;
 
 /* Method parameters.  Probe volume: a counts[0] x counts[1] x counts[2] grid,
@@ -106,7 +111,8 @@ typedef struct {
 /* G-buffer planes (device): g0 = position.xyz, distance to camera;
  * g1 = normal.xyz, triangle index (uint32 bits, 0xFFFFFFFF = no valid
  * front-facing hit); g2 = albedo.rgb, previous-frame pixel (int32 bits, -1 =
- * none). */
+ * none; bit 30 set: the surface belongs to a rigid instance, whose motion
+ * restir_temporal undoes before its distance test). */
 typedef struct {
     float* g0;
     float* g1;
@@ -153,6 +159,22 @@ ddgi_status ddgi_get_info(ddgi_ctx* ctx, ddgi_info* out);
 ddgi_status ddgi_probe_update(ddgi_ctx* ctx, uint32_t frame, void* stream);
 ddgi_status ddgi_probe_trace(ddgi_ctx* ctx, uint32_t frame, void* stream);
 ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream);
+
+/* Scene dynamics, enqueued on `stream` (the paper's scenes are fully
+ * dynamic, Sec. 1, Sec. 4).  xf (host [n][12], n = num_instances, or NULL):
+ * row-major 3x4 transforms [R | t] of the instances relative to their
+ * identity pose; the instanced triangles move there, and the BVH boxes over
+ * them are refitted (the topology of ddgi_create is kept, so large motions
+ * cost traversal time, not correctness).  The transforms of the previous call
+ * are kept: ddgi_gbuffer reprojects a surface on an instance through
+ * M_prev M_cur^-1 and marks it (bit 30 of the previous-pixel word).
+ * emitter_radiance (host [E][3] in increasing triangle order of the emissive
+ * triangles of ddgi_create, or NULL): new radiance, 0 switches an emitter
+ * off; the emitter list and its area distribution do not change.  Host
+ * buffers may be reused when the call returns.  Calls on other streams
+ * must be ordered with this one by the caller. */
+ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const float* emitter_radiance,
+                              void* stream);
 
 /* Probe relocation from the rays of the last ddgi_probe_trace of `frame`
  * (the paper's probe volume, Sec. 2, cites it; the rule is that of Majercik

@@ -600,10 +600,13 @@ class Renderer:
         self.prev_res: Optional[Reservoirs] = None
         self.prev_cam = None
 
-    def frame(self, f: int, cam=None, probe_update_enabled=True):
+    def frame(self, f: int, cam=None, probe_update_enabled=True, xf=None, emitter_radiance=None):
+        """One frame; xf / emitter_radiance (optional) first move the scene."""
         sc, S = self.sc, self.scene
         cam = cam or sc.cameras[f % len(sc.cameras)]
         out = {}
+        if xf is not None or emitter_radiance is not None:
+            S.update(xf, emitter_radiance)
         if probe_update_enabled:
             probe_update(S, self.vol, f)
         g = gbuffer(S, cam, self.prev_cam)

@@ -15,7 +15,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libddgi.so")
 SOURCES = ["capi.cpp", "bvh_build.cpp", "probe.cu", "restir.cu", "shade.cu", "metrics.cu",
            "metrics_static.cu", "mlp.cu",
-           "reference.cu"]
+           "reference.cu", "dynamics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "--ftz=true", "--prec-div=false",
            "--prec-sqrt=false", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE]

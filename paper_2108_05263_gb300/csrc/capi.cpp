@@ -60,6 +60,17 @@ struct ddgi_ctx {
     float* tmp_grad = nullptr;
     uint32_t updates = 0;
     uint32_t bvh_nodes = 0, bvh_depth = 0;
+    // scene dynamics
+    uint32_t I = 0, NI = 0;          // instances, instanced triangles
+    int32_t* tri_inst = nullptr;     // [T] instance or -1
+    uint4* inst_map = nullptr;       // [NI] BVH slot, triangle, instance
+    float4* inst_obj = nullptr;      // [3 NI] identity-pose vertices
+    float4* inst_xf = nullptr;       // [3 I] current transform rows
+    float4* inst_delta = nullptr;    // [3 I] rows of M_prev M_cur^-1
+    uint32_t* refit_list = nullptr;  // nodes over instanced triangles, deepest depth first
+    std::vector<uint32_t> refit_levels;
+    std::vector<double> xf_cur, xf_prev;   // [12 I] host copies
+    float* le_stage = nullptr;       // [3 E] staged emitter radiance
     uint64_t device_bytes = 0;
     std::vector<void*> allocs;
     std::string last_error;
@@ -142,6 +153,9 @@ SceneView scene_view(ddgi_ctx* c) {
     s.num_emitters = c->E;
     s.area_total = c->area_total;
     s.err = c->err;
+    s.tri_inst = c->I ? c->tri_inst : nullptr;
+    s.num_tris = c->T;
+    s.inst_delta = c->inst_delta;
     return s;
 }
 
@@ -352,6 +366,108 @@ cudaError_t ensure_hits(ddgi_ctx* c, size_t n, cudaStream_t st) {
     return e;
 }
 
+// Tables of the rigid instances: BVH slots of the instanced triangles with
+// their identity-pose vertices, and the BVH4 nodes whose subtrees hold any of
+// them, grouped by depth (deepest first) for the bottom-up refit.
+cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bvh) {
+    const uint32_t T = c->T, I = scene->num_instances, N = bvh.num_nodes;
+    std::vector<uint4> map;
+    std::vector<float4> obj;
+    std::vector<uint8_t> slot_moving(T, 0);
+    for (uint32_t k = 0; k < T; ++k) {
+        uint32_t orig;
+        std::memcpy(&orig, &bvh.tris[12ull * k + 3], 4);
+        const int32_t inst = scene->tri_instance[orig];
+        if (inst < 0) continue;
+        slot_moving[k] = 1;
+        map.push_back(make_uint4(k, orig, (uint32_t)inst, 0u));
+        const float* v = scene->vertices + 9ull * orig;
+        for (int q = 0; q < 3; ++q) obj.push_back(make_float4(v[3 * q], v[3 * q + 1], v[3 * q + 2], 0.f));
+    }
+    // dirty nodes: children follow their parent in the node order, so one
+    // backward sweep sees every child before its parent
+    std::vector<uint8_t> dirty(N, 0);
+    std::vector<uint32_t> depth(N, 0);
+    for (uint32_t n = 0; n < N; ++n)
+        for (int s = 0; s < 4; ++s) {
+            int ch;
+            std::memcpy(&ch, &bvh.nodes[32ull * n + 24 + s], 4);
+            if (ch >= 0) depth[ch] = depth[n] + 1;
+        }
+    uint32_t maxd = 0;
+    for (uint32_t n = N; n-- > 0;) {
+        for (int s = 0; s < 4; ++s) {
+            int ch, cnt;
+            std::memcpy(&ch, &bvh.nodes[32ull * n + 24 + s], 4);
+            std::memcpy(&cnt, &bvh.nodes[32ull * n + 28 + s], 4);
+            if (ch >= 0) {
+                dirty[n] |= dirty[ch];
+            } else {
+                for (int k = ~ch; k < ~ch + cnt; ++k) dirty[n] |= slot_moving[k];
+            }
+        }
+        if (dirty[n]) maxd = std::max(maxd, depth[n]);
+    }
+    std::vector<uint32_t> list;
+    c->refit_levels.assign(1, 0u);
+    for (uint32_t d = maxd + 1; d-- > 0;) {
+        for (uint32_t n = 0; n < N; ++n)
+            if (dirty[n] && depth[n] == d) list.push_back(n);
+        c->refit_levels.push_back((uint32_t)list.size());
+    }
+    std::vector<int32_t> ti(scene->tri_instance, scene->tri_instance + T);
+    c->I = I;
+    c->NI = (uint32_t)map.size();
+    c->xf_cur.assign(12ull * I, 0.0);
+    for (uint32_t k = 0; k < I; ++k) c->xf_cur[12 * k] = c->xf_cur[12 * k + 5] = c->xf_cur[12 * k + 10] = 1.0;
+    c->xf_prev = c->xf_cur;
+    std::vector<float4> ident(3ull * I);
+    for (uint32_t k = 0; k < I; ++k) {
+        ident[3 * k] = make_float4(1.f, 0.f, 0.f, 0.f);
+        ident[3 * k + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
+        ident[3 * k + 2] = make_float4(0.f, 0.f, 1.f, 0.f);
+    }
+    cudaError_t e = dalloc(c, &c->tri_inst, T);
+    if (e == cudaSuccess) e = dalloc(c, &c->inst_map, map.size());
+    if (e == cudaSuccess) e = dalloc(c, &c->inst_obj, obj.size());
+    if (e == cudaSuccess) e = dalloc(c, &c->inst_xf, 3ull * I);
+    if (e == cudaSuccess) e = dalloc(c, &c->inst_delta, 3ull * I);
+    if (e == cudaSuccess) e = dalloc(c, &c->refit_list, list.size());
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(c->tri_inst, ti.data(), T * sizeof(int32_t));
+    up(c->inst_map, map.data(), map.size() * sizeof(uint4));
+    up(c->inst_obj, obj.data(), obj.size() * sizeof(float4));
+    up(c->inst_xf, ident.data(), ident.size() * sizeof(float4));
+    up(c->inst_delta, ident.data(), ident.size() * sizeof(float4));
+    up(c->refit_list, list.data(), list.size() * sizeof(uint32_t));
+    return e;
+}
+
+// rows of A B for row-major 3x4 affine transforms
+void compose34(const double* A, const double* B, double* out) {
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k)
+            out[4 * r + k] = A[4 * r] * B[k] + A[4 * r + 1] * B[4 + k] + A[4 * r + 2] * B[8 + k];
+        out[4 * r + 3] = A[4 * r] * B[3] + A[4 * r + 1] * B[7] + A[4 * r + 2] * B[11] + A[4 * r + 3];
+    }
+}
+
+// inverse of a 3x4 affine transform (cofactors); false if singular
+bool invert34(const double* M, double* out) {
+    const double a = M[0], b = M[1], cc = M[2], d = M[4], e = M[5], f = M[6], g = M[8], h = M[9], i = M[10];
+    const double C[9] = {e * i - f * h, cc * h - b * i, b * f - cc * e, f * g - d * i, a * i - cc * g,
+                         cc * d - a * f, d * h - e * g, b * g - a * h, a * e - b * d};
+    const double det = a * C[0] + b * C[3] + cc * C[6];
+    if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return false;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) out[4 * r + k] = C[3 * r + k] / det;
+        out[4 * r + 3] = -(out[4 * r] * M[3] + out[4 * r + 1] * M[7] + out[4 * r + 2] * M[11]);
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -371,6 +487,15 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
         if (!(scene->albedo[i] >= 0.f && scene->albedo[i] <= 1.f) ||
             !(scene->emission[i] >= 0.f) || !std::isfinite(scene->emission[i]))
             return DDGI_ERR_INVALID_ARG;
+    if (scene->tri_instance) {
+        if (scene->num_instances == 0 || scene->num_instances > (1u << 20)) return DDGI_ERR_INVALID_ARG;
+        for (uint32_t i = 0; i < scene->num_tris; ++i) {
+            const int32_t k = scene->tri_instance[i];
+            const float* e = scene->emission + 3ull * i;
+            if (k < -1 || k >= (int32_t)scene->num_instances) return DDGI_ERR_INVALID_ARG;
+            if (k >= 0 && (e[0] > 0.f || e[1] > 0.f || e[2] > 0.f)) return DDGI_ERR_INVALID_ARG;
+        }
+    }
 
     ddgi_ctx* ctx = new (std::nothrow) ddgi_ctx;
     if (!ctx) return DDGI_ERR_OOM;
@@ -487,6 +612,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(mlp_w16s, MLP_NW)
     ALLOC(mlp_state, 1)
     ALLOC(train_smp, 3ull * cfg->train_samples)
+    ALLOC(le_stage, 3ull * ctx->E)
     ALLOC(train_sf, cfg->train_samples ? cfg->train_samples / P : 0)
 #undef ALLOC
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -502,6 +628,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
     up(ctx->guide, guide.data(), guide.size() * sizeof(uint32_t));
     up(ctx->sf, sf.data(), R * sizeof(float4));
+    if (e == cudaSuccess && scene->tri_instance) e = setup_instances(ctx, scene, bvh);
     if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->depth, 0, P * td * td * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemset(ctx->offset, 0, P * sizeof(float4));
@@ -594,6 +721,42 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     probe_params(ctx, frame, &p);
     CK(launch_probe_blend(volume_view(ctx), p, ctx->rays, (cudaStream_t)stream));
     ctx->updates++;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const float* emitter_radiance,
+                              void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (xf) {
+        if (ctx->I == 0 || n != ctx->I) return fail(ctx, DDGI_ERR_INVALID_ARG, "transform count != instance count");
+        std::vector<double> cur(12ull * n), delta(12ull * n);
+        for (size_t k = 0; k < 12ull * n; ++k) {
+            if (!std::isfinite(xf[k])) return fail(ctx, DDGI_ERR_INVALID_ARG, "non-finite transform");
+            cur[k] = xf[k];
+        }
+        for (uint32_t k = 0; k < n; ++k) {
+            double inv[12];
+            if (!invert34(&cur[12ull * k], inv)) return fail(ctx, DDGI_ERR_INVALID_ARG, "singular transform");
+            compose34(&ctx->xf_cur[12ull * k], inv, &delta[12ull * k]);
+        }
+        std::vector<float> df(delta.begin(), delta.end());
+        CK(cudaMemcpyAsync(ctx->inst_xf, xf, 12ull * n * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->inst_delta, df.data(), df.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(launch_instance_update(ctx->inst_obj, ctx->inst_map, ctx->NI, ctx->inst_xf, ctx->tris, ctx->nrm,
+                                  ctx->nodes, ctx->refit_list, ctx->refit_levels, st));
+        ctx->xf_prev = ctx->xf_cur;
+        ctx->xf_cur = cur;
+    }
+    if (emitter_radiance) {
+        if (ctx->E == 0) return fail(ctx, DDGI_ERR_INVALID_ARG, "the scene has no emitters");
+        for (size_t k = 0; k < 3ull * ctx->E; ++k)
+            if (!(emitter_radiance[k] >= 0.f) || !std::isfinite(emitter_radiance[k]))
+                return fail(ctx, DDGI_ERR_INVALID_ARG, "emitter radiance must be finite and >= 0");
+        CK(cudaMemcpyAsync(ctx->le_stage, emitter_radiance, 3ull * ctx->E * sizeof(float), cudaMemcpyHostToDevice,
+                           st));
+        CK(launch_emitter_radiance(ctx->le_stage, ctx->etri, ctx->emi, ctx->evert, ctx->E, st));
+    }
     return DDGI_OK;
 }
 

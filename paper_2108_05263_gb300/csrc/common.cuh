@@ -85,7 +85,27 @@ struct SceneView {
     uint32_t num_emitters;
     float area_total;
     uint32_t* err;           // device error word
+    const int* tri_inst;     // rigid instance of each original triangle (-1 static); null: static scene
+    uint32_t num_tris;
+    const float4* inst_delta;   // per instance: rows of M_prev M_cur^-1 (current -> previous pose)
 };
+
+// bit of the G-buffer's previous-pixel word marking a surface on a rigid
+// instance (its previous position is M_prev M_cur^-1 x)
+#define DDGI_PREV_MOVING 0x40000000
+
+// previous-pose position of a point x on triangle tri
+__device__ __forceinline__ f3 prev_position(const SceneView& s, uint32_t tri, f3 x, bool* moving) {
+    *moving = false;
+    if (!s.tri_inst || tri >= s.num_tris) return x;
+    const int k = __ldg(s.tri_inst + tri);
+    if (k < 0) return x;
+    *moving = true;
+    const float4 r0 = __ldg(s.inst_delta + 3 * k), r1 = __ldg(s.inst_delta + 3 * k + 1),
+                 r2 = __ldg(s.inst_delta + 3 * k + 2);
+    return {r0.x * x.x + r0.y * x.y + r0.z * x.z + r0.w, r1.x * x.x + r1.y * x.y + r1.z * x.z + r1.w,
+            r2.x * x.x + r2.y * x.y + r2.z * x.z + r2.w};
+}
 
 struct VolumeView {
     float4* irr;             // [P][ti*ti] rgb, 0

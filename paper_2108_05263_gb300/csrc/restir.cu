@@ -203,6 +203,8 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
     float4* o = out.rec + 4 * (size_t)pix;
     float4 g2 = g.g2[pix];
     int pq = __float_as_int(g2.w);
+    const bool moving = pq >= 0 && (pq & DDGI_PREV_MOVING);
+    pq &= ~DDGI_PREV_MOVING;
     // the owner validity of the current record is this pixel's G-buffer validity
     bool merge = __float_as_uint(c.q3.z) != 0u && pq >= 0 && (uint32_t)pq < prev.n;
     Rec p;
@@ -212,7 +214,13 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
         g0 = g.g0[pix];
         merge = __float_as_uint(p.q3.z) != 0u && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
         if (merge) {
-            float de = length(xyz(g0) - f3{cam_prev.x, cam_prev.y, cam_prev.z});
+            // a surface on a moving instance is compared at its previous position
+            f3 xp = xyz(g0);
+            if (moving) {
+                bool mv;
+                xp = prev_position(s, __float_as_uint(__ldg(&g.g1[pix].w)), xp, &mv);
+            }
+            float de = length(xp - f3{cam_prev.x, cam_prev.y, cam_prev.z});
             merge = fabsf(de - p.q2.w) <= rp.depth_reject_frac * de;
         }
     }

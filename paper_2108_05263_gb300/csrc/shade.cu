@@ -38,14 +38,15 @@ __global__ void __launch_bounds__(128) k_gbuffer(SceneView s, CamView cam, CamVi
             f3 a = xyz(__ldg(s.alb + h.tri));
             int prev = -1;
             if (has_prev) {
-                f3 v = p - f3{pc.pos.x, pc.pos.y, pc.pos.z};
+                bool moving;
+                f3 v = prev_position(s, h.tri, p, &moving) - f3{pc.pos.x, pc.pos.y, pc.pos.z};
                 float z = dot(v, f3{pc.fwd.x, pc.fwd.y, pc.fwd.z});
                 if (z > 0.f) {
                     float qx = dot(v, f3{pc.right.x, pc.right.y, pc.right.z}) / z / (pc.tan_half_fovy * aspect);
                     float qy = dot(v, f3{pc.up.x, pc.up.y, pc.up.z}) / z / pc.tan_half_fovy;
                     float fx = (qx + 1.f) * 0.5f * W, fy = (1.f - qy) * 0.5f * H;
                     if (fx >= 0.f && fy >= 0.f && fx < W && fy < H)
-                        prev = (int)floorf(fy) * cam.width + (int)floorf(fx);
+                        prev = ((int)floorf(fy) * cam.width + (int)floorf(fx)) | (moving ? DDGI_PREV_MOVING : 0);
                 }
             }
             g0 = make_float4(p.x, p.y, p.z, h.t);

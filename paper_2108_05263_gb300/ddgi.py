@@ -31,7 +31,7 @@ _i3 = C.c_int32 * 3
 
 class Scene(C.Structure):
     _fields_ = [("num_tris", C.c_uint32), ("vertices", C.c_void_p), ("albedo", C.c_void_p),
-                ("emission", C.c_void_p)]
+                ("emission", C.c_void_p), ("tri_instance", C.c_void_p), ("num_instances", C.c_uint32)]
 
 
 class Config(C.Structure):
@@ -77,7 +77,7 @@ _lib = None
 
 # entry points declared in include/ddgi.h (all return ddgi_status except the last)
 EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
-           "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_probe_state_get", "ddgi_probe_state_set",
+           "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_scene_update", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
@@ -108,6 +108,7 @@ def load(path: Optional[str] = None):
     L.ddgi_get_info.argtypes = [vp, C.POINTER(Info)]
     for fn in ("ddgi_probe_update", "ddgi_probe_trace", "ddgi_probe_blend", "ddgi_probe_relocate"):
         getattr(L, fn).argtypes = [vp, C.c_uint32, vp]
+    L.ddgi_scene_update.argtypes = [vp, vp, C.c_uint32, vp, vp]
     L.ddgi_probe_state_get.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_uint32), vp]
     L.ddgi_probe_state_set.argtypes = [vp, vp, vp, vp, C.c_uint32, vp]
     L.ddgi_probe_rays_get.argtypes = [vp, vp, vp]
@@ -253,13 +254,17 @@ def config_from(grid, settings) -> Config:
 class Context:
     """Owns a ddgi_ctx (scene BVH, emitter table, probe maps, probe rays)."""
 
-    def __init__(self, verts, albedo, emission, grid, settings):
+    def __init__(self, verts, albedo, emission, grid, settings, tri_instance=None):
         L = load()
         self.L = L
         self._v = np.ascontiguousarray(verts, np.float32)
         self._a = np.ascontiguousarray(albedo, np.float32)
         self._e = np.ascontiguousarray(emission, np.float32)
         sc = Scene(self._v.shape[0], self._v.ctypes.data, self._a.ctypes.data, self._e.ctypes.data)
+        if tri_instance is not None:
+            self._ti = np.ascontiguousarray(tri_instance, np.int32)
+            sc.tri_instance = self._ti.ctypes.data
+            sc.num_instances = int(self._ti.max(initial=-1)) + 1
         self.cfg = config_from(grid, settings)
         self.settings = settings
         h = C.c_void_p()
@@ -271,7 +276,8 @@ class Context:
 
     @staticmethod
     def from_scene(sc, settings=None) -> "Context":
-        return Context(sc.verts, sc.albedo, sc.emission, sc.grid, settings or sc.settings)
+        return Context(sc.verts, sc.albedo, sc.emission, sc.grid, settings or sc.settings,
+                       getattr(sc, "tri_instance", None))
 
     def close(self):
         if getattr(self, "h", None):
@@ -292,6 +298,17 @@ class Context:
         i = Info()
         self._check("ddgi_get_info", self.L.ddgi_get_info(self.h, C.byref(i)))
         return i
+
+    # --- scene dynamics ---
+    def scene_update(self, xf=None, emitter_radiance=None, stream=None):
+        """Instance transforms ([I][12] row-major 3x4) and / or emitter
+        radiance ([E][3]); either may be None."""
+        a = None if xf is None else np.ascontiguousarray(xf, np.float32).reshape(-1, 12)
+        b = None if emitter_radiance is None else np.ascontiguousarray(emitter_radiance, np.float32)
+        self._check("ddgi_scene_update",
+                    self.L.ddgi_scene_update(self.h, None if a is None else a.ctypes.data,
+                                             0 if a is None else a.shape[0],
+                                             None if b is None else b.ctypes.data, _stream(stream)))
 
     # --- probe update (Sec. 3.2) ---
     def probe_update(self, frame, stream=None):
@@ -450,10 +467,13 @@ class Frame:
         self.cur = 0
 
     def render(self, frame: int, cam, gbuf: Optional[GBuffer] = None, stream=None,
-               probe_update=True):
+               probe_update=True, xf=None, emitter_radiance=None):
         """One frame.  If ``gbuf`` is given it is used as this frame's
-        G-buffer (the primary-visibility pass is skipped)."""
+        G-buffer (the primary-visibility pass is skipped); xf /
+        emitter_radiance (optional) first move the scene."""
         ctx = self.ctx
+        if xf is not None or emitter_radiance is not None:
+            ctx.scene_update(xf, emitter_radiance, stream)
         if probe_update:
             ctx.probe_update(frame, stream)
         g = gbuf
