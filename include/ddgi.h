@@ -176,6 +176,20 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream);
 ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const float* emitter_radiance,
                               void* stream);
 
+/* Snapshot of the context's evolving state, for checkpoint / resume: probe
+ * maps, offsets and update count, instance poses (current and previous),
+ * emitter radiance, and for a learned-target context the network (master,
+ * Adam moments, served average, fp16 copies, optimiser / judge state, step
+ * count, serving mode).  Scene geometry, configuration and the caller's
+ * per-pixel buffers are not included.  ddgi_state_save with host_buf NULL
+ * sets *bytes to the size needed; otherwise *bytes must be at least that and
+ * is set to the bytes written.  ddgi_state_load accepts only a snapshot of a
+ * context created from the same scene and configuration (probe count, map
+ * sizes, instance and emitter counts, learned target; else
+ * DDGI_ERR_INVALID_ARG).  Both synchronise `stream`. */
+ddgi_status ddgi_state_save(ddgi_ctx* ctx, void* host_buf, size_t* bytes, void* stream);
+ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
+
 /* Probe relocation from the rays of the last ddgi_probe_trace of `frame`
  * (the paper's probe volume, Sec. 2, cites it; the rule is that of Majercik
  * et al. 2021).  delta = 0.1 x the smallest grid spacing.  A probe with more

@@ -468,6 +468,41 @@ bool invert34(const double* M, double* out) {
     return true;
 }
 
+// --- state snapshot --------------------------------------------------------
+// Layout (host byte stream): a header of 16 uint32 (magic, version, P,
+// irradiance tile, distance tile, instances, emitters, learned flag,
+// probe updates, Adam steps, serve mode, 5 zero), then, in this order:
+// irradiance [P][ti^2] float4, distance moments [P][td^2] float2, offsets
+// [P] float4, current / previous instance transforms [I][12] double each,
+// emitter radiance [E][3] float, and for a learned-target context the master
+// parameters, Adam moments m and v, served (averaged) parameters [NPARAM]
+// float each, their fp16 copies [NW] x 2, and the optimiser / judge state.
+const uint32_t kStateMagic = 0x44444749u;   // "IGDD"
+const uint32_t kStateVersion = 1u;
+
+struct StateLayout {
+    size_t irr, dep, off, xf, le, mlp32, mlp16, mst, total;
+};
+
+StateLayout state_layout(const ddgi_ctx* c) {
+    StateLayout L;
+    const size_t P = c->P, ti = c->cfg.irr_texels + 2, td = c->cfg.depth_texels + 2;
+    size_t o = 16 * sizeof(uint32_t);
+    L.irr = o; o += P * ti * ti * sizeof(float4);
+    L.dep = o; o += P * td * td * sizeof(float2);
+    L.off = o; o += P * sizeof(float4);
+    L.xf = o; o += 2 * 12ull * c->I * sizeof(double);
+    L.le = o; o += 3ull * c->E * sizeof(float);
+    L.mlp32 = o;
+    L.mlp16 = L.mst = o;
+    if (c->cfg.learned_target) {
+        o += 4ull * MLP_NPARAM * sizeof(float);
+        L.mlp16 = o; o += 2ull * MLP_NW * sizeof(__half);
+        L.mst = o; o += sizeof(MLPState);
+    }
+    L.total = o;
+    return L;
+}
 }  // namespace
 
 extern "C" {
@@ -799,6 +834,102 @@ ddgi_status ddgi_probe_state_set(ddgi_ctx* ctx, const float* irr, const float* d
     if (offsets) CK(cudaMemcpyAsync(ctx->offset, offsets, P * sizeof(float4), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     ctx->updates = updates;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_state_save(ddgi_ctx* ctx, void* host_buf, size_t* bytes, void* stream) {
+    if (!ctx || !bytes) return DDGI_ERR_INVALID_ARG;
+    const StateLayout L = state_layout(ctx);
+    if (!host_buf) {
+        *bytes = L.total;
+        return DDGI_OK;
+    }
+    if (*bytes < L.total) return fail(ctx, DDGI_ERR_INVALID_ARG, "state buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t* b = static_cast<uint8_t*>(host_buf);
+    uint32_t h[16] = {kStateMagic, kStateVersion, ctx->P, ctx->cfg.irr_texels + 2, ctx->cfg.depth_texels + 2,
+                      ctx->I, ctx->E, ctx->cfg.learned_target ? 1u : 0u, ctx->updates, ctx->mlp_step,
+                      (uint32_t)ctx->serve, 0, 0, 0, 0, 0};
+    std::memcpy(b, h, sizeof(h));
+    CK(cudaMemcpyAsync(b + L.irr, ctx->irr, L.dep - L.irr, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(b + L.dep, ctx->depth, L.off - L.dep, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(b + L.off, ctx->offset, L.xf - L.off, cudaMemcpyDeviceToHost, st));
+    if (ctx->I) {
+        std::memcpy(b + L.xf, ctx->xf_cur.data(), 12ull * ctx->I * sizeof(double));
+        std::memcpy(b + L.xf + 12ull * ctx->I * sizeof(double), ctx->xf_prev.data(), 12ull * ctx->I * sizeof(double));
+    }
+    float* le = reinterpret_cast<float*>(b + L.le);
+    if (ctx->E) {   // the radiance words of the emitter records
+        std::vector<float4> ev(4ull * ctx->E);
+        CK(cudaMemcpyAsync(ev.data(), ctx->evert, ev.size() * sizeof(float4), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (uint32_t e = 0; e < ctx->E; ++e) {
+            le[3 * e] = ev[4 * e + 1].w;
+            le[3 * e + 1] = ev[4 * e + 2].w;
+            le[3 * e + 2] = ev[4 * e + 3].w;
+        }
+    }
+    if (ctx->cfg.learned_target) {
+        float* const src32[4] = {ctx->mlp_params, ctx->mlp_m, ctx->mlp_v, ctx->mlp_ema};
+        for (int k = 0; k < 4; ++k)
+            CK(cudaMemcpyAsync(b + L.mlp32 + k * MLP_NPARAM * sizeof(float), src32[k], MLP_NPARAM * sizeof(float),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b + L.mlp16, ctx->mlp_w16, MLP_NW * sizeof(__half), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b + L.mlp16 + MLP_NW * sizeof(__half), ctx->mlp_w16s, MLP_NW * sizeof(__half),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b + L.mst, ctx->mlp_state, sizeof(MLPState), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    *bytes = L.total;
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, void* stream) {
+    if (!ctx || !host_buf) return DDGI_ERR_INVALID_ARG;
+    const StateLayout L = state_layout(ctx);
+    const uint8_t* b = static_cast<const uint8_t*>(host_buf);
+    uint32_t h[16];
+    if (bytes < sizeof(h)) return fail(ctx, DDGI_ERR_INVALID_ARG, "state buffer too small");
+    std::memcpy(h, b, sizeof(h));
+    if (h[0] != kStateMagic || h[1] != kStateVersion) return fail(ctx, DDGI_ERR_INVALID_ARG, "not a state snapshot");
+    if (h[2] != ctx->P || h[3] != ctx->cfg.irr_texels + 2 || h[4] != ctx->cfg.depth_texels + 2 || h[5] != ctx->I ||
+        h[6] != ctx->E || h[7] != (ctx->cfg.learned_target ? 1u : 0u) || bytes != L.total)
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "snapshot of a different scene or configuration");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->I) {
+        // replay the last two poses: the triangles land on the current one and
+        // the reprojection delta is that of the saved pair
+        std::vector<double> cur(12ull * ctx->I), prev(12ull * ctx->I);
+        std::memcpy(cur.data(), b + L.xf, cur.size() * sizeof(double));
+        std::memcpy(prev.data(), b + L.xf + cur.size() * sizeof(double), prev.size() * sizeof(double));
+        std::vector<float> pf(prev.begin(), prev.end()), cf(cur.begin(), cur.end());
+        ddgi_status s = ddgi_scene_update(ctx, pf.data(), ctx->I, nullptr, stream);
+        if (s == DDGI_OK) s = ddgi_scene_update(ctx, cf.data(), ctx->I, nullptr, stream);
+        if (s != DDGI_OK) return s;
+        ctx->xf_cur = cur;   // exact fp64 copies (the replay went through float)
+        ctx->xf_prev = prev;
+    }
+    if (ctx->E) {
+        ddgi_status s = ddgi_scene_update(ctx, nullptr, 0, reinterpret_cast<const float*>(b + L.le), stream);
+        if (s != DDGI_OK) return s;
+    }
+    CK(cudaMemcpyAsync(ctx->irr, b + L.irr, L.dep - L.irr, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->depth, b + L.dep, L.off - L.dep, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->offset, b + L.off, L.xf - L.off, cudaMemcpyHostToDevice, st));
+    if (ctx->cfg.learned_target) {
+        float* const dst32[4] = {ctx->mlp_params, ctx->mlp_m, ctx->mlp_v, ctx->mlp_ema};
+        for (int k = 0; k < 4; ++k)
+            CK(cudaMemcpyAsync(dst32[k], b + L.mlp32 + k * MLP_NPARAM * sizeof(float), MLP_NPARAM * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->mlp_w16, b + L.mlp16, MLP_NW * sizeof(__half), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->mlp_w16s, b + L.mlp16 + MLP_NW * sizeof(__half), MLP_NW * sizeof(__half),
+                           cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->mlp_state, b + L.mst, sizeof(MLPState), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    ctx->updates = h[8];
+    ctx->mlp_step = h[9];
+    ctx->serve = (int)h[10];
     return DDGI_OK;
 }
 

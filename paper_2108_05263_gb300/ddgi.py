@@ -77,7 +77,8 @@ _lib = None
 
 # entry points declared in include/ddgi.h (all return ddgi_status except the last)
 EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", "ddgi_probe_trace",
-           "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_scene_update", "ddgi_probe_state_get", "ddgi_probe_state_set",
+           "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_scene_update", "ddgi_state_save",
+           "ddgi_state_load", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
            "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
@@ -109,6 +110,8 @@ def load(path: Optional[str] = None):
     for fn in ("ddgi_probe_update", "ddgi_probe_trace", "ddgi_probe_blend", "ddgi_probe_relocate"):
         getattr(L, fn).argtypes = [vp, C.c_uint32, vp]
     L.ddgi_scene_update.argtypes = [vp, vp, C.c_uint32, vp, vp]
+    L.ddgi_state_save.argtypes = [vp, vp, C.POINTER(C.c_size_t), vp]
+    L.ddgi_state_load.argtypes = [vp, vp, C.c_size_t, vp]
     L.ddgi_probe_state_get.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_uint32), vp]
     L.ddgi_probe_state_set.argtypes = [vp, vp, vp, vp, C.c_uint32, vp]
     L.ddgi_probe_rays_get.argtypes = [vp, vp, vp]
@@ -309,6 +312,18 @@ class Context:
                     self.L.ddgi_scene_update(self.h, None if a is None else a.ctypes.data,
                                              0 if a is None else a.shape[0],
                                              None if b is None else b.ctypes.data, _stream(stream)))
+
+    # --- checkpoint / resume ---
+    def state_save(self, stream=None) -> bytes:
+        n = C.c_size_t(0)
+        self._check("ddgi_state_save", self.L.ddgi_state_save(self.h, None, C.byref(n), _stream(stream)))
+        buf = C.create_string_buffer(n.value)
+        self._check("ddgi_state_save", self.L.ddgi_state_save(self.h, buf, C.byref(n), _stream(stream)))
+        return buf.raw[:n.value]
+
+    def state_load(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check("ddgi_state_load", self.L.ddgi_state_load(self.h, buf, len(blob), _stream(stream)))
 
     # --- probe update (Sec. 3.2) ---
     def probe_update(self, frame, stream=None):
