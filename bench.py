@@ -162,6 +162,24 @@ BYTES_PER_PX = {
 }
 
 
+def job_time_ms(local_ms: float, ws: int, device) -> float:
+    """The job's timed region: the slowest rank's (every rank renders its own
+    replica; the reduction is the only cross-rank traffic)."""
+    if ws == 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def frame_times(total_ms: float, steps: int, ws: int):
+    """(ms per step on the slowest rank, whole-job ms per frame): ws replicas
+    render ws frames per step."""
+    return total_ms / steps, total_ms / (steps * ws)
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -253,12 +271,7 @@ def run_ours(args, ws, rank, local):
     t1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    total_ms = t0.elapsed_time(t1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_time_ms(t0.elapsed_time(t1), ws, dev)
     per_pass = {p: 0.0 for p in passes}
     for k in range(K):
         for i, p in enumerate(passes):
@@ -291,8 +304,7 @@ def run_ours(args, ws, rank, local):
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None}
 
-    ms_frame = total_ms / K
-    value = total_ms / (K * ws)
+    ms_frame, value = frame_times(total_ms, K, ws)
     out = {"metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": ws,
            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_frame, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
