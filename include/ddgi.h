@@ -45,6 +45,7 @@ typedef int32_t ddgi_status;
 #define DDGI_ERR_TRAVERSAL_LIMIT (-4)
 #define DDGI_ERR_BOUNDS (-5)
 #define DDGI_ERR_OOM (-6)
+#define DDGI_ERR_DEVICE_WAIT (-7)   /* a device-side wait hit its iteration bound */
 
 typedef struct ddgi_ctx ddgi_ctx;
 
@@ -357,8 +358,11 @@ ddgi_status ddgi_mlp_samples_get(ddgi_ctx* ctx, float* out, void* stream);
 ddgi_status ddgi_mlp_status(ddgi_ctx* ctx, double* out, void* stream);
 
 /* Synchronise `stream`, return (and clear) the device error word:
- * DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded the node-visit cap or the
- * traversal stack, else DDGI_OK. */
+ * DDGI_ERR_DEVICE_WAIT if a network kernel's wait for its tensor-core
+ * results ran past its iteration bound (the kernel then skipped its
+ * remaining work and released its tensor memory), DDGI_ERR_TRAVERSAL_LIMIT
+ * if a ray exceeded the node-visit cap or the traversal stack, else
+ * DDGI_OK. */
 ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream);
 const char* ddgi_last_error(ddgi_ctx* ctx);
 

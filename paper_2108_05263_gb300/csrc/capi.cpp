@@ -317,6 +317,7 @@ MLPView mlp_view(ddgi_ctx* c, bool served = true) {
     m.params = served ? c->mlp_ema : c->mlp_params;
     for (int a = 0; a < 3; ++a) m.lo[a] = c->mlp_lo[a];
     m.scale = c->mlp_scale;
+    m.err = c->err;
     return m;
 }
 
@@ -1187,6 +1188,10 @@ ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream) {
     CK(cudaMemcpyAsync(w, ctx->err, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaMemsetAsync(ctx->err, 0, sizeof(w), st));
     CK(cudaStreamSynchronize(st));
+    if (w[0] & ERRBIT_MMA_WAIT) {
+        ctx->last_error = "tensor-core completion wait ran past its bound";
+        return DDGI_ERR_DEVICE_WAIT;
+    }
     if (w[0] & (ERRBIT_TRAVERSAL | ERRBIT_STACK)) {
         ctx->last_error = (w[0] & ERRBIT_STACK) ? "traversal stack overflow" : "traversal visit limit";
         return DDGI_ERR_TRAVERSAL_LIMIT;

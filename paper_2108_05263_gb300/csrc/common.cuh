@@ -19,6 +19,7 @@
 // device error word bits
 #define ERRBIT_TRAVERSAL 1u
 #define ERRBIT_STACK 2u
+#define ERRBIT_MMA_WAIT 4u   // a tensor-core completion wait ran past its bound
 
 // ---------------------------------------------------------------------------
 // small vector helpers
