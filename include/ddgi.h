@@ -100,6 +100,8 @@ typedef struct {
                                    * the old average (the probes' hysteresis 0.97 is
                                    * the default); 0 serves the trained weights */
     uint32_t probe_relocation;    /* 1: ddgi_probe_update ends with ddgi_probe_relocate */
+    uint32_t mlp_bf16;            /* network weights and activations in bf16 (1) or fp16 (0),
+                                   * fp32 accumulation either way */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */

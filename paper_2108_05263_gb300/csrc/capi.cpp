@@ -44,9 +44,9 @@ struct ddgi_ctx {
     float* mlp_grad = nullptr;
     float* mlp_m = nullptr;
     float* mlp_v = nullptr;
-    __half* mlp_w16 = nullptr;     // fp16 weights [MLP_NW]
+    uint16_t* mlp_w16 = nullptr;   // 16-bit weights (fp16 or bf16 bits) [MLP_NW]
     float* mlp_ema = nullptr;      // served network: moving average of the master weights
-    __half* mlp_w16s = nullptr;    // its fp16 weights
+    uint16_t* mlp_w16s = nullptr;  // its 16-bit weights
     MLPState* mlp_state = nullptr;
     float4* train_smp = nullptr;   // [train_samples][3]
     float4* train_sf = nullptr;    // [train_per]
@@ -318,6 +318,7 @@ MLPView mlp_view(ddgi_ctx* c, bool served = true) {
     for (int a = 0; a < 3; ++a) m.lo[a] = c->mlp_lo[a];
     m.scale = c->mlp_scale;
     m.err = c->err;
+    m.bf16 = c->cfg.mlp_bf16 ? 1 : 0;
     return m;
 }
 
@@ -337,12 +338,14 @@ void mlp_init(uint32_t seed, std::vector<float>& p) {
 }
 
 cudaError_t mlp_upload(ddgi_ctx* c, const float* host_params) {
-    std::vector<__half> h(MLP_NW);
-    for (int i = 0; i < MLP_NW; ++i) h[i] = __float2half_rn(host_params[i]);
+    std::vector<uint16_t> h(MLP_NW);
+    for (int i = 0; i < MLP_NW; ++i)
+        h[i] = c->cfg.mlp_bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(host_params[i]))
+                               : __half_as_ushort(__float2half_rn(host_params[i]));
     cudaError_t e = cudaMemcpy(c->mlp_params, host_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault);
-    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16, h.data(), MLP_NW * sizeof(__half), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16, h.data(), MLP_NW * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->mlp_ema, host_params, MLP_NPARAM * sizeof(float), cudaMemcpyDefault);
-    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16s, h.data(), MLP_NW * sizeof(__half), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16s, h.data(), MLP_NW * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->mlp_m, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_v, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, MLP_NPARAM * sizeof(float));
@@ -498,7 +501,7 @@ StateLayout state_layout(const ddgi_ctx* c) {
     L.mlp16 = L.mst = o;
     if (c->cfg.learned_target) {
         o += 4ull * MLP_NPARAM * sizeof(float);
-        L.mlp16 = o; o += 2ull * MLP_NW * sizeof(__half);
+        L.mlp16 = o; o += 2ull * MLP_NW * sizeof(uint16_t);
         L.mst = o; o += sizeof(MLPState);
     }
     L.total = o;
@@ -875,8 +878,8 @@ ddgi_status ddgi_state_save(ddgi_ctx* ctx, void* host_buf, size_t* bytes, void* 
         for (int k = 0; k < 4; ++k)
             CK(cudaMemcpyAsync(b + L.mlp32 + k * MLP_NPARAM * sizeof(float), src32[k], MLP_NPARAM * sizeof(float),
                                cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(b + L.mlp16, ctx->mlp_w16, MLP_NW * sizeof(__half), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(b + L.mlp16 + MLP_NW * sizeof(__half), ctx->mlp_w16s, MLP_NW * sizeof(__half),
+        CK(cudaMemcpyAsync(b + L.mlp16, ctx->mlp_w16, MLP_NW * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b + L.mlp16 + MLP_NW * sizeof(uint16_t), ctx->mlp_w16s, MLP_NW * sizeof(uint16_t),
                            cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(b + L.mst, ctx->mlp_state, sizeof(MLPState), cudaMemcpyDeviceToHost, st));
     }
@@ -922,8 +925,8 @@ ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, v
         for (int k = 0; k < 4; ++k)
             CK(cudaMemcpyAsync(dst32[k], b + L.mlp32 + k * MLP_NPARAM * sizeof(float), MLP_NPARAM * sizeof(float),
                                cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(ctx->mlp_w16, b + L.mlp16, MLP_NW * sizeof(__half), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(ctx->mlp_w16s, b + L.mlp16 + MLP_NW * sizeof(__half), MLP_NW * sizeof(__half),
+        CK(cudaMemcpyAsync(ctx->mlp_w16, b + L.mlp16, MLP_NW * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->mlp_w16s, b + L.mlp16 + MLP_NW * sizeof(uint16_t), MLP_NW * sizeof(uint16_t),
                            cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(ctx->mlp_state, b + L.mst, sizeof(MLPState), cudaMemcpyHostToDevice, st));
     }

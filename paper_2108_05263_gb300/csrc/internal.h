@@ -95,19 +95,19 @@ cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, floa
 // average, blended with weight ema_a on the old average after the steps)
 cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const MLPView& ms,
                                    const TrainParams& tp, float4* smp, float2* hits, uint32_t* counter,
-                                   MLPState* state, float* params, float* grad, float* mom, float* vel, __half* w16,
-                                   float* ema, __half* w16s, float ema_a, float lr, uint32_t step, int serve,
+                                   MLPState* state, float* params, float* grad, float* mom, float* vel, uint16_t* w16,
+                                   float* ema, uint16_t* w16s, float ema_a, float lr, uint32_t step, int serve,
                                    cudaStream_t st);
 cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st);
 cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                                  float* out, cudaStream_t st);
 cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* params,
-                            float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
+                            float* grad, float* mom, float* vel, uint16_t* w16, float lr, uint32_t step,
                             cudaStream_t st);
 cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                             cudaStream_t st);
-cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, __half* w16, MLPState* state,
-                            float lr, uint32_t step, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, uint16_t* w16, int bf16,
+                            MLPState* state, float lr, uint32_t step, cudaStream_t st);
 
 cudaError_t launch_reference(const SceneView& s, const CamView& cam, uint32_t seed, uint32_t sample0,
                              uint32_t spp, uint32_t max_depth, double* accum, float4* mean, cudaStream_t st);

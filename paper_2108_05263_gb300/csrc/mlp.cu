@@ -36,7 +36,7 @@ size_t train_smem() {
 }
 
 template <int KT>
-__device__ __forceinline__ void store_frags(__half* s, int ld, int rowbase, const uint32_t (&a)[2][KT][4],
+__device__ __forceinline__ void store_frags(uint16_t* s, int ld, int rowbase, const uint32_t (&a)[2][KT][4],
                                             int g, int t) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -54,36 +54,36 @@ __device__ __forceinline__ void store_frags(__half* s, int ld, int rowbase, cons
 
 // acc[m = samples][n = layer input] = d[m][k = layer output] x W[k][n];
 // W in shared memory [out][ld]; rows >= OUT_ROWS read as 0
-template <int KT, int NT, int OUT_ROWS>
-__device__ __forceinline__ void bwd_data(const __half* __restrict__ sW, int ld, const uint32_t (&d)[2][KT][4],
+template <bool BF, int KT, int NT, int OUT_ROWS>
+__device__ __forceinline__ void bwd_data(const uint16_t* __restrict__ sW, int ld, const uint32_t (&d)[2][KT][4],
                                          float (&acc)[2][NT][4], int g, int t) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
-    const __half z = __float2half(0.f);
+    const uint16_t z = 0;
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt) {
         const int k0 = kt * 16 + 2 * t;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
             const int col = nt * 8 + g;
-            __half w0 = k0 < OUT_ROWS ? sW[k0 * ld + col] : z;
-            __half w1 = k0 + 1 < OUT_ROWS ? sW[(k0 + 1) * ld + col] : z;
-            __half w2 = k0 + 8 < OUT_ROWS ? sW[(k0 + 8) * ld + col] : z;
-            __half w3 = k0 + 9 < OUT_ROWS ? sW[(k0 + 9) * ld + col] : z;
+            uint16_t w0 = k0 < OUT_ROWS ? sW[k0 * ld + col] : z;
+            uint16_t w1 = k0 + 1 < OUT_ROWS ? sW[(k0 + 1) * ld + col] : z;
+            uint16_t w2 = k0 + 8 < OUT_ROWS ? sW[(k0 + 8) * ld + col] : z;
+            uint16_t w3 = k0 + 9 < OUT_ROWS ? sW[(k0 + 9) * ld + col] : z;
             uint32_t b0 = h2_from(w0, w1), b1 = h2_from(w2, w3);
-            mma16816(acc[0][nt], d[0][kt], b0, b1);
-            mma16816(acc[1][nt], d[1][kt], b0, b1);
+            H16<BF>::mma(acc[0][nt], d[0][kt], b0, b1);
+            H16<BF>::mma(acc[1][nt], d[1][kt], b0, b1);
         }
     }
 }
 
 // ReLU derivative from the stored activations of the layer input, then the
 // masked deltas as A fragments (k-tiles of 16 outputs) and into sD
-template <int NT>
-__device__ __forceinline__ void mask_delta(const float (&acc)[2][NT][4], const __half* sAct, int ld_act,
-                                           __half* sD, int ld_d, int rowbase, uint32_t (&d)[2][NT / 2][4],
+template <bool BF, int NT>
+__device__ __forceinline__ void mask_delta(const float (&acc)[2][NT][4], const uint16_t* sAct, int ld_act,
+                                           uint16_t* sD, int ld_d, int rowbase, uint32_t (&d)[2][NT / 2][4],
                                            int g, int t) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -91,13 +91,13 @@ __device__ __forceinline__ void mask_delta(const float (&acc)[2][NT][4], const _
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
             int c = nt * 8 + 2 * t;
-            __half2 a0 = *reinterpret_cast<const __half2*>(sAct + r0 * ld_act + c);
-            __half2 a1 = *reinterpret_cast<const __half2*>(sAct + r1 * ld_act + c);
-            float v0 = __low2float(a0) > 0.f ? acc[mt][nt][0] : 0.f;
-            float v1 = __high2float(a0) > 0.f ? acc[mt][nt][1] : 0.f;
-            float v2 = __low2float(a1) > 0.f ? acc[mt][nt][2] : 0.f;
-            float v3 = __high2float(a1) > 0.f ? acc[mt][nt][3] : 0.f;
-            uint32_t p0 = pack_h2(v0, v1), p1 = pack_h2(v2, v3);
+            const uint16_t* a0 = sAct + r0 * ld_act + c;
+            const uint16_t* a1 = sAct + r1 * ld_act + c;
+            float v0 = H16<BF>::val(a0[0]) > 0.f ? acc[mt][nt][0] : 0.f;
+            float v1 = H16<BF>::val(a0[1]) > 0.f ? acc[mt][nt][1] : 0.f;
+            float v2 = H16<BF>::val(a1[0]) > 0.f ? acc[mt][nt][2] : 0.f;
+            float v3 = H16<BF>::val(a1[1]) > 0.f ? acc[mt][nt][3] : 0.f;
+            uint32_t p0 = H16<BF>::pack(v0, v1), p1 = H16<BF>::pack(v2, v3);
             *reinterpret_cast<uint32_t*>(sD + r0 * ld_d + c) = p0;
             *reinterpret_cast<uint32_t*>(sD + r1 * ld_d + c) = p1;
             d[mt][nt >> 1][(nt & 1) ? 2 : 0] = p0;
@@ -108,8 +108,8 @@ __device__ __forceinline__ void mask_delta(const float (&acc)[2][NT][4], const _
 
 // weight gradient of one 16-row output tile: grad[o][i] += sum_s D[s][o] * A[s][i]
 // over the 128 samples of the block (8 k-tiles)
-template <int NT>
-__device__ __forceinline__ void wgrad_tile(const __half* sD, int ld_d, int o0, int out_real, const __half* sA,
+template <bool BF, int NT>
+__device__ __forceinline__ void wgrad_tile(const uint16_t* sD, int ld_d, int o0, int out_real, const uint16_t* sA,
                                            int ld_a, int in, float* grad_w, int g, int t) {
     float acc[NT][4];
 #pragma unroll
@@ -127,7 +127,7 @@ __device__ __forceinline__ void wgrad_tile(const __half* sD, int ld_d, int o0, i
             const int col = nt * 8 + g;
             uint32_t b0 = h2_from(sA[s0 * ld_a + col], sA[(s0 + 1) * ld_a + col]);
             uint32_t b1 = h2_from(sA[(s0 + 8) * ld_a + col], sA[(s0 + 9) * ld_a + col]);
-            mma16816(acc[nt], a, b0, b1);
+            H16<BF>::mma(acc[nt], a, b0, b1);
         }
     }
 #pragma unroll
@@ -145,31 +145,42 @@ __device__ __forceinline__ void wgrad_tile(const __half* sD, int ld_d, int o0, i
     }
 }
 
-__device__ __forceinline__ void bias_grad(const __half* sD, int ld_d, int out_real, float* grad_b) {
-    for (int o = threadIdx.x; o < out_real; o += blockDim.x) {
-        float s = 0.f;
-        for (int r = 0; r < kTrainRows; ++r) s += __half2float(sD[r * ld_d + o]);
-        atomicAdd(grad_b + o, s);
+// bias gradient: column sums of the deltas; thread (o, part) sums the rows
+// part, part + P, ... of output o, P = blockDim / 64 partial sums per output
+template <bool BF>
+__device__ __forceinline__ void bias_grad(const uint16_t* sD, int ld_d, int out_real, float* grad_b) {
+    const int o = threadIdx.x & 63, part = threadIdx.x >> 6, P = blockDim.x >> 6;
+    if (o >= out_real) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int r = part;
+    for (; r + 3 * P < kTrainRows; r += 4 * P) {
+        s0 += H16<BF>::val(sD[r * ld_d + o]);
+        s1 += H16<BF>::val(sD[(r + P) * ld_d + o]);
+        s2 += H16<BF>::val(sD[(r + 2 * P) * ld_d + o]);
+        s3 += H16<BF>::val(sD[(r + 3 * P) * ld_d + o]);
     }
+    for (; r < kTrainRows; r += P) s0 += H16<BF>::val(sD[r * ld_d + o]);
+    atomicAdd(grad_b + o, (s0 + s1) + (s2 + s3));
 }
 
 // samples [n][3] float4: (y.xyz, _), (n.xyz, _), (target.rgb, weight); weight 0
 // excludes a sample.  Gradients of sum_s w_s sum_c (f - t)^2 / (sg(f)^2 + 0.01)
 // times the loss scale are added to grad; the weights are summed into
 // st->count.
+template <bool BF>
 __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train(MLPView m, const float4* __restrict__ smp,
                                                             uint32_t n, MLPState* __restrict__ st,
                                                             float* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __half* sW = reinterpret_cast<__half*>(smem_raw);
+    uint16_t* sW = reinterpret_cast<uint16_t*>(smem_raw);
     float* sb = reinterpret_cast<float*>(sW + MLP_SW_HALVES);
-    __half* sA0 = reinterpret_cast<__half*>(sb + 264);
-    __half* sA[5];
+    uint16_t* sA0 = reinterpret_cast<uint16_t*>(sb + 264);
+    uint16_t* sA[5];
     sA[0] = sA0;
     sA[1] = sA0 + kTrainRows * MLP_LD_IN;
     for (int l = 2; l < 5; ++l) sA[l] = sA[l - 1] + kTrainRows * MLP_LD_H;
-    __half* sD = sA[4] + kTrainRows * MLP_LD_H;
-    __half* sD5 = sD + kTrainRows * MLP_LD_H;
+    uint16_t* sD = sA[4] + kTrainRows * MLP_LD_H;
+    uint16_t* sD5 = sD + kTrainRows * MLP_LD_H;
     float* sq_all = reinterpret_cast<float*>(sD5 + kTrainRows * kLdD5);
     float* st_all = sq_all + kTrainRows * 8;
 
@@ -203,20 +214,20 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train(MLPView m, const fl
     float out[2][1][4];
     {
         uint32_t a0[2][5][4];
-        mlp_input_frags(sq, a0, g, t);
+        mlp_input_frags<BF>(sq, a0, g, t);
         store_frags<5>(sA[0], MLP_LD_IN, rowbase, a0, g, t);
         float acc[2][8][4];
         uint32_t a[2][4][4];
-        mlp_layer<5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
-        relu_to_frags<8>(acc, a);
+        mlp_layer<BF, 5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
+        relu_to_frags<BF, 8>(acc, a);
         store_frags<4>(sA[1], MLP_LD_H, rowbase, a, g, t);
 #pragma unroll
         for (int l = 1; l < 4; ++l) {
-            mlp_layer<4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
-            relu_to_frags<8>(acc, a);
+            mlp_layer<BF, 4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
+            relu_to_frags<BF, 8>(acc, a);
             store_frags<4>(sA[l + 1], MLP_LD_H, rowbase, a, g, t);
         }
-        mlp_layer<4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
+        mlp_layer<BF, 4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
     }
 
     // ---- output gradient (relative L2, denominator held constant) -------------
@@ -234,8 +245,8 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train(MLPView m, const fl
             const float* q = st_all + row * 4;
             v[e] = col < 3 ? q[3] * S * 2.f * (f - q[col]) / (f * f + 0.01f) : 0.f;
         }
-        d5[mt][0][0] = pack_h2(v[0], v[1]);
-        d5[mt][0][1] = pack_h2(v[2], v[3]);
+        d5[mt][0][0] = H16<BF>::pack(v[0], v[1]);
+        d5[mt][0][1] = H16<BF>::pack(v[2], v[3]);
         d5[mt][0][2] = 0u;
         d5[mt][0][3] = 0u;
         *reinterpret_cast<uint32_t*>(sD5 + r0 * kLdD5 + 2 * t) = d5[mt][0][0];
@@ -245,30 +256,30 @@ __global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train(MLPView m, const fl
     }
     __syncthreads();
     // output layer: M = 16 (3 real rows), N = 64, split over the 4 warps
-    if (warp == 0) wgrad_tile<8>(sD5, kLdD5, 0, 3, sA[4], MLP_LD_H, 64, grad + mlp_off_w(4), g, t);
-    bias_grad(sD5, kLdD5, 3, grad + mlp_off_b(4));
+    if (warp == 0) wgrad_tile<BF, 8>(sD5, kLdD5, 0, 3, sA[4], MLP_LD_H, 64, grad + mlp_off_w(4), g, t);
+    bias_grad<BF>(sD5, kLdD5, 3, grad + mlp_off_b(4));
 
     // ---- hidden layers, last to first -----------------------------------------
     uint32_t d[2][4][4];
     {
         float acc[2][8][4];
-        bwd_data<1, 8, 8>(sW + mlp_soff(4), MLP_LD_H, d5, acc, g, t);
+        bwd_data<BF, 1, 8, 8>(sW + mlp_soff(4), MLP_LD_H, d5, acc, g, t);
         __syncthreads();
-        mask_delta<8>(acc, sA[4], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
+        mask_delta<BF, 8>(acc, sA[4], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
     }
     for (int l = 3; l >= 0; --l) {
         __syncthreads();
         // gradient of layer l (input sA[l], output deltas in sD)
         if (l == 0)
-            wgrad_tile<10>(sD, MLP_LD_H, warp * 16, 64, sA[0], MLP_LD_IN, 80, grad + mlp_off_w(0), g, t);
+            wgrad_tile<BF, 10>(sD, MLP_LD_H, warp * 16, 64, sA[0], MLP_LD_IN, 80, grad + mlp_off_w(0), g, t);
         else
-            wgrad_tile<8>(sD, MLP_LD_H, warp * 16, 64, sA[l], MLP_LD_H, 64, grad + mlp_off_w(l), g, t);
-        bias_grad(sD, MLP_LD_H, 64, grad + mlp_off_b(l));
+            wgrad_tile<BF, 8>(sD, MLP_LD_H, warp * 16, 64, sA[l], MLP_LD_H, 64, grad + mlp_off_w(l), g, t);
+        bias_grad<BF>(sD, MLP_LD_H, 64, grad + mlp_off_b(l));
         if (l == 0) break;
         float acc[2][8][4];
-        bwd_data<4, 8, 64>(sW + mlp_soff(l), MLP_LD_H, d, acc, g, t);
+        bwd_data<BF, 4, 8, 64>(sW + mlp_soff(l), MLP_LD_H, d, acc, g, t);
         __syncthreads();
-        mask_delta<8>(acc, sA[l], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
+        mask_delta<BF, 8>(acc, sA[l], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
     }
 }
 
@@ -287,7 +298,7 @@ __global__ void k_mlp_check(const float* __restrict__ grad, MLPState* st) {
 }
 
 __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ grad, float* __restrict__ mom,
-                           float* __restrict__ vel, __half* __restrict__ w16, MLPState* st, float lr,
+                           float* __restrict__ vel, uint16_t* __restrict__ w16, int bf16, MLPState* st, float lr,
                            float b1, float b2, float eps, uint32_t step) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool overflow = st->overflow != 0;
@@ -303,7 +314,7 @@ __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ grad,
             const float vh = vv / (1.f - powf(b2, (float)step));
             const float p = params[i] - lr * mh / (sqrtf(vh) + eps);
             params[i] = p;
-            if (i < MLP_NW) w16[i] = __float2half_rn(p);
+            if (i < MLP_NW) w16[i] = bf16 ? H16<true>::bits(p) : H16<false>::bits(p);
         }
         grad[i] = 0.f;
     }
@@ -475,13 +486,14 @@ __global__ void k_mlp_judge(MLPState* st, int serve) {
 }
 
 // served network: ema <- a ema + (1 - a) params, fp16 copy of its weights
-__global__ void k_mlp_ema(const float* __restrict__ params, float* __restrict__ ema, __half* __restrict__ w16s,
+__global__ void k_mlp_ema(const float* __restrict__ params, float* __restrict__ ema, uint16_t* __restrict__ w16s,
+                          int bf16,
                           float a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < MLP_NPARAM) {
         const float e = a * ema[i] + (1.f - a) * params[i];
         ema[i] = e;
-        if (i < MLP_NW) w16s[i] = __float2half_rn(e);
+        if (i < MLP_NW) w16s[i] = bf16 ? H16<true>::bits(e) : H16<false>::bits(e);
     }
 }
 
@@ -505,35 +517,42 @@ cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, floa
                             n, st);
 }
 
-cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
-                            cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
+template <bool BF>
+cudaError_t launch_mlp_grad_t(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
+                              cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_train<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)train_smem());
         if (e != cudaSuccess) return e;
         attr = true;
     }
     uint32_t grid = (n + kTrainRows - 1) / kTrainRows;
-    k_mlp_train<<<grid, kTrainRows, train_smem(), st>>>(m, smp, n, state, grad);
+    k_mlp_train<BF><<<grid, kTrainRows, train_smem(), st>>>(m, smp, n, state, grad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, __half* w16, MLPState* state,
-                            float lr, uint32_t step, cudaStream_t st) {
+cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
+                            cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    return m.bf16 ? launch_mlp_grad_t<true>(m, smp, n, state, grad, st)
+                  : launch_mlp_grad_t<false>(m, smp, n, state, grad, st);
+}
+
+cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, uint16_t* w16, int bf16,
+                            MLPState* state, float lr, uint32_t step, cudaStream_t st) {
     k_mlp_check<<<1, 1024, 0, st>>>(grad, state);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, grad, mom, vel, w16, state, lr, 0.9f, 0.99f,
-                                                           1e-8f, step);
+    k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, grad, mom, vel, w16, bf16, state, lr, 0.9f,
+                                                           0.99f, 1e-8f, step);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, const MLPView& m, const MLPView& ms,
                                    const TrainParams& tp, float4* smp, float2* hits, uint32_t* counter,
-                                   MLPState* state, float* params, float* grad, float* mom, float* vel, __half* w16,
-                                   float* ema, __half* w16s, float ema_a, float lr, uint32_t step, int serve,
+                                   MLPState* state, float* params, float* grad, float* mom, float* vel, uint16_t* w16,
+                                   float* ema, uint16_t* w16s, float ema_a, float lr, uint32_t step, int serve,
                                    cudaStream_t st) {
     k_mlp_begin<<<1, 1, 0, st>>>(state);
     k_train_primary<<<(tp.samples + 127) / 128, 128, 0, st>>>(s, v, tp, smp);
@@ -549,10 +568,10 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
         k_mlp_count_reset<<<1, 1, 0, st>>>(state);
         e = launch_mlp_grad(m, smp + 3 * (size_t)b0, nb, state, grad, st);
         if (e != cudaSuccess) return e;
-        e = launch_mlp_adam(params, grad, mom, vel, w16, state, lr, step + k, st);
+        e = launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step + k, st);
         if (e != cudaSuccess) return e;
     }
-    k_mlp_ema<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, ema, w16s, ema_a);
+    k_mlp_ema<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, ema, w16s, m.bf16, ema_a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the judge compares the served network with the probes on held-out samples
@@ -581,10 +600,10 @@ cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n
 }
 
 cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* params,
-                            float* grad, float* mom, float* vel, __half* w16, float lr, uint32_t step,
+                            float* grad, float* mom, float* vel, uint16_t* w16, float lr, uint32_t step,
                             cudaStream_t st) {
     k_mlp_begin<<<1, 1, 0, st>>>(state);
     cudaError_t e = launch_mlp_grad(m, smp, n, state, grad, st);
     if (e != cudaSuccess) return e;
-    return launch_mlp_adam(params, grad, mom, vel, w16, state, lr, step, st);
+    return launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step, st);
 }

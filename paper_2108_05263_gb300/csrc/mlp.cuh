@@ -8,6 +8,7 @@
 // Shared-memory weights use padded row strides (88 / 72 halves) so that the
 // fragment loads of a warp hit distinct banks.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -46,58 +47,101 @@ struct MLPState {
 };
 
 struct MLPView {
-    const __half* w16;     // [MLP_NW] fp16 weights, unpadded rows
+    const uint16_t* w16;   // [MLP_NW] 16-bit weights (fp16 or bf16 bits), unpadded rows
     const float* params;   // [MLP_NPARAM] fp32 master (biases read from here)
     float lo[3];           // position normalisation p' = (p - lo) * scale
     float scale;
     uint32_t* err;         // device error word (bounded waits)
+    int bf16;              // 1: weights and activations are bf16, else fp16
 };
 
-__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
+// The network's 16-bit formats: fp16 (BF = false) or bf16 (BF = true), both
+// with fp32 accumulation.  Values travel as raw 16-bit words.
+template <bool BF>
+struct H16;
 
-__device__ __forceinline__ uint32_t h2_from(__half a, __half b) {
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
+template <>
+struct H16<false> {
+    static constexpr uint32_t umma_fmt = 0u;   // kind::f16 operand format code
+    __device__ static __forceinline__ uint32_t pack(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ static __forceinline__ uint16_t bits(float a) { return __half_as_ushort(__float2half_rn(a)); }
+    __device__ static __forceinline__ float val(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+    // two fp32 -> packed pair with ReLU (negative values and -0 become +0)
+    __device__ static __forceinline__ uint32_t relu2(uint32_t lo, uint32_t hi) {
+        uint32_t r;
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(lo));
+        return r;
+    }
+    __device__ static __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+};
 
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+template <>
+struct H16<true> {
+    static constexpr uint32_t umma_fmt = 1u;
+    __device__ static __forceinline__ uint32_t pack(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+    __device__ static __forceinline__ uint16_t bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    __device__ static __forceinline__ float val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+    __device__ static __forceinline__ uint32_t relu2(uint32_t lo, uint32_t hi) {
+        uint32_t r;
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(lo));
+        return r;
+    }
+    __device__ static __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+};
+
+__device__ __forceinline__ uint32_t h2_from(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
+
 
 // Copy the fp16 weights into padded shared rows and the biases (fp32).
-__device__ __forceinline__ void mlp_load_smem(const MLPView& m, __half* sW, float* sb) {
-    for (int e = threadIdx.x; e < MLP_NW; e += blockDim.x) {
-        int l = e < 5120 ? 0 : (e < 9216 ? 1 : (e < 13312 ? 2 : (e < 17408 ? 3 : 4)));
-        int r = e - mlp_off_w(l);
-        int in = mlp_in(l);
-        int o = r / in, i = r - o * in;
-        sW[mlp_soff(l) + o * mlp_ld(l) + i] = m.w16[e];
+__device__ __forceinline__ void mlp_load_smem(const MLPView& m, uint16_t* sW, float* sb) {
+    // 16-byte chunks (rows of 80 / 64 halves hold whole chunks; padded rows of
+    // 88 / 72 halves keep them 16-byte aligned)
+    for (int c = threadIdx.x; c < MLP_NW / 8; c += blockDim.x) {
+        const int e = 8 * c;
+        const int l = e < 5120 ? 0 : (e < 9216 ? 1 : (e < 13312 ? 2 : (e < 17408 ? 3 : 4)));
+        const int r = e - mlp_off_w(l), in = mlp_in(l);
+        const int o = r / in, i = r - o * in;
+        *reinterpret_cast<uint4*>(sW + mlp_soff(l) + o * mlp_ld(l) + i) = *reinterpret_cast<const uint4*>(m.w16 + e);
     }
     for (int e = threadIdx.x; e < 264; e += blockDim.x) sb[e] = m.params[17920 + e];
 }
 
 // feature pair (c, c+1) of the input encoding (c even): sin / cos of
 // 2^k pi p'_a for c < 72, the normal for c = 72, 74, zeros beyond
+template <bool BF>
 __device__ __forceinline__ uint32_t feature_pair(const float* q, int c) {
     if (c < 72) {
         int a = c / 24, k = (c % 24) >> 1;
         float sn, cs;
         sincospif(ldexpf(q[a], k), &sn, &cs);
-        return pack_h2(sn, cs);
+        return H16<BF>::pack(sn, cs);
     }
-    if (c == 72) return pack_h2(q[3], q[4]);
-    if (c == 74) return pack_h2(q[5], 0.f);
+    if (c == 72) return H16<BF>::pack(q[3], q[4]);
+    if (c == 74) return H16<BF>::pack(q[5], 0.f);
     return 0u;
 }
 
 // A fragments of the encoded inputs of a warp's 32 samples (2 m-tiles);
 // sq: per-sample (p'.xyz, n.xyz, valid, 0) rows of 8 floats.
+template <bool BF>
 __device__ __forceinline__ void mlp_input_frags(const float* sq, uint32_t (&a)[2][5][4], int g, int t) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -106,18 +150,18 @@ __device__ __forceinline__ void mlp_input_frags(const float* sq, uint32_t (&a)[2
 #pragma unroll
         for (int kt = 0; kt < 5; ++kt) {
             int c = kt * 16 + 2 * t;
-            a[mt][kt][0] = feature_pair(q0, c);
-            a[mt][kt][1] = feature_pair(q1, c);
-            a[mt][kt][2] = feature_pair(q0, c + 8);
-            a[mt][kt][3] = feature_pair(q1, c + 8);
+            a[mt][kt][0] = feature_pair<BF>(q0, c);
+            a[mt][kt][1] = feature_pair<BF>(q1, c);
+            a[mt][kt][2] = feature_pair<BF>(q0, c + 8);
+            a[mt][kt][3] = feature_pair<BF>(q1, c + 8);
         }
     }
 }
 
 // acc = bias + A x W^T for one layer (KT k-tiles of the input, NT n-tiles of
 // the output), W in shared memory [out][ld] fp16
-template <int KT, int NT>
-__device__ __forceinline__ void mlp_layer(const __half* __restrict__ sW, int ld, const float* __restrict__ sb,
+template <bool BF, int KT, int NT>
+__device__ __forceinline__ void mlp_layer(const uint16_t* __restrict__ sW, int ld, const float* __restrict__ sb,
                                           const uint32_t (&a)[2][KT][4], float (&acc)[2][NT][4], int g, int t) {
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
@@ -134,18 +178,18 @@ __device__ __forceinline__ void mlp_layer(const __half* __restrict__ sW, int ld,
     for (int kt = 0; kt < KT; ++kt) {
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-            const __half* w = sW + (nt * 8 + g) * ld + kt * 16 + 2 * t;
+            const uint16_t* w = sW + (nt * 8 + g) * ld + kt * 16 + 2 * t;
             uint32_t b0 = *reinterpret_cast<const uint32_t*>(w);
             uint32_t b1 = *reinterpret_cast<const uint32_t*>(w + 8);
-            mma16816(acc[0][nt], a[0][kt], b0, b1);
-            mma16816(acc[1][nt], a[1][kt], b0, b1);
+            H16<BF>::mma(acc[0][nt], a[0][kt], b0, b1);
+            H16<BF>::mma(acc[1][nt], a[1][kt], b0, b1);
         }
     }
 }
 
 // ReLU and conversion of an output (D) fragment set into the A fragments of
 // the next layer: output n-tiles 2k and 2k+1 form input k-tile k.
-template <int NT>
+template <bool BF, int NT>
 __device__ __forceinline__ void relu_to_frags(const float (&acc)[2][NT][4], uint32_t (&a)[2][NT / 2][4]) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -153,29 +197,30 @@ __device__ __forceinline__ void relu_to_frags(const float (&acc)[2][NT][4], uint
         for (int k = 0; k < NT / 2; ++k) {
             const float* lo = acc[mt][2 * k];
             const float* hi = acc[mt][2 * k + 1];
-            a[mt][k][0] = pack_h2(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
-            a[mt][k][1] = pack_h2(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
-            a[mt][k][2] = pack_h2(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
-            a[mt][k][3] = pack_h2(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
+            a[mt][k][0] = H16<BF>::pack(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
+            a[mt][k][1] = H16<BF>::pack(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
+            a[mt][k][2] = H16<BF>::pack(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
+            a[mt][k][3] = H16<BF>::pack(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
         }
 }
 
 // Full forward pass of a warp's 32 samples; out: acc of the output layer
 // (rows g / g+8 of each m-tile, columns 2t, 2t+1 of 8).
-__device__ __forceinline__ void mlp_forward(const __half* sW, const float* sb, const float* sq,
+template <bool BF>
+__device__ __forceinline__ void mlp_forward(const uint16_t* sW, const float* sb, const float* sq,
                                             float (&out)[2][1][4], int g, int t) {
     uint32_t a0[2][5][4];
-    mlp_input_frags(sq, a0, g, t);
+    mlp_input_frags<BF>(sq, a0, g, t);
     float acc[2][8][4];
     uint32_t a[2][4][4];
-    mlp_layer<5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
-    relu_to_frags<8>(acc, a);
+    mlp_layer<BF, 5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
+    relu_to_frags<BF, 8>(acc, a);
 #pragma unroll
     for (int l = 1; l < 4; ++l) {
-        mlp_layer<4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
-        relu_to_frags<8>(acc, a);
+        mlp_layer<BF, 4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
+        relu_to_frags<BF, 8>(acc, a);
     }
-    mlp_layer<4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
+    mlp_layer<BF, 4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,10 +271,11 @@ __device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24
-__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor of kind::f16: fp32 accumulator, A and B of the
+// given format (0 fp16, 1 bf16) at bits 7 and 10, both K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -261,12 +307,6 @@ __device__ __forceinline__ int wg_or(int g, int pred) {
     return r;
 }
 
-// two fp32 -> fp16x2 with ReLU (negative values and -0 become +0)
-__device__ __forceinline__ uint32_t relu_h2(uint32_t a, uint32_t b) {
-    uint32_t r;
-    asm("cvt.rn.relu.f16x2.f32 %0, %2, %1;" : "=r"(r) : "r"(a), "r"(b));
-    return r;
-}
 
 #define TMEM_LD_X16(taddr, v, o)                                                                          \
     asm volatile(                                                                                        \
@@ -279,6 +319,7 @@ __device__ __forceinline__ uint32_t relu_h2(uint32_t a, uint32_t b) {
 
 // weights of layer l as [rows][80] fp16 in the canonical layout: the real
 // inputs, the bias (fp16) in column 75, zeros elsewhere; W5 padded to 16 rows
+template <bool BF>
 __device__ __forceinline__ void mlp_tc_load_weights(const MLPView& m, uint8_t* sm) {
     for (int e = threadIdx.x; e < 4 * 64 * MLP_TC_K + 16 * MLP_TC_K; e += blockDim.x) {
         const int l = e < 4 * 64 * MLP_TC_K ? e / (64 * MLP_TC_K) : 4;
@@ -286,10 +327,10 @@ __device__ __forceinline__ void mlp_tc_load_weights(const MLPView& m, uint8_t* s
         const int K = mlp_in(l), rows = l == 4 ? 3 : 64;
         float v = 0.f;
         if (r < rows) {
-            if (k < K && !(l == 0 && k >= 75)) v = __half2float(m.w16[mlp_off_w(l) + r * K + k]);
+            if (k < K && !(l == 0 && k >= 75)) v = H16<BF>::val(m.w16[mlp_off_w(l) + r * K + k]);
             else if (k == MLP_TC_ONE_COL) v = m.params[mlp_off_b(l) + r];
         }
-        *reinterpret_cast<__half*>(sm + MLP_TC_W_OFF(l) + kmajor_off(r, k)) = __float2half_rn(v);
+        *reinterpret_cast<uint16_t*>(sm + MLP_TC_W_OFF(l) + kmajor_off(r, k)) = H16<BF>::bits(v);
     }
 }
 
@@ -299,6 +340,7 @@ __device__ __forceinline__ void mlp_tc_load_weights(const MLPView& m, uint8_t* s
 // and doubled for the three frequencies after each (sin 2a = 2 sin a cos a,
 // cos 2a = (cos a - sin a)(cos a + sin a)): a few ulp of fp32, far below the
 // fp16 rounding of the features.
+template <bool BF>
 __device__ __forceinline__ void mlp_tc_encode_row(uint8_t* sA, int r, const float (&q)[6]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -307,13 +349,13 @@ __device__ __forceinline__ void mlp_tc_encode_row(uint8_t* sA, int r, const floa
         for (int k0 = 0; k0 < 12; k0 += 4) {
             float sn, cs;
             sincospif(q[a] * (float)(1 << k0), &sn, &cs);
-            w[k0] = pack_h2(sn, cs);
+            w[k0] = H16<BF>::pack(sn, cs);
 #pragma unroll
             for (int d = 1; d < 4; ++d) {
                 const float s2 = 2.f * sn * cs, c2 = (cs - sn) * (cs + sn);
                 sn = s2;
                 cs = c2;
-                w[k0 + d] = pack_h2(sn, cs);
+                w[k0 + d] = H16<BF>::pack(sn, cs);
             }
         }
 #pragma unroll
@@ -322,17 +364,17 @@ __device__ __forceinline__ void mlp_tc_encode_row(uint8_t* sA, int r, const floa
                 make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     }
     *reinterpret_cast<uint4*>(sA + kmajor_off(r, 72)) =
-        make_uint4(pack_h2(q[3], q[4]), pack_h2(q[5], 1.f), 0u, 0u);
+        make_uint4(H16<BF>::pack(q[3], q[4]), H16<BF>::pack(q[5], 1.f), 0u, 0u);
 }
 
-template <class Q>
+template <class Q, bool BF>
 __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q, uint32_t n) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint32_t s_taddr;
     const int t = threadIdx.x & 127, g = threadIdx.x >> 7, w = threadIdx.x >> 5;
     uint8_t* sA = sm + MLP_TC_A_OFF(g);
     const uint32_t bar = smem_u32(sm + MLP_TC_BAR_OFF + 8 * g);
-    mlp_tc_load_weights(m, sm);
+    mlp_tc_load_weights<BF>(m, sm);
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
                      "r"(MLP_TC_COLS));
@@ -364,7 +406,7 @@ __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q,
         {
             const float qv[6] = {(p.x - m.lo[0]) * m.scale, (p.y - m.lo[1]) * m.scale,
                                  (p.z - m.lo[2]) * m.scale, nr.x, nr.y, nr.z};
-            mlp_tc_encode_row(sA, t, qv);
+            mlp_tc_encode_row<BF>(sA, t, qv);
         }
         f3 out = {0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -375,7 +417,8 @@ __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q,
             wg_sync(g);
             if (t == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = l == 4 ? umma_idesc_f16(128, 16) : umma_idesc_f16(128, 64);
+                const uint32_t idesc =
+                    l == 4 ? umma_idesc_f16(128, 16, H16<BF>::umma_fmt) : umma_idesc_f16(128, 64, H16<BF>::umma_fmt);
                 const uint32_t wl = w_addr + (uint32_t)MLP_TC_W_OFF(l);
 #pragma unroll
                 for (int s = 0; s < MLP_TC_K / 16; ++s)
@@ -410,8 +453,9 @@ __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q,
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
                         *reinterpret_cast<uint4*>(sA + kmajor_off(t, 16 * c2 + 8 * h)) =
-                            make_uint4(relu_h2(v[8 * h], v[8 * h + 1]), relu_h2(v[8 * h + 2], v[8 * h + 3]),
-                                       relu_h2(v[8 * h + 4], v[8 * h + 5]), relu_h2(v[8 * h + 6], v[8 * h + 7]));
+                            make_uint4(H16<BF>::relu2(v[8 * h], v[8 * h + 1]), H16<BF>::relu2(v[8 * h + 2], v[8 * h + 3]),
+                                       H16<BF>::relu2(v[8 * h + 4], v[8 * h + 5]),
+                                       H16<BF>::relu2(v[8 * h + 6], v[8 * h + 7]));
                 }
             } else {
                 uint32_t v[16];
@@ -431,12 +475,11 @@ __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q,
 
 // Launches k_mlp_infer over n queries: one persistent CTA per SM (6 tile
 // streams, 384 of the SM's 512 tensor-memory columns).
-template <class Q>
-cudaError_t launch_mlp_infer(const MLPView& m, const Q& q, uint32_t n, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
+template <class Q, bool BF>
+cudaError_t launch_mlp_infer_t(const MLPView& m, const Q& q, uint32_t n, cudaStream_t st) {
     static int sms = 0;
     if (!sms) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_infer<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_infer<Q, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)MLP_TC_SMEM);
         if (e != cudaSuccess) return e;
         int dev = 0;
@@ -447,6 +490,15 @@ cudaError_t launch_mlp_infer(const MLPView& m, const Q& q, uint32_t n, cudaStrea
     const uint32_t tiles = (n + 127) / 128;
     const uint32_t need = (tiles + MLP_TC_WG - 1) / MLP_TC_WG;
     const uint32_t grid = need < (uint32_t)sms ? need : (uint32_t)sms;
-    k_mlp_infer<Q><<<grid, MLP_TC_THREADS, MLP_TC_SMEM, st>>>(m, q, n);
+    k_mlp_infer<Q, BF><<<grid, MLP_TC_THREADS, MLP_TC_SMEM, st>>>(m, q, n);
     return cudaGetLastError();
+}
+
+// Launches k_mlp_infer over n queries in the network's format: one
+// persistent CTA per SM (6 tile streams, 384 of the SM's 512 tensor-memory
+// columns).
+template <class Q>
+cudaError_t launch_mlp_infer(const MLPView& m, const Q& q, uint32_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    return m.bf16 ? launch_mlp_infer_t<Q, true>(m, q, n, st) : launch_mlp_infer_t<Q, false>(m, q, n, st);
 }

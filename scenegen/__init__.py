@@ -103,6 +103,7 @@ class Settings:
     train_lr: float = 1e-3
     mlp_seed: int = 1
     train_ema: float = 0.97      # served network: moving average of the trained weights
+    mlp_bf16: int = 0            # network in bf16 (1) or fp16 (0), fp32 accumulation
 
 
 @dataclasses.dataclass

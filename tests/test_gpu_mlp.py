@@ -35,16 +35,23 @@ def M():
     return mlp
 
 
-def _to_oracle(flat, M, round16=True):
-    """GPU parameter layout -> oracle [(W, b)] (weights rounded to fp16 as the
-    kernels use them; biases stay fp32)."""
+def _bf16(x):
+    """float32 -> nearest bf16 (round half to even), returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _to_oracle(flat, M, round16=True, bf16=False):
+    """GPU parameter layout -> oracle [(W, b)] (weights rounded to fp16 or
+    bf16 as the kernels use them; biases stay fp32)."""
     flat = np.asarray(flat, np.float32)
     offs_w = [0, 5120, 9216, 13312, 17408]
     out = []
     for l, (o, i) in enumerate(M.layer_shapes()):
         W = flat[offs_w[l]:offs_w[l] + o * i].reshape(o, i)
         if round16:
-            W = W.astype(np.float16)
+            W = _bf16(W) if bf16 else W.astype(np.float16)
         b = flat[17920 + 64 * l:17920 + 64 * l + o]
         out.append((W.astype(np.float64), b.astype(np.float64)))
     return out
@@ -320,3 +327,68 @@ def test_learned_form_has_less_bias_than_probes(dd):
     assert np.mean(served) >= 0.5
     assert mse_l < 0.9 * mse_p
     assert mape_l < 0.75 * mape_p
+
+
+def _bf16_ctx(dd):
+    sc = scenegen.tiny_room()
+    sc.settings = dataclasses.replace(sc.settings, mlp_bf16=1)
+    return sc, dd.Context.from_scene(sc)
+
+
+def test_bf16_inference_matches_oracle(dd, M):
+    """bf16 weights and activations (8-bit significand), fp32 accumulation:
+    outputs within 5e-2 relative (+5e-2 of the mean magnitude) of the fp64
+    oracle on the bf16-rounded weights."""
+    import torch
+    sc, ctx = _bf16_ctx(dd)
+    params = _to_oracle(ctx.mlp_params(), M, bf16=True)
+    lo, scale = M.scene_box(sc.verts)
+    rng = np.random.default_rng(13)
+    n = 5000
+    p = rng.uniform(-1, 1, (n, 3))
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    q = np.zeros((n, 8), np.float32)
+    q[:, 0:3], q[:, 3], q[:, 4:7] = p, 1.0, nrm
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.mlp_infer(torch.from_numpy(q).cuda(), out)
+    got = out.cpu().numpy()
+    ref, _ = M.forward(params, M.encode(p, nrm, lo, scale))
+    assert _close_frac(got[:, :3], ref, 5e-2, 5e-2 * np.abs(ref).mean()) >= 0.99
+    assert ctx.get_status() == dd.OK
+
+
+def test_bf16_gradients_match_oracle(dd, M):
+    sc, ctx = _bf16_ctx(dd)
+    params = _to_oracle(ctx.mlp_params(), M, bf16=True)
+    lo, scale = M.scene_box(sc.verts)
+    s = _samples(sc, 4096, 15)
+    g = ctx.mlp_grad(s)
+    x = M.encode(s[:, 0:3].astype(np.float64), s[:, 4:7].astype(np.float64), lo, scale)
+    out, cache = M.forward(params, x)
+    _, dout = M.rel_l2(out, s[:, 8:11].astype(np.float64), s[:, 11] > 0)
+    ref = _flat(M.backward(params, cache, dout))
+    offs = [0, 5120, 9216, 13312, 17408, 17920, 18184]
+    for a, b in zip(offs[:-1], offs[1:]):
+        err = np.linalg.norm(g[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
+        assert err < 1.5e-1, (a, b, err)
+
+
+def test_bf16_learned_frame_trains(dd):
+    """A bf16 learned-target context trains (held-out error falls) and renders
+    finite frames."""
+    sc = scenegen.tiny_room(frames=16)
+    sc.settings = dataclasses.replace(sc.settings, learned_target=1, train_samples=8192, train_ema=0.0,
+                                      mlp_bf16=1)
+    ctx = dd.Context.from_scene(sc)
+    fr = dd.Frame(ctx, 128, 128, sc.settings.spatial_passes)
+    errs = []
+    for f in range(16):
+        ctx.probe_update(f)
+        ctx.mlp_train(f)
+        st = ctx.mlp_status()
+        errs.append(st["judge_mlp"] / max(st["judge_n"], 1))
+        rad = fr.render(f, sc.cameras[f], probe_update=False).cpu().numpy()
+        assert np.all(np.isfinite(rad))
+    assert np.mean(errs[-3:]) < 0.5 * np.mean(errs[:2])
+    assert ctx.get_status() == dd.OK
