@@ -509,6 +509,8 @@ def restir_initial(scene: Scene, vol: Volume, g: GBuffer, frame: int, pix=None, 
 
 def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Reservoirs,
                     prev: Reservoirs, frame: int, pix=None, settings=None):
+    _need_full(g, cur)
+    _need_full(gp, prev)
     st = settings or scene.settings
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
@@ -523,6 +525,7 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
 
 def restir_spatial(scene: Scene, g: GBuffer, res_in: Reservoirs, frame: int, pass_idx: int,
                    pix=None, settings=None):
+    _need_full(g, res_in)
     st = settings or scene.settings
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
@@ -534,7 +537,16 @@ def restir_spatial(scene: Scene, g: GBuffer, res_in: Reservoirs, frame: int, pas
     return out
 
 
+def _need_full(g: GBuffer, *bufs):
+    """Inputs indexed by pixel must cover the whole image."""
+    for b in bufs:
+        m = b.W.shape[0] if isinstance(b, Reservoirs) else np.asarray(b).shape[0]
+        if m != g.tri.shape[0]:
+            raise ValueError(f"input buffer holds {m} entries, the image {g.tri.shape[0]} pixels")
+
+
 def shade(scene: Scene, vol: Volume, g: GBuffer, res: Reservoirs, resid, pix=None):
+    _need_full(g, res, resid)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     rad = np.zeros((n, 3))

@@ -23,6 +23,9 @@ not available):
                      relocation on, 64 frames.
 * ``tiny_room_dynamic`` -- the box with 3 moving boxes and toggling emitters
                      (small full-image case of the dynamics).
+* ``multistorey`` -- 4-storey building, about 1M triangles, 8192 emissive
+                     triangles, 500 moving boxes, 3840x2160, 32x16x32 probes,
+                     64 candidates, 3 spatial passes, bf16 learned target.
 """
 from __future__ import annotations
 
@@ -34,7 +37,8 @@ import numpy as np
 
 __all__ = [
     "Scene", "Camera", "ProbeGrid", "Settings", "Motion",
-    "tiny_room", "tiny_room_1080p", "apartment", "apartment_dynamic", "tiny_room_dynamic", "make_scene",
+    "tiny_room", "tiny_room_1080p", "apartment", "apartment_dynamic", "tiny_room_dynamic", "multistorey",
+    "make_scene",
     "synthetic_gbuffer", "synthetic_reservoirs", "synthetic_irradiance_interior",
     "synthetic_depth_interior",
 ]
@@ -188,6 +192,19 @@ def _quad(c, a, b, facing, nu=1, nv=1):
     if np.dot(np.cross(a, b), facing) < 0:
         a, b = b, a
         nu, nv = nv, nu
+    if nu * nv > 64:   # same triangles in the same order, built with array arithmetic
+        i = np.repeat(np.arange(nu), nv)[:, None]
+        j = np.tile(np.arange(nv), nu)[:, None]
+        s0, s1 = -1 + 2 * i / nu, -1 + 2 * (i + 1) / nu
+        t0, t1 = -1 + 2 * j / nv, -1 + 2 * (j + 1) / nv
+        p0 = c + s0 * a + t0 * b
+        p1 = c + s1 * a + t0 * b
+        p2 = c + s1 * a + t1 * b
+        p3 = c + s0 * a + t1 * b
+        out = np.empty((2 * nu * nv, 3, 3))
+        out[0::2] = np.stack([p0, p1, p2], 1)
+        out[1::2] = np.stack([p0, p2, p3], 1)
+        return out
     tris = []
     for i in range(nu):
         for j in range(nv):
@@ -434,10 +451,106 @@ def tiny_room_dynamic(seed: int = 1, width: int = 64, height: int = 48, frames: 
     return _with_instances(sc, boxes, motion, rng, 2, "tiny_room_dynamic")
 
 
+def multistorey(seed: int = 11, width: int = 3840, height: int = 2160, frames: int = 128,
+                target_tris: int = 1_000_000, moving_boxes: int = 500) -> Scene:
+    """Large workload: a 4-storey building, 16 m x 12 m x 12 m.
+
+    * every storey (3 m) has the apartment's two interior walls with doors,
+      200 furniture boxes and 32 x 32 ceiling panels (2048 emissive triangles,
+      8192 in the building, radiance log-uniform in [1, 100], albedo 0);
+      floors are 0.2 m slabs;
+    * the storeys' shells are tessellated so that the building has about
+      ``target_tris`` triangles;
+    * 500 boxes in sinusoidal rigid motion spread over the storeys (the
+      dynamic apartment's motion model), emitter halves swapping every 8
+      frames, probe relocation on;
+    * camera on the second storey at (2, 4.6, 3), translating 5 cm per frame
+      along +x; 3840 x 2160;
+    * 32 x 16 x 32 probes, 256 rays; 63 emitter + 1 BSDF candidates, temporal
+      + 3 spatial passes; learned target in bf16 with 65,536 samples per
+      frame.
+    """
+    rng = np.random.default_rng(seed)
+    X, S, Z, NS = 16.0, 3.0, 12.0, 4
+    Y = S * NS
+    blocks, albs, emis = [], [], []
+
+    def add(tris, a, e=(0.0, 0.0, 0.0)):
+        t = np.asarray(tris, np.float64).reshape(-1, 3, 3)
+        blocks.append(t)
+        albs.append(np.broadcast_to(np.asarray(a, np.float64), (len(t), 3)))
+        emis.append(np.broadcast_to(np.asarray(e, np.float64), (len(t), 3)))
+
+    t = 0.1
+    for st in range(NS):
+        y0 = S * st
+        walls = []
+        for z0, z1 in ((0.0, 2.5), (3.5, 8.5), (9.5, Z)):
+            walls.append(((8 - t, y0, z0), (8 + t, y0 + S, z1)))
+        for z0, z1 in ((2.5, 3.5), (8.5, 9.5)):
+            walls.append(((8 - t, y0 + 2.1, z0), (8 + t, y0 + S, z1)))
+        for x0, x1 in ((0.0, 3.5), (4.5, 8 - t), (8 + t, 11.5), (12.5, X)):
+            walls.append(((x0, y0, 6 - t), (x1, y0 + S, 6 + t)))
+        for x0, x1 in ((3.5, 4.5), (11.5, 12.5)):
+            walls.append(((x0, y0 + 2.1, 6 - t), (x1, y0 + S, 6 + t)))
+        if st > 0:
+            walls.append(((0.0, y0 - 0.1, 0.0), (X, y0 + 0.1, Z)))   # floor slab
+        for lo, hi in walls:
+            a = rng.uniform(0.5, 0.8, 3)
+            for f in _box_faces(lo, hi):
+                add(f, a)
+        nbox = 0
+        while nbox < 200:
+            sx, sz = rng.uniform(0.3, 1.5, 2)
+            sy = rng.uniform(0.3, 2.0)
+            cx = rng.uniform(0.3 + sx / 2, X - 0.3 - sx / 2)
+            cz = rng.uniform(0.3 + sz / 2, Z - 0.3 - sz / 2)
+            if cz + sz / 2 > 2.2 and cz - sz / 2 < 3.8:
+                continue
+            a = rng.uniform(0.2, 0.8, 3)
+            for f in _box_faces((cx - sx / 2, y0 + 0.1, cz - sz / 2), (cx + sx / 2, y0 + 0.1 + sy, cz + sz / 2)):
+                add(f, a)
+            nbox += 1
+        for i in range(32):
+            for j in range(32):
+                q = _quad(((i + 0.5) * X / 32, y0 + S - 0.12, (j + 0.5) * Z / 32), (0.12, 0, 0), (0, 0, 0.09),
+                          (0, -1, 0))
+                for tri in q:
+                    le = math.exp(rng.uniform(math.log(1.0), math.log(100.0)))
+                    add([tri], (0, 0, 0), (le, le, le))
+    # storey shells, tessellated to reach target_tris
+    n_now = sum(len(b) for b in blocks)
+    remaining = max(target_tris - n_now - 12 * moving_boxes, 12 * NS)
+    area = NS * (2 * X * Z + 2 * X * S + 2 * Z * S)
+    cell = math.sqrt(area * 2 / remaining)
+    nx, ny, nz = max(1, int(X / cell)), max(1, int(S / cell)), max(1, int(Z / cell))
+    for st in range(NS):
+        shell_alb = [rng.uniform(0.3, 0.8, 3) for _ in range(6)]
+        for k, f in enumerate(_box_faces((0, S * st, 0), (X, S * st + S, Z), inward=True, tess=(nx, ny, nz))):
+            add(f, shell_alb[k])
+    verts = np.concatenate(blocks).astype(np.float32)
+    counts = np.array([32, 16, 32], np.int32)
+    spacing = np.array([X / 32, Y / 16, Z / 32], np.float32)
+    grid = ProbeGrid((spacing * 0.5).astype(np.float32), spacing, counts)
+    cams = []
+    for f in range(frames):
+        pos = np.array([2.0 + 0.05 * f, S + 1.6, 3.0])
+        cams.append(_look_camera(pos, pos + np.array([1.0, -0.15, 0.35]), width, height))
+    st = Settings(rays_per_probe=256, spatial_passes=3, num_light_candidates=63, seed=seed,
+                  learned_target=1, train_samples=65536, mlp_bf16=1)
+    sc = Scene("multistorey", verts, np.concatenate(albs).astype(np.float32),
+               np.concatenate(emis).astype(np.float32), grid, cams, st)
+    mrng = np.random.default_rng([seed, 0x6D6F74])
+    boxes, motion = _moving_boxes(mrng, moving_boxes, (0.3, 0.2, 0.3), (15.7, Y - 0.2, 11.7), (0.2, 0.6),
+                                  keep_out=lambda c, s: (c[2] + s[2] / 2 > 2.2 and c[2] - s[2] / 2 < 3.8
+                                                         and S < c[1] < 2 * S))
+    return _with_instances(sc, boxes, motion, mrng, 8, "multistorey")
+
+
 def make_scene(name: str, **kw) -> Scene:
     return {"tiny_room": tiny_room, "tiny_room_1080p": tiny_room_1080p,
             "apartment": apartment, "apartment_dynamic": apartment_dynamic,
-            "tiny_room_dynamic": tiny_room_dynamic}[name](**kw)
+            "tiny_room_dynamic": tiny_room_dynamic, "multistorey": multistorey}[name](**kw)
 
 
 # ---------------------------------------------------------------------------
