@@ -71,9 +71,12 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
             return h;
         }
         const float4* np = s.nodes + (size_t)node * 8;
-        float4 lx = ldg4(np), hx = ldg4(np + 1), ly = ldg4(np + 2), hy = ldg4(np + 3);
-        float4 lz = ldg4(np + 4), hz = ldg4(np + 5);
-        float4 chf = ldg4(np + 6), cnf = ldg4(np + 7);
+        // a node is four 32-byte loads (nodes are 128-byte aligned)
+        float4 lx, hx, ly, hy, lz, hz, chf, cnf;
+        ld32(np, lx, hx);
+        ld32(np + 2, ly, hy);
+        ld32(np + 4, lz, hz);
+        ld32(np + 6, chf, cnf);
         const float blo[4][3] = {{lx.x, ly.x, lz.x}, {lx.y, ly.y, lz.y}, {lx.z, ly.z, lz.z}, {lx.w, ly.w, lz.w}};
         const float bhi[4][3] = {{hx.x, hy.x, hz.x}, {hx.y, hy.y, hz.y}, {hx.z, hy.z, hz.z}, {hx.w, hy.w, hz.w}};
         const int child[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),

@@ -94,9 +94,12 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
                 break;
             }
             const float4* np = s.nodes + (size_t)node * 8;
-            float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3);
-            float4 lz = __ldg(np + 4), hz = __ldg(np + 5);
-            float4 chf = __ldg(np + 6), cnf = __ldg(np + 7);
+            // a node is four 32-byte loads (nodes are 128-byte aligned)
+            float4 lx, hx, ly, hy, lz, hz, chf, cnf;
+            ld32(np, lx, hx);
+            ld32(np + 2, ly, hy);
+            ld32(np + 4, lz, hz);
+            ld32(np + 6, chf, cnf);
             float t0[4];
             int ent[4];
             const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
