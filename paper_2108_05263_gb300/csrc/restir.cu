@@ -109,63 +109,11 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     sel.p = 0.f;
     sel.y = sel.L = f3{0.f, 0.f, 0.f};
     f3 res = {0.f, 0.f, 0.f};
-    for (uint32_t c = 0; c < M; ++c) {
-        const uint32_t cp = rng_cand(prefix, c);
-        f3 y, L;
-        float d2, cx, cy, pL;
-        uint32_t tri;
-        if (c < NL) {
-            pL = inv_area;
-            float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
-            float u2 = u01(rng_u32_dim(cp, 2));
-            uint32_t e = sample_emitter(s, u0);
-            const float4* rec = s.evert + 4 * (size_t)e;
-            float4 q0, q1, q2, q3;
-            ld32(rec, q0, q1);
-            ld32(rec + 2, q2, q3);
-            tri = __float_as_uint(q0.w);
-            float sq = sqrtf(u1);
-            float b1 = sq * (1.f - u2), b2 = sq * u2;
-            y = xyz(q0) + xyz(q1) * b1 + xyz(q2) * b2;
-            f3 d = y - x;
-            d2 = dot(d, d);
-            if (d2 <= 0.f) continue;
-            f3 w = d * rsqrtf(d2);
-            cx = dot(nx, w);
-            f3 ny = xyz(q3);
-            float cyn = dot(ny, w);
-            cy = fabsf(cyn);
-            if (s.emitters_reflect) {
-                L = radiance_at(s, v, y, tri, x);
-            } else {
-                // pure emitter: one-sided Le toward x
-                L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
-            }
-        } else {
-            f3 w = bsdf_dir(rp, pix, frame, c, nx);
-            float2 hb = __ldg(bsdf_hits + (size_t)pix * NB + (c - NL));
-            Hit h{hb.x, __float_as_uint(hb.y)};
-            if (h.tri == DDGI_NONE) continue;
-            tri = h.tri;
-            pL = __ldg(s.emi + tri).w > 0.f ? inv_area : 0.f;
-            y = x + w * h.t;
-            d2 = h.t * h.t;
-            cx = dot(nx, w);
-            float cyn = dot(xyz(__ldg(s.nrm + tri)), w);
-            cy = fabsf(cyn);
-            if (mst != nullptr && mst->use_mlp) {
-                // learned target: Le + the network's rho max(f, 0), front faces only
-                const uint32_t qi = pix * NB + (c - NL);
-                L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
-            } else {
-                L = radiance_at(s, v, y, tri, x);
-            }
-            if (cx > 0.f) {
-                float G = cx * cy / d2;
-                if (G > 1.f) res = res + mul(rho, L) * ((1.f - 1.f / G) / (float)NB);
-            }
-        }
-        if (cx <= 0.f) continue;
+    // streaming weighted reservoir sampling over the candidates in order
+    // (emitter points first, then BSDF rays); balance-heuristic mixture
+    // density in area measure, bounded geometry term in the target
+    auto stream_in = [&](uint32_t c, uint32_t cp, f3 y, f3 L, uint32_t tri, float d2, float cx, float cy, float pL) {
+        if (cx <= 0.f) return;
         float pB = cx * (1.f / DDGI_PI) * cy / d2;
         float pmix = ((float)NL * pL + (float)NB * pB) * invM;
         float G = cx * cy / d2;
@@ -180,6 +128,62 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             sel.tag = pix * 64u + c;
             sel.p = ph;
         }
+    };
+    // emitter candidates: points uniform in emitter area
+    for (uint32_t c = 0; c < NL; ++c) {
+        const uint32_t cp = rng_cand(prefix, c);
+        float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
+        float u2 = u01(rng_u32_dim(cp, 2));
+        uint32_t e = sample_emitter(s, u0);
+        const float4* er = s.evert + 4 * (size_t)e;
+        float4 q0, q1, q2, q3;
+        ld32(er, q0, q1);
+        ld32(er + 2, q2, q3);
+        const uint32_t tri = __float_as_uint(q0.w);
+        float sq = sqrtf(u1);
+        float b1 = sq * (1.f - u2), b2 = sq * u2;
+        const f3 y = xyz(q0) + xyz(q1) * b1 + xyz(q2) * b2;
+        f3 d = y - x;
+        float d2 = dot(d, d);
+        if (d2 <= 0.f) continue;
+        f3 w = d * rsqrtf(d2);
+        float cx = dot(nx, w);
+        float cyn = dot(xyz(q3), w);
+        f3 L;
+        if (s.emitters_reflect) {
+            L = radiance_at(s, v, y, tri, x);
+        } else {
+            // pure emitter: one-sided Le toward x
+            L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
+        }
+        stream_in(c, cp, y, L, tri, d2, cx, fabsf(cyn), inv_area);
+    }
+    // BSDF candidates: cosine-distributed rays, traced before this kernel;
+    // their residual transport (Sec. 3.5) on the side
+    for (uint32_t c = NL; c < M; ++c) {
+        const uint32_t cp = rng_cand(prefix, c);
+        f3 w = bsdf_dir(rp, pix, frame, c, nx);
+        float2 hb = __ldg(bsdf_hits + (size_t)pix * NB + (c - NL));
+        const uint32_t tri = __float_as_uint(hb.y);
+        if (tri == DDGI_NONE) continue;
+        const float pL = __ldg(s.emi + tri).w > 0.f ? inv_area : 0.f;
+        const f3 y = x + w * hb.x;
+        const float d2 = hb.x * hb.x;
+        const float cx = dot(nx, w);
+        const float cyn = dot(xyz(__ldg(s.nrm + tri)), w);
+        f3 L;
+        if (mst != nullptr && mst->use_mlp) {
+            // learned target: Le + the network's rho max(f, 0), front faces only
+            const uint32_t qi = pix * NB + (c - NL);
+            L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
+        } else {
+            L = radiance_at(s, v, y, tri, x);
+        }
+        if (cx > 0.f) {
+            float G = cx * fabsf(cyn) / d2;
+            if (G > 1.f) res = res + mul(rho, L) * ((1.f - 1.f / G) / (float)NB);
+        }
+        stream_in(c, cp, y, L, tri, d2, cx, fabsf(cyn), pL);
     }
     resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
     if (sel.tri == DDGI_NONE) {
