@@ -444,12 +444,15 @@ def equal_time_mse(dev, frames=256, measure=32, ref_spp=4096):
                       False)
         r.update({"candidates": nl + s0.num_bsdf_candidates, "spatial_passes": sp})
         sweep.append(r)
+    secondary = _form_run(ddgi, torch, dataclasses.replace(base, settings=scenegen.secondary_ddgi(s0)), cam, g, ref,
+                          frames, measure, False)
     within = [r for r in sweep if r["ms"] <= 1.05 * learned["ms"]]
     best = min(within, key=lambda r: r["mse"]) if within else None
     return {"scene": "24-triangle box (emitter Le 10), 1920x1080, static view, 4x4x4 probes x 64 rays",
             "reference": f"path-traced, {ref_spp} spp, fp64 accumulation ({ref_s:.1f} s)",
             "frames": frames, "measured_frames": measure,
             "learned": learned, "probe_sweep": sweep,
+            "secondary_ddgi": secondary,
             "probe_at_equal_time": best,
             "mse_ratio_learned_over_probe": round(learned["mse"] / best["mse"], 4) if best else None,
             "mape_ratio_learned_over_probe": round(learned["mape"] / best["mape"], 4) if best else None}

@@ -38,7 +38,7 @@ import numpy as np
 __all__ = [
     "Scene", "Camera", "ProbeGrid", "Settings", "Motion",
     "tiny_room", "tiny_room_1080p", "apartment", "apartment_dynamic", "tiny_room_dynamic", "multistorey",
-    "make_scene",
+    "make_scene", "secondary_ddgi",
     "synthetic_gbuffer", "synthetic_reservoirs", "synthetic_irradiance_interior",
     "synthetic_depth_interior",
 ]
@@ -545,6 +545,14 @@ def multistorey(seed: int = 11, width: int = 3840, height: int = 2160, frames: i
                                   keep_out=lambda c, s: (c[2] + s[2] / 2 > 2.2 and c[2] - s[2] / 2 < 3.8
                                                          and S < c[1] < 2 * S))
     return _with_instances(sc, boxes, motion, mrng, 8, "multistorey")
+
+
+def secondary_ddgi(settings: Settings) -> Settings:
+    """The paper's "secondary DDGI" comparison (Sec. 4): one cosine BSDF ray
+    per pixel terminated in the probe volume, no emitter candidates, no
+    temporal or spatial reuse (the same passes with M = 1 and reuse off)."""
+    return dataclasses.replace(settings, num_light_candidates=0, num_bsdf_candidates=1, spatial_passes=0,
+                               temporal_mcap=0.0)
 
 
 def make_scene(name: str, **kw) -> Scene:

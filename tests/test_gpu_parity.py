@@ -301,6 +301,17 @@ def test_whole_frame_chain_ragged_image(dd, orc):
         assert tags >= 0.999 and rad >= 0.999, (f, stats)
 
 
+def test_whole_frame_chain_secondary_ddgi(dd, orc):
+    """The paper's "secondary DDGI" comparison through the same passes: one
+    BSDF candidate, no emitter candidates, no reuse."""
+    import dataclasses
+    sc = scenegen.tiny_room(frames=4)
+    sc = dataclasses.replace(sc, settings=scenegen.secondary_ddgi(sc.settings))
+    stats = _chain(dd, orc, sc, 4)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
 def test_whole_frame_chain_dynamic_box(dd, orc):
     """Three boxes in rigid motion (turning and shifting every frame), the
     two emitter triangles swapping every 2 frames, probe relocation on:

@@ -861,3 +861,27 @@ def test_gbuffer_reprojects_a_moving_box(oracle_lib):
     assert np.mean(pcol == exp) > 0.95
     static = np.flatnonzero((g.tri >= 0) & (sc.tri_instance[np.maximum(g.tri, 0)] < 0))
     np.testing.assert_array_equal(g.prev[static], static)
+
+
+def test_secondary_ddgi_collapses_to_the_one_bounce_estimator(oracle_lib):
+    """With one BSDF candidate, no emitter candidates and no reuse (the
+    paper's "secondary DDGI" comparison), the resampled term f W (W = 1/p_B)
+    plus the residual of Sec. 3.5 collapse to rho_x L(y_B) for every pixel
+    and frame: Le(x) + rho_x times the radiance cached at the BSDF hit."""
+    o = oracle_lib
+    base = scenegen.tiny_room(width=32, height=32)
+    st = scenegen.secondary_ddgi(base.settings)
+    sc = dataclasses.replace(base, settings=st)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    for f in range(3):
+        o.probe_update(S, vol, f)
+    g = o.gbuffer(S, sc.cameras[0])
+    le_x = S.emission.reshape(-1, 3)[np.maximum(g.tri, 0)] * (g.tri >= 0)[:, None]
+    for f in (4, 5):
+        res, resid = o.restir_initial(S, vol, g, f)
+        assert np.all(res.M[g.tri >= 0] == 1.0)
+        out = o.shade(S, vol, g, res, resid)
+        exp = le_x + g.alb * res.L * (res.tri >= 0)[:, None]
+        np.testing.assert_allclose(out, exp, rtol=1e-9, atol=1e-12)
+        assert (res.L.max(axis=1) > 0).mean() > 0.5
