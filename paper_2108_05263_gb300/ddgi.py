@@ -484,10 +484,12 @@ class Frame:
         self.cur = 0
 
     def render(self, frame: int, cam, gbuf: Optional[GBuffer] = None, stream=None,
-               probe_update=True, xf=None, emitter_radiance=None):
+               probe_update=True, xf=None, emitter_radiance=None, out: Optional[torch.Tensor] = None):
         """One frame.  If ``gbuf`` is given it is used as this frame's
         G-buffer (the primary-visibility pass is skipped); xf /
-        emitter_radiance (optional) first move the scene."""
+        emitter_radiance (optional) first move the scene; ``out`` (optional,
+        [n][4] float32 on the device) receives the radiance instead of the
+        frame's own buffer."""
         ctx = self.ctx
         if xf is not None or emitter_radiance is not None:
             ctx.scene_update(xf, emitter_radiance, stream)
@@ -507,10 +509,11 @@ class Frame:
             nxt = self._other(res)
             ctx.restir_spatial(g, res, nxt, frame, i, stream)
             res = nxt
-        ctx.shade(g, res, self.resid, self.radiance, stream)
+        rad = self.radiance if out is None else out
+        ctx.shade(g, res, self.resid, rad, stream)
         self.prev_final, self.prev_cam = res, cam
         self.cur ^= 1
-        return self.radiance
+        return rad
 
     def _free_pair(self):
         free = [r for r in self.res if r is not self.prev_final]
@@ -522,3 +525,55 @@ class Frame:
             if c is not r:
                 return c
         raise AssertionError
+
+
+class HostFramePipeline:
+    """Frames from host G-buffers to host radiance, the copies overlapped
+    with the computation: the next frame's G-buffer uploads on one stream
+    and the last frame's radiance downloads on another while the current
+    frame runs on the caller's stream (double-buffered device G-buffers and
+    radiance, ordered by events).  Host buffers should be pinned."""
+
+    def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda"):
+        n = width * height
+        self.frame = Frame(ctx, width, height, spatial_passes, device)
+        self.gbuf = [GBuffer(width, height, device), GBuffer(width, height, device)]
+        self.rad = [torch.empty((n, 4), dtype=torch.float32, device=device) for _ in range(2)]
+        self.up = torch.cuda.Stream(device)
+        self.down = torch.cuda.Stream(device)
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]     # upload into slot done
+        self.ev_used = [torch.cuda.Event() for _ in range(2)]   # frame on slot done
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]    # download from slot done
+        self.k = 0       # frames run
+        self.n_up = 0    # G-buffers uploaded
+
+    def upload(self, host_planes):
+        """Queue the upload of the G-buffer of the next frame to run (at most
+        one frame ahead of `run`)."""
+        b = self.n_up % 2
+        self.n_up += 1
+        with torch.cuda.stream(self.up):
+            self.up.wait_event(self.ev_used[b])                 # the slot's last frame is done with it
+            for d, h in zip((self.gbuf[b].g0, self.gbuf[b].g1, self.gbuf[b].g2), host_planes):
+                d.copy_(h, non_blocking=True)
+            self.ev_in[b].record(self.up)
+
+    def run(self, frame: int, cam, host_out, stream=None):
+        """Render the frame whose G-buffer was queued first and queue the
+        download of its radiance into host_out."""
+        st = stream or torch.cuda.current_stream()
+        b = self.k % 2
+        st.wait_event(self.ev_in[b])
+        st.wait_event(self.ev_out[b])                           # the slot's radiance was read out
+        self.frame.render(frame, cam, gbuf=self.gbuf[b], stream=st, probe_update=True, out=self.rad[b])
+        self.ev_used[b].record(st)
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(self.ev_used[b])
+            host_out.copy_(self.rad[b], non_blocking=True)
+            self.ev_out[b].record(self.down)
+        self.k += 1
+
+    def finish(self, stream=None):
+        """Make `stream` wait for the last download."""
+        st = stream or torch.cuda.current_stream()
+        st.wait_event(self.ev_out[(self.k - 1) % 2])

@@ -781,3 +781,34 @@ def test_large_learned_bf16_frames_run(dd, large):
     st = ctx.mlp_status()
     assert st["judge_n"] > 0 and st["overflow"] == 0
     assert ctx.get_status() == dd.OK
+
+
+def test_host_pipeline_matches_frame_render(dd):
+    """The overlapped host-to-host pipeline (uploads of the next G-buffer and
+    downloads of the last radiance on their own streams) gives the same
+    frames as Frame.render on device buffers."""
+    import torch
+    sc = scenegen.tiny_room(width=96, height=64, frames=6)
+    W, H = 96, 64
+    ref_ctx, ctx = dd.Context.from_scene(sc), dd.Context.from_scene(sc)
+    gbufs, prev = [], None
+    for f in range(6):
+        g = dd.GBuffer(W, H)
+        ref_ctx.gbuffer(sc.cameras[f], prev, g)
+        prev = sc.cameras[f]
+        gbufs.append(g)
+    fr = dd.Frame(ref_ctx, W, H, sc.settings.spatial_passes)
+    ref = [fr.render(f, sc.cameras[f], gbuf=gbufs[f]).cpu().numpy().copy() for f in range(6)]
+    host = [[t.cpu().pin_memory() for t in (g.g0, g.g1, g.g2)] for g in gbufs]
+    outs = [torch.empty((W * H, 4), dtype=torch.float32).pin_memory() for _ in range(6)]
+    pipe = dd.HostFramePipeline(ctx, W, H, sc.settings.spatial_passes)
+    pipe.upload(host[0])
+    for f in range(6):
+        if f + 1 < 6:
+            pipe.upload(host[f + 1])
+        pipe.run(f, sc.cameras[f], outs[f])
+    pipe.finish()
+    torch.cuda.synchronize()
+    for f in range(6):
+        np.testing.assert_array_equal(outs[f].numpy(), ref[f])
+    assert ctx.get_status() == dd.OK
