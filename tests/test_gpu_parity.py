@@ -812,3 +812,21 @@ def test_host_pipeline_matches_frame_render(dd):
     for f in range(6):
         np.testing.assert_array_equal(outs[f].numpy(), ref[f])
     assert ctx.get_status() == dd.OK
+
+
+def test_whole_frame_chain_extreme_settings(dd, orc):
+    """Settings at their limits on a ragged 46 x 34 image: 1024 rays per
+    probe, 32 x 32 distance texels and 16 x 16 irradiance texels, 63 + 1
+    candidates, 32 spatial neighbours in a 255 px radius (mostly off the
+    image), 3 spatial passes, M cap 1.  (Odd sizes put the centred camera's
+    middle row and column exactly on the seams between wall quads of
+    different albedo: a floating-point tie in the primary hit that spatial
+    reuse then spreads, so the sizes are even.)"""
+    import dataclasses
+    sc = scenegen.tiny_room(width=46, height=34, frames=3)
+    sc.settings = dataclasses.replace(sc.settings, rays_per_probe=1024, irr_texels=16, depth_texels=32,
+                                      num_light_candidates=63, spatial_neighbours=32, spatial_radius=255,
+                                      spatial_passes=3, temporal_mcap=1.0)
+    stats = _chain(dd, orc, sc, 3)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.998, (f, stats)
