@@ -88,7 +88,7 @@ class _GBuf(C.Structure):
 
 
 class _Res(C.Structure):
-    _fields_ = [("y", _dp), ("W", _dp), ("L", _dp), ("M", _dp), ("tri", _ip), ("tag", _up)]
+    _fields_ = [("y", _dp), ("W", _dp), ("L", _dp), ("M", _dp), ("tri", _ip), ("tag", _up), ("ny", _dp)]
 
 
 def lib():
@@ -308,6 +308,11 @@ class GBuffer:
 
 
 class Reservoirs:
+    """Per-pixel reservoirs: the kept sample (point y, its triangle, its unit
+    normal ny when found, cached radiance L), W, M and the origin tag."""
+
+    FIELDS = ("y", "W", "L", "M", "tri", "tag", "ny")
+
     def __init__(self, n):
         self.y = np.zeros((n, 3))
         self.W = np.zeros(n)
@@ -315,15 +320,20 @@ class Reservoirs:
         self.M = np.zeros(n)
         self.tri = np.full(n, -1, np.int32)
         self.tag = np.zeros(n, np.uint32)
+        self.ny = np.zeros((n, 3))
 
     def c(self) -> _Res:
         r = _Res()
         r.y, r.W, r.L, r.M = _p(self.y), _p(self.W), _p(self.L), _p(self.M)
         r.tri, r.tag = _p(self.tri, _ip), _p(self.tag, _up)
+        r.ny = _p(self.ny)
         return r
 
     @staticmethod
-    def from_planes(r0, r1, r2):
+    def from_planes(r0, r1, r2, scene=None):
+        """From float32 planes (y, W | L, M | triangle, tag); the samples'
+        normals are those of their triangles in `scene` (required when any
+        reservoir holds a sample)."""
         n = r0.shape[0]
         o = Reservoirs(n)
         o.y[:] = r0[:, :3]
@@ -332,6 +342,11 @@ class Reservoirs:
         o.M[:] = r1[:, 3]
         o.tri[:] = np.ascontiguousarray(r2[:, 0]).view(np.int32)
         o.tag[:] = r2[:, 1]
+        has = o.tri >= 0
+        if np.any(has):
+            if scene is None:
+                raise ValueError("Reservoirs.from_planes: the samples' normals need the scene")
+            o.ny[has] = scene.normals[o.tri[has]]
         return o
 
     def planes(self):

@@ -688,9 +688,9 @@ int or_gbuffer(const or_scene* s, const or_camera* cam, const or_camera* pc,
 /* Target function at shading point x for a sample y on triangle tri with
  * outgoing radiance L (Sec. 3.1 step 2, bounded geometry term of Sec. 3.5):
  * luminance of rho_x / pi * L * min(G, 1); no visibility. */
-double or_target(const or_scene* s, const double x[3], const double nx[3],
-                 const double rho[3], const double y[3], int32_t tri, const double L[3]) {
-    if (tri < 0) return 0.0;
+/* target of a point y with unit normal ny (only |cos| at y enters) */
+static double target_with_normal(const double x[3], const double nx[3], const double rho[3], const double y[3],
+                                 const double ny[3], const double L[3]) {
     double d[3];
     sub3(y, x, d);
     double d2 = dot3(d, d);
@@ -699,11 +699,17 @@ double or_target(const or_scene* s, const double x[3], const double nx[3],
     double w[3] = {d[0] / l, d[1] / l, d[2] / l};
     double cx = dot3(nx, w);
     if (cx <= 0.0) return 0.0;
-    double cy = fabs(dot3(s->normal + 3 * tri, w));
+    double cy = fabs(dot3(ny, w));
     double G = cx * cy / d2;
     double Gb = G < 1.0 ? G : 1.0;
     double f[3] = {rho[0] / PI * L[0] * Gb, rho[1] / PI * L[1] * Gb, rho[2] / PI * L[2] * Gb};
     return lum(f);
+}
+
+double or_target(const or_scene* s, const double x[3], const double nx[3],
+                 const double rho[3], const double y[3], int32_t tri, const double L[3]) {
+    if (tri < 0) return 0.0;
+    return target_with_normal(x, nx, rho, y, s->normal + 3 * tri, L);
 }
 
 /* Orthonormal basis around n (Duff et al., "Building an Orthonormal Basis,
@@ -793,11 +799,16 @@ void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const d
 static void res_set_empty(or_res* r, int32_t k, double M) {
     r->y[3 * k] = r->y[3 * k + 1] = r->y[3 * k + 2] = 0.0;
     r->L[3 * k] = r->L[3 * k + 1] = r->L[3 * k + 2] = 0.0;
+    r->ny[3 * k] = r->ny[3 * k + 1] = r->ny[3 * k + 2] = 0.0;
     r->W[k] = 0.0; r->M[k] = M; r->tri[k] = -1; r->tag[k] = 0u;
 }
 
 static void res_copy(or_res* dst, int32_t k, const or_res* src, int32_t q) {
-    for (int a = 0; a < 3; ++a) { dst->y[3 * k + a] = src->y[3 * q + a]; dst->L[3 * k + a] = src->L[3 * q + a]; }
+    for (int a = 0; a < 3; ++a) {
+        dst->y[3 * k + a] = src->y[3 * q + a];
+        dst->L[3 * k + a] = src->L[3 * q + a];
+        dst->ny[3 * k + a] = src->ny[3 * q + a];
+    }
     dst->W[k] = src->W[q]; dst->M[k] = src->M[q]; dst->tri[k] = src->tri[q]; dst->tag[k] = src->tag[q];
 }
 
@@ -882,7 +893,11 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
             }
         }
         if (sel_c < 0) { res_set_empty(out, k, (double)M); continue; }
-        for (int a = 0; a < 3; ++a) { out->y[3 * k + a] = sel_y[a]; out->L[3 * k + a] = sel_L[a]; }
+        for (int a = 0; a < 3; ++a) {
+            out->y[3 * k + a] = sel_y[a];
+            out->L[3 * k + a] = sel_L[a];
+            out->ny[3 * k + a] = s->normal[3 * sel_tri + a];
+        }
         out->W[k] = sel_p > 0.0 ? wsum / (M * sel_p) : 0.0;
         out->M[k] = M;
         out->tri[k] = sel_tri;
@@ -891,8 +906,14 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
     return 0;
 }
 
+/* target at pixel q of a reused sample: its cached point, normal and
+ * radiance (Sec. 3.6 caches the query with the sample; the point and normal
+ * stay those of the frame the sample was found in, as the radiance does) */
 static double target_of(const or_scene* s, const or_gbuf* g, int32_t q, const or_res* r, int32_t k) {
-    return or_target(s, g->pos + 3 * q, g->nrm + 3 * q, g->alb + 3 * q, r->y + 3 * k, r->tri[k], r->L + 3 * k);
+    (void)s;
+    if (r->tri[k] < 0) return 0.0;
+    return target_with_normal(g->pos + 3 * q, g->nrm + 3 * q, g->alb + 3 * q, r->y + 3 * k, r->ny + 3 * k,
+                              r->L + 3 * k);
 }
 
 /* Sec. 3.1 step 2 (temporal reuse, mechanics of the cited ReSTIR): the

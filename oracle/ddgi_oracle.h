@@ -91,6 +91,7 @@ typedef struct {          /* reservoirs (full or compact) */
     double* M;            /* [N]   candidate count */
     int32_t* tri;         /* [N]   triangle of y, -1 = empty */
     uint32_t* tag;        /* [N]   origin id: pixel * 64 + candidate */
+    double* ny;           /* [N][3] unit normal at y when the sample was found */
 } or_res;
 
 /* pass identifiers used in the random-number keys */

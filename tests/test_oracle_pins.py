@@ -592,12 +592,45 @@ def test_reservoir_merge_special_case(oracle_lib):
         r.y[:] = [-0.5, 1.0, 0.0]
         r.L[:] = 10.0
         r.tri[:] = ytri[0]
+        r.ny[:] = S.normals[ytri[0]]
         r.W[:] = W
         r.M[:] = M
         r.tag[:] = 7 if r is cur else 9
     out = o.restir_temporal(S, g, g, np.array([0.0, 1.0, 0.0]), cur, prev, 3)
     np.testing.assert_allclose(out.M, 132.0)
     np.testing.assert_allclose(out.W, (0.8 * 32 + 2.0 * 100) / 132.0, rtol=1e-12)
+
+
+def test_reused_sample_keeps_its_normal(oracle_lib):
+    """A reused sample is evaluated with the normal it was found with (cached
+    with its point and radiance), not its triangle's current one: with the
+    previous sample's normal turned from (0,-1,0) to (1,0,0), |cos| at y drops
+    from 2 / sqrt(4.25) to 0.5 / sqrt(4.25), so its target is a quarter of the
+    current sample's and the merged W follows in closed form."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    pts = np.array([[0.0, -1.0, 0.0]] * 2)
+    g = _point_gbuffer(o, S, pts, np.tile([0, 1.0, 0], (2, 1)), np.tile([0.5] * 3, (2, 1)),
+                       np.array([0.0, 1.0, 0.0]), width=2)
+    ytri, _ = o.intersect(S, np.array([[-0.5, 0.5, 0.0]]), np.array([[0, 1.0, 0]]))
+    np.testing.assert_allclose(S.normals[ytri[0]], [0.0, -1.0, 0.0], atol=1e-12)
+    cur, prev = o.Reservoirs(2), o.Reservoirs(2)
+    for r, W, M, n in ((cur, 0.8, 32.0, [0.0, -1.0, 0.0]), (prev, 2.0, 100.0, [1.0, 0.0, 0.0])):
+        r.y[:] = [-0.5, 1.0, 0.0]
+        r.L[:] = 10.0
+        r.tri[:] = ytri[0]
+        r.ny[:] = n
+        r.W[:] = W
+        r.M[:] = M
+        r.tag[:] = 7 if r is cur else 9
+    out = o.restir_temporal(S, g, g, np.array([0.0, 1.0, 0.0]), cur, prev, 3)
+    np.testing.assert_allclose(out.M, 132.0)
+    for k in range(2):
+        exp = (0.8 * 32 + 0.25 * 2.0 * 100) / 132.0 if out.tag[k] == 7 else (4 * 0.8 * 32 + 2.0 * 100) / 132.0
+        assert out.tag[k] in (7, 9)
+        np.testing.assert_allclose(out.W[k], exp, rtol=1e-12)
+        np.testing.assert_array_equal(out.ny[k], [0.0, -1.0, 0.0] if out.tag[k] == 7 else [1.0, 0.0, 0.0])
 
 
 def test_mape_definition():
