@@ -487,7 +487,7 @@ class OracleSample:
         self.vol = vol
         gp = scenegen.synthetic_gbuffer(sc, self.W, self.H, 21)
         self.g = oracle.GBuffer.from_planes(*gp, self.W, self.H)
-        self.res = oracle.Reservoirs.from_planes(*scenegen.synthetic_reservoirs(sc, self.W * self.H, 31))
+        self.res = oracle.Reservoirs.from_planes(*scenegen.synthetic_reservoirs(sc, self.W * self.H, 31), scene=self.S)
         self.zero_resid = np.zeros((self.W * self.H, 3))
 
     def _pixels_run(self, pix):

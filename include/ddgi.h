@@ -111,7 +111,8 @@ typedef struct {
     uint32_t width, height;
 } ddgi_camera;
 
-/* G-buffer planes (device): g0 = position.xyz, distance to camera;
+/* G-buffer planes (device): g0 = position.xyz, distance to camera (> 0 at
+ * a hit: reservoir records take the owner's validity from it);
  * g1 = normal.xyz, triangle index (uint32 bits, 0xFFFFFFFF = no valid
  * front-facing hit); g2 = albedo.rgb, previous-frame pixel (int32 bits, -1 =
  * none; bit 30 set: the surface belongs to a rigid instance, whose motion
@@ -128,11 +129,16 @@ typedef struct {
  *   [0..3]   y.xyz (selected point), W (unbiased contribution weight)
  *   [4..7]   cached radiance L(y).rgb leaving y toward its pixel, M
  *   [8..11]  the owning pixel's normal.xyz and distance to the camera
- *   [12..15] uint32 bits: triangle of y (0xFFFFFFFF = empty), tag (origin
- *            pixel * 64 + candidate index), 1 if the owning pixel has a valid
- *            G-buffer hit else 0, 0.
- * Words 8..11 and 14 repeat the owning pixel's G-buffer so that neighbour and
- * previous-frame reuse read one record (two 32-byte sectors) per candidate. */
+ *            (0 when the owning pixel has no valid G-buffer hit: the owner
+ *            is valid exactly when this distance is > 0)
+ *   [12..13] uint32 bits: triangle of y (0xFFFFFFFF = empty), tag (origin
+ *            pixel * 64 + candidate index)
+ *   [14..15] y's unit normal, octahedral map (u, v) in [-1, 1]^2 as floats
+ *            (0, 0 for an empty reservoir); ddgi_reservoirs_attach_normals
+ *            fills them for records written by the caller.
+ * Words 8..11 repeat the owning pixel's G-buffer and words 14..15 the normal
+ * of y's triangle, so that neighbour and previous-frame reuse read one record
+ * (two 32-byte sectors) per candidate and gather nothing else. */
 typedef struct {
     float* rec;
     uint32_t num_pixels;
@@ -174,8 +180,12 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream);
  * emitter_radiance (host [E][3] in increasing triangle order of the emissive
  * triangles of ddgi_create, or NULL): new radiance, 0 switches an emitter
  * off; the emitter list and its area distribution do not change.  Host
- * buffers may be reused when the call returns.  Calls on other streams
- * must be ordered with this one by the caller. */
+ * buffers may be reused when the call returns: they are copied into a
+ * page-locked staging buffer of the context, from which the device copies
+ * run asynchronously; a call first waits (on the host) until the copies of
+ * the previous call have run.  Both arguments are validated before anything
+ * is enqueued.  Calls on other streams must be ordered with this one by the
+ * caller. */
 ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const float* emitter_radiance,
                               void* stream);
 
@@ -235,7 +245,7 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservo
  * distances (within depth_reject_frac) agree; the previous M is capped at
  * temporal_mcap times the current M; targets use the cached radiance
  * (Sec. 3.6).  The previous pixel's normal, distance and validity come from
- * its reservoir record (words 8..11, 14); prev may hold a different number of
+ * its reservoir record (words 8..11); prev may hold a different number of
  * pixels than cur.  prev_cam_pos: host float[3], the previous camera
  * position.  out must not alias cur or prev. */
 ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g,
@@ -250,6 +260,13 @@ ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g,
 ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* in,
                            const ddgi_reservoirs* out, uint32_t frame, uint32_t pass,
                            void* stream);
+
+/* Words 14..15 of n caller-written records (triangle of y in word 12): the
+ * octahedral map of that triangle's unit normal, as restir_initial writes it
+ * (0, 0 where word 12 is not a triangle of the scene).  For reservoirs built
+ * outside the library before they enter restir_temporal, restir_spatial or
+ * ddgi_shade. */
+ddgi_status ddgi_reservoirs_attach_normals(ddgi_ctx* ctx, const ddgi_reservoirs* r, void* stream);
 
 /* Sec. 3.1 steps 3-4, Eq. Algorithm: radiance (device [N][4], rgb, 1) = Le(x)
  * + residual + (if the shadow ray to y is clear) rho_x / pi (Le +

@@ -71,6 +71,12 @@ struct ddgi_ctx {
     std::vector<uint32_t> refit_levels;
     std::vector<double> xf_cur, xf_prev;   // [12 I] host copies
     float* le_stage = nullptr;       // [3 E] staged emitter radiance
+    // page-locked host staging of ddgi_scene_update ([12 I] transforms,
+    // [12 I] reprojection rows, [3 E] radiance), so that its copies are
+    // asynchronous; the event marks the end of the last copies out of it
+    float* pin = nullptr;
+    cudaEvent_t pin_ev = nullptr;
+    bool pin_pending = false;
     uint64_t device_bytes = 0;
     std::vector<void*> allocs;
     std::string last_error;
@@ -289,6 +295,14 @@ void release(ddgi_ctx* c) {
     if (c->tmp_smp) cudaFree(c->tmp_smp);
     c->tmp_smp = nullptr;
     c->tmp_cap = 0;
+    if (c->pin_ev) {
+        cudaEventSynchronize(c->pin_ev);
+        cudaEventDestroy(c->pin_ev);
+    }
+    c->pin_ev = nullptr;
+    c->pin_pending = false;
+    if (c->pin) cudaFreeHost(c->pin);
+    c->pin = nullptr;
 }
 
 // stream-ordered growth of a scratch buffer of T
@@ -763,10 +777,37 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     return DDGI_OK;
 }
 
+namespace {
+// the staging buffer may be rewritten once the copies of the previous update
+// out of it have run (allocated on first use)
+cudaError_t stage_ready(ddgi_ctx* c) {
+    if (!c->pin) {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->pin), (24ull * c->I + 3ull * c->E) * sizeof(float));
+        if (e != cudaSuccess) {
+            c->pin = nullptr;
+            return e;
+        }
+        e = cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) c->pin_ev = nullptr;
+        return e;
+    }
+    if (!c->pin_pending) return cudaSuccess;
+    c->pin_pending = false;
+    return cudaEventSynchronize(c->pin_ev);
+}
+}  // namespace
+
 ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const float* emitter_radiance,
                               void* stream) {
     if (!ctx) return DDGI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    bool staged = false;
+    if (emitter_radiance) {   // both arguments are checked before anything is enqueued
+        if (ctx->E == 0) return fail(ctx, DDGI_ERR_INVALID_ARG, "the scene has no emitters");
+        for (size_t k = 0; k < 3ull * ctx->E; ++k)
+            if (!(emitter_radiance[k] >= 0.f) || !std::isfinite(emitter_radiance[k]))
+                return fail(ctx, DDGI_ERR_INVALID_ARG, "emitter radiance must be finite and >= 0");
+    }
     if (xf) {
         if (ctx->I == 0 || n != ctx->I) return fail(ctx, DDGI_ERR_INVALID_ARG, "transform count != instance count");
         std::vector<double> cur(12ull * n), delta(12ull * n);
@@ -779,22 +820,30 @@ ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const 
             if (!invert34(&cur[12ull * k], inv)) return fail(ctx, DDGI_ERR_INVALID_ARG, "singular transform");
             compose34(&ctx->xf_cur[12ull * k], inv, &delta[12ull * k]);
         }
-        std::vector<float> df(delta.begin(), delta.end());
-        CK(cudaMemcpyAsync(ctx->inst_xf, xf, 12ull * n * sizeof(float), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(ctx->inst_delta, df.data(), df.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(stage_ready(ctx));
+        float* sx = ctx->pin;
+        float* sd = ctx->pin + 12ull * ctx->I;
+        std::memcpy(sx, xf, 12ull * n * sizeof(float));
+        for (size_t k = 0; k < 12ull * n; ++k) sd[k] = (float)delta[k];
+        CK(cudaMemcpyAsync(ctx->inst_xf, sx, 12ull * n * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->inst_delta, sd, 12ull * n * sizeof(float), cudaMemcpyHostToDevice, st));
+        staged = true;
         CK(launch_instance_update(ctx->inst_obj, ctx->inst_map, ctx->NI, ctx->inst_xf, ctx->tris, ctx->nrm,
                                   ctx->nodes, ctx->refit_list, ctx->refit_levels, st));
         ctx->xf_prev = ctx->xf_cur;
         ctx->xf_cur = cur;
     }
     if (emitter_radiance) {
-        if (ctx->E == 0) return fail(ctx, DDGI_ERR_INVALID_ARG, "the scene has no emitters");
-        for (size_t k = 0; k < 3ull * ctx->E; ++k)
-            if (!(emitter_radiance[k] >= 0.f) || !std::isfinite(emitter_radiance[k]))
-                return fail(ctx, DDGI_ERR_INVALID_ARG, "emitter radiance must be finite and >= 0");
-        CK(cudaMemcpyAsync(ctx->le_stage, emitter_radiance, 3ull * ctx->E * sizeof(float), cudaMemcpyHostToDevice,
-                           st));
+        if (!staged) CK(stage_ready(ctx));
+        float* sl = ctx->pin + 24ull * ctx->I;
+        std::memcpy(sl, emitter_radiance, 3ull * ctx->E * sizeof(float));
+        CK(cudaMemcpyAsync(ctx->le_stage, sl, 3ull * ctx->E * sizeof(float), cudaMemcpyHostToDevice, st));
+        staged = true;
         CK(launch_emitter_radiance(ctx->le_stage, ctx->etri, ctx->emi, ctx->evert, ctx->E, st));
+    }
+    if (staged) {
+        CK(cudaEventRecord(ctx->pin_ev, st));
+        ctx->pin_pending = true;
     }
     return DDGI_OK;
 }
@@ -1034,6 +1083,15 @@ ddgi_status restir_spatial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     if (pass > 3) return fail(ctx, DDGI_ERR_INVALID_ARG, "spatial pass index must be 0..3");
     CK(launch_restir_spatial(scene_view(ctx), restir_params(ctx), g, ri, ro, frame, pass,
                              (cudaStream_t)stream));
+    return DDGI_OK;
+}
+
+ddgi_status ddgi_reservoirs_attach_normals(ddgi_ctx* ctx, const ddgi_reservoirs* r, void* stream) {
+    if (!ctx || !r) return DDGI_ERR_INVALID_ARG;
+    ResView v;
+    ddgi_status s;
+    if ((s = check_res(ctx, r, r->num_pixels, &v)) != DDGI_OK) return s;
+    CK(launch_attach_normals(scene_view(ctx), v, (cudaStream_t)stream));
     return DDGI_OK;
 }
 

@@ -280,10 +280,9 @@ __device__ __forceinline__ f3 radiance_at(const SceneView& s, const VolumeView& 
     return le;
 }
 
-// target function: luminance of rho_x / pi * L * min(G, 1)
-__device__ __forceinline__ float target_fn(const SceneView& s, f3 x, f3 nx, f3 rho, f3 y,
-                                           uint32_t tri, f3 L) {
-    if (tri == DDGI_NONE) return 0.f;
+// target function: luminance of rho_x / pi * L * min(G, 1) for a point y with
+// unit normal ny (only |cos| at y enters)
+__device__ __forceinline__ float target_at(f3 x, f3 nx, f3 rho, f3 y, f3 ny, f3 L) {
     f3 d = y - x;
     float d2 = dot(d, d);
     if (d2 <= 0.f) return 0.f;
@@ -291,7 +290,7 @@ __device__ __forceinline__ float target_fn(const SceneView& s, f3 x, f3 nx, f3 r
     f3 w = d * inv;
     float cx = dot(nx, w);
     if (cx <= 0.f) return 0.f;
-    float cy = fabsf(dot(xyz(__ldg(s.nrm + tri)), w));
+    float cy = fabsf(dot(ny, w));
     float G = cx * cy / d2;
     float Gb = fminf(G, 1.f);
     return luminance(mul(rho, L)) * (Gb * (1.f / DDGI_PI));
@@ -322,7 +321,8 @@ __device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
 }
 
 // reservoir record: q0 = (y, W), q1 = (L, M), q2 = (owner normal, owner
-// distance), q3 = (triangle of y, tag, owner valid, 0)
+// distance, > 0 exactly when the owner has a G-buffer hit), q3 = (triangle of
+// y, tag, octahedral map of y's unit normal)
 struct Rec {
     float4 q0, q1, q2, q3;
 };
@@ -334,16 +334,28 @@ __device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
         : "l"(p));
 }
 
+// the same from L2 only (scattered neighbour records: L1 seldom hits), issued
+// where written so that the loads start before the arithmetic that follows
+__device__ __forceinline__ void ld32_l2(const float4* p, float4& a, float4& b) {
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 __device__ __forceinline__ void st32(float4* p, float4 a, float4 b) {
     asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
                  "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
                  : "memory");
 }
 
-__device__ __forceinline__ void store_rec(float4* p, float4 q0, float4 q1, float4 q2, uint32_t tri,
-                                          uint32_t tag, uint32_t valid) {
+// words 12..15: triangle of y, tag, y's normal (octahedral, 0 0 without a sample)
+__device__ __forceinline__ float4 rec_tail(uint32_t tri, uint32_t tag, float2 ny) {
+    return make_float4(__uint_as_float(tri), __uint_as_float(tag), ny.x, ny.y);
+}
+
+__device__ __forceinline__ void store_rec(float4* p, float4 q0, float4 q1, float4 q2, float4 q3) {
     st32(p, q0, q1);
-    st32(p + 2, q2, make_float4(__uint_as_float(tri), __uint_as_float(tag), __uint_as_float(valid), 0.f));
+    st32(p + 2, q2, q3);
 }
 
 __device__ __forceinline__ void copy_rec(float4* p, const Rec& r) {
@@ -359,8 +371,11 @@ __device__ __forceinline__ Rec load_rec(const float4* p) {
 }
 
 __device__ __forceinline__ uint32_t rec_tri(const Rec& r) { return __float_as_uint(r.q3.x); }
+__device__ __forceinline__ bool rec_owner_valid(const Rec& r) { return r.q2.w > 0.f; }
 
-__device__ __forceinline__ float rec_target(const SceneView& s, f3 x, f3 nx, f3 rho, const Rec& r) {
-    return target_fn(s, x, nx, rho, xyz(r.q0), rec_tri(r), xyz(r.q1));
+// target of a record's sample at x (the sample's normal travels in the record)
+__device__ __forceinline__ float rec_target(f3 x, f3 nx, f3 rho, float4 q0, float4 q1, float4 q3) {
+    if (__float_as_uint(q3.x) == DDGI_NONE) return 0.f;
+    return target_at(x, nx, rho, xyz(q0), oct_decode(q3.z, q3.w), xyz(q1));
 }
 

@@ -78,6 +78,7 @@ cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, c
 cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                   const ResView& in, const ResView& out, uint32_t frame,
                                   uint32_t pass, cudaStream_t st);
+cudaError_t launch_attach_normals(const SceneView& s, const ResView& r, cudaStream_t st);
 // learned target form (mlp.cu)
 #include "mlp.cuh"
 #define PASS_TRAIN_ROT 9u

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     float4* rec = out.rec + 4 * (size_t)pix;
     if (xtri == DDGI_NONE) {
         store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                  make_float4(0.f, 0.f, 0.f, 0.f), DDGI_NONE, 0u, 0u);
+                  make_float4(0.f, 0.f, 0.f, 0.f), rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
         resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
     if (sel.tri == DDGI_NONE) {
         store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
-                  DDGI_NONE, 0u, 1u);
+                  rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
         return;
     }
     float W = sel.p > 0.f ? wsum / ((float)M * sel.p) : 0.f;
-    store_rec(rec, make_float4(sel.y.x, sel.y.y, sel.y.z, W),
-              make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo, sel.tri, sel.tag, 1u);
+    store_rec(rec, make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
+              rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))));
 }
 
 __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirParams rp, GBufView g,
@@ -210,13 +210,13 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
     const bool moving = pq >= 0 && (pq & DDGI_PREV_MOVING);
     pq &= ~DDGI_PREV_MOVING;
     // the owner validity of the current record is this pixel's G-buffer validity
-    bool merge = __float_as_uint(c.q3.z) != 0u && pq >= 0 && (uint32_t)pq < prev.n;
+    bool merge = rec_owner_valid(c) && pq >= 0 && (uint32_t)pq < prev.n;
     Rec p;
     float4 g0;
     if (merge) {
         p = load_rec(prev.rec + 4 * (size_t)pq);
         g0 = g.g0[pix];
-        merge = __float_as_uint(p.q3.z) != 0u && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
+        merge = rec_owner_valid(p) && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
         if (merge) {
             // a surface on a moving instance is compared at its previous position
             f3 xp = xyz(g0);
@@ -235,27 +235,25 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
     const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
     float Mc = c.q1.w;
     float Mp = fminf(p.q1.w, rp.temporal_mcap * Mc);
-    float pc = rec_target(s, x, nx, rho, c);
+    float pc = rec_target(x, nx, rho, c.q0, c.q1, c.q3);
     float wsum = pc * c.q0.w * Mc;
-    float pp = rec_target(s, x, nx, rho, p);
+    float pp = rec_target(x, nx, rho, p.q0, p.q1, p.q3);
     float wp = pp * p.q0.w * Mp;
     wsum += wp;
     uint32_t h = rng_u32_dim(rng_cand(rng_prefix(rp.seed, pix, frame, PASS_TEMPORAL), 0u), 0u);
     float u = u01(h);
-    float4 q0 = c.q0, q1 = c.q1;
-    uint32_t tri = rec_tri(c), tag = __float_as_uint(c.q3.y);
+    float4 q0 = c.q0, q1 = c.q1, q3 = c.q3;
     float psel = pc;
     if (wp > 0.f && u * wsum < wp) {
         q0 = p.q0;
         q1 = p.q1;
-        tri = rec_tri(p);
-        tag = __float_as_uint(p.q3.y);
+        q3 = p.q3;
         psel = pp;
     }
     float Mo = Mc + Mp;
     q0.w = psel > 0.f ? wsum / (Mo * psel) : 0.f;
     q1.w = Mo;
-    store_rec(o, q0, q1, c.q2, tri, tag, 1u);
+    store_rec(o, q0, q1, c.q2, q3);
 }
 
 // x mod span for x < 2^16 via a multiply-high reciprocal (exact in that range)
@@ -263,55 +261,70 @@ __device__ __forceinline__ uint32_t mod_span(uint32_t x, uint32_t span, uint32_t
     return x - __umulhi(x, magic) * span;
 }
 
-__global__ void __launch_bounds__(128) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
-                                                        ResView in, ResView out, uint32_t frame,
-                                                        uint32_t pass) {
+// the j-th neighbour of pixel (px, py): integer offsets drawn by rejection
+// from hashed lattice points of the disk of radius R (at most 8 tries);
+// -1 when the tries run out or the point leaves the image
+__device__ __forceinline__ int spatial_neighbour(const RestirParams& rp, const GBufView& g, uint32_t cp, int px,
+                                                 int py) {
+    const int R = (int)rp.spatial_radius;
+    const uint32_t span = 2u * rp.spatial_radius + 1u;
+    for (uint32_t a = 0; a < 8u; ++a) {
+        uint32_t h = rng_u32_dim(cp, a);
+        int ox = (int)mod_span(h & 0xFFFFu, span, rp.span_magic) - R;
+        int oy = (int)mod_span(h >> 16, span, rp.span_magic) - R;
+        if ((ox != 0 || oy != 0) && ox * ox + oy * oy <= R * R) {
+            int qx = px + ox, qy = py + oy;
+            return qx >= 0 && qy >= 0 && qx < g.width && qy < g.height ? qy * g.width + qx : -1;
+        }
+    }
+    return -1;
+}
+
+// The neighbour gathers are L2 hits whose latency bounds this kernel: both
+// halves of a neighbour record are requested together (the sample's normal
+// rides in the record, so nothing else is gathered), and the next neighbour's
+// pixel is drawn while they are in flight.  At most 56 registers keep nine
+// CTAs per SM.
+__global__ void __launch_bounds__(128, 9) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
+                                                           ResView in, ResView out, uint32_t frame,
+                                                           uint32_t pass) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     Rec c = load_rec(in.rec + 4 * (size_t)pix);
     float4* o = out.rec + 4 * (size_t)pix;
-    if (__float_as_uint(c.q3.z) == 0u) {
+    if (!rec_owner_valid(c)) {
         copy_rec(o, c);
         return;
     }
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
     const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
     const float dist = c.q2.w;
-    float psel = rec_target(s, x, nx, rho, c);
+    float psel = rec_target(x, nx, rho, c.q0, c.q1, c.q3);
     float wsum = psel * c.q0.w * c.q1.w;
     float M = c.q1.w;
-    float4 q0 = c.q0, q1 = c.q1;
-    uint32_t tri = rec_tri(c), tag = __float_as_uint(c.q3.y);
+    float4 q0 = c.q0, q1 = c.q1, q3 = c.q3;
     const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_SPATIAL0 + pass);
-    const int R = (int)rp.spatial_radius;
-    const uint32_t span = 2u * rp.spatial_radius + 1u;
+    uint32_t cp_next = rng_cand(prefix, 0u);
+    int nq_next = rp.spatial_neighbours > 0 ? spatial_neighbour(rp, g, cp_next, px, py) : -1;
     for (uint32_t j = 0; j < rp.spatial_neighbours; ++j) {
-        const uint32_t cp = rng_cand(prefix, j);
-        int nq = -1;
-        for (uint32_t a = 0; a < 8u; ++a) {
-            uint32_t h = rng_u32_dim(cp, a);
-            int ox = (int)mod_span(h & 0xFFFFu, span, rp.span_magic) - R;
-            int oy = (int)mod_span(h >> 16, span, rp.span_magic) - R;
-            if ((ox != 0 || oy != 0) && ox * ox + oy * oy <= R * R) {
-                int qx = px + ox, qy = py + oy;
-                if (qx >= 0 && qy >= 0 && qx < g.width && qy < g.height) nq = qy * g.width + qx;
-                break;
-            }
+        const uint32_t cp = cp_next;
+        const int nq = nq_next;
+        // without a neighbour the pixel's own record stands in (read, not used)
+        const float4* nr = in.rec + 4 * (size_t)(nq >= 0 ? (uint32_t)nq : pix);
+        float4 n0, n1, n2, n3;
+        ld32_l2(nr, n0, n1);
+        ld32_l2(nr + 2, n2, n3);
+        if (j + 1 < rp.spatial_neighbours) {
+            cp_next = rng_cand(prefix, j + 1);
+            nq_next = spatial_neighbour(rp, g, cp_next, px, py);
         }
         if (nq < 0) continue;
-        const float4* nr = in.rec + 4 * (size_t)nq;
-        // geometry half of the neighbour record first: rejection needs only it
-        float4 n2, n3;
-        ld32(nr + 2, n2, n3);
-        if (__float_as_uint(n3.z) == 0u) continue;
+        if (!(n2.w > 0.f)) continue;
         if (dot(nx, xyz(n2)) <= rp.normal_reject_cos) continue;
         if (fabsf(dist - n2.w) > rp.depth_reject_frac * dist) continue;
-        float4 n0, n1;
-        ld32(nr, n0, n1);
-        uint32_t ntri = __float_as_uint(n3.x);
-        float pn = target_fn(s, x, nx, rho, xyz(n0), ntri, xyz(n1));
+        float pn = rec_target(x, nx, rho, n0, n1, n3);
         float wn = pn * n0.w * n1.w;
         wsum += wn;
         M += n1.w;
@@ -319,14 +332,27 @@ __global__ void __launch_bounds__(128) k_restir_spatial(SceneView s, RestirParam
         if (wn > 0.f && u * wsum < wn) {
             q0 = n0;
             q1 = n1;
-            tri = ntri;
-            tag = __float_as_uint(n3.y);
+            q3 = n3;
             psel = pn;
         }
     }
     q0.w = psel > 0.f ? wsum / (M * psel) : 0.f;
     q1.w = M;
-    store_rec(o, q0, q1, c.q2, tri, tag, 1u);
+    store_rec(o, q0, q1, c.q2, q3);
+}
+
+// words 14..15 of caller-written records: the octahedral map of the normal of
+// the sample's triangle
+__global__ void k_attach_normals(const float4* __restrict__ nrm, uint32_t num_tris, float4* __restrict__ rec,
+                                 uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4* q3 = rec + 4 * (size_t)i + 3;
+    const uint32_t tri = __float_as_uint(q3->x);
+    float2 o = make_float2(0.f, 0.f);
+    if (tri < num_tris) o = oct_encode(xyz(__ldg(nrm + tri)));
+    q3->z = o.x;
+    q3->w = o.y;
 }
 
 inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
@@ -370,5 +396,11 @@ cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, co
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     dim3 b(16, 8);
     k_restir_spatial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, in, out, frame, pass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_attach_normals(const SceneView& s, const ResView& r, cudaStream_t st) {
+    if (r.n == 0) return cudaSuccess;
+    k_attach_normals<<<(r.n + 255) / 256, 256, 0, st>>>(s.nrm, s.num_tris, r.rec, r.n);
     return cudaGetLastError();
 }

@@ -81,7 +81,7 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_scene_update", "ddgi_state_save",
            "ddgi_state_load", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
-           "restir_temporal", "restir_spatial", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
+           "restir_temporal", "restir_spatial", "ddgi_reservoirs_attach_normals", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
            "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_served_get",
            "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
@@ -123,6 +123,7 @@ def load(path: Optional[str] = None):
                                   C.POINTER(Res), C.POINTER(Res), C.c_uint32, vp]
     L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
                                  C.c_uint32, vp]
+    L.ddgi_reservoirs_attach_normals.argtypes = [vp, C.POINTER(Res), vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
     L.ddgi_reference_accumulate.argtypes = [vp, C.POINTER(Camera), C.c_uint32, C.c_uint32, vp, vp, vp]
     L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
@@ -179,8 +180,9 @@ class GBuffer:
 
 class Reservoirs:
     """One 64-byte record per pixel: a [N, 16] float32 tensor (see
-    ddgi_reservoirs): y.xyz, W | L.rgb, M | owner normal.xyz, owner distance |
-    uint32 bits of (triangle of y, tag, owner valid, 0)."""
+    ddgi_reservoirs): y.xyz, W | L.rgb, M | owner normal.xyz, owner distance
+    (> 0 exactly for a valid owner) | uint32 bits of (triangle of y, tag),
+    octahedral map of y's normal (2 floats)."""
 
     def __init__(self, n: int, device="cuda", rec: Optional[torch.Tensor] = None):
         self.n = n
@@ -198,7 +200,7 @@ class Reservoirs:
         bits = np.ascontiguousarray(rec[:, 12:16]).view(np.uint32)
         return {"y": rec[:, 0:3], "W": rec[:, 3], "L": rec[:, 4:7], "M": rec[:, 7],
                 "n": rec[:, 8:11], "dist": rec[:, 11], "tri": bits[:, 0].view(np.int32),
-                "tag": bits[:, 1], "valid": bits[:, 2]}
+                "tag": bits[:, 1], "valid": (rec[:, 11] > 0).astype(np.uint32), "ny_oct": rec[:, 14:16]}
 
 
 METRIC_SCRATCH_DOUBLES = 2048
@@ -396,6 +398,12 @@ class Context:
         self._check("restir_spatial", self.L.restir_spatial(self.h, C.byref(gc), C.byref(ic),
                                                             C.byref(oc), frame, pass_idx,
                                                             _stream(stream)))
+
+    def reservoirs_attach_normals(self, res: Reservoirs, stream=None):
+        """Words 14..15 (normal of y's triangle) of records written by the caller."""
+        rc = res.c()
+        self._check("ddgi_reservoirs_attach_normals",
+                    self.L.ddgi_reservoirs_attach_normals(self.h, C.byref(rc), _stream(stream)))
 
     def shade(self, g: GBuffer, res: Reservoirs, residual: torch.Tensor, radiance: torch.Tensor,
               stream=None):

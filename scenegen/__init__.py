@@ -171,7 +171,11 @@ class Scene:
         during the others."""
         if not self.emitter_toggle:
             return None
-        le = self.emission[self.emission.max(axis=1) > 0]
+        cached = self.__dict__.get("_emitter_le")
+        if cached is None or cached[0] is not self.emission:
+            cached = (self.emission, self.emission[self.emission.max(axis=1) > 0])
+            self.__dict__["_emitter_le"] = cached   # the scan over every triangle runs once
+        le = cached[1]
         on_even = (frame // self.emitter_toggle) % 2 == 0
         odd = (np.arange(len(le)) % 2) == 1
         lit = odd != on_even

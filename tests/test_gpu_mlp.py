@@ -271,15 +271,16 @@ def test_learned_initial_and_shade_match_oracle(dd, M):
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     rec = np.zeros((n, 16), np.float32)
     rec[:, 0:3], rec[:, 3], rec[:, 4:7], rec[:, 7] = ref.y, ref.W, ref.L, ref.M
-    rec[:, 8:11], rec[:, 11] = g.nrm, g.dist
-    bits = np.zeros((n, 4), np.uint32)
+    rec[:, 8:11], rec[:, 11] = g.nrm, np.where(g.tri >= 0, g.dist, 0.0)
+    bits = np.zeros((n, 2), np.uint32)
     bits[:, 0] = ref.tri.astype(np.int64).astype(np.uint32)
     bits[:, 1] = ref.tag
-    bits[:, 2] = (g.tri >= 0)
-    rec[:, 12:16] = bits.view(np.float32)
+    rec[:, 12:14] = bits.view(np.float32)
     res4 = np.zeros((n, 4), np.float32)
     res4[:, :3] = resid
-    ctx.shade(gg, dd.Reservoirs(n, rec=torch.from_numpy(rec).cuda()), torch.from_numpy(res4).cuda(), rad)
+    rs = dd.Reservoirs(n, rec=torch.from_numpy(rec).cuda())
+    ctx.reservoirs_attach_normals(rs)
+    ctx.shade(gg, rs, torch.from_numpy(res4).cuda(), rad)
     sref = oracle.shade(S, vol, g, ref, resid)
     assert _close_frac(rad.cpu().numpy()[:, :3], sref, 2e-2, 1e-3) >= 0.99
     assert ctx.get_status() == dd.OK

@@ -56,33 +56,40 @@ def _gbuf_to_gpu(dd, g):
 
 
 def _pack(y, W, L, M, tri, tag, nrm, dist, valid):
-    """Reservoir records in the library's layout (the owning pixel's normal,
-    distance and validity come from its G-buffer)."""
+    """Reservoir records in the library's layout (the owning pixel's normal
+    and distance come from its G-buffer; an invalid owner has distance 0).
+    Words 14..15, the normal of y's triangle, are left to
+    ddgi_reservoirs_attach_normals."""
     n = len(W)
     rec = np.zeros((n, 16), np.float32)
     rec[:, 0:3], rec[:, 3] = y, W
     rec[:, 4:7], rec[:, 7] = L, M
-    rec[:, 8:11], rec[:, 11] = nrm, dist
+    rec[:, 8:11], rec[:, 11] = nrm, np.where(np.asarray(valid) != 0, dist, 0.0)
     bits = np.zeros((n, 4), np.uint32)
     bits[:, 0] = np.asarray(tri).astype(np.int64).astype(np.uint32)
     bits[:, 1] = tag
-    bits[:, 2] = valid
-    rec[:, 12:16] = bits.view(np.float32)
+    rec[:, 12:14] = bits[:, :2].view(np.float32)
     return rec
 
 
-def _res_to_gpu(dd, r, g):
+def _upload_res(dd, ctx, rec):
+    r = dd.Reservoirs(rec.shape[0], rec=_t(rec))
+    ctx.reservoirs_attach_normals(r)
+    return r
+
+
+def _res_to_gpu(dd, ctx, r, g):
     rec = _pack(r.y, r.W, r.L, r.M, r.tri, r.tag, g.nrm, g.dist, (g.tri >= 0).astype(np.uint32))
-    return dd.Reservoirs(rec.shape[0], rec=_t(rec))
+    return _upload_res(dd, ctx, rec)
 
 
-def _synthetic_res_to_gpu(dd, res, gplanes):
+def _synthetic_res_to_gpu(dd, ctx, res, gplanes):
     r0, r1, r2 = res
     g0, g1, _ = gplanes
     valid = (np.ascontiguousarray(g1[:, 3]).view(np.uint32) != 0xFFFFFFFF).astype(np.uint32)
     rec = _pack(r0[:, :3], r0[:, 3], r1[:, :3], r1[:, 3], r2[:, 0].view(np.int32), r2[:, 1],
                 g1[:, :3], g0[:, 3], valid)
-    return dd.Reservoirs(rec.shape[0], rec=_t(rec))
+    return _upload_res(dd, ctx, rec)
 
 
 def _vol_to_gpu(ctx, vol):
@@ -215,6 +222,17 @@ def test_initial_parity(dd, orc, tiny):
     np.testing.assert_array_equal(f["valid"], valid.astype(np.uint32))
     np.testing.assert_array_equal(f["n"][valid], g1[valid, :3])
     np.testing.assert_array_equal(f["dist"][valid], g0[valid, 3])
+    # and the unit normal of its sample's triangle, octahedral map (Meyer et
+    # al. 2010): (u, v, 1 - |u| - |v|), the lower half folded, normalised
+    has = f["tri"] >= 0
+    u, v = f["ny_oct"][has, 0].astype(np.float64), f["ny_oct"][has, 1].astype(np.float64)
+    z = 1.0 - np.abs(u) - np.abs(v)
+    x = np.where(z < 0, (1.0 - np.abs(v)) * np.where(u >= 0, 1.0, -1.0), u)
+    y = np.where(z < 0, (1.0 - np.abs(u)) * np.where(v >= 0, 1.0, -1.0), v)
+    d = np.stack([x, y, z], 1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    np.testing.assert_allclose(d, S.normals[f["tri"][has]], atol=1e-6)
+    assert np.all(f["ny_oct"][~has] == 0)
     assert _frac(_close(rr.cpu().numpy()[:, :3], resid, 1e-5).all(1)) >= 0.999
     assert ctx.get_status() == dd.OK
 
@@ -227,8 +245,8 @@ def test_temporal_parity(dd, orc, tiny):
     ctx = dd.Context.from_scene(sc)
     out = dd.Reservoirs(ref.W.shape[0])
     ctx.restir_temporal(_gbuf_to_gpu(dd, f1["gbuffer"]), sc.cameras[0].pos,
-                        _res_to_gpu(dd, f1["initial"], f1["gbuffer"]),
-                        _res_to_gpu(dd, f0["final"], f0["gbuffer"]), out, 1)
+                        _res_to_gpu(dd, ctx, f1["initial"], f1["gbuffer"]),
+                        _res_to_gpu(dd, ctx, f0["final"], f0["gbuffer"]), out, 1)
     _res_compare(out.numpy(), ref, what="temporal")
 
 
@@ -239,7 +257,7 @@ def test_spatial_parity(dd, orc, tiny):
     ref = orc.restir_spatial(S, f1["gbuffer"], f1["temporal"], 1, 0)
     ctx = dd.Context.from_scene(sc)
     out = dd.Reservoirs(ref.W.shape[0])
-    ctx.restir_spatial(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["temporal"], f1["gbuffer"]),
+    ctx.restir_spatial(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, ctx, f1["temporal"], f1["gbuffer"]),
                        out, 1, 0)
     _res_compare(out.numpy(), ref, what="spatial")
 
@@ -256,7 +274,7 @@ def test_shade_parity(dd, orc, tiny):
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     resid = np.zeros((n, 4), np.float32)
     resid[:, :3] = f1["resid"]
-    ctx.shade(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, f1["final"], f1["gbuffer"]), _t(resid), rad)
+    ctx.shade(_gbuf_to_gpu(dd, f1["gbuffer"]), _res_to_gpu(dd, ctx, f1["final"], f1["gbuffer"]), _t(resid), rad)
     out = rad.cpu().numpy()
     assert _frac(_close(out[:, :3], ref, 1e-5).all(1)) >= 0.999
     assert ctx.get_status() == dd.OK
@@ -452,22 +470,22 @@ def test_apartment_resampling_passes_sampled(dd, orc, apt):
     # temporal / spatial on synthetic reservoirs
     rc = scenegen.synthetic_reservoirs(sc, n, 31)
     rp = scenegen.synthetic_reservoirs(sc, n, 32)
-    oc, op = orc.Reservoirs.from_planes(*rc), orc.Reservoirs.from_planes(*rp)
+    oc, op = orc.Reservoirs.from_planes(*rc, scene=S), orc.Reservoirs.from_planes(*rp, scene=S)
     cam_prev = np.array([4.0, 1.5, 6.0])
     tout = dd.Reservoirs(n)
-    ctx.restir_temporal(gg, cam_prev, _synthetic_res_to_gpu(dd, rc, gp),
-                        _synthetic_res_to_gpu(dd, rp, gq), tout, 5)
+    ctx.restir_temporal(gg, cam_prev, _synthetic_res_to_gpu(dd, ctx, rc, gp),
+                        _synthetic_res_to_gpu(dd, ctx, rp, gq), tout, 5)
     tref = orc.restir_temporal(S, og, oq, cam_prev, oc, op, 5, pix=sample)
     _res_compare(tout.numpy()[sample], tref, what="temporal@1080p")
     sout = dd.Reservoirs(n)
-    ctx.restir_spatial(gg, _synthetic_res_to_gpu(dd, rc, gp), sout, 5, 1)
+    ctx.restir_spatial(gg, _synthetic_res_to_gpu(dd, ctx, rc, gp), sout, 5, 1)
     sref = orc.restir_spatial(S, og, oc, 5, 1, pix=sample)
     _res_compare(sout.numpy()[sample], sref, what="spatial@1080p")
     # shade
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     rs = np.zeros((n, 4), np.float32)
     rs[:, :3] = np.random.default_rng(3).uniform(0, 0.1, (n, 3))
-    ctx.shade(gg, _synthetic_res_to_gpu(dd, rc, gp), _t(rs), rad)
+    ctx.shade(gg, _synthetic_res_to_gpu(dd, ctx, rc, gp), _t(rs), rad)
     shref = orc.shade(S, vol, og, oc, rs[:, :3].astype(np.float64), pix=sample)
     assert _frac(_close(rad.cpu().numpy()[sample, :3], shref, 1e-4).all(1)) >= 0.99
     assert ctx.get_status() == dd.OK
@@ -754,7 +772,7 @@ def test_large_initial_and_shade_sampled(dd, orc, large):
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     ctx.shade(g, out, resid, rad)
     full = orc.Reservoirs(n)                       # the oracle's shading reads full buffers
-    for a in ("y", "W", "L", "M", "tri", "tag"):
+    for a in orc.Reservoirs.FIELDS:
         getattr(full, a)[sample] = getattr(ref, a)
     full_resid = np.zeros((n, 3))
     full_resid[sample] = rref
