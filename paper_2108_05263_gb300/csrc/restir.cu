@@ -199,8 +199,10 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
 __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirParams rp, GBufView g,
                                                          float3 cam_prev, ResView cur, ResView prev,
                                                          ResView out, uint32_t frame) {
+    // rows bottom-up: the candidate pass wrote the current records top-down,
+    // so its last rows are still in L2 when this pass starts
     int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     Rec c = load_rec(cur.rec + 4 * (size_t)pix);
@@ -288,8 +290,12 @@ __device__ __forceinline__ int spatial_neighbour(const RestirParams& rp, const G
 __global__ void __launch_bounds__(128, 9) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
                                                            ResView in, ResView out, uint32_t frame,
                                                            uint32_t pass) {
+    // sweep direction alternates with the pass (temporal reuse runs
+    // bottom-up), so each pass starts on the rows its input's producer wrote
+    // last, which are still in L2
     int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    const uint32_t by = (pass & 1u) ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    int py = (int)(by * blockDim.y + threadIdx.y);
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     Rec c = load_rec(in.rec + 4 * (size_t)pix);
