@@ -74,45 +74,17 @@ struct BsdfHitQuery {
     }
 };
 
-__global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
-                                                        GBufView g, ResView out,
-                                                        float4* __restrict__ resid, uint32_t frame,
-                                                        const float2* __restrict__ bsdf_hits,
-                                                        const float4* __restrict__ ind,
-                                                        const MLPState* __restrict__ mst) {
-    int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = blockIdx.y * blockDim.y + threadIdx.y;
-    if (px >= g.width || py >= g.height) return;
-    uint32_t pix = (uint32_t)py * g.width + px;
-    float4 g1 = g.g1[pix];
-    uint32_t xtri = __float_as_uint(g1.w);
-    const uint32_t NL = s.num_emitters > 0 ? rp.n_light : 0u;
-    const uint32_t NB = rp.n_bsdf;
-    const uint32_t M = NL + NB;
-    float4* rec = out.rec + 4 * (size_t)pix;
-    if (xtri == DDGI_NONE) {
-        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                  make_float4(0.f, 0.f, 0.f, 0.f), rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
-        resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    float4 g0 = g.g0[pix], g2 = g.g2[pix];
-    const float4 geo = make_float4(g1.x, g1.y, g1.z, g0.w);
-    const f3 x = xyz(g0), nx = xyz(g1), rho = xyz(g2);
-    const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
-    const float inv_area = 1.f / s.area_total;
-    const float invM = 1.f / (float)M;
-    float wsum = 0.f;
+// streaming weighted reservoir sampling over one pixel's candidates in order
+// (emitter points first, then BSDF rays): balance-heuristic mixture density in
+// area measure, bounded geometry term in the target
+struct CandidateStream {
+    f3 rho;
+    uint32_t pix, NL, NB;
+    float invM;
+    float wsum;
     Sel sel;
-    sel.tri = DDGI_NONE;
-    sel.tag = 0u;
-    sel.p = 0.f;
-    sel.y = sel.L = f3{0.f, 0.f, 0.f};
-    f3 res = {0.f, 0.f, 0.f};
-    // streaming weighted reservoir sampling over the candidates in order
-    // (emitter points first, then BSDF rays); balance-heuristic mixture
-    // density in area measure, bounded geometry term in the target
-    auto stream_in = [&](uint32_t c, uint32_t cp, f3 y, f3 L, uint32_t tri, float d2, float cx, float cy, float pL) {
+    __device__ __forceinline__ void add(uint32_t c, uint32_t cp, f3 y, f3 L, uint32_t tri, float d2, float cx, float cy,
+                                        float pL) {
         if (cx <= 0.f) return;
         float pB = cx * (1.f / DDGI_PI) * cy / d2;
         float pmix = ((float)NL * pL + (float)NB * pB) * invM;
@@ -128,9 +100,41 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             sel.tag = pix * 64u + c;
             sel.p = ph;
         }
-    };
-    // emitter candidates: points uniform in emitter area
-    for (uint32_t c = 0; c < NL; ++c) {
+    }
+};
+
+// Candidates of step 1, emitter part: points uniform in emitter area.  The
+// stream's state after them (selected y, its radiance and target, triangle,
+// tag, running weight sum) is left in the pixel's output record for
+// k_restir_initial, which continues the same stream with the BSDF rays; the
+// split keeps this loop free of the probe query's registers (REFLECT: some
+// emitter also reflects, so its candidates need the query too).  Rows run
+// bottom-up, so that k_restir_initial, top-down, starts on rows still in L2.
+template <bool REFLECT>
+__global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView v, RestirParams rp, GBufView g,
+                                                         ResView out, uint32_t frame) {
+    int px = blockIdx.x * blockDim.x + threadIdx.x;
+    int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
+    if (px >= g.width || py >= g.height) return;
+    uint32_t pix = (uint32_t)py * g.width + px;
+    const float4 g1 = g.g1[pix];
+    if (__float_as_uint(g1.w) == DDGI_NONE) return;
+    const float4 g0 = g.g0[pix], g2 = g.g2[pix];
+    const f3 x = xyz(g0), nx = xyz(g1);
+    CandidateStream cs;
+    cs.rho = xyz(g2);
+    cs.pix = pix;
+    cs.NL = rp.n_light;
+    cs.NB = rp.n_bsdf;
+    cs.invM = 1.f / (float)(cs.NL + cs.NB);
+    cs.wsum = 0.f;
+    cs.sel.tri = DDGI_NONE;
+    cs.sel.tag = 0u;
+    cs.sel.p = 0.f;
+    cs.sel.y = cs.sel.L = f3{0.f, 0.f, 0.f};
+    const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
+    const float inv_area = 1.f / s.area_total;
+    for (uint32_t c = 0; c < cs.NL; ++c) {
         const uint32_t cp = rng_cand(prefix, c);
         float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
         float u2 = u01(rng_u32_dim(cp, 2));
@@ -150,16 +154,75 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         float cx = dot(nx, w);
         float cyn = dot(xyz(q3), w);
         f3 L;
-        if (s.emitters_reflect) {
+        if (REFLECT) {
             L = radiance_at(s, v, y, tri, x);
         } else {
             // pure emitter: one-sided Le toward x
             L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
         }
-        stream_in(c, cp, y, L, tri, d2, cx, fabsf(cyn), inv_area);
+        cs.add(c, cp, y, L, tri, d2, cx, fabsf(cyn), inv_area);
     }
-    // BSDF candidates: cosine-distributed rays, traced before this kernel;
-    // their residual transport (Sec. 3.5) on the side
+    float4* rec = out.rec + 4 * (size_t)pix;
+    st32(rec, make_float4(cs.sel.y.x, cs.sel.y.y, cs.sel.y.z, cs.wsum),
+         make_float4(cs.sel.L.x, cs.sel.L.y, cs.sel.L.z, cs.sel.p));
+    rec[3] = make_float4(__uint_as_float(cs.sel.tri), __uint_as_float(cs.sel.tag), 0.f, 0.f);
+}
+
+// Candidates of step 1, BSDF part, and the reservoir of step 2: continues the
+// stream k_restir_emitters left in the record (when there are emitter
+// candidates) with the cosine-distributed rays traced before this kernel;
+// their residual transport (Sec. 3.5) on the side.
+__global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
+                                                        GBufView g, ResView out,
+                                                        float4* __restrict__ resid, uint32_t frame,
+                                                        const float2* __restrict__ bsdf_hits,
+                                                        const float4* __restrict__ ind,
+                                                        const MLPState* __restrict__ mst, uint32_t nl) {
+    int px = blockIdx.x * blockDim.x + threadIdx.x;
+    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    if (px >= g.width || py >= g.height) return;
+    uint32_t pix = (uint32_t)py * g.width + px;
+    float4 g1 = g.g1[pix];
+    uint32_t xtri = __float_as_uint(g1.w);
+    const uint32_t NL = nl;
+    const uint32_t NB = rp.n_bsdf;
+    const uint32_t M = NL + NB;
+    float4* rec = out.rec + 4 * (size_t)pix;
+    if (xtri == DDGI_NONE) {
+        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                  make_float4(0.f, 0.f, 0.f, 0.f), rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
+        resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    float4 g0 = g.g0[pix], g2 = g.g2[pix];
+    const float4 geo = make_float4(g1.x, g1.y, g1.z, g0.w);
+    const f3 x = xyz(g0), nx = xyz(g1);
+    CandidateStream cs;
+    cs.rho = xyz(g2);
+    cs.pix = pix;
+    cs.NL = NL;
+    cs.NB = NB;
+    cs.invM = 1.f / (float)M;
+    if (NL > 0) {
+        float4 a, b;
+        ld32(rec, a, b);
+        const float4 t = rec[3];
+        cs.wsum = a.w;
+        cs.sel.y = xyz(a);
+        cs.sel.L = xyz(b);
+        cs.sel.p = b.w;
+        cs.sel.tri = __float_as_uint(t.x);
+        cs.sel.tag = __float_as_uint(t.y);
+    } else {
+        cs.wsum = 0.f;
+        cs.sel.tri = DDGI_NONE;
+        cs.sel.tag = 0u;
+        cs.sel.p = 0.f;
+        cs.sel.y = cs.sel.L = f3{0.f, 0.f, 0.f};
+    }
+    const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
+    const float inv_area = 1.f / s.area_total;
+    f3 res = {0.f, 0.f, 0.f};
     for (uint32_t c = NL; c < M; ++c) {
         const uint32_t cp = rng_cand(prefix, c);
         f3 w = bsdf_dir(rp, pix, frame, c, nx);
@@ -181,17 +244,18 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         }
         if (cx > 0.f) {
             float G = cx * fabsf(cyn) / d2;
-            if (G > 1.f) res = res + mul(rho, L) * ((1.f - 1.f / G) / (float)NB);
+            if (G > 1.f) res = res + mul(cs.rho, L) * ((1.f - 1.f / G) / (float)NB);
         }
-        stream_in(c, cp, y, L, tri, d2, cx, fabsf(cyn), pL);
+        cs.add(c, cp, y, L, tri, d2, cx, fabsf(cyn), pL);
     }
     resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
+    const Sel& sel = cs.sel;
     if (sel.tri == DDGI_NONE) {
         store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
                   rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
         return;
     }
-    float W = sel.p > 0.f ? wsum / ((float)M * sel.p) : 0.f;
+    float W = sel.p > 0.f ? cs.wsum / ((float)M * sel.p) : 0.f;
     store_rec(rec, make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
               rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))));
 }
@@ -290,12 +354,8 @@ __device__ __forceinline__ int spatial_neighbour(const RestirParams& rp, const G
 __global__ void __launch_bounds__(128, 9) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
                                                            ResView in, ResView out, uint32_t frame,
                                                            uint32_t pass) {
-    // sweep direction alternates with the pass (temporal reuse runs
-    // bottom-up), so each pass starts on the rows its input's producer wrote
-    // last, which are still in L2
     int px = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t by = (pass & 1u) ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
-    int py = (int)(by * blockDim.y + threadIdx.y);
+    int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     Rec c = load_rec(in.rec + 4 * (size_t)pix);
@@ -381,8 +441,16 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
         if (e != cudaSuccess) return e;
     }
     dim3 b(16, 8);
+    if (nl > 0) {
+        if (s.emitters_reflect)
+            k_restir_emitters<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+        else
+            k_restir_emitters<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind,
-                                                                     mlp ? mst : nullptr);
+                                                                     mlp ? mst : nullptr, nl);
     return cudaGetLastError();
 }
 
