@@ -1,7 +1,8 @@
 // Persistent ray-traversal kernel with per-warp dynamic work refill.
 //
-// Each lane owns one ray at a time and advances it by one BVH entry per loop
-// iteration; when a lane's ray finishes, the warp hands it the next work item
+// Each lane owns one ray at a time; per loop iteration it descends inner
+// nodes until the warp's lanes each hold a leaf (speculative traversal), then
+// intersects that leaf; when a lane's ray finishes, the warp hands it the next work item
 // from a warp-private pool (refilled 64 items at a time from a global
 // counter), so lanes with short rays do not idle behind lanes with long ones.
 // A generator functor turns a work index into a ray; the result of work item
@@ -19,6 +20,18 @@
 
 __device__ __forceinline__ int leaf_entry(int first, int count) { return -1 - (first * 8 + count - 1); }
 
+// pops the next entry that can still hold a hit closer than `limit`
+__device__ __forceinline__ bool pop_entry(const int* stack, const float* stack_t, int& sp, float limit, int& node) {
+    while (sp > 0) {
+        --sp;
+        if (stack_t[sp] <= limit) {
+            node = stack[sp];
+            return true;
+        }
+    }
+    return false;
+}
+
 template <class Gen, bool ANY_HIT>
 __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, uint32_t n,
                                                           uint32_t* __restrict__ counter,
@@ -32,6 +45,7 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
     float tmin = 0.f, tmax = 0.f, best_t = 0.f;
     uint32_t best_tri = DDGI_NONE;
     int node = 0, sp = 0, visits = 0;
+    bool more = false;   // node holds an entry still to visit
     int stack[TRAV_STACK];
     float stack_t[TRAV_STACK];
     // warp-uniform work pool
@@ -72,6 +86,7 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
                     best_t = tmax;
                     best_tri = DDGI_NONE;
                     node = 0;
+                    more = true;
                     sp = 0;
                     visits = 0;
                 } else {
@@ -83,9 +98,21 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
         if (__all_sync(FULL, idx == DDGI_NONE)) break;
         if (idx == DDGI_NONE) continue;
 
-        // ---- descend inner nodes until a leaf, then intersect that leaf -------
+        // ---- descend inner nodes; the first leaf a lane meets is set aside and
+        // the lane keeps descending from its stack while other lanes of the
+        // warp still look for one (Aila & Laine 2009, speculative traversal);
+        // then the set-aside leaves are intersected together
         bool done = false;
-        while (!done && node >= 0) {
+        int leaf = 0;   // set-aside leaf entry (< 0), 0: none
+        while (true) {
+            if (more && node < 0 && leaf == 0) {
+                leaf = node;
+                more = pop_entry(stack, stack_t, sp, best_t * widen, node);
+            }
+            if (!(more && node >= 0)) break;
+            // every lane still descending takes part in the vote
+            const bool all_hold = __all_sync(__activemask(), leaf != 0);
+            if (leaf != 0 && all_hold) break;
             if (++visits > TRAV_MAX_VISITS) {
                 atomicOr(s.err, ERRBIT_TRAVERSAL);
                 best_tri = DDGI_NONE;
@@ -153,24 +180,13 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
                     stack[sp] = ent[k];
                     ++sp;
                 }
-            if (nhit > 0) {
+            if (nhit > 0)
                 node = ent[0];
-            } else {
-                bool found = false;
-                while (sp > 0) {
-                    --sp;
-                    if (stack_t[sp] <= best_t * widen) {
-                        node = stack[sp];
-                        found = true;
-                        break;
-                    }
-                }
-                if (!found) done = true;
-            }
+            else
+                more = pop_entry(stack, stack_t, sp, best_t * widen, node);
         }
-        if (!done) {
-            // node < 0: a leaf entry
-            const int v = -1 - node;
+        if (!done && leaf != 0) {
+            const int v = -1 - leaf;
             const int first = v >> 3, count = (v & 7) + 1;
             for (int k = 0; k < count; ++k) {
                 uint32_t orig;
@@ -188,19 +204,8 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
                     }
                 }
             }
-            if (!done) {
-                bool found = false;
-                while (sp > 0) {
-                    --sp;
-                    if (stack_t[sp] <= best_t * widen) {
-                        node = stack[sp];
-                        found = true;
-                        break;
-                    }
-                }
-                if (!found) done = true;
-            }
         }
+        if (!done && !more) done = true;
         if (done) {
             hits[idx] = make_float2(best_t, __uint_as_float(best_tri));
             idx = DDGI_NONE;
