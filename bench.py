@@ -169,9 +169,10 @@ BYTES_PER_PX = {
 
 def launches_per_frame(spatial_passes: int) -> int:
     """Kernels of one timed frame: probe trace + blend, BSDF-ray traversal +
-    candidates, temporal, one per spatial pass, shadow-ray traversal + shade
-    (the launch lists in profiles/ show the same count)."""
-    return 2 + 2 + 1 + spatial_passes + 2
+    emitter candidates + BSDF candidates, temporal, one per spatial pass,
+    shadow-ray traversal + shade (the launch lists in profiles/ show the same
+    count)."""
+    return 2 + 3 + 1 + spatial_passes + 2
 
 
 def job_time_ms(local_ms: float, ws: int, device) -> float:
