@@ -57,8 +57,7 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
     h.tri = DDGI_NONE;
     const f3 inv = {safe_inv(ray.d.x), safe_inv(ray.d.y), safe_inv(ray.d.z)};
     const f3 oi = {ray.o.x * inv.x, ray.o.y * inv.y, ray.o.z * inv.z};
-    int stack[TRAV_STACK];
-    float stack_t[TRAV_STACK];
+    int2 stack[TRAV_STACK];   // (node, entry distance bits): one 8-byte access
     int sp = 0;
     int node = 0;
     int visits = 0;
@@ -138,19 +137,16 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
                 h.t = ray.tmax;
                 return h;
             }
-            for (int i = 0; i < ninner - 1; ++i) {
-                stack_t[sp] = tnear[i];
-                stack[sp++] = order[i];
-            }
+            for (int i = 0; i < ninner - 1; ++i) stack[sp++] = make_int2(order[i], __float_as_int(tnear[i]));
             node = order[ninner - 1];
             continue;
         }
         // pop the next node that can still hold a closer hit
         bool found = false;
         while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= h.t * widen) {
-                node = stack[sp];
+            const int2 e = stack[--sp];
+            if (__int_as_float(e.y) <= h.t * widen) {
+                node = e.x;
                 found = true;
                 break;
             }

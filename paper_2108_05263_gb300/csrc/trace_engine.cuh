@@ -20,12 +20,14 @@
 
 __device__ __forceinline__ int leaf_entry(int first, int count) { return -1 - (first * 8 + count - 1); }
 
+// traversal stack entry: (BVH entry, entry distance bits), one 8-byte access
 // pops the next entry that can still hold a hit closer than `limit`
-__device__ __forceinline__ bool pop_entry(const int* stack, const float* stack_t, int& sp, float limit, int& node) {
+__device__ __forceinline__ bool pop_entry(const int2* stack, int& sp, float limit, int& node) {
     while (sp > 0) {
         --sp;
-        if (stack_t[sp] <= limit) {
-            node = stack[sp];
+        const int2 e = stack[sp];
+        if (__int_as_float(e.y) <= limit) {
+            node = e.x;
             return true;
         }
     }
@@ -46,8 +48,7 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
     uint32_t best_tri = DDGI_NONE;
     int node = 0, sp = 0, visits = 0;
     bool more = false;   // node holds an entry still to visit
-    int stack[TRAV_STACK];
-    float stack_t[TRAV_STACK];
+    int2 stack[TRAV_STACK];
     // warp-uniform work pool
     uint32_t pool = 0, pool_end = 0;
     bool exhausted = false;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
         while (true) {
             if (more && node < 0 && leaf == 0) {
                 leaf = node;
-                more = pop_entry(stack, stack_t, sp, best_t * widen, node);
+                more = pop_entry(stack, sp, best_t * widen, node);
             }
             if (!(more && node >= 0)) break;
             // every lane still descending takes part in the vote
@@ -176,14 +177,13 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
 #pragma unroll
             for (int k = 3; k >= 1; --k)
                 if (k < nhit) {
-                    stack_t[sp] = t0[k];
-                    stack[sp] = ent[k];
+                    stack[sp] = make_int2(ent[k], __float_as_int(t0[k]));
                     ++sp;
                 }
             if (nhit > 0)
                 node = ent[0];
             else
-                more = pop_entry(stack, stack_t, sp, best_t * widen, node);
+                more = pop_entry(stack, sp, best_t * widen, node);
         }
         if (!done && leaf != 0) {
             const int v = -1 - leaf;
