@@ -1,4 +1,5 @@
-// Host BVH construction: binned surface-area-heuristic binary BVH, collapsed
+// Host BVH construction: surface-area-heuristic binary BVH (binned for large
+// nodes, an exact sweep over sorted centroids for the rest), collapsed
 // into 4-wide nodes whose children boxes are stored as SoA float4 rows so
 // that one node is eight 16-byte loads on the device.
 #include <algorithm>
@@ -40,8 +41,9 @@ struct BNode {
     int first = 0, count = 0;    // leaf range in the index array
 };
 
-constexpr int kBins = 16;
+constexpr int kBins = 128;
 constexpr int kMaxLeaf = 4;
+constexpr int kSweepMax = 4096;   // nodes up to this size: exact SAH sweep over sorted centroids
 
 struct Builder {
     const float* verts;
@@ -49,6 +51,8 @@ struct Builder {
     std::vector<float> cent;     // 3 per triangle
     std::vector<int> idx;
     std::vector<BNode> nodes;
+    std::vector<int> ord;        // sweep scratch
+    std::vector<float> rarea;
 
     int make_leaf(int first, int count, const Box& b) {
         BNode n;
@@ -76,8 +80,37 @@ struct Builder {
                 cb.grow(&cent[3 * idx[k]]);
             }
             int self;
-            int split_axis = -1, split_bin = -1;
-            if (it.count > 2) {
+            int split_axis = -1, split_bin = -1, sweep_pos = -1;
+            if (it.count > 2 && it.count <= kSweepMax) {
+                // every split position along each axis, centroids sorted
+                // (ties by triangle index, so the order is deterministic)
+                float best = FLT_MAX;
+                ord.assign(idx.begin() + it.first, idx.begin() + it.first + it.count);
+                rarea.resize(it.count);
+                for (int a = 0; a < 3; ++a) {
+                    std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+                        return cent[3 * x + a] < cent[3 * y + a] || (cent[3 * x + a] == cent[3 * y + a] && x < y);
+                    });
+                    Box acc;
+                    for (int i = it.count - 1; i >= 1; --i) {
+                        acc.grow(tbox[ord[i]]);
+                        rarea[i] = acc.area();
+                    }
+                    acc = Box();
+                    for (int i = 0; i + 1 < it.count; ++i) {
+                        acc.grow(tbox[ord[i]]);
+                        float c = acc.area() * (i + 1) + rarea[i + 1] * (it.count - i - 1);
+                        if (c < best) {
+                            best = c;
+                            split_axis = a;
+                            sweep_pos = i;
+                        }
+                    }
+                }
+                float leaf_cost = b.area() * it.count;
+                float sah = 0.5f * b.area() + best;   // traversal cost of one node
+                if (split_axis >= 0 && it.count <= kMaxLeaf && sah >= leaf_cost) split_axis = -1;
+            } else if (it.count > 2) {
                 float best = FLT_MAX;
                 for (int a = 0; a < 3; ++a) {
                     float ext = cb.hi[a] - cb.lo[a];
@@ -124,7 +157,13 @@ struct Builder {
                 if (split_axis >= 0 && it.count <= kMaxLeaf && sah >= leaf_cost) split_axis = -1;
             }
             int mid = -1;
-            if (split_axis >= 0) {
+            if (split_axis >= 0 && sweep_pos >= 0) {
+                const int a = split_axis;
+                std::sort(idx.begin() + it.first, idx.begin() + it.first + it.count, [&](int x, int y) {
+                    return cent[3 * x + a] < cent[3 * y + a] || (cent[3 * x + a] == cent[3 * y + a] && x < y);
+                });
+                mid = it.first + sweep_pos + 1;
+            } else if (split_axis >= 0) {
                 float ext = cb.hi[split_axis] - cb.lo[split_axis];
                 float scale = kBins / ext;
                 auto beg = idx.begin() + it.first, end = beg + it.count;
