@@ -3,6 +3,7 @@
 // into 4-wide nodes whose children boxes are stored as SoA float4 rows so
 // that one node is eight 16-byte loads on the device.
 #include <algorithm>
+#include <array>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -246,6 +247,82 @@ void build_bvh4(const float* verts, uint32_t num_tris, Bvh4* out) {
         out->depth = 1;
         return;
     }
+    // SAH-optimal collapse (dynamic programming over the binary tree):
+    // cost[n][k] is the least cost of the subtree of binary node n spread
+    // over at most k slots of the enclosing 4-wide node; a slot holding an
+    // inner node costs its area x kNodeCost plus its own children's best
+    // spread over 4 slots, a leaf its area x triangles x kTriCost
+    constexpr double kNodeCost = 1.0, kTriCost = 0.4;
+    const size_t BN = b.nodes.size();
+    std::vector<std::array<double, 5>> cost(BN);
+    std::vector<std::array<signed char, 5>> split(BN);   // k1 of the best spread over exactly k slots, 0: fewer
+    {
+        std::vector<int> post;
+        post.reserve(BN);
+        std::vector<int> st{root};
+        while (!st.empty()) {   // reverse pre-order (node, right, left) = a post-order
+            int n = st.back();
+            st.pop_back();
+            post.push_back(n);
+            if (b.nodes[n].left >= 0) {
+                st.push_back(b.nodes[n].left);
+                st.push_back(b.nodes[n].right);
+            }
+        }
+        for (auto it = post.rbegin(); it != post.rend(); ++it) {
+            const int n = *it;
+            const BNode& bn = b.nodes[n];
+            const double A = bn.box.area();
+            if (bn.left < 0) {
+                for (int k = 1; k <= 4; ++k) {
+                    cost[n][k] = A * bn.count * kTriCost;
+                    split[n][k] = 0;
+                }
+                continue;
+            }
+            const auto& L = cost[bn.left];
+            const auto& R = cost[bn.right];
+            double open[5] = {0, 0, 0, 0, 0};
+            signed char ok1[5] = {0, 0, 0, 0, 0};
+            for (int k = 2; k <= 4; ++k) {
+                open[k] = 1e300;
+                for (int k1 = 1; k1 < k; ++k1) {
+                    double c = L[k1] + R[k - k1];
+                    if (c < open[k]) {
+                        open[k] = c;
+                        ok1[k] = (signed char)k1;
+                    }
+                }
+            }
+            cost[n][1] = A * kNodeCost + open[4];
+            split[n][1] = 0;
+            for (int k = 2; k <= 4; ++k) {
+                if (open[k] < cost[n][k - 1]) {
+                    cost[n][k] = open[k];
+                    split[n][k] = ok1[k];
+                } else {
+                    cost[n][k] = cost[n][k - 1];
+                    split[n][k] = 0;
+                }
+            }
+        }
+    }
+    // the slots of binary node n spread over at most k slots
+    auto collect = [&](int n, int k, std::vector<int>& out) {
+        std::vector<std::pair<int, int>> st{{n, k}};
+        while (!st.empty()) {
+            auto [m, km] = st.back();
+            st.pop_back();
+            while (km > 1 && split[m][km] == 0) --km;
+            if (km <= 1 || b.nodes[m].left < 0) {
+                out.push_back(m);
+                continue;
+            }
+            const int k1 = split[m][km];
+            st.push_back({b.nodes[m].right, km - k1});
+            st.push_back({b.nodes[m].left, k1});
+        }
+    };
     queue.push_back({root, 1});
     uint32_t max_depth = 1;
     for (size_t qi = 0; qi < queue.size(); ++qi) {
@@ -254,23 +331,18 @@ void build_bvh4(const float* verts, uint32_t num_tris, Bvh4* out) {
         if (b.nodes[bn].left < 0) {
             ch.push_back(bn);   // a leaf root: one leaf slot
         } else {
-            ch.push_back(b.nodes[bn].left);
-            ch.push_back(b.nodes[bn].right);
-            while (ch.size() < 4) {
-                int best = -1;
-                float ba = -1.f;
-                for (int i = 0; i < (int)ch.size(); ++i) {
-                    const BNode& c = b.nodes[ch[i]];
-                    if (c.left >= 0 && c.box.area() > ba) {
-                        ba = c.box.area();
-                        best = i;
-                    }
+            // the node's children: its two binary children spread over 4 slots
+            double bestc = 1e300;
+            int bk1 = 1;
+            for (int k1 = 1; k1 < 4; ++k1) {
+                double c = cost[b.nodes[bn].left][k1] + cost[b.nodes[bn].right][4 - k1];
+                if (c < bestc) {
+                    bestc = c;
+                    bk1 = k1;
                 }
-                if (best < 0) break;
-                int x = ch[best];
-                ch[best] = b.nodes[x].left;
-                ch.push_back(b.nodes[x].right);
             }
+            collect(b.nodes[bn].left, bk1, ch);
+            collect(b.nodes[bn].right, 4 - bk1, ch);
         }
         slots.push_back(ch);
         for (int c : ch)
