@@ -45,6 +45,8 @@ struct BNode {
 constexpr int kBins = 128;
 constexpr int kMaxLeaf = 4;
 constexpr int kSweepMax = 4096;   // nodes up to this size: exact SAH sweep over sorted centroids
+constexpr int kSplitDepth = 2;    // early split clipping: at most 2^kSplitDepth references per triangle
+constexpr double kSplitAreaFactor = 4.0;   // split boxes larger than this x the mean triangle box
 
 struct Builder {
     const float* verts;
@@ -197,28 +199,116 @@ struct Builder {
     }
 };
 
+// Sutherland-Hodgman clip of a convex polygon against one axis-aligned
+// half-space (keep side <= c when `below`, else >= c)
+int clip_poly(const float (*in)[3], int n, int axis, float c, bool below, float (*out)[3]) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const float* p = in[i];
+        const float* q = in[(i + 1) % n];
+        const float dp = below ? c - p[axis] : p[axis] - c;
+        const float dq = below ? c - q[axis] : q[axis] - c;
+        if (dp >= 0.f) {
+            for (int a = 0; a < 3; ++a) out[m][a] = p[a];
+            ++m;
+        }
+        if ((dp >= 0.f) != (dq >= 0.f)) {
+            const float s = dp / (dp - dq);
+            for (int a = 0; a < 3; ++a) out[m][a] = p[a] + s * (q[a] - p[a]);
+            out[m][axis] = c;
+            ++m;
+        }
+    }
+    return m;
+}
+
+struct SplitRef {
+    int tri;
+    Box box;
+};
+
+// Early split clipping (Ernst & Greiner 2007): a triangle whose box is large
+// is entered as several references, each with the box of the part of the
+// triangle inside one half of its parent box (halved along the longest axis)
+void split_refs(int tri, const float (*poly)[3], int n, const Box& box, int depth, float area_limit,
+                std::vector<SplitRef>& out) {
+    float ext[3];
+    for (int a = 0; a < 3; ++a) ext[a] = box.hi[a] - box.lo[a];
+    if (depth >= kSplitDepth || box.area() <= area_limit || n < 3) {
+        out.push_back({tri, box});
+        return;
+    }
+    const int axis = ext[0] >= ext[1] && ext[0] >= ext[2] ? 0 : (ext[1] >= ext[2] ? 1 : 2);
+    const float c = 0.5f * (box.lo[axis] + box.hi[axis]);
+    for (int side = 0; side < 2; ++side) {
+        float part[16][3];
+        const int m = clip_poly(poly, n, axis, c, side == 0, part);
+        if (m < 3) continue;
+        Box pb;
+        for (int i = 0; i < m; ++i) pb.grow(part[i]);
+        for (int a = 0; a < 3; ++a) {   // stay inside the parent box
+            pb.lo[a] = std::max(pb.lo[a], box.lo[a]);
+            pb.hi[a] = std::min(pb.hi[a], box.hi[a]);
+        }
+        if (!pb.valid()) continue;
+        split_refs(tri, part, m, pb, depth + 1, area_limit, out);
+    }
+}
+
 }  // namespace
 
-void build_bvh4(const float* verts, uint32_t num_tris, Bvh4* out) {
+void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* out) {
     Builder b;
     b.verts = verts;
     int T = (int)num_tris;
-    b.tbox.resize(T);
-    b.cent.resize(3 * (size_t)T);
-    b.idx.resize(T);
+    // references: one per triangle, several for triangles with large boxes
+    std::vector<SplitRef> refs;
+    refs.reserve((size_t)T + T / 4);
+    std::vector<Box> tb(T);
+    double mean_area = 0.0;
     for (int t = 0; t < T; ++t) {
         const float* v = verts + 9 * (size_t)t;
-        for (int k = 0; k < 3; ++k) b.tbox[t].grow(v + 3 * k);
-        for (int a = 0; a < 3; ++a) b.cent[3 * t + a] = (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
-        b.idx[t] = t;
+        for (int k = 0; k < 3; ++k) tb[t].grow(v + 3 * k);
+        mean_area += tb[t].area();
     }
-    b.nodes.reserve(2 * (size_t)T + 1);
-    int root = T > 0 ? b.build(T) : -1;
+    mean_area = T > 0 ? mean_area / T : 0.0;
+    const float area_limit = (float)(kSplitAreaFactor * mean_area);
+    std::vector<char> was_split(T, 0);
+    for (int t = 0; t < T; ++t) {
+        const float* v = verts + 9 * (size_t)t;
+        if (split_large && kSplitDepth > 0 && tb[t].area() > area_limit) {
+            float poly[3][3];
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 3; ++a) poly[k][a] = v[3 * k + a];
+            const size_t before = refs.size();
+            split_refs(t, poly, 3, tb[t], 0, area_limit, refs);
+            was_split[t] = refs.size() - before > 1;
+            if (refs.size() == before) refs.push_back({t, tb[t]});
+        } else {
+            refs.push_back({t, tb[t]});
+        }
+    }
+    const int S = (int)refs.size();
+    b.tbox.resize(S);
+    b.cent.resize(3 * (size_t)S);
+    b.idx.resize(S);
+    for (int r = 0; r < S; ++r) {
+        const int t = refs[r].tri;
+        const float* v = verts + 9 * (size_t)t;
+        b.tbox[r] = refs[r].box;
+        for (int a = 0; a < 3; ++a)
+            b.cent[3 * r + a] = was_split[t] ? 0.5f * (refs[r].box.lo[a] + refs[r].box.hi[a])
+                                         : (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
+        b.idx[r] = r;
+    }
+    b.nodes.reserve(2 * (size_t)S + 1);
+    int root = S > 0 ? b.build(S) : -1;
 
-    // triangles in leaf order (the index array is already leaf-ordered)
-    out->tris.assign(12 * (size_t)T, 0.f);
-    for (int k = 0; k < T; ++k) {
-        int t = b.idx[k];
+    // triangles in leaf order (the index array is already leaf-ordered); a
+    // split triangle appears once per reference
+    out->tris.assign(12 * (size_t)S, 0.f);
+    for (int k = 0; k < S; ++k) {
+        int t = refs[b.idx[k]].tri;
         const float* v = verts + 9 * (size_t)t;
         float* o = &out->tris[12 * (size_t)k];
         uint32_t tid = (uint32_t)t;

@@ -388,11 +388,11 @@ cudaError_t ensure_hits(ddgi_ctx* c, size_t n, cudaStream_t st) {
 // their identity-pose vertices, and the BVH4 nodes whose subtrees hold any of
 // them, grouped by depth (deepest first) for the bottom-up refit.
 cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bvh) {
-    const uint32_t T = c->T, I = scene->num_instances, N = bvh.num_nodes;
+    const uint32_t S = (uint32_t)(bvh.tris.size() / 12), I = scene->num_instances, N = bvh.num_nodes;
     std::vector<uint4> map;
     std::vector<float4> obj;
-    std::vector<uint8_t> slot_moving(T, 0);
-    for (uint32_t k = 0; k < T; ++k) {
+    std::vector<uint8_t> slot_moving(S, 0);
+    for (uint32_t k = 0; k < S; ++k) {
         uint32_t orig;
         std::memcpy(&orig, &bvh.tris[12ull * k + 3], 4);
         const int32_t inst = scene->tri_instance[orig];
@@ -433,7 +433,7 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
             if (dirty[n] && depth[n] == d) list.push_back(n);
         c->refit_levels.push_back((uint32_t)list.size());
     }
-    std::vector<int32_t> ti(scene->tri_instance, scene->tri_instance + T);
+    std::vector<int32_t> ti(scene->tri_instance, scene->tri_instance + c->T);
     c->I = I;
     c->NI = (uint32_t)map.size();
     c->xf_cur.assign(12ull * I, 0.0);
@@ -445,7 +445,7 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
         ident[3 * k + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
         ident[3 * k + 2] = make_float4(0.f, 0.f, 1.f, 0.f);
     }
-    cudaError_t e = dalloc(c, &c->tri_inst, T);
+    cudaError_t e = dalloc(c, &c->tri_inst, c->T);
     if (e == cudaSuccess) e = dalloc(c, &c->inst_map, map.size());
     if (e == cudaSuccess) e = dalloc(c, &c->inst_obj, obj.size());
     if (e == cudaSuccess) e = dalloc(c, &c->inst_xf, 3ull * I);
@@ -454,7 +454,7 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
-    up(c->tri_inst, ti.data(), T * sizeof(int32_t));
+    up(c->tri_inst, ti.data(), c->T * sizeof(int32_t));
     up(c->inst_map, map.data(), map.size() * sizeof(uint4));
     up(c->inst_obj, obj.data(), obj.size() * sizeof(float4));
     up(c->inst_xf, ident.data(), ident.size() * sizeof(float4));
@@ -559,7 +559,8 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
 
     // scene tables (host), fp64 geometry for normals / areas
     Bvh4 bvh;
-    build_bvh4(scene->vertices, T, &bvh);
+    // instanced scenes refit slot boxes from whole triangles: no split references
+    build_bvh4(scene->vertices, T, scene->num_instances == 0, &bvh);
     ctx->bvh_nodes = bvh.num_nodes;
     ctx->bvh_depth = bvh.depth;
     std::vector<float4> nrm(T), alb(T), emi(T);
@@ -640,7 +641,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
 #define ALLOC(ptr, n)                                 \
     if (e == cudaSuccess) e = dalloc(ctx, &ctx->ptr, (n));
     ALLOC(nodes, 8ull * bvh.num_nodes)
-    ALLOC(tris, 3ull * T)
+    ALLOC(tris, bvh.tris.size() / 4)
     ALLOC(nrm, T)
     ALLOC(alb, T)
     ALLOC(emi, T)
