@@ -77,6 +77,7 @@ struct ddgi_ctx {
     float* pin = nullptr;
     cudaEvent_t pin_ev = nullptr;
     bool pin_pending = false;
+    bool offsets_used = false;       // some probe offset may be non-zero (relocation ran or offsets were set)
     uint64_t device_bytes = 0;
     std::vector<void*> allocs;
     std::string last_error;
@@ -170,6 +171,7 @@ VolumeView volume_view(ddgi_ctx* c) {
     v.irr = c->irr;
     v.depth = c->depth;
     v.offset = c->offset;
+    v.has_offset = c->offsets_used ? 1 : 0;
     v.origin = make_float3(c->cfg.origin[0], c->cfg.origin[1], c->cfg.origin[2]);
     v.spacing = make_float3(c->cfg.spacing[0], c->cfg.spacing[1], c->cfg.spacing[2]);
     v.counts = make_int3(c->cfg.counts[0], c->cfg.counts[1], c->cfg.counts[2]);
@@ -854,6 +856,7 @@ ddgi_status ddgi_probe_relocate(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     ProbeParams p;
     probe_params(ctx, frame, &p);
     CK(launch_probe_relocate(volume_view(ctx), p, ctx->rays, ctx->offset, (cudaStream_t)stream));
+    ctx->offsets_used = true;
     return DDGI_OK;
 }
 
@@ -885,7 +888,10 @@ ddgi_status ddgi_probe_state_set(ddgi_ctx* ctx, const float* irr, const float* d
     const size_t P = ctx->P, ti = ctx->cfg.irr_texels + 2, td = ctx->cfg.depth_texels + 2;
     if (irr) CK(cudaMemcpyAsync(ctx->irr, irr, P * ti * ti * sizeof(float4), cudaMemcpyDefault, st));
     if (depth) CK(cudaMemcpyAsync(ctx->depth, depth, P * td * td * sizeof(float2), cudaMemcpyDefault, st));
-    if (offsets) CK(cudaMemcpyAsync(ctx->offset, offsets, P * sizeof(float4), cudaMemcpyDefault, st));
+    if (offsets) {
+        CK(cudaMemcpyAsync(ctx->offset, offsets, P * sizeof(float4), cudaMemcpyDefault, st));
+        ctx->offsets_used = true;
+    }
     CK(cudaStreamSynchronize(st));
     ctx->updates = updates;
     return DDGI_OK;
@@ -970,6 +976,7 @@ ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, v
     CK(cudaMemcpyAsync(ctx->irr, b + L.irr, L.dep - L.irr, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->depth, b + L.dep, L.off - L.dep, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->offset, b + L.off, L.xf - L.off, cudaMemcpyHostToDevice, st));
+    ctx->offsets_used = true;
     if (ctx->cfg.learned_target) {
         float* const dst32[4] = {ctx->mlp_params, ctx->mlp_m, ctx->mlp_v, ctx->mlp_ema};
         for (int k = 0; k < 4; ++k)

@@ -112,6 +112,7 @@ struct VolumeView {
     float4* irr;             // [P][ti*ti] rgb, 0
     float2* depth;           // [P][td*td] mean, mean square
     const float4* offset;    // [P] xyz, 0
+    int has_offset;          // 0 while every offset is zero (they are then not read)
     float3 origin, spacing;
     int3 counts;
     int irr_n, depth_n;      // interior texels per side
@@ -196,7 +197,7 @@ __device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) 
 }
 
 __device__ __forceinline__ f3 probe_pos(const VolumeView& v, int i, int j, int k, int p) {
-    float4 o = __ldg(v.offset + p);
+    const float4 o = v.has_offset ? __ldg(v.offset + p) : make_float4(0.f, 0.f, 0.f, 0.f);
     return {v.origin.x + v.spacing.x * i + o.x, v.origin.y + v.spacing.y * j + o.y,
             v.origin.z + v.spacing.z * k + o.z};
 }
@@ -220,6 +221,10 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
         al[a] = cnt[a] > 1 ? fminf(fmaxf(g[a] - (float)b, 0.f), 1.f) : 0.f;
     }
     const int ti = v.irr_n + 2, td = v.depth_n + 2;
+    // the irradiance taps depend on n only: one set for the 8 probes
+    const Taps tn = oct_taps(n, v.irr_n);
+    const float n00 = (1.f - tn.ax) * (1.f - tn.ay), n10 = tn.ax * (1.f - tn.ay);
+    const float n01 = (1.f - tn.ax) * tn.ay, n11 = tn.ax * tn.ay;
     float sw = 0.f;
     f3 se = {0.f, 0.f, 0.f};
 #pragma unroll 2
@@ -247,7 +252,10 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
         w = fmaxf(w, 1e-6f);
         if (w < 0.2f) w = w * w * w * 25.f;
         w *= tri;
-        f3 e = sample_irr(v.irr + (size_t)p * ti * ti, v.irr_n, n);
+        const float4* tile = v.irr + (size_t)p * ti * ti + tn.i00;
+        const float4 a = __ldg(tile), b = __ldg(tile + 1), cc = __ldg(tile + ti), d = __ldg(tile + ti + 1);
+        const f3 e = {n00 * a.x + n10 * b.x + n01 * cc.x + n11 * d.x, n00 * a.y + n10 * b.y + n01 * cc.y + n11 * d.y,
+                      n00 * a.z + n10 * b.z + n01 * cc.z + n11 * d.z};
         se = se + e * w;
         sw += w;
     }
