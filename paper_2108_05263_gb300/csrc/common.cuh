@@ -318,6 +318,16 @@ __device__ __forceinline__ uint32_t sample_emitter(const SceneView& s, float u) 
     return i;
 }
 
+// the same search on tables staged in shared memory
+__device__ __forceinline__ uint32_t sample_emitter_smem(const float* cdf, const uint32_t* guide, uint32_t E,
+                                                        uint32_t G, float u) {
+    const float target = u * cdf[E - 1];
+    uint32_t j = min((uint32_t)(u * (float)G), G - 1);
+    uint32_t i = guide[j];
+    while (i < E - 1 && !(target < cdf[i])) ++i;
+    return i;
+}
+
 // orthonormal basis around n (Duff et al., JCGT 2017)
 __device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
     float sign = n.z >= 0.f ? 1.f : -1.f;

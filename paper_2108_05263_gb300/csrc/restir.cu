@@ -3,6 +3,8 @@
 // residual), temporal reuse and spatial reuse with the cached probe query of
 // Sec. 3.6.  One thread per pixel; SoA planes read and written as 16-byte
 // records.
+#include <algorithm>
+
 #include "internal.h"
 #include "trace_engine.cuh"
 
@@ -103,20 +105,19 @@ struct CandidateStream {
     }
 };
 
-// Candidates of step 1, emitter part: points uniform in emitter area.  The
-// stream's state after them (selected y, its radiance and target, triangle,
-// tag, running weight sum) is left in the pixel's output record for
-// k_restir_initial, which continues the same stream with the BSDF rays; the
-// split keeps this loop free of the probe query's registers (REFLECT: some
-// emitter also reflects, so its candidates need the query too).  Rows run
-// bottom-up, so that k_restir_initial, top-down, starts on rows still in L2.
-template <bool REFLECT>
-__global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView v, RestirParams rp, GBufView g,
-                                                         ResView out, uint32_t frame) {
-    int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
-    if (px >= g.width || py >= g.height) return;
-    uint32_t pix = (uint32_t)py * g.width + px;
+// Candidates of step 1, emitter part, for one pixel: points uniform in
+// emitter area.  The stream's state after them (selected y, its radiance and
+// target, triangle, tag, running weight sum) is left in the pixel's output
+// record for k_restir_initial, which continues the same stream with the BSDF
+// rays; the split keeps this loop free of the probe query's registers
+// (REFLECT: some emitter also reflects, so its candidates need the query
+// too).  SMEM: the emitter records, cumulative areas and guide table are read
+// from shared memory (e_cdf, e_guide, e_vert), else from the scene tables.
+template <bool REFLECT, bool SMEM>
+__device__ __forceinline__ void emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
+                                                   const GBufView& g, const ResView& out, uint32_t frame,
+                                                   uint32_t pix, const float4* e_vert, const float* e_cdf,
+                                                   const uint32_t* e_guide) {
     const float4 g1 = g.g1[pix];
     if (__float_as_uint(g1.w) == DDGI_NONE) return;
     const float4 g0 = g.g0[pix], g2 = g.g2[pix];
@@ -138,11 +139,22 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
         const uint32_t cp = rng_cand(prefix, c);
         float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
         float u2 = u01(rng_u32_dim(cp, 2));
-        uint32_t e = sample_emitter(s, u0);
-        const float4* er = s.evert + 4 * (size_t)e;
         float4 q0, q1, q2, q3;
-        ld32(er, q0, q1);
-        ld32(er + 2, q2, q3);
+        if (SMEM) {
+            // four planes of E records each (SoA: consecutive emitters on
+            // consecutive 16-byte bank groups)
+            const uint32_t E = s.num_emitters;
+            const uint32_t e = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u0);
+            q0 = e_vert[e];
+            q1 = e_vert[E + e];
+            q2 = e_vert[2 * E + e];
+            q3 = e_vert[3 * E + e];
+        } else {
+            const uint32_t e = sample_emitter(s, u0);
+            const float4* er = s.evert + 4 * (size_t)e;
+            ld32(er, q0, q1);
+            ld32(er + 2, q2, q3);
+        }
         const uint32_t tri = __float_as_uint(q0.w);
         float sq = sqrtf(u1);
         float b1 = sq * (1.f - u2), b2 = sq * u2;
@@ -166,6 +178,48 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
     st32(rec, make_float4(cs.sel.y.x, cs.sel.y.y, cs.sel.y.z, cs.wsum),
          make_float4(cs.sel.L.x, cs.sel.L.y, cs.sel.L.z, cs.sel.p));
     rec[3] = make_float4(__uint_as_float(cs.sel.tri), __uint_as_float(cs.sel.tag), 0.f, 0.f);
+}
+
+// one thread per pixel, emitter tables from global memory (L1); rows run
+// bottom-up, so that k_restir_initial, top-down, starts on rows still in L2
+template <bool REFLECT>
+__global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView v, RestirParams rp, GBufView g,
+                                                         ResView out, uint32_t frame) {
+    int px = blockIdx.x * blockDim.x + threadIdx.x;
+    int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
+    if (px >= g.width || py >= g.height) return;
+    emitter_candidates<REFLECT, false>(s, v, rp, g, out, frame, (uint32_t)py * g.width + px, nullptr, nullptr,
+                                       nullptr);
+}
+
+// Persistent variant for emitter tables that fit in shared memory: each CTA
+// copies the records, cumulative areas and guide table once, then walks
+// 32 x 16 pixel tiles (bottom row of tiles first); the 32-byte record reads
+// of the candidates then come from shared memory instead of the L1 that the
+// per-pixel kernel saturates.
+constexpr int kEmitTileW = 32, kEmitTileH = 16;
+template <bool REFLECT>
+__global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
+                                                              ResView out, uint32_t frame) {
+    extern __shared__ float4 e_smem[];
+    const uint32_t E = s.num_emitters, G = s.guide_size;
+    float4* e_vert = e_smem;
+    float* e_cdf = reinterpret_cast<float*>(e_smem + 4 * (size_t)E);
+    uint32_t* e_guide = reinterpret_cast<uint32_t*>(e_cdf + E);
+    for (uint32_t i = threadIdx.x; i < 4 * E; i += blockDim.x) e_vert[(i & 3u) * E + (i >> 2)] = __ldg(s.evert + i);
+    for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) e_cdf[i] = __ldg(s.cdf + i);
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) e_guide[i] = __ldg(s.guide + i);
+    __syncthreads();
+    const int tiles_x = (g.width + kEmitTileW - 1) / kEmitTileW;
+    const int tiles_y = (g.height + kEmitTileH - 1) / kEmitTileH;
+    const int tx = threadIdx.x % kEmitTileW, ty = threadIdx.x / kEmitTileW;
+    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
+        const int bx = t % tiles_x, by = tiles_y - 1 - t / tiles_x;
+        const int px = bx * kEmitTileW + tx, py = by * kEmitTileH + ty;
+        if (px >= g.width || py >= g.height) continue;
+        emitter_candidates<REFLECT, true>(s, v, rp, g, out, frame, (uint32_t)py * g.width + px, e_vert, e_cdf,
+                                          e_guide);
+    }
 }
 
 // Candidates of step 1, BSDF part, and the reservoir of step 2: continues the
@@ -425,6 +479,40 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 
 }  // namespace
 
+// the emitter-candidate pass: the shared-memory kernel when the emitter
+// tables fit beside enough resident threads, else the per-pixel kernel
+cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
+                                      const GBufView& g, const ResView& out, uint32_t frame, cudaStream_t st) {
+    const size_t smem = sizeof(float4) * 4 * (size_t)s.num_emitters +
+                        sizeof(float) * (size_t)s.num_emitters + sizeof(uint32_t) * (size_t)s.guide_size;
+    static int dev_sms = 0, max_smem = 0;
+    if (dev_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    if (smem <= 96 * 1024 && (int)smem <= max_smem) {
+        auto kern = s.emitters_reflect ? k_restir_emitters_smem<true> : k_restir_emitters_smem<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm > 0) {
+            const int tiles = ((g.width + kEmitTileW - 1) / kEmitTileW) * ((g.height + kEmitTileH - 1) / kEmitTileH);
+            const int grid = std::min(tiles, dev_sms * per_sm);
+            kern<<<grid, 512, smem, st>>>(s, v, rp, g, out, frame);
+            return cudaGetLastError();
+        }
+    }
+    dim3 b(16, 8);
+    if (s.emitters_reflect)
+        k_restir_emitters<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+    else
+        k_restir_emitters<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, float2* hits, uint32_t* counter, const MLPView* mlp,
@@ -442,11 +530,7 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
     }
     dim3 b(16, 8);
     if (nl > 0) {
-        if (s.emitters_reflect)
-            k_restir_emitters<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
-        else
-            k_restir_emitters<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
-        e = cudaGetLastError();
+        e = launch_emitter_candidates(s, v, rp, g, out, frame, st);
         if (e != cudaSuccess) return e;
     }
     k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind,
