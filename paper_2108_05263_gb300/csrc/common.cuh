@@ -206,6 +206,9 @@ __device__ __forceinline__ f3 probe_pos(const VolumeView& v, int i, int j, int k
 // probe query: irradiance E(q, n) blended from the 8 surrounding probes
 // (trilinear x wrap shading x cubed Chebyshev visibility, crushed below 0.2)
 // ---------------------------------------------------------------------------
+// U: unroll factor of the loop over the 8 probes (kernels differ in which
+// register / latency balance suits them)
+template <int U = 1>
 __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
     float g[3] = {(q.x - v.origin.x) / v.spacing.x, (q.y - v.origin.y) / v.spacing.y,
                   (q.z - v.origin.z) / v.spacing.z};
@@ -227,7 +230,7 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
     const float n01 = (1.f - tn.ax) * tn.ay, n11 = tn.ax * tn.ay;
     float sw = 0.f;
     f3 se = {0.f, 0.f, 0.f};
-#pragma unroll 2
+#pragma unroll U
     for (int c = 0; c < 8; ++c) {
         int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
         int gi = min(base[0] + ox, cnt[0] - 1);
@@ -263,6 +266,7 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
 }
 
 // view-path bias (Sec. 3.4): move from y toward the previous vertex `from`
+template <int U = 1>
 __device__ __forceinline__ f3 ddgi_irradiance_biased(const VolumeView& v, f3 y, f3 n, f3 from) {
     f3 d = from - y;
     float l = length(d);
@@ -271,10 +275,11 @@ __device__ __forceinline__ f3 ddgi_irradiance_biased(const VolumeView& v, f3 y, 
         float dv = fminf(0.2f * v.min_spacing, 0.5f * l);
         q = y + d * (dv / l);
     }
-    return ddgi_irradiance(v, q, n);
+    return ddgi_irradiance<U>(v, q, n);
 }
 
 // outgoing radiance (Le + L_DDGI+)(y, y -> from) of a triangle point
+template <int U = 1>
 __device__ __forceinline__ f3 radiance_at(const SceneView& s, const VolumeView& v, f3 y,
                                           uint32_t tri, f3 from) {
     f3 n = xyz(__ldg(s.nrm + tri));
@@ -282,7 +287,7 @@ __device__ __forceinline__ f3 radiance_at(const SceneView& s, const VolumeView& 
     f3 le = xyz(__ldg(s.emi + tri));
     f3 rho = xyz(__ldg(s.alb + tri));
     if (any_pos(rho)) {
-        f3 E = ddgi_irradiance_biased(v, y, n, from);
+        f3 E = ddgi_irradiance_biased<U>(v, y, n, from);
         le = le + mul(rho, E) * (1.f / DDGI_PI);
     }
     return le;

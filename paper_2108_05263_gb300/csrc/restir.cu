@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             const uint32_t qi = pix * NB + (c - NL);
             L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
         } else {
-            L = radiance_at(s, v, y, tri, x);
+            L = radiance_at<4>(s, v, y, tri, x);
         }
         if (cx > 0.f) {
             float G = cx * fabsf(cyn) / d2;
