@@ -138,8 +138,9 @@ def kernel_source_hash():
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+    """DRAM bytes per launch of `kernel` (or per run of a pass) from the
+    committed ncu summary, if it was taken on the current kernel sources (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -306,13 +307,16 @@ def run_ours(args, ws, rank, local):
     dom_key = "restir_spatial" if dom.startswith("restir_spatial") else dom
     if dom_key in BYTES_PER_PX:
         achieved = BYTES_PER_PX[dom_key] * N / (per_pass[dom] * 1e-3) / 1e9
-        kernel = {"restir_initial": "k_restir_initial", "restir_temporal": "k_restir_temporal",
-                  "restir_spatial": "k_restir_spatial", "ddgi_shade": "k_shade"}[dom_key]
-        roof = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": ncu_traffic(kernel),
-                "note": "algorithmic bytes = compulsory per-pixel plane traffic; ray traversal of "
-                        "this kernel is L2/latency-bound, see the per-pass list"}
+        # a pass and the kernels it launches; traffic = their DRAM bytes per pass
+        kernels = {"restir_initial": "k_trace<BsdfGen> + k_restir_emitters_smem + k_restir_initial",
+                   "restir_temporal": "k_restir_temporal", "restir_spatial": "k_restir_spatial",
+                   "ddgi_shade": "k_trace<ShadowGen> + k_shade"}[dom_key]
+        roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": ncu_traffic(dom_key),
+                "note": "algorithmic bytes = compulsory per-pixel plane traffic of the pass, timed by CUDA "
+                        "events around its launches; its time goes into BVH traversal and candidate "
+                        "arithmetic on L2-resident scene data (see the per-pass list)"}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None}
