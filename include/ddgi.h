@@ -126,7 +126,8 @@ typedef struct {
 
 /* Reservoirs (device): one 64-byte record per pixel, 64-byte aligned, as
  * 16 floats:
- *   [0..3]   y.xyz (selected point), W (unbiased contribution weight)
+ *   [0..3]   y.xyz (selected point), W (unbiased contribution weight; 0 for
+ *            an empty reservoir)
  *   [4..7]   cached radiance L(y).rgb leaving y toward its pixel, M
  *   [8..11]  the owning pixel's normal.xyz and distance to the camera
  *            (0 when the owning pixel has no valid G-buffer hit: the owner

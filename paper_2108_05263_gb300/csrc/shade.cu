@@ -67,9 +67,9 @@ struct ShadowGen {
         ry.tmax = 0.f;
         float4 g1 = g.g1[pix];
         if (__float_as_uint(g1.w) == DDGI_NONE) return false;
-        const float4* rec = r.rec + 4 * (size_t)pix;
-        float4 r0 = __ldg(rec);
-        if (__float_as_uint(__ldg(rec + 3).x) == DDGI_NONE || !(r0.w > 0.f)) return false;
+        // an empty reservoir has W = 0: the first half of the record decides
+        const float4 r0 = __ldg(r.rec + 4 * (size_t)pix);
+        if (!(r0.w > 0.f)) return false;
         f3 x = xyz(g.g0[pix]);
         f3 d = xyz(r0) - x;
         float d2 = dot(d, d);
@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
                                                const float2* __restrict__ vis,
                                                const float4* __restrict__ ind,
                                                const MLPState* __restrict__ mst) {
+    // rows bottom-up: the shadow-ray pass read the pixels' planes top-down,
+    // so its last rows are still in L2
     int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     float4 g1 = g.g1[pix];
