@@ -66,7 +66,8 @@ class _Settings(C.Structure):
                 ("depth_sharpness", C.c_double), ("n_light", C.c_int32), ("n_bsdf", C.c_int32),
                 ("temporal_mcap", C.c_double), ("spatial_neighbours", C.c_int32),
                 ("spatial_radius", C.c_int32), ("normal_reject_cos", C.c_double),
-                ("depth_reject_frac", C.c_double), ("seed", C.c_uint32), ("relocate", C.c_int32)]
+                ("depth_reject_frac", C.c_double), ("seed", C.c_uint32), ("relocate", C.c_int32),
+                ("candidate_stride", C.c_int32)]
 
 
 class _Volume(C.Structure):
@@ -180,6 +181,13 @@ class Scene:
         return np.ctypeslib.as_array(self.s.area, (self.s.num_tris,)).copy()
 
 
+def _settings(scene, settings):
+    """The scene's settings, or the given ones (ctypes struct or scenegen Settings)."""
+    if settings is None:
+        return scene.settings
+    return settings if isinstance(settings, _Settings) else settings_of(settings)
+
+
 def settings_of(st) -> _Settings:
     o = _Settings()
     o.rays_per_probe = st.rays_per_probe
@@ -197,6 +205,7 @@ def settings_of(st) -> _Settings:
     o.depth_reject_frac = st.depth_reject_frac
     o.seed = st.seed
     o.relocate = int(getattr(st, "probe_relocation", 0))
+    o.candidate_stride = int(getattr(st, "candidate_stride", 1))
     return o
 
 
@@ -465,7 +474,7 @@ def ddgi_query(vol: Volume, q, n):
 
 
 def probe_trace(scene: Scene, vol: Volume, frame: int, probes=None, settings=None):
-    st = settings or scene.settings
+    st = _settings(scene, settings)
     pr, pp = _pixarg(probes)
     n = vol.P if probes is None else len(pr)
     rays = np.zeros((n, st.rays_per_probe, 4))
@@ -492,7 +501,7 @@ def probe_relocate(vol: Volume, rays, frame: int, settings, probes=None):
 
 
 def probe_update(scene: Scene, vol: Volume, frame: int, settings=None):
-    st = settings or scene.settings
+    st = _settings(scene, settings)
     rc = lib().or_probe_update(C.byref(scene.s), C.byref(vol.v), C.byref(st), C.c_uint32(frame))
     if rc != 0:
         raise MemoryError("or_probe_update")
@@ -511,7 +520,7 @@ def gbuffer(scene: Scene, cam, prev_cam=None, pix=None) -> GBuffer:
 
 
 def restir_initial(scene: Scene, vol: Volume, g: GBuffer, frame: int, pix=None, settings=None):
-    st = settings or scene.settings
+    st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     out = Reservoirs(n)
@@ -526,7 +535,7 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
                     prev: Reservoirs, frame: int, pix=None, settings=None):
     _need_full(g, cur)
     _need_full(gp, prev)
-    st = settings or scene.settings
+    st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     out = Reservoirs(n)
@@ -541,7 +550,7 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
 def restir_spatial(scene: Scene, g: GBuffer, res_in: Reservoirs, frame: int, pass_idx: int,
                    pix=None, settings=None):
     _need_full(g, res_in)
-    st = settings or scene.settings
+    st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     out = Reservoirs(n)

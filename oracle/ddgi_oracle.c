@@ -823,6 +823,15 @@ static int wrs_take(double u, double wsum, double w) {
  * Sec. 3.1 step 2: one is kept by weighted reservoir sampling with
  * W = w_sum / (M target(y)).  The BSDF rays also estimate the residual
  * transport of Sec. 3.5: rho_x L(y) max(0, 1 - 1/G) per ray. */
+/* Sec. 5 (subsampling): with a candidate stride n >= 2 only every n-th
+ * pixel, on diagonals that move by one pixel per frame, generates new
+ * candidates; the others start from an empty reservoir and only reuse. */
+static int generates_candidates(const or_settings* st, const or_gbuf* g, int32_t q, uint32_t frame) {
+    if (st->candidate_stride <= 1) return 1;
+    const uint32_t x = (uint32_t)(q % g->width), y = (uint32_t)(q / g->width);
+    return (x + y + frame) % (uint32_t)st->candidate_stride == 0u;
+}
+
 int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* st,
                       const or_gbuf* g, uint32_t frame, const int32_t* pix, int32_t npix,
                       or_res* out, double* resid) {
@@ -833,6 +842,7 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
         int32_t q = pix ? pix[k] : k;
         resid[3 * k] = resid[3 * k + 1] = resid[3 * k + 2] = 0.0;
         if (g->tri[q] < 0) { res_set_empty(out, k, 0.0); continue; }
+        if (!generates_candidates(st, g, q, frame)) { res_set_empty(out, k, 0.0); continue; }
         const double* x = g->pos + 3 * q;
         const double* nx = g->nrm + 3 * q;
         const double* rho = g->alb + 3 * q;
@@ -939,7 +949,11 @@ int or_restir_temporal(const or_scene* s, const or_settings* st, const or_gbuf* 
         if (fabs(de - gp->dist[pq]) > st->depth_reject_frac * de) continue;
         double Mc = cur->M[q];
         double Mp = prev->M[pq];
-        if (Mp > st->temporal_mcap * Mc) Mp = st->temporal_mcap * Mc;
+        /* the cap is relative to the current M, or to the nominal candidate
+         * count for a pixel that generated none (subsampling) */
+        const double Mnom = (double)((s->num_emitters > 0 ? st->n_light : 0) + st->n_bsdf);
+        const double Mref = Mc > 0.0 ? Mc : Mnom;
+        if (Mp > st->temporal_mcap * Mref) Mp = st->temporal_mcap * Mref;
         double pc = target_of(s, g, q, cur, q);
         double wsum = pc * cur->W[q] * Mc;
         double pp = target_of(s, g, q, prev, pq);

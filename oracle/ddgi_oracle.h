@@ -51,6 +51,8 @@ typedef struct {
     double normal_reject_cos, depth_reject_frac;
     uint32_t seed;
     int32_t relocate;        /* probe relocation after each blend (1) or not */
+    int32_t candidate_stride;   /* >= 2: pixel (x, y) generates candidates in frame f only when
+                                 * (x + y + f) mod stride == 0 (Sec. 5, subsampling); 0, 1: every pixel */
 } or_settings;
 
 typedef struct {

@@ -94,6 +94,7 @@ class Settings:
     depth_sharpness: float = 50.0
     num_light_candidates: int = 31
     num_bsdf_candidates: int = 1
+    candidate_stride: int = 1       # >= 2: only pixels with (x + y + frame) % stride == 0 generate candidates
     temporal_mcap: float = 20.0
     spatial_passes: int = 1
     spatial_neighbours: int = 5

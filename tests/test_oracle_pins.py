@@ -576,6 +576,78 @@ def test_temporal_and_spatial_reuse_keep_the_estimate_unbiased(oracle_lib):
     assert np.all(np.abs(mean - exp) <= 4 * sd), (mean, exp, sd)
 
 
+def test_candidate_subsampling_pattern_and_cap(oracle_lib):
+    """Sec. 5 subsampling, stride 3: only pixels with (x + y + f) % 3 == 0
+    generate candidates (M = 32), the others start empty with M = 0; a
+    pixel that generated none merges the previous reservoir capped at
+    20 x the nominal 32 candidates, and its W is then the previous W."""
+    import dataclasses
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    st = dataclasses.replace(sc.settings, candidate_stride=3)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    p = np.array([-0.3, -1.0, 0.2])
+    W_, H_ = 6, 4
+    cam = np.array([-0.3, 1.0, 0.2])
+    g = _point_gbuffer(o, S, np.tile(p, (W_ * H_, 1)), np.tile([0, 1.0, 0], (W_ * H_, 1)),
+                       np.tile([0.5, 0.5, 0.5], (W_ * H_, 1)), cam, width=W_)
+    x, y = np.arange(W_ * H_) % W_, np.arange(W_ * H_) // W_
+    for f in (4, 5):
+        res, resid = o.restir_initial(S, vol, g, f, settings=st)
+        gen = (x + y + f) % 3 == 0
+        np.testing.assert_array_equal(res.M, np.where(gen, 32.0, 0.0))
+        assert np.all(res.tri[~gen] == -1) and np.all(res.W[~gen] == 0) and np.all(resid[~gen] == 0)
+        assert np.all(res.tri[gen] >= 0)
+    # stride 1 is the plain method
+    a, _ = o.restir_initial(S, vol, g, 7, settings=dataclasses.replace(st, candidate_stride=1))
+    b, _ = o.restir_initial(S, vol, g, 7)
+    np.testing.assert_array_equal(a.W, b.W)
+    np.testing.assert_array_equal(a.tag, b.tag)
+    # temporal merge onto a pixel without candidates
+    prev, _ = o.restir_initial(S, vol, g, 4)             # every pixel generated
+    prev.M[:] = 5000.0
+    cur, _ = o.restir_initial(S, vol, g, 5, settings=st)
+    out = o.restir_temporal(S, g, g, cam, cur, prev, 5, settings=st)
+    empty = cur.M == 0
+    np.testing.assert_array_equal(out.M[empty], 20.0 * 32.0)
+    has = empty & (prev.tri >= 0)
+    np.testing.assert_allclose(out.W[has], prev.W[has], rtol=1e-12)
+    np.testing.assert_array_equal(out.tag[has], prev.tag[has])
+
+
+@pytest.mark.slow
+def test_subsampled_reuse_keeps_the_estimate_unbiased(oracle_lib):
+    """The equal-target 8x8 image of the previous test with candidate stride
+    2: half the pixels generate candidates each frame (alternating), the rest
+    only reuse through temporal and spatial merges; the mean still converges
+    to rho * Le * F (with empty probes there is no residual term to lose)."""
+    import dataclasses
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    st = dataclasses.replace(sc.settings, candidate_stride=2)
+    S = o.Scene(sc)
+    vol = o.Volume(sc.grid)
+    p = np.array([-0.3, -1.0, 0.2])
+    n = 64
+    cam = np.array([-0.3, 1.0, 0.2])
+    g = _point_gbuffer(o, S, np.tile(p, (n, 1)), np.tile([0, 1.0, 0], (n, 1)),
+                       np.tile([0.5, 0.5, 0.5], (n, 1)), cam, width=8)
+    F = _rect_form_factor(-1 - p[0], -p[0], -1 - p[2], 1 - p[2], 2.0)
+    exp = 0.5 * 10.0 * F
+    T = 700
+    acc = np.zeros((T, 3))
+    for k in range(T):
+        f0, f1 = 2 * k, 2 * k + 1
+        prev, _ = o.restir_initial(S, vol, g, f0, settings=st)
+        cur, resid = o.restir_initial(S, vol, g, f1, settings=st)
+        tmp = o.restir_temporal(S, g, g, cam, cur, prev, f1, settings=st)
+        res = o.restir_spatial(S, g, tmp, f1, 0, settings=st)
+        acc[k] = o.shade(S, vol, g, res, resid).mean(0)
+    mean, sd = acc.mean(0), acc.std(0) / math.sqrt(T)
+    assert np.all(np.abs(mean - exp) <= 4 * sd), (mean, exp, sd)
+
+
 def test_reservoir_merge_special_case(oracle_lib):
     """Two reservoirs with equal target: the merged W equals the M-weighted
     mean of the input W (target cancels), and M adds up (no cap hit)."""
