@@ -102,6 +102,12 @@ typedef struct {
     uint32_t probe_relocation;    /* 1: ddgi_probe_update ends with ddgi_probe_relocate */
     uint32_t mlp_bf16;            /* network weights and activations in bf16 (1) or fp16 (0),
                                    * fp32 accumulation either way */
+    uint32_t candidate_stride;    /* Sec. 5 subsampling: 0 or 1, every pixel generates
+                                   * candidates; n >= 2 (at most 64), only pixels with
+                                   * (x + y + frame) % n == 0 do, the others start from an
+                                   * empty reservoir (M = 0, no residual) and only reuse;
+                                   * temporal reuse then caps the previous M at
+                                   * temporal_mcap x the nominal candidate count */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */

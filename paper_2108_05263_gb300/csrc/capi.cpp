@@ -194,6 +194,7 @@ RestirParams restir_params(ddgi_ctx* c) {
     r.depth_reject_frac = c->cfg.depth_reject_frac;
     const uint64_t span = 2ull * c->cfg.spatial_radius + 1ull;
     r.span_magic = (uint32_t)(((1ull << 32) + span - 1) / span);
+    r.stride = c->cfg.candidate_stride > 1 ? c->cfg.candidate_stride : 1u;
     return r;
 }
 
@@ -249,6 +250,7 @@ ddgi_status check_config(const ddgi_config* c, std::string* why) {
     if (c->num_bsdf_candidates < 1 || M > 64) { *why = "need 1..64 candidates with at least one BSDF candidate"; return DDGI_ERR_INVALID_ARG; }
     if (!(c->temporal_mcap >= 0.f) || !std::isfinite(c->temporal_mcap)) { *why = "temporal_mcap must be >= 0"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_neighbours > 32) { *why = "spatial_neighbours must be <= 32"; return DDGI_ERR_INVALID_ARG; }
+    if (c->candidate_stride > 64) { *why = "candidate_stride must be <= 64"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_radius < 1 || c->spatial_radius > 255) { *why = "spatial_radius must be 1..255"; return DDGI_ERR_INVALID_ARG; }
     if (!std::isfinite(c->normal_reject_cos) || !(c->depth_reject_frac >= 0.f)) { *why = "bad rejection thresholds"; return DDGI_ERR_INVALID_ARG; }
     const uint64_t P = (uint64_t)c->counts[0] * c->counts[1] * c->counts[2];

@@ -40,6 +40,7 @@ struct RestirParams {
     uint32_t spatial_neighbours, spatial_radius;
     float normal_reject_cos, depth_reject_frac;
     uint32_t span_magic;   // ceil(2^32 / (2 radius + 1)): x / span = mulhi(x, magic) for x < 2^16
+    uint32_t stride;       // candidate subsampling: 1 every pixel, n: (x + y + frame) % n == 0
 };
 
 struct ProbeParams {

@@ -27,6 +27,13 @@ __device__ __forceinline__ f3 bsdf_dir(const RestirParams& rp, uint32_t pix, uin
     return onb_to_world(nx, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
 }
 
+// Sec. 5 subsampling: does pixel pix generate candidates in this frame?
+__device__ __forceinline__ bool generates(const RestirParams& rp, int width, uint32_t pix, uint32_t frame) {
+    if (rp.stride <= 1u) return true;
+    const uint32_t x = pix % (uint32_t)width, y = pix / (uint32_t)width;
+    return (x + y + frame) % rp.stride == 0u;
+}
+
 // BSDF candidate rays: work item i = pixel * n_bsdf + b
 struct BsdfGen {
     GBufView g;
@@ -36,7 +43,7 @@ struct BsdfGen {
         const uint32_t pix = i / nb, b = i - pix * nb;
         r.tmax = DDGI_MISS_T;
         float4 g1 = g.g1[pix];
-        if (__float_as_uint(g1.w) == DDGI_NONE) return false;
+        if (__float_as_uint(g1.w) == DDGI_NONE || !generates(rp, g.width, pix, frame)) return false;
         r.o = xyz(g.g0[pix]);
         r.d = bsdf_dir(rp, pix, frame, nl + b, xyz(g1));
         r.tmin = DDGI_T_EPS;
@@ -119,7 +126,7 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
                                                    uint32_t pix, const float4* e_vert, const float* e_cdf,
                                                    const uint32_t* e_guide) {
     const float4 g1 = g.g1[pix];
-    if (__float_as_uint(g1.w) == DDGI_NONE) return;
+    if (__float_as_uint(g1.w) == DDGI_NONE || !generates(rp, g.width, pix, frame)) return;
     const float4 g0 = g.g0[pix], g2 = g.g2[pix];
     const f3 x = xyz(g0), nx = xyz(g1);
     CandidateStream cs;
@@ -250,6 +257,12 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     }
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
     const float4 geo = make_float4(g1.x, g1.y, g1.z, g0.w);
+    if (!generates(rp, g.width, pix, frame)) {   // subsampling: an empty reservoir that only reuses
+        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), geo,
+                  rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
+        resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const f3 x = xyz(g0), nx = xyz(g1);
     CandidateStream cs;
     cs.rho = xyz(g2);
@@ -354,7 +367,10 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
     }
     const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
     float Mc = c.q1.w;
-    float Mp = fminf(p.q1.w, rp.temporal_mcap * Mc);
+    // the cap is relative to the current M, or to the nominal candidate count
+    // for a pixel that generated none (subsampling)
+    const float Mref = Mc > 0.f ? Mc : (float)((s.num_emitters > 0 ? rp.n_light : 0u) + rp.n_bsdf);
+    float Mp = fminf(p.q1.w, rp.temporal_mcap * Mref);
     float pc = rec_target(x, nx, rho, c.q0, c.q1, c.q3);
     float wsum = pc * c.q0.w * Mc;
     float pp = rec_target(x, nx, rho, p.q0, p.q1, p.q3);

@@ -44,7 +44,7 @@ class Config(C.Structure):
                 ("depth_reject_frac", C.c_float), ("seed", C.c_uint32),
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
                 ("mlp_seed", C.c_uint32), ("train_ema", C.c_float), ("probe_relocation", C.c_uint32),
-                ("mlp_bf16", C.c_uint32)]
+                ("mlp_bf16", C.c_uint32), ("candidate_stride", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -255,6 +255,7 @@ def config_from(grid, settings) -> Config:
     c.train_ema = float(getattr(settings, "train_ema", 0.97))
     c.probe_relocation = int(getattr(settings, "probe_relocation", 0))
     c.mlp_bf16 = int(getattr(settings, "mlp_bf16", 0))
+    c.candidate_stride = int(getattr(settings, "candidate_stride", 1))
     return c
 
 

@@ -330,6 +330,19 @@ def test_whole_frame_chain_secondary_ddgi(dd, orc):
         assert tags >= 0.999 and rad >= 0.999, (f, stats)
 
 
+@pytest.mark.parametrize("stride", [2, 3])
+def test_whole_frame_chain_candidate_subsampling(dd, orc, stride):
+    """Sec. 5 subsampling: only every stride-th pixel (rotating diagonals)
+    generates candidates, the rest start empty and only reuse; every pass of
+    the frame chain still matches the oracle."""
+    import dataclasses
+    sc = scenegen.tiny_room(frames=5)
+    sc = dataclasses.replace(sc, settings=dataclasses.replace(sc.settings, candidate_stride=stride))
+    stats = _chain(dd, orc, sc, 5)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
 def test_whole_frame_chain_dynamic_box(dd, orc):
     """Three boxes in rigid motion (turning and shifting every frame), the
     two emitter triangles swapping every 2 frames, probe relocation on:
