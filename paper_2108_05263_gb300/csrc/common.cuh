@@ -173,18 +173,6 @@ __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
     return t;
 }
 
-__device__ __forceinline__ f3 sample_irr(const float4* tile, int n, f3 d) {
-    Taps t = oct_taps(d, n);
-    int w = n + 2;
-    float4 a = __ldg(tile + t.i00), b = __ldg(tile + t.i00 + 1);
-    float4 c = __ldg(tile + t.i00 + w), e = __ldg(tile + t.i00 + w + 1);
-    float w00 = (1.f - t.ax) * (1.f - t.ay), w10 = t.ax * (1.f - t.ay);
-    float w01 = (1.f - t.ax) * t.ay, w11 = t.ax * t.ay;
-    return {w00 * a.x + w10 * b.x + w01 * c.x + w11 * e.x,
-            w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y,
-            w00 * a.z + w10 * b.z + w01 * c.z + w11 * e.z};
-}
-
 __device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) {
     Taps t = oct_taps(d, n);
     int w = n + 2;
@@ -393,7 +381,6 @@ __device__ __forceinline__ Rec load_rec(const float4* p) {
     return r;
 }
 
-__device__ __forceinline__ uint32_t rec_tri(const Rec& r) { return __float_as_uint(r.q3.x); }
 __device__ __forceinline__ bool rec_owner_valid(const Rec& r) { return r.q2.w > 0.f; }
 
 // target of a record's sample at x (the sample's normal travels in the record)
