@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128) k_train_primary(SceneView s, VolumeView v
     const uint32_t p = i / tp.per, r = i - p * tp.per;
     f3 P = probe_center(v, (int)p);
     f3 w = train_ray_dir(tp, r);
-    Hit h = trace_bvh<false>(s, Ray{P, w, DDGI_T_EPS, DDGI_MISS_T});
+    Hit h = trace_spec<false>(s, Ray{P, w, DDGI_T_EPS, DDGI_MISS_T});   // probe-origin rays, as in the probe trace
     bool valid = false;
     f3 n = {0.f, 0.f, 1.f}, y = P;
     if (h.tri != DDGI_NONE) {

@@ -35,8 +35,9 @@ __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, 
     int p = tid / R, r = tid - p * R;
     f3 P = probe_of(v, p);
     f3 w = rotate(pp, __ldg(sf + r));
-    // coherent rays (one origin per 32-lane warp): traversal in place
-    Hit h = trace_bvh<false>(s, Ray{P, w, DDGI_T_EPS, DDGI_MISS_T});
+    // one origin per 32-lane warp, directions over the sphere: per-thread
+    // traversal with the speculative descent of the persistent engine
+    Hit h = trace_spec<false>(s, Ray{P, w, DDGI_T_EPS, DDGI_MISS_T});
     float4 out = make_float4(0.f, 0.f, 0.f, DDGI_MISS_T);
     if (h.tri != DDGI_NONE) {
         f3 n = xyz(__ldg(s.nrm + h.tri));

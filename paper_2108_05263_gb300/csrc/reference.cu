@@ -6,7 +6,7 @@
 // same centres), random numbers keyed (seed, pixel, sample, pass 8, vertex,
 // dimension).
 #include "internal.h"
-#include "trace.cuh"
+#include "trace_engine.cuh"
 
 namespace {
 
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) k_pt(SceneView s, CamView cam, uint32_t s
             }
             o = x;
             d = w;
-            h = trace_bvh<false>(s, Ray{o, d, DDGI_T_EPS, DDGI_MISS_T});
+            h = trace_spec<false>(s, Ray{o, d, DDGI_T_EPS, DDGI_MISS_T});   // incoherent bounces
         }
         sr += L.x;
         sg += L.y;

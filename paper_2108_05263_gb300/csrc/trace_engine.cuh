@@ -34,6 +34,143 @@ __device__ __forceinline__ bool pop_entry(const int2* stack, int& sp, float limi
     return false;
 }
 
+// One step of a ray's traversal: descend inner nodes; the first leaf the
+// lane meets is set aside and the lane keeps descending from its stack while
+// other lanes of the warp still look for one (Aila & Laine 2009, speculative
+// traversal); then the set-aside leaf is intersected.  Returns true when the
+// ray is done (best_t / best_tri hold its result).  Shared by the persistent
+// engine and the per-thread trace_spec.
+template <bool ANY_HIT>
+__device__ __forceinline__ bool trav_step(const SceneView& s, const f3& o, const f3& d, const f3& inv, const f3& oi,
+                                          float tmin, float tmax, float& best_t, uint32_t& best_tri, int& node,
+                                          int& sp, int& visits, bool& more, int2* stack) {
+    const float widen = 1.0000004f;
+    bool done = false;
+    int leaf = 0;   // set-aside leaf entry (< 0), 0: none
+    while (true) {
+        if (more && node < 0 && leaf == 0) {
+            leaf = node;
+            more = pop_entry(stack, sp, best_t * widen, node);
+        }
+        if (!(more && node >= 0)) break;
+        // every lane still descending takes part in the vote
+        const bool all_hold = __all_sync(__activemask(), leaf != 0);
+        if (leaf != 0 && all_hold) break;
+        if (++visits > TRAV_MAX_VISITS) {
+            atomicOr(s.err, ERRBIT_TRAVERSAL);
+            best_tri = DDGI_NONE;
+            best_t = tmax;
+            done = true;
+            break;
+        }
+        const float4* np = s.nodes + (size_t)node * 8;
+        // a node is four 32-byte loads (nodes are 128-byte aligned)
+        float4 lx, hx, ly, hy, lz, hz, chf, cnf;
+        ld32(np, lx, hx);
+        ld32(np + 2, ly, hy);
+        ld32(np + 4, lz, hz);
+        ld32(np + 6, chf, cnf);
+        float t0[4];
+        int ent[4];
+        const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float lya[4] = {ly.x, ly.y, ly.z, ly.w}, hya[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
+        const int cha[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
+                            __float_as_int(chf.w)};
+        const int cna[4] = {__float_as_int(cnf.x), __float_as_int(cnf.y), __float_as_int(cnf.z),
+                            __float_as_int(cnf.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float tx0 = fmaf(lxa[c], inv.x, -oi.x), tx1 = fmaf(hxa[c], inv.x, -oi.x);
+            float ty0 = fmaf(lya[c], inv.y, -oi.y), ty1 = fmaf(hya[c], inv.y, -oi.y);
+            float tz0 = fmaf(lza[c], inv.z, -oi.z), tz1 = fmaf(hza[c], inv.z, -oi.z);
+            float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+            float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), best_t)) * widen;
+            bool valid = cna[c] > 0 || cha[c] >= 0;
+            bool hit = valid && a <= b;
+            t0[c] = hit ? a : INFINITY;
+            ent[c] = cna[c] > 0 ? leaf_entry(~cha[c], cna[c]) : cha[c];
+        }
+        // sort the 4 (t, entry) pairs by t, ascending (sorting network)
+#define CSWAP(i, j)                                          \
+if (t0[j] < t0[i]) {                                     \
+    float tt = t0[i];                                    \
+    t0[i] = t0[j];                                       \
+    t0[j] = tt;                                          \
+    int ee = ent[i];                                     \
+    ent[i] = ent[j];                                     \
+    ent[j] = ee;                                         \
+}
+        CSWAP(0, 1)
+        CSWAP(2, 3)
+        CSWAP(0, 2)
+        CSWAP(1, 3)
+        CSWAP(1, 2)
+#undef CSWAP
+        const int nhit = (t0[0] < INFINITY) + (t0[1] < INFINITY) + (t0[2] < INFINITY) + (t0[3] < INFINITY);
+        if (sp + nhit > TRAV_STACK) {
+            atomicOr(s.err, ERRBIT_STACK);
+            best_tri = DDGI_NONE;
+            best_t = tmax;
+            done = true;
+            break;
+        }
+        // push far-to-near, continue with the nearest
+#pragma unroll
+        for (int k = 3; k >= 1; --k)
+            if (k < nhit) {
+                stack[sp] = make_int2(ent[k], __float_as_int(t0[k]));
+                ++sp;
+            }
+        if (nhit > 0)
+            node = ent[0];
+        else
+            more = pop_entry(stack, sp, best_t * widen, node);
+    }
+    if (!done && leaf != 0) {
+        const int v = -1 - leaf;
+        const int first = v >> 3, count = (v & 7) + 1;
+        for (int k = 0; k < count; ++k) {
+            uint32_t orig;
+            float t = tri_hit(s.tris + (size_t)(first + k) * 3, o, d, &orig);
+            if (t > tmin && t < tmax) {
+                if (ANY_HIT) {
+                    best_t = t;
+                    best_tri = orig;
+                    done = true;
+                    break;
+                }
+                if (t < best_t || (t == best_t && orig < best_tri)) {
+                    best_t = t;
+                    best_tri = orig;
+                }
+            }
+        }
+    }
+    if (!done && !more) done = true;
+    return done;
+}
+
+// closest (or any) hit of one ray per thread with the same speculative
+// descent, for kernels whose rays are not pooled
+template <bool ANY_HIT>
+__device__ __forceinline__ Hit trace_spec(const SceneView& s, const Ray& ray) {
+    const f3 inv = {safe_inv(ray.d.x), safe_inv(ray.d.y), safe_inv(ray.d.z)};
+    const f3 oi = {ray.o.x * inv.x, ray.o.y * inv.y, ray.o.z * inv.z};
+    float best_t = ray.tmax;
+    uint32_t best_tri = DDGI_NONE;
+    int node = 0, sp = 0, visits = 0;
+    bool more = true;
+    int2 stack[TRAV_STACK];
+    while (!trav_step<ANY_HIT>(s, ray.o, ray.d, inv, oi, ray.tmin, ray.tmax, best_t, best_tri, node, sp, visits, more,
+                               stack)) {
+    }
+    Hit h;
+    h.t = best_t;
+    h.tri = best_tri;
+    return h;
+}
+
 template <class Gen, bool ANY_HIT>
 __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, uint32_t n,
                                                           uint32_t* __restrict__ counter,
@@ -52,7 +189,6 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
     // warp-uniform work pool
     uint32_t pool = 0, pool_end = 0;
     bool exhausted = false;
-    const float widen = 1.0000004f;
 
     while (true) {
         // ---- refill idle lanes ------------------------------------------------
@@ -99,113 +235,8 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
         if (__all_sync(FULL, idx == DDGI_NONE)) break;
         if (idx == DDGI_NONE) continue;
 
-        // ---- descend inner nodes; the first leaf a lane meets is set aside and
-        // the lane keeps descending from its stack while other lanes of the
-        // warp still look for one (Aila & Laine 2009, speculative traversal);
-        // then the set-aside leaves are intersected together
-        bool done = false;
-        int leaf = 0;   // set-aside leaf entry (< 0), 0: none
-        while (true) {
-            if (more && node < 0 && leaf == 0) {
-                leaf = node;
-                more = pop_entry(stack, sp, best_t * widen, node);
-            }
-            if (!(more && node >= 0)) break;
-            // every lane still descending takes part in the vote
-            const bool all_hold = __all_sync(__activemask(), leaf != 0);
-            if (leaf != 0 && all_hold) break;
-            if (++visits > TRAV_MAX_VISITS) {
-                atomicOr(s.err, ERRBIT_TRAVERSAL);
-                best_tri = DDGI_NONE;
-                best_t = tmax;
-                done = true;
-                break;
-            }
-            const float4* np = s.nodes + (size_t)node * 8;
-            // a node is four 32-byte loads (nodes are 128-byte aligned)
-            float4 lx, hx, ly, hy, lz, hz, chf, cnf;
-            ld32(np, lx, hx);
-            ld32(np + 2, ly, hy);
-            ld32(np + 4, lz, hz);
-            ld32(np + 6, chf, cnf);
-            float t0[4];
-            int ent[4];
-            const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
-            const float lya[4] = {ly.x, ly.y, ly.z, ly.w}, hya[4] = {hy.x, hy.y, hy.z, hy.w};
-            const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
-            const int cha[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
-                                __float_as_int(chf.w)};
-            const int cna[4] = {__float_as_int(cnf.x), __float_as_int(cnf.y), __float_as_int(cnf.z),
-                                __float_as_int(cnf.w)};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float tx0 = fmaf(lxa[c], inv.x, -oi.x), tx1 = fmaf(hxa[c], inv.x, -oi.x);
-                float ty0 = fmaf(lya[c], inv.y, -oi.y), ty1 = fmaf(hya[c], inv.y, -oi.y);
-                float tz0 = fmaf(lza[c], inv.z, -oi.z), tz1 = fmaf(hza[c], inv.z, -oi.z);
-                float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
-                float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), best_t)) * widen;
-                bool valid = cna[c] > 0 || cha[c] >= 0;
-                bool hit = valid && a <= b;
-                t0[c] = hit ? a : INFINITY;
-                ent[c] = cna[c] > 0 ? leaf_entry(~cha[c], cna[c]) : cha[c];
-            }
-            // sort the 4 (t, entry) pairs by t, ascending (sorting network)
-#define CSWAP(i, j)                                          \
-    if (t0[j] < t0[i]) {                                     \
-        float tt = t0[i];                                    \
-        t0[i] = t0[j];                                       \
-        t0[j] = tt;                                          \
-        int ee = ent[i];                                     \
-        ent[i] = ent[j];                                     \
-        ent[j] = ee;                                         \
-    }
-            CSWAP(0, 1)
-            CSWAP(2, 3)
-            CSWAP(0, 2)
-            CSWAP(1, 3)
-            CSWAP(1, 2)
-#undef CSWAP
-            const int nhit = (t0[0] < INFINITY) + (t0[1] < INFINITY) + (t0[2] < INFINITY) + (t0[3] < INFINITY);
-            if (sp + nhit > TRAV_STACK) {
-                atomicOr(s.err, ERRBIT_STACK);
-                best_tri = DDGI_NONE;
-                best_t = tmax;
-                done = true;
-                break;
-            }
-            // push far-to-near, continue with the nearest
-#pragma unroll
-            for (int k = 3; k >= 1; --k)
-                if (k < nhit) {
-                    stack[sp] = make_int2(ent[k], __float_as_int(t0[k]));
-                    ++sp;
-                }
-            if (nhit > 0)
-                node = ent[0];
-            else
-                more = pop_entry(stack, sp, best_t * widen, node);
-        }
-        if (!done && leaf != 0) {
-            const int v = -1 - leaf;
-            const int first = v >> 3, count = (v & 7) + 1;
-            for (int k = 0; k < count; ++k) {
-                uint32_t orig;
-                float t = tri_hit(s.tris + (size_t)(first + k) * 3, o, d, &orig);
-                if (t > tmin && t < tmax) {
-                    if (ANY_HIT) {
-                        best_t = t;
-                        best_tri = orig;
-                        done = true;
-                        break;
-                    }
-                    if (t < best_t || (t == best_t && orig < best_tri)) {
-                        best_t = t;
-                        best_tri = orig;
-                    }
-                }
-            }
-        }
-        if (!done && !more) done = true;
+        const bool done = trav_step<ANY_HIT>(s, o, d, inv, oi, tmin, tmax, best_t, best_tri, node, sp, visits, more,
+                                             stack);
         if (done) {
             hits[idx] = make_float2(best_t, __uint_as_float(best_tri));
             idx = DDGI_NONE;
