@@ -51,6 +51,7 @@ struct ProbeParams {
     float le_attenuation;
     float depth_sharpness;
     float depth_tmax;
+    float depth_cmin;    // rays with cos <= this weigh < 2^-40 in the distance blend
 };
 
 // kernel launchers (return the launch error)

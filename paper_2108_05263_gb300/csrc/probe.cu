@@ -1,6 +1,8 @@
 // Probe update of Sec. 3.2 (Eq. probeUpdate): per-ray trace with the
 // attenuated emission and the probe-augmented bounce, then a per-probe blend
 // of irradiance and distance moments with hysteresis and border refresh.
+#include <algorithm>
+
 #include "internal.h"
 #include "trace_engine.cuh"
 
@@ -89,7 +91,7 @@ __device__ __forceinline__ int border_source(int X, int Y, int n) {
 }
 
 // one CTA per probe; rays and directions staged in shared memory
-__global__ void __launch_bounds__(256) k_probe_blend(VolumeView v, ProbeParams pp,
+__global__ void __launch_bounds__(512) k_probe_blend(VolumeView v, ProbeParams pp,
                                                      const float4* __restrict__ sf,
                                                      const float4* __restrict__ rays) {
     extern __shared__ float4 smem[];
@@ -142,7 +144,9 @@ __global__ void __launch_bounds__(256) k_probe_blend(VolumeView v, ProbeParams p
             for (int r = 0; r < R; ++r) {
                 float4 d = s_dir[r];
                 float c = dt.x * d.x + dt.y * d.y + dt.z * d.z;
-                if (c > 0.f) {
+                // weights below 2^-40 are skipped (no change at fp32 resolution);
+                // a warp's texels face nearby directions, so whole warps skip most rays
+                if (c > pp.depth_cmin && c > 0.f) {
                     float wr = __powf(c, pp.depth_sharpness);
                     float t = fminf(fabsf(s_ray[r].w), pp.depth_tmax);
                     sw += wr;
@@ -271,6 +275,10 @@ cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const 
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_probe_blend<<<P, 256, smem, st>>>(v, p, p.sf, rays);
+    // one thread per texel of both maps when they fit one CTA (320 for 8x8 +
+    // 16x16), so that the texel loop runs once
+    const int texels = v.irr_n * v.irr_n + v.depth_n * v.depth_n;
+    const int threads = std::min(512, (texels + 31) / 32 * 32);
+    k_probe_blend<<<P, threads, smem, st>>>(v, p, p.sf, rays);
     return cudaGetLastError();
 }
