@@ -25,265 +25,6 @@ struct BufferQuery {
 };
 
 // ---------------------------------------------------------------------------
-// training: fused forward + backward over tiles of 128 samples
-// ---------------------------------------------------------------------------
-constexpr int kTrainRows = 128;
-constexpr int kLdD5 = 24;
-
-size_t train_smem() {
-    return MLP_SW_HALVES * 2 + 264 * 4 + kTrainRows * MLP_LD_IN * 2 + 4 * kTrainRows * MLP_LD_H * 2 +
-           kTrainRows * MLP_LD_H * 2 + kTrainRows * kLdD5 * 2 + kTrainRows * 8 * 4 + kTrainRows * 4 * 4;
-}
-
-template <int KT>
-__device__ __forceinline__ void store_frags(uint16_t* s, int ld, int rowbase, const uint32_t (&a)[2][KT][4],
-                                            int g, int t) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        int r0 = rowbase + mt * 16 + g, r1 = r0 + 8;
-#pragma unroll
-        for (int kt = 0; kt < KT; ++kt) {
-            int c = kt * 16 + 2 * t;
-            *reinterpret_cast<uint32_t*>(s + r0 * ld + c) = a[mt][kt][0];
-            *reinterpret_cast<uint32_t*>(s + r1 * ld + c) = a[mt][kt][1];
-            *reinterpret_cast<uint32_t*>(s + r0 * ld + c + 8) = a[mt][kt][2];
-            *reinterpret_cast<uint32_t*>(s + r1 * ld + c + 8) = a[mt][kt][3];
-        }
-    }
-}
-
-// acc[m = samples][n = layer input] = d[m][k = layer output] x W[k][n];
-// W in shared memory [out][ld]; rows >= OUT_ROWS read as 0
-template <bool BF, int KT, int NT, int OUT_ROWS>
-__device__ __forceinline__ void bwd_data(const uint16_t* __restrict__ sW, int ld, const uint32_t (&d)[2][KT][4],
-                                         float (&acc)[2][NT][4], int g, int t) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
-    const uint16_t z = 0;
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-        const int k0 = kt * 16 + 2 * t;
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int col = nt * 8 + g;
-            uint16_t w0 = k0 < OUT_ROWS ? sW[k0 * ld + col] : z;
-            uint16_t w1 = k0 + 1 < OUT_ROWS ? sW[(k0 + 1) * ld + col] : z;
-            uint16_t w2 = k0 + 8 < OUT_ROWS ? sW[(k0 + 8) * ld + col] : z;
-            uint16_t w3 = k0 + 9 < OUT_ROWS ? sW[(k0 + 9) * ld + col] : z;
-            uint32_t b0 = h2_from(w0, w1), b1 = h2_from(w2, w3);
-            H16<BF>::mma(acc[0][nt], d[0][kt], b0, b1);
-            H16<BF>::mma(acc[1][nt], d[1][kt], b0, b1);
-        }
-    }
-}
-
-// ReLU derivative from the stored activations of the layer input, then the
-// masked deltas as A fragments (k-tiles of 16 outputs) and into sD
-template <bool BF, int NT>
-__device__ __forceinline__ void mask_delta(const float (&acc)[2][NT][4], const uint16_t* sAct, int ld_act,
-                                           uint16_t* sD, int ld_d, int rowbase, uint32_t (&d)[2][NT / 2][4],
-                                           int g, int t) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        int r0 = rowbase + mt * 16 + g, r1 = r0 + 8;
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            int c = nt * 8 + 2 * t;
-            const uint16_t* a0 = sAct + r0 * ld_act + c;
-            const uint16_t* a1 = sAct + r1 * ld_act + c;
-            float v0 = H16<BF>::val(a0[0]) > 0.f ? acc[mt][nt][0] : 0.f;
-            float v1 = H16<BF>::val(a0[1]) > 0.f ? acc[mt][nt][1] : 0.f;
-            float v2 = H16<BF>::val(a1[0]) > 0.f ? acc[mt][nt][2] : 0.f;
-            float v3 = H16<BF>::val(a1[1]) > 0.f ? acc[mt][nt][3] : 0.f;
-            uint32_t p0 = H16<BF>::pack(v0, v1), p1 = H16<BF>::pack(v2, v3);
-            *reinterpret_cast<uint32_t*>(sD + r0 * ld_d + c) = p0;
-            *reinterpret_cast<uint32_t*>(sD + r1 * ld_d + c) = p1;
-            d[mt][nt >> 1][(nt & 1) ? 2 : 0] = p0;
-            d[mt][nt >> 1][(nt & 1) ? 3 : 1] = p1;
-        }
-    }
-}
-
-// weight gradient of one 16-row output tile: grad[o][i] += sum_s D[s][o] * A[s][i]
-// over the 128 samples of the block (8 k-tiles)
-template <bool BF, int NT>
-__device__ __forceinline__ void wgrad_tile(const uint16_t* sD, int ld_d, int o0, int out_real, const uint16_t* sA,
-                                           int ld_a, int in, float* grad_w, int g, int t) {
-    float acc[NT][4];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll 2
-    for (int kt = 0; kt < kTrainRows / 16; ++kt) {
-        const int s0 = kt * 16 + 2 * t;
-        uint32_t a[4];
-        a[0] = h2_from(sD[s0 * ld_d + o0 + g], sD[(s0 + 1) * ld_d + o0 + g]);
-        a[1] = h2_from(sD[s0 * ld_d + o0 + g + 8], sD[(s0 + 1) * ld_d + o0 + g + 8]);
-        a[2] = h2_from(sD[(s0 + 8) * ld_d + o0 + g], sD[(s0 + 9) * ld_d + o0 + g]);
-        a[3] = h2_from(sD[(s0 + 8) * ld_d + o0 + g + 8], sD[(s0 + 9) * ld_d + o0 + g + 8]);
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int col = nt * 8 + g;
-            uint32_t b0 = h2_from(sA[s0 * ld_a + col], sA[(s0 + 1) * ld_a + col]);
-            uint32_t b1 = h2_from(sA[(s0 + 8) * ld_a + col], sA[(s0 + 9) * ld_a + col]);
-            H16<BF>::mma(acc[nt], a, b0, b1);
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        int i = nt * 8 + 2 * t;
-        int r0 = o0 + g, r1 = o0 + g + 8;
-        if (r0 < out_real) {
-            atomicAdd(grad_w + r0 * in + i, acc[nt][0]);
-            atomicAdd(grad_w + r0 * in + i + 1, acc[nt][1]);
-        }
-        if (r1 < out_real) {
-            atomicAdd(grad_w + r1 * in + i, acc[nt][2]);
-            atomicAdd(grad_w + r1 * in + i + 1, acc[nt][3]);
-        }
-    }
-}
-
-// bias gradient: column sums of the deltas; thread (o, part) sums the rows
-// part, part + P, ... of output o, P = blockDim / 64 partial sums per output
-template <bool BF>
-__device__ __forceinline__ void bias_grad(const uint16_t* sD, int ld_d, int out_real, float* grad_b) {
-    const int o = threadIdx.x & 63, part = threadIdx.x >> 6, P = blockDim.x >> 6;
-    if (o >= out_real) return;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int r = part;
-    for (; r + 3 * P < kTrainRows; r += 4 * P) {
-        s0 += H16<BF>::val(sD[r * ld_d + o]);
-        s1 += H16<BF>::val(sD[(r + P) * ld_d + o]);
-        s2 += H16<BF>::val(sD[(r + 2 * P) * ld_d + o]);
-        s3 += H16<BF>::val(sD[(r + 3 * P) * ld_d + o]);
-    }
-    for (; r < kTrainRows; r += P) s0 += H16<BF>::val(sD[r * ld_d + o]);
-    atomicAdd(grad_b + o, (s0 + s1) + (s2 + s3));
-}
-
-// samples [n][3] float4: (y.xyz, _), (n.xyz, _), (target.rgb, weight); weight 0
-// excludes a sample.  Gradients of sum_s w_s sum_c (f - t)^2 / (sg(f)^2 + 0.01)
-// times the loss scale are added to grad; the weights are summed into
-// st->count.
-template <bool BF>
-__global__ void __launch_bounds__(kTrainRows, 1) k_mlp_train(MLPView m, const float4* __restrict__ smp,
-                                                            uint32_t n, MLPState* __restrict__ st,
-                                                            float* __restrict__ grad) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint16_t* sW = reinterpret_cast<uint16_t*>(smem_raw);
-    float* sb = reinterpret_cast<float*>(sW + MLP_SW_HALVES);
-    uint16_t* sA0 = reinterpret_cast<uint16_t*>(sb + 264);
-    uint16_t* sA[5];
-    sA[0] = sA0;
-    sA[1] = sA0 + kTrainRows * MLP_LD_IN;
-    for (int l = 2; l < 5; ++l) sA[l] = sA[l - 1] + kTrainRows * MLP_LD_H;
-    uint16_t* sD = sA[4] + kTrainRows * MLP_LD_H;
-    uint16_t* sD5 = sD + kTrainRows * MLP_LD_H;
-    float* sq_all = reinterpret_cast<float*>(sD5 + kTrainRows * kLdD5);
-    float* st_all = sq_all + kTrainRows * 8;
-
-    mlp_load_smem(m, sW, sb);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int rowbase = warp * 32;
-    const uint32_t s = blockIdx.x * kTrainRows + threadIdx.x;
-    {
-        float4 y = s < n ? smp[3 * (size_t)s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 nn = s < n ? smp[3 * (size_t)s + 1] : make_float4(0.f, 0.f, 1.f, 0.f);
-        float4 tg = s < n ? smp[3 * (size_t)s + 2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        unsigned cnt = __ballot_sync(0xffffffffu, tg.w > 0.f);
-        if (lane == 0 && cnt) atomicAdd(&st->count, (unsigned)__popc(cnt));
-        float* r = sq_all + threadIdx.x * 8;
-        r[0] = (y.x - m.lo[0]) * m.scale;
-        r[1] = (y.y - m.lo[1]) * m.scale;
-        r[2] = (y.z - m.lo[2]) * m.scale;
-        r[3] = nn.x;
-        r[4] = nn.y;
-        r[5] = nn.z;
-        float* q = st_all + threadIdx.x * 4;
-        q[0] = tg.x;
-        q[1] = tg.y;
-        q[2] = tg.z;
-        q[3] = tg.w;
-    }
-    __syncthreads();
-    const float* sq = sq_all + rowbase * 8;
-
-    // ---- forward, keeping every layer input in shared memory ------------------
-    float out[2][1][4];
-    {
-        uint32_t a0[2][5][4];
-        mlp_input_frags<BF>(sq, a0, g, t);
-        store_frags<5>(sA[0], MLP_LD_IN, rowbase, a0, g, t);
-        float acc[2][8][4];
-        uint32_t a[2][4][4];
-        mlp_layer<BF, 5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
-        relu_to_frags<BF, 8>(acc, a);
-        store_frags<4>(sA[1], MLP_LD_H, rowbase, a, g, t);
-#pragma unroll
-        for (int l = 1; l < 4; ++l) {
-            mlp_layer<BF, 4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
-            relu_to_frags<BF, 8>(acc, a);
-            store_frags<4>(sA[l + 1], MLP_LD_H, rowbase, a, g, t);
-        }
-        mlp_layer<BF, 4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
-    }
-
-    // ---- output gradient (relative L2, denominator held constant) -------------
-    const float S = st->loss_scale;
-    uint32_t d5[2][1][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        int r0 = rowbase + mt * 16 + g, r1 = r0 + 8;
-        float v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int row = e < 2 ? r0 : r1;
-            int col = 2 * t + (e & 1);
-            float f = out[mt][0][e];
-            const float* q = st_all + row * 4;
-            v[e] = col < 3 ? q[3] * S * 2.f * (f - q[col]) / (f * f + 0.01f) : 0.f;
-        }
-        d5[mt][0][0] = H16<BF>::pack(v[0], v[1]);
-        d5[mt][0][1] = H16<BF>::pack(v[2], v[3]);
-        d5[mt][0][2] = 0u;
-        d5[mt][0][3] = 0u;
-        *reinterpret_cast<uint32_t*>(sD5 + r0 * kLdD5 + 2 * t) = d5[mt][0][0];
-        *reinterpret_cast<uint32_t*>(sD5 + r1 * kLdD5 + 2 * t) = d5[mt][0][1];
-        *reinterpret_cast<uint32_t*>(sD5 + r0 * kLdD5 + 8 + 2 * t) = 0u;
-        *reinterpret_cast<uint32_t*>(sD5 + r1 * kLdD5 + 8 + 2 * t) = 0u;
-    }
-    __syncthreads();
-    // output layer: M = 16 (3 real rows), N = 64, split over the 4 warps
-    if (warp == 0) wgrad_tile<BF, 8>(sD5, kLdD5, 0, 3, sA[4], MLP_LD_H, 64, grad + mlp_off_w(4), g, t);
-    bias_grad<BF>(sD5, kLdD5, 3, grad + mlp_off_b(4));
-
-    // ---- hidden layers, last to first -----------------------------------------
-    uint32_t d[2][4][4];
-    {
-        float acc[2][8][4];
-        bwd_data<BF, 1, 8, 8>(sW + mlp_soff(4), MLP_LD_H, d5, acc, g, t);
-        __syncthreads();
-        mask_delta<BF, 8>(acc, sA[4], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
-    }
-    for (int l = 3; l >= 0; --l) {
-        __syncthreads();
-        // gradient of layer l (input sA[l], output deltas in sD)
-        if (l == 0)
-            wgrad_tile<BF, 10>(sD, MLP_LD_H, warp * 16, 64, sA[0], MLP_LD_IN, 80, grad + mlp_off_w(0), g, t);
-        else
-            wgrad_tile<BF, 8>(sD, MLP_LD_H, warp * 16, 64, sA[l], MLP_LD_H, 64, grad + mlp_off_w(l), g, t);
-        bias_grad<BF>(sD, MLP_LD_H, 64, grad + mlp_off_b(l));
-        if (l == 0) break;
-        float acc[2][8][4];
-        bwd_data<BF, 4, 8, 64>(sW + mlp_soff(l), MLP_LD_H, d, acc, g, t);
-        __syncthreads();
-        mask_delta<BF, 8>(acc, sA[l], MLP_LD_H, sD, MLP_LD_H, rowbase, d, g, t);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // optimiser: overflow check, Adam, fp16 copy, loss-scale update
 // ---------------------------------------------------------------------------
 __global__ void k_mlp_check(const float* __restrict__ grad, MLPState* st) {
@@ -517,18 +258,267 @@ cudaError_t launch_mlp_infer_buffer(const MLPView& m, const float* queries, floa
                             n, st);
 }
 
+// ---------------------------------------------------------------------------
+// training on the tensor cores (tcgen05): one CTA (two warpgroups) per tile of
+// 128 samples.  Forward: the inference kernel's K = 80 products with the bias
+// in column 75, every layer input kept in shared memory (X0..X4).  Backward,
+// layer l = 4..0, two products per commit:
+//   dW_l^T [in (padded to 128) x out] = X_l^T dZ_l   (A and B read MN-major:
+//       the K-major tiles seen with the sample index as K);
+//   dX_l [128 x 80] = dZ_l W_l                       (B = W_l read MN-major);
+// row 75 of dW_l^T is the bias gradient (column 75 of X_l is the constant 1).
+// The gradients accumulate in tensor memory in fp32 over the tile's 128
+// samples and are added to the global sums with one atomic per entry.
+// ---------------------------------------------------------------------------
+#define TR_X_OFF(l) (43520 + 20480 * (l))      // layer inputs X0..X4 [128 x 80]
+#define TR_DZ_OFF(b) (145920 + 20480 * (b))    // deltas, two buffers [128 x 80]
+#define TR_BAR_OFF 186880
+#define TR_SMEM (TR_BAR_OFF + 16)
+#define TR_COLS 256                            // tensor memory: [0, 80) products, [128, 256) dW^T x 2
+
+// MN-major operand bit (15: A, 16: B) of the kind::f16 instruction descriptor
+__host__ __device__ constexpr uint32_t umma_idesc_f16_mn(int M, int N, uint32_t fmt, uint32_t a_mn, uint32_t b_mn) {
+    return umma_idesc_f16(M, N, fmt) | (a_mn << 15) | (b_mn << 16);
+}
+
+// Weight and bias gradients of layer l from tensor memory (dW_l^T, lane =
+// input index r) into the global sums: warpgroup g takes column half g (the
+// output layer's 16 columns go to warpgroup 0).
+template <int OUTS>
+__device__ __forceinline__ void tc_grad_out(int l, uint32_t tcol, int r, int g, float* __restrict__ grad) {
+    const int K = l == 0 ? 75 : 64, real_out = l == 4 ? 3 : 64;
+    const bool wrow = r < K, brow = r == MLP_TC_ONE_COL;
+    constexpr int PER = OUTS == 16 ? 16 : OUTS / 2;
+    if (OUTS == 16 && g != 0) return;
+    const int c_begin = OUTS == 16 ? 0 : PER * g;
+#pragma unroll
+    for (int c0 = c_begin; c0 < c_begin + PER; c0 += 16) {
+        uint32_t v[16];
+        TMEM_LD_X16(tcol + (uint32_t)c0, v, 0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (wrow || brow) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int o = c0 + j;
+                if (o < real_out) {
+                    const float gv = __uint_as_float(v[j]);
+                    if (wrow)
+                        atomicAdd(grad + mlp_off_w(l) + o * mlp_in(l) + r, gv);
+                    else
+                        atomicAdd(grad + mlp_off_b(l) + o, gv);
+                }
+            }
+        }
+    }
+}
+
+// samples [n][3] float4: (y.xyz, _), (n.xyz, _), (target.rgb, weight); weight 0
+// excludes a sample.  Gradients of sum_s w_s sum_c (f - t)^2 / (sg(f)^2 + 0.01)
+// times the loss scale are added to grad; the weights are summed into
+// st->count.  Two warpgroups: thread t owns
+// sample row r = t mod 128 (its tensor-memory lane) and column half g = t / 128
+// of every epilogue.  The gradient atomics of layer l + 1 run while the tensor
+// core computes layer l's products (dW^T alternates between columns 128 and
+// 192 of tensor memory).
+template <bool BF>
+__global__ void __launch_bounds__(256, 1) k_mlp_train_tc(MLPView m, const float4* __restrict__ smp, uint32_t n,
+                                                         MLPState* __restrict__ st, float* __restrict__ grad) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint32_t s_taddr;
+    const int t = threadIdx.x, w = t >> 5, r = t & 127, g = t >> 7;
+    const uint32_t bar = smem_u32(sm + TR_BAR_OFF);
+    mlp_tc_load_weights<BF>(m, sm);
+    float4 tg = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g == 0) {
+        // this thread's sample: encoded input row, target and weight
+        const uint32_t s_i = blockIdx.x * 128u + (uint32_t)r;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f), nn = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (s_i < n) {
+            y = smp[3 * (size_t)s_i];
+            nn = smp[3 * (size_t)s_i + 1];
+            tg = smp[3 * (size_t)s_i + 2];
+        }
+        const unsigned cnt = __ballot_sync(0xffffffffu, tg.w > 0.f);
+        if ((t & 31) == 0 && cnt) atomicAdd(&st->count, (unsigned)__popc(cnt));
+        const float qv[6] = {(y.x - m.lo[0]) * m.scale, (y.y - m.lo[1]) * m.scale, (y.z - m.lo[2]) * m.scale,
+                             nn.x, nn.y, nn.z};
+        mlp_tc_encode_row<BF>(sm + TR_X_OFF(0), r, qv);
+    } else {
+        // columns 64..79 of the hidden layers' inputs: zeros and the constant 1;
+        // both delta buffers zeroed (their unused columns stay zero)
+        const uint32_t one = H16<BF>::pack(0.f, 0.f) | ((uint32_t)H16<BF>::bits(1.f) << 16);
+        for (int l = 1; l < 5; ++l) {
+            *reinterpret_cast<uint4*>(sm + TR_X_OFF(l) + kmajor_off(r, 64)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sm + TR_X_OFF(l) + kmajor_off(r, 72)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint32_t*>(sm + TR_X_OFF(l) + kmajor_off(r, 74)) = one;   // (74, 75) = (0, 1)
+        }
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 80; k += 8)
+                *reinterpret_cast<uint4*>(sm + TR_DZ_OFF(b) + kmajor_off(r, k)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(TR_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = s_taddr;
+    const uint32_t trow = tbase + ((uint32_t)(32 * (w & 3)) << 16);   // this warp's 32 lanes
+    const uint32_t base = smem_u32(sm);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    // ---- forward ----------------------------------------------------------------
+    float out[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int l = 0; l < 5 && !failed; ++l) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = umma_idesc_f16(128, l == 4 ? 16 : 64, H16<BF>::umma_fmt);
+            const uint32_t xa = base + TR_X_OFF(l), wl = base + MLP_TC_W_OFF(l);
+#pragma unroll
+            for (int s = 0; s < MLP_TC_K / 16; ++s)
+                umma_f16(tbase, umma_sdesc(xa + 256u * s, 128u, 1280u), umma_sdesc(wl + 256u * s, 128u, 1280u), idesc,
+                         s > 0 ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (l < 4) {
+            uint8_t* xn = sm + TR_X_OFF(l + 1);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int c2 = 2 * g + i;
+                uint32_t v[16];
+                TMEM_LD_X16(trow + 16u * (uint32_t)c2, v, 0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    *reinterpret_cast<uint4*>(xn + kmajor_off(r, 16 * c2 + 8 * h)) =
+                        make_uint4(H16<BF>::relu2(v[8 * h], v[8 * h + 1]), H16<BF>::relu2(v[8 * h + 2], v[8 * h + 3]),
+                                   H16<BF>::relu2(v[8 * h + 4], v[8 * h + 5]),
+                                   H16<BF>::relu2(v[8 * h + 6], v[8 * h + 7]));
+            }
+        } else if (g == 0) {
+            uint32_t v[16];
+            TMEM_LD_X16(trow, v, 0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            out[0] = __uint_as_float(v[0]);
+            out[1] = __uint_as_float(v[1]);
+            out[2] = __uint_as_float(v[2]);
+        }
+    }
+    // ---- output gradient (relative L2, denominator held constant) ----------------
+    if (!failed && g == 0) {
+        const float S = st->loss_scale;
+        const float tv[3] = {tg.x, tg.y, tg.z};
+        float d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = tg.w * S * 2.f * (out[c] - tv[c]) / (out[c] * out[c] + 0.01f);
+        *reinterpret_cast<uint4*>(sm + TR_DZ_OFF(0) + kmajor_off(r, 0)) =
+            make_uint4(H16<BF>::pack(d[0], d[1]), H16<BF>::pack(d[2], 0.f), 0u, 0u);
+    }
+    // ---- backward ---------------------------------------------------------------
+    int cur = 0;   // buffer holding dZ_l
+#pragma unroll 1
+    for (int l = 4; l >= 0 && !failed; --l) {
+        const int outs = l == 4 ? 16 : 64;
+        const uint32_t dw_col = 128u + 64u * (uint32_t)(l & 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t == 0) {
+            const uint32_t xa = base + TR_X_OFF(l), dz = base + TR_DZ_OFF(cur), wl = base + MLP_TC_W_OFF(l);
+            // dW^T = X^T dZ: M = 128 (inputs, padded), N = outs, K = 128 samples (two 8-row groups per step)
+            const uint32_t idw = umma_idesc_f16_mn(128, outs, H16<BF>::umma_fmt, 1u, 1u);
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                umma_f16(tbase + dw_col, umma_sdesc(xa + 2560u * s, 1280u, 128u), umma_sdesc(dz + 2560u * s, 1280u, 128u),
+                         idw, s > 0 ? 1u : 0u);
+            if (l > 0) {
+                // dX = dZ W: M = 128 samples, N = 80 inputs, K = outs
+                const uint32_t idx = umma_idesc_f16_mn(128, 80, H16<BF>::umma_fmt, 0u, 1u);
+                for (int s = 0; s < outs / 16; ++s)
+                    umma_f16(tbase, umma_sdesc(dz + 256u * s, 128u, 1280u), umma_sdesc(wl + 2560u * s, 1280u, 128u), idx,
+                             s > 0 ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        // the previous layer's gradients, while these products run
+        if (l == 3)
+            tc_grad_out<16>(4, trow + 128u, r, g, grad);
+        else if (l < 3)
+            tc_grad_out<64>(l + 1, trow + 128u + 64u * (uint32_t)((l + 1) & 1), r, g, grad);
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (l > 0) {
+            // dZ_{l-1} = dX_l masked by the ReLU of X_l (its first 64 columns)
+            const uint8_t* xl = sm + TR_X_OFF(l);
+            uint8_t* dn = sm + TR_DZ_OFF(cur ^ 1);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int c2 = 2 * g + i;
+                uint32_t v[16];
+                TMEM_LD_X16(trow + 16u * (uint32_t)c2, v, 0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k0 = 16 * c2 + 8 * h;
+                    const uint4 xv = *reinterpret_cast<const uint4*>(xl + kmajor_off(r, k0));
+                    const uint32_t xs[4] = {xv.x, xv.y, xv.z, xv.w};
+                    uint32_t o4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float a0 = __uint_as_float(v[8 * h + 2 * q]), a1 = __uint_as_float(v[8 * h + 2 * q + 1]);
+                        const float m0 = H16<BF>::val((uint16_t)(xs[q] & 0xFFFFu)) > 0.f ? a0 : 0.f;
+                        const float m1 = H16<BF>::val((uint16_t)(xs[q] >> 16)) > 0.f ? a1 : 0.f;
+                        o4[q] = H16<BF>::pack(m0, m1);
+                    }
+                    *reinterpret_cast<uint4*>(dn + kmajor_off(r, k0)) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+                }
+            }
+            cur ^= 1;
+        } else {
+            tc_grad_out<64>(0, trow + 128u, r, g, grad);
+        }
+    }
+    if (failed && t == 0) atomicOr(m.err, ERRBIT_MMA_WAIT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TR_COLS));
+}
+
 template <bool BF>
 cudaError_t launch_mlp_grad_t(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                               cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_train<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)train_smem());
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    uint32_t grid = (n + kTrainRows - 1) / kTrainRows;
-    k_mlp_train<BF><<<grid, kTrainRows, train_smem(), st>>>(m, smp, n, state, grad);
+    uint32_t grid = (n + 127) / 128;
+    k_mlp_train_tc<BF><<<grid, 256, TR_SMEM, st>>>(m, smp, n, state, grad);
     return cudaGetLastError();
 }
 

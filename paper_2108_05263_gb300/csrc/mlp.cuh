@@ -19,20 +19,12 @@
 #define MLP_NPARAM 18184
 #define MLP_NW 17920
 #define MLP_BATCH 16384u   // training samples per Adam step
-#define MLP_LD_IN 88
-#define MLP_LD_H 72
-#define MLP_SW_HALVES (64 * 88 + 3 * 64 * 72 + 8 * 72)   // 20032
 
 __host__ __device__ constexpr int mlp_off_w(int l) {
     return l == 0 ? 0 : (l == 1 ? 5120 : (l == 2 ? 9216 : (l == 3 ? 13312 : 17408)));
 }
 __host__ __device__ constexpr int mlp_off_b(int l) { return 17920 + 64 * l; }
 __host__ __device__ constexpr int mlp_in(int l) { return l == 0 ? 80 : 64; }
-__host__ __device__ constexpr int mlp_out(int l) { return l == 4 ? 8 : 64; }
-__host__ __device__ constexpr int mlp_ld(int l) { return l == 0 ? MLP_LD_IN : MLP_LD_H; }
-__host__ __device__ constexpr int mlp_soff(int l) {
-    return l == 0 ? 0 : (l == 1 ? 5632 : (l == 2 ? 10240 : (l == 3 ? 14848 : 19456)));
-}
 
 // device-side optimiser / judge state
 struct MLPState {
@@ -75,13 +67,6 @@ struct H16<false> {
         asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(lo));
         return r;
     }
-    __device__ static __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    }
 };
 
 template <>
@@ -98,130 +83,7 @@ struct H16<true> {
         asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(lo));
         return r;
     }
-    __device__ static __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    }
 };
-
-__device__ __forceinline__ uint32_t h2_from(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
-
-
-// Copy the fp16 weights into padded shared rows and the biases (fp32).
-__device__ __forceinline__ void mlp_load_smem(const MLPView& m, uint16_t* sW, float* sb) {
-    // 16-byte chunks (rows of 80 / 64 halves hold whole chunks; padded rows of
-    // 88 / 72 halves keep them 16-byte aligned)
-    for (int c = threadIdx.x; c < MLP_NW / 8; c += blockDim.x) {
-        const int e = 8 * c;
-        const int l = e < 5120 ? 0 : (e < 9216 ? 1 : (e < 13312 ? 2 : (e < 17408 ? 3 : 4)));
-        const int r = e - mlp_off_w(l), in = mlp_in(l);
-        const int o = r / in, i = r - o * in;
-        *reinterpret_cast<uint4*>(sW + mlp_soff(l) + o * mlp_ld(l) + i) = *reinterpret_cast<const uint4*>(m.w16 + e);
-    }
-    for (int e = threadIdx.x; e < 264; e += blockDim.x) sb[e] = m.params[17920 + e];
-}
-
-// feature pair (c, c+1) of the input encoding (c even): sin / cos of
-// 2^k pi p'_a for c < 72, the normal for c = 72, 74, zeros beyond
-template <bool BF>
-__device__ __forceinline__ uint32_t feature_pair(const float* q, int c) {
-    if (c < 72) {
-        int a = c / 24, k = (c % 24) >> 1;
-        float sn, cs;
-        sincospif(ldexpf(q[a], k), &sn, &cs);
-        return H16<BF>::pack(sn, cs);
-    }
-    if (c == 72) return H16<BF>::pack(q[3], q[4]);
-    if (c == 74) return H16<BF>::pack(q[5], 0.f);
-    return 0u;
-}
-
-// A fragments of the encoded inputs of a warp's 32 samples (2 m-tiles);
-// sq: per-sample (p'.xyz, n.xyz, valid, 0) rows of 8 floats.
-template <bool BF>
-__device__ __forceinline__ void mlp_input_frags(const float* sq, uint32_t (&a)[2][5][4], int g, int t) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const float* q0 = sq + (mt * 16 + g) * 8;
-        const float* q1 = sq + (mt * 16 + g + 8) * 8;
-#pragma unroll
-        for (int kt = 0; kt < 5; ++kt) {
-            int c = kt * 16 + 2 * t;
-            a[mt][kt][0] = feature_pair<BF>(q0, c);
-            a[mt][kt][1] = feature_pair<BF>(q1, c);
-            a[mt][kt][2] = feature_pair<BF>(q0, c + 8);
-            a[mt][kt][3] = feature_pair<BF>(q1, c + 8);
-        }
-    }
-}
-
-// acc = bias + A x W^T for one layer (KT k-tiles of the input, NT n-tiles of
-// the output), W in shared memory [out][ld] fp16
-template <bool BF, int KT, int NT>
-__device__ __forceinline__ void mlp_layer(const uint16_t* __restrict__ sW, int ld, const float* __restrict__ sb,
-                                          const uint32_t (&a)[2][KT][4], float (&acc)[2][NT][4], int g, int t) {
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        float b0 = sb[nt * 8 + 2 * t], b1 = sb[nt * 8 + 2 * t + 1];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            acc[mt][nt][0] = b0;
-            acc[mt][nt][1] = b1;
-            acc[mt][nt][2] = b0;
-            acc[mt][nt][3] = b1;
-        }
-    }
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const uint16_t* w = sW + (nt * 8 + g) * ld + kt * 16 + 2 * t;
-            uint32_t b0 = *reinterpret_cast<const uint32_t*>(w);
-            uint32_t b1 = *reinterpret_cast<const uint32_t*>(w + 8);
-            H16<BF>::mma(acc[0][nt], a[0][kt], b0, b1);
-            H16<BF>::mma(acc[1][nt], a[1][kt], b0, b1);
-        }
-    }
-}
-
-// ReLU and conversion of an output (D) fragment set into the A fragments of
-// the next layer: output n-tiles 2k and 2k+1 form input k-tile k.
-template <bool BF, int NT>
-__device__ __forceinline__ void relu_to_frags(const float (&acc)[2][NT][4], uint32_t (&a)[2][NT / 2][4]) {
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int k = 0; k < NT / 2; ++k) {
-            const float* lo = acc[mt][2 * k];
-            const float* hi = acc[mt][2 * k + 1];
-            a[mt][k][0] = H16<BF>::pack(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
-            a[mt][k][1] = H16<BF>::pack(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
-            a[mt][k][2] = H16<BF>::pack(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
-            a[mt][k][3] = H16<BF>::pack(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
-        }
-}
-
-// Full forward pass of a warp's 32 samples; out: acc of the output layer
-// (rows g / g+8 of each m-tile, columns 2t, 2t+1 of 8).
-template <bool BF>
-__device__ __forceinline__ void mlp_forward(const uint16_t* sW, const float* sb, const float* sq,
-                                            float (&out)[2][1][4], int g, int t) {
-    uint32_t a0[2][5][4];
-    mlp_input_frags<BF>(sq, a0, g, t);
-    float acc[2][8][4];
-    uint32_t a[2][4][4];
-    mlp_layer<BF, 5, 8>(sW + mlp_soff(0), MLP_LD_IN, sb, a0, acc, g, t);
-    relu_to_frags<BF, 8>(acc, a);
-#pragma unroll
-    for (int l = 1; l < 4; ++l) {
-        mlp_layer<BF, 4, 8>(sW + mlp_soff(l), MLP_LD_H, sb + 64 * l, a, acc, g, t);
-        relu_to_frags<BF, 8>(acc, a);
-    }
-    mlp_layer<BF, 4, 1>(sW + mlp_soff(4), MLP_LD_H, sb + 256, a, out, g, t);
-}
 
 // ---------------------------------------------------------------------------
 // inference on the 5th-generation tensor cores: Q::query(i, p, n) -> valid,
@@ -317,20 +179,30 @@ __device__ __forceinline__ int wg_or(int g, int pred) {
           "=r"(v[o + 12]), "=r"(v[o + 13]), "=r"(v[o + 14]), "=r"(v[o + 15])                             \
         : "r"(taddr))
 
-// weights of layer l as [rows][80] fp16 in the canonical layout: the real
-// inputs, the bias (fp16) in column 75, zeros elsewhere; W5 padded to 16 rows
+// weights of layer l as [rows][80] fp16 tiles in the canonical layout, copied
+// in 16-byte chunks of the weight rows (8 inputs each): the real inputs, the
+// bias (fp16) in input 75, zeros elsewhere.  The chunk of inputs 72..79 is
+// rebuilt: layer 0 keeps its inputs 72..74 there, the hidden layers have none.
+// W5 is padded to 16 rows; rows past a layer's outputs stay zero.
 template <bool BF>
 __device__ __forceinline__ void mlp_tc_load_weights(const MLPView& m, uint8_t* sm) {
-    for (int e = threadIdx.x; e < 4 * 64 * MLP_TC_K + 16 * MLP_TC_K; e += blockDim.x) {
-        const int l = e < 4 * 64 * MLP_TC_K ? e / (64 * MLP_TC_K) : 4;
-        const int r = (e - l * 64 * MLP_TC_K) / MLP_TC_K, k = (e - l * 64 * MLP_TC_K) % MLP_TC_K;
+    for (int e = threadIdx.x; e < 4 * 64 * 10 + 16 * 10; e += blockDim.x) {
+        const int l = e < 2560 ? e / 640 : 4;
+        const int rem = e < 2560 ? e - l * 640 : e - 2560;
+        const int r = rem / 10, c = rem - r * 10;
         const int K = mlp_in(l), rows = l == 4 ? 3 : 64;
-        float v = 0.f;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (r < rows) {
-            if (k < K && !(l == 0 && k >= 75)) v = H16<BF>::val(m.w16[mlp_off_w(l) + r * K + k]);
-            else if (k == MLP_TC_ONE_COL) v = m.params[mlp_off_b(l) + r];
+            if (8 * c < K) v = __ldg(reinterpret_cast<const uint4*>(m.w16 + mlp_off_w(l) + r * K + 8 * c));
+            if (c == 9) {
+                const uint32_t b = H16<BF>::bits(m.params[mlp_off_b(l) + r]);
+                v.y = (l == 0 ? (v.y & 0xFFFFu) : 0u) | (b << 16);
+                v.x = l == 0 ? v.x : 0u;
+                v.z = 0u;
+                v.w = 0u;
+            }
         }
-        *reinterpret_cast<uint16_t*>(sm + MLP_TC_W_OFF(l) + kmajor_off(r, k)) = H16<BF>::bits(v);
+        *reinterpret_cast<uint4*>(sm + MLP_TC_W_OFF(l) + kmajor_off(r, 8 * c)) = v;
     }
 }
 
