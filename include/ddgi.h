@@ -18,6 +18,9 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls enqueue work and return without synchronising, except
  *    ddgi_get_status and the *_get functions, which synchronise `stream`.
+ *    restir_initial forks part of its work to a stream the context owns and
+ *    joins it back into `stream` (events; also under graph capture), so
+ *    every effect is still ordered on `stream`.
  *  - Argument errors (NULL, misalignment, size mismatch, out-of-range
  *    configuration) are detected on the host before anything is enqueued and
  *    return DDGI_ERR_INVALID_ARG.  Launch failures return DDGI_ERR_CUDA with

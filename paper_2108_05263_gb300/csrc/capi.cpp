@@ -77,6 +77,10 @@ struct ddgi_ctx {
     float* pin = nullptr;
     cudaEvent_t pin_ev = nullptr;
     bool pin_pending = false;
+    // second stream of restir_initial: the emitter candidates run there while
+    // the BSDF rays are traced on the caller's stream (fork / join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool offsets_used = false;       // some probe offset may be non-zero (relocation ran or offsets were set)
     uint64_t device_bytes = 0;
     std::vector<void*> allocs;
@@ -308,6 +312,14 @@ void release(ddgi_ctx* c) {
     }
     c->pin_ev = nullptr;
     c->pin_pending = false;
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     if (c->pin) cudaFreeHost(c->pin);
     c->pin = nullptr;
 }
@@ -1052,10 +1064,15 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     MLPView mv = mlp_view(ctx);
     if (ctx->cfg.learned_target)
         CK(grow(ctx, &ctx->ind, &ctx->ind_cap, (size_t)n * ctx->cfg.num_bsdf_candidates, (cudaStream_t)stream));
+    if (!ctx->side) {
+        CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
     CK(launch_restir_initial(scene_view(ctx), volume_view(ctx), restir_params(ctx), g, r,
                              reinterpret_cast<float4*>(residual), frame, ctx->hits, ctx->counter,
                              ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind,
-                             (cudaStream_t)stream));
+                             (cudaStream_t)stream, ctx->side, ctx->ev_fork, ctx->ev_join));
     return DDGI_OK;
 }
 

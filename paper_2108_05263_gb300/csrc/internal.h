@@ -72,7 +72,8 @@ cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, float2* hits, uint32_t* counter, const struct MLPView* mlp,
-                                  struct MLPState* mst, float4* ind, cudaStream_t st);
+                                  struct MLPState* mst, float4* ind, cudaStream_t st, cudaStream_t side,
+                                  cudaEvent_t ev_fork, cudaEvent_t ev_join);
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                    float3 prev_cam, const ResView& cur,
                                    const ResView& prev, const ResView& out, uint32_t frame,

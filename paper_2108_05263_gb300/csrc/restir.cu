@@ -532,20 +532,37 @@ cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, c
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, float2* hits, uint32_t* counter, const MLPView* mlp,
-                                  MLPState* mst, float4* ind, cudaStream_t st) {
+                                  MLPState* mst, float4* ind, cudaStream_t st, cudaStream_t side,
+                                  cudaEvent_t ev_fork, cudaEvent_t ev_join) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     const uint32_t nl = s.num_emitters > 0 ? rp.n_light : 0u;
     BsdfGen gen{g, rp, frame, nl, rp.n_bsdf};
-    cudaError_t e = launch_trace<BsdfGen, false>(s, gen, (uint32_t)g.width * g.height * rp.n_bsdf,
-                                                 counter, hits, st);
+    // The emitter candidates and the BSDF rays read only the G-buffer and
+    // write disjoint buffers (the records' stream state / the hits): with a
+    // side stream they run concurrently, each at full occupancy, so that one
+    // kernel's tail on the SMs overlaps the other; k_restir_initial waits for
+    // both.
+    const bool fork = nl > 0 && side && ev_fork && ev_join;
+    cudaError_t e;
+    if (fork) {
+        if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
+    }
+    e = launch_trace<BsdfGen, false>(s, gen, (uint32_t)g.width * g.height * rp.n_bsdf, counter, hits, st);
     if (e != cudaSuccess) return e;
+    if (fork) {
+        if ((e = launch_emitter_candidates(s, v, rp, g, out, frame, side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
+    }
     if (mlp) {
         e = launch_mlp_infer(*mlp, BsdfHitQuery{s, g, rp, frame, nl, rp.n_bsdf, hits, ind},
                              (uint32_t)g.width * g.height * rp.n_bsdf, st);
         if (e != cudaSuccess) return e;
     }
     dim3 b(16, 8);
-    if (nl > 0) {
+    if (fork) {
+        if ((e = cudaStreamWaitEvent(st, ev_join, 0)) != cudaSuccess) return e;
+    } else if (nl > 0) {
         e = launch_emitter_candidates(s, v, rp, g, out, frame, st);
         if (e != cudaSuccess) return e;
     }
