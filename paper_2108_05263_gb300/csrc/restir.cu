@@ -184,7 +184,10 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
     float4* rec = out.rec + 4 * (size_t)pix;
     st32(rec, make_float4(cs.sel.y.x, cs.sel.y.y, cs.sel.y.z, cs.wsum),
          make_float4(cs.sel.L.x, cs.sel.L.y, cs.sel.L.z, cs.sel.p));
-    rec[3] = make_float4(__uint_as_float(cs.sel.tri), __uint_as_float(cs.sel.tag), 0.f, 0.f);
+    // the second half whole (q2 unused here): a 16-byte store would leave the
+    // 32-byte sector partial, which the memory then reads to merge
+    st32(rec + 2, make_float4(0.f, 0.f, 0.f, 0.f),
+         make_float4(__uint_as_float(cs.sel.tri), __uint_as_float(cs.sel.tag), 0.f, 0.f));
 }
 
 // one thread per pixel, emitter tables from global memory (L1); rows run
