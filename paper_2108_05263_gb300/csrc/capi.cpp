@@ -381,7 +381,7 @@ cudaError_t mlp_upload(ddgi_ctx* c, const float* host_params) {
     if (e == cudaSuccess) e = cudaMemcpy(c->mlp_w16s, h.data(), MLP_NW * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->mlp_m, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_v, 0, MLP_NPARAM * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, 2 * MLP_NPARAM * sizeof(float));
     c->mlp_step = 0;
     return e;
 }
@@ -676,7 +676,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(err, 4)
     ALLOC(counter, 4)
     ALLOC(mlp_params, MLP_NPARAM)
-    ALLOC(mlp_grad, MLP_NPARAM)
+    ALLOC(mlp_grad, 2 * MLP_NPARAM)   // two buffers: Adam step t accumulates in buffer t & 1
     ALLOC(mlp_m, MLP_NPARAM)
     ALLOC(mlp_v, MLP_NPARAM)
     ALLOC(tmp_grad, MLP_NPARAM)
@@ -1003,6 +1003,8 @@ ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, v
         CK(cudaMemcpyAsync(ctx->mlp_w16s, b + L.mlp16 + MLP_NW * sizeof(uint16_t), MLP_NW * sizeof(uint16_t),
                            cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(ctx->mlp_state, b + L.mst, sizeof(MLPState), cudaMemcpyHostToDevice, st));
+        // both gradient buffers zero, whichever the restored step uses next
+        CK(cudaMemsetAsync(ctx->mlp_grad, 0, 2 * MLP_NPARAM * sizeof(float), st));
     }
     CK(cudaStreamSynchronize(st));
     ctx->updates = h[8];
@@ -1196,7 +1198,7 @@ ddgi_status ddgi_mlp_grad(ddgi_ctx* ctx, const float* samples, uint32_t n, float
     cudaStream_t st = (cudaStream_t)stream;
     ddgi_status s = stage_samples(ctx, samples, n, st);
     if (s != DDGI_OK) return s;
-    CK(launch_mlp_grad_only(mlp_view(ctx, false), ctx->tmp_smp, n, ctx->mlp_state, ctx->mlp_grad, ctx->tmp_grad, st));
+    CK(launch_mlp_grad_only(mlp_view(ctx, false), ctx->tmp_smp, n, ctx->mlp_state, ctx->tmp_grad, st));
     CK(cudaMemcpyAsync(grad, ctx->tmp_grad, MLP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     return DDGI_OK;

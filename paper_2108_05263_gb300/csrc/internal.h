@@ -103,8 +103,8 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
                                    float* ema, uint16_t* w16s, float ema_a, float lr, uint32_t step, int serve,
                                    cudaStream_t st);
 cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st);
-cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
-                                 float* out, cudaStream_t st);
+cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* out,
+                                 cudaStream_t st);
 cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* params,
                             float* grad, float* mom, float* vel, uint16_t* w16, float lr, uint32_t step,
                             cudaStream_t st);

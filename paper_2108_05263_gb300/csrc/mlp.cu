@@ -27,26 +27,40 @@ struct BufferQuery {
 // ---------------------------------------------------------------------------
 // optimiser: overflow check, Adam, fp16 copy, loss-scale update
 // ---------------------------------------------------------------------------
-__global__ void k_mlp_check(const float* __restrict__ grad, MLPState* st) {
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    int local = 0;
-    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) local |= !isfinite(grad[i]);
-    if (local) atomicOr(&bad, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) st->overflow = bad;
-}
-
-__global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ grad, float* __restrict__ mom,
-                           float* __restrict__ vel, uint16_t* __restrict__ w16, int bf16, MLPState* st, float lr,
-                           float b1, float b2, float eps, uint32_t step) {
+// One Adam step, fused with the overflow check and the loss-scale update.
+// The gradient of Adam step t (1-based) accumulates in buffer t & 1 of grad2
+// (two buffers of MLP_NPARAM floats).  Every CTA checks the whole buffer for
+// non-finite values, so all CTAs agree on skipping the step without a
+// grid-wide barrier, updates its slice of the parameters and zeroes its slice
+// of the other buffer, which step t + 1 accumulates into and which nothing
+// reads during this step.  The last CTA to finish (every CTA has read the
+// loss scale and the sample count by then) updates the loss scale, records
+// the step's sample count and resets the accumulator.
+constexpr int kOptThreads = 512;
+__global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ params, float* __restrict__ grad2,
+                                                         float* __restrict__ mom, float* __restrict__ vel,
+                                                         uint16_t* __restrict__ w16, int bf16, MLPState* st, float lr,
+                                                         float b1, float b2, float eps, uint32_t step) {
+    __shared__ float s_scale;
+    __shared__ uint32_t s_acc;
+    __shared__ int s_last;
+    const float* __restrict__ g = grad2 + (size_t)(step & 1u) * MLP_NPARAM;
+    float* __restrict__ gz = grad2 + (size_t)((step + 1u) & 1u) * MLP_NPARAM;
+    if (threadIdx.x == 0) {
+        s_scale = st->loss_scale;
+        s_acc = st->acc;
+    }
+    int bad = 0;
+    for (int i = threadIdx.x; i < MLP_NPARAM / 4; i += blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(g)[i];
+        bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+    }
+    const bool overflow = __syncthreads_or(bad) != 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool overflow = st->overflow != 0;
     if (i < MLP_NPARAM) {
         if (!overflow) {
-            const float denom = st->loss_scale * 3.f * (float)max(st->count, 1u);
-            const float gr = grad[i] / denom;
+            const float denom = s_scale * 3.f * (float)max(s_acc, 1u);
+            const float gr = g[i] / denom;
             const float mm = b1 * mom[i] + (1.f - b1) * gr;
             const float vv = b2 * vel[i] + (1.f - b2) * gr * gr;
             mom[i] = mm;
@@ -57,14 +71,25 @@ __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ grad,
             params[i] = p;
             if (i < MLP_NW) w16[i] = bf16 ? H16<true>::bits(p) : H16<false>::bits(p);
         }
-        grad[i] = 0.f;
+        gz[i] = 0.f;
     }
-    if (i == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        st->done = 0;
+        st->overflow = overflow ? 1u : 0u;
+        st->count = s_acc;
+        st->acc = 0;
         if (overflow) {
-            st->loss_scale = fmaxf(st->loss_scale * 0.5f, 1.f / 1024.f);
+            st->loss_scale = fmaxf(s_scale * 0.5f, 1.f / 1024.f);
             st->good = 0;
         } else if (++st->good >= 512u) {
-            st->loss_scale = fminf(st->loss_scale * 2.f, 32768.f);
+            st->loss_scale = fminf(s_scale * 2.f, 32768.f);
             st->good = 0;
         }
     }
@@ -209,13 +234,13 @@ struct JudgeQuery {
 
 __global__ void k_mlp_begin(MLPState* st) {
     st->count = 0;
+    st->acc = 0;
     st->judge_mlp = 0.0;
     st->judge_probe = 0.0;
     st->judge_n = 0;
 }
 
 // serve: 0 = the judge decides, 1 = always the network, 2 = always the probes
-__global__ void k_mlp_count_reset(MLPState* st) { st->count = 0; }
 
 __global__ void k_mlp_judge(MLPState* st, int serve) {
     if (serve == 1)
@@ -239,9 +264,9 @@ __global__ void k_mlp_ema(const float* __restrict__ params, float* __restrict__ 
 }
 
 // gradient of the mean loss (unscaled) into out
-__global__ void k_mlp_grad_out(const float* __restrict__ grad, const MLPState* st, float* __restrict__ out) {
+__global__ void k_mlp_grad_out(const float* grad, const MLPState* st, float* out) {   // may run in place
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < MLP_NPARAM) out[i] = grad[i] / (st->loss_scale * 3.f * (float)max(st->count, 1u));
+    if (i < MLP_NPARAM) out[i] = grad[i] / (st->loss_scale * 3.f * (float)max(st->acc, 1u));
 }
 
 __global__ void k_zero(float* p, int n) {
@@ -315,7 +340,7 @@ __device__ __forceinline__ void tc_grad_out(int l, uint32_t tcol, int r, int g, 
 // samples [n][3] float4: (y.xyz, _), (n.xyz, _), (target.rgb, weight); weight 0
 // excludes a sample.  Gradients of sum_s w_s sum_c (f - t)^2 / (sg(f)^2 + 0.01)
 // times the loss scale are added to grad; the weights are summed into
-// st->count.  Two warpgroups: thread t owns
+// st->acc.  Two warpgroups: thread t owns
 // sample row r = t mod 128 (its tensor-memory lane) and column half g = t / 128
 // of every epilogue.  The gradient atomics of layer l + 1 run while the tensor
 // core computes layer l's products (dW^T alternates between columns 128 and
@@ -339,7 +364,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train_tc(MLPView m, const float4
             tg = smp[3 * (size_t)s_i + 2];
         }
         const unsigned cnt = __ballot_sync(0xffffffffu, tg.w > 0.f);
-        if ((t & 31) == 0 && cnt) atomicAdd(&st->count, (unsigned)__popc(cnt));
+        if ((t & 31) == 0 && cnt) atomicAdd(&st->acc, (unsigned)__popc(cnt));
         const float qv[6] = {(y.x - m.lo[0]) * m.scale, (y.y - m.lo[1]) * m.scale, (y.z - m.lo[2]) * m.scale,
                              nn.x, nn.y, nn.z};
         mlp_tc_encode_row<BF>(sm + TR_X_OFF(0), r, qv);
@@ -529,13 +554,11 @@ cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLP
                   : launch_mlp_grad_t<false>(m, smp, n, state, grad, st);
 }
 
-cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, uint16_t* w16, int bf16,
+// grad2: the two gradient buffers (step t reads buffer t & 1)
+cudaError_t launch_mlp_adam(float* params, float* grad2, float* mom, float* vel, uint16_t* w16, int bf16,
                             MLPState* state, float lr, uint32_t step, cudaStream_t st) {
-    k_mlp_check<<<1, 1024, 0, st>>>(grad, state);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, grad, mom, vel, w16, bf16, state, lr, 0.9f,
-                                                           0.99f, 1e-8f, step);
+    k_mlp_opt<<<(MLP_NPARAM + kOptThreads - 1) / kOptThreads, kOptThreads, 0, st>>>(
+        params, grad2, mom, vel, w16, bf16, state, lr, 0.9f, 0.99f, 1e-8f, step);
     return cudaGetLastError();
 }
 
@@ -555,8 +578,7 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
     // minibatches of MLP_BATCH samples, one Adam step each
     for (uint32_t b0 = 0, k = 0; b0 < tp.samples; b0 += MLP_BATCH, ++k) {
         const uint32_t nb = min(MLP_BATCH, tp.samples - b0);
-        k_mlp_count_reset<<<1, 1, 0, st>>>(state);
-        e = launch_mlp_grad(m, smp + 3 * (size_t)b0, nb, state, grad, st);
+        e = launch_mlp_grad(m, smp + 3 * (size_t)b0, nb, state, grad + (size_t)((step + k) & 1u) * MLP_NPARAM, st);
         if (e != cudaSuccess) return e;
         e = launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step + k, st);
         if (e != cudaSuccess) return e;
@@ -576,16 +598,14 @@ cudaError_t launch_mlp_serve(MLPState* state, int serve, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
-                                 float* out, cudaStream_t st) {
-    k_zero<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(grad, MLP_NPARAM);
+cudaError_t launch_mlp_grad_only(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* out,
+                                 cudaStream_t st) {
+    // accumulated in `out` itself, apart from the optimiser's buffers
+    k_zero<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(out, MLP_NPARAM);
     k_mlp_begin<<<1, 1, 0, st>>>(state);
-    cudaError_t e = launch_mlp_grad(m, smp, n, state, grad, st);
+    cudaError_t e = launch_mlp_grad(m, smp, n, state, out, st);
     if (e != cudaSuccess) return e;
-    k_mlp_grad_out<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(grad, state, out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_zero<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(grad, MLP_NPARAM);
+    k_mlp_grad_out<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(out, state, out);
     return cudaGetLastError();
 }
 
@@ -593,7 +613,7 @@ cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLP
                             float* grad, float* mom, float* vel, uint16_t* w16, float lr, uint32_t step,
                             cudaStream_t st) {
     k_mlp_begin<<<1, 1, 0, st>>>(state);
-    cudaError_t e = launch_mlp_grad(m, smp, n, state, grad, st);
+    cudaError_t e = launch_mlp_grad(m, smp, n, state, grad + (size_t)(step & 1u) * MLP_NPARAM, st);
     if (e != cudaSuccess) return e;
     return launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step, st);
 }

@@ -31,11 +31,13 @@ struct MLPState {
     float loss_scale;      // gradients are computed for loss * loss_scale
     uint32_t overflow;     // last step saw a non-finite gradient (skipped)
     uint32_t good;         // steps since the last loss-scale change
-    uint32_t count;        // training samples of the current step
+    uint32_t count;        // training samples of the last Adam step
     double judge_mlp;      // held-out relative squared error of the network
     double judge_probe;    // ... and of the probe lookup
     uint32_t judge_n;      // held-out samples counted
     uint32_t use_mlp;      // 1: the network serves queries this frame
+    uint32_t acc;          // training samples of the step in progress
+    uint32_t done;         // optimiser CTAs finished (the last one resets it)
 };
 
 struct MLPView {
