@@ -110,8 +110,9 @@ cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLP
                             cudaStream_t st);
 cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                             cudaStream_t st);
-cudaError_t launch_mlp_adam(float* params, float* grad, float* mom, float* vel, uint16_t* w16, int bf16,
-                            MLPState* state, float lr, uint32_t step, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* params, float* grad2, float* mom, float* vel, uint16_t* w16, int bf16,
+                            MLPState* state, float lr, uint32_t step, cudaStream_t st, float* ema, uint16_t* w16s,
+                            float ema_a);
 
 cudaError_t launch_reference(const SceneView& s, const CamView& cam, uint32_t seed, uint32_t sample0,
                              uint32_t spp, uint32_t max_depth, double* accum, float4* mean, cudaStream_t st);

@@ -3,6 +3,9 @@
 // forward + backward training step with fp32 gradient accumulation and
 // dynamic loss scaling, Adam, and the generation of self-training samples
 // from probe-origin rays with one cosine bounce.
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include "internal.h"
 #include "mlp.cuh"
 #include "trace_engine.cuh"
@@ -40,7 +43,9 @@ constexpr int kOptThreads = 512;
 __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ params, float* __restrict__ grad2,
                                                          float* __restrict__ mom, float* __restrict__ vel,
                                                          uint16_t* __restrict__ w16, int bf16, MLPState* st, float lr,
-                                                         float b1, float b2, float eps, uint32_t step) {
+                                                         float b1, float b2, float eps, uint32_t step,
+                                                         float* __restrict__ ema, uint16_t* __restrict__ w16s,
+                                                         float ema_a) {
     __shared__ float s_scale;
     __shared__ uint32_t s_acc;
     __shared__ int s_last;
@@ -58,6 +63,7 @@ __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ par
     const bool overflow = __syncthreads_or(bad) != 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < MLP_NPARAM) {
+        float p = params[i];
         if (!overflow) {
             const float denom = s_scale * 3.f * (float)max(s_acc, 1u);
             const float gr = g[i] / denom;
@@ -67,11 +73,16 @@ __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ par
             vel[i] = vv;
             const float mh = mm / (1.f - powf(b1, (float)step));
             const float vh = vv / (1.f - powf(b2, (float)step));
-            const float p = params[i] - lr * mh / (sqrtf(vh) + eps);
+            p = p - lr * mh / (sqrtf(vh) + eps);
             params[i] = p;
             if (i < MLP_NW) w16[i] = bf16 ? H16<true>::bits(p) : H16<false>::bits(p);
         }
         gz[i] = 0.f;
+        if (ema) {   // the frame's last step: the served moving average follows
+            const float e = ema_a * ema[i] + (1.f - ema_a) * p;
+            ema[i] = e;
+            if (i < MLP_NW) w16s[i] = bf16 ? H16<true>::bits(e) : H16<false>::bits(e);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -119,8 +130,16 @@ __device__ __forceinline__ f3 bounce_dir(const TrainParams& tp, uint32_t s, f3 n
     return onb_to_world(n, r * cs, r * sn, sqrtf(fmaxf(0.f, 1.f - u0)));
 }
 
-__global__ void __launch_bounds__(128) k_train_primary(SceneView s, VolumeView v, TrainParams tp, float4* smp) {
+__global__ void __launch_bounds__(128) k_train_primary(SceneView s, VolumeView v, TrainParams tp, float4* smp,
+                                                       MLPState* st) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {   // the frame's counters (nothing reads them before the training kernels)
+        st->count = 0;
+        st->acc = 0;
+        st->judge_mlp = 0.0;
+        st->judge_probe = 0.0;
+        st->judge_n = 0;
+    }
     if (i >= tp.samples) return;
     const uint32_t p = i / tp.per, r = i - p * tp.per;
     f3 P = probe_center(v, (int)p);
@@ -226,9 +245,17 @@ struct JudgeQuery {
             em += (mv[c] - tv[c]) * (mv[c] - tv[c]) / den;
             ep += (pv[c] - tv[c]) * (pv[c] - tv[c]) / den;
         }
-        atomicAdd(&st->judge_mlp, (double)em);
-        atomicAdd(&st->judge_probe, (double)ep);
-        atomicAdd(&st->judge_n, 1u);
+        // one atomic per converged group of lanes: three same-address
+        // atomics per sample serialise at one L2 slice
+        namespace cg = cooperative_groups;
+        const cg::coalesced_group grp = cg::coalesced_threads();
+        const double sm = cg::reduce(grp, (double)em, cg::plus<double>());
+        const double sp = cg::reduce(grp, (double)ep, cg::plus<double>());
+        if (grp.thread_rank() == 0) {
+            atomicAdd(&st->judge_mlp, sm);
+            atomicAdd(&st->judge_probe, sp);
+            atomicAdd(&st->judge_n, grp.size());
+        }
     }
 };
 
@@ -252,17 +279,6 @@ __global__ void k_mlp_judge(MLPState* st, int serve) {
 }
 
 // served network: ema <- a ema + (1 - a) params, fp16 copy of its weights
-__global__ void k_mlp_ema(const float* __restrict__ params, float* __restrict__ ema, uint16_t* __restrict__ w16s,
-                          int bf16,
-                          float a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < MLP_NPARAM) {
-        const float e = a * ema[i] + (1.f - a) * params[i];
-        ema[i] = e;
-        if (i < MLP_NW) w16s[i] = bf16 ? H16<true>::bits(e) : H16<false>::bits(e);
-    }
-}
-
 // gradient of the mean loss (unscaled) into out
 __global__ void k_mlp_grad_out(const float* grad, const MLPState* st, float* out) {   // may run in place
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -556,9 +572,10 @@ cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLP
 
 // grad2: the two gradient buffers (step t reads buffer t & 1)
 cudaError_t launch_mlp_adam(float* params, float* grad2, float* mom, float* vel, uint16_t* w16, int bf16,
-                            MLPState* state, float lr, uint32_t step, cudaStream_t st) {
+                            MLPState* state, float lr, uint32_t step, cudaStream_t st, float* ema, uint16_t* w16s,
+                            float ema_a) {
     k_mlp_opt<<<(MLP_NPARAM + kOptThreads - 1) / kOptThreads, kOptThreads, 0, st>>>(
-        params, grad2, mom, vel, w16, bf16, state, lr, 0.9f, 0.99f, 1e-8f, step);
+        params, grad2, mom, vel, w16, bf16, state, lr, 0.9f, 0.99f, 1e-8f, step, ema, w16s, ema_a);
     return cudaGetLastError();
 }
 
@@ -567,8 +584,7 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
                                    MLPState* state, float* params, float* grad, float* mom, float* vel, uint16_t* w16,
                                    float* ema, uint16_t* w16s, float ema_a, float lr, uint32_t step, int serve,
                                    cudaStream_t st) {
-    k_mlp_begin<<<1, 1, 0, st>>>(state);
-    k_train_primary<<<(tp.samples + 127) / 128, 128, 0, st>>>(s, v, tp, smp);
+    k_train_primary<<<(tp.samples + 127) / 128, 128, 0, st>>>(s, v, tp, smp, state);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_trace<BounceGen, false>(s, BounceGen{smp, tp}, tp.samples, counter, hits, st);
@@ -580,12 +596,11 @@ cudaError_t launch_mlp_train_frame(const SceneView& s, const VolumeView& v, cons
         const uint32_t nb = min(MLP_BATCH, tp.samples - b0);
         e = launch_mlp_grad(m, smp + 3 * (size_t)b0, nb, state, grad + (size_t)((step + k) & 1u) * MLP_NPARAM, st);
         if (e != cudaSuccess) return e;
-        e = launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step + k, st);
+        const bool last = b0 + MLP_BATCH >= tp.samples;
+        e = launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step + k, st, last ? ema : nullptr,
+                            w16s, ema_a);
         if (e != cudaSuccess) return e;
     }
-    k_mlp_ema<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(params, ema, w16s, m.bf16, ema_a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     // the judge compares the served network with the probes on held-out samples
     e = launch_mlp_infer(ms, JudgeQuery{v, tp, smp, state}, tp.samples / 16, st);
     if (e != cudaSuccess) return e;
@@ -615,5 +630,5 @@ cudaError_t launch_mlp_step(const MLPView& m, const float4* smp, uint32_t n, MLP
     k_mlp_begin<<<1, 1, 0, st>>>(state);
     cudaError_t e = launch_mlp_grad(m, smp, n, state, grad + (size_t)(step & 1u) * MLP_NPARAM, st);
     if (e != cudaSuccess) return e;
-    return launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step, st);
+    return launch_mlp_adam(params, grad, mom, vel, w16, m.bf16, state, lr, step, st, nullptr, nullptr, 0.f);
 }
