@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -382,6 +383,8 @@ cudaError_t mlp_upload(ddgi_ctx* c, const float* host_params) {
     if (e == cudaSuccess) e = cudaMemset(c->mlp_m, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_v, 0, MLP_NPARAM * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->mlp_grad, 0, 2 * MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess && c->mlp_state)   // Adam restarts: no step applied yet
+        e = cudaMemset(reinterpret_cast<char*>(c->mlp_state) + offsetof(MLPState, adam_t), 0, sizeof(uint32_t));
     c->mlp_step = 0;
     return e;
 }

@@ -30,8 +30,12 @@ struct BufferQuery {
 // ---------------------------------------------------------------------------
 // optimiser: overflow check, Adam, fp16 copy, loss-scale update
 // ---------------------------------------------------------------------------
-// One Adam step, fused with the overflow check and the loss-scale update.
-// The gradient of Adam step t (1-based) accumulates in buffer t & 1 of grad2
+// One Adam step, fused with the overflow check and the loss-scale update
+// (dynamic loss scaling: a step whose gradient holds a non-finite value is
+// skipped -- parameters and moments untouched, the scale halved -- and does
+// not count in Adam's bias correction, which uses the steps applied).
+// The gradient of optimiser step t (1-based, skipped steps included)
+// accumulates in buffer t & 1 of grad2
 // (two buffers of MLP_NPARAM floats).  Every CTA checks the whole buffer for
 // non-finite values, so all CTAs agree on skipping the step without a
 // grid-wide barrier, updates its slice of the parameters and zeroes its slice
@@ -47,13 +51,14 @@ __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ par
                                                          float* __restrict__ ema, uint16_t* __restrict__ w16s,
                                                          float ema_a) {
     __shared__ float s_scale;
-    __shared__ uint32_t s_acc;
+    __shared__ uint32_t s_acc, s_t;
     __shared__ int s_last;
     const float* __restrict__ g = grad2 + (size_t)(step & 1u) * MLP_NPARAM;
     float* __restrict__ gz = grad2 + (size_t)((step + 1u) & 1u) * MLP_NPARAM;
     if (threadIdx.x == 0) {
         s_scale = st->loss_scale;
         s_acc = st->acc;
+        s_t = st->adam_t + 1u;   // this step's index in Adam's bias correction
     }
     int bad = 0;
     for (int i = threadIdx.x; i < MLP_NPARAM / 4; i += blockDim.x) {
@@ -71,8 +76,8 @@ __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ par
             const float vv = b2 * vel[i] + (1.f - b2) * gr * gr;
             mom[i] = mm;
             vel[i] = vv;
-            const float mh = mm / (1.f - powf(b1, (float)step));
-            const float vh = vv / (1.f - powf(b2, (float)step));
+            const float mh = mm / (1.f - powf(b1, (float)s_t));
+            const float vh = vv / (1.f - powf(b2, (float)s_t));
             p = p - lr * mh / (sqrtf(vh) + eps);
             params[i] = p;
             if (i < MLP_NW) w16[i] = bf16 ? H16<true>::bits(p) : H16<false>::bits(p);
@@ -96,6 +101,7 @@ __global__ void __launch_bounds__(kOptThreads) k_mlp_opt(float* __restrict__ par
         st->overflow = overflow ? 1u : 0u;
         st->count = s_acc;
         st->acc = 0;
+        if (!overflow) st->adam_t = s_t;
         if (overflow) {
             st->loss_scale = fmaxf(s_scale * 0.5f, 1.f / 1024.f);
             st->good = 0;

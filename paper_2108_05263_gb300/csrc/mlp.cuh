@@ -38,6 +38,7 @@ struct MLPState {
     uint32_t use_mlp;      // 1: the network serves queries this frame
     uint32_t acc;          // training samples of the step in progress
     uint32_t done;         // optimiser CTAs finished (the last one resets it)
+    uint32_t adam_t;       // Adam steps applied (a skipped step does not count)
 };
 
 struct MLPView {

@@ -148,6 +148,43 @@ def test_adam_step_matches_oracle(dd, M):
     np.testing.assert_array_equal(p1[17408 + 3 * 64:17920], 0.0)   # padded output rows stay 0
 
 
+def test_overflowing_step_is_skipped(dd, M):
+    """Dynamic loss scaling: a step whose gradient overflows (one sample's
+    target 1e38) leaves the parameters as they were, halves the loss scale
+    and reports the overflow; the next, clean step is Adam's first (the
+    skipped step does not count in the bias correction) and starts from clean
+    gradient buffers, so it equals the oracle's first step."""
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    p0 = ctx.mlp_params()
+    s = _samples(sc, 4096, 6)
+    bad = s.copy()
+    k = int(np.flatnonzero(s[:, 11] > 0)[0])
+    bad[k, 8:11] = 1e38
+    scale0 = ctx.mlp_status()["loss_scale"]
+    ctx.mlp_step(bad)
+    st = ctx.mlp_status()
+    assert st["overflow"] == 1 and st["loss_scale"] == max(scale0 * 0.5, 1.0 / 1024.0)
+    np.testing.assert_array_equal(ctx.mlp_params(), p0)
+    ctx.mlp_step(s)
+    st = ctx.mlp_status()
+    assert st["overflow"] == 0 and st["step"] == 2
+    p1 = ctx.mlp_params()
+    assert np.isfinite(p1).all()
+    params16 = _to_oracle(p0, M)
+    lo, scale = M.scene_box(sc.verts)
+    x = M.encode(s[:, 0:3].astype(np.float64), s[:, 4:7].astype(np.float64), lo, scale)
+    out, cache = M.forward(params16, x)
+    _, dout = M.rel_l2(out, s[:, 8:11].astype(np.float64), s[:, 11] > 0)
+    grads = M.backward(params16, cache, dout)
+    master = _to_oracle(p0, M, round16=False)
+    ref = _flat(M.Adam(master).step(master, grads))
+    d_gpu, d_ref = p1 - p0, ref - p0
+    live = np.abs(_flat(grads)) > 0
+    assert _close_frac(d_gpu[live], d_ref[live], 0.0, 1e-4) >= 0.95
+    assert np.abs(d_gpu - d_ref).max() <= 2.1e-3
+
+
 def test_training_samples_match_oracle(dd, M):
     import oracle
     sc = scenegen.tiny_room()
