@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128) k_train_primary(SceneView s, VolumeView v
     if (i == 0) {   // the frame's counters (nothing reads them before the training kernels)
         st->count = 0;
         st->acc = 0;
+        st->done = 0;
         st->judge_mlp = 0.0;
         st->judge_probe = 0.0;
         st->judge_n = 0;
@@ -268,6 +269,7 @@ struct JudgeQuery {
 __global__ void k_mlp_begin(MLPState* st) {
     st->count = 0;
     st->acc = 0;
+    st->done = 0;
     st->judge_mlp = 0.0;
     st->judge_probe = 0.0;
     st->judge_n = 0;
