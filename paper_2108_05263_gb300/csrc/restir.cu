@@ -424,11 +424,15 @@ __device__ __forceinline__ int spatial_neighbour(const RestirParams& rp, const G
 // rides in the record, so nothing else is gathered), and the next neighbour's
 // pixel is drawn while they are in flight.  At most 56 registers keep nine
 // CTAs per SM.
+// UP: rows bottom-up (odd passes), so that each pass starts on the rows the
+// pass before it wrote last, still in L2; a compile-time direction keeps the
+// register count.
+template <bool UP>
 __global__ void __launch_bounds__(128, 9) k_restir_spatial(SceneView s, RestirParams rp, GBufView g,
                                                            ResView in, ResView out, uint32_t frame,
                                                            uint32_t pass) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
-    int py = blockIdx.y * blockDim.y + threadIdx.y;
+    int py = (UP ? gridDim.y - 1 - blockIdx.y : blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
     Rec c = load_rec(in.rec + 4 * (size_t)pix);
@@ -589,7 +593,10 @@ cudaError_t launch_restir_spatial(const SceneView& s, const RestirParams& rp, co
                                   uint32_t pass, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     dim3 b(16, 8);
-    k_restir_spatial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, in, out, frame, pass);
+    if (pass & 1u)
+        k_restir_spatial<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, in, out, frame, pass);
+    else
+        k_restir_spatial<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, rp, g, in, out, frame, pass);
     return cudaGetLastError();
 }
 
