@@ -343,7 +343,7 @@ ddgi_status ddgi_image_metrics_static(const float* img, const float* ref, uint32
  * weights (train_ema).  Samples 16 j + 15 are held out and judge the served
  * network against the probe lookup (squared error relative to the mean of
  * the two predictions squared plus 0.01, so that the target's noise weighs
- * both equally); the verdict decides for the following resampling / shading
+ * both equally); the decision holds for the following resampling / shading
  * calls whether the network or the probes serve the queries.  Requires
  * train_samples > 0. */
 ddgi_status ddgi_mlp_train(ddgi_ctx* ctx, uint32_t frame, void* stream);
