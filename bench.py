@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-equal-time", action="store_true",
                     help="skip the equal-time MSE comparison of the learned and probe forms")
     ap.add_argument("--equal-time-frames", type=int, default=256)
+    ap.add_argument("--no-two-pass-side", action="store_true",
+                    help="skip the two-pass frames timed after the fused ones (their per-pass rooflines)")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="run restir_initial and restir_temporal as two passes (default: the fused "
+                         "restir_initial_temporal, the same computation)")
     ap.add_argument("--workload", default="apartment", choices=["apartment", "large", "learned"],
                     help="apartment: the 1080p metric workload; large: the 4K multi-storey building "
                          "with 500 moving boxes and the bf16 learned target; learned: the 24-triangle "
@@ -163,17 +168,18 @@ def ncu_traffic(kernel: str):
 BYTES_PER_PX = {
     "restir_initial": 48 + 64 + 16,             # G in; record + residual out
     "restir_temporal": 64 + 32 + 64 + 64,       # cur record, G (pos, albedo+prev), prev record; out
+    "restir_initial_temporal": 48 + 64 + 64 + 16,   # G, previous record in; record + residual out
     "restir_spatial": 64 + 32 + 64,             # own record, G (pos, albedo); out
     "ddgi_shade": 48 + 64 + 16 + 16,            # G, record, residual; radiance out
 }
 
 
-def launches_per_frame(spatial_passes: int) -> int:
+def launches_per_frame(spatial_passes: int, fused: bool = False) -> int:
     """Kernels of one timed frame: probe trace + blend, BSDF-ray traversal +
-    emitter candidates + BSDF candidates, temporal, one per spatial pass,
-    shadow-ray traversal + shade (the launch lists in profiles/ show the same
-    count)."""
-    return 2 + 3 + 1 + spatial_passes + 2
+    emitter candidates + BSDF candidates, temporal (inside the BSDF-candidate
+    kernel when fused), one per spatial pass, shadow-ray traversal + shade
+    (the launch lists in profiles/ show the same count)."""
+    return 2 + 3 + (0 if fused else 1) + spatial_passes + 2
 
 
 def job_time_ms(local_ms: float, ws: int, device) -> float:
@@ -232,10 +238,16 @@ def run_ours(args, ws, rank, local):
     gb_ms = ev0.elapsed_time(ev1) / 4
 
     fr = ddgi.Frame(ctx, W, H, st.spatial_passes, dev)
-    passes = ["probe_update", "restir_initial", "restir_temporal"] + \
-             [f"restir_spatial{i}" for i in range(st.spatial_passes)] + ["ddgi_shade"]
+    fused = not args.two_pass
 
-    def step(k, evs=None):
+    def pass_names(fz):
+        return (["probe_update", "restir_initial_temporal"] if fz else
+                ["probe_update", "restir_initial", "restir_temporal"]) + \
+               [f"restir_spatial{i}" for i in range(st.spatial_passes)] + ["ddgi_shade"]
+
+    passes = pass_names(fused)
+
+    def step(k, evs=None, fz=fused):
         f = k
         cam = sc.cameras[f % args.frames]
         g = gbufs[f % args.frames]
@@ -250,12 +262,17 @@ def run_ours(args, ws, rank, local):
         ctx.probe_update(f, stream)
         mark()
         init, tmp = fr._free_pair()
-        ctx.restir_initial(g, init, fr.resid, f, stream)
-        mark()
-        res = init
-        if fr.prev_final is not None:
-            ctx.restir_temporal(g, fr.prev_cam.pos, init, fr.prev_final, tmp, f, stream)
+        if fz and fr.prev_final is not None:
+            ctx.restir_initial_temporal(g, fr.prev_cam.pos, init, fr.prev_final, tmp, fr.resid, f, stream)
             res = tmp
+        else:
+            ctx.restir_initial(g, init, fr.resid, f, stream)
+            if not fz:
+                mark()
+            res = init
+            if fr.prev_final is not None:
+                ctx.restir_temporal(g, fr.prev_cam.pos, init, fr.prev_final, tmp, f, stream)
+                res = tmp
         mark()
         for i in range(st.spatial_passes):
             nxt = fr._other(res)
@@ -290,6 +307,19 @@ def run_ours(args, ws, rank, local):
     for k in range(K):
         for i, p in enumerate(passes):
             per_pass[p] += evs[k][i].elapsed_time(evs[k][i + 1]) / K
+    # the two-pass form of the same frames (separate initial and temporal
+    # passes), untimed for the metric: the per-pass rooflines of both passes
+    two_pass = None
+    if fused and not args.no_two_pass_side:
+        K2 = min(K, 100)
+        names2 = pass_names(False)
+        evs2 = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names2) + 1)] for _ in range(K2)]
+        for k in range(K2):
+            step(args.warmup + K + k, evs2[k], fz=False)
+        torch.cuda.synchronize()
+        pp2 = {p: sum(evs2[k][i].elapsed_time(evs2[k][i + 1]) for k in range(K2)) / K2
+               for i, p in enumerate(names2)}
+        two_pass = {"frames": K2, "ms_per_frame": round(sum(pp2.values()), 4), "passes": pp2}
     status = ctx.get_status(stream)
 
     hbm, peak_kind = peaks()
@@ -302,6 +332,16 @@ def run_ours(args, ws, rank, local):
             entry.update({"bytes": BYTES_PER_PX[key] * N, "gbs": round(gbs, 1),
                           "hbm_frac": round(gbs / hbm, 4)})
         pass_report[p] = entry
+    if two_pass is not None:
+        rep2 = {}
+        for p, ms in two_pass["passes"].items():
+            key = "restir_spatial" if p.startswith("restir_spatial") else p
+            entry = {"ms": round(ms, 4)}
+            if key in BYTES_PER_PX:
+                gbs = BYTES_PER_PX[key] * N / (ms * 1e-3) / 1e9
+                entry.update({"gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)})
+            rep2[p] = entry
+        two_pass["passes"] = rep2
     # roofline of the dominant kernel
     dom = max(per_pass, key=per_pass.get)
     dom_key = "restir_spatial" if dom.startswith("restir_spatial") else dom
@@ -309,6 +349,8 @@ def run_ours(args, ws, rank, local):
         achieved = BYTES_PER_PX[dom_key] * N / (per_pass[dom] * 1e-3) / 1e9
         # a pass and the kernels it launches; traffic = their DRAM bytes per pass
         kernels = {"restir_initial": "k_trace<BsdfGen> + k_restir_emitters_smem + k_restir_initial",
+                   "restir_initial_temporal": "k_trace<BsdfGen> + k_restir_emitters_smem + "
+                                              "k_restir_initial<fused temporal>",
                    "restir_temporal": "k_restir_temporal", "restir_spatial": "k_restir_spatial",
                    "ddgi_shade": "k_trace<ShadowGen> + k_shade"}[dom_key]
         roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "hbm", "achieved": round(achieved, 1),
@@ -332,7 +374,9 @@ def run_ours(args, ws, rank, local):
                       "parallelism": "replicas" if ws > 1 else "single GPU",
                       "gbuffer_ms_untimed": round(gb_ms, 4)},
            "passes": pass_report, "roofline": roof, "clocks": clocks,
-           "gpu_launches": K * launches_per_frame(st.spatial_passes), "device_status": int(status)}
+           "gpu_launches": K * launches_per_frame(st.spatial_passes, fused), "device_status": int(status)}
+    if two_pass is not None:
+        out["two_pass"] = two_pass
 
     # end to end through the public API: host G-buffer in, radiance out
     if not args.no_e2e:
@@ -341,7 +385,7 @@ def run_ours(args, ws, rank, local):
         # download of frame k overlap frame k's passes (HostFramePipeline)
         host = [[t.cpu().pin_memory() for t in (g.g0, g.g1, g.g2)] for g in gbufs]
         out_host = [torch.empty((N, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
-        pipe = ddgi.HostFramePipeline(ctx, W, H, st.spatial_passes, dev)
+        pipe = ddgi.HostFramePipeline(ctx, W, H, st.spatial_passes, dev, fused=fused)
         pipe.upload(host[0])
         for k in range(3):
             pipe.upload(host[(k + 1) % args.frames])

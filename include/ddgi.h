@@ -263,6 +263,22 @@ ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g,
                             const ddgi_reservoirs* prev, const ddgi_reservoirs* out,
                             uint32_t frame, void* stream);
 
+/* restir_initial followed by restir_temporal in one pass over the pixels
+ * (Sec. 3.1 step 2 fused into step 1): each pixel's initial reservoir is
+ * merged with its previous-frame pixel's reservoir before it is stored, so
+ * only the merged reservoir reaches memory.  out and residual are those of
+ * restir_initial into some buffer c followed by restir_temporal(c, prev)
+ * into out: the same arithmetic, up to a few ulp where the compiler fuses a
+ * multiply and an add differently in the one kernel (a selection can
+ * differ where two weights tie that closely).  scratch (N records) receives the
+ * emitter candidates' partial state and holds no reservoirs afterwards.
+ * out, scratch and prev must be distinct; prev may hold a different number
+ * of pixels; prev_cam_pos: host float[3]. */
+ddgi_status restir_initial_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g, const float* prev_cam_pos,
+                                    const ddgi_reservoirs* scratch, const ddgi_reservoirs* prev,
+                                    const ddgi_reservoirs* out, float* residual, uint32_t frame,
+                                    void* stream);
+
 /* Sec. 3.1 step 2 (spatial): merge with spatial_neighbours reservoirs drawn in
  * a disk of spatial_radius pixels, with the same rejection and cached
  * radiance.  `pass` (0-based) keys the random numbers.  out must not alias

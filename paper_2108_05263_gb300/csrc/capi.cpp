@@ -1054,15 +1054,10 @@ ddgi_status ddgi_gbuffer(ddgi_ctx* ctx, const ddgi_camera* cam, const ddgi_camer
     return DDGI_OK;
 }
 
-ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* out,
-                           float* residual, uint32_t frame, void* stream) {
-    if (!ctx) return DDGI_ERR_INVALID_ARG;
-    GBufView g;
-    ResView r;
-    ddgi_status s = check_gbuf(ctx, gb, &g);
-    if (s != DDGI_OK) return s;
-    uint64_t n = (uint64_t)g.width * g.height;
-    if ((s = check_res(ctx, out, n, &r)) != DDGI_OK) return s;
+// restir_initial, and with fin / prev set the fused initial + temporal pass
+static ddgi_status initial_impl(ddgi_ctx* ctx, const GBufView& g, const ResView& r, float* residual, uint32_t frame,
+                                void* stream, const ResView* prev, const ResView* fin, float3 cam_prev) {
+    const uint64_t n = (uint64_t)g.width * g.height;
     if (n > 0 && (!residual || !aligned(residual, 16)))
         return fail(ctx, DDGI_ERR_INVALID_ARG, "residual NULL or misaligned");
     CK(ensure_hits(ctx, (size_t)n * ctx->cfg.num_bsdf_candidates, (cudaStream_t)stream));
@@ -1077,8 +1072,39 @@ ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reserv
     CK(launch_restir_initial(scene_view(ctx), volume_view(ctx), restir_params(ctx), g, r,
                              reinterpret_cast<float4*>(residual), frame, ctx->hits, ctx->counter,
                              ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind,
-                             (cudaStream_t)stream, ctx->side, ctx->ev_fork, ctx->ev_join));
+                             (cudaStream_t)stream, ctx->side, ctx->ev_fork, ctx->ev_join, prev, fin, cam_prev));
     return DDGI_OK;
+}
+
+ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* out,
+                           float* residual, uint32_t frame, void* stream) {
+    if (!ctx) return DDGI_ERR_INVALID_ARG;
+    GBufView g;
+    ResView r;
+    ddgi_status s = check_gbuf(ctx, gb, &g);
+    if (s != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height;
+    if ((s = check_res(ctx, out, n, &r)) != DDGI_OK) return s;
+    return initial_impl(ctx, g, r, residual, frame, stream, nullptr, nullptr, make_float3(0.f, 0.f, 0.f));
+}
+
+ddgi_status restir_initial_temporal(ddgi_ctx* ctx, const ddgi_gbuf* gb, const float* prev_cam_pos,
+                                    const ddgi_reservoirs* scratch, const ddgi_reservoirs* prev,
+                                    const ddgi_reservoirs* out, float* residual, uint32_t frame, void* stream) {
+    if (!ctx || !prev_cam_pos) return fail(ctx, DDGI_ERR_INVALID_ARG, "NULL argument");
+    GBufView g;
+    ResView rs, rpv, ro;
+    ddgi_status s;
+    if ((s = check_gbuf(ctx, gb, &g)) != DDGI_OK) return s;
+    uint64_t n = (uint64_t)g.width * g.height;
+    if ((s = check_res(ctx, scratch, n, &rs)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, prev, UINT64_MAX, &rpv)) != DDGI_OK) return s;
+    if ((s = check_res(ctx, out, n, &ro)) != DDGI_OK) return s;
+    if (n > 0 && (ro.rec == rs.rec || ro.rec == rpv.rec || rs.rec == rpv.rec))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "reservoir buffers alias");
+    if (!finite3(prev_cam_pos)) return fail(ctx, DDGI_ERR_INVALID_ARG, "camera position not finite");
+    return initial_impl(ctx, g, rs, residual, frame, stream, &rpv, &ro,
+                        make_float3(prev_cam_pos[0], prev_cam_pos[1], prev_cam_pos[2]));
 }
 
 ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* gb, const float* prev_cam_pos,

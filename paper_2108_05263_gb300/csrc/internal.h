@@ -73,7 +73,8 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, float2* hits, uint32_t* counter, const struct MLPView* mlp,
                                   struct MLPState* mst, float4* ind, cudaStream_t st, cudaStream_t side,
-                                  cudaEvent_t ev_fork, cudaEvent_t ev_join);
+                                  cudaEvent_t ev_fork, cudaEvent_t ev_join, const ResView* fuse_prev = nullptr,
+                                  const ResView* fuse_out = nullptr, float3 cam_prev = float3{0.f, 0.f, 0.f});
 cudaError_t launch_restir_temporal(const SceneView& s, const RestirParams& rp, const GBufView& g,
                                    float3 prev_cam, const ResView& cur,
                                    const ResView& prev, const ResView& out, uint32_t frame,

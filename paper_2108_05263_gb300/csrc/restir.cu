@@ -236,12 +236,78 @@ __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, Volum
 // stream k_restir_emitters left in the record (when there are emitter
 // candidates) with the cosine-distributed rays traced before this kernel;
 // their residual transport (Sec. 3.5) on the side.
+// Temporal reuse of pixel pix (Sec. 3.1 step 2, Sec. 3.6): merge its current
+// record c with the previous frame's record at the reprojected pixel (cached
+// radiance, normal and depth rejection, M capped relative to the current M)
+// and store the result at o.
+__device__ __forceinline__ void temporal_merge(const SceneView& s, const RestirParams& rp, const GBufView& g,
+                                               float3 cam_prev, const ResView& prev, uint32_t frame, uint32_t pix,
+                                               const Rec& c, float4 g2, float4* o) {
+    int pq = __float_as_int(g2.w);
+    const bool moving = pq >= 0 && (pq & DDGI_PREV_MOVING);
+    pq &= ~DDGI_PREV_MOVING;
+    // the owner validity of the current record is this pixel's G-buffer validity
+    bool merge = rec_owner_valid(c) && pq >= 0 && (uint32_t)pq < prev.n;
+    Rec p;
+    float4 g0;
+    if (merge) {
+        p = load_rec(prev.rec + 4 * (size_t)pq);
+        g0 = g.g0[pix];
+        merge = rec_owner_valid(p) && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
+        if (merge) {
+            // a surface on a moving instance is compared at its previous position
+            f3 xp = xyz(g0);
+            if (moving) {
+                bool mv;
+                xp = prev_position(s, __float_as_uint(__ldg(&g.g1[pix].w)), xp, &mv);
+            }
+            float de = length(xp - f3{cam_prev.x, cam_prev.y, cam_prev.z});
+            merge = fabsf(de - p.q2.w) <= rp.depth_reject_frac * de;
+        }
+    }
+    if (!merge) {
+        store_rec(o, c.q0, c.q1, c.q2, c.q3);
+        return;
+    }
+    const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
+    float Mc = c.q1.w;
+    // the cap is relative to the current M, or to the nominal candidate count
+    // for a pixel that generated none (subsampling)
+    const float Mref = Mc > 0.f ? Mc : (float)((s.num_emitters > 0 ? rp.n_light : 0u) + rp.n_bsdf);
+    float Mp = fminf(p.q1.w, rp.temporal_mcap * Mref);
+    float pc = rec_target(x, nx, rho, c.q0, c.q1, c.q3);
+    float wsum = pc * c.q0.w * Mc;
+    float pp = rec_target(x, nx, rho, p.q0, p.q1, p.q3);
+    float wp = pp * p.q0.w * Mp;
+    wsum += wp;
+    uint32_t h = rng_u32_dim(rng_cand(rng_prefix(rp.seed, pix, frame, PASS_TEMPORAL), 0u), 0u);
+    float u = u01(h);
+    float4 q0 = c.q0, q1 = c.q1, q3 = c.q3;
+    float psel = pc;
+    if (wp > 0.f && u * wsum < wp) {
+        q0 = p.q0;
+        q1 = p.q1;
+        q3 = p.q3;
+        psel = pp;
+    }
+    float Mo = Mc + Mp;
+    q0.w = psel > 0.f ? wsum / (Mo * psel) : 0.f;
+    q1.w = Mo;
+    store_rec(o, q0, q1, c.q2, q3);
+}
+
+// FUSE: the pixel's initial record goes straight into temporal reuse with
+// the previous frame's records (prev) and only the merged record is stored
+// (in fin); the arithmetic is that of the two separate passes, up to the
+// compiler's multiply-add contraction in each kernel (a few ulp).
+template <bool FUSE>
 __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
                                                         float4* __restrict__ resid, uint32_t frame,
                                                         const float2* __restrict__ bsdf_hits,
                                                         const float4* __restrict__ ind,
-                                                        const MLPState* __restrict__ mst, uint32_t nl) {
+                                                        const MLPState* __restrict__ mst, uint32_t nl,
+                                                        float3 cam_prev, ResView prev, ResView fin) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = blockIdx.y * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
@@ -252,17 +318,29 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     const uint32_t NB = rp.n_bsdf;
     const uint32_t M = NL + NB;
     float4* rec = out.rec + 4 * (size_t)pix;
-    if (xtri == DDGI_NONE) {
-        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                  make_float4(0.f, 0.f, 0.f, 0.f), rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
+    const auto emit = [&](float4 q0, float4 q1, float4 q2, float4 q3, float4 g2v) {
+        if (FUSE) {
+            Rec c;
+            c.q0 = q0;
+            c.q1 = q1;
+            c.q2 = q2;
+            c.q3 = q3;
+            temporal_merge(s, rp, g, cam_prev, prev, frame, pix, c, g2v, fin.rec + 4 * (size_t)pix);
+        } else {
+            store_rec(rec, q0, q1, q2, q3);
+        }
+    };
+    if (xtri == DDGI_NONE) {   // no owner: temporal reuse keeps the empty record
+        emit(make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+             rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)), make_float4(0.f, 0.f, 0.f, __int_as_float(-1)));
         resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     float4 g0 = g.g0[pix], g2 = g.g2[pix];
     const float4 geo = make_float4(g1.x, g1.y, g1.z, g0.w);
     if (!generates(rp, g.width, pix, frame)) {   // subsampling: an empty reservoir that only reuses
-        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), geo,
-                  rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
+        emit(make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), geo,
+             rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)), g2);
         resid[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
@@ -321,13 +399,13 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
     const Sel& sel = cs.sel;
     if (sel.tri == DDGI_NONE) {
-        store_rec(rec, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
-                  rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)));
+        emit(make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
+             rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)), g2);
         return;
     }
     float W = sel.p > 0.f ? cs.wsum / ((float)M * sel.p) : 0.f;
-    store_rec(rec, make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
-              rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))));
+    emit(make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
+         rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))), g2);
 }
 
 __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirParams rp, GBufView g,
@@ -339,60 +417,8 @@ __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirPara
     int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
     uint32_t pix = (uint32_t)py * g.width + px;
-    Rec c = load_rec(cur.rec + 4 * (size_t)pix);
-    float4* o = out.rec + 4 * (size_t)pix;
-    float4 g2 = g.g2[pix];
-    int pq = __float_as_int(g2.w);
-    const bool moving = pq >= 0 && (pq & DDGI_PREV_MOVING);
-    pq &= ~DDGI_PREV_MOVING;
-    // the owner validity of the current record is this pixel's G-buffer validity
-    bool merge = rec_owner_valid(c) && pq >= 0 && (uint32_t)pq < prev.n;
-    Rec p;
-    float4 g0;
-    if (merge) {
-        p = load_rec(prev.rec + 4 * (size_t)pq);
-        g0 = g.g0[pix];
-        merge = rec_owner_valid(p) && dot(xyz(c.q2), xyz(p.q2)) > rp.normal_reject_cos;
-        if (merge) {
-            // a surface on a moving instance is compared at its previous position
-            f3 xp = xyz(g0);
-            if (moving) {
-                bool mv;
-                xp = prev_position(s, __float_as_uint(__ldg(&g.g1[pix].w)), xp, &mv);
-            }
-            float de = length(xp - f3{cam_prev.x, cam_prev.y, cam_prev.z});
-            merge = fabsf(de - p.q2.w) <= rp.depth_reject_frac * de;
-        }
-    }
-    if (!merge) {
-        copy_rec(o, c);
-        return;
-    }
-    const f3 x = xyz(g0), nx = xyz(c.q2), rho = xyz(g2);
-    float Mc = c.q1.w;
-    // the cap is relative to the current M, or to the nominal candidate count
-    // for a pixel that generated none (subsampling)
-    const float Mref = Mc > 0.f ? Mc : (float)((s.num_emitters > 0 ? rp.n_light : 0u) + rp.n_bsdf);
-    float Mp = fminf(p.q1.w, rp.temporal_mcap * Mref);
-    float pc = rec_target(x, nx, rho, c.q0, c.q1, c.q3);
-    float wsum = pc * c.q0.w * Mc;
-    float pp = rec_target(x, nx, rho, p.q0, p.q1, p.q3);
-    float wp = pp * p.q0.w * Mp;
-    wsum += wp;
-    uint32_t h = rng_u32_dim(rng_cand(rng_prefix(rp.seed, pix, frame, PASS_TEMPORAL), 0u), 0u);
-    float u = u01(h);
-    float4 q0 = c.q0, q1 = c.q1, q3 = c.q3;
-    float psel = pc;
-    if (wp > 0.f && u * wsum < wp) {
-        q0 = p.q0;
-        q1 = p.q1;
-        q3 = p.q3;
-        psel = pp;
-    }
-    float Mo = Mc + Mp;
-    q0.w = psel > 0.f ? wsum / (Mo * psel) : 0.f;
-    q1.w = Mo;
-    store_rec(o, q0, q1, c.q2, q3);
+    const Rec c = load_rec(cur.rec + 4 * (size_t)pix);
+    temporal_merge(s, rp, g, cam_prev, prev, frame, pix, c, g.g2[pix], out.rec + 4 * (size_t)pix);
 }
 
 // x mod span for x < 2^16 via a multiply-high reciprocal (exact in that range)
@@ -540,7 +566,8 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
                                   const GBufView& g, const ResView& out, float4* resid,
                                   uint32_t frame, float2* hits, uint32_t* counter, const MLPView* mlp,
                                   MLPState* mst, float4* ind, cudaStream_t st, cudaStream_t side,
-                                  cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+                                  cudaEvent_t ev_fork, cudaEvent_t ev_join, const ResView* fuse_prev,
+                                  const ResView* fuse_out, float3 cam_prev) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     const uint32_t nl = s.num_emitters > 0 ? rp.n_light : 0u;
     BsdfGen gen{g, rp, frame, nl, rp.n_bsdf};
@@ -573,8 +600,12 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
         e = launch_emitter_candidates(s, v, rp, g, out, frame, st);
         if (e != cudaSuccess) return e;
     }
-    k_restir_initial<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind,
-                                                                     mlp ? mst : nullptr, nl);
+    if (fuse_prev && fuse_out)
+        k_restir_initial<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(
+            s, v, rp, g, out, resid, frame, hits, ind, mlp ? mst : nullptr, nl, cam_prev, *fuse_prev, *fuse_out);
+    else
+        k_restir_initial<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(
+            s, v, rp, g, out, resid, frame, hits, ind, mlp ? mst : nullptr, nl, cam_prev, out, out);
     return cudaGetLastError();
 }
 

@@ -81,7 +81,7 @@ EXPORTS = ["ddgi_create", "ddgi_destroy", "ddgi_get_info", "ddgi_probe_update", 
            "ddgi_probe_blend", "ddgi_probe_relocate", "ddgi_scene_update", "ddgi_state_save",
            "ddgi_state_load", "ddgi_probe_state_get", "ddgi_probe_state_set",
            "ddgi_probe_rays_get", "ddgi_probe_rays_set", "ddgi_gbuffer", "restir_initial",
-           "restir_temporal", "restir_spatial", "ddgi_reservoirs_attach_normals", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
+           "restir_temporal", "restir_initial_temporal", "restir_spatial", "ddgi_reservoirs_attach_normals", "ddgi_shade", "ddgi_reference_accumulate", "ddgi_image_metrics",
            "ddgi_image_metrics_static", "ddgi_mlp_train", "ddgi_mlp_infer", "ddgi_mlp_grad",
            "ddgi_mlp_step", "ddgi_mlp_params_get", "ddgi_mlp_params_served_get",
            "ddgi_mlp_params_set", "ddgi_mlp_serve", "ddgi_mlp_samples_get",
@@ -123,6 +123,8 @@ def load(path: Optional[str] = None):
                                   C.POINTER(Res), C.POINTER(Res), C.c_uint32, vp]
     L.restir_spatial.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), C.POINTER(Res), C.c_uint32,
                                  C.c_uint32, vp]
+    L.restir_initial_temporal.argtypes = [vp, C.POINTER(GBuf), C.POINTER(C.c_float), C.POINTER(Res),
+                                          C.POINTER(Res), C.POINTER(Res), vp, C.c_uint32, vp]
     L.ddgi_reservoirs_attach_normals.argtypes = [vp, C.POINTER(Res), vp]
     L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
     L.ddgi_reference_accumulate.argtypes = [vp, C.POINTER(Camera), C.c_uint32, C.c_uint32, vp, vp, vp]
@@ -393,6 +395,16 @@ class Context:
                     self.L.restir_temporal(self.h, C.byref(gc), cp, C.byref(cc), C.byref(pc),
                                            C.byref(oc), frame, _stream(stream)))
 
+    def restir_initial_temporal(self, g: GBuffer, prev_cam_pos, scratch: Reservoirs, prev: Reservoirs,
+                                out: Reservoirs, residual: torch.Tensor, frame, stream=None):
+        """restir_initial and restir_temporal in one pass; scratch holds no
+        reservoirs afterwards."""
+        gc, sc_, pc, oc = g.c(), scratch.c(), prev.c(), out.c()
+        cp = _f3(*map(float, prev_cam_pos))
+        self._check("restir_initial_temporal",
+                    self.L.restir_initial_temporal(self.h, C.byref(gc), cp, C.byref(sc_), C.byref(pc),
+                                                   C.byref(oc), _ptr(residual), frame, _stream(stream)))
+
     def restir_spatial(self, g: GBuffer, src: Reservoirs, out: Reservoirs, frame, pass_idx,
                        stream=None):
         gc, ic, oc = g.c(), src.c(), out.c()
@@ -493,12 +505,14 @@ class Frame:
         self.cur = 0
 
     def render(self, frame: int, cam, gbuf: Optional[GBuffer] = None, stream=None,
-               probe_update=True, xf=None, emitter_radiance=None, out: Optional[torch.Tensor] = None):
+               probe_update=True, xf=None, emitter_radiance=None, out: Optional[torch.Tensor] = None,
+               fused: bool = False):
         """One frame.  If ``gbuf`` is given it is used as this frame's
         G-buffer (the primary-visibility pass is skipped); xf /
         emitter_radiance (optional) first move the scene; ``out`` (optional,
         [n][4] float32 on the device) receives the radiance instead of the
-        frame's own buffer."""
+        frame's own buffer; ``fused`` runs the initial and temporal passes as
+        one (restir_initial_temporal; same results)."""
         ctx = self.ctx
         if xf is not None or emitter_radiance is not None:
             ctx.scene_update(xf, emitter_radiance, stream)
@@ -509,11 +523,16 @@ class Frame:
             g = self.g[self.cur]
             ctx.gbuffer(cam, self.prev_cam, g, stream)
         init, tmp = self._free_pair()
-        ctx.restir_initial(g, init, self.resid, frame, stream)
-        res = init
-        if self.prev_final is not None:
-            ctx.restir_temporal(g, self.prev_cam.pos, init, self.prev_final, tmp, frame, stream)
+        if fused and self.prev_final is not None:
+            ctx.restir_initial_temporal(g, self.prev_cam.pos, init, self.prev_final, tmp, self.resid, frame,
+                                        stream)
             res = tmp
+        else:
+            ctx.restir_initial(g, init, self.resid, frame, stream)
+            res = init
+            if self.prev_final is not None:
+                ctx.restir_temporal(g, self.prev_cam.pos, init, self.prev_final, tmp, frame, stream)
+                res = tmp
         for i in range(self.spatial_passes):
             nxt = self._other(res)
             ctx.restir_spatial(g, res, nxt, frame, i, stream)
@@ -543,8 +562,10 @@ class HostFramePipeline:
     frame runs on the caller's stream (double-buffered device G-buffers and
     radiance, ordered by events).  Host buffers should be pinned."""
 
-    def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda"):
+    def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda",
+                 fused: bool = False):
         n = width * height
+        self.fused = fused   # restir_initial_temporal instead of the two passes
         self.frame = Frame(ctx, width, height, spatial_passes, device)
         self.gbuf = [GBuffer(width, height, device), GBuffer(width, height, device)]
         self.rad = [torch.empty((n, 4), dtype=torch.float32, device=device) for _ in range(2)]
@@ -574,7 +595,8 @@ class HostFramePipeline:
         b = self.k % 2
         st.wait_event(self.ev_in[b])
         st.wait_event(self.ev_out[b])                           # the slot's radiance was read out
-        self.frame.render(frame, cam, gbuf=self.gbuf[b], stream=st, probe_update=True, out=self.rad[b])
+        self.frame.render(frame, cam, gbuf=self.gbuf[b], stream=st, probe_update=True, out=self.rad[b],
+                          fused=self.fused)
         self.ev_used[b].record(st)
         with torch.cuda.stream(self.down):
             self.down.wait_event(self.ev_used[b])

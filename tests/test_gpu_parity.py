@@ -284,7 +284,7 @@ def test_shade_parity(dd, orc, tiny):
 # whole frames on both sides
 # ---------------------------------------------------------------------------
 
-def _chain(dd, orc, sc, nframes):
+def _chain(dd, orc, sc, nframes, fused=False):
     R = orc.Renderer(sc)
     ctx = dd.Context.from_scene(sc)
     cam0 = sc.cameras[0]
@@ -294,7 +294,7 @@ def _chain(dd, orc, sc, nframes):
         cam = sc.cameras[f % len(sc.cameras)]
         xf, le = sc.instance_transforms(f), sc.emitter_radiance(f)
         ref = R.frame(f, cam, xf=xf, emitter_radiance=le)
-        rad = fr.render(f, cam, xf=xf, emitter_radiance=le).cpu().numpy()[:, :3]
+        rad = fr.render(f, cam, xf=xf, emitter_radiance=le, fused=fused).cpu().numpy()[:, :3]
         fl = dd.Reservoirs.fields(fr.prev_final.numpy())
         tag_ok = (fl["tri"] == ref["final"].tri) & (fl["tag"] == ref["final"].tag)
         close = _close(rad, ref["radiance"], 1e-5).all(1)
@@ -352,6 +352,68 @@ def test_whole_frame_chain_dynamic_box(dd, orc):
     stats = _chain(dd, orc, sc, 8)
     for f, (tags, rad) in enumerate(stats):
         assert tags >= 0.995 and rad >= 0.995, (f, stats)
+
+
+def _fused_vs_two_passes(dd, sc, nframes):
+    """Twin contexts render the same frames, one with restir_initial +
+    restir_temporal, the other with restir_initial_temporal: the same
+    arithmetic up to multiply-add contraction, so the final reservoirs select
+    the same samples (but for near-ties) and the radiance agrees to the
+    parity tolerance."""
+    cam0 = sc.cameras[0]
+    a, b = dd.Context.from_scene(sc), dd.Context.from_scene(sc)
+    fa = dd.Frame(a, cam0.width, cam0.height, sc.settings.spatial_passes)
+    fb = dd.Frame(b, cam0.width, cam0.height, sc.settings.spatial_passes)
+    for f in range(nframes):
+        cam = sc.cameras[f % len(sc.cameras)]
+        xf, le = sc.instance_transforms(f), sc.emitter_radiance(f)
+        ra = fa.render(f, cam, xf=xf, emitter_radiance=le).cpu().numpy()[:, :3].copy()
+        rb = fb.render(f, cam, xf=xf, emitter_radiance=le, fused=True).cpu().numpy()[:, :3].copy()
+        la, lb = dd.Reservoirs.fields(fa.prev_final.numpy()), dd.Reservoirs.fields(fb.prev_final.numpy())
+        same = (la["tri"] == lb["tri"]) & (la["tag"] == lb["tag"])
+        assert _frac(same) >= 0.999, (f, _frac(same))
+        assert _frac(_close(rb, ra, 1e-5).all(1)) >= 0.999, f
+    assert a.get_status() == dd.OK and b.get_status() == dd.OK
+
+
+def test_fused_initial_temporal_equals_two_passes(dd):
+    _fused_vs_two_passes(dd, scenegen.tiny_room(width=100, height=75, frames=4), 4)
+
+
+def test_fused_initial_temporal_equals_two_passes_moving_and_subsampled(dd):
+    """Moving boxes (reprojection at previous positions) and candidate
+    subsampling (pixels that only reuse, M capped against the nominal count)."""
+    import dataclasses
+    _fused_vs_two_passes(dd, scenegen.tiny_room_dynamic(width=64, height=48, frames=6), 6)
+    sc = scenegen.tiny_room(frames=4)
+    sc = dataclasses.replace(sc, settings=dataclasses.replace(sc.settings, candidate_stride=3))
+    _fused_vs_two_passes(dd, sc, 4)
+
+
+def test_whole_frame_chain_fused_initial_temporal(dd, orc):
+    """The frame chain with the fused initial + temporal pass against the
+    oracle's separate passes, on the moving-box scene."""
+    sc = scenegen.tiny_room_dynamic(width=64, height=48, frames=6)
+    stats = _chain(dd, orc, sc, 6, fused=True)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.995 and rad >= 0.995, (f, stats)
+
+
+def test_fused_initial_temporal_argument_errors(dd):
+    sc = scenegen.tiny_room(width=32, height=16, frames=1)
+    ctx = dd.Context.from_scene(sc)
+    g = dd.GBuffer(32, 16)
+    ctx.gbuffer(sc.cameras[0], None, g)
+    import torch
+    r = [dd.Reservoirs(32 * 16, rec=torch.zeros((32 * 16, 16), dtype=torch.float32, device="cuda"))
+         for _ in range(3)]
+    resid = torch.zeros((32 * 16, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(dd.DDGIError):
+        ctx.restir_initial_temporal(g, [0.0, 0.0, 0.0], r[0], r[1], r[1], resid, 0)
+    with pytest.raises(dd.DDGIError):
+        ctx.restir_initial_temporal(g, [0.0, 0.0, float("nan")], r[0], r[1], r[2], resid, 0)
+    ctx.restir_initial_temporal(g, [0.0, 0.0, 0.0], r[0], r[1], r[2], resid, 0)
+    assert ctx.get_status() == dd.OK
 
 
 def test_identity_update_keeps_the_bvh_exact(dd):
