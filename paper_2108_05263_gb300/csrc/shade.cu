@@ -190,7 +190,7 @@ cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView
         e = launch_mlp_infer(*mlp, ShadeQuery{s, g, r, hits, ind}, (uint32_t)g.width * g.height, st);
         if (e != cudaSuccess) return e;
     }
-    dim3 b(16, 8);
+    dim3 b(32, 4);   // measured best for this kernel (16 x 8 slower)
     k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
                                                            mlp ? mst : nullptr);
     return cudaGetLastError();
