@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
 
 // Persistent variant for emitter tables that fit in shared memory: each CTA
 // copies the records, cumulative areas and guide table once, then walks
-// 32 x 16 pixel tiles (bottom row of tiles first); the 32-byte record reads
+// 64 x 8 pixel tiles (bottom row of tiles first); the 32-byte record reads
 // of the candidates then come from shared memory instead of the L1 that the
 // per-pixel kernel saturates.
-constexpr int kEmitTileW = 32, kEmitTileH = 16;
+constexpr int kEmitTileW = 64, kEmitTileH = 8;   // measured best (32 x 16, 128 x 4, 16 x 32 slower)
 template <bool REFLECT>
 __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
                                                               ResView out, uint32_t frame) {
@@ -232,10 +232,6 @@ __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, Volum
     }
 }
 
-// Candidates of step 1, BSDF part, and the reservoir of step 2: continues the
-// stream k_restir_emitters left in the record (when there are emitter
-// candidates) with the cosine-distributed rays traced before this kernel;
-// their residual transport (Sec. 3.5) on the side.
 // Temporal reuse of pixel pix (Sec. 3.1 step 2, Sec. 3.6): merge its current
 // record c with the previous frame's record at the reprojected pixel (cached
 // radiance, normal and depth rejection, M capped relative to the current M)
@@ -296,6 +292,10 @@ __device__ __forceinline__ void temporal_merge(const SceneView& s, const RestirP
     store_rec(o, q0, q1, c.q2, q3);
 }
 
+// Candidates of step 1, BSDF part, and the reservoir of step 2: continues the
+// stream k_restir_emitters left in the record (when there are emitter
+// candidates) with the cosine-distributed rays traced before this kernel;
+// their residual transport (Sec. 3.5) on the side.
 // FUSE: the pixel's initial record goes straight into temporal reuse with
 // the previous frame's records (prev) and only the merged record is stored
 // (in fin); the arithmetic is that of the two separate passes, up to the
