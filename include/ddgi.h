@@ -111,6 +111,10 @@ typedef struct {
                                    * empty reservoir (M = 0, no residual) and only reuse;
                                    * temporal reuse then caps the previous M at
                                    * temporal_mcap x the nominal candidate count */
+    uint32_t traversal_visit_cap; /* BVH nodes one ray may visit before its traversal
+                                   * gives up (the ray then reports no hit and
+                                   * ddgi_get_status returns DDGI_ERR_TRAVERSAL_LIMIT);
+                                   * 0 = the default 65536 */
 } ddgi_config;
 
 /* Pinhole camera: orthonormal right/up/fwd, vertical half-angle tangent. */
@@ -317,7 +321,8 @@ ddgi_status ddgi_reference_accumulate(ddgi_ctx* ctx, const ddgi_camera* cam, uin
  * (rgb, ignored), 16-byte aligned; out: device double[2]; scratch: device
  * memory of at least scratch_doubles doubles for per-block partial sums
  * (2048 always suffice), 8-byte aligned, owned by the caller and overwritten.
- * Does not depend on a context. */
+ * n may be any uint32 value (the kernels index with 64 bits).  Does not
+ * depend on a context. */
 ddgi_status ddgi_image_metrics(const float* img, const float* ref, uint32_t n, double* scratch,
                                uint32_t scratch_doubles, double* out, void* stream);
 
@@ -331,7 +336,10 @@ ddgi_status ddgi_image_metrics(const float* img, const float* ref, uint32_t n, d
  *  - n must be <= 2^26 pixels; larger n returns DDGI_ERR_INVALID_ARG.
  *  - The first call on each device looks up that array's device address (with
  *    the device current) and caches it; make that first call before any
- *    stream capture.
+ *    stream capture.  The cached address belongs to the device's current
+ *    primary context: after cudaDeviceReset (or anything else that tears
+ *    that context down) the array may sit elsewhere, so do not call this
+ *    entry point again in that process.
  *  - All calls share the one array: calls that overlap on the GPU (different
  *    streams, or different host threads) race and may return wrong values;
  *    serialise them.  Each call writes every partial sum it reads, so what an
@@ -404,10 +412,15 @@ ddgi_status ddgi_mlp_status(ddgi_ctx* ctx, double* out, void* stream);
 
 /* Synchronise `stream`, return (and clear) the device error word:
  * DDGI_ERR_DEVICE_WAIT if a network kernel's wait for its tensor-core
- * results ran past its iteration bound (the kernel then skipped its
- * remaining work and released its tensor memory), DDGI_ERR_TRAVERSAL_LIMIT
- * if a ray exceeded the node-visit cap or the traversal stack, else
- * DDGI_OK. */
+ * results ran past its iteration bound (the kernel then waited once more,
+ * bounded, for the products it had issued, skipped its remaining work and
+ * released its tensor memory), DDGI_ERR_TRAVERSAL_LIMIT if a ray exceeded
+ * the node-visit cap (traversal_visit_cap) or the traversal stack, else
+ * DDGI_OK.  DDGI_ERR_DEVICE_WAIT is fatal for the context: the network
+ * state is undefined from then on, every later ddgi_get_status returns it
+ * again, and the context should be destroyed.  A traversal limit is not:
+ * the frame finished with "no hit" for the rays concerned, and the error
+ * word is clear again for the next frame. */
 ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream);
 const char* ddgi_last_error(ddgi_ctx* ctx);
 

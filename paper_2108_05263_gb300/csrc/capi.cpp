@@ -54,6 +54,7 @@ struct ddgi_ctx {
     uint32_t train_per = 0;
     uint32_t mlp_step = 0;
     int serve = 0;                 // 0 judge, 1 network, 2 probes
+    bool wait_failed = false;      // a tensor-core wait gave up: the context is unusable
     float mlp_lo[3] = {0.f, 0.f, 0.f};
     float mlp_scale = 1.f;
     float4* tmp_smp = nullptr;     // caller samples staged on the device
@@ -168,6 +169,7 @@ SceneView scene_view(ddgi_ctx* c) {
     s.tri_inst = c->I ? c->tri_inst : nullptr;
     s.num_tris = c->T;
     s.inst_delta = c->inst_delta;
+    s.max_visits = c->cfg.traversal_visit_cap ? (int)c->cfg.traversal_visit_cap : TRAV_MAX_VISITS;
     return s;
 }
 
@@ -256,6 +258,7 @@ ddgi_status check_config(const ddgi_config* c, std::string* why) {
     if (!(c->temporal_mcap >= 0.f) || !std::isfinite(c->temporal_mcap)) { *why = "temporal_mcap must be >= 0"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_neighbours > 32) { *why = "spatial_neighbours must be <= 32"; return DDGI_ERR_INVALID_ARG; }
     if (c->candidate_stride > 64) { *why = "candidate_stride must be <= 64"; return DDGI_ERR_INVALID_ARG; }
+    if (c->traversal_visit_cap > (1u << 30)) { *why = "traversal_visit_cap must be <= 2^30"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_radius < 1 || c->spatial_radius > 255) { *why = "spatial_radius must be 1..255"; return DDGI_ERR_INVALID_ARG; }
     if (!std::isfinite(c->normal_reject_cos) || !(c->depth_reject_frac >= 0.f)) { *why = "bad rejection thresholds"; return DDGI_ERR_INVALID_ARG; }
     const uint64_t P = (uint64_t)c->counts[0] * c->counts[1] * c->counts[2];
@@ -1310,7 +1313,9 @@ ddgi_status ddgi_get_status(ddgi_ctx* ctx, void* stream) {
     CK(cudaMemcpyAsync(w, ctx->err, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaMemsetAsync(ctx->err, 0, sizeof(w), st));
     CK(cudaStreamSynchronize(st));
-    if (w[0] & ERRBIT_MMA_WAIT) {
+    if ((w[0] & ERRBIT_MMA_WAIT) || ctx->wait_failed) {
+        // fatal: tensor memory may have been freed under a running product
+        ctx->wait_failed = true;
         ctx->last_error = "tensor-core completion wait ran past its bound";
         return DDGI_ERR_DEVICE_WAIT;
     }

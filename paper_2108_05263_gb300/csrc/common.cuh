@@ -17,6 +17,7 @@
 #define PASS_PROBE_ROT 7u
 
 // device error word bits
+#define TRAV_MAX_VISITS (1 << 16)   // default node-visit cap of one ray's traversal
 #define ERRBIT_TRAVERSAL 1u
 #define ERRBIT_STACK 2u
 #define ERRBIT_MMA_WAIT 4u   // a tensor-core completion wait ran past its bound
@@ -89,6 +90,7 @@ struct SceneView {
     const int* tri_inst;     // rigid instance of each original triangle (-1 static); null: static scene
     uint32_t num_tris;
     const float4* inst_delta;   // per instance: rows of M_prev M_cur^-1 (current -> previous pose)
+    int max_visits;             // BVH nodes one ray may visit (traversal_visit_cap)
 };
 
 // bit of the G-buffer's previous-pixel word marking a surface on a rigid

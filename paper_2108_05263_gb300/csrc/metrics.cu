@@ -19,7 +19,10 @@ __global__ void __launch_bounds__(kThreads) k_metric_partials(const float4* __re
                                                               const float4* __restrict__ ref,
                                                               uint32_t n, double* __restrict__ part) {
     double se = 0.0, ape = 0.0;
-    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    // 64-bit index: with a 32-bit one, i + stride wraps for n near 2^32 and
+    // the loop would never end
+    const size_t stride = (size_t)gridDim.x * kThreads;
+    for (size_t i = (size_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
         float4 a = img[i], b = ref[i];
         double d0 = (double)a.x - b.x, d1 = (double)a.y - b.y, d2 = (double)a.z - b.z;
         se += d0 * d0 + d1 * d1 + d2 * d2;

@@ -22,7 +22,9 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached.  The cache is never invalidated: a
+// device reset that reloads the module could move the array, which is why
+// the header rules out calls after a reset.
 cudaError_t scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -440,11 +440,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train_tc(MLPView m, const float4
                          : "memory");
         }
         const bool ok = mbar_wait(bar, phase);
-        phase ^= 1u;
         if (__syncthreads_or(!ok)) {
+            mbar_drain(bar, phase);
             failed = true;
             break;
         }
+        phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (l < 4) {
             uint8_t* xn = sm + TR_X_OFF(l + 1);
@@ -514,11 +515,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train_tc(MLPView m, const float4
         else if (l < 3)
             tc_grad_out<64>(l + 1, trow + 128u + 64u * (uint32_t)((l + 1) & 1), r, g, grad);
         const bool ok = mbar_wait(bar, phase);
-        phase ^= 1u;
         if (__syncthreads_or(!ok)) {
+            mbar_drain(bar, phase);
             failed = true;
             break;
         }
+        phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (l > 0) {
             // dZ_{l-1} = dX_l masked by the ReLU of X_l (its first 64 columns)

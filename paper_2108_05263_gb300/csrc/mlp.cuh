@@ -106,7 +106,8 @@ struct H16<true> {
 // fp32 accumulate) into the warpgroup's 64 tensor-memory columns and commits
 // to its mbarrier; the warpgroup's warps read their 32 rows back with
 // tcgen05.ld.  Every wait is bounded: past the bound the warpgroup sets
-// ERRBIT_MMA_WAIT and stops, and the CTA frees its tensor memory.
+// ERRBIT_MMA_WAIT, waits (bounded again) for the products it committed, and
+// stops; the CTA then frees its tensor memory.
 // ---------------------------------------------------------------------------
 #define MLP_TC_WG 6                       // warpgroups (tile streams) per CTA
 #define MLP_TC_THREADS (128 * MLP_TC_WG)
@@ -159,6 +160,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
     return done != 0;
+}
+
+// After a wait gave up: the products committed to `bar` may still be
+// writing tensor memory, so wait for that commit once more, with a bound 16x
+// the first, before the columns are freed.  Returns whether it arrived; if it
+// did not, the error bit the caller sets is fatal for the context.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+    for (int k = 0; k < 16; ++k)
+        if (mbar_wait(bar, parity)) return true;
+    return false;
 }
 
 // barrier of one warpgroup (ids 1..MLP_TC_WG; 0 is __syncthreads)
@@ -313,11 +324,12 @@ __global__ void __launch_bounds__(MLP_TC_THREADS, 1) k_mlp_infer(MLPView m, Q q,
                 }
             }
             const bool ok = mbar_wait(bar, phase);
-            phase ^= 1u;
             if (wg_or(g, !ok)) {
+                mbar_drain(bar, phase);
                 failed = true;
                 break;
             }
+            phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (l < 4) {
 #pragma unroll

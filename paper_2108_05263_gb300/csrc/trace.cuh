@@ -13,7 +13,6 @@
 #include "common.cuh"
 
 #define TRAV_STACK 64
-#define TRAV_MAX_VISITS (1 << 16)
 
 struct Ray {
     f3 o, d;
@@ -63,7 +62,7 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
     int visits = 0;
     const float widen = 1.0000004f;   // robust slab test (a few ulp of slack)
     while (true) {
-        if (++visits > TRAV_MAX_VISITS) {
+        if (++visits > s.max_visits) {
             atomicOr(s.err, ERRBIT_TRAVERSAL);
             h.tri = DDGI_NONE;
             h.t = ray.tmax;

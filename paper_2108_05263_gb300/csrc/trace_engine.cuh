@@ -56,7 +56,7 @@ __device__ __forceinline__ bool trav_step(const SceneView& s, const f3& o, const
         // every lane still descending takes part in the vote
         const bool all_hold = __all_sync(__activemask(), leaf != 0);
         if (leaf != 0 && all_hold) break;
-        if (++visits > TRAV_MAX_VISITS) {
+        if (++visits > s.max_visits) {
             atomicOr(s.err, ERRBIT_TRAVERSAL);
             best_tri = DDGI_NONE;
             best_t = tmax;

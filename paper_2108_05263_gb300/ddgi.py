@@ -24,6 +24,7 @@ ERR_NOT_READY = -3
 ERR_TRAVERSAL_LIMIT = -4
 ERR_BOUNDS = -5
 ERR_OOM = -6
+ERR_DEVICE_WAIT = -7
 
 _f3 = C.c_float * 3
 _i3 = C.c_int32 * 3
@@ -44,7 +45,8 @@ class Config(C.Structure):
                 ("depth_reject_frac", C.c_float), ("seed", C.c_uint32),
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
                 ("mlp_seed", C.c_uint32), ("train_ema", C.c_float), ("probe_relocation", C.c_uint32),
-                ("mlp_bf16", C.c_uint32), ("candidate_stride", C.c_uint32)]
+                ("mlp_bf16", C.c_uint32), ("candidate_stride", C.c_uint32),
+                ("traversal_visit_cap", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -258,6 +260,7 @@ def config_from(grid, settings) -> Config:
     c.probe_relocation = int(getattr(settings, "probe_relocation", 0))
     c.mlp_bf16 = int(getattr(settings, "mlp_bf16", 0))
     c.candidate_stride = int(getattr(settings, "candidate_stride", 1))
+    c.traversal_visit_cap = int(getattr(settings, "traversal_visit_cap", 0))
     return c
 
 
@@ -485,6 +488,9 @@ class Context:
 
     def get_status(self, stream=None) -> int:
         return self.L.ddgi_get_status(self.h, _stream(stream))
+
+    def last_error(self) -> str:
+        return self.L.ddgi_last_error(self.h).decode()
 
 
 class Frame:

@@ -71,3 +71,28 @@ def test_static_metrics_reject_oversized_images(lib):
     rc = lib.ddgi_image_metrics_static(C.c_void_p(img.data_ptr()), C.c_void_p(img.data_ptr()),
                                        (1 << 26) + 1, C.c_void_p(out.data_ptr()), None)
     assert rc == -1
+
+
+def test_static_metrics_of_an_empty_image_are_zero(lib):
+    """n = 0: the second kernel still runs and must write zeros (and not
+    whatever the shared array or the output held before)."""
+    import torch
+    out = torch.full((2,), 7.0, dtype=torch.float64, device="cuda")
+    img = torch.ones((4, 4), dtype=torch.float32, device="cuda")
+    got = _metrics_static(lib, img[:0], img[:0], out)
+    np.testing.assert_array_equal(got, [0.0, 0.0])
+
+
+def test_static_metrics_reject_a_misaligned_image(lib):
+    """Image rows are 16-byte records: a pointer 4 bytes into one is refused
+    on the host, before anything is launched, and the output is untouched."""
+    import torch
+    out = torch.full((2,), 7.0, dtype=torch.float64, device="cuda")
+    img, ref = _images(1024, 3)
+    rc = lib.ddgi_image_metrics_static(C.c_void_p(img.data_ptr() + 4), C.c_void_p(ref.data_ptr()),
+                                       1000, C.c_void_p(out.data_ptr()), None)
+    assert rc == -1
+    rc = lib.ddgi_image_metrics_static(C.c_void_p(img.data_ptr()), C.c_void_p(ref.data_ptr()),
+                                       1000, C.c_void_p(out.data_ptr() + 4), None)
+    assert rc == -1
+    np.testing.assert_array_equal(out.cpu().numpy(), [7.0, 7.0])
