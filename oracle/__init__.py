@@ -473,6 +473,15 @@ def ddgi_query(vol: Volume, q, n):
     return E, sw
 
 
+def biased_query(vol: Volume, y, n, frm):
+    """Irradiance E at y (normal n) with the view-path bias of Sec. 3.4: the
+    query point moves from y toward the previous path vertex ``frm``."""
+    E = np.zeros(3)
+    a = [np.ascontiguousarray(v, np.float64) for v in (y, n, frm)]
+    lib().or_biased_query(C.byref(vol.v), _p(a[0]), _p(a[1]), _p(a[2]), _p(E))
+    return E
+
+
 def probe_trace(scene: Scene, vol: Volume, frame: int, probes=None, settings=None):
     st = _settings(scene, settings)
     pr, pp = _pixarg(probes)
@@ -532,7 +541,10 @@ def restir_initial(scene: Scene, vol: Volume, g: GBuffer, frame: int, pix=None, 
 
 
 def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Reservoirs,
-                    prev: Reservoirs, frame: int, pix=None, settings=None):
+                    prev: Reservoirs, frame: int, pix=None, settings=None, requery: "Volume" = None):
+    """Temporal reuse (Sec. 3.1 step 2) with the radiance cached in the
+    reservoirs (Sec. 3.6), or, with ``requery`` (a test setting: caching off),
+    queried afresh from that volume at the current pixel."""
     _need_full(g, cur)
     _need_full(gp, prev)
     st = _settings(scene, settings)
@@ -541,23 +553,26 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
     out = Reservoirs(n)
     gc, gpc, cc, prc, oc = g.c(), gp.c(), cur.c(), prev.c(), out.c()
     cp = np.ascontiguousarray(prev_cam_pos, np.float64)
-    lib().or_restir_temporal(C.byref(scene.s), C.byref(st), C.byref(gc), C.byref(gpc), _p(cp),
-                             C.byref(cc), C.byref(prc), C.c_uint32(frame), pp, C.c_int32(n),
-                             C.byref(oc))
+    rq = C.byref(requery.v) if requery is not None else None
+    lib().or_restir_temporal_rq(C.byref(scene.s), C.byref(st), C.byref(gc), C.byref(gpc), _p(cp),
+                                C.byref(cc), C.byref(prc), C.c_uint32(frame), pp, C.c_int32(n), rq,
+                                C.byref(oc))
     return out
 
 
 def restir_spatial(scene: Scene, g: GBuffer, res_in: Reservoirs, frame: int, pass_idx: int,
-                   pix=None, settings=None):
+                   pix=None, settings=None, requery: "Volume" = None):
+    """Spatial reuse pass (Sec. 3.1 step 2); ``requery`` as in restir_temporal."""
     _need_full(g, res_in)
     st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     out = Reservoirs(n)
     gc, ic, oc = g.c(), res_in.c(), out.c()
-    lib().or_restir_spatial(C.byref(scene.s), C.byref(st), C.byref(gc), C.byref(ic),
-                            C.c_uint32(frame), C.c_uint32(pass_idx), pp, C.c_int32(n),
-                            C.byref(oc))
+    rq = C.byref(requery.v) if requery is not None else None
+    lib().or_restir_spatial_rq(C.byref(scene.s), C.byref(st), C.byref(gc), C.byref(ic),
+                               C.c_uint32(frame), C.c_uint32(pass_idx), pp, C.c_int32(n), rq,
+                               C.byref(oc))
     return out
 
 

@@ -918,12 +918,20 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
 
 /* target at pixel q of a reused sample: its cached point, normal and
  * radiance (Sec. 3.6 caches the query with the sample; the point and normal
- * stay those of the frame the sample was found in, as the radiance does) */
-static double target_of(const or_scene* s, const or_gbuf* g, int32_t q, const or_res* r, int32_t k) {
-    (void)s;
+ * stay those of the frame the sample was found in, as the radiance does).
+ * With rq != NULL caching is off (a test setting, to check Sec. 3.6's claim
+ * that caching adds no bias): the radiance leaving y toward this pixel is
+ * queried afresh from the volume rq instead of read from the reservoir. */
+static double target_of(const or_scene* s, const or_gbuf* g, int32_t q, const or_res* r, int32_t k,
+                        const or_volume* rq) {
     if (r->tri[k] < 0) return 0.0;
-    return target_with_normal(g->pos + 3 * q, g->nrm + 3 * q, g->alb + 3 * q, r->y + 3 * k, r->ny + 3 * k,
-                              r->L + 3 * k);
+    const double* L = r->L + 3 * k;
+    double Lf[3];
+    if (rq) {
+        radiance_at(s, rq, r->y + 3 * k, r->tri[k], g->pos + 3 * q, Lf);
+        L = Lf;
+    }
+    return target_with_normal(g->pos + 3 * q, g->nrm + 3 * q, g->alb + 3 * q, r->y + 3 * k, r->ny + 3 * k, L);
 }
 
 /* Sec. 3.1 step 2 (temporal reuse, mechanics of the cited ReSTIR): the
@@ -935,6 +943,13 @@ int or_restir_temporal(const or_scene* s, const or_settings* st, const or_gbuf* 
                        const or_gbuf* gp, const double cpos[3], const or_res* cur,
                        const or_res* prev, uint32_t frame, const int32_t* pix, int32_t npix,
                        or_res* out) {
+    return or_restir_temporal_rq(s, st, g, gp, cpos, cur, prev, frame, pix, npix, NULL, out);
+}
+
+int or_restir_temporal_rq(const or_scene* s, const or_settings* st, const or_gbuf* g,
+                          const or_gbuf* gp, const double cpos[3], const or_res* cur,
+                          const or_res* prev, uint32_t frame, const int32_t* pix, int32_t npix,
+                          const or_volume* rq, or_res* out) {
     for (int32_t k = 0; k < npix; ++k) {
         int32_t q = pix ? pix[k] : k;
         res_copy(out, k, cur, q);
@@ -954,9 +969,9 @@ int or_restir_temporal(const or_scene* s, const or_settings* st, const or_gbuf* 
         const double Mnom = (double)((s->num_emitters > 0 ? st->n_light : 0) + st->n_bsdf);
         const double Mref = Mc > 0.0 ? Mc : Mnom;
         if (Mp > st->temporal_mcap * Mref) Mp = st->temporal_mcap * Mref;
-        double pc = target_of(s, g, q, cur, q);
+        double pc = target_of(s, g, q, cur, q, rq);
         double wsum = pc * cur->W[q] * Mc;
-        double pp = target_of(s, g, q, prev, pq);
+        double pp = target_of(s, g, q, prev, pq, rq);
         double wp = pp * prev->W[pq] * Mp;
         wsum += wp;
         double u = or_rng(st->seed, q, frame, OR_PASS_TEMPORAL, 0, 0);
@@ -987,6 +1002,12 @@ static int spatial_offset(uint32_t seed, int32_t q, uint32_t frame, uint32_t pas
 int or_restir_spatial(const or_scene* s, const or_settings* st, const or_gbuf* g,
                       const or_res* in, uint32_t frame, uint32_t pass_idx,
                       const int32_t* pix, int32_t npix, or_res* out) {
+    return or_restir_spatial_rq(s, st, g, in, frame, pass_idx, pix, npix, NULL, out);
+}
+
+int or_restir_spatial_rq(const or_scene* s, const or_settings* st, const or_gbuf* g,
+                         const or_res* in, uint32_t frame, uint32_t pass_idx,
+                         const int32_t* pix, int32_t npix, const or_volume* rq, or_res* out) {
     uint32_t pass = OR_PASS_SPATIAL0 + pass_idx;
     int32_t W = g->width, H = g->height;
     for (int32_t k = 0; k < npix; ++k) {
@@ -994,7 +1015,7 @@ int or_restir_spatial(const or_scene* s, const or_settings* st, const or_gbuf* g
         res_copy(out, k, in, q);
         if (g->tri[q] < 0) continue;
         int32_t px = q % W, py = q / W;
-        double psel = target_of(s, g, q, in, q);
+        double psel = target_of(s, g, q, in, q, rq);
         double wsum = psel * in->W[q] * in->M[q];
         double M = in->M[q];
         for (int32_t j = 0; j < st->spatial_neighbours; ++j) {
@@ -1006,7 +1027,7 @@ int or_restir_spatial(const or_scene* s, const or_settings* st, const or_gbuf* g
             if (g->tri[nq] < 0) continue;
             if (dot3(g->nrm + 3 * q, g->nrm + 3 * nq) <= st->normal_reject_cos) continue;
             if (fabs(g->dist[q] - g->dist[nq]) > st->depth_reject_frac * g->dist[q]) continue;
-            double pn = target_of(s, g, q, in, nq);
+            double pn = target_of(s, g, q, in, nq, rq);
             double wn = pn * in->W[nq] * in->M[nq];
             wsum += wn;
             M += in->M[nq];

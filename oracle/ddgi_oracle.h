@@ -158,6 +158,16 @@ int or_restir_temporal(const or_scene* s, const or_settings* st, const or_gbuf* 
 int or_restir_spatial(const or_scene* s, const or_settings* st, const or_gbuf* g,
                       const or_res* in, uint32_t frame, uint32_t pass,
                       const int32_t* pix, int32_t npix, or_res* out);
+/* the same two passes with caching off when rq != NULL (a test setting): the
+ * target of a reused sample queries its radiance afresh from the volume rq,
+ * from the current pixel, instead of the radiance cached with it (Sec. 3.6) */
+int or_restir_temporal_rq(const or_scene* s, const or_settings* st, const or_gbuf* g,
+                          const or_gbuf* gp, const double prev_cam_pos[3], const or_res* cur,
+                          const or_res* prev, uint32_t frame, const int32_t* pix, int32_t npix,
+                          const or_volume* rq, or_res* out);
+int or_restir_spatial_rq(const or_scene* s, const or_settings* st, const or_gbuf* g,
+                         const or_res* in, uint32_t frame, uint32_t pass,
+                         const int32_t* pix, int32_t npix, const or_volume* rq, or_res* out);
 int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_res* r,
              const double* resid, const int32_t* pix, int32_t npix, double* radiance);
 void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const double* y,

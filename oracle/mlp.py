@@ -206,3 +206,48 @@ def training_samples(o, S, sc, params, frame, samples, seed, lo, scale):
         fz = np.maximum(predict(params, z[face], nz[face], lo, scale), 0.0)
         target[face] = sc.emission[tzf] + sc.albedo[tzf] * fz
     return y, ny, target, valid
+
+
+# ---------------------------------------------------------------------------
+# fallback judge (the probes stay the judge of the network's error)
+# ---------------------------------------------------------------------------
+
+def judge(o, vol, params, y, ny, target, valid, per, lo, scale):
+    """Held-out comparison of the served network with the probe lookup.
+
+    Samples 16 j + 15 are held out of training.  For each held-out sample
+    whose ray hit a front face (``valid``), the network predicts
+    m = max(f(y), 0) and the probes predict p = E(y) / pi, E the irradiance
+    query at y with the view-path bias of Sec. 3.4 taken from the sample's
+    probe (the ray's origin, probe index // per).  Per colour channel, both
+    squared errors against the one-bounce target t are divided by the same
+    denominator 0.5 (m^2 + p^2) + 0.01, which does not depend on t: the
+    target's noise then adds the same expected amount to both sums, and their
+    difference weighs only the two predictions' biases.  The network serves
+    the next queries when its sum is not larger.
+
+    Returns (sum over the network, sum over the probes, count, use network).
+    """
+    y = np.asarray(y, np.float64)
+    ny = np.asarray(ny, np.float64)
+    target = np.asarray(target, np.float64)
+    held = np.arange(15, len(y), 16)
+    held = held[np.asarray(valid)[held]]
+    if len(held) == 0:
+        return 0.0, 0.0, 0, False
+    m = np.maximum(predict(params, y[held], ny[held], lo, scale), 0.0)
+    grid_counts = np.asarray(vol.v.counts[:], np.int64)
+    origin = np.asarray(vol.v.origin[:], np.float64)
+    spacing = np.asarray(vol.v.spacing[:], np.float64)
+    pr = np.zeros_like(m)
+    for k, i in enumerate(held):
+        p = i // per
+        ijk = np.array([p % grid_counts[0], (p // grid_counts[0]) % grid_counts[1],
+                        p // (grid_counts[0] * grid_counts[1])])
+        P = origin + spacing * ijk + vol.offset[p]
+        pr[k] = o.biased_query(vol, y[i], ny[i], P) / math.pi
+    den = 0.5 * (m * m + pr * pr) + 0.01
+    t = target[held]
+    s_net = float(np.sum((m - t) ** 2 / den))
+    s_probe = float(np.sum((pr - t) ** 2 / den))
+    return s_net, s_probe, int(len(held)), bool(s_net <= s_probe)

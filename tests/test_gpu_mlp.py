@@ -430,3 +430,43 @@ def test_bf16_learned_frame_trains(dd):
         assert np.all(np.isfinite(rad))
     assert np.mean(errs[-3:]) < 0.5 * np.mean(errs[:2])
     assert ctx.get_status() == dd.OK
+
+
+def test_judge_matches_the_oracle_judge(dd, M):
+    """The fallback judge (reading c16) against the oracle's judge, given the
+    same inputs: the frame's held-out samples and targets, the served network
+    after its moving-average blend, and the context's probe maps.  The error
+    sums must agree to the network's fp16 tolerance (the probe sum, fp32
+    against fp64, far tighter), the held-out count exactly, and the verdict
+    wherever the two sums are not within that tolerance of each other."""
+    import oracle
+    sc = scenegen.tiny_room()
+    sc.settings = dataclasses.replace(sc.settings, learned_target=1, train_samples=16384)
+    ctx = dd.Context.from_scene(sc)
+    lo, scale = M.scene_box(sc.verts)
+    per = 16384 // int(np.prod(sc.grid.counts))
+    decided = 0
+    for f in range(8):
+        ctx.probe_update(f)
+        ctx.mlp_train(f)
+        st = ctx.mlp_status()
+        smp = ctx.mlp_samples()
+        served = ctx.mlp_params_served()
+        irr, dep, off, _ = ctx.probe_state_get()
+        vol = oracle.Volume(sc.grid)
+        vol.irr[:] = irr[..., :3]
+        vol.depth[:] = dep
+        vol.offset[:] = off[:, :3]
+        params = _to_oracle(served, M)
+        # inference rounds the biases to fp16 too (they ride in the weight tile)
+        params = [(W, b.astype(np.float16).astype(np.float64)) for W, b in params]
+        s_net, s_probe, n, use = M.judge(oracle, vol, params, smp[:, 0:3], smp[:, 4:7], smp[:, 8:11],
+                                         smp[:, 3] > 0, per, lo, scale)
+        assert st["judge_n"] == n > 0
+        assert st["judge_mlp"] == pytest.approx(s_net, rel=1e-2), f
+        assert st["judge_probe"] == pytest.approx(s_probe, rel=1e-4), f
+        if abs(s_net - s_probe) > 2e-2 * max(s_net, s_probe):
+            assert st["use_mlp"] == float(use), (f, s_net, s_probe)
+            decided += 1
+    assert decided >= 4
+    assert ctx.get_status() == dd.OK

@@ -509,19 +509,23 @@ def test_apartment_probe_trace_sampled(dd, orc, apt):
     _vol_to_gpu(ctx, vol)
     ctx.probe_trace(9)
     rays = ctx.probe_rays_get()
-    probes = np.array([0, 77, 500, 1023, 1500, 2047], np.int32)
+    # 16 probes x 256 rays = 4096 rays, so that 99.9 % leaves room for 4
+    probes = np.sort(np.random.default_rng(8).choice(sc.grid.num_probes, 16, replace=False)).astype(np.int32)
     ref = orc.probe_trace(S, vol, 9, probes=probes)
     got = rays[probes]
     same = np.sign(got[..., 3]) == np.sign(ref[..., 3])
-    assert _frac(same) >= 0.99
-    assert _frac(_close(got[..., :3][same], ref[..., :3][same], 1e-4).all(-1)) >= 0.99
+    assert _frac(same) >= 0.999
+    assert _frac(_close(got[..., 3][same], ref[..., 3][same], 1e-5)) >= 0.999
+    assert _frac(_close(got[..., :3][same], ref[..., :3][same], 1e-5).all(-1)) >= 0.999
 
 
 def test_apartment_resampling_passes_sampled(dd, orc, apt):
     """initial / temporal / spatial / shade at 1920x1080 on synthetic
-    G-buffers, reservoirs and probe maps, compared on sampled pixels."""
+    G-buffers, reservoirs and probe maps, compared on 4096 sampled pixels
+    (so that 99.9 % allows 4 ties)."""
     import torch
-    sc, ctx, S, sample = apt
+    sc, ctx, S, _ = apt
+    sample = np.sort(np.random.default_rng(19).choice(1920 * 1080, 4096, replace=False)).astype(np.int32)
     W, H = 1920, 1080
     n = W * H
     vol = orc.Volume(sc.grid)
@@ -541,7 +545,7 @@ def test_apartment_resampling_passes_sampled(dd, orc, apt):
     ctx.restir_initial(gg, out, resid, 5)
     ref, rref = orc.restir_initial(S, vol, og, 5, pix=sample)
     _res_compare(out.numpy()[sample], ref, what="initial@1080p")
-    assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-4).all(1)) >= 0.99
+    assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-5).all(1)) >= 0.999
     # temporal / spatial on synthetic reservoirs
     rc = scenegen.synthetic_reservoirs(sc, n, 31)
     rp = scenegen.synthetic_reservoirs(sc, n, 32)
@@ -562,8 +566,86 @@ def test_apartment_resampling_passes_sampled(dd, orc, apt):
     rs[:, :3] = np.random.default_rng(3).uniform(0, 0.1, (n, 3))
     ctx.shade(gg, _synthetic_res_to_gpu(dd, ctx, rc, gp), _t(rs), rad)
     shref = orc.shade(S, vol, og, oc, rs[:, :3].astype(np.float64), pix=sample)
-    assert _frac(_close(rad.cpu().numpy()[sample, :3], shref, 1e-4).all(1)) >= 0.99
+    assert _frac(_close(rad.cpu().numpy()[sample, :3], shref, 1e-5).all(1)) >= 0.999
     assert ctx.get_status() == dd.OK
+
+
+def _oracle_res_full(orc, S, rec):
+    """Oracle reservoirs for every pixel from the library's [N, 16] records
+    (the samples' normals from their triangles, as restir_initial stores them)."""
+    from paper_2108_05263_gb300 import ddgi
+    f = ddgi.Reservoirs.fields(rec)
+    r = orc.Reservoirs(rec.shape[0])
+    r.y[:], r.W[:], r.L[:], r.M[:] = f["y"], f["W"], f["L"], f["M"]
+    r.tri[:], r.tag[:] = f["tri"], f["tag"]
+    has = r.tri >= 0
+    r.ny[has] = S.normals[r.tri[has]]
+    return r
+
+
+def _scatter_res(orc, n, pix, part):
+    """A full-image oracle Reservoirs holding `part` (compact, entry k for
+    pixel pix[k]) at its pixels."""
+    r = orc.Reservoirs(n)
+    for name in orc.Reservoirs.FIELDS:
+        getattr(r, name)[pix] = getattr(part, name)
+    return r
+
+
+def test_apartment_fused_initial_temporal_sampled(dd, orc):
+    """The kernel the frame time is measured on, at the measured size: the
+    1920x1080 apartment with its real G-buffers (frame 1, reprojected onto
+    frame 0), probe maps after two GPU updates and frame 0's final
+    reservoirs, through restir_initial_temporal; the oracle runs
+    restir_initial then restir_temporal on the same inputs (teacher forcing)
+    at 4096 sampled pixels.  Then ddgi_shade of the fused output against the
+    oracle's shading of the same reservoirs.  Tolerances as everywhere:
+    >= 99.9 % identical selections, values within 1e-4 relative (floors:
+    radiance 1e-5, W 1e-6) on >= 99.9 % of the sampled pixels."""
+    import torch
+    sc = scenegen.apartment(frames=2)
+    W, H = sc.cameras[0].width, sc.cameras[0].height
+    n = W * H
+    ctx = dd.Context.from_scene(sc)
+    S = orc.Scene(sc)
+    for f in range(2):
+        ctx.probe_update(f)
+    irr, dep, off, upd = ctx.probe_state_get()
+    vol = orc.Volume(sc.grid)
+    vol.irr[:], vol.depth[:], vol.offset[:] = irr[..., :3], dep, off[:, :3]
+    vol.updates = upd
+    cam0, cam1 = sc.cameras[0], sc.cameras[1]
+    fr = dd.Frame(ctx, W, H, sc.settings.spatial_passes)
+    fr.render(0, cam0, probe_update=False)
+    prev = fr.prev_final
+    g0_planes = [a.copy() for a in fr.g[0].numpy()]
+    g1 = dd.GBuffer(W, H)
+    ctx.gbuffer(cam1, cam0, g1)
+    scratch, out = dd.Reservoirs(n), dd.Reservoirs(n)
+    resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial_temporal(g1, np.asarray(cam0.pos, np.float32), scratch, prev, out, resid, 1)
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.shade(g1, out, resid, rad)
+    got, got_resid, got_rad = out.numpy(), resid.cpu().numpy(), rad.cpu().numpy()
+    assert ctx.get_status() == dd.OK
+
+    og1 = orc.GBuffer.from_planes(*g1.numpy(), W, H)
+    og0 = orc.GBuffer.from_planes(*g0_planes, W, H)
+    rng = np.random.default_rng(17)
+    valid = np.flatnonzero(og1.tri >= 0)
+    sample = np.sort(rng.choice(valid, 4096, replace=False)).astype(np.int32)
+    ref_i, rref = orc.restir_initial(S, vol, og1, 1, pix=sample)
+    cur = _scatter_res(orc, n, sample, ref_i)
+    oprev = _oracle_res_full(orc, S, prev.numpy())
+    tref = orc.restir_temporal(S, og1, og0, cam0.pos, cur, oprev, 1, pix=sample)
+    reused = np.mean(tref.M > ref_i.M)
+    assert reused > 0.5, reused                        # most pixels really merged a previous reservoir
+    _res_compare(got[sample], tref, what="fused initial+temporal@1080p")
+    assert _frac(_close(got_resid[sample, :3], rref, 1e-5).all(1)) >= 0.999
+    # shading of the fused output (the GPU's reservoirs and residual as input)
+    ores = _oracle_res_full(orc, S, got)
+    shref = orc.shade(S, vol, og1, ores, got_resid[:, :3].astype(np.float64), pix=sample)
+    assert _frac(_close(got_rad[sample, :3], shref, 1e-5).all(1)) >= 0.999
 
 
 # ---------------------------------------------------------------------------

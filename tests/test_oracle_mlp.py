@@ -193,3 +193,130 @@ def test_c_network_matches_numpy_network(M):
     n /= np.linalg.norm(n, axis=1, keepdims=True)
     ref, _ = M.forward(params, M.encode(p, n, lo, scale))
     np.testing.assert_allclose(oracle.mlp_eval(vol, p, n), ref, rtol=1e-11, atol=1e-12)
+
+
+def _constant_net(M, c):
+    """Zero weights, output bias c: f = c for every input."""
+    params = [(np.zeros_like(W), np.zeros_like(b)) for W, b in M.init_params(0)]
+    params[-1][1][:] = c
+    return params
+
+
+def _triangle_of_points(verts, pts):
+    """Index of the triangle each point lies on (plane distance and
+    barycentric coordinates, computed here in numpy), -1 if none."""
+    v0, e1, e2 = verts[:, 0], verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0]
+    nrm = np.cross(e1, e2)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    out = np.full(len(pts), -1)
+    for k, y in enumerate(pts):
+        d = y - v0
+        on_plane = np.abs(np.einsum("ij,ij->i", d, nrm)) < 1e-5
+        a11, a12, a22 = (e1 * e1).sum(1), (e1 * e2).sum(1), (e2 * e2).sum(1)
+        b1, b2 = (d * e1).sum(1), (d * e2).sum(1)
+        det = a11 * a22 - a12 * a12
+        u, v = (a22 * b1 - a12 * b2) / det, (a11 * b2 - a12 * b1) / det
+        inside = on_plane & (u >= -1e-6) & (v >= -1e-6) & (u + v <= 1 + 1e-6)
+        if inside.any():
+            out[k] = int(np.argmax(inside))
+    return out
+
+
+def test_training_targets_with_a_constant_network(M):
+    """A network with zero weights and output bias c predicts f = c at every
+    point, so the self-training target of a sample is Le(z) + rho(z) max(c, 0)
+    with z the point its cosine bounce hits: 10 where z is on the emitter,
+    else the albedo of z's quad times max(c, 0).  With c = (0.3, -0.2, 0.7):
+    channel 1 must be exactly 0 (the clamp), and (t_r / 0.3, t_b / 0.7) must
+    be the (r, b) albedo of one of the room's quads -- never that of the quad
+    y lies on, since a bounce cannot return to its own plane.  Dropping the
+    rho(z) factor or the clamp, or using rho(y), fails here."""
+    import oracle
+    import scenegen
+    sc = scenegen.tiny_room()
+    S = oracle.Scene(sc)
+    c = np.array([0.3, -0.2, 0.7])
+    lo, scale = M.scene_box(sc.verts)
+    y, ny, target, valid = M.training_samples(oracle, S, sc, _constant_net(M, c), 0, 4096, 1, lo, scale)
+    assert valid.mean() > 0.99
+    t = target[valid]
+    emit = np.all(t == 10.0, axis=1)
+    assert 0.0 < emit.mean() < 0.5
+    assert np.all(t[~emit, 1] == 0.0)
+    alb = sc.albedo.astype(np.float64)
+    ytri = _triangle_of_points(sc.verts.astype(np.float64), y[valid])
+    assert np.all(ytri >= 0)
+    implied = np.stack([t[~emit, 0] / c[0], t[~emit, 2] / c[2]], 1)
+    dist = np.abs(implied[:, None, :] - alb[None, :, [0, 2]]).max(2)       # [samples, triangles]
+    match = dist < 1e-9
+    assert np.all(match.any(1))
+    # the matched albedo is never y's own quad's
+    own = alb[ytri[~emit]][:, [0, 2]]
+    assert np.all(np.abs(implied - own).max(1) > 1e-6)
+    # every non-emitting quad seen from the others is hit by some bounce
+    assert len(np.unique(np.round(implied, 9), axis=0)) >= 8
+
+
+def _constant_volume(o, grid, E):
+    """Probe maps of constant irradiance E (per channel) with open distance
+    maps: the probe query returns E everywhere."""
+    v = o.Volume(grid)
+    P = int(np.prod(grid.counts))
+    depth = np.zeros((P, 16, 16, 2))
+    depth[..., 0], depth[..., 1] = 100.0, 1e4
+    v.set_interior(np.broadcast_to(np.asarray(E, np.float64), (P, 8, 8, 3)), depth)
+    return v
+
+
+def _judge_inputs(M, sc, n, m, seed):
+    """n synthetic samples: points and normals in the room, targets m * X
+    with X ~ Exp(1) (positive, heavy-tailed Monte-Carlo noise around m)."""
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(-0.9, 0.9, (n, 3))
+    ny = rng.normal(size=(n, 3))
+    ny /= np.linalg.norm(ny, axis=1, keepdims=True)
+    target = m * rng.exponential(1.0, (n, 3))
+    valid = rng.random(n) > 0.05
+    return y, ny, target, valid
+
+
+def test_judge_counts_only_held_out_samples_and_an_exact_network_wins(M):
+    """Samples 16 j + 15 with a valid hit are the held-out set; a network
+    that reproduces every target exactly has error 0 and serves."""
+    import oracle
+    import scenegen
+    sc = scenegen.tiny_room()
+    lo, scale = M.scene_box(sc.verts)
+    y, ny, target, valid = _judge_inputs(M, sc, 4096, 1.0, 1)
+    c = np.array([0.4, 0.9, 1.7])
+    target[:] = c
+    vol = _constant_volume(oracle, sc.grid, math.pi * 2.0)
+    s_net, s_probe, cnt, use = M.judge(oracle, vol, _constant_net(M, c), y, ny, target, valid, 64, lo, scale)
+    assert cnt == int(valid[15::16].sum())
+    assert s_net == 0.0 and s_probe > 0.0 and use
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_judge_weighs_bias_not_the_targets_noise(M, seed):
+    """The two errors share a denominator that does not depend on the noisy
+    target, so the noise adds the same expected amount to both and the
+    verdict follows the bias: against targets m X (X ~ Exp(1), as noisy as
+    their mean), an unbiased cache must beat one biased 30 % low, in either
+    role.  A denominator built from the target instead (relative error
+    against the noisy target) prefers the prediction biased toward zero and
+    fails the second case."""
+    import oracle
+    import scenegen
+    sc = scenegen.tiny_room()
+    lo, scale = M.scene_box(sc.verts)
+    m = np.array([0.8, 0.5, 0.3])
+    y, ny, target, valid = _judge_inputs(M, sc, 65536, m, seed)
+    # network unbiased, probes 30 % low
+    vol = _constant_volume(oracle, sc.grid, math.pi * 0.7 * m)
+    s_net, s_probe, _, use = M.judge(oracle, vol, _constant_net(M, m), y, ny, target, valid, 1024, lo, scale)
+    assert use and s_net < s_probe
+    # network 30 % low, probes unbiased
+    vol = _constant_volume(oracle, sc.grid, math.pi * m)
+    s_net, s_probe, _, use = M.judge(oracle, vol, _constant_net(M, 0.7 * m), y, ny, target, valid, 1024, lo,
+                                     scale)
+    assert not use and s_probe < s_net

@@ -427,6 +427,74 @@ def test_occluded_probe_is_suppressed(oracle_lib):
     assert o.ddgi_query(v_occ, q, n)[0][0] < 1.0 + 1e-6
 
 
+def _two_probe_volume(o, E0, E1, mean=100.0, var=0.0):
+    """Two probes on the x axis (x = 0 and x = 1; spacings 1, 0.5, 0.7, so the
+    smallest is 0.5), each with a constant irradiance map (E0, E1) and a
+    constant distance map (mean, mean^2 + var)."""
+    grid = scenegen.ProbeGrid(np.zeros(3, np.float32), np.array([1.0, 0.5, 0.7], np.float32),
+                              np.array([2, 1, 1], np.int32))
+    v = o.Volume(grid)
+    irr = np.zeros((2, 8, 8, 3))
+    irr[0], irr[1] = E0, E1
+    depth = np.zeros((2, 16, 16, 2))
+    depth[..., 0], depth[..., 1] = mean, mean * mean + var
+    v.set_interior(irr, depth)
+    return v
+
+
+def test_view_path_bias_distance_in_a_hand_case(oracle_lib):
+    """Sec. 3.4, reading c4: the query point moves from y toward the previous
+    path vertex by min(0.2 x smallest spacing, half the segment).  Two probes
+    with open distance maps and a normal perpendicular to the axis that joins
+    them weigh the two maps linearly in x (wrap-shading and visibility equal
+    for both), so the returned irradiance reveals where the query was taken:
+    E = (1 - x) E0 + x E1.  A bias away from the vertex, max in place of min,
+    or a distance not scaled by the smallest spacing fails here."""
+    o = oracle_lib
+    E0, E1 = 1.0, 3.0
+    v = _two_probe_volume(o, E0, E1)
+    n = np.array([0.0, 1.0, 0.0])
+    y = np.array([0.3, 0.0, 0.0])
+
+    def x_of(E):
+        np.testing.assert_allclose(E, E[0], rtol=1e-13)
+        return (E[0] - E0) / (E1 - E0)
+
+    # far previous vertex: d = 0.2 x 0.5 = 0.1, toward it (+x)
+    assert x_of(o.biased_query(v, y, n, [0.9, 0.0, 0.0])) == pytest.approx(0.4, abs=1e-12)
+    # near previous vertex (segment 0.12): d = half the segment = 0.06
+    assert x_of(o.biased_query(v, y, n, [0.42, 0.0, 0.0])) == pytest.approx(0.36, abs=1e-12)
+    # the vertex on the other side (-x): the point moves the other way
+    assert x_of(o.biased_query(v, y, n, [-0.5, 0.0, 0.0])) == pytest.approx(0.2, abs=1e-12)
+    # a vertex off the axis moves the point along the segment (0.3, 0.4):
+    # d = 0.1, of which 0.06 along x; the normal is turned to z so that both
+    # probes still see the same wrap-shading term
+    E = o.biased_query(v, y, [0.0, 0.0, 1.0], [0.6, 0.4, 0.0])
+    assert x_of(E) == pytest.approx(0.3 + 0.1 * 0.6, abs=1e-12)
+    # no segment (the vertex is y itself): the plain query at y
+    assert x_of(o.biased_query(v, y, n, y)) == pytest.approx(0.3, abs=1e-12)
+
+
+def test_view_path_bias_keeps_a_thin_wall_from_leaking(oracle_lib):
+    """A thin wall at x = 0.5 between the two probes: each probe's distance
+    map puts a surface 0.5 m away in every direction (zero variance).  Seen
+    from the previous vertex on probe 0's side, the wall's face toward it must
+    return probe 0's irradiance alone, and from the other side probe 1's;
+    the query exactly on the wall (no bias) mixes the two, which is the leak
+    the bias exists to prevent.  Biasing away from the previous vertex picks
+    the wrong probe and fails."""
+    o = oracle_lib
+    E0, E1 = np.array([1.0, 2.0, 3.0]), np.array([30.0, 20.0, 10.0])
+    v = _two_probe_volume(o, E0, E1, mean=0.5, var=0.0)
+    left = o.biased_query(v, [0.5, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.2, 0.1, 0.0])
+    right = o.biased_query(v, [0.5, 0.0, 0.0], [1.0, 0.0, 0.0], [0.8, -0.1, 0.05])
+    np.testing.assert_allclose(left, E0, rtol=1e-9)
+    np.testing.assert_allclose(right, E1, rtol=1e-9)
+    on_wall = o.biased_query(v, [0.5, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.5, 0.0, 0.0])
+    frac = (on_wall - E0) / (E1 - E0)                 # 1/7 of the way: weights 1.2 : 0.2
+    assert np.all(frac > 0.1) and np.all(frac < 0.9), frac
+
+
 # ---------------------------------------------------------------------------
 # primary visibility
 # ---------------------------------------------------------------------------
@@ -574,6 +642,75 @@ def test_temporal_and_spatial_reuse_keep_the_estimate_unbiased(oracle_lib):
         acc[k] = o.shade(S, vol, g, res, resid).mean(0)
     mean, sd = acc.mean(0), acc.std(0) / math.sqrt(T)
     assert np.all(np.abs(mean - exp) <= 4 * sd), (mean, exp, sd)
+
+
+def _constant_volume(o, grid, E):
+    """Probe maps of constant irradiance E with open distance maps (the query
+    returns E everywhere: pinned by test_query_of_constant_field_is_that_constant)."""
+    v = o.Volume(grid)
+    P = int(np.prod(grid.counts))
+    depth = np.zeros((P, 16, 16, 2))
+    depth[..., 0], depth[..., 1] = 100.0, 1e4
+    v.set_interior(np.full((P, 8, 8, 3), E, np.float64), depth)
+    return v
+
+
+@pytest.mark.slow
+def test_query_caching_adds_no_bias(oracle_lib):
+    """Sec. 3.6: reusing a sample with the radiance cached when it was found
+    adds noise but no bias.  The 8x8 one-point image of the reuse test above,
+    with indirect light: the previous frame's reservoirs were made under a
+    probe field of E0 = 1.5 and the current frame's under E1 = 6, so every
+    cached wall radiance in a temporally reused sample is stale by a factor
+    of 4.  The chain initial -> temporal (M cap active) -> spatial -> shade
+    is run with caching on (the library's reading) and off (the target of a
+    reused sample re-queried from the current probes); both must average to
+    the brute-force one-bounce integral rho_x E[L(y)] under E1 (cosine-
+    sampled, 2^17 directions).  Shading with the cached radiance instead of
+    a fresh query, or a contribution weight whose target is not the selected
+    sample's own, fails here."""
+    o = oracle_lib
+    sc = scenegen.tiny_room()
+    S = o.Scene(sc)
+    vol0 = _constant_volume(o, sc.grid, 1.5)
+    vol1 = _constant_volume(o, sc.grid, 6.0)
+    p = np.array([-0.3, -1.0, 0.2])
+    nrm = np.array([0.0, 1.0, 0.0])
+    rho = 0.5
+    n = 64
+    cam = np.array([-0.3, 1.0, 0.2])
+    g = _point_gbuffer(o, S, np.tile(p, (n, 1)), np.tile(nrm, (n, 1)),
+                       np.tile([rho, rho, rho], (n, 1)), cam, width=8)
+    # brute force under the current field
+    rng = np.random.default_rng(11)
+    K = 1 << 17
+    u0, u1 = rng.random(K), rng.random(K)
+    r, ph = np.sqrt(u0), 2 * np.pi * u1
+    loc = np.column_stack([r * np.cos(ph), r * np.sin(ph), np.sqrt(1 - u0)])
+    w = np.array([o.onb_local_to_world(nrm, l) for l in loc])
+    tri, t = o.intersect(S, np.tile(p, (K, 1)), w)
+    L = o.radiance(S, vol1, p + t[:, None] * w, tri, np.tile(p, (K, 1)))
+    L[tri < 0] = 0
+    ref, ref_sd = rho * L.mean(0), rho * L.std(0) / math.sqrt(K)
+    T = 600
+    acc = {"cached": np.zeros((T, 3)), "fresh": np.zeros((T, 3))}
+    differ = 0
+    for k in range(T):
+        f0, f1 = 2 * k, 2 * k + 1
+        prev, _ = o.restir_initial(S, vol0, g, f0)
+        prev.M[:] = 5000.0
+        cur, resid = o.restir_initial(S, vol1, g, f1)
+        out = {}
+        for mode, rq in (("cached", None), ("fresh", vol1)):
+            tmp = o.restir_temporal(S, g, g, cam, cur, prev, f1, requery=rq)
+            res = o.restir_spatial(S, g, tmp, f1, 0, requery=rq)
+            out[mode] = o.shade(S, vol1, g, res, resid)
+            acc[mode][k] = out[mode].mean(0)
+        differ += int(not np.array_equal(out["cached"], out["fresh"]))
+    assert differ > T // 2                     # the two settings really select differently
+    for mode in acc:
+        mean, sd = acc[mode].mean(0), acc[mode].std(0) / math.sqrt(T)
+        assert np.all(np.abs(mean - ref) <= 4 * np.sqrt(sd ** 2 + ref_sd ** 2)), (mode, mean, ref, sd)
 
 
 def test_candidate_subsampling_pattern_and_cap(oracle_lib):
