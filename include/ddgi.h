@@ -111,6 +111,11 @@ typedef struct {
                                    * empty reservoir (M = 0, no residual) and only reuse;
                                    * temporal reuse then caps the previous M at
                                    * temporal_mcap x the nominal candidate count */
+    uint32_t mlp_fp32;            /* 1: a debug form of the network for gradient checks --
+                                   * every network evaluation and gradient runs in fp32 on
+                                   * the CUDA cores (fp32 weights, activations and
+                                   * accumulation, one thread per query or sample); 0: the
+                                   * tensor-core kernels (mlp_bf16 selects their format) */
     uint32_t traversal_visit_cap; /* BVH nodes one ray may visit before its traversal
                                    * gives up (the ray then reports no hit and
                                    * ddgi_get_status returns DDGI_ERR_TRAVERSAL_LIMIT);

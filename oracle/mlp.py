@@ -75,29 +75,43 @@ def init_params(seed: int):
     return params
 
 
-def forward(params, x):
-    """Returns the output [N, 3] and the per-layer inputs / pre-activations."""
-    acts = [x]
+def forward(params, x, q=None):
+    """Returns the output [N, 3] and the per-layer inputs / pre-activations.
+
+    q (optional) rounds every product operand the activations supply -- the
+    input of each layer -- to the operand precision the tensor-core form
+    fixes (fp16 or bf16 operands, Sec. "precision" of the learned form); the
+    products and sums stay fp64.  Without q every value is fp64."""
+    acts = []
     pre = []
     a = x
     for l, (W, b) in enumerate(params):
+        if q is not None:
+            a = q(a)
+        acts.append(a)
         z = a @ W.T + b
         pre.append(z)
         a = np.maximum(z, 0.0) if l < N_LAYERS - 1 else z
-        acts.append(a)
+    acts.append(a)
     return a, (acts, pre)
 
 
-def backward(params, cache, dout):
-    """Gradients (dW, db) of every layer for upstream gradient dout [N, 3]."""
+def backward(params, cache, dout, q=None):
+    """Gradients (dW, db) of every layer for upstream gradient dout [N, 3].
+
+    q (optional) rounds each layer's delta, the product operand of both of
+    its gradient products, as forward's q rounds the layer inputs."""
     acts, pre = cache
     grads = [None] * N_LAYERS
-    d = dout
+    d = dout if q is None else q(dout)
     for l in range(N_LAYERS - 1, -1, -1):
         W, _ = params[l]
         grads[l] = (d.T @ acts[l], d.sum(axis=0))
         if l > 0:
-            d = (d @ W) * (pre[l - 1] > 0.0)
+            # ReLU derivative: 1 where layer l's input (the ReLU output) is > 0
+            d = (d @ W) * (acts[l] > 0.0)
+            if q is not None:
+                d = q(d)
     return grads
 
 

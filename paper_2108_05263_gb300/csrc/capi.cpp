@@ -356,6 +356,7 @@ MLPView mlp_view(ddgi_ctx* c, bool served = true) {
     m.scale = c->mlp_scale;
     m.err = c->err;
     m.bf16 = c->cfg.mlp_bf16 ? 1 : 0;
+    m.fp32 = c->cfg.mlp_fp32 ? 1 : 0;
     return m;
 }
 

@@ -573,9 +573,99 @@ cudaError_t launch_mlp_grad_t(const MLPView& m, const float4* smp, uint32_t n, M
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// fp32 debug form of the gradient: the same samples, loss, loss scaling and
+// counters as k_mlp_train_tc, computed on the CUDA cores in fp32, one thread
+// per sample (forward with every layer input kept, then backward).  Each
+// parameter's gradient is summed over a warp's 32 samples with shuffles and
+// added to the global sum by one atomic.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(MLP_F32_THREADS) k_mlp_grad_f32(MLPView m, const float4* __restrict__ smp,
+                                                                  uint32_t n, MLPState* __restrict__ st,
+                                                                  float* __restrict__ grad) {
+    extern __shared__ float sw[];
+    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) sw[i] = m.params[i];
+    __syncthreads();
+    const uint32_t s_i = blockIdx.x * MLP_F32_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f), nn = make_float4(0.f, 0.f, 1.f, 0.f), tg = y;
+    if (s_i < n) {   // threads past n carry weight 0 but join the warp's reductions
+        y = smp[3 * (size_t)s_i];
+        nn = smp[3 * (size_t)s_i + 1];
+        tg = smp[3 * (size_t)s_i + 2];
+    }
+    const unsigned cnt = __ballot_sync(0xffffffffu, tg.w > 0.f);
+    if (lane == 0 && cnt) atomicAdd(&st->acc, (unsigned)__popc(cnt));
+    // a[0]: the encoded input; a[l]: the ReLU output of layer l - 1 (input of layer l)
+    float a[5][MLP_IN];
+    mlp_f32_encode(m, xyz(y), xyz(nn), a[0]);
+    mlp_f32_layer<MLP_IN, MLP_H, true>(sw, 0, a[0], a[1]);
+    mlp_f32_layer<MLP_H, MLP_H, true>(sw, 1, a[1], a[2]);
+    mlp_f32_layer<MLP_H, MLP_H, true>(sw, 2, a[2], a[3]);
+    mlp_f32_layer<MLP_H, MLP_H, true>(sw, 3, a[3], a[4]);
+    float out[3];
+    mlp_f32_layer<MLP_H, 3, false>(sw, 4, a[4], out);
+    // output delta of the relative-L2 loss (denominator held constant), scaled
+    float dz[MLP_H], da[MLP_H];
+    const float S = st->loss_scale, tv[3] = {tg.x, tg.y, tg.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dz[c] = tg.w * S * 2.f * (out[c] - tv[c]) / (out[c] * out[c] + 0.01f);
+#pragma unroll 1
+    for (int l = 4; l >= 0; --l) {
+        const int ins = mlp_in(l), kin = l == 0 ? 75 : MLP_H, outs = l == 4 ? 3 : MLP_H;
+        const float* W = sw + mlp_off_w(l);
+#pragma unroll 1
+        for (int o = 0; o < outs; ++o) {
+            const float d = dz[o];
+#pragma unroll 1
+            for (int i = 0; i < kin; ++i) {
+                const float v = warp_sum_f32(d * a[l][i]);
+                if (lane == 0) atomicAdd(grad + mlp_off_w(l) + o * ins + i, v);
+            }
+            const float vb = warp_sum_f32(d);
+            if (lane == 0) atomicAdd(grad + mlp_off_b(l) + o, vb);
+        }
+        if (l > 0) {
+            // delta of layer l - 1's pre-activation: W_l^T dz, masked by its ReLU
+#pragma unroll 1
+            for (int i = 0; i < MLP_H; ++i) {
+                float acc = 0.f;
+                for (int o = 0; o < outs; ++o) acc = fmaf(W[o * ins + i], dz[o], acc);
+                da[i] = a[l][i] > 0.f ? acc : 0.f;
+            }
+#pragma unroll 1
+            for (int i = 0; i < MLP_H; ++i) dz[i] = da[i];
+        }
+    }
+}
+
+cudaError_t launch_mlp_grad_f32(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
+                                cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_F32_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_mlp_grad_f32<<<(n + MLP_F32_THREADS - 1) / MLP_F32_THREADS, MLP_F32_THREADS, MLP_F32_SMEM, st>>>(m, smp, n,
+                                                                                                     state, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_mlp_grad(const MLPView& m, const float4* smp, uint32_t n, MLPState* state, float* grad,
                             cudaStream_t st) {
     if (n == 0) return cudaSuccess;
+    if (m.fp32) return launch_mlp_grad_f32(m, smp, n, state, grad, st);
     return m.bf16 ? launch_mlp_grad_t<true>(m, smp, n, state, grad, st)
                   : launch_mlp_grad_t<false>(m, smp, n, state, grad, st);
 }

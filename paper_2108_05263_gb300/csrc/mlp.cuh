@@ -48,6 +48,7 @@ struct MLPView {
     float scale;
     uint32_t* err;         // device error word (bounded waits)
     int bf16;              // 1: weights and activations are bf16, else fp16
+    int fp32;              // 1: fp32 CUDA-core debug form (params only; w16 unused)
 };
 
 // The network's 16-bit formats: fp16 (BF = false) or bf16 (BF = true), both
@@ -381,11 +382,14 @@ cudaError_t launch_mlp_infer_t(const MLPView& m, const Q& q, uint32_t n, cudaStr
     return cudaGetLastError();
 }
 
+#include "mlp_f32.cuh"
+
 // Launches k_mlp_infer over n queries in the network's format: one
 // persistent CTA per SM (6 tile streams, 384 of the SM's 512 tensor-memory
-// columns).
+// columns); or the fp32 debug form when the view asks for it.
 template <class Q>
 cudaError_t launch_mlp_infer(const MLPView& m, const Q& q, uint32_t n, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
+    if (m.fp32) return launch_mlp_infer_f32<Q>(m, q, n, st);
     return m.bf16 ? launch_mlp_infer_t<Q, true>(m, q, n, st) : launch_mlp_infer_t<Q, false>(m, q, n, st);
 }

@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
                 ("mlp_seed", C.c_uint32), ("train_ema", C.c_float), ("probe_relocation", C.c_uint32),
                 ("mlp_bf16", C.c_uint32), ("candidate_stride", C.c_uint32),
-                ("traversal_visit_cap", C.c_uint32)]
+                ("mlp_fp32", C.c_uint32), ("traversal_visit_cap", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -260,6 +260,7 @@ def config_from(grid, settings) -> Config:
     c.probe_relocation = int(getattr(settings, "probe_relocation", 0))
     c.mlp_bf16 = int(getattr(settings, "mlp_bf16", 0))
     c.candidate_stride = int(getattr(settings, "candidate_stride", 1))
+    c.mlp_fp32 = int(getattr(settings, "mlp_fp32", 0))
     c.traversal_visit_cap = int(getattr(settings, "traversal_visit_cap", 0))
     return c
 

@@ -83,6 +83,60 @@ def test_backward_matches_torch_autograd(M):
         np.testing.assert_allclose(gb, lin.bias.grad.numpy(), rtol=1e-10, atol=1e-14)
 
 
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+def test_operand_rounding_matches_torch_autograd_with_rounding_hooks(M, fmt):
+    """forward / backward with q (the 16-bit operand precision of the
+    tensor-core form) against torch's fp64 autograd where each layer's input
+    passes through a rounding function whose backward is the identity and
+    each pre-activation's gradient is rounded by a hook: layer inputs and
+    deltas rounded, products and sums fp64.  With q = None the rounding must
+    vanish (bit-identical to the plain forward / backward)."""
+    def q_np(a):
+        a = np.asarray(a, np.float64)
+        if fmt == "fp16":
+            return a.astype(np.float16).astype(np.float64)
+        b = a.astype(np.float32).view(np.uint32).astype(np.uint64)
+        b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+    def q_t(t):
+        return torch.from_numpy(q_np(t.detach().numpy()))
+
+    class Round(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            return q_t(a)
+
+        @staticmethod
+        def backward(ctx, g):
+            return g
+
+    params = M.init_params(6)
+    for W, b in params:
+        b += np.random.default_rng(2).normal(0, 0.1, b.shape)
+    x, t, valid = _batch(M, seed=3)
+    out, cache = M.forward(params, x, q=q_np)
+    dout = np.where(valid[:, None], 2.0 * (out - t) / (out ** 2 + 0.01), 0.0)
+    grads = M.backward(params, cache, dout, q=q_np)
+    net = _torch_net(M, params)
+    lins = [m for m in net if isinstance(m, torch.nn.Linear)]
+    a = torch.from_numpy(x)
+    for l, lin in enumerate(lins):
+        z = lin(Round.apply(a))
+        z.register_hook(lambda g: q_t(g))
+        a = torch.relu(z) if l < len(lins) - 1 else z
+    np.testing.assert_allclose(out, a.detach().numpy(), rtol=1e-12, atol=1e-12)
+    a.backward(torch.from_numpy(dout))
+    for (gW, gb), lin in zip(grads, lins):
+        np.testing.assert_allclose(gW, lin.weight.grad.numpy(), rtol=1e-10, atol=1e-13)
+        np.testing.assert_allclose(gb, lin.bias.grad.numpy(), rtol=1e-10, atol=1e-13)
+    # rounding really happened, and q = None is the plain fp64 network
+    out0, cache0 = M.forward(params, x)
+    assert np.abs(out0 - out).max() > 1e-6
+    out1, cache1 = M.forward(params, x, q=None)
+    np.testing.assert_array_equal(out0, out1)
+
+
 def test_gradients_match_finite_differences(M):
     params = M.init_params(5)
     x, t, valid = _batch(M, n=64, seed=2)
