@@ -291,7 +291,10 @@ class GBuffer:
 
     @staticmethod
     def from_planes(g0, g1, g2, width, height):
-        """From packed float32 planes (pos+dist, normal+tri bits, albedo+prev bits)."""
+        """From packed float32 planes (pos+dist, normal+tri bits, albedo+prev
+        bits).  The library marks a surface on a moving instance with bit 30
+        of the previous-pixel word; the oracle finds that from the triangle's
+        instance itself, so the flag is dropped here."""
         n = g0.shape[0]
         o = GBuffer(n, width, height)
         o.pos[:] = g0[:, :3]
@@ -299,7 +302,8 @@ class GBuffer:
         o.nrm[:] = g1[:, :3]
         o.alb[:] = g2[:, :3]
         o.tri[:] = np.ascontiguousarray(g1[:, 3]).view(np.int32)
-        o.prev[:] = np.ascontiguousarray(g2[:, 3]).view(np.int32)
+        prev = np.ascontiguousarray(g2[:, 3]).view(np.int32)
+        o.prev[:] = np.where(prev >= 0, prev & ~0x40000000, prev)
         return o
 
     def planes(self):
@@ -547,6 +551,8 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
     queried afresh from that volume at the current pixel."""
     _need_full(g, cur)
     _need_full(gp, prev)
+    if np.any(g.prev >= gp.tri.shape[0]):
+        raise ValueError("previous-pixel indices beyond the previous G-buffer")
     st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
