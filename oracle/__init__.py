@@ -57,7 +57,7 @@ class _Scene(C.Structure):
                 ("tri_instance", _ip), ("num_instances", C.c_int32), ("object_verts", _dp),
                 ("normal", _dp), ("area", _dp), ("num_emitters", C.c_int32),
                 ("emitter_tri", _ip), ("emitter_of", _ip), ("emitter_cdf", _fp), ("area_total", C.c_double),
-                ("inst_cur", _dp), ("inst_prev", _dp)]
+                ("inst_cur", _dp), ("inst_prev", _dp), ("glossy", _dp)]
 
 
 class _Settings(C.Structure):
@@ -67,7 +67,7 @@ class _Settings(C.Structure):
                 ("temporal_mcap", C.c_double), ("spatial_neighbours", C.c_int32),
                 ("spatial_radius", C.c_int32), ("normal_reject_cos", C.c_double),
                 ("depth_reject_frac", C.c_double), ("seed", C.c_uint32), ("relocate", C.c_int32),
-                ("candidate_stride", C.c_int32)]
+                ("candidate_stride", C.c_int32), ("footprint_c", C.c_double)]
 
 
 class _Volume(C.Structure):
@@ -85,7 +85,7 @@ class _Camera(C.Structure):
 
 class _GBuf(C.Structure):
     _fields_ = [("pos", _dp), ("dist", _dp), ("nrm", _dp), ("alb", _dp), ("tri", _ip),
-                ("prev", _ip), ("width", C.c_int32), ("height", C.c_int32)]
+                ("prev", _ip), ("width", C.c_int32), ("height", C.c_int32), ("eye", C.c_double * 3)]
 
 
 class _Res(C.Structure):
@@ -108,6 +108,8 @@ def lib():
             L.or_target.restype = C.c_double
             L.or_sample_emitter.restype = C.c_int32
             L.or_sample_emitter.argtypes = [C.POINTER(_Scene), C.c_double]
+            L.or_ggx_D.restype = C.c_double
+            L.or_ggx_G1.restype = C.c_double
         return _lib
 
 
@@ -148,6 +150,10 @@ class Scene:
             self.s.tri_instance = _p(self.tri_instance, _ip)
             self.s.num_instances = int(self.tri_instance.max(initial=-1)) + 1
             self.s.object_verts = _p(self.object_verts)
+        gl = getattr(sc, "glossy", None)
+        if gl is not None:
+            self.glossy = np.ascontiguousarray(gl, np.float64).reshape(-1)
+            self.s.glossy = _p(self.glossy)
         if lib().or_scene_init(C.byref(self.s)) != 0:
             raise MemoryError("or_scene_init")
         self.settings = settings_of(sc.settings)
@@ -206,6 +212,7 @@ def settings_of(st) -> _Settings:
     o.seed = st.seed
     o.relocate = int(getattr(st, "probe_relocation", 0))
     o.candidate_stride = int(getattr(st, "candidate_stride", 1))
+    o.footprint_c = float(getattr(st, "footprint_c", 0.2))
     return o
 
 
@@ -281,16 +288,18 @@ class GBuffer:
         self.tri = np.full(n, -1, np.int32)
         self.prev = np.full(n, -1, np.int32)
         self.width, self.height = width, height
+        self.eye = np.zeros(3)          # camera position the G-buffer was rendered from
 
     def c(self) -> _GBuf:
         g = _GBuf()
         g.pos, g.dist, g.nrm, g.alb = _p(self.pos), _p(self.dist), _p(self.nrm), _p(self.alb)
         g.tri, g.prev = _p(self.tri, _ip), _p(self.prev, _ip)
         g.width, g.height = self.width, self.height
+        g.eye = _v3(self.eye)
         return g
 
     @staticmethod
-    def from_planes(g0, g1, g2, width, height):
+    def from_planes(g0, g1, g2, width, height, eye=None):
         """From packed float32 planes (pos+dist, normal+tri bits, albedo+prev
         bits).  The library marks a surface on a moving instance with bit 30
         of the previous-pixel word; the oracle finds that from the triangle's
@@ -304,6 +313,8 @@ class GBuffer:
         o.tri[:] = np.ascontiguousarray(g1[:, 3]).view(np.int32)
         prev = np.ascontiguousarray(g2[:, 3]).view(np.int32)
         o.prev[:] = np.where(prev >= 0, prev & ~0x40000000, prev)
+        if eye is not None:
+            o.eye[:] = eye
         return o
 
     def planes(self):
@@ -529,6 +540,7 @@ def gbuffer(scene: Scene, cam, prev_cam=None, pix=None) -> GBuffer:
     pc = camera(prev_cam) if prev_cam is not None else None
     lib().or_gbuffer(C.byref(scene.s), C.byref(c), C.byref(pc) if pc is not None else None,
                      pp, C.c_int32(n), C.byref(gc))
+    g.eye[:] = cam.pos
     return g
 
 
@@ -590,26 +602,68 @@ def _need_full(g: GBuffer, *bufs):
             raise ValueError(f"input buffer holds {m} entries, the image {g.tri.shape[0]} pixels")
 
 
-def shade(scene: Scene, vol: Volume, g: GBuffer, res: Reservoirs, resid, pix=None):
+def shade(scene: Scene, vol: Volume, g: GBuffer, res: Reservoirs, resid, pix=None, frame: int = 0,
+          settings=None):
+    """Eq. Algorithm's estimate per pixel; ``frame`` keys the random numbers
+    of the specular recursion (glossy scenes only)."""
     _need_full(g, res, resid)
+    st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
     n = g.tri.shape[0] if pix is None else len(pr)
     rad = np.zeros((n, 3))
     gc, rc = g.c(), res.c()
     resid = np.ascontiguousarray(resid, np.float64)
-    lib().or_shade(C.byref(scene.s), C.byref(vol.v), C.byref(gc), C.byref(rc), _p(resid),
-                   pp, C.c_int32(n), _p(rad))
+    lib().or_shade(C.byref(scene.s), C.byref(vol.v), C.byref(st), C.byref(gc), C.byref(rc), _p(resid),
+                   C.c_uint32(frame), pp, C.c_int32(n), _p(rad))
     return rad
 
 
-def radiance(scene: Scene, vol: Volume, y, tri, frm):
-    """Outgoing radiance (Le + L_DDGI+)(y, y -> frm) for batches of points."""
+def shade_radiance(scene: Scene, vol: Volume, eye, x1, n1, y, tri: int, pix: int, frame: int, settings=None):
+    """Radiance at y toward x1 with the specular recursion of Sec. 3.3, and
+    the number of path vertices it used (x1 counted)."""
+    st = _settings(scene, settings)
+    a = [np.ascontiguousarray(v, np.float64) for v in (eye, x1, n1, y)]
+    L = np.zeros(3)
+    verts = C.c_int32(0)
+    lib().or_shade_radiance(C.byref(scene.s), C.byref(vol.v), C.byref(st), _p(a[0]), _p(a[1]), _p(a[2]),
+                            _p(a[3]), C.c_int32(tri), C.c_uint32(pix), C.c_uint32(frame), _p(L), C.byref(verts))
+    return L, verts.value
+
+
+def ggx_D(nh, alpha) -> float:
+    return lib().or_ggx_D(C.c_double(nh), C.c_double(alpha))
+
+
+def ggx_G1(nw, alpha) -> float:
+    return lib().or_ggx_G1(C.c_double(nw), C.c_double(alpha))
+
+
+def ggx_sample_h(n, alpha, u0, u1):
+    h = np.zeros(3)
+    lib().or_ggx_sample_h(_p(np.ascontiguousarray(n, np.float64)), C.c_double(alpha), C.c_double(u0),
+                          C.c_double(u1), _p(h))
+    return h
+
+
+def glossy_sample(n, wo, ks, alpha, u0, u1):
+    """(wi, weight f_g cos / pdf per channel, pdf), or None below the surface."""
+    wi, wgt, pdf = np.zeros(3), np.zeros(3), C.c_double(0.0)
+    a = [np.ascontiguousarray(v, np.float64) for v in (n, wo, ks)]
+    ok = lib().or_glossy_sample(_p(a[0]), _p(a[1]), _p(a[2]), C.c_double(alpha), C.c_double(u0),
+                                C.c_double(u1), _p(wi), _p(wgt), C.byref(pdf))
+    return (wi, wgt, pdf.value) if ok else None
+
+
+def radiance(scene: Scene, vol: Volume, y, tri, frm, u=None):
+    """Outgoing radiance (Le + L_DDGI+)(y, y -> frm) for batches of points;
+    u ([n][2], optional) are the random numbers of the glossy sample."""
     y = np.ascontiguousarray(y, np.float64).reshape(-1, 3)
     frm = np.ascontiguousarray(frm, np.float64).reshape(-1, 3)
     tri = np.ascontiguousarray(tri, np.int32)
+    uu = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1, 2)
     L = np.zeros_like(y)
     lib().or_radiance_batch(C.byref(scene.s), C.byref(vol.v), C.c_int32(y.shape[0]), _p(y),
-                            _p(tri, _ip), _p(frm), _p(L))
+                            _p(tri, _ip), _p(frm), _p(uu), _p(L))
     return L
 
 
@@ -677,7 +731,7 @@ class Renderer:
             res = restir_spatial(S, g, res, f, i)
             out[f"spatial{i}"] = res
         out["final"] = res
-        out["radiance"] = shade(S, self.vol, g, res, resid)
+        out["radiance"] = shade(S, self.vol, g, res, resid, frame=f)
         self.prev_g, self.prev_res, self.prev_cam = g, res, cam
         return out
 

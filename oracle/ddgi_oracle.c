@@ -395,18 +395,95 @@ double or_ddgi_query(const or_volume* v, const double q[3], const double n[3], d
 
 /* View-path bias (Sec. 3.4): the query point moves from y back toward the
  * previous path vertex by d = min(0.2 * min probe spacing, half the segment). */
-void or_biased_query(const or_volume* v, const double y[3], const double n_y[3],
-                     const double from[3], double E[3]) {
+static void biased_point(const or_volume* v, const double y[3], const double from[3], double q[3]) {
     double d[3];
     sub3(from, y, d);
     double l = len3(d);
-    double q[3] = {y[0], y[1], y[2]};
+    q[0] = y[0]; q[1] = y[1]; q[2] = y[2];
     if (l > 0.0) {
         double dv = 0.2 * min_spacing(v);
         if (0.5 * l < dv) dv = 0.5 * l;
         for (int a = 0; a < 3; ++a) q[a] = y[a] + dv * d[a] / l;
     }
+}
+
+void or_biased_query(const or_volume* v, const double y[3], const double n_y[3],
+                     const double from[3], double E[3]) {
+    double q[3];
+    biased_point(v, y, from, q);
     or_ddgi_query(v, q, n_y, E);
+}
+
+/* ------------------------------------------------------------------------ */
+/* glossy lobe (Sec. 3.3): a GGX microfacet lobe per triangle, reflectance   */
+/* k_s and roughness alpha, f_g = k_s D(h) G1(wo) G1(wi) / (4 |n.wo| |n.wi|) */
+/* (separable Smith masking, no Fresnel term)                               */
+/* ------------------------------------------------------------------------ */
+
+/* GGX (Trowbridge-Reitz) distribution of normals */
+double or_ggx_D(double nh, double a) {
+    if (nh <= 0.0) return 0.0;
+    double a2 = a * a;
+    double den = nh * nh * (a2 - 1.0) + 1.0;
+    return a2 / (PI * den * den);
+}
+
+/* Smith masking of one direction for GGX */
+double or_ggx_G1(double nw, double a) {
+    if (nw <= 0.0) return 0.0;
+    double a2 = a * a;
+    return 2.0 * nw / (nw + sqrt(a2 + (1.0 - a2) * nw * nw));
+}
+
+/* half vector with density D(h) (n.h): cos^2 theta = (1 - u0) / (1 + (a^2 - 1) u0),
+ * azimuth 2 pi u1 in the basis around n */
+void or_ggx_sample_h(const double n[3], double a, double u0, double u1, double h[3]) {
+    double c2 = (1.0 - u0) / (1.0 + (a * a - 1.0) * u0);
+    double c = sqrt(c2), sn = sqrt(fmax(0.0, 1.0 - c2)), ph = 2.0 * PI * u1;
+    double l[3] = {sn * cos(ph), sn * sin(ph), c};
+    or_onb_local_to_world(n, l, h);
+}
+
+/* One direction wi drawn proportionally to the glossy lobe (the mirror of wo
+ * about a half vector drawn by or_ggx_sample_h), its density
+ * pdf = D (n.h) / (4 |wo.h|) and the weight f_g (n.wi) / pdf per channel.
+ * Returns 0 (weight 0) when wi falls below the surface. */
+int or_glossy_sample(const double n[3], const double wo[3], const double ks[3], double a, double u0,
+                     double u1, double wi[3], double wgt[3], double* pdf) {
+    double h[3];
+    or_ggx_sample_h(n, a, u0, u1, h);
+    double oh = dot3(wo, h);
+    for (int k = 0; k < 3; ++k) wi[k] = 2.0 * oh * h[k] - wo[k];
+    wgt[0] = wgt[1] = wgt[2] = 0.0;
+    *pdf = 0.0;
+    double ni = dot3(n, wi), no = dot3(n, wo), nh = dot3(n, h);
+    if (ni <= 0.0 || no <= 0.0 || nh <= 0.0 || oh <= 0.0) return 0;
+    *pdf = or_ggx_D(nh, a) * nh / (4.0 * oh);
+    double g = or_ggx_G1(no, a) * or_ggx_G1(ni, a) * oh / (no * nh);
+    for (int k = 0; k < 3; ++k) wgt[k] = ks[k] * g;
+    return 1;
+}
+
+/* The glossy half of Eq. lddgiplus at a point with normal n seen from wo:
+ * one sample wi of the glossy lobe, E(q, wi) read as cosine-prefiltered
+ * incident radiance around wi, (1 / pi) E(q, wi) f_g (n.wi) / pdf.  (With E
+ * normalised so that uniform radiance L gives pi L, 1 / pi reflects a uniform
+ * environment exactly; the paper prints 1 / (2 pi) for its own
+ * normalisation of E.) */
+static void glossy_ddgi(const or_volume* v, const double q[3], const double n[3], const double wo[3],
+                        const double* spec, double u0, double u1, double out[3]) {
+    double wi[3], wgt[3], pdf;
+    out[0] = out[1] = out[2] = 0.0;
+    if (!or_glossy_sample(n, wo, spec, spec[3], u0, u1, wi, wgt, &pdf)) return;
+    double E[3];
+    or_ddgi_query(v, q, wi, E);
+    for (int k = 0; k < 3; ++k) out[k] = E[k] / PI * wgt[k];
+}
+
+static int has_glossy(const or_scene* s, int32_t tri) {
+    if (!s->glossy) return 0;
+    const double* g = s->glossy + 4 * tri;
+    return g[0] > 0 || g[1] > 0 || g[2] > 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -495,9 +572,17 @@ int or_probe_trace(const or_scene* s, const or_volume* v, const or_settings* st,
             const double* le = s->emission + 3 * tri;
             const double* rho = s->albedo + 3 * tri;
             double y[3] = {P[0] + t * w[0], P[1] + t * w[1], P[2] + t * w[2]};
-            double E[3] = {0, 0, 0};
-            if (rho[0] > 0 || rho[1] > 0 || rho[2] > 0) or_biased_query(v, y, n_y, P, E);
+            double q[3], E[3] = {0, 0, 0};
+            biased_point(v, y, P, q);
+            if (rho[0] > 0 || rho[1] > 0 || rho[2] > 0) or_ddgi_query(v, q, n_y, E);
             for (int c = 0; c < 3; ++c) out[c] = le[c] * att + rho[c] / PI * E[c];
+            if (has_glossy(s, tri)) {   /* the glossy half of L_DDGI+ toward the probe */
+                double wo[3] = {-w[0], -w[1], -w[2]}, G[3];
+                double u0 = or_rng(st->seed, (uint32_t)p, frame, OR_PASS_PROBE_GLOSSY, (uint32_t)r, 0);
+                double u1 = or_rng(st->seed, (uint32_t)p, frame, OR_PASS_PROBE_GLOSSY, (uint32_t)r, 1);
+                glossy_ddgi(v, q, n_y, wo, s->glossy + 4 * tri, u0, u1, G);
+                for (int c = 0; c < 3; ++c) out[c] += G[c];
+            }
         }
     }
     return 0;
@@ -762,9 +847,11 @@ void or_mlp_eval(const or_volume* v, const double p[3], const double n[3], doubl
 
 /* outgoing radiance (Le + L_DDGI+)(y, y -> x): emission is one-sided, back
  * faces carry nothing, the probe term is queried with the view-path bias (or
- * the network is evaluated at y in the learned target form) */
+ * the network is evaluated at y in the learned target form); a glossy
+ * triangle adds the one-sample glossy half of Eq. lddgiplus, drawn with the
+ * random numbers (u0, u1) */
 static void radiance_at(const or_scene* s, const or_volume* v, const double y[3], int32_t tri,
-                        const double x[3], double L[3]) {
+                        const double x[3], double u0, double u1, double L[3]) {
     const double* n = s->normal + 3 * tri;
     double d[3];
     sub3(x, y, d);
@@ -772,7 +859,8 @@ static void radiance_at(const or_scene* s, const or_volume* v, const double y[3]
     if (dot3(n, d) <= 0.0) return;
     const double* le = s->emission + 3 * tri;
     const double* rho = s->albedo + 3 * tri;
-    if (!(rho[0] > 0 || rho[1] > 0 || rho[2] > 0)) {
+    const int glossy = has_glossy(s, tri) && !(v->use_mlp && v->mlp);
+    if (!(rho[0] > 0 || rho[1] > 0 || rho[2] > 0) && !glossy) {
         for (int c = 0; c < 3; ++c) L[c] = le[c];
         return;
     }
@@ -782,18 +870,101 @@ static void radiance_at(const or_scene* s, const or_volume* v, const double y[3]
         for (int c = 0; c < 3; ++c) L[c] = le[c] + rho[c] * (f[c] > 0.0 ? f[c] : 0.0);
         return;
     }
-    double E[3] = {0, 0, 0};
-    or_biased_query(v, y, n, x, E);
+    double q[3], E[3] = {0, 0, 0};
+    biased_point(v, y, x, q);
+    or_ddgi_query(v, q, n, E);
     for (int c = 0; c < 3; ++c) L[c] = le[c] + rho[c] / PI * E[c];
+    if (glossy) {
+        double l = len3(d), wo[3] = {d[0] / l, d[1] / l, d[2] / l}, G[3];
+        glossy_ddgi(v, q, n, wo, s->glossy + 4 * tri, u0, u1, G);
+        for (int c = 0; c < 3; ++c) L[c] += G[c];
+    }
 }
 
-/* batch form of the outgoing radiance, for estimator tests */
+/* batch form of the outgoing radiance, for estimator tests; u: [n][2]
+ * random numbers of the glossy sample (NULL: 0.5, 0.5) */
 void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const double* y,
-                       const int32_t* tri, const double* from, double* L) {
+                       const int32_t* tri, const double* from, const double* u, double* L) {
     for (int32_t k = 0; k < n; ++k) {
         L[3 * k] = L[3 * k + 1] = L[3 * k + 2] = 0.0;
-        if (tri[k] >= 0) radiance_at(s, v, y + 3 * k, tri[k], from + 3 * k, L + 3 * k);
+        if (tri[k] >= 0)
+            radiance_at(s, v, y + 3 * k, tri[k], from + 3 * k, u ? u[2 * k] : 0.5, u ? u[2 * k + 1] : 0.5,
+                        L + 3 * k);
     }
+}
+
+/* Outgoing radiance at the selected sample y toward the shaded point x1
+ * (normal n1, seen from the camera at eye), for shading (Sec. 3.3, specular
+ * recursion): at each path vertex x_n (n >= 2) the emission and the diffuse
+ * half rho / pi E(x_n, n_n) are added; the glossy half is either estimated
+ * by the one-sample glossy term of Eq. lddgiplus -- once the path footprint
+ * a(x_1 .. x_n) exceeds c a_0, or at the last of OR_MAX_SHADE_VERTS vertices
+ * -- or continued by tracing the sampled glossy direction to x_{n+1}.  The
+ * footprint (Bekaert et al., as the paper adopts it) is
+ * a = (sum_i sqrt(|x_i - x_{i+1}|^2 / (p_i <n_{i+1}, -w_i>)))^2 with p_1 the
+ * density of sampling w_1 at the (Lambertian) primary vertex, cos / pi, and
+ * p_i the glossy sampling density beyond it; a_0 = |x_0 - x_1|^2 /
+ * (4 pi <n_1, -w_0>).  Random numbers: (seed, pixel, frame, OR_PASS_SHADE,
+ * vertex n, dimension 0 / 1).  verts (optional) receives the vertices used. */
+void or_shade_radiance(const or_scene* s, const or_volume* v, const or_settings* st, const double eye[3],
+                       const double x1[3], const double n1[3], const double y[3], int32_t tri, uint32_t pix,
+                       uint32_t frame, double L[3], int32_t* verts) {
+    L[0] = L[1] = L[2] = 0.0;
+    double e0[3], d1[3];
+    sub3(eye, x1, e0);
+    sub3(y, x1, d1);
+    double l0 = len3(e0), l1 = len3(d1);
+    double c0 = dot3(n1, e0) / l0;
+    double a0 = l0 * l0 / (4.0 * PI * c0);
+    double alim = st->footprint_c * a0;
+    double w1[3] = {d1[0] / l1, d1[1] / l1, d1[2] / l1};
+    double p1 = dot3(n1, w1) / PI;
+    double c2 = fabs(dot3(s->normal + 3 * tri, w1));
+    double sa = sqrt(l1 * l1 / (p1 * c2));
+    double thr[3] = {1.0, 1.0, 1.0};
+    double prev[3] = {x1[0], x1[1], x1[2]}, cur[3] = {y[0], y[1], y[2]};
+    int32_t t = tri, n = 2;
+    for (;;) {
+        const double* nrm = s->normal + 3 * t;
+        double back[3];
+        sub3(prev, cur, back);
+        if (dot3(nrm, back) <= 0.0) break;
+        const double* le = s->emission + 3 * t;
+        const double* rho = s->albedo + 3 * t;
+        for (int c = 0; c < 3; ++c) L[c] += thr[c] * le[c];
+        const int glossy = has_glossy(s, t);
+        if (!(rho[0] > 0 || rho[1] > 0 || rho[2] > 0) && !glossy) break;
+        double q[3], E[3];
+        biased_point(v, cur, prev, q);
+        or_ddgi_query(v, q, nrm, E);
+        for (int c = 0; c < 3; ++c) L[c] += thr[c] * rho[c] / PI * E[c];
+        if (!glossy) break;
+        double lb = len3(back), wo[3] = {back[0] / lb, back[1] / lb, back[2] / lb};
+        double u0 = or_rng(st->seed, pix, frame, OR_PASS_SHADE, (uint32_t)n, 0);
+        double u1 = or_rng(st->seed, pix, frame, OR_PASS_SHADE, (uint32_t)n, 1);
+        const double* spec = s->glossy + 4 * t;
+        double wi[3], wgt[3], pdf;
+        if (!or_glossy_sample(nrm, wo, spec, spec[3], u0, u1, wi, wgt, &pdf)) break;
+        if (st->footprint_c < 0.0 || sa * sa > alim || n >= OR_MAX_SHADE_VERTS) {
+            or_ddgi_query(v, q, wi, E);
+            for (int c = 0; c < 3; ++c) L[c] += thr[c] * wgt[c] * E[c] / PI;
+            break;
+        }
+        int32_t hit;
+        double th;
+        if (!or_intersect(s, cur, wi, T_EPS, MISS_T, &hit, &th)) break;
+        double c3 = -dot3(s->normal + 3 * hit, wi);
+        if (c3 <= 0.0) break;
+        sa += sqrt(th * th / (pdf * c3));
+        for (int c = 0; c < 3; ++c) {
+            thr[c] *= wgt[c];
+            prev[c] = cur[c];
+            cur[c] += th * wi[c];
+        }
+        t = hit;
+        ++n;
+    }
+    if (verts) *verts = n;
 }
 
 static void res_set_empty(or_res* r, int32_t k, double M) {
@@ -867,7 +1038,7 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
                 double w[3] = {d[0] / l, d[1] / l, d[2] / l};
                 cx = dot3(nx, w);
                 cy = fabs(dot3(s->normal + 3 * tri, w));
-                radiance_at(s, v, y, tri, x, L);
+                radiance_at(s, v, y, tri, x, 0.5, 0.5, L);   /* an emitter: no glossy lobe */
             } else {
                 double u0 = or_rng(st->seed, q, frame, OR_PASS_INITIAL, c, 0);
                 double u1 = or_rng(st->seed, q, frame, OR_PASS_INITIAL, c, 1);
@@ -881,7 +1052,8 @@ int or_restir_initial(const or_scene* s, const or_volume* v, const or_settings* 
                 dist2 = t * t;
                 cx = dot3(nx, w);
                 cy = fabs(dot3(s->normal + 3 * tri, w));
-                radiance_at(s, v, y, tri, x, L);
+                radiance_at(s, v, y, tri, x, or_rng(st->seed, q, frame, OR_PASS_INITIAL, c, 4),
+                            or_rng(st->seed, q, frame, OR_PASS_INITIAL, c, 5), L);
                 if (cx > 0.0) {
                     double G = cx * cy / dist2;
                     if (G > 1.0)
@@ -928,7 +1100,7 @@ static double target_of(const or_scene* s, const or_gbuf* g, int32_t q, const or
     const double* L = r->L + 3 * k;
     double Lf[3];
     if (rq) {
-        radiance_at(s, rq, r->y + 3 * k, r->tri[k], g->pos + 3 * q, Lf);
+        radiance_at(s, rq, r->y + 3 * k, r->tri[k], g->pos + 3 * q, 0.5, 0.5, Lf);
         L = Lf;
     }
     return target_with_normal(g->pos + 3 * q, g->nrm + 3 * q, g->alb + 3 * q, r->y + 3 * k, r->ny + 3 * k, L);
@@ -1043,9 +1215,10 @@ int or_restir_spatial_rq(const or_scene* s, const or_settings* st, const or_gbuf
 /* Sec. 3.1 steps 3-4 and Eq. Algorithm: Le at x, plus one shadow ray to the
  * selected y and, if visible, rho_x / pi * (Le + L_DDGI+)(y) * min(G, 1) * W
  * with a fresh probe query at y, plus the residual estimated by the BSDF
- * ray. */
-int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_res* r,
-             const double* resid, const int32_t* pix, int32_t npix, double* rad) {
+ * ray.  In a scene with glossy triangles the radiance at y comes from the
+ * specular recursion of Sec. 3.3 (or_shade_radiance). */
+int or_shade(const or_scene* s, const or_volume* v, const or_settings* st, const or_gbuf* g, const or_res* r,
+             const double* resid, uint32_t frame, const int32_t* pix, int32_t npix, double* rad) {
     for (int32_t k = 0; k < npix; ++k) {
         int32_t q = pix ? pix[k] : k;
         rad[3 * k] = rad[3 * k + 1] = rad[3 * k + 2] = 0.0;
@@ -1068,7 +1241,10 @@ int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_r
         if (cx <= 0.0) continue;
         if (occluded(s, x, w, T_EPS, (1.0 - 1e-4) * l)) continue;
         double L[3];
-        radiance_at(s, v, y, ty, x, L);
+        if (s->glossy)
+            or_shade_radiance(s, v, st, g->eye, x, nx, y, ty, (uint32_t)q, frame, L, NULL);
+        else
+            radiance_at(s, v, y, ty, x, 0.5, 0.5, L);
         double cy = fabs(dot3(s->normal + 3 * ty, w));
         double G = cx * cy / d2;
         double Gb = G < 1.0 ? G : 1.0;

@@ -40,6 +40,9 @@ typedef struct {
     double area_total;       /* total emissive area (fp64) */
     double* inst_cur;        /* [I][12] current instance transforms (row-major 3x4) */
     double* inst_prev;       /* [I][12] the transforms of the previous update */
+    /* glossy lobe of every triangle (NULL: a diffuse scene): [T][4] =
+     * reflectance k_s.rgb and GGX roughness alpha (Sec. 3.3) */
+    const double* glossy;
 } or_scene;
 
 typedef struct {
@@ -53,6 +56,7 @@ typedef struct {
     int32_t relocate;        /* probe relocation after each blend (1) or not */
     int32_t candidate_stride;   /* >= 2: pixel (x, y) generates candidates in frame f only when
                                  * (x + y + f) mod stride == 0 (Sec. 5, subsampling); 0, 1: every pixel */
+    double footprint_c;      /* threshold c of the shading recursion (Sec. 3.3); < 0: never recurse */
 } or_settings;
 
 typedef struct {
@@ -84,6 +88,7 @@ typedef struct {          /* full per-pixel G-buffer */
     int32_t* tri;         /* [N]   -1: no valid front-facing hit */
     int32_t* prev;        /* [N]   previous-frame pixel or -1 */
     int32_t width, height;
+    double eye[3];        /* the camera position the G-buffer was rendered from */
 } or_gbuf;
 
 typedef struct {          /* reservoirs (full or compact) */
@@ -101,6 +106,9 @@ typedef struct {          /* reservoirs (full or compact) */
 #define OR_PASS_SPATIAL0 1u
 #define OR_PASS_TEMPORAL 5u
 #define OR_PASS_PROBE_ROT 7u
+#define OR_PASS_SHADE 12u          /* glossy directions of the shading recursion (cand = vertex) */
+#define OR_PASS_PROBE_GLOSSY 13u   /* glossy direction at a probe ray's hit (pixel = probe, cand = ray) */
+#define OR_MAX_SHADE_VERTS 8       /* path vertices of the shading recursion, x1 included */
 
 #ifdef __cplusplus
 extern "C" {
@@ -168,10 +176,18 @@ int or_restir_temporal_rq(const or_scene* s, const or_settings* st, const or_gbu
 int or_restir_spatial_rq(const or_scene* s, const or_settings* st, const or_gbuf* g,
                          const or_res* in, uint32_t frame, uint32_t pass,
                          const int32_t* pix, int32_t npix, const or_volume* rq, or_res* out);
-int or_shade(const or_scene* s, const or_volume* v, const or_gbuf* g, const or_res* r,
-             const double* resid, const int32_t* pix, int32_t npix, double* radiance);
+int or_shade(const or_scene* s, const or_volume* v, const or_settings* st, const or_gbuf* g, const or_res* r,
+             const double* resid, uint32_t frame, const int32_t* pix, int32_t npix, double* radiance);
 void or_radiance_batch(const or_scene* s, const or_volume* v, int32_t n, const double* y,
-                       const int32_t* tri, const double* from, double* L);
+                       const int32_t* tri, const double* from, const double* u, double* L);
+double or_ggx_D(double nh, double alpha);
+double or_ggx_G1(double nw, double alpha);
+void or_ggx_sample_h(const double n[3], double alpha, double u0, double u1, double h[3]);
+int or_glossy_sample(const double n[3], const double wo[3], const double ks[3], double alpha, double u0,
+                     double u1, double wi[3], double wgt[3], double* pdf);
+void or_shade_radiance(const or_scene* s, const or_volume* v, const or_settings* st, const double eye[3],
+                       const double x1[3], const double n1[3], const double y[3], int32_t tri, uint32_t pix,
+                       uint32_t frame, double L[3], int32_t* verts);
 void or_pt_pixel(const or_scene* s, const or_camera* cam, int32_t pix, uint32_t seed, uint32_t sample0,
                  uint32_t spp, double out[3]);
 void or_mlp_eval(const or_volume* v, const double p[3], const double n[3], double out[3]);

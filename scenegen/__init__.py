@@ -109,6 +109,7 @@ class Settings:
     mlp_seed: int = 1
     train_ema: float = 0.97      # served network: moving average of the trained weights
     mlp_bf16: int = 0            # network in bf16 (1) or fp16 (0), fp32 accumulation
+    footprint_c: float = 0.2     # path-footprint threshold c of the shading recursion (glossy scenes)
 
 
 @dataclasses.dataclass
@@ -153,6 +154,9 @@ class Scene:
     tri_instance: Optional[np.ndarray] = None     # int32[T]
     motion: Optional[Motion] = None
     emitter_toggle: int = 0
+    # glossy lobe per triangle (None: a diffuse scene): k_s.rgb and GGX
+    # roughness alpha; emitters have none
+    glossy: Optional[np.ndarray] = None           # float32[T, 4]
 
     @property
     def num_tris(self) -> int:
@@ -296,6 +300,29 @@ def tiny_room(seed: int = 1, width: int = 128, height: int = 128,
     st = Settings(rays_per_probe=64, spatial_passes=1, seed=seed)
     return Scene(name, verts, np.asarray(alb, np.float32), np.asarray(emi, np.float32),
                  grid, cams, st)
+
+
+def _tri_normals(verts):
+    n = np.cross(verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0]).astype(np.float64)
+    return n / np.linalg.norm(n, axis=1, keepdims=True)
+
+
+def tiny_room_glossy(seed: int = 1, width: int = 128, height: int = 128, frames: int = 16) -> Scene:
+    """The tiny room with microfacet materials: a near-mirror floor (GGX
+    roughness 0.05, k_s 0.5, albedo halved) and a rough glossy back wall
+    (roughness 0.3, k_s 0.25, albedo x 0.75), the rest Lambertian."""
+    sc = tiny_room(seed, width, height, frames, name="tiny_room_glossy")
+    n = _tri_normals(sc.verts)
+    c = sc.verts.mean(axis=1)
+    floor = (n[:, 1] > 0.99) & (c[:, 1] < -0.99)
+    back = (n[:, 2] > 0.99) & (c[:, 2] < -0.99)
+    gl = np.zeros((sc.num_tris, 4), np.float32)
+    alb = sc.albedo.copy()
+    gl[floor] = (0.5, 0.5, 0.5, 0.05)
+    alb[floor] *= 0.5
+    gl[back] = (0.25, 0.25, 0.25, 0.3)
+    alb[back] *= 0.75
+    return dataclasses.replace(sc, albedo=alb, glossy=gl)
 
 
 def tiny_room_1080p(seed: int = 1, frames: int = 32, learned: bool = True) -> Scene:
