@@ -279,7 +279,7 @@ def run_ours(args, ws, rank, local):
             ctx.restir_spatial(g, res, nxt, f, i, stream)
             res = nxt
             mark()
-        ctx.shade(g, res, fr.resid, fr.radiance, stream)
+        ctx.shade(g, res, fr.resid, fr.radiance, stream, frame=f)
         mark()
         fr.prev_final, fr.prev_cam = res, cam
 
@@ -687,7 +687,7 @@ def run_large(args, ws, rank, local):
             ctx.restir_spatial(gb, res, nxt, f, i, stream)
             res = nxt
             mark()
-        ctx.shade(gb, res, fr.resid, fr.radiance, stream)
+        ctx.shade(gb, res, fr.resid, fr.radiance, stream, frame=f)
         mark()
         fr.prev_final, fr.prev_cam = res, cam
 
@@ -786,7 +786,7 @@ def run_learned(args, ws, rank, local):
             ctx.restir_spatial(g, res, nxt, k, i, stream)
             res = nxt
             mark()
-        ctx.shade(g, res, fr.resid, fr.radiance, stream)
+        ctx.shade(g, res, fr.resid, fr.radiance, stream, frame=k)
         mark()
         fr.prev_final, fr.prev_cam = res, cam
 

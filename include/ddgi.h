@@ -66,6 +66,17 @@ typedef struct {
      * are the instances' identity pose; instanced triangles may not emit */
     const int32_t* tri_instance;   /* host [num_tris] or NULL */
     uint32_t num_instances;        /* <= 2^20 */
+    /* glossy materials (Sec. 3.3; NULL: every triangle is Lambertian):
+     * host [num_tris][4] = reflectance k_s.rgb (>= 0) and GGX roughness
+     * alpha in [1e-3, 1] of a microfacet lobe f_g = k_s D(h) G1(wo) G1(wi) /
+     * (4 |n.wo| |n.wi|) (GGX distribution, separable Smith masking, no
+     * Fresnel term) added to the diffuse lobe rho / pi.  It enters L_DDGI+
+     * (Eq. lddgiplus) wherever the probes are queried -- the probe update,
+     * the radiance of BSDF candidates, shading -- and shading follows it by
+     * specular recursion (ddgi_shade).  The primary vertex (the G-buffer
+     * surface) is shaded with its diffuse lobe.  Emitters may not be glossy,
+     * and a glossy scene may not use the learned target. */
+    const float* glossy;
 } ddgi_scene;
 
 /* Method parameters.  Probe volume: a counts[0] x counts[1] x counts[2] grid,
@@ -111,6 +122,10 @@ typedef struct {
                                    * empty reservoir (M = 0, no residual) and only reuse;
                                    * temporal reuse then caps the previous M at
                                    * temporal_mcap x the nominal candidate count */
+    float footprint_c;            /* threshold c of the shading recursion in glossy scenes
+                                   * (Sec. 3.3): a glossy path stops when its footprint
+                                   * exceeds c x the pixel's; 0 = the paper's 0.2,
+                                   * < 0 = never recurse (one glossy sample per query) */
     uint32_t mlp_fp32;            /* 1: a debug form of the network for gradient checks --
                                    * every network evaluation and gradient runs in fp32 on
                                    * the CUDA cores (fp32 weights, activations and
@@ -140,6 +155,9 @@ typedef struct {
     float* g1;
     float* g2;
     uint32_t width, height;
+    float eye[3];   /* the camera position the planes were rendered from; read
+                     * only by ddgi_shade in glossy scenes (the pixel footprint
+                     * of the shading recursion) */
 } ddgi_gbuf;
 
 /* Reservoirs (device): one 64-byte record per pixel, 64-byte aligned, as
@@ -305,9 +323,16 @@ ddgi_status ddgi_reservoirs_attach_normals(ddgi_ctx* ctx, const ddgi_reservoirs*
 
 /* Sec. 3.1 steps 3-4, Eq. Algorithm: radiance (device [N][4], rgb, 1) = Le(x)
  * + residual + (if the shadow ray to y is clear) rho_x / pi (Le +
- * L_DDGI+)(y) min(G, 1) W, with a fresh probe query at y. */
+ * L_DDGI+)(y) min(G, 1) W, with a fresh probe query at y.  In a glossy scene
+ * the radiance at y follows the specular recursion of Sec. 3.3: at each path
+ * vertex the emission and the diffuse half rho / pi E are added; the glossy
+ * half is traced on (one sampled direction of the lobe) while the path
+ * footprint a(x1..xn) stays within footprint_c x the pixel footprint a0 (g's
+ * eye and the G-buffer give a0), else estimated by one glossy sample of
+ * Eq. lddgiplus; at most 8 path vertices.  `frame` keys the random numbers
+ * of that recursion. */
 ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* r,
-                       const float* residual, float* radiance, void* stream);
+                       const float* residual, float* radiance, uint32_t frame, void* stream);
 
 /* Path-traced reference of Sec. 4 ("Reference" images for MAPE): unbiased
  * path tracing with next-event estimation toward area-sampled emitters,

@@ -22,6 +22,7 @@ struct ddgi_ctx {
     float4* nrm = nullptr;
     float4* alb = nullptr;
     float4* emi = nullptr;
+    float4* spec = nullptr;        // glossy lobe per triangle (k_s.rgb, alpha); null: a diffuse scene
     float4* evert = nullptr;
     float* cdf = nullptr;
     uint32_t* etri = nullptr;
@@ -170,6 +171,7 @@ SceneView scene_view(ddgi_ctx* c) {
     s.num_tris = c->T;
     s.inst_delta = c->inst_delta;
     s.max_visits = c->cfg.traversal_visit_cap ? (int)c->cfg.traversal_visit_cap : TRAV_MAX_VISITS;
+    s.spec = c->spec;
     return s;
 }
 
@@ -222,6 +224,7 @@ ddgi_status check_gbuf(ddgi_ctx* ctx, const ddgi_gbuf* g, GBufView* out) {
     out->g2 = reinterpret_cast<float4*>(g->g2);
     out->width = (int)g->width;
     out->height = (int)g->height;
+    out->eye = make_float3(g->eye[0], g->eye[1], g->eye[2]);
     return DDGI_OK;
 }
 
@@ -259,6 +262,7 @@ ddgi_status check_config(const ddgi_config* c, std::string* why) {
     if (c->spatial_neighbours > 32) { *why = "spatial_neighbours must be <= 32"; return DDGI_ERR_INVALID_ARG; }
     if (c->candidate_stride > 64) { *why = "candidate_stride must be <= 64"; return DDGI_ERR_INVALID_ARG; }
     if (c->traversal_visit_cap > (1u << 30)) { *why = "traversal_visit_cap must be <= 2^30"; return DDGI_ERR_INVALID_ARG; }
+    if (!std::isfinite(c->footprint_c)) { *why = "footprint_c must be finite"; return DDGI_ERR_INVALID_ARG; }
     if (c->spatial_radius < 1 || c->spatial_radius > 255) { *why = "spatial_radius must be 1..255"; return DDGI_ERR_INVALID_ARG; }
     if (!std::isfinite(c->normal_reject_cos) || !(c->depth_reject_frac >= 0.f)) { *why = "bad rejection thresholds"; return DDGI_ERR_INVALID_ARG; }
     const uint64_t P = (uint64_t)c->counts[0] * c->counts[1] * c->counts[2];
@@ -295,6 +299,8 @@ ddgi_status probe_params(ddgi_ctx* c, uint32_t frame, ProbeParams* p) {
     // cos^sharpness < 2^-40 below this cosine: at most R such terms, far below
     // one ulp of the blend's sums (the nearest of the rays has cos near 1)
     p->depth_cmin = c->cfg.depth_sharpness > 1.f ? (float)std::pow(0.5, 40.0 / c->cfg.depth_sharpness) : 0.f;
+    p->seed = c->cfg.seed;
+    p->frame = frame;
     return DDGI_OK;
 }
 
@@ -566,6 +572,20 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
         if (!(scene->albedo[i] >= 0.f && scene->albedo[i] <= 1.f) ||
             !(scene->emission[i] >= 0.f) || !std::isfinite(scene->emission[i]))
             return DDGI_ERR_INVALID_ARG;
+    bool glossy = false;   // some triangle has a glossy lobe
+    if (scene->glossy) {
+        for (uint32_t i = 0; i < scene->num_tris; ++i) {
+            const float* gl = scene->glossy + 4ull * i;
+            const float* e = scene->emission + 3ull * i;
+            for (int a = 0; a < 3; ++a)
+                if (!(gl[a] >= 0.f && gl[a] <= 1.f)) return DDGI_ERR_INVALID_ARG;
+            const bool has = gl[0] > 0.f || gl[1] > 0.f || gl[2] > 0.f;
+            if (has && !(gl[3] >= 1e-3f && gl[3] <= 1.f)) return DDGI_ERR_INVALID_ARG;
+            if (has && (e[0] > 0.f || e[1] > 0.f || e[2] > 0.f)) return DDGI_ERR_INVALID_ARG;   // emitters
+            glossy = glossy || has;
+        }
+        if (glossy && cfg->learned_target) return DDGI_ERR_INVALID_ARG;
+    }
     if (scene->tri_instance) {
         if (scene->num_instances == 0 || scene->num_instances > (1u << 20)) return DDGI_ERR_INVALID_ARG;
         for (uint32_t i = 0; i < scene->num_tris; ++i) {
@@ -694,6 +714,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(train_smp, 3ull * cfg->train_samples)
     ALLOC(le_stage, 3ull * ctx->E)
     ALLOC(train_sf, cfg->train_samples ? cfg->train_samples / P : 0)
+    ALLOC(spec, glossy ? T : 0)
 #undef ALLOC
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -708,6 +729,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
     up(ctx->guide, guide.data(), guide.size() * sizeof(uint32_t));
     up(ctx->sf, sf.data(), R * sizeof(float4));
+    if (glossy) up(ctx->spec, scene->glossy, T * sizeof(float4));
     if (e == cudaSuccess && scene->tri_instance) e = setup_instances(ctx, scene, bvh);
     if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->depth, 0, P * td * td * sizeof(float2));
@@ -1161,7 +1183,7 @@ ddgi_status ddgi_reservoirs_attach_normals(ddgi_ctx* ctx, const ddgi_reservoirs*
 }
 
 ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs* res,
-                       const float* residual, float* radiance, void* stream) {
+                       const float* residual, float* radiance, uint32_t frame, void* stream) {
     if (!ctx) return DDGI_ERR_INVALID_ARG;
     GBufView g;
     ResView r;
@@ -1174,9 +1196,15 @@ ddgi_status ddgi_shade(ddgi_ctx* ctx, const ddgi_gbuf* gb, const ddgi_reservoirs
     CK(ensure_hits(ctx, (size_t)n, (cudaStream_t)stream));
     MLPView mv = mlp_view(ctx);
     if (ctx->cfg.learned_target) CK(grow(ctx, &ctx->ind, &ctx->ind_cap, (size_t)n, (cudaStream_t)stream));
+    ShadeParams sp;
+    sp.seed = ctx->cfg.seed;
+    sp.frame = frame;
+    sp.footprint_c = ctx->cfg.footprint_c == 0.f ? 0.2f : ctx->cfg.footprint_c;   // the paper's c by default
+    if (ctx->spec && n > 0 && !(std::isfinite(gb->eye[0]) && std::isfinite(gb->eye[1]) && std::isfinite(gb->eye[2])))
+        return fail(ctx, DDGI_ERR_INVALID_ARG, "gbuffer eye not finite");
     CK(launch_shade(scene_view(ctx), volume_view(ctx), g, r, reinterpret_cast<const float4*>(residual),
                     reinterpret_cast<float4*>(radiance), ctx->hits, ctx->counter,
-                    ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind, (cudaStream_t)stream));
+                    ctx->cfg.learned_target ? &mv : nullptr, ctx->mlp_state, ctx->ind, sp, (cudaStream_t)stream));
     return DDGI_OK;
 }
 

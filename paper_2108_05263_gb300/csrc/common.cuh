@@ -15,6 +15,9 @@
 #define PASS_SPATIAL0 1u
 #define PASS_TEMPORAL 5u
 #define PASS_PROBE_ROT 7u
+#define PASS_SHADE 12u          // glossy directions of the shading recursion (candidate = path vertex)
+#define PASS_PROBE_GLOSSY 13u   // glossy direction at a probe ray's hit (pixel = probe, candidate = ray)
+#define SHADE_MAX_VERTS 8       // path vertices of the shading recursion, the shaded point included
 
 // device error word bits
 #define TRAV_MAX_VISITS (1 << 16)   // default node-visit cap of one ray's traversal
@@ -91,6 +94,7 @@ struct SceneView {
     uint32_t num_tris;
     const float4* inst_delta;   // per instance: rows of M_prev M_cur^-1 (current -> previous pose)
     int max_visits;             // BVH nodes one ray may visit (traversal_visit_cap)
+    const float4* spec;         // per original triangle: glossy k_s.rgb, GGX alpha; null: a diffuse scene
 };
 
 // bit of the G-buffer's previous-pixel word marking a surface on a rigid
@@ -283,6 +287,95 @@ __device__ __forceinline__ f3 radiance_at(const SceneView& s, const VolumeView& 
     return le;
 }
 
+// orthonormal basis around n (Duff et al., JCGT 2017)
+__device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
+    float sign = n.z >= 0.f ? 1.f : -1.f;
+    float a = -1.f / (sign + n.z);
+    float b = n.x * n.y * a;
+    f3 t = {1.f + sign * n.x * n.x * a, sign * b, -sign * n.x};
+    f3 bt = {b, sign + n.y * n.y * a, -n.y};
+    return t * lx + bt * ly + n * lz;
+}
+
+// ---------------------------------------------------------------------------
+// glossy lobe (Sec. 3.3): per triangle a GGX microfacet lobe with reflectance
+// k_s and roughness alpha, f_g = k_s D(h) G1(wo) G1(wi) / (4 |n.wo| |n.wi|)
+// (separable Smith masking, no Fresnel term)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ggx_D(float nh, float a) {
+    if (nh <= 0.f) return 0.f;
+    const float a2 = a * a, den = nh * nh * (a2 - 1.f) + 1.f;
+    return a2 / (DDGI_PI * den * den);
+}
+
+__device__ __forceinline__ float ggx_G1(float nw, float a) {
+    if (nw <= 0.f) return 0.f;
+    const float a2 = a * a;
+    return 2.f * nw / (nw + sqrtf(a2 + (1.f - a2) * nw * nw));
+}
+
+// One direction wi of the glossy lobe around n seen from wo: the mirror of
+// wo about a half vector drawn from D(h) (n.h).  Returns false when wi falls
+// below the surface; else g = f_g (n.wi) / (k_s pdf) and the density pdf.
+__device__ __forceinline__ bool glossy_sample(f3 n, f3 wo, float a, float u0, float u1, f3& wi, float& g,
+                                              float& pdf) {
+    const float c2 = (1.f - u0) / (1.f + (a * a - 1.f) * u0);
+    const float c = sqrtf(c2), sn = sqrtf(fmaxf(0.f, 1.f - c2));
+    float sp, cp;
+    sincospif(2.f * u1, &sp, &cp);
+    const f3 h = onb_to_world(n, sn * cp, sn * sp, c);
+    const float oh = dot(wo, h);
+    wi = h * (2.f * oh) - wo;
+    const float ni = dot(n, wi), no = dot(n, wo), nh = dot(n, h);
+    if (!(ni > 0.f && no > 0.f && nh > 0.f && oh > 0.f)) return false;
+    pdf = ggx_D(nh, a) * nh / (4.f * oh);
+    g = ggx_G1(no, a) * ggx_G1(ni, a) * oh / (no * nh);
+    return true;
+}
+
+// view-path-biased query point (Sec. 3.4) of y seen from `from`
+__device__ __forceinline__ f3 biased_point(const VolumeView& v, f3 y, f3 from) {
+    f3 d = from - y;
+    float l = length(d);
+    if (!(l > 0.f)) return y;
+    float dv = fminf(0.2f * v.min_spacing, 0.5f * l);
+    return y + d * (dv / l);
+}
+
+// The glossy half of Eq. lddgiplus at query point q (normal n, seen from
+// wo): one sample wi of the lobe, E(q, wi) read as cosine-prefiltered
+// incident radiance around wi, (1 / pi) E(q, wi) f_g (n.wi) / pdf.  With E
+// normalised so that uniform radiance L gives pi L, the factor 1 / pi
+// reflects a uniform environment exactly.
+template <int U = 1>
+__device__ __forceinline__ f3 glossy_ddgi(const VolumeView& v, f3 q, f3 n, f3 wo, float4 spec, float u0, float u1) {
+    f3 wi;
+    float g, pdf;
+    if (!glossy_sample(n, wo, spec.w, u0, u1, wi, g, pdf)) return {0.f, 0.f, 0.f};
+    const f3 E = ddgi_irradiance<U>(v, q, wi);
+    return mul(E, xyz(spec)) * (g * (1.f / DDGI_PI));
+}
+
+__device__ __forceinline__ bool is_glossy(float4 spec) { return spec.x > 0.f || spec.y > 0.f || spec.z > 0.f; }
+
+// (Le + L_DDGI+)(y, y -> from) of a glossy scene: radiance_at plus the
+// one-sample glossy half drawn with (u0, u1); the same value as radiance_at
+// on a triangle without a glossy lobe
+template <int U = 1>
+__device__ __forceinline__ f3 radiance_at_glossy(const SceneView& s, const VolumeView& v, f3 y, uint32_t tri,
+                                                 f3 from, float u0, float u1) {
+    const float4 spec = __ldg(s.spec + tri);
+    if (!is_glossy(spec)) return radiance_at<U>(s, v, y, tri, from);
+    f3 n = xyz(__ldg(s.nrm + tri));
+    const f3 back = from - y;
+    if (dot(n, back) <= 0.f) return {0.f, 0.f, 0.f};
+    f3 L = xyz(__ldg(s.emi + tri));
+    const f3 rho = xyz(__ldg(s.alb + tri));
+    const f3 q = biased_point(v, y, from);
+    if (any_pos(rho)) L = L + mul(rho, ddgi_irradiance<U>(v, q, n)) * (1.f / DDGI_PI);
+    return L + glossy_ddgi<U>(v, q, n, back * rsqrtf(dot(back, back)), spec, u0, u1);
+}
+
 // target function: luminance of rho_x / pi * L * min(G, 1) for a point y with
 // unit normal ny (only |cos| at y enters)
 __device__ __forceinline__ float target_at(f3 x, f3 nx, f3 rho, f3 y, f3 ny, f3 L) {
@@ -323,15 +416,6 @@ __device__ __forceinline__ uint32_t sample_emitter_smem(const float* cdf, const 
     return i;
 }
 
-// orthonormal basis around n (Duff et al., JCGT 2017)
-__device__ __forceinline__ f3 onb_to_world(f3 n, float lx, float ly, float lz) {
-    float sign = n.z >= 0.f ? 1.f : -1.f;
-    float a = -1.f / (sign + n.z);
-    float b = n.x * n.y * a;
-    f3 t = {1.f + sign * n.x * n.x * a, sign * b, -sign * n.x};
-    f3 bt = {b, sign + n.y * n.y * a, -n.y};
-    return t * lx + bt * ly + n * lz;
-}
 
 // reservoir record: q0 = (y, W), q1 = (L, M), q2 = (owner normal, owner
 // distance, > 0 exactly when the owner has a G-buffer hit), q3 = (triangle of

@@ -19,6 +19,13 @@ struct GBufView {
     float4* g1;
     float4* g2;
     int width, height;
+    float3 eye;   // camera position (the pixel footprint of glossy shading)
+};
+
+// shading parameters of glossy scenes (Sec. 3.3 recursion)
+struct ShadeParams {
+    uint32_t seed, frame;
+    float footprint_c;   // < 0: never recurse
 };
 
 // reservoir records: 4 float4 per pixel (see ddgi_reservoirs)
@@ -52,6 +59,7 @@ struct ProbeParams {
     float depth_sharpness;
     float depth_tmax;
     float depth_cmin;    // rays with cos <= this weigh < 2^-40 in the distance blend
+    uint32_t seed, frame;   // keys of the glossy samples at the rays' hits
 };
 
 // kernel launchers (return the launch error)
@@ -127,4 +135,4 @@ cudaError_t launch_metrics(const float4* img, const float4* ref, uint32_t n, dou
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
                          const ResView& r, const float4* resid, float4* radiance, float2* hits,
                          uint32_t* counter, const struct MLPView* mlp, struct MLPState* mst, float4* ind,
-                         cudaStream_t st);
+                         const ShadeParams& sp, cudaStream_t st);

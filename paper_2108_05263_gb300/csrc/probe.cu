@@ -28,6 +28,8 @@ __device__ __forceinline__ f3 probe_of(const VolumeView& v, int p) {
 }
 
 // one thread per (probe, ray): trace, then the radiance of Eq. probeUpdate
+// (GLOSSY: with the glossy half of L_DDGI+ toward the probe, Sec. 3.3)
+template <bool GLOSSY>
 __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, ProbeParams pp,
                                                      const float4* __restrict__ sf,
                                                      float4* __restrict__ rays, int total) {
@@ -62,6 +64,15 @@ __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, 
                 f3 y = P + w * h.t;
                 f3 E = ddgi_irradiance_biased(v, y, n, P);
                 L = L + mul(rho, E) * (1.f / DDGI_PI);
+            }
+            if (GLOSSY) {
+                const float4 spec = __ldg(s.spec + h.tri);
+                if (is_glossy(spec)) {
+                    const uint32_t cp = rng_cand(rng_prefix(pp.seed, (uint32_t)p, pp.frame, PASS_PROBE_GLOSSY),
+                                                 (uint32_t)r);
+                    const f3 q = biased_point(v, P + w * h.t, P);
+                    L = L + glossy_ddgi(v, q, n, -w, spec, u01(rng_u32_dim(cp, 0)), u01(rng_u32_dim(cp, 1)));
+                }
             }
             out.x = L.x;
             out.y = L.y;
@@ -256,7 +267,10 @@ cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const Pr
     int P = v.counts.x * v.counts.y * v.counts.z;
     int total = P * (int)p.rays;
     if (total == 0) return cudaSuccess;
-    k_probe_trace<<<(total + 127) / 128, 128, 0, st>>>(s, v, p, p.sf, rays, total);
+    if (s.spec)
+        k_probe_trace<true><<<(total + 127) / 128, 128, 0, st>>>(s, v, p, p.sf, rays, total);
+    else
+        k_probe_trace<false><<<(total + 127) / 128, 128, 0, st>>>(s, v, p, p.sf, rays, total);
     return cudaGetLastError();
 }
 

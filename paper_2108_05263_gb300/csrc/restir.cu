@@ -300,7 +300,9 @@ __device__ __forceinline__ void temporal_merge(const SceneView& s, const RestirP
 // the previous frame's records (prev) and only the merged record is stored
 // (in fin); the arithmetic is that of the two separate passes, up to the
 // compiler's multiply-add contraction in each kernel (a few ulp).
-template <bool FUSE>
+// GLOSSY: the radiance at a BSDF hit includes the one-sample glossy half of
+// L_DDGI+ (Sec. 3.3), drawn with dimensions 4 and 5 of the candidate's keys.
+template <bool FUSE, bool GLOSSY>
 __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
                                                         float4* __restrict__ resid, uint32_t frame,
@@ -387,6 +389,8 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             // learned target: Le + the network's rho max(f, 0), front faces only
             const uint32_t qi = pix * NB + (c - NL);
             L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
+        } else if constexpr (GLOSSY) {
+            L = radiance_at_glossy<4>(s, v, y, tri, x, u01(rng_u32_dim(cp, 4)), u01(rng_u32_dim(cp, 5)));
         } else {
             L = radiance_at<4>(s, v, y, tri, x);
         }
@@ -600,12 +604,25 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
         e = launch_emitter_candidates(s, v, rp, g, out, frame, st);
         if (e != cudaSuccess) return e;
     }
-    if (fuse_prev && fuse_out)
-        k_restir_initial<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(
-            s, v, rp, g, out, resid, frame, hits, ind, mlp ? mst : nullptr, nl, cam_prev, *fuse_prev, *fuse_out);
-    else
-        k_restir_initial<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(
-            s, v, rp, g, out, resid, frame, hits, ind, mlp ? mst : nullptr, nl, cam_prev, out, out);
+    const dim3 grid = tile_grid(g.width, g.height, b);
+    const MLPState* ms = mlp ? mst : nullptr;
+    const bool fuse = fuse_prev && fuse_out;
+    const ResView& fp = fuse ? *fuse_prev : out;
+    const ResView& fo = fuse ? *fuse_out : out;
+    if (s.spec) {   // a glossy scene (no network: the two are exclusive)
+        if (fuse)
+            k_restir_initial<true, true><<<grid, b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind, ms, nl,
+                                                             cam_prev, fp, fo);
+        else
+            k_restir_initial<false, true><<<grid, b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind, ms, nl,
+                                                              cam_prev, fp, fo);
+    } else if (fuse) {
+        k_restir_initial<true, false><<<grid, b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind, ms, nl,
+                                                          cam_prev, fp, fo);
+    } else {
+        k_restir_initial<false, false><<<grid, b, 0, st>>>(s, v, rp, g, out, resid, frame, hits, ind, ms, nl,
+                                                           cam_prev, fp, fo);
+    }
     return cudaGetLastError();
 }
 

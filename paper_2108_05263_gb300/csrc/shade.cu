@@ -115,12 +115,72 @@ struct ShadeQuery {
     }
 };
 
+// Radiance at the selected sample y (triangle tri) toward the shaded point x1
+// (normal n1, camera at eye) with the specular recursion of Sec. 3.3: at each
+// path vertex x_n (n >= 2) the emission and the diffuse half rho / pi E are
+// added; the glossy half is estimated by one sample of Eq. lddgiplus once the
+// path footprint a(x1..xn) exceeds c a0 (or at the last of SHADE_MAX_VERTS
+// vertices), else traced on along the sampled direction.  The footprint
+// (Bekaert et al., as the paper adopts it): sqrt(a) is the sum over the
+// path's segments of sqrt(|x_i - x_{i+1}|^2 / (p_i <n_{i+1}, -w_i>)), p_1 the
+// Lambertian density cos / pi at x1, p_i the glossy density beyond;
+// a0 = |x0 - x1|^2 / (4 pi <n1, -w0>).  Keys: (seed, pixel, frame,
+// PASS_SHADE, vertex n, dimension 0 / 1).
+__device__ f3 shade_radiance(const SceneView& s, const VolumeView& v, const ShadeParams& sp, f3 eye, f3 x1, f3 n1,
+                             f3 y, uint32_t tri, uint32_t pix) {
+    const f3 e0 = eye - x1, d1 = y - x1;
+    const float l0 = length(e0), l1 = length(d1);
+    const float a0 = l0 * l0 / (4.f * DDGI_PI * (dot(n1, e0) / l0));
+    const float alim = sp.footprint_c * a0;
+    const f3 w1 = d1 * (1.f / l1);
+    const float p1 = dot(n1, w1) * (1.f / DDGI_PI);
+    float sa = sqrtf(l1 * l1 / (p1 * fabsf(dot(xyz(__ldg(s.nrm + tri)), w1))));
+    const uint32_t prefix = rng_prefix(sp.seed, pix, sp.frame, PASS_SHADE);
+    f3 thr = {1.f, 1.f, 1.f}, L = {0.f, 0.f, 0.f}, prev = x1, cur = y;
+    uint32_t t = tri;
+#pragma unroll 1
+    for (int n = 2;; ++n) {
+        const f3 nrm = xyz(__ldg(s.nrm + t));
+        const f3 back = prev - cur;
+        if (dot(nrm, back) <= 0.f) break;
+        L = L + mul(thr, xyz(__ldg(s.emi + t)));
+        const f3 rho = xyz(__ldg(s.alb + t));
+        const float4 spec = __ldg(s.spec + t);
+        const bool glossy = is_glossy(spec);
+        if (!any_pos(rho) && !glossy) break;
+        const f3 q = biased_point(v, cur, prev);
+        if (any_pos(rho)) L = L + mul(thr, mul(rho, ddgi_irradiance(v, q, nrm))) * (1.f / DDGI_PI);
+        if (!glossy) break;
+        const uint32_t cp = rng_cand(prefix, (uint32_t)n);
+        const f3 wo = back * rsqrtf(dot(back, back));
+        f3 wi;
+        float g, pdf;
+        if (!glossy_sample(nrm, wo, spec.w, u01(rng_u32_dim(cp, 0)), u01(rng_u32_dim(cp, 1)), wi, g, pdf)) break;
+        const f3 wgt = xyz(spec) * g;
+        if (sp.footprint_c < 0.f || sa * sa > alim || n >= SHADE_MAX_VERTS) {
+            L = L + mul(thr, mul(wgt, ddgi_irradiance(v, q, wi))) * (1.f / DDGI_PI);
+            break;
+        }
+        const Hit h = trace_bvh<false>(s, Ray{cur, wi, DDGI_T_EPS, DDGI_MISS_T});
+        if (h.tri == DDGI_NONE) break;
+        const float c3 = -dot(xyz(__ldg(s.nrm + h.tri)), wi);
+        if (!(c3 > 0.f)) break;
+        sa += sqrtf(h.t * h.t / (pdf * c3));
+        thr = mul(thr, wgt);
+        prev = cur;
+        cur = cur + wi * h.t;
+        t = h.tri;
+    }
+    return L;
+}
+
+template <bool GLOSSY>
 __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
                                                const float4* __restrict__ resid,
                                                float4* __restrict__ radiance,
                                                const float2* __restrict__ vis,
                                                const float4* __restrict__ ind,
-                                               const MLPState* __restrict__ mst) {
+                                               const MLPState* __restrict__ mst, ShadeParams sp) {
     // rows bottom-up: the shadow-ray pass read the pixels' planes top-down,
     // so its last rows are still in L2
     int px = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,6 +213,8 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
                     if (mst != nullptr && mst->use_mlp) {
                         bool front = dot(xyz(__ldg(s.nrm + ty)), x - y) > 0.f;
                         L = front ? xyz(__ldg(s.emi + ty)) + xyz(__ldg(ind + pix)) : f3{0.f, 0.f, 0.f};
+                    } else if constexpr (GLOSSY) {
+                        L = shade_radiance(s, v, sp, f3{g.eye.x, g.eye.y, g.eye.z}, x, nx, y, ty, pix);
                     } else {
                         L = radiance_at(s, v, y, ty, x);
                     }
@@ -181,7 +243,7 @@ cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView
 cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView& g,
                          const ResView& r, const float4* resid, float4* radiance, float2* hits,
                          uint32_t* counter, const MLPView* mlp, MLPState* mst, float4* ind,
-                         cudaStream_t st) {
+                         const ShadeParams& sp, cudaStream_t st) {
     if (g.width == 0 || g.height == 0) return cudaSuccess;
     cudaError_t e = launch_trace<ShadowGen, true>(s, ShadowGen{g, r}, (uint32_t)g.width * g.height,
                                                   counter, hits, st);
@@ -191,7 +253,11 @@ cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView
         if (e != cudaSuccess) return e;
     }
     dim3 b(32, 4);   // measured best for this kernel (16 x 8 slower)
-    k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
-                                                           mlp ? mst : nullptr);
+    if (s.spec)
+        k_shade<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
+                                                                     mlp ? mst : nullptr, sp);
+    else
+        k_shade<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
+                                                                      mlp ? mst : nullptr, sp);
     return cudaGetLastError();
 }

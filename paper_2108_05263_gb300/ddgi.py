@@ -32,7 +32,8 @@ _i3 = C.c_int32 * 3
 
 class Scene(C.Structure):
     _fields_ = [("num_tris", C.c_uint32), ("vertices", C.c_void_p), ("albedo", C.c_void_p),
-                ("emission", C.c_void_p), ("tri_instance", C.c_void_p), ("num_instances", C.c_uint32)]
+                ("emission", C.c_void_p), ("tri_instance", C.c_void_p), ("num_instances", C.c_uint32),
+                ("glossy", C.c_void_p)]
 
 
 class Config(C.Structure):
@@ -46,7 +47,7 @@ class Config(C.Structure):
                 ("learned_target", C.c_uint32), ("train_samples", C.c_uint32), ("train_lr", C.c_float),
                 ("mlp_seed", C.c_uint32), ("train_ema", C.c_float), ("probe_relocation", C.c_uint32),
                 ("mlp_bf16", C.c_uint32), ("candidate_stride", C.c_uint32),
-                ("mlp_fp32", C.c_uint32), ("traversal_visit_cap", C.c_uint32)]
+                ("footprint_c", C.c_float), ("mlp_fp32", C.c_uint32), ("traversal_visit_cap", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -56,7 +57,7 @@ class Camera(C.Structure):
 
 class GBuf(C.Structure):
     _fields_ = [("g0", C.c_void_p), ("g1", C.c_void_p), ("g2", C.c_void_p),
-                ("width", C.c_uint32), ("height", C.c_uint32)]
+                ("width", C.c_uint32), ("height", C.c_uint32), ("eye", _f3)]
 
 
 class Res(C.Structure):
@@ -128,7 +129,7 @@ def load(path: Optional[str] = None):
     L.restir_initial_temporal.argtypes = [vp, C.POINTER(GBuf), C.POINTER(C.c_float), C.POINTER(Res),
                                           C.POINTER(Res), C.POINTER(Res), vp, C.c_uint32, vp]
     L.ddgi_reservoirs_attach_normals.argtypes = [vp, C.POINTER(Res), vp]
-    L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, vp]
+    L.ddgi_shade.argtypes = [vp, C.POINTER(GBuf), C.POINTER(Res), vp, vp, C.c_uint32, vp]
     L.ddgi_reference_accumulate.argtypes = [vp, C.POINTER(Camera), C.c_uint32, C.c_uint32, vp, vp, vp]
     L.ddgi_image_metrics.argtypes = [vp, vp, C.c_uint32, vp, C.c_uint32, vp, vp]
     L.ddgi_image_metrics_static.argtypes = [vp, vp, C.c_uint32, vp, vp]
@@ -168,15 +169,18 @@ def _stream(stream) -> C.c_void_p:
 class GBuffer:
     """Three [N, 4] float32 planes (see ddgi_gbuf)."""
 
-    def __init__(self, width: int, height: int, device="cuda", planes=None):
+    def __init__(self, width: int, height: int, device="cuda", planes=None, eye=None):
         self.width, self.height = width, height
         n = width * height
         if planes is None:
             planes = [torch.empty((n, 4), dtype=torch.float32, device=device) for _ in range(3)]
         self.g0, self.g1, self.g2 = planes
+        # camera position the planes were rendered from (Context.gbuffer sets it)
+        self.eye = np.zeros(3, np.float32) if eye is None else np.asarray(eye, np.float32)
 
     def c(self) -> GBuf:
-        return GBuf(self.g0.data_ptr(), self.g1.data_ptr(), self.g2.data_ptr(), self.width, self.height)
+        return GBuf(self.g0.data_ptr(), self.g1.data_ptr(), self.g2.data_ptr(), self.width, self.height,
+                    _f3(*[float(a) for a in self.eye]))
 
     def numpy(self):
         return tuple(t.cpu().numpy() for t in (self.g0, self.g1, self.g2))
@@ -260,6 +264,7 @@ def config_from(grid, settings) -> Config:
     c.probe_relocation = int(getattr(settings, "probe_relocation", 0))
     c.mlp_bf16 = int(getattr(settings, "mlp_bf16", 0))
     c.candidate_stride = int(getattr(settings, "candidate_stride", 1))
+    c.footprint_c = float(getattr(settings, "footprint_c", 0.2))
     c.mlp_fp32 = int(getattr(settings, "mlp_fp32", 0))
     c.traversal_visit_cap = int(getattr(settings, "traversal_visit_cap", 0))
     return c
@@ -268,7 +273,7 @@ def config_from(grid, settings) -> Config:
 class Context:
     """Owns a ddgi_ctx (scene BVH, emitter table, probe maps, probe rays)."""
 
-    def __init__(self, verts, albedo, emission, grid, settings, tri_instance=None):
+    def __init__(self, verts, albedo, emission, grid, settings, tri_instance=None, glossy=None):
         L = load()
         self.L = L
         self._v = np.ascontiguousarray(verts, np.float32)
@@ -279,6 +284,9 @@ class Context:
             self._ti = np.ascontiguousarray(tri_instance, np.int32)
             sc.tri_instance = self._ti.ctypes.data
             sc.num_instances = int(self._ti.max(initial=-1)) + 1
+        if glossy is not None:
+            self._gl = np.ascontiguousarray(glossy, np.float32)
+            sc.glossy = self._gl.ctypes.data
         self.cfg = config_from(grid, settings)
         self.settings = settings
         h = C.c_void_p()
@@ -291,7 +299,7 @@ class Context:
     @staticmethod
     def from_scene(sc, settings=None) -> "Context":
         return Context(sc.verts, sc.albedo, sc.emission, sc.grid, settings or sc.settings,
-                       getattr(sc, "tri_instance", None))
+                       getattr(sc, "tri_instance", None), getattr(sc, "glossy", None))
 
     def close(self):
         if getattr(self, "h", None):
@@ -382,6 +390,7 @@ class Context:
     def gbuffer(self, cam, prev_cam, out: GBuffer, stream=None):
         c = camera(cam)
         pc = camera(prev_cam) if prev_cam is not None else None
+        out.eye = np.asarray(cam.pos, np.float32)
         g = out.c()
         self._check("ddgi_gbuffer", self.L.ddgi_gbuffer(self.h, C.byref(c), C.byref(pc) if pc else None,
                                                         C.byref(g), _stream(stream)))
@@ -423,10 +432,10 @@ class Context:
                     self.L.ddgi_reservoirs_attach_normals(self.h, C.byref(rc), _stream(stream)))
 
     def shade(self, g: GBuffer, res: Reservoirs, residual: torch.Tensor, radiance: torch.Tensor,
-              stream=None):
+              stream=None, frame: int = 0):
         gc, rc = g.c(), res.c()
         self._check("ddgi_shade", self.L.ddgi_shade(self.h, C.byref(gc), C.byref(rc), _ptr(residual),
-                                                    _ptr(radiance), _stream(stream)))
+                                                    _ptr(radiance), frame, _stream(stream)))
 
     def reference_accumulate(self, cam, sample0: int, spp: int, accum: torch.Tensor,
                              mean: Optional[torch.Tensor] = None, stream=None):
@@ -545,7 +554,7 @@ class Frame:
             ctx.restir_spatial(g, res, nxt, frame, i, stream)
             res = nxt
         rad = self.radiance if out is None else out
-        ctx.shade(g, res, self.resid, rad, stream)
+        ctx.shade(g, res, self.resid, rad, stream, frame=frame)
         self.prev_final, self.prev_cam = res, cam
         self.cur ^= 1
         return rad

@@ -437,6 +437,94 @@ def test_dynamic_64_frames_track_the_per_frame_oracle(dd, orc):
     assert all(trend[k] == -trend[k + 1] != 0 for k in range(7)), trend
 
 
+# ---------------------------------------------------------------------------
+# glossy materials (Sec. 3.3): glossy term of L_DDGI+, specular recursion
+# ---------------------------------------------------------------------------
+
+def test_glossy_probe_trace_parity(dd, orc):
+    """Probe rays on the glossy room (near-mirror floor, rough glossy back
+    wall): the radiance at each hit includes the one-sample glossy half of
+    L_DDGI+ toward the probe; from the same probe maps (teacher forced, after
+    two oracle updates) every ray matches the oracle."""
+    sc = scenegen.tiny_room_glossy()
+    ctx = dd.Context.from_scene(sc)
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    for f in range(2):
+        orc.probe_update(S, vol, f)
+    _vol_to_gpu(ctx, vol)
+    ctx.probe_trace(2)
+    got = ctx.probe_rays_get()
+    ref = orc.probe_trace(S, vol, 2)
+    same = np.sign(got[..., 3]) == np.sign(ref[..., 3])
+    assert _frac(same) >= 0.999
+    assert _frac(_close(got[..., :3][same], ref[..., :3][same], 1e-5).all(-1)) >= 0.999
+    # the glossy surfaces really contribute: rays that hit them differ from
+    # the same update with the lobes removed
+    import dataclasses
+    plain = orc.Scene(dataclasses.replace(sc, glossy=None))
+    ref0 = orc.probe_trace(plain, vol, 2)
+    assert np.abs(ref[..., :3] - ref0[..., :3]).max() > 1e-2
+    assert ctx.get_status() == dd.OK
+
+
+@pytest.mark.parametrize("c", [0.2, 1e4])
+def test_whole_frame_chain_glossy(dd, orc, c):
+    """The frame chain on the glossy room: probe updates with the glossy
+    term, BSDF candidates whose cached radiance carries it, and shading with
+    the specular recursion -- at the paper's threshold c = 0.2 and at c = 1e4,
+    where every glossy path is traced on to the 8-vertex cap."""
+    import dataclasses
+    sc = scenegen.tiny_room_glossy(width=96, height=64, frames=4)
+    sc = dataclasses.replace(sc, settings=dataclasses.replace(sc.settings, footprint_c=c))
+    stats = _chain(dd, orc, sc, 4)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
+def test_glossy_recursion_changes_the_image(dd):
+    """The footprint threshold matters where it should: on the glossy room a
+    large c (paths traced on) and c < 0 (one glossy sample at the first
+    vertex) give different images, and both stay finite."""
+    import dataclasses
+    base = scenegen.tiny_room_glossy(width=96, height=64, frames=2)
+    out = {}
+    for c in (1e4, -1.0):
+        sc = dataclasses.replace(base, settings=dataclasses.replace(base.settings, footprint_c=c))
+        ctx = dd.Context.from_scene(sc)
+        fr = dd.Frame(ctx, 96, 64, sc.settings.spatial_passes)
+        for f in range(2):
+            rad = fr.render(f, sc.cameras[f]).cpu().numpy()[:, :3]
+        assert np.all(np.isfinite(rad)) and ctx.get_status() == dd.OK
+        out[c] = rad
+    assert np.abs(out[1e4] - out[-1.0]).max() > 1e-3
+
+
+def test_glossy_fused_chain(dd, orc):
+    """The fused initial + temporal pass on the glossy room."""
+    sc = scenegen.tiny_room_glossy(width=64, height=48, frames=4)
+    stats = _chain(dd, orc, sc, 4, fused=True)
+    for f, (tags, rad) in enumerate(stats):
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
+
+
+def test_glossy_scene_argument_errors(dd):
+    """Glossy emitters, out-of-range lobes and a glossy scene with the
+    learned target are refused at creation."""
+    import dataclasses
+    sc = scenegen.tiny_room_glossy(width=16, height=16, frames=1)
+    bad = sc.glossy.copy()
+    emitter = int(np.flatnonzero(sc.emission.max(1) > 0)[0])
+    bad[emitter] = (0.3, 0.3, 0.3, 0.2)
+    for gl in (bad, np.where(sc.glossy > 0, 0.0, sc.glossy) + np.array([0.5, 0.5, 0.5, 0.0], np.float32)):
+        with pytest.raises(dd.DDGIError):
+            dd.Context.from_scene(dataclasses.replace(sc, glossy=gl.astype(np.float32)))
+    learned = dataclasses.replace(sc, settings=dataclasses.replace(sc.settings, learned_target=1,
+                                                                   train_samples=1024))
+    with pytest.raises(dd.DDGIError):
+        dd.Context.from_scene(learned)
+
+
 def _fused_vs_two_passes(dd, sc, nframes):
     """Twin contexts render the same frames, one with restir_initial +
     restir_temporal, the other with restir_initial_temporal: the same
