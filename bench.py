@@ -142,30 +142,57 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` (or per run of a pass) from the
-    committed ncu summary, if it was taken on the current kernel sources (else
+def _profile_value(fname: str, key: str):
+    """Per-launch (or per-pass) figure `key` from a committed ncu summary
+    under profiles/, if it was taken on the current kernel sources (else
     None)."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     src = kernel_source_hash()
     for ln in open(path):
         parts = ln.split()
-        if len(parts) >= 3 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
+        if len(parts) >= 3 and not ln.startswith("#") and parts[0] == key and parts[1] == src:
             return float(parts[2])
     return None
 
 
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` (or per run of a pass)."""
+    return _profile_value("dram_traffic.txt", kernel)
+
+
+def ncu_instructions(kernel: str):
+    """Warp instructions executed (smsp__inst_executed.sum) per launch of
+    `kernel` (or per run of a pass)."""
+    return _profile_value("instructions.txt", kernel)
+
+
+# instruction issue peak of the GPU: every SM has 4 schedulers, each issuing
+# at most one warp instruction per cycle
+ISSUE_PER_SM_CLK = 4
+
+
 # ---------------------------------------------------------------------------
-# algorithmic bytes per pixel of each pass (compulsory HBM traffic)
-# ---------------------------------------------------------------------------
-# G-buffer planes 16 B each (position+distance, normal+triangle, albedo+
-# previous pixel), reservoir record 64 B (it carries its pixel's normal and
-# distance), residual and radiance 16 B/px.  Neighbour reads of the spatial
-# pass and BVH / probe-map reads are cache traffic (scene, BVH and maps are
-# ~12 MB, L2-resident) and are not counted.
+# algorithmic bytes per pixel of each pass: the method's compulsory HBM
+# traffic for a 48-byte reservoir and 16-byte G-buffer planes (the per-pass
+# figures of the hot-path scope): initial = G 48 in, reservoir 48 + residual
+# 16 out; temporal = current G 48 + previous G 32 + previous and current
+# reservoirs 96 in, 48 out; fused = the two minus the 96 bytes the fusion
+# keeps on chip; spatial = 144 per pass (its neighbour reads are L2 reuse);
+# shade = G 48 + reservoir 48 + residual 16 in, radiance 16 out.  This
+# library's records are 64 bytes (they carry the owner's normal and distance,
+# so reuse reads no previous G-buffer): LAYOUT_BYTES_PER_PX is what its
+# kernels must move.  BVH, scene and probe-map reads are L2-resident cache
+# traffic (~12 MB) and are not counted.
 BYTES_PER_PX = {
+    "restir_initial": 112,
+    "restir_temporal": 224,
+    "restir_initial_temporal": 240,
+    "restir_spatial": 144,
+    "ddgi_shade": 128,
+}
+LAYOUT_BYTES_PER_PX = {
     "restir_initial": 48 + 64 + 16,             # G in; record + residual out
     "restir_temporal": 64 + 32 + 64 + 64,       # cur record, G (pos, albedo+prev), prev record; out
     "restir_initial_temporal": 48 + 64 + 64 + 16,   # G, previous record in; record + residual out
@@ -329,8 +356,9 @@ def run_ours(args, ws, rank, local):
         entry = {"ms": round(ms, 4)}
         if key in BYTES_PER_PX:
             gbs = BYTES_PER_PX[key] * N / (ms * 1e-3) / 1e9
+            lgbs = LAYOUT_BYTES_PER_PX[key] * N / (ms * 1e-3) / 1e9
             entry.update({"bytes": BYTES_PER_PX[key] * N, "gbs": round(gbs, 1),
-                          "hbm_frac": round(gbs / hbm, 4)})
+                          "hbm_frac": round(gbs / hbm, 4), "layout_hbm_frac": round(lgbs / hbm, 4)})
         pass_report[p] = entry
     if two_pass is not None:
         rep2 = {}
@@ -353,12 +381,30 @@ def run_ours(args, ws, rank, local):
                                               "k_restir_initial<fused temporal>",
                    "restir_temporal": "k_restir_temporal", "restir_spatial": "k_restir_spatial",
                    "ddgi_shade": "k_trace<ShadowGen> + k_shade"}[dom_key]
-        roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": ncu_traffic(dom_key),
-                "note": "algorithmic bytes = compulsory per-pixel plane traffic of the pass, timed by CUDA "
-                        "events around its launches; its time goes into BVH traversal and candidate "
-                        "arithmetic on L2-resident scene data (see the per-pass list)"}
+        hbm_roof = {"achieved": round(achieved, 1), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(dom_key)}
+        inst = ncu_instructions(dom_key)
+        if inst is not None:
+            # the pass is bound by instruction issue (BVH traversal and
+            # candidate arithmetic on L2-resident scene data), not by HBM
+            sm_mhz = clocks.get("sm_mhz") or 2070.0
+            peak_issue = torch.cuda.get_device_properties(dev).multi_processor_count * ISSUE_PER_SM_CLK * \
+                sm_mhz * 1e6
+            ach = inst / (per_pass[dom] * 1e-3)
+            roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "alu",
+                    "achieved": round(ach / 1e9, 1), "peak": round(peak_issue / 1e9, 1),
+                    "unit": "G warp-instructions/s", "frac": round(ach / peak_issue, 4),
+                    "traffic": hbm_roof["traffic"], "hbm": hbm_roof,
+                    "note": "achieved = warp instructions the pass executes per frame (ncu "
+                            "smsp__inst_executed.sum summed over its kernels, profiles/instructions.txt, "
+                            "same kernel sources) / the pass's CUDA-event time; peak = SMs x 4 schedulers x "
+                            "1 instruction / cycle x the SM clock sampled during the run; hbm = the "
+                            "pass's algorithmic bytes (240 B/px) against the measured copy peak"}
+        else:
+            roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "hbm", **hbm_roof,
+                    "note": "algorithmic bytes = compulsory per-pixel plane traffic of the pass, timed by "
+                            "CUDA events around its launches; its time goes into BVH traversal and "
+                            "candidate arithmetic on L2-resident scene data (see the per-pass list)"}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None}
@@ -368,11 +414,10 @@ def run_ours(args, ws, rank, local):
            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_frame, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded procedural apartment standing in for the paper's scenes)",
-           "config": {"workload": WORKLOAD if (W, H) == (1920, 1080) else
-                      WORKLOAD.replace("1920x1080", f"{W}x{H}").replace("1080p", f"{H}p"), "l2": "inputs larger than L2: 16 distinct 1080p "
-                      "G-buffers (0.8 GB) cycled; ~0.8 GB of per-pixel planes touched per frame",
-                      "parallelism": "replicas" if ws > 1 else "single GPU",
-                      "gbuffer_ms_untimed": round(gb_ms, 4)},
+           "config": workload_config(ws) if (W, H) == (1920, 1080) else
+                     dict(workload_config(ws), workload=WORKLOAD.replace("1920x1080", f"{W}x{H}").replace(
+                         "1080p", f"{H}p")),
+           "gbuffer_ms_untimed": round(gb_ms, 4),
            "passes": pass_report, "roofline": roof, "clocks": clocks,
            "gpu_launches": K * launches_per_frame(st.spatial_passes, fused), "device_status": int(status)}
     if two_pass is not None:
@@ -553,6 +598,7 @@ class OracleSample:
         self.g = oracle.GBuffer.from_planes(*gp, self.W, self.H)
         self.res = oracle.Reservoirs.from_planes(*scenegen.synthetic_reservoirs(sc, self.W * self.H, 31), scene=self.S)
         self.zero_resid = np.zeros((self.W * self.H, 3))
+        self.vols = []   # one scratch volume per thread for the probe blends, made outside the timing
 
     def _pixels_run(self, pix):
         o, S, g, res = self.o, self.S, self.g, self.res
@@ -562,11 +608,11 @@ class OracleSample:
             o.restir_spatial(S, g, res, 1, i, pix=pix)
         o.shade(S, self.vol, g, res, self.zero_resid, pix=pix)
 
-    def _probes_run(self, probes):
+    def _probes_run(self, job):
+        k, probes = job
         o = self.o
         rays = o.probe_trace(self.S, self.vol, 1, probes=probes)
-        v2 = self.vol.copy()
-        o.probe_blend(v2, rays, 1, self.S.settings, probes=probes)
+        o.probe_blend(self.vols[k], rays, 1, self.S.settings, probes=probes)
 
     def pixels(self, npix, threads=1):
         """Seconds per pixel; with threads > 1 the pixels are split over that
@@ -576,12 +622,24 @@ class OracleSample:
         return self._timed(self._pixels_run, np.array_split(pix, threads)) / npix
 
     def probes(self, nprobes, threads=1):
+        while len(self.vols) < threads:
+            self.vols.append(self.vol.copy())
         probes = self.rng.choice(self.sc.grid.num_probes, nprobes, replace=False).astype(np.int32)
-        return self._timed(self._probes_run, np.array_split(probes, threads)) / nprobes
+        parts = [(k, p) for k, p in enumerate(np.array_split(probes, threads)) if len(p)]
+        return self._timed(self._probes_run, parts) / nprobes
+
+    def step(self, threads):
+        """One reference step: SAMPLE_PIXELS_PER_THREAD pixels and
+        SAMPLE_PROBES_PER_THREAD probes per thread; returns (seconds per
+        pixel, seconds per probe, wall seconds)."""
+        t0 = time.perf_counter()
+        t_px = self.pixels(SAMPLE_PIXELS_PER_THREAD * threads, threads)
+        t_pr = self.probes(SAMPLE_PROBES_PER_THREAD * threads, threads)
+        return t_px, t_pr, time.perf_counter() - t0
 
     @staticmethod
     def _timed(fn, parts):
-        parts = [p for p in parts if len(p)]
+        parts = [p for p in parts if len(p[1] if isinstance(p, tuple) else p)]
         t0 = time.perf_counter()
         if len(parts) == 1:
             fn(parts[0])
@@ -602,25 +660,35 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+# the oracle's sample unit, shared by the CPU baseline and the reference arm:
+# per host thread, this many random pixels (initial + temporal + spatial
+# passes + shade) and probes (trace + blend), extrapolated to a frame
+SAMPLE_PIXELS_PER_THREAD = 64     # fewer pixels per call: the wrappers' fixed cost shows (2-4x at 16)
+SAMPLE_PROBES_PER_THREAD = 1
+
+
 def cpu_baseline(sc, budget_s=12.0):
-    """The oracle on the host cores: one thread per core over a bounded
-    sample of the frame; the single-thread rate of the same sample size is
-    reported beside it."""
+    """The oracle on the host cores: reference steps (one sample unit per
+    thread, one thread per core) repeated for about budget_s seconds, their
+    per-pixel and per-probe times pooled; the single-thread rate of a pixel
+    sample is reported beside it."""
     s = OracleSample(sc)
     T = host_cores()
-    est = s.pixels(8)
-    npix = int(max(16 * T, min(4096 * T, 0.45 * budget_s * T / max(est, 1e-6))))
-    t_px = s.pixels(npix, T)
-    nprobes = int(max(T, min(16 * T, 0.3 * budget_s * T / max(256 * est / 2, 1e-6))))
-    t_pr = s.probes(nprobes, T)
-    n1 = max(8, npix // (4 * T))
-    t_px1 = s.pixels(n1)
+    px, pr, steps, wall = [], [], 0, 0.0
+    while wall < budget_s or steps < 2:
+        t_px, t_pr, w = s.step(T)
+        px.append(t_px)
+        pr.append(t_pr)
+        steps += 1
+        wall += w
+    t_px, t_pr = float(np.mean(px)), float(np.mean(pr))
+    t_px1 = s.pixels(max(8, SAMPLE_PIXELS_PER_THREAD))
     return {"value": round(s.frame_ms(t_px, t_pr), 1), "unit": "ms/frame", "cores": T,
             "kind": "oracle",
-            "sample": f"{npix} random pixels of a synthetic 1080p G-buffer (initial + temporal + "
-                      f"{sc.settings.spatial_passes} spatial + shade) and {nprobes} probes (trace + "
-                      f"blend) of the apartment on {T} threads, extrapolated to 2,073,600 pixels + "
-                      f"{sc.grid.num_probes} probes",
+            "sample": f"{steps} steps of {SAMPLE_PIXELS_PER_THREAD * T} random pixels of a synthetic 1080p "
+                      f"G-buffer (initial + temporal + {sc.settings.spatial_passes} spatial + shade) and "
+                      f"{SAMPLE_PROBES_PER_THREAD * T} probes (trace + blend) of the apartment on {T} threads "
+                      f"({wall:.1f} s), extrapolated to 2,073,600 pixels + {sc.grid.num_probes} probes",
             "per_pixel_ms": round(t_px * 1e3, 5), "per_probe_ms": round(t_pr * 1e3, 4),
             "single_thread_per_pixel_ms": round(t_px1 * 1e3, 4)}
 
@@ -819,30 +887,46 @@ def run_learned(args, ws, rank, local):
     print(json.dumps(out))
 
 
+def workload_config(ws: int) -> dict:
+    """The `config` of the metric's workload, the same for both arms."""
+    return {"workload": WORKLOAD, "l2": "inputs larger than L2: 16 distinct 1080p G-buffers (0.8 GB) "
+                                          "cycled; ~0.8 GB of per-pixel planes touched per frame",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 def run_reference(args, ws, rank):
-    """The oracle as the reference arm: every step is a bounded sample of the
-    frame (32 pixels + 1 probe per host core, one thread per core),
-    extrapolated to ms per 1080p frame."""
+    """The oracle as the reference arm: every step is one sample unit per host
+    thread (SAMPLE_PIXELS_PER_THREAD pixels, SAMPLE_PROBES_PER_THREAD probes,
+    one thread per core), the unit the CPU baseline pools; `value` is the ms
+    per 1080p frame those steps extrapolate to, `ms_per_step` the measured
+    wall time of a step."""
     if rank != 0:
         return
     import scenegen
     sc = scenegen.apartment(frames=1)
     s = OracleSample(sc)
     T = host_cores()
-    vals = []
+    px, pr, walls = [], [], []
     for k in range(args.warmup + args.steps):
-        v = s.frame_ms(s.pixels(32 * T, T), s.probes(T, T))
+        t_px, t_pr, w = s.step(T)
         if k >= args.warmup:
-            vals.append(v)
-    v = float(np.mean(vals))
+            px.append(t_px)
+            pr.append(t_pr)
+            walls.append(w)
+    v = s.frame_ms(float(np.mean(px)), float(np.mean(pr)))
+    sample = (f"per step: {SAMPLE_PIXELS_PER_THREAD * T} random pixels of a synthetic 1080p G-buffer (initial + "
+              f"temporal + {sc.settings.spatial_passes} spatial + shade) and {SAMPLE_PROBES_PER_THREAD * T} probes "
+              f"(trace + blend) on {T} threads; the frame time is extrapolated to 2,073,600 pixels + "
+              f"{sc.grid.num_probes} probes")
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms/frame",
-           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1),
+           "value_kind": "extrapolated from the steps' per-pixel and per-probe times",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * float(np.mean(walls)), 2),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "data": "synthetic (seeded procedural apartment standing in for the paper's scenes)",
+           "config": workload_config(ws),
            "cpu_baseline": {"value": round(v, 1), "unit": "ms/frame", "cores": T, "kind": "oracle",
-                            "sample": f"per step: {32 * T} random pixels (initial + temporal + spatial + "
-                                      f"shade) and {T} probes (trace + blend) on {T} threads, extrapolated "
-                                      f"to a frame"},
+                            "sample": sample},
            "e2e": {"value": round(v, 1), "unit": "ms/frame", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -563,7 +563,8 @@ def restir_temporal(scene: Scene, g: GBuffer, gp: GBuffer, prev_cam_pos, cur: Re
     queried afresh from that volume at the current pixel."""
     _need_full(g, cur)
     _need_full(gp, prev)
-    if np.any(g.prev >= gp.tri.shape[0]):
+    prev_px = g.prev if pix is None else g.prev[np.asarray(pix)]
+    if np.any(prev_px >= gp.tri.shape[0]):
         raise ValueError("previous-pixel indices beyond the previous G-buffer")
     st = _settings(scene, settings)
     pr, pp = _pixarg(pix)
