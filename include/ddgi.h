@@ -273,7 +273,8 @@ ddgi_status ddgi_gbuffer(ddgi_ctx* ctx, const ddgi_camera* cam, const ddgi_camer
  * reservoir), weighted by target / mixture density in area measure; one is
  * kept by weighted reservoir sampling, W = w_sum / (M target(y)).  residual
  * (device [N][4]) receives the BSDF-ray estimate rho_x L(y) max(0, 1 - 1/G)
- * of the residual transport. */
+ * of the residual transport (on the way it carries the emitter candidates'
+ * state between the pass's kernels). */
 ddgi_status restir_initial(ddgi_ctx* ctx, const ddgi_gbuf* g, const ddgi_reservoirs* out,
                            float* residual, uint32_t frame, void* stream);
 
@@ -297,10 +298,11 @@ ddgi_status restir_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g,
  * restir_initial into some buffer c followed by restir_temporal(c, prev)
  * into out: the same arithmetic, up to a few ulp where the compiler fuses a
  * multiply and an add differently in the one kernel (a selection can
- * differ where two weights tie that closely).  scratch (N records) receives the
- * emitter candidates' partial state and holds no reservoirs afterwards.
- * out, scratch and prev must be distinct; prev may hold a different number
- * of pixels; prev_cam_pos: host float[3]. */
+ * differ where two weights tie that closely).  scratch (N records) is not
+ * written (the emitter candidates hand their state to the BSDF candidates
+ * through `residual`); it is validated and kept for compatibility.  out,
+ * scratch and prev must be distinct; prev may hold a different number of
+ * pixels; prev_cam_pos: host float[3]. */
 ddgi_status restir_initial_temporal(ddgi_ctx* ctx, const ddgi_gbuf* g, const float* prev_cam_pos,
                                     const ddgi_reservoirs* scratch, const ddgi_reservoirs* prev,
                                     const ddgi_reservoirs* out, float* residual, uint32_t frame,

@@ -92,9 +92,10 @@ struct CandidateStream {
     float invM;
     float wsum;
     Sel sel;
-    __device__ __forceinline__ void add(uint32_t c, uint32_t cp, f3 y, f3 L, uint32_t tri, float d2, float cx, float cy,
+    // returns whether the candidate was taken
+    __device__ __forceinline__ bool add(uint32_t c, uint32_t cp, f3 y, f3 L, uint32_t tri, float d2, float cx, float cy,
                                         float pL) {
-        if (cx <= 0.f) return;
+        if (cx <= 0.f) return false;
         float pB = cx * (1.f / DDGI_PI) * cy / d2;
         float pmix = ((float)NL * pL + (float)NB * pB) * invM;
         float G = cx * cy / d2;
@@ -108,21 +109,86 @@ struct CandidateStream {
             sel.tri = tri;
             sel.tag = pix * 64u + c;
             sel.p = ph;
+            return true;
         }
+        return false;
     }
 };
 
+// Emitter candidate c of pixel x (key prefix cp): the emitter drawn by area,
+// the point y on it, its triangle, the unit direction's cosines and the
+// radiance toward x.  The emitter kernel runs it for every candidate, the
+// BSDF kernel once more for the candidate the emitter part selected (the
+// same code and random numbers: the same values).
+struct EmitterCand {
+    f3 y, L;
+    uint32_t tri, e;
+    float d2, cx, cy;
+};
+
+// the point of emitter candidate cp on emitter record (q0..q3) and what it
+// sends toward x
+template <bool REFLECT>
+__device__ __forceinline__ bool emitter_point(const SceneView& s, const VolumeView& v, f3 x, f3 nx, uint32_t cp,
+                                              float4 q0, float4 q1, float4 q2, float4 q3, EmitterCand& ec) {
+    float u1 = u01(rng_u32_dim(cp, 1)), u2 = u01(rng_u32_dim(cp, 2));
+    ec.tri = __float_as_uint(q0.w);
+    float sq = sqrtf(u1);
+    float b1 = sq * (1.f - u2), b2 = sq * u2;
+    ec.y = xyz(q0) + xyz(q1) * b1 + xyz(q2) * b2;
+    f3 d = ec.y - x;
+    ec.d2 = dot(d, d);
+    if (ec.d2 <= 0.f) return false;
+    f3 w = d * rsqrtf(ec.d2);
+    ec.cx = dot(nx, w);
+    const float cyn = dot(xyz(q3), w);
+    ec.cy = fabsf(cyn);
+    if (REFLECT) {
+        ec.L = radiance_at(s, v, ec.y, ec.tri, x);
+    } else {
+        // pure emitter: one-sided Le toward x
+        ec.L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
+    }
+    return true;
+}
+
+template <bool REFLECT, bool SMEM>
+__device__ __forceinline__ bool emitter_candidate(const SceneView& s, const VolumeView& v, f3 x, f3 nx, uint32_t cp,
+                                                  const float4* e_vert, const float* e_cdf, const uint32_t* e_guide,
+                                                  EmitterCand& ec) {
+    const float u0 = u01(rng_u32_dim(cp, 0));
+    float4 q0, q1, q2, q3;
+    if (SMEM) {
+        // four planes of E records each (SoA: consecutive emitters on
+        // consecutive 16-byte bank groups)
+        const uint32_t E = s.num_emitters;
+        ec.e = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u0);
+        q0 = e_vert[ec.e];
+        q1 = e_vert[E + ec.e];
+        q2 = e_vert[2 * E + ec.e];
+        q3 = e_vert[3 * E + ec.e];
+    } else {
+        ec.e = sample_emitter(s, u0);
+        const float4* er = s.evert + 4 * (size_t)ec.e;
+        ld32(er, q0, q1);
+        ld32(er + 2, q2, q3);
+    }
+    return emitter_point<REFLECT>(s, v, x, nx, cp, q0, q1, q2, q3, ec);
+}
+
 // Candidates of step 1, emitter part, for one pixel: points uniform in
-// emitter area.  The stream's state after them (selected y, its radiance and
-// target, triangle, tag, running weight sum) is left in the pixel's output
-// record for k_restir_initial, which continues the same stream with the BSDF
-// rays; the split keeps this loop free of the probe query's registers
-// (REFLECT: some emitter also reflects, so its candidates need the query
-// too).  SMEM: the emitter records, cumulative areas and guide table are read
-// from shared memory (e_cdf, e_guide, e_vert), else from the scene tables.
+// emitter area.  The stream's state after them -- running weight sum, the
+// selected candidate's target and index -- is left in the pixel's 16-byte
+// residual slot (state) for k_restir_initial, which recomputes that one
+// candidate's point and radiance and continues the stream with the BSDF rays
+// (it overwrites the slot with the residual); the split keeps this loop free
+// of the probe query's registers (REFLECT: some emitter also reflects, so its
+// candidates need the query too).  SMEM: the emitter records, cumulative
+// areas and guide table are read from shared memory (e_cdf, e_guide,
+// e_vert), else from the scene tables.
 template <bool REFLECT, bool SMEM>
 __device__ __forceinline__ void emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
-                                                   const GBufView& g, const ResView& out, uint32_t frame,
+                                                   const GBufView& g, float4* __restrict__ state, uint32_t frame,
                                                    uint32_t pix, const float4* e_vert, const float* e_cdf,
                                                    const uint32_t* e_guide) {
     const float4 g1 = g.g1[pix];
@@ -142,63 +208,28 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
     cs.sel.y = cs.sel.L = f3{0.f, 0.f, 0.f};
     const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
     const float inv_area = 1.f / s.area_total;
+    uint32_t esel = 0u;
     for (uint32_t c = 0; c < cs.NL; ++c) {
         const uint32_t cp = rng_cand(prefix, c);
-        float u0 = u01(rng_u32_dim(cp, 0)), u1 = u01(rng_u32_dim(cp, 1));
-        float u2 = u01(rng_u32_dim(cp, 2));
-        float4 q0, q1, q2, q3;
-        if (SMEM) {
-            // four planes of E records each (SoA: consecutive emitters on
-            // consecutive 16-byte bank groups)
-            const uint32_t E = s.num_emitters;
-            const uint32_t e = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u0);
-            q0 = e_vert[e];
-            q1 = e_vert[E + e];
-            q2 = e_vert[2 * E + e];
-            q3 = e_vert[3 * E + e];
-        } else {
-            const uint32_t e = sample_emitter(s, u0);
-            const float4* er = s.evert + 4 * (size_t)e;
-            ld32(er, q0, q1);
-            ld32(er + 2, q2, q3);
-        }
-        const uint32_t tri = __float_as_uint(q0.w);
-        float sq = sqrtf(u1);
-        float b1 = sq * (1.f - u2), b2 = sq * u2;
-        const f3 y = xyz(q0) + xyz(q1) * b1 + xyz(q2) * b2;
-        f3 d = y - x;
-        float d2 = dot(d, d);
-        if (d2 <= 0.f) continue;
-        f3 w = d * rsqrtf(d2);
-        float cx = dot(nx, w);
-        float cyn = dot(xyz(q3), w);
-        f3 L;
-        if (REFLECT) {
-            L = radiance_at(s, v, y, tri, x);
-        } else {
-            // pure emitter: one-sided Le toward x
-            L = cyn < 0.f ? f3{q1.w, q2.w, q3.w} : f3{0.f, 0.f, 0.f};
-        }
-        cs.add(c, cp, y, L, tri, d2, cx, fabsf(cyn), inv_area);
+        EmitterCand ec;
+        if (!emitter_candidate<REFLECT, SMEM>(s, v, x, nx, cp, e_vert, e_cdf, e_guide, ec)) continue;
+        if (cs.add(c, cp, ec.y, ec.L, ec.tri, ec.d2, ec.cx, ec.cy, inv_area)) esel = ec.e;
     }
-    float4* rec = out.rec + 4 * (size_t)pix;
-    st32(rec, make_float4(cs.sel.y.x, cs.sel.y.y, cs.sel.y.z, cs.wsum),
-         make_float4(cs.sel.L.x, cs.sel.L.y, cs.sel.L.z, cs.sel.p));
-    // the second half whole (q2 unused here): a 16-byte store would leave the
-    // 32-byte sector partial, which the memory then reads to merge
-    st32(rec + 2, make_float4(0.f, 0.f, 0.f, 0.f),
-         make_float4(__uint_as_float(cs.sel.tri), __uint_as_float(cs.sel.tag), 0.f, 0.f));
+    // the selected candidate's index (tag = pixel * 64 + candidate) or none,
+    // and its emitter
+    const uint32_t csel = cs.sel.tri == DDGI_NONE ? DDGI_NONE : cs.sel.tag - pix * 64u;
+    state[pix] = make_float4(cs.wsum, cs.sel.p, __uint_as_float(csel), __uint_as_float(esel));
 }
 
 // one thread per pixel, emitter tables from global memory (L1); rows run
 // bottom-up, so that k_restir_initial, top-down, starts on rows still in L2
 template <bool REFLECT>
 __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView v, RestirParams rp, GBufView g,
-                                                         ResView out, uint32_t frame) {
+                                                         float4* __restrict__ state, uint32_t frame) {
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
-    emitter_candidates<REFLECT, false>(s, v, rp, g, out, frame, (uint32_t)py * g.width + px, nullptr, nullptr,
+    emitter_candidates<REFLECT, false>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, nullptr, nullptr,
                                        nullptr);
 }
 
@@ -210,7 +241,7 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
 constexpr int kEmitTileW = 64, kEmitTileH = 8;   // measured best (32 x 16, 128 x 4, 16 x 32 slower)
 template <bool REFLECT>
 __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
-                                                              ResView out, uint32_t frame) {
+                                                              float4* __restrict__ state, uint32_t frame) {
     extern __shared__ float4 e_smem[];
     const uint32_t E = s.num_emitters, G = s.guide_size;
     float4* e_vert = e_smem;
@@ -227,7 +258,7 @@ __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, Volum
         const int bx = t % tiles_x, by = tiles_y - 1 - t / tiles_x;
         const int px = bx * kEmitTileW + tx, py = by * kEmitTileH + ty;
         if (px >= g.width || py >= g.height) continue;
-        emitter_candidates<REFLECT, true>(s, v, rp, g, out, frame, (uint32_t)py * g.width + px, e_vert, e_cdf,
+        emitter_candidates<REFLECT, true>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, e_vert, e_cdf,
                                           e_guide);
     }
 }
@@ -353,16 +384,21 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
     cs.NL = NL;
     cs.NB = NB;
     cs.invM = 1.f / (float)M;
+    const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
+    // the emitter part's state: weight sum, selected target, candidate index
+    // and emitter; the stream needs only the first two until its end, so the
+    // selected emitter candidate is rebuilt after the BSDF candidates, and
+    // only if none of them displaced it
+    uint32_t csel = DDGI_NONE, esel = 0u;
     if (NL > 0) {
-        float4 a, b;
-        ld32(rec, a, b);
-        const float4 t = rec[3];
-        cs.wsum = a.w;
-        cs.sel.y = xyz(a);
-        cs.sel.L = xyz(b);
-        cs.sel.p = b.w;
-        cs.sel.tri = __float_as_uint(t.x);
-        cs.sel.tag = __float_as_uint(t.y);
+        const float4 st = resid[pix];
+        csel = __float_as_uint(st.z);
+        esel = __float_as_uint(st.w);
+        cs.wsum = st.x;
+        cs.sel.p = st.y;
+        cs.sel.tri = csel != DDGI_NONE ? 0u : DDGI_NONE;   // 0: the emitter candidate, rebuilt below
+        cs.sel.tag = 0u;
+        cs.sel.y = cs.sel.L = f3{0.f, 0.f, 0.f};
     } else {
         cs.wsum = 0.f;
         cs.sel.tri = DDGI_NONE;
@@ -370,7 +406,6 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         cs.sel.p = 0.f;
         cs.sel.y = cs.sel.L = f3{0.f, 0.f, 0.f};
     }
-    const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
     const float inv_area = 1.f / s.area_total;
     f3 res = {0.f, 0.f, 0.f};
     for (uint32_t c = NL; c < M; ++c) {
@@ -400,16 +435,35 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         }
         cs.add(c, cp, y, L, tri, d2, cx, fabsf(cyn), pL);
     }
-    resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
+    // (the residual is stored last: a store before them would keep the loads
+    // below -- emitter record, previous frame's record -- from overlapping)
+    if (csel != DDGI_NONE && cs.sel.tag == 0u && cs.sel.tri == 0u) {
+        // still the emitter part's selection (a BSDF candidate sets a tag >=
+        // pixel * 64 + NL > 0): its record only, no emitter search
+        const float4* er = s.evert + 4 * (size_t)esel;
+        float4 q0, q1, q2, q3;
+        ld32(er, q0, q1);
+        ld32(er + 2, q2, q3);
+        EmitterCand ec;
+        if (s.emitters_reflect)
+            emitter_point<true>(s, v, x, nx, rng_cand(prefix, csel), q0, q1, q2, q3, ec);
+        else
+            emitter_point<false>(s, v, x, nx, rng_cand(prefix, csel), q0, q1, q2, q3, ec);
+        cs.sel.y = ec.y;
+        cs.sel.L = ec.L;
+        cs.sel.tri = ec.tri;
+        cs.sel.tag = pix * 64u + csel;
+    }
     const Sel& sel = cs.sel;
     if (sel.tri == DDGI_NONE) {
         emit(make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, (float)M), geo,
              rec_tail(DDGI_NONE, 0u, make_float2(0.f, 0.f)), g2);
-        return;
+    } else {
+        float W = sel.p > 0.f ? cs.wsum / ((float)M * sel.p) : 0.f;
+        emit(make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
+             rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))), g2);
     }
-    float W = sel.p > 0.f ? cs.wsum / ((float)M * sel.p) : 0.f;
-    emit(make_float4(sel.y.x, sel.y.y, sel.y.z, W), make_float4(sel.L.x, sel.L.y, sel.L.z, (float)M), geo,
-         rec_tail(sel.tri, sel.tag, oct_encode(xyz(__ldg(s.nrm + sel.tri)))), g2);
+    resid[pix] = make_float4(res.x, res.y, res.z, 0.f);
 }
 
 __global__ void __launch_bounds__(256) k_restir_temporal(SceneView s, RestirParams rp, GBufView g,
@@ -535,7 +589,7 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 // the emitter-candidate pass: the shared-memory kernel when the emitter
 // tables fit beside enough resident threads, else the per-pixel kernel
 cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
-                                      const GBufView& g, const ResView& out, uint32_t frame, cudaStream_t st) {
+                                      const GBufView& g, float4* state, uint32_t frame, cudaStream_t st) {
     const size_t smem = sizeof(float4) * 4 * (size_t)s.num_emitters +
                         sizeof(float) * (size_t)s.num_emitters + sizeof(uint32_t) * (size_t)s.guide_size;
     static int dev_sms = 0, max_smem = 0;
@@ -554,15 +608,15 @@ cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, c
         if (per_sm > 0) {
             const int tiles = ((g.width + kEmitTileW - 1) / kEmitTileW) * ((g.height + kEmitTileH - 1) / kEmitTileH);
             const int grid = std::min(tiles, dev_sms * per_sm);
-            kern<<<grid, 512, smem, st>>>(s, v, rp, g, out, frame);
+            kern<<<grid, 512, smem, st>>>(s, v, rp, g, state, frame);
             return cudaGetLastError();
         }
     }
     dim3 b(16, 8);
     if (s.emitters_reflect)
-        k_restir_emitters<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+        k_restir_emitters<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, state, frame);
     else
-        k_restir_emitters<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, out, frame);
+        k_restir_emitters<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, rp, g, state, frame);
     return cudaGetLastError();
 }
 
@@ -589,7 +643,7 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
     e = launch_trace<BsdfGen, false>(s, gen, (uint32_t)g.width * g.height * rp.n_bsdf, counter, hits, st);
     if (e != cudaSuccess) return e;
     if (fork) {
-        if ((e = launch_emitter_candidates(s, v, rp, g, out, frame, side)) != cudaSuccess) return e;
+        if ((e = launch_emitter_candidates(s, v, rp, g, resid, frame, side)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
     }
     if (mlp) {
@@ -601,7 +655,7 @@ cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const
     if (fork) {
         if ((e = cudaStreamWaitEvent(st, ev_join, 0)) != cudaSuccess) return e;
     } else if (nl > 0) {
-        e = launch_emitter_candidates(s, v, rp, g, out, frame, st);
+        e = launch_emitter_candidates(s, v, rp, g, resid, frame, st);
         if (e != cudaSuccess) return e;
     }
     const dim3 grid = tile_grid(g.width, g.height, b);
