@@ -14,6 +14,7 @@ there is no data exchange between ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -33,6 +34,10 @@ WORKLOAD = ("apartment-1080p: 65,180 triangles (400 boxes, walls with doors), 10
             "texels, 31 emitter + 1 BSDF candidates, temporal (M cap 20) + 2 spatial passes x 5 "
             "neighbours (30 px)")
 METRIC = "ms/frame 1080p ReSTIR+DDGI (% HBM roofline); MSE at equal time, MLP vs probes"
+GLOSSY_WORKLOAD = ("apartment-glossy-1080p: the metric's apartment with GGX materials (polished floor, "
+                   "roughness 0.15, k_s 0.35; glossy furniture tops, roughness 0.3, k_s 0.3): the glossy half "
+                   "of L_DDGI+ in the probe update and the BSDF candidates, shading with specular recursion "
+                   "(footprint threshold c = 0.2, at most 8 vertices)")
 
 
 def parse():
@@ -54,10 +59,13 @@ def parse():
     ap.add_argument("--two-pass", action="store_true",
                     help="run restir_initial and restir_temporal as two passes (default: the fused "
                          "restir_initial_temporal, the same computation)")
-    ap.add_argument("--workload", default="apartment", choices=["apartment", "large", "learned"],
+    ap.add_argument("--workload", default="apartment", choices=["apartment", "large", "learned", "glossy"],
                     help="apartment: the 1080p metric workload; large: the 4K multi-storey building "
                          "with 500 moving boxes and the bf16 learned target; learned: the 24-triangle "
-                         "box at 1080p with the fp16 learned target (neither is the metric)")
+                         "box at 1080p with the fp16 learned target; glossy: the apartment with GGX "
+                         "materials (none but apartment is the metric)")
+    ap.add_argument("--footprint-c", type=float, default=0.2,
+                    help="glossy workload: footprint threshold of the shading recursion")
     return ap.parse_args()
 
 
@@ -241,7 +249,12 @@ def run_ours(args, ws, rank, local):
     build.build()
     ddgi.load()
     W, H = (int(v) for v in args.res.lower().split("x"))
-    sc = scenegen.apartment(width=W, height=H, frames=args.frames)
+    glossy = args.workload == "glossy"
+    if glossy:
+        sc = scenegen.apartment_glossy(width=W, height=H, frames=args.frames)
+        sc.settings = dataclasses.replace(sc.settings, footprint_c=args.footprint_c)
+    else:
+        sc = scenegen.apartment(width=W, height=H, frames=args.frames)
     st = sc.settings
     ctx = ddgi.Context.from_scene(sc)
     N = W * H
@@ -383,7 +396,7 @@ def run_ours(args, ws, rank, local):
                    "ddgi_shade": "k_trace<ShadowGen> + k_shade"}[dom_key]
         hbm_roof = {"achieved": round(achieved, 1), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(dom_key)}
-        inst = ncu_instructions(dom_key)
+        inst = None if glossy else ncu_instructions(dom_key)   # counts of the diffuse kernels
         if inst is not None:
             # the pass is bound by instruction issue (BVH traversal and
             # candidate arithmetic on L2-resident scene data), not by HBM
@@ -414,7 +427,8 @@ def run_ours(args, ws, rank, local):
            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_frame, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded procedural apartment standing in for the paper's scenes)",
-           "config": workload_config(ws) if (W, H) == (1920, 1080) else
+           "config": dict(workload_config(ws), workload=GLOSSY_WORKLOAD + f", c = {args.footprint_c}")
+                     if glossy else workload_config(ws) if (W, H) == (1920, 1080) else
                      dict(workload_config(ws), workload=WORKLOAD.replace("1920x1080", f"{W}x{H}").replace(
                          "1080p", f"{H}p")),
            "gbuffer_ms_untimed": round(gb_ms, 4),
@@ -450,10 +464,12 @@ def run_ours(args, ws, rank, local):
                       "h2d_bytes_per_step": 48 * N, "d2h_bytes_per_step": 16 * N,
                       "path": "ddgi.HostFramePipeline through the C ABI: pinned host G-buffer in, host radiance "
                               "out, every frame, copies overlapped with the previous / next frame"}
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and not glossy:
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=12.0)
-    if rank == 0 and not args.no_equal_time and ws == 1:
+    if rank == 0 and not args.no_equal_time and ws == 1 and not glossy:
         out["equal_time_mse"] = equal_time_mse(dev, args.equal_time_frames)
+    if glossy:
+        out["metric_workload"] = False   # a side line: the metric is the diffuse apartment
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -938,7 +954,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload in ("large", "learned"):
+    if args.workload in ("large", "learned"):   # (glossy runs the metric's frame loop on its own scene)
         if rank == 0:
             (run_large if args.workload == "large" else run_learned)(args, ws, rank, local)
         return

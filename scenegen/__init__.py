@@ -325,6 +325,26 @@ def tiny_room_glossy(seed: int = 1, width: int = 128, height: int = 128, frames:
     return dataclasses.replace(sc, albedo=alb, glossy=gl)
 
 
+def apartment_glossy(seed: int = 7, width: int = 1920, height: int = 1080, frames: int = 16) -> Scene:
+    """The apartment with microfacet materials: a polished floor (GGX
+    roughness 0.15, k_s 0.35, albedo x 0.6) and glossy tops on the furniture
+    and the wall ends (every other upward-facing surface below the ceiling:
+    roughness 0.3, k_s 0.3, albedo x 0.7)."""
+    sc = apartment(seed, width, height, frames)
+    n = _tri_normals(sc.verts)
+    c = sc.verts.mean(axis=1)
+    up = n[:, 1] > 0.99
+    floor = up & (c[:, 1] < 0.01)
+    tops = up & ~floor & (c[:, 1] < 2.95) & (sc.emission.max(axis=1) == 0)
+    gl = np.zeros((sc.num_tris, 4), np.float32)
+    alb = sc.albedo.copy()
+    gl[floor] = (0.35, 0.35, 0.35, 0.15)
+    alb[floor] *= 0.6
+    gl[tops] = (0.3, 0.3, 0.3, 0.3)
+    alb[tops] *= 0.7
+    return dataclasses.replace(sc, name="apartment_glossy", albedo=alb, glossy=gl)
+
+
 def tiny_room_1080p(seed: int = 1, frames: int = 32, learned: bool = True) -> Scene:
     """The tiny room rendered at 1920x1080 with the learned target: 65,536
     self-training samples per frame, Adam lr 1e-3."""

@@ -525,6 +525,64 @@ def test_glossy_scene_argument_errors(dd):
         dd.Context.from_scene(learned)
 
 
+@pytest.mark.parametrize("c", [0.2, 1e4])
+def test_apartment_glossy_sampled(dd, orc, c):
+    """The glossy apartment at 1920x1080 (polished floor, glossy furniture
+    tops): probe rays with the glossy term (8 probes), restir_initial (BSDF
+    candidates whose cached radiance carries the glossy sample) and
+    ddgi_shade with the specular recursion, teacher forced on the GPU's
+    G-buffer, probe maps and reservoirs, on 2048 sampled pixels; at the
+    paper's c = 0.2 and at c = 1e4 (glossy paths traced on to the cap)."""
+    import dataclasses
+    import torch
+    sc = scenegen.apartment_glossy(frames=1)
+    sc = dataclasses.replace(sc, settings=dataclasses.replace(sc.settings, footprint_c=c))
+    W, H = sc.cameras[0].width, sc.cameras[0].height
+    n = W * H
+    ctx = dd.Context.from_scene(sc)
+    S = orc.Scene(sc)
+    for f in range(2):
+        ctx.probe_update(f)
+    irr, dep, off, upd = ctx.probe_state_get()
+    vol = orc.Volume(sc.grid)
+    vol.irr[:], vol.depth[:], vol.offset[:] = irr[..., :3], dep, off[:, :3]
+    vol.updates = upd
+    # probe rays of frame 2 from these maps
+    ctx.probe_trace(2)
+    rays = ctx.probe_rays_get()
+    probes = np.sort(np.random.default_rng(9).choice(sc.grid.num_probes, 8, replace=False)).astype(np.int32)
+    rref = orc.probe_trace(S, vol, 2, probes=probes)
+    got = rays[probes]
+    same = np.sign(got[..., 3]) == np.sign(rref[..., 3])
+    assert _frac(same) >= 0.999
+    assert _frac(_close(got[..., :3][same], rref[..., :3][same], 1e-5).all(-1)) >= 0.999
+    cam = sc.cameras[0]
+    g = dd.GBuffer(W, H)
+    ctx.gbuffer(cam, None, g)
+    out = dd.Reservoirs(n)
+    resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(g, out, resid, 2)
+    rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.shade(g, out, resid, rad, frame=2)
+    rec, got_resid, got_rad = out.numpy(), resid.cpu().numpy(), rad.cpu().numpy()
+    assert ctx.get_status() == dd.OK
+    og = orc.GBuffer.from_planes(*g.numpy(), W, H, eye=cam.pos)
+    rng = np.random.default_rng(23)
+    glossy_px = np.flatnonzero((og.tri >= 0) & (sc.glossy[np.maximum(og.tri, 0), 0] > 0))
+    sample = np.sort(np.concatenate([rng.choice(np.flatnonzero(og.tri >= 0), 1024, replace=False),
+                                     rng.choice(glossy_px, 1024, replace=False)]))
+    sample = np.unique(sample).astype(np.int32)
+    ref, rres = orc.restir_initial(S, vol, og, 2, pix=sample)
+    _res_compare(rec[sample], ref, what=f"glossy initial@1080p c={c}")
+    assert _frac(_close(got_resid[sample, :3], rres, 1e-5).all(1)) >= 0.999
+    ores = _oracle_res_full(orc, S, rec)
+    shref = orc.shade(S, vol, og, ores, got_resid[:, :3].astype(np.float64), pix=sample, frame=2)
+    assert _frac(_close(got_rad[sample, :3], shref, 1e-5).all(1)) >= 0.999
+    # the selected samples really include glossy surfaces
+    f = dd.Reservoirs.fields(rec[sample])
+    assert np.mean(sc.glossy[np.maximum(f["tri"], 0), 0] > 0) > 0.05
+
+
 def _fused_vs_two_passes(dd, sc, nframes):
     """Twin contexts render the same frames, one with restir_initial +
     restir_temporal, the other with restir_initial_temporal: the same
