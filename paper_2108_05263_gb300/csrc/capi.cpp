@@ -35,6 +35,7 @@ struct ddgi_ctx {
     float4* offset = nullptr;
     float4* rays = nullptr;
     float4* sf = nullptr;
+    uint32_t* sf_order = nullptr;  // probe rays in an order that keeps a warp's directions together
     uint32_t* err = nullptr;
     uint32_t* counter = nullptr;   // work counter of the persistent trace kernel
     float2* hits = nullptr;        // per-ray hit records (t, triangle), grown on demand
@@ -290,6 +291,7 @@ CamView cam_view(const ddgi_camera* c) {
 
 ddgi_status probe_params(ddgi_ctx* c, uint32_t frame, ProbeParams* p) {
     p->sf = c->sf;
+    p->order = c->sf_order;
     p->rays = c->cfg.rays_per_probe;
     frame_rotation(c->cfg.seed, frame, p->R);
     p->hysteresis = c->updates == 0 ? 0.f : c->cfg.hysteresis;
@@ -680,6 +682,33 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
         ph = 2.0 * 3.14159265358979323846 * (ph - std::floor(ph));
         sf[i] = make_float4((float)(r * std::cos(ph)), (float)(r * std::sin(ph)), (float)z, 0.f);
     }
+    // the order in which a probe's threads take its rays: by the Morton code
+    // of each direction's octahedral map, so that every 32 consecutive rays
+    // form a compact patch of the sphere (the per-frame rotation moves all of
+    // them rigidly and keeps the patches); a spherical Fibonacci index step
+    // turns the azimuth by the golden angle, which scatters a warp's rays
+    std::vector<uint32_t> sf_order(R);
+    {
+        std::vector<std::pair<uint64_t, uint32_t>> key(R);
+        for (uint32_t i = 0; i < R; ++i) {
+            double x = sf[i].x, y = sf[i].y, zz = sf[i].z;
+            double s = std::fabs(x) + std::fabs(y) + std::fabs(zz);
+            double u = x / s, w = y / s;
+            if (zz < 0.0) {
+                double fu = (1.0 - std::fabs(w)) * (u >= 0.0 ? 1.0 : -1.0);
+                double fw = (1.0 - std::fabs(u)) * (w >= 0.0 ? 1.0 : -1.0);
+                u = fu;
+                w = fw;
+            }
+            uint32_t qu = (uint32_t)std::min(65535.0, std::floor((u + 1.0) * 32768.0));
+            uint32_t qw = (uint32_t)std::min(65535.0, std::floor((w + 1.0) * 32768.0));
+            uint64_t m = 0;
+            for (int b = 0; b < 16; ++b) m |= (uint64_t)((qu >> b) & 1u) << (2 * b) | (uint64_t)((qw >> b) & 1u) << (2 * b + 1);
+            key[i] = {m, i};
+        }
+        std::sort(key.begin(), key.end());
+        for (uint32_t i = 0; i < R; ++i) sf_order[i] = key[i].second;
+    }
 
     const size_t ti = cfg->irr_texels + 2, td = cfg->depth_texels + 2;
     const size_t P = ctx->P;
@@ -700,6 +729,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(offset, P)
     ALLOC(rays, P * R)
     ALLOC(sf, R)
+    ALLOC(sf_order, R)
     ALLOC(err, 4)
     ALLOC(counter, 4)
     ALLOC(mlp_params, MLP_NPARAM)
@@ -729,6 +759,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
     up(ctx->guide, guide.data(), guide.size() * sizeof(uint32_t));
     up(ctx->sf, sf.data(), R * sizeof(float4));
+    up(ctx->sf_order, sf_order.data(), R * sizeof(uint32_t));
     if (glossy) up(ctx->spec, scene->glossy, T * sizeof(float4));
     if (e == cudaSuccess && scene->tri_instance) e = setup_instances(ctx, scene, bvh);
     if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));

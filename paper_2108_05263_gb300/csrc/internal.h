@@ -52,6 +52,7 @@ struct RestirParams {
 
 struct ProbeParams {
     const float4* sf;    // spherical Fibonacci directions, [rays]
+    const uint32_t* order;   // ray traced by each thread of a probe: directions of a warp lie together
     uint32_t rays;
     float R[9];          // per-frame rotation of the ray set
     float hysteresis;    // effective (0 on the first update)

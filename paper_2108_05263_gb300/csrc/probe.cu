@@ -36,7 +36,10 @@ __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, 
     int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= total) return;
     int R = (int)pp.rays;
-    int p = tid / R, r = tid - p * R;
+    int p = tid / R;
+    // thread -> ray: consecutive threads take neighbouring directions, so a
+    // warp traverses one patch of the sphere (the results go to the ray's slot)
+    int r = (int)__ldg(pp.order + (tid - p * R));
     f3 P = probe_of(v, p);
     f3 w = rotate(pp, __ldg(sf + r));
     // one origin per 32-lane warp, directions over the sphere: per-thread
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, 
             out.z = L.z;
         }
     }
-    rays[tid] = out;
+    rays[(size_t)p * R + r] = out;
 }
 
 // padded-tile index of the texel whose value border texel (X, Y) repeats
