@@ -1098,43 +1098,70 @@ def large(dd, orc):
     return sc, ctx, S
 
 
+def _threaded(fn, items, parts=16):
+    """fn over chunks of items on host threads (the C oracle releases the
+    interpreter lock): the brute-force oracle over ~1M triangles."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = [c for c in np.array_split(np.asarray(items), parts) if len(c)]
+    with ThreadPoolExecutor(len(chunks)) as ex:
+        return list(ex.map(fn, chunks))
+
+
+def _cat_res(orc, parts):
+    r = orc.Reservoirs(sum(p.W.shape[0] for p in parts))
+    for name in orc.Reservoirs.FIELDS:
+        getattr(r, name)[:] = np.concatenate([getattr(p, name) for p in parts])
+    return r
+
+
 def test_large_geometry_sampled(dd, orc, large):
-    """After 3 updates of the 500 moving boxes: sampled 4K G-buffer (hits,
-    distances, previous pixels) and the rays of 2 probes match the oracle's
-    brute force over the ~1M triangles."""
+    """After 3 updates of the 500 moving boxes: sampled 4K G-buffer (1024
+    pixels: hits, distances, previous pixels) and the rays of 4 probes (1024
+    rays) match the oracle's brute force over the ~1M triangles.  Ties are
+    counted, not folded into a lower fraction: a hit on another triangle at
+    the same distance (|dt| <= 1e-5 t) is a closest-hit tie; for probe rays
+    that includes the coincident, oppositely facing faces of boxes resting on
+    the slabs, where one side records a front face and the other a back face
+    at the same t (measured: 10 of 1024 rays)."""
     sc, ctx, S = large
     cam, pc = sc.cameras[2], sc.cameras[1]
     g = dd.GBuffer(cam.width, cam.height)
     ctx.gbuffer(cam, pc, g)
     g0, g1, g2 = g.numpy()
     rng = np.random.default_rng(41)
-    sample = np.sort(rng.choice(cam.width * cam.height, 48, replace=False)).astype(np.int32)
-    ref = orc.gbuffer(S, cam, pc, pix=sample)
-    tri = g1[sample, 3].view(np.int32)
-    same = tri == ref.tri
-    assert _frac(same) >= 0.97
-    assert _frac(_close(g0[sample][same, 3], ref.dist[same], 1e-5)) >= 0.97
+    sample = np.sort(rng.choice(cam.width * cam.height, 1024, replace=False)).astype(np.int32)
+    parts = _threaded(lambda c: orc.gbuffer(S, cam, pc, pix=c), sample)
+    ref_tri = np.concatenate([p.tri for p in parts])
+    ref_dist = np.concatenate([p.dist for p in parts])
+    ref_prev = np.concatenate([p.prev for p in parts])
+    tri, dist = g1[sample, 3].view(np.int32), g0[sample, 3]
+    same = tri == ref_tri
+    tie = ~same & (tri >= 0) & (ref_tri >= 0) & (np.abs(dist - ref_dist) <= 1e-5 * ref_dist)
+    assert _frac(same | tie) >= 0.999, (same.mean(), tie.sum())
+    assert _frac(_close(dist[same], ref_dist[same], 1e-5)) >= 0.999
     prev = g2[sample, 3].view(np.int32)
     prev = np.where(prev >= 0, prev & ~0x40000000, prev)
-    assert _frac((prev == ref.prev)[same]) >= 0.95
+    # the previous pixel is the floor of a reprojected coordinate: a
+    # float32-vs-fp64 tie at a pixel boundary moves it by one
+    assert _frac((prev == ref_prev)[same]) >= 0.995
     ctx.probe_trace(2)
     rays = ctx.probe_rays_get()
     vol = orc.Volume(sc.grid)
-    probes = np.array([1234, 9876], np.int32)
-    rr = orc.probe_trace(S, vol, 2, probes=probes)
+    probes = np.array([1234, 5000, 9876, 15000], np.int32)
+    rr = np.concatenate(_threaded(lambda c: orc.probe_trace(S, vol, 2, probes=c), probes, parts=4))
     t_gpu, t_ref = rays[probes, :, 3], rr[:, :, 3]
     close = np.abs(t_gpu - t_ref) <= 1e-4 * np.abs(t_ref)
-    # the finely tessellated shells put many rays near shared edges, where
-    # the float32 and fp64 tests may pick a neighbouring triangle (same
-    # surface, same distance) or, at silhouettes, the surface behind
-    assert _frac(close) >= 0.98, (t_gpu[~close][:8], t_ref[~close][:8])
+    tie = ~close & (np.abs(np.abs(t_gpu) - np.abs(t_ref)) <= 1e-5 * np.abs(t_ref))
+    assert _frac(close | tie) >= 0.999, (t_gpu[~close & ~tie][:8], t_ref[~close & ~tie][:8])
+    assert _frac(tie) <= 0.03
     assert ctx.get_status() == dd.OK
 
 
 def test_large_initial_and_shade_sampled(dd, orc, large):
-    """64 candidates over 8192 emitters on sampled pixels of the 4K G-buffer
-    (synthetic probe maps, probes serving): reservoirs, residuals and shading
-    match the oracle."""
+    """64 candidates over 8192 emitters on 512 sampled pixels of the 4K
+    G-buffer (synthetic probe maps, probes serving): reservoirs, residuals
+    and shading match the oracle at the bar of the other workloads
+    (>= 99.9 % selections, 1e-4 relative)."""
     import torch
     sc, ctx, S = large
     cam = sc.cameras[2]
@@ -1151,27 +1178,24 @@ def test_large_initial_and_shade_sampled(dd, orc, large):
     og = orc.GBuffer.from_planes(*g.numpy(), W, H)
     rng = np.random.default_rng(43)
     valid = np.flatnonzero(og.tri >= 0)
-    sample = np.sort(rng.choice(valid, 40, replace=False)).astype(np.int32)
+    sample = np.sort(rng.choice(valid, 512, replace=False)).astype(np.int32)
     out = dd.Reservoirs(n)
     resid = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     ctx.restir_initial(g, out, resid, 6)
-    ref, rref = orc.restir_initial(S, vol, og, 6, pix=sample)
-    f = dd.Reservoirs.fields(out.numpy()[sample])
-    same = (f["tri"] == ref.tri) & (f["tag"] == ref.tag)
-    assert _frac(same) >= 0.97
-    np.testing.assert_array_equal(f["M"], ref.M.astype(np.float32))
-    ok = same & (ref.tri >= 0)
-    assert _frac(_close(f["W"][ok], ref.W[ok], 1e-6)) >= 0.97
-    assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-4).all(1)) >= 0.97
+    parts = _threaded(lambda c: orc.restir_initial(S, vol, og, 6, pix=c), sample)
+    ref = _cat_res(orc, [p[0] for p in parts])
+    rref = np.concatenate([p[1] for p in parts])
+    _res_compare(out.numpy()[sample], ref, what="initial@4K, 1M triangles")
+    assert _frac(_close(resid.cpu().numpy()[sample, :3], rref, 1e-5).all(1)) >= 0.999
     rad = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     ctx.shade(g, out, resid, rad)
-    full = orc.Reservoirs(n)                       # the oracle's shading reads full buffers
-    for a in orc.Reservoirs.FIELDS:
-        getattr(full, a)[sample] = getattr(ref, a)
+    full = _scatter_res(orc, n, sample, ref)       # the oracle's shading reads full buffers
     full_resid = np.zeros((n, 3))
     full_resid[sample] = rref
-    sref = orc.shade(S, vol, og, full, full_resid, pix=sample)
-    assert _frac(_close(rad.cpu().numpy()[sample, :3], sref, 1e-4).all(1)[same]) >= 0.97
+    sref = np.concatenate(_threaded(lambda c: orc.shade(S, vol, og, full, full_resid, pix=c), sample))
+    f = dd.Reservoirs.fields(out.numpy()[sample])
+    same = (f["tri"] == ref.tri) & (f["tag"] == ref.tag)
+    assert _frac(_close(rad.cpu().numpy()[sample, :3], sref, 1e-5).all(1)[same]) >= 0.999
     ctx.mlp_serve(0)
     assert ctx.get_status() == dd.OK
 
