@@ -194,9 +194,11 @@ def test_probe_update_chain_parity(dd, orc, tiny):
         orc.probe_update(S, vol, f)
         ctx.probe_update(f)
     irr, dep, _, _ = ctx.probe_state_get()
-    assert _frac(_close(irr[..., :3], vol.irr, 1e-4, rel=1e-3)) >= 0.999
-    assert _frac(_close(dep, vol.depth, 1e-4, rel=1e-3)) >= 0.999
-    assert np.abs(irr[..., :3] - vol.irr).max() <= 1e-3 * np.abs(vol.irr).max()
+    # six free-running updates (each frame's maps feed the next trace):
+    # the parity bar of 1e-4 relative with the radiance floor 1e-5
+    assert _frac(_close(irr[..., :3], vol.irr, 1e-5)) >= 0.999
+    assert _frac(_close(dep, vol.depth, 1e-5)) >= 0.999
+    assert np.abs(irr[..., :3] - vol.irr).max() <= 1e-4 * np.abs(vol.irr).max()
 
 
 def test_initial_parity(dd, orc, tiny):
@@ -351,7 +353,7 @@ def test_whole_frame_chain_dynamic_box(dd, orc):
     sc = scenegen.tiny_room_dynamic(width=64, height=48, frames=8)
     stats = _chain(dd, orc, sc, 8)
     for f, (tags, rad) in enumerate(stats):
-        assert tags >= 0.995 and rad >= 0.995, (f, stats)
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
 
 
 def _oracle_volume_from(orc, grid, state):
@@ -625,7 +627,7 @@ def test_whole_frame_chain_fused_initial_temporal(dd, orc):
     sc = scenegen.tiny_room_dynamic(width=64, height=48, frames=6)
     stats = _chain(dd, orc, sc, 6, fused=True)
     for f, (tags, rad) in enumerate(stats):
-        assert tags >= 0.995 and rad >= 0.995, (f, stats)
+        assert tags >= 0.999 and rad >= 0.999, (f, stats)
 
 
 def test_fused_initial_temporal_argument_errors(dd):
@@ -658,9 +660,10 @@ def test_identity_update_keeps_the_bvh_exact(dd):
 
 
 def test_apartment_dynamic_sampled(dd, orc):
-    """The dynamic apartment after 5 updates of 200 moving boxes and an
-    emitter swap: sampled G-buffer (hits, previous pixels) and probe rays
-    match the oracle's brute force on the moved geometry."""
+    """The dynamic apartment after 10 updates of 200 moving boxes and an
+    emitter swap: sampled G-buffer (2048 pixels, half on moving boxes: hits,
+    previous pixels) and the rays of 16 probes match the oracle's brute
+    force on the moved geometry, ties counted as in the large workload."""
     import torch
     sc = scenegen.apartment_dynamic(frames=12)
     ctx = dd.Context.from_scene(sc)
@@ -676,27 +679,42 @@ def test_apartment_dynamic_sampled(dd, orc):
     moving_pix = np.flatnonzero((g1[:, 3].view(np.int32) >= 0) &
                                 (sc.tri_instance[np.maximum(g1[:, 3].view(np.int32), 0)] >= 0))
     assert len(moving_pix) > 1000
-    sample = np.sort(np.concatenate([rng.choice(moving_pix, 192, replace=False),
-                                     rng.choice(cam.width * cam.height, 192, replace=False)])).astype(np.int32)
-    ref = orc.gbuffer(S, cam, pc, pix=sample)
-    tri = g1[sample, 3].view(np.int32)
-    same = tri == ref.tri
-    assert _frac(same) >= 0.99
-    assert _frac(_close(g0[sample][same, 3], ref.dist[same], 1e-5)) >= 0.99
+    sample = np.unique(np.concatenate([rng.choice(moving_pix, 1024, replace=False),
+                                       rng.choice(cam.width * cam.height, 1024, replace=False)])).astype(np.int32)
+    parts = _threaded(lambda c: orc.gbuffer(S, cam, pc, pix=c), sample)
+    ref_tri = np.concatenate([p.tri for p in parts])
+    ref_dist = np.concatenate([p.dist for p in parts])
+    ref_prev = np.concatenate([p.prev for p in parts])
+    tri, dist = g1[sample, 3].view(np.int32), g0[sample, 3]
+    same = tri == ref_tri
+    tie = ~same & (tri >= 0) & (ref_tri >= 0) & (np.abs(dist - ref_dist) <= 1e-5 * ref_dist)
+    assert _frac(same | tie) >= 0.999, (same.mean(), tie.sum())
+    assert _frac(_close(dist[same], ref_dist[same], 1e-5)) >= 0.999
     prev = g2[sample, 3].view(np.int32)
     moving = (prev >= 0) & ((prev & 0x40000000) != 0)
-    np.testing.assert_array_equal(moving[same], (sc.tri_instance[np.maximum(ref.tri, 0)] >= 0)[same] & (ref.prev[same] >= 0))
+    np.testing.assert_array_equal(moving[same], (sc.tri_instance[np.maximum(ref_tri, 0)] >= 0)[same] &
+                                  (ref_prev[same] >= 0))
     prev = np.where(prev >= 0, prev & ~0x40000000, prev)
-    assert _frac((prev == ref.prev)[same]) >= 0.98
+    # the previous pixel is the floor of a reprojected coordinate (through the
+    # instance's motion for moving boxes): a pixel-boundary tie moves it by one
+    assert _frac((prev == ref_prev)[same]) >= 0.995
     # probe rays on the moved geometry
     ctx.probe_trace(10)
     rays = ctx.probe_rays_get()
     vol = orc.Volume(sc.grid)
     vol.offset[:] = ctx.probe_state_get()[2][:, :3]
-    probes = np.sort(rng.choice(sc.grid.num_probes, 6, replace=False)).astype(np.int32)
-    rr = orc.probe_trace(S, vol, 10, probes=probes)
+    probes = np.sort(rng.choice(sc.grid.num_probes, 16, replace=False)).astype(np.int32)
+    rr = np.concatenate(_threaded(lambda c: orc.probe_trace(S, vol, 10, probes=c), probes, parts=16))
     t_gpu, t_ref = rays[probes, :, 3], rr[:, :, 3]
-    assert _frac(np.abs(t_gpu - t_ref) <= 1e-4 * np.abs(t_ref)) >= 0.99
+    # the moved boxes' vertices are transformed in fp32 on the GPU and in
+    # fp64 by the oracle: with coordinates up to 16 m (fp32 spacing 1.9e-6 m)
+    # and the rotation's and translation's terms cancelling, a vertex moves by
+    # up to ~1e-5 m, which the short back-face hits of relocated probes
+    # inside boxes turn into up to 2e-5 m of distance: an absolute floor of
+    # 5e-5 m on hit distances here (3e-6 of the scene's extent)
+    close = np.abs(t_gpu - t_ref) <= 1e-4 * np.abs(t_ref) + 5e-5
+    tie = ~close & (np.abs(np.abs(t_gpu) - np.abs(t_ref)) <= 1e-5 * np.abs(t_ref))
+    assert _frac(close | tie) >= 0.999, (t_gpu[~close & ~tie][:8], t_ref[~close & ~tie][:8])
     assert ctx.get_status() == dd.OK
 
 
@@ -715,18 +733,25 @@ def apt(dd, orc):
 
 
 def test_apartment_gbuffer_sampled(dd, orc, apt):
-    sc, ctx, S, sample = apt
+    """Primary visibility at 1920x1080 on 4096 pixels: hits (ties at equal
+    distance counted), distances and previous pixels."""
+    sc, ctx, S, _ = apt
     cam, pc = sc.cameras[3], sc.cameras[2]
     g = dd.GBuffer(cam.width, cam.height)
     ctx.gbuffer(cam, pc, g)
     g0, g1, g2 = g.numpy()
-    ref = orc.gbuffer(S, cam, pc, pix=sample)
-    tri = g1[sample, 3].view(np.int32)
-    same = tri == ref.tri
-    assert _frac(same) >= 0.99
-    assert _frac(_close(g0[sample][same, 3], ref.dist[same], 1e-5)) >= 0.99
-    prev_same = g2[sample, 3].view(np.int32) == ref.prev
-    assert _frac(prev_same[same]) >= 0.99
+    sample = np.sort(np.random.default_rng(29).choice(cam.width * cam.height, 4096, replace=False)).astype(np.int32)
+    parts = _threaded(lambda c: orc.gbuffer(S, cam, pc, pix=c), sample)
+    ref_tri = np.concatenate([p.tri for p in parts])
+    ref_dist = np.concatenate([p.dist for p in parts])
+    ref_prev = np.concatenate([p.prev for p in parts])
+    tri, dist = g1[sample, 3].view(np.int32), g0[sample, 3]
+    same = tri == ref_tri
+    tie = ~same & (tri >= 0) & (ref_tri >= 0) & (np.abs(dist - ref_dist) <= 1e-5 * ref_dist)
+    assert _frac(same | tie) >= 0.999, (same.mean(), tie.sum())
+    assert _frac(_close(dist[same], ref_dist[same], 1e-5)) >= 0.999
+    prev_same = g2[sample, 3].view(np.int32) == ref_prev
+    assert _frac(prev_same[same]) >= 0.995
 
 
 def test_apartment_probe_trace_sampled(dd, orc, apt):
