@@ -209,6 +209,33 @@ LAYOUT_BYTES_PER_PX = {
 }
 
 
+def measure_fp32_peak(dev, n: int = 8192, reps: int = 5) -> float:
+    """FP32 FMA throughput of this GPU measured in the run (TFLOP/s): the
+    best of `reps` n^3 single-precision GEMMs on the CUDA cores (TF32 off),
+    the denominator of the FP32-bound probe blend."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        c = torch.empty(n, n, device=dev)
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def launches_per_frame(spatial_passes: int, fused: bool = False) -> int:
     """Kernels of one timed frame: probe trace + blend, BSDF-ray traversal +
     emitter candidates + BSDF candidates, temporal (inside the BSDF-candidate
@@ -281,8 +308,8 @@ def run_ours(args, ws, rank, local):
     fused = not args.two_pass
 
     def pass_names(fz):
-        return (["probe_update", "restir_initial_temporal"] if fz else
-                ["probe_update", "restir_initial", "restir_temporal"]) + \
+        return (["probe_trace", "probe_blend", "restir_initial_temporal"] if fz else
+                ["probe_trace", "probe_blend", "restir_initial", "restir_temporal"]) + \
                [f"restir_spatial{i}" for i in range(st.spatial_passes)] + ["ddgi_shade"]
 
     passes = pass_names(fused)
@@ -299,7 +326,10 @@ def run_ours(args, ws, rank, local):
                 next(e).record(stream)
 
         mark()
-        ctx.probe_update(f, stream)
+        # ddgi_probe_update is these two calls (no relocation in this workload)
+        ctx.probe_trace(f, stream)
+        mark()
+        ctx.probe_blend(f, stream)
         mark()
         init, tmp = fr._free_pair()
         if fz and fr.prev_final is not None:
@@ -373,6 +403,22 @@ def run_ours(args, ws, rank, local):
             entry.update({"bytes": BYTES_PER_PX[key] * N, "gbs": round(gbs, 1),
                           "hbm_frac": round(gbs / hbm, 4), "layout_hbm_frac": round(lgbs / hbm, 4)})
         pass_report[p] = entry
+    # the probe blend is bound by FP32 arithmetic: (irradiance + distance
+    # texels) x rays x 10 flop per probe (the scope's count), against the
+    # FP32 GEMM throughput measured here
+    blend_flop = (st.irr_texels ** 2 + st.depth_texels ** 2) * st.rays_per_probe * 10 * sc.grid.num_probes
+    fp32_peak = measure_fp32_peak(dev)
+    blend_tf = blend_flop / (per_pass["probe_blend"] * 1e-3) / 1e12
+    pass_report["probe_blend"].update({"gflop": round(blend_flop / 1e9, 3), "tflops": round(blend_tf, 2),
+                                       "fp32_peak_tflops_measured": round(fp32_peak, 1),
+                                       "fp32_frac": round(blend_tf / fp32_peak, 4)})
+    pass_report["probe_update"] = {"ms": round(per_pass["probe_trace"] + per_pass["probe_blend"], 4)}
+    pass_report["probe_trace"]["rays_per_s"] = round(
+        sc.grid.num_probes * st.rays_per_probe / (per_pass["probe_trace"] * 1e-3), 1)
+    cand_key = "restir_initial_temporal" if fused else "restir_initial"
+    n_cand = N * ((st.num_light_candidates if ctx.info.num_emitters else 0) + st.num_bsdf_candidates)
+    pass_report[cand_key].update({"candidates": n_cand,
+                                  "pixel_candidates_per_s": round(n_cand / (per_pass[cand_key] * 1e-3), 1)})
     if two_pass is not None:
         rep2 = {}
         for p, ms in two_pass["passes"].items():
