@@ -506,7 +506,17 @@ class Context:
 class Frame:
     """Per-frame buffers of one resolution and a driver for the whole path
     (probe update, initial, temporal, spatial passes, shade) on one stream;
-    ping-pongs the G-buffer and the final reservoirs between frames."""
+    ping-pongs the G-buffer and the final reservoirs between frames.
+
+    With ``pipelined`` renders, a frame's probe trace runs during the frame
+    before it: once frame f's maps are blended (and probes relocated), the
+    trace of frame f + 1 -- which reads only those maps and writes only the
+    probe ray buffer, which nothing else reads until the next blend -- is
+    issued on a side stream, beside frame f's resampling and shading; the
+    next render waits for it and blends.  The results are those of the
+    sequential frame.  If the next render moves the scene or renders another
+    frame index, it waits for that trace and traces again on its own
+    stream."""
 
     def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda"):
         n = width * height
@@ -519,21 +529,55 @@ class Frame:
         self.prev_final: Optional[Reservoirs] = None
         self.prev_cam = None
         self.cur = 0
+        self.side = torch.cuda.Stream(device)   # the next frame's probe trace
+        self.ev_maps = torch.cuda.Event()        # this frame's maps blended (and probes relocated)
+        self.ev_trace = torch.cuda.Event()       # the next frame's probe rays traced
+        self.pending: Optional[int] = None      # frame whose probe trace is in flight on `side`
+
+    def _probe_update(self, frame: int, stream, moved: bool, pipelined: bool):
+        ctx = self.ctx
+        st = stream if stream is not None else torch.cuda.current_stream()
+        if self.pending is not None:
+            st.wait_event(self.ev_trace)     # done before the ray buffer is read or rewritten
+        if self.pending != frame or moved:
+            ctx.probe_trace(frame, stream)
+        self.pending = None
+        ctx.probe_blend(frame, stream)
+        if ctx.cfg.probe_relocation:
+            ctx.probe_relocate(frame, stream)
+        if pipelined:
+            self.ev_maps.record(st)
+            self.side.wait_event(self.ev_maps)
+            ctx.probe_trace(frame + 1, self.side)
+            self.ev_trace.record(self.side)
+            self.pending = frame + 1
+
+    def finish(self, stream=None):
+        """Make `stream` wait for a probe trace still in flight."""
+        if self.pending is not None:
+            (stream or torch.cuda.current_stream()).wait_event(self.ev_trace)
 
     def render(self, frame: int, cam, gbuf: Optional[GBuffer] = None, stream=None,
                probe_update=True, xf=None, emitter_radiance=None, out: Optional[torch.Tensor] = None,
-               fused: bool = False):
+               fused: bool = False, pipelined: bool = False):
         """One frame.  If ``gbuf`` is given it is used as this frame's
         G-buffer (the primary-visibility pass is skipped); xf /
         emitter_radiance (optional) first move the scene; ``out`` (optional,
         [n][4] float32 on the device) receives the radiance instead of the
         frame's own buffer; ``fused`` runs the initial and temporal passes as
-        one (restir_initial_temporal; same results)."""
+        one (restir_initial_temporal; same results); ``pipelined`` issues the
+        next frame's probe trace on the side stream (class docstring)."""
         ctx = self.ctx
-        if xf is not None or emitter_radiance is not None:
+        moved = xf is not None or emitter_radiance is not None
+        if moved:
+            if self.pending is not None:   # the scene must not move under a trace in flight
+                (stream or torch.cuda.current_stream()).wait_event(self.ev_trace)
             ctx.scene_update(xf, emitter_radiance, stream)
         if probe_update:
-            ctx.probe_update(frame, stream)
+            self._probe_update(frame, stream, moved, pipelined)
+        elif self.pending is not None:
+            self.finish(stream)
+            self.pending = None
         g = gbuf
         if g is None:
             g = self.g[self.cur]
@@ -579,9 +623,10 @@ class HostFramePipeline:
     radiance, ordered by events).  Host buffers should be pinned."""
 
     def __init__(self, ctx: Context, width: int, height: int, spatial_passes: int, device="cuda",
-                 fused: bool = False):
+                 fused: bool = False, pipelined: bool = False):
         n = width * height
         self.fused = fused   # restir_initial_temporal instead of the two passes
+        self.pipelined = pipelined   # the next frame's probe trace beside this frame (Frame)
         self.frame = Frame(ctx, width, height, spatial_passes, device)
         self.gbuf = [GBuffer(width, height, device), GBuffer(width, height, device)]
         self.rad = [torch.empty((n, 4), dtype=torch.float32, device=device) for _ in range(2)]
@@ -612,7 +657,7 @@ class HostFramePipeline:
         st.wait_event(self.ev_in[b])
         st.wait_event(self.ev_out[b])                           # the slot's radiance was read out
         self.frame.render(frame, cam, gbuf=self.gbuf[b], stream=st, probe_update=True, out=self.rad[b],
-                          fused=self.fused)
+                          fused=self.fused, pipelined=self.pipelined)
         self.ev_used[b].record(st)
         with torch.cuda.stream(self.down):
             self.down.wait_event(self.ev_used[b])
@@ -621,6 +666,8 @@ class HostFramePipeline:
         self.k += 1
 
     def finish(self, stream=None):
-        """Make `stream` wait for the last download."""
+        """Make `stream` wait for the last download (and a probe trace still
+        in flight)."""
         st = stream or torch.cuda.current_stream()
         st.wait_event(self.ev_out[(self.k - 1) % 2])
+        self.frame.finish(st)

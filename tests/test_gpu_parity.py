@@ -1326,3 +1326,31 @@ def test_whole_frame_chain_extreme_settings(dd, orc):
     stats = _chain(dd, orc, sc, 3)
     for f, (tags, rad) in enumerate(stats):
         assert tags >= 0.999 and rad >= 0.998, (f, stats)
+
+
+def test_pipelined_frames_equal_sequential_frames(dd):
+    """Frame.render with the next frame's probe trace on the side stream
+    gives bit-identical radiance and reservoirs to the sequential frame, on
+    a static scene, across a jump in the frame index (the trace in flight is
+    for a frame that is not rendered: the render traces again) and on the
+    moving-box scene with relocation (every render moves the scene, so each
+    one traces again after waiting for the trace in flight)."""
+    for sc, frames in ((scenegen.tiny_room(width=96, height=64, frames=6), [0, 1, 2, 4, 5]),
+                       (scenegen.tiny_room_dynamic(width=64, height=48, frames=5), [0, 1, 2, 3, 4])):
+        cam0 = sc.cameras[0]
+        a, b = dd.Context.from_scene(sc), dd.Context.from_scene(sc)
+        fa = dd.Frame(a, cam0.width, cam0.height, sc.settings.spatial_passes)
+        fb = dd.Frame(b, cam0.width, cam0.height, sc.settings.spatial_passes)
+        for f in frames:
+            cam = sc.cameras[f % len(sc.cameras)]
+            xf, le = sc.instance_transforms(f), sc.emitter_radiance(f)
+            ra = fa.render(f, cam, xf=xf, emitter_radiance=le, fused=True).cpu().numpy().copy()
+            rb = fb.render(f, cam, xf=xf, emitter_radiance=le, fused=True, pipelined=True).cpu().numpy().copy()
+            np.testing.assert_array_equal(ra, rb)
+            np.testing.assert_array_equal(fa.prev_final.numpy(), fb.prev_final.numpy())
+        fb.finish()
+        ia, _, _, ua = a.probe_state_get()
+        ib, _, _, ub = b.probe_state_get()
+        np.testing.assert_array_equal(ia, ib)
+        assert ua == ub
+        assert a.get_status() == dd.OK and b.get_status() == dd.OK
