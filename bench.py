@@ -406,6 +406,16 @@ def run_ours(args, ws, rank, local):
         for i, p in enumerate(passes):
             per_pass[p] += evs[k][i].elapsed_time(evs[k][i + 1]) / K
     side_ms = (sum(a.elapsed_time(b) for a, b in side_evs) / len(side_evs)) if side_evs else None
+    # pipelined, the next frame's probe trace runs on the side stream inside
+    # some pass's window: per pass, the mean time of the side trace that falls
+    # in it (event times on both streams taken from t0)
+    side_in = {p: 0.0 for p in passes}
+    if side_evs:
+        for k, (a, b) in enumerate(side_evs):
+            sa, sb = t0.elapsed_time(a), t0.elapsed_time(b)
+            for i, p in enumerate(passes):
+                w0, w1 = t0.elapsed_time(evs[k][i]), t0.elapsed_time(evs[k][i + 1])
+                side_in[p] += max(0.0, min(sb, w1) - max(sa, w0)) / K
     # the two-pass form of the same frames (separate initial and temporal
     # passes), untimed for the metric: the per-pass rooflines of both passes
     two_pass = None
@@ -431,6 +441,8 @@ def run_ours(args, ws, rank, local):
             lgbs = LAYOUT_BYTES_PER_PX[key] * N / (ms * 1e-3) / 1e9
             entry.update({"bytes": BYTES_PER_PX[key] * N, "gbs": round(gbs, 1),
                           "hbm_frac": round(gbs / hbm, 4), "layout_hbm_frac": round(lgbs / hbm, 4)})
+        if side_in[p] > 0:
+            entry["concurrent_probe_trace_ms"] = round(side_in[p], 4)
         pass_report[p] = entry
     # the probe blend is bound by FP32 arithmetic: (irradiance + distance
     # texels) x rays x 10 flop per probe (the scope's count), against the
@@ -483,16 +495,24 @@ def run_ours(args, ws, rank, local):
             sm_mhz = clocks.get("sm_mhz") or 2070.0
             peak_issue = torch.cuda.get_device_properties(dev).multi_processor_count * ISSUE_PER_SM_CLK * \
                 sm_mhz * 1e6
-            ach = inst / (per_pass[dom] * 1e-3)
+            # instructions issued in the pass's window: its own, plus the
+            # share of the concurrent side-stream probe trace that ran inside it
+            inst_side = ncu_instructions("k_probe_trace")
+            shared = side_in[dom] / side_ms if side_ms and inst_side is not None else 0.0
+            ach = (inst + shared * (inst_side or 0.0)) / (per_pass[dom] * 1e-3)
             roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "alu",
                     "achieved": round(ach / 1e9, 1), "peak": round(peak_issue / 1e9, 1),
                     "unit": "G warp-instructions/s", "frac": round(ach / peak_issue, 4),
                     "traffic": hbm_roof["traffic"], "hbm": hbm_roof,
-                    "note": "achieved = warp instructions the pass executes per frame (ncu "
-                            "smsp__inst_executed.sum summed over its kernels, profiles/instructions.txt, "
-                            "same kernel sources) / the pass's CUDA-event time; peak = SMs x 4 schedulers x "
-                            "1 instruction / cycle x the SM clock sampled during the run; hbm = the "
-                            "pass's algorithmic bytes (240 B/px) against the measured copy peak"}
+                    "concurrent_probe_trace_ms": round(side_in[dom], 4),
+                    "note": "achieved = warp instructions issued in the pass's CUDA-event window per "
+                            "frame (ncu smsp__inst_executed.sum summed over its kernels, "
+                            "profiles/instructions.txt, same kernel sources; plus, pipelined, "
+                            "k_probe_trace's count times the fraction of the next frame's probe trace "
+                            "that ran inside the window on the side stream) / the window's time; peak = "
+                            "SMs x 4 schedulers x 1 instruction / cycle x the SM clock sampled during the "
+                            "run; hbm = the pass's algorithmic bytes (240 B/px) against the measured copy "
+                            "peak, over the same window"}
         else:
             roof = {"kernel": f"{dom_key} pass: {kernels}", "bound": "hbm", **hbm_roof,
                     "note": "algorithmic bytes = compulsory per-pixel plane traffic of the pass, timed by "
@@ -531,19 +551,28 @@ def run_ours(args, ws, rank, local):
             pipe.run(k, sc.cameras[k % args.frames], out_host[k % 2], stream)
         pipe.finish(stream)
         torch.cuda.synchronize()
+        # three segments of Ke frames: the median, so that one host-side
+        # stall in a segment (other processes on the host) does not set it
         Ke = max(10, min(K, 50))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for k in range(3, 3 + Ke):
-            pipe.upload(host[(k + 1) % args.frames])
-            pipe.run(k, sc.cameras[k % args.frames], out_host[k % 2], stream)
-        pipe.finish(stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        out["e2e"] = {"value": round(a.elapsed_time(b) / Ke, 4), "unit": "ms/frame",
+        seg = []
+        k0 = 3
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for k in range(k0, k0 + Ke):
+                pipe.upload(host[(k + 1) % args.frames])
+                pipe.run(k, sc.cameras[k % args.frames], out_host[k % 2], stream)
+            pipe.finish(stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            seg.append(a.elapsed_time(b) / Ke)
+            k0 += Ke   # the uploads run one frame ahead across segments
+        out["e2e"] = {"value": round(statistics.median(seg), 4), "unit": "ms/frame",
                       "h2d_bytes_per_step": 48 * N, "d2h_bytes_per_step": 16 * N,
+                      "segments_ms": [round(x, 4) for x in seg],
                       "path": "ddgi.HostFramePipeline through the C ABI: pinned host G-buffer in, host radiance "
-                              "out, every frame, copies overlapped with the previous / next frame"}
+                              "out, every frame, copies overlapped with the previous / next frame; median of "
+                              f"3 segments of {Ke} frames"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and not glossy:
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=12.0)
     if rank == 0 and not args.no_equal_time and ws == 1 and not glossy:
