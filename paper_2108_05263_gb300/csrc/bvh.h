@@ -11,6 +11,17 @@ struct Bvh4 {
     uint32_t depth = 0;
 };
 
+// Slot entry codes (row 6 of a node): 0 an empty slot (its box is inverted,
+// so no ray enters it), > 0 the index of an inner node (the root, node 0, is
+// nobody's child), < 0 a leaf of `count` (1..8) consecutive triangle slots
+// from `first`, coded -1 - (first * 8 + count - 1).
+inline int32_t bvh_leaf_entry(int32_t first, int32_t count) { return -1 - (first * 8 + count - 1); }
+inline void bvh_leaf_range(int32_t entry, int32_t* first, int32_t* count) {
+    const int32_t v = -1 - entry;
+    *first = v >> 3;
+    *count = (v & 7) + 1;
+}
+
 // Builds an SAH binary BVH over `num_tris` triangles (9 floats each) and
 // collapses it to 4-wide nodes.  split_large: triangles with large boxes
 // enter as several clipped references (a triangle then fills several slots of

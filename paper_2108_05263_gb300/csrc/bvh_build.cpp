@@ -1,7 +1,8 @@
 // Host BVH construction: surface-area-heuristic binary BVH (binned for large
 // nodes, an exact sweep over sorted centroids for the rest), collapsed
-// into 4-wide nodes whose children boxes are stored as SoA float4 rows so
-// that one node is eight 16-byte loads on the device.
+// into 4-wide nodes whose children boxes are stored as SoA float4 rows, with
+// each slot's entry code (bvh.h) precomputed, so that one node is six box rows
+// and one entry row of 16 bytes on the device.
 #include <algorithm>
 #include <array>
 #include <cfloat>
@@ -328,11 +329,11 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
     };
     std::vector<Q> queue;
     std::vector<std::vector<int>> slots;
-    if (root < 0) {
+    if (root < 0) {   // no triangles: a root of four empty slots
         out->nodes.assign(32, 0.f);
         float* n = out->nodes.data();
-        int neg1 = -1;
-        for (int c = 0; c < 4; ++c) std::memcpy(&n[24 + c], &neg1, 4);
+        for (int c = 0; c < 4; ++c)
+            for (int r = 0; r < 6; r += 2) n[4 * r + c] = FLT_MAX, n[4 * r + 4 + c] = -FLT_MAX;
         out->num_nodes = 1;
         out->depth = 1;
         return;
@@ -447,20 +448,16 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
         float* n = &out->nodes[32 * qi];
         const std::vector<int>& ch = slots[qi];
         for (int c = 0; c < 4; ++c) {
-            int child_bits = -1, count = 0;
-            float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+            // an empty slot: inverted box, entry 0
+            int32_t entry = 0;
+            float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
             if (c < (int)ch.size()) {
                 const BNode& cn = b.nodes[ch[c]];
                 for (int a = 0; a < 3; ++a) {
                     lo[a] = cn.box.lo[a];
                     hi[a] = cn.box.hi[a];
                 }
-                if (cn.left < 0) {
-                    child_bits = ~cn.first;
-                    count = cn.count;
-                } else {
-                    child_bits = (int)next++;
-                }
+                entry = cn.left < 0 ? bvh_leaf_entry(cn.first, cn.count) : (int32_t)next++;
             }
             n[0 + c] = lo[0];
             n[4 + c] = hi[0];
@@ -468,8 +465,8 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
             n[12 + c] = hi[1];
             n[16 + c] = lo[2];
             n[20 + c] = hi[2];
-            std::memcpy(&n[24 + c], &child_bits, 4);
-            std::memcpy(&n[28 + c], &count, 4);
+            std::memcpy(&n[24 + c], &entry, 4);
+            n[28 + c] = 0.f;   // row 7: unused
         }
     }
     out->num_nodes = (uint32_t)N;

@@ -442,20 +442,20 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
     std::vector<uint32_t> depth(N, 0);
     for (uint32_t n = 0; n < N; ++n)
         for (int s = 0; s < 4; ++s) {
-            int ch;
-            std::memcpy(&ch, &bvh.nodes[32ull * n + 24 + s], 4);
-            if (ch >= 0) depth[ch] = depth[n] + 1;
+            int32_t en;
+            std::memcpy(&en, &bvh.nodes[32ull * n + 24 + s], 4);
+            if (en > 0) depth[en] = depth[n] + 1;
         }
     uint32_t maxd = 0;
     for (uint32_t n = N; n-- > 0;) {
         for (int s = 0; s < 4; ++s) {
-            int ch, cnt;
-            std::memcpy(&ch, &bvh.nodes[32ull * n + 24 + s], 4);
-            std::memcpy(&cnt, &bvh.nodes[32ull * n + 28 + s], 4);
-            if (ch >= 0) {
-                dirty[n] |= dirty[ch];
-            } else {
-                for (int k = ~ch; k < ~ch + cnt; ++k) dirty[n] |= slot_moving[k];
+            int32_t en, first, cnt;
+            std::memcpy(&en, &bvh.nodes[32ull * n + 24 + s], 4);
+            if (en > 0) {
+                dirty[n] |= dirty[en];
+            } else if (en < 0) {
+                bvh_leaf_range(en, &first, &cnt);
+                for (int k = first; k < first + cnt; ++k) dirty[n] |= slot_moving[k];
             }
         }
         if (dirty[n]) maxd = std::max(maxd, depth[n]);

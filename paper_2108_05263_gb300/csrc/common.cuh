@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cfloat>
+
 #define DDGI_PI 3.14159265358979323846f
 #define DDGI_T_EPS 1e-4f
 #define DDGI_MISS_T 1e30f

@@ -48,11 +48,12 @@ __global__ void __launch_bounds__(128) k_refit(float4* __restrict__ nodes, const
     if (i >= n) return;
     float* nd = reinterpret_cast<float*>(nodes + 8 * (size_t)list[i]);
     for (int c = 0; c < 4; ++c) {
-        const int child = __float_as_int(nd[24 + c]), cnt = __float_as_int(nd[28 + c]);
-        if (child < 0 && cnt <= 0) continue;
-        f3 lo = {INFINITY, INFINITY, INFINITY}, hi = {-INFINITY, -INFINITY, -INFINITY};
-        if (child < 0) {
-            const int first = ~child;
+        // slot entry: 0 empty, > 0 inner node, < 0 leaf (-1 - (first * 8 + count - 1))
+        const int entry = __float_as_int(nd[24 + c]);
+        if (entry == 0) continue;
+        f3 lo = {FLT_MAX, FLT_MAX, FLT_MAX}, hi = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        if (entry < 0) {
+            const int v = -1 - entry, first = v >> 3, cnt = (v & 7) + 1;
             for (int k = first; k < first + cnt; ++k) {
                 const f3 v0 = xyz(tris[3 * (size_t)k]);
                 const f3 p1 = v0 + xyz(tris[3 * (size_t)k + 1]), p2 = v0 + xyz(tris[3 * (size_t)k + 2]);
@@ -62,14 +63,14 @@ __global__ void __launch_bounds__(128) k_refit(float4* __restrict__ nodes, const
                       fmaxf(hi.z, fmaxf(v0.z, fmaxf(p1.z, p2.z)))};
             }
         } else {
-            const float* cn = reinterpret_cast<const float*>(nodes + 8 * (size_t)child);
+            const float* cn = reinterpret_cast<const float*>(nodes + 8 * (size_t)entry);
             for (int cc = 0; cc < 4; ++cc) {
-                if (__float_as_int(cn[24 + cc]) < 0 && __float_as_int(cn[28 + cc]) <= 0) continue;
+                if (__float_as_int(cn[24 + cc]) == 0) continue;
                 lo = {fminf(lo.x, cn[0 + cc]), fminf(lo.y, cn[8 + cc]), fminf(lo.z, cn[16 + cc])};
                 hi = {fmaxf(hi.x, cn[4 + cc]), fmaxf(hi.y, cn[12 + cc]), fmaxf(hi.z, cn[20 + cc])};
             }
         }
-        if (!(lo.x <= hi.x)) lo = hi = {0.f, 0.f, 0.f};   // a slot over empty leaves keeps a point box
+        // (a slot whose subtree holds no occupied slot keeps the inverted box: never entered)
         nd[0 + c] = lo.x;
         nd[4 + c] = hi.x;
         nd[8 + c] = lo.y;

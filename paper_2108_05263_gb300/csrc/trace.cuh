@@ -1,12 +1,15 @@
 // Software ray traversal of the 4-wide BVH (the ray-casting operation h of
 // Sec. 3.2; the paper uses DXR hardware, here it is plain SM code).
 //
-// Node layout (128 B = 8 float4, loaded with 16-byte read-only loads):
+// Node layout (128 B = 8 float4, 128-byte aligned):
 //   [0] lo.x of children 0..3   [1] hi.x   [2] lo.y   [3] hi.y
 //   [4] lo.z                    [5] hi.z
-//   [6] child (int bits): >= 0 inner node index, < 0 leaf with first
-//       triangle ~child;  [7] triangle count of leaf children (0 = inner)
-// Empty child slots have an inverted box and are never entered.
+//   [6] slot entry (int bits): > 0 inner node index, < 0 a leaf of count
+//       triangle slots from first, coded -1 - (first * 8 + count - 1);
+//       0 an empty slot   [7] unused
+// Empty slots have an inverted box (lo = FLT_MAX, hi = -FLT_MAX) and entry 0:
+// a slab test that takes each axis's near and far plane by the ray's sign
+// never enters them; the symmetric min / max form tests the entry.
 // Triangles are stored in leaf order as 3 float4: (v0, original index
 // bits), (e1 = v1 - v0, 0), (e2 = v2 - v0, 0).
 #pragma once
@@ -69,18 +72,16 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
             return h;
         }
         const float4* np = s.nodes + (size_t)node * 8;
-        // a node is four 32-byte loads (nodes are 128-byte aligned)
-        float4 lx, hx, ly, hy, lz, hz, chf, cnf;
+        // a node is three 32-byte box loads and the 16-byte entry row
+        float4 lx, hx, ly, hy, lz, hz;
         ld32(np, lx, hx);
         ld32(np + 2, ly, hy);
         ld32(np + 4, lz, hz);
-        ld32(np + 6, chf, cnf);
+        const float4 ef = ldg4(np + 6);
         const float blo[4][3] = {{lx.x, ly.x, lz.x}, {lx.y, ly.y, lz.y}, {lx.z, ly.z, lz.z}, {lx.w, ly.w, lz.w}};
         const float bhi[4][3] = {{hx.x, hy.x, hz.x}, {hx.y, hy.y, hz.y}, {hx.z, hy.z, hz.z}, {hx.w, hy.w, hz.w}};
-        const int child[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
-                              __float_as_int(chf.w)};
-        const int count[4] = {__float_as_int(cnf.x), __float_as_int(cnf.y), __float_as_int(cnf.z),
-                              __float_as_int(cnf.w)};
+        const int entry[4] = {__float_as_int(ef.x), __float_as_int(ef.y), __float_as_int(ef.z),
+                              __float_as_int(ef.w)};
         float tnear[4];
         int order[4];
         int ninner = 0;
@@ -92,10 +93,10 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
             float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), ray.tmin));
             float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), h.t)) * widen;
             bool hit = t0 <= t1;
-            if (hit && count[c] > 0) {
+            if (hit && entry[c] < 0) {
                 // leaf: intersect its triangles now
-                int first = ~child[c];
-                for (int k = 0; k < count[c]; ++k) {
+                const int v = -1 - entry[c], first = v >> 3, count = (v & 7) + 1;
+                for (int k = 0; k < count; ++k) {
                     uint32_t orig;
                     float t = tri_hit(s.tris + (size_t)(first + k) * 3, ray.o, ray.d, &orig);
                     if (t > ray.tmin && t < ray.tmax) {
@@ -110,9 +111,9 @@ __device__ __forceinline__ Hit trace_bvh(const SceneView& s, const Ray& ray) {
                         }
                     }
                 }
-            } else if (hit && child[c] >= 0) {
+            } else if (hit && entry[c] > 0) {
                 tnear[ninner] = t0;
-                order[ninner] = child[c];
+                order[ninner] = entry[c];
                 ++ninner;
             }
         }

@@ -40,7 +40,13 @@ __device__ __forceinline__ bool pop_entry(const int2* stack, int& sp, float limi
 // traversal); then the set-aside leaf is intersected.  Returns true when the
 // ray is done (best_t / best_tri hold its result).  Shared by the persistent
 // engine and the per-thread trace_spec.
-template <bool ANY_HIT>
+// element c (0..3) of a 4-array held in registers, without local memory
+template <class T>
+__device__ __forceinline__ T sel4(const T (&a)[4], int c) {
+    return c == 0 ? a[0] : c == 1 ? a[1] : c == 2 ? a[2] : a[3];
+}
+
+template <bool ANY_HIT, bool SORTED>
 __device__ __forceinline__ bool trav_step(const SceneView& s, const f3& o, const f3& d, const f3& inv, const f3& oi,
                                           float tmin, float tmax, float& best_t, uint32_t& best_tri, int& node,
                                           int& sp, int& visits, bool& more, int2* stack) {
@@ -64,49 +70,28 @@ __device__ __forceinline__ bool trav_step(const SceneView& s, const f3& o, const
             break;
         }
         const float4* np = s.nodes + (size_t)node * 8;
-        // a node is four 32-byte loads (nodes are 128-byte aligned)
-        float4 lx, hx, ly, hy, lz, hz, chf, cnf;
-        ld32(np, lx, hx);
-        ld32(np + 2, ly, hy);
-        ld32(np + 4, lz, hz);
-        ld32(np + 6, chf, cnf);
+        // each axis's near and far rows by the ray's sign: an inverted
+        // (empty) box never passes
+        const int ox = inv.x < 0.f, oy = inv.y < 0.f, oz = inv.z < 0.f;
+        const float4 nx = ldg4(np + ox), fx = ldg4(np + 1 - ox);
+        const float4 ny = ldg4(np + 2 + oy), fy = ldg4(np + 3 - oy);
+        const float4 nz = ldg4(np + 4 + oz), fz = ldg4(np + 5 - oz);
+        const float4 ef = ldg4(np + 6);
+        const float nxa[4] = {nx.x, nx.y, nx.z, nx.w}, fxa[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float nya[4] = {ny.x, ny.y, ny.z, ny.w}, fya[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float nza[4] = {nz.x, nz.y, nz.z, nz.w}, fza[4] = {fz.x, fz.y, fz.z, fz.w};
+        const int ent[4] = {__float_as_int(ef.x), __float_as_int(ef.y), __float_as_int(ef.z), __float_as_int(ef.w)};
         float t0[4];
-        int ent[4];
-        const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float lya[4] = {ly.x, ly.y, ly.z, ly.w}, hya[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
-        const int cha[4] = {__float_as_int(chf.x), __float_as_int(chf.y), __float_as_int(chf.z),
-                            __float_as_int(chf.w)};
-        const int cna[4] = {__float_as_int(cnf.x), __float_as_int(cnf.y), __float_as_int(cnf.z),
-                            __float_as_int(cnf.w)};
+        int key[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float tx0 = fmaf(lxa[c], inv.x, -oi.x), tx1 = fmaf(hxa[c], inv.x, -oi.x);
-            float ty0 = fmaf(lya[c], inv.y, -oi.y), ty1 = fmaf(hya[c], inv.y, -oi.y);
-            float tz0 = fmaf(lza[c], inv.z, -oi.z), tz1 = fmaf(hza[c], inv.z, -oi.z);
-            float a = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
-            float b = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), best_t)) * widen;
-            bool valid = cna[c] > 0 || cha[c] >= 0;
-            bool hit = valid && a <= b;
-            t0[c] = hit ? a : INFINITY;
-            ent[c] = cna[c] > 0 ? leaf_entry(~cha[c], cna[c]) : cha[c];
+            float a = fmaxf(fmaxf(fmaf(nxa[c], inv.x, -oi.x), fmaf(nya[c], inv.y, -oi.y)),
+                            fmaxf(fmaf(nza[c], inv.z, -oi.z), tmin));
+            float b = fminf(fminf(fmaf(fxa[c], inv.x, -oi.x), fmaf(fya[c], inv.y, -oi.y)),
+                            fminf(fmaf(fza[c], inv.z, -oi.z), best_t)) * widen;
+            t0[c] = a <= b ? a : INFINITY;
+            key[c] = (__float_as_int(t0[c]) & ~3) | c;
         }
-        // sort the 4 (t, entry) pairs by t, ascending (sorting network)
-#define CSWAP(i, j)                                          \
-if (t0[j] < t0[i]) {                                     \
-    float tt = t0[i];                                    \
-    t0[i] = t0[j];                                       \
-    t0[j] = tt;                                          \
-    int ee = ent[i];                                     \
-    ent[i] = ent[j];                                     \
-    ent[j] = ee;                                         \
-}
-        CSWAP(0, 1)
-        CSWAP(2, 3)
-        CSWAP(0, 2)
-        CSWAP(1, 3)
-        CSWAP(1, 2)
-#undef CSWAP
         const int nhit = (t0[0] < INFINITY) + (t0[1] < INFINITY) + (t0[2] < INFINITY) + (t0[3] < INFINITY);
         if (sp + nhit > TRAV_STACK) {
             atomicOr(s.err, ERRBIT_STACK);
@@ -115,17 +100,47 @@ if (t0[j] < t0[i]) {                                     \
             done = true;
             break;
         }
-        // push far-to-near, continue with the nearest
+        if (SORTED) {
+            // all hit children by entry distance: push far-to-near, continue
+            // with the nearest (sorting network on the keys)
+#define KSWAP(i, j)                 \
+    {                               \
+        const int lo_ = min(key[i], key[j]); \
+        key[j] = max(key[i], key[j]);        \
+        key[i] = lo_;                        \
+    }
+            KSWAP(0, 1)
+            KSWAP(2, 3)
+            KSWAP(0, 2)
+            KSWAP(1, 3)
+            KSWAP(1, 2)
+#undef KSWAP
 #pragma unroll
-        for (int k = 3; k >= 1; --k)
-            if (k < nhit) {
-                stack[sp] = make_int2(ent[k], __float_as_int(t0[k]));
-                ++sp;
-            }
-        if (nhit > 0)
-            node = ent[0];
-        else
-            more = pop_entry(stack, sp, best_t * widen, node);
+            for (int k = 3; k >= 1; --k)
+                if (k < nhit) {
+                    const int c = key[k] & 3;
+                    stack[sp] = make_int2(sel4(ent, c), __float_as_int(sel4(t0, c)));
+                    ++sp;
+                }
+            if (nhit > 0)
+                node = sel4(ent, key[0] & 3);
+            else
+                more = pop_entry(stack, sp, best_t * widen, node);
+        } else {
+            // continue with the nearest child; push the others in slot order
+            // (far ones are culled when popped)
+            const int near = min(min(key[0], key[1]), min(key[2], key[3])) & 3;
+#pragma unroll
+            for (int c = 3; c >= 0; --c)
+                if (c != near && t0[c] < INFINITY) {
+                    stack[sp] = make_int2(ent[c], __float_as_int(t0[c]));
+                    ++sp;
+                }
+            if (nhit > 0)
+                node = sel4(ent, near);
+            else
+                more = pop_entry(stack, sp, best_t * widen, node);
+        }
     }
     if (!done && leaf != 0) {
         const int v = -1 - leaf;
@@ -162,8 +177,8 @@ __device__ __forceinline__ Hit trace_spec(const SceneView& s, const Ray& ray) {
     int node = 0, sp = 0, visits = 0;
     bool more = true;
     int2 stack[TRAV_STACK];
-    while (!trav_step<ANY_HIT>(s, ray.o, ray.d, inv, oi, ray.tmin, ray.tmax, best_t, best_tri, node, sp, visits, more,
-                               stack)) {
+    while (!trav_step<ANY_HIT, true>(s, ray.o, ray.d, inv, oi, ray.tmin, ray.tmax, best_t, best_tri, node, sp, visits,
+                                     more, stack)) {
     }
     Hit h;
     h.t = best_t;
@@ -235,8 +250,8 @@ __global__ void __launch_bounds__(ENGINE_THREADS) k_trace(SceneView s, Gen gen, 
         if (__all_sync(FULL, idx == DDGI_NONE)) break;
         if (idx == DDGI_NONE) continue;
 
-        const bool done = trav_step<ANY_HIT>(s, o, d, inv, oi, tmin, tmax, best_t, best_tri, node, sp, visits, more,
-                                             stack);
+        const bool done = trav_step<ANY_HIT, false>(s, o, d, inv, oi, tmin, tmax, best_t, best_tri, node, sp, visits,
+                                                    more, stack);
         if (done) {
             hits[idx] = make_float2(best_t, __uint_as_float(best_tri));
             idx = DDGI_NONE;

@@ -3,6 +3,7 @@
 // argv[1], builds with split references on or off (argv[2] = 1 / 0) and
 // checks the structure and the geometry:
 //   - every inner child index is a node other than the root, reached once;
+//     empty slots carry the inverted box, and row 7 is zero;
 //   - every triangle is referenced by some leaf (exactly once without split
 //     references), and each child box contains its child node's boxes;
 //   - without split references, each leaf box contains its triangles;
@@ -12,6 +13,7 @@
 //     triangle would miss.
 // Prints one line of counts; exit status 0 when all are clean.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -48,17 +50,13 @@ double tri_t(const float* v, V3 o, V3 d) {
     return t > 1e-9 ? t : INFINITY;
 }
 
-int child_of(const float* nd, int c) {
-    int x;
+// slot entry: 0 empty, > 0 inner node, < 0 leaf (bvh.h)
+int32_t entry_of(const float* nd, int c) {
+    int32_t x;
     std::memcpy(&x, &nd[24 + c], 4);
     return x;
 }
-int count_of(const float* nd, int c) {
-    int x;
-    std::memcpy(&x, &nd[28 + c], 4);
-    return x;
-}
-bool used(const float* nd, int c) { return child_of(nd, c) >= 0 || count_of(nd, c) > 0; }
+bool used(const float* nd, int c) { return entry_of(nd, c) != 0; }
 
 }  // namespace
 
@@ -80,11 +78,18 @@ int main(int argc, char** argv) {
     for (uint32_t n = 0; n < b.num_nodes; ++n) {
         const float* nd = &b.nodes[32 * (size_t)n];
         for (int c = 0; c < 4; ++c) {
-            if (!used(nd, c)) continue;
+            if (nd[28 + c] != 0.f) bad_child++;   // row 7 is unused
+            if (!used(nd, c)) {
+                // an empty slot's box is inverted on every axis
+                for (int a = 0; a < 3; ++a)
+                    if (nd[8 * a + c] != FLT_MAX || nd[8 * a + 4 + c] != -FLT_MAX) bad_box++;
+                continue;
+            }
             const float lo[3] = {nd[0 + c], nd[8 + c], nd[16 + c]}, hi[3] = {nd[4 + c], nd[12 + c], nd[20 + c]};
-            const int ch = child_of(nd, c), cnt = count_of(nd, c);
+            const int32_t ch = entry_of(nd, c);
             if (ch < 0) {
-                const int first = ~ch;
+                int32_t first, cnt;
+                bvh_leaf_range(ch, &first, &cnt);
                 if (first < 0 || first + cnt > (int)S) {
                     bad_child++;
                     continue;
@@ -110,7 +115,7 @@ int main(int argc, char** argv) {
                         }
                 }
             } else {
-                if (ch == 0 || (uint32_t)ch >= b.num_nodes) {
+                if ((uint32_t)ch >= b.num_nodes) {
                     bad_child++;
                     continue;
                 }
@@ -170,11 +175,13 @@ int main(int argc, char** argv) {
                     t1 = std::min(t1, tb);
                 }
                 if (!(t0 <= t1)) continue;
-                const int ch = child_of(nd, c), cnt = count_of(nd, c);
-                if (ch >= 0) {
+                const int32_t ch = entry_of(nd, c);
+                if (ch > 0) {
                     st.push_back(ch);
                 } else {
-                    for (int k = ~ch; k < ~ch + cnt; ++k) {
+                    int32_t first, cnt;
+                    bvh_leaf_range(ch, &first, &cnt);
+                    for (int k = first; k < first + cnt; ++k) {
                         uint32_t orig;
                         std::memcpy(&orig, &b.tris[12 * (size_t)k + 3], 4);
                         if (orig < T) best = std::min(best, tri_t(&v[9 * (size_t)orig], o, d));
