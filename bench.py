@@ -240,11 +240,12 @@ def measure_fp32_peak(dev, n: int = 8192, reps: int = 5) -> float:
 
 
 def launches_per_frame(spatial_passes: int, fused: bool = False) -> int:
-    """Kernels of one timed frame: probe trace + blend, BSDF-ray traversal +
-    emitter candidates + BSDF candidates, temporal (inside the BSDF-candidate
-    kernel when fused), one per spatial pass, shadow-ray traversal + shade
-    (the launch lists in profiles/ show the same count)."""
-    return 2 + 3 + (0 if fused else 1) + spatial_passes + 2
+    """Kernels of one timed frame: probe trace + the frame's blend weights +
+    blend, BSDF-ray traversal + emitter candidates + BSDF candidates, temporal
+    (inside the BSDF-candidate kernel when fused), one per spatial pass,
+    shadow-ray traversal + shade (the launch lists in profiles/ show the same
+    count)."""
+    return 3 + 3 + (0 if fused else 1) + spatial_passes + 2
 
 
 def job_time_ms(local_ms: float, ws: int, device) -> float:
@@ -444,13 +445,18 @@ def run_ours(args, ws, rank, local):
         if side_in[p] > 0:
             entry["concurrent_probe_trace_ms"] = round(side_in[p], 4)
         pass_report[p] = entry
-    # the probe blend is bound by FP32 arithmetic: (irradiance + distance
-    # texels) x rays x 10 flop per probe (the scope's count), against the
-    # FP32 GEMM throughput measured here
-    blend_flop = (st.irr_texels ** 2 + st.depth_texels ** 2) * st.rays_per_probe * 10 * sc.grid.num_probes
+    # the probe blend is bound by FP32 arithmetic.  Its weights are the same
+    # for every probe of a frame, so it runs as two products per probe:
+    # (irradiance texels x 3 + distance texels x 2) x rays FMAs, against the
+    # FP32 GEMM throughput measured here; gflop_scope is the scope's count,
+    # (irradiance + distance texels) x rays x 10 flop per probe, which
+    # recomputes the weights for every probe
+    blend_flop = 2 * (3 * st.irr_texels ** 2 + 2 * st.depth_texels ** 2) * st.rays_per_probe * sc.grid.num_probes
+    scope_flop = (st.irr_texels ** 2 + st.depth_texels ** 2) * st.rays_per_probe * 10 * sc.grid.num_probes
     fp32_peak = measure_fp32_peak(dev)
     blend_tf = blend_flop / (per_pass["probe_blend"] * 1e-3) / 1e12
     pass_report["probe_blend"].update({"gflop": round(blend_flop / 1e9, 3), "tflops": round(blend_tf, 2),
+                                       "gflop_scope": round(scope_flop / 1e9, 3),
                                        "fp32_peak_tflops_measured": round(fp32_peak, 1),
                                        "fp32_frac": round(blend_tf / fp32_peak, 4)})
     trace_ms = side_ms if side_ms is not None else per_pass["probe_trace"]

@@ -34,6 +34,7 @@ struct ddgi_ctx {
     float2* depth = nullptr;
     float4* offset = nullptr;
     float4* rays = nullptr;
+    float* blend_w = nullptr;      // the probe blend's per-frame weight tables
     float4* sf = nullptr;
     uint32_t* sf_order = nullptr;  // probe rays in an order that keeps a warp's directions together
     uint32_t* err = nullptr;
@@ -728,6 +729,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(depth, P * td * td)
     ALLOC(offset, P)
     ALLOC(rays, P * R)
+    ALLOC(blend_w, probe_blend_weights_size(volume_view(ctx), R))
     ALLOC(sf, R)
     ALLOC(sf_order, R)
     ALLOC(err, 4)
@@ -852,7 +854,7 @@ ddgi_status ddgi_probe_blend(ddgi_ctx* ctx, uint32_t frame, void* stream) {
     if (!ctx) return DDGI_ERR_INVALID_ARG;
     ProbeParams p;
     probe_params(ctx, frame, &p);
-    CK(launch_probe_blend(volume_view(ctx), p, ctx->rays, (cudaStream_t)stream));
+    CK(launch_probe_blend(volume_view(ctx), p, ctx->rays, ctx->blend_w, (cudaStream_t)stream));
     ctx->updates++;
     return DDGI_OK;
 }

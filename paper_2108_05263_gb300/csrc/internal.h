@@ -74,7 +74,10 @@ cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float
 cudaError_t launch_probe_relocate(const VolumeView& v, const ProbeParams& p, const float4* rays, float4* offset,
                                   cudaStream_t st);
 size_t probe_blend_smem(const VolumeView& v, uint32_t rays);
-cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays,
+// floats of the blend's per-frame weight tables (ray-major weights of every
+// texel, then each texel's weight sum)
+size_t probe_blend_weights_size(const VolumeView& v, uint32_t rays);
+cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays, float* weights,
                                cudaStream_t st);
 cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
                            const GBufView& g, float2* hits, uint32_t* counter, cudaStream_t st);

@@ -104,88 +104,273 @@ __device__ __forceinline__ int border_source(int X, int Y, int n) {
     return sy * w + sx;
 }
 
-// one CTA per probe; rays and directions staged in shared memory
-__global__ void __launch_bounds__(512) k_probe_blend(VolumeView v, ProbeParams pp,
-                                                     const float4* __restrict__ sf,
-                                                     const float4* __restrict__ rays) {
-    extern __shared__ float4 smem[];
-    const int R = (int)pp.rays;
-    float4* s_ray = smem;            // R: L.rgb, signed distance
-    float4* s_dir = smem + R;        // R: direction
-    const int ni = v.irr_n, nd = v.depth_n, ti = ni + 2, td = nd + 2;
-    float4* s_irr = smem + 2 * R;                             // ti*ti
-    float2* s_dep = reinterpret_cast<float2*>(s_irr + ti * ti);  // td*td
-    const int p = blockIdx.x;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        s_ray[r] = rays[(size_t)p * R + r];
-        f3 w = rotate(pp, __ldg(sf + r));
-        s_dir[r] = make_float4(w.x, w.y, w.z, 0.f);
+// The blend's weights depend on the texel and the frame's ray directions
+// only, not on the probe: irradiance texel t weighs ray k by c = max(0,
+// dir_t . w_k), distance texel t by c^sharpness (0 where c <= the cut below
+// which the weight is < 2^-40).  They are written once per frame, ray-major
+// (W[k][t] over the padded texel list: irradiance texels, padded to a
+// multiple of 4, then distance texels, padded likewise; pads weigh 0), with
+// partial weight sums over groups of 8 rays after them.  The blend is then,
+// for each probe, a product of these fixed matrices with the probe's ray
+// radiance and distances.
+struct BlendShape {
+    int G;          // probes per CTA (even)
+    int nip, ndp;   // irradiance / distance texels, padded to multiples of 4
+    int ci;         // irradiance columns per ray row: 3G padded to a multiple of 4
+    int rg_d, cg_d, rg_i, cg_i;   // warps of each product: groups of 8 row tiles x 4 column tiles
+    int warps;      // warps per CTA (one slice of the products' warps, <= 32)
+    int slices;     // CTAs per probe group
+    int kc;         // rays per staged chunk of weights
+};
+
+// CTA of 32 texels x 8 rays, one thread per (ray, padded texel); the CTA's
+// 8 weights of each texel are added in ray order into its partial sum
+__global__ void __launch_bounds__(256) k_blend_weights(VolumeView v, ProbeParams pp, BlendShape bs,
+                                                       const float4* __restrict__ sf, float* __restrict__ w) {
+    __shared__ float s_w8[8][32];
+    const int ntp = bs.nip + bs.ndp, R = (int)pp.rays;
+    const int t = blockIdx.x * 32 + (threadIdx.x & 31), k = blockIdx.y * 8 + (threadIdx.x >> 5);
+    float wk = 0.f;
+    if (t < ntp && k < R) {
+        const bool irr = t < bs.nip;
+        const int tt = irr ? t : t - bs.nip;
+        const int n = irr ? v.irr_n : v.depth_n;
+        if (tt < n * n) {
+            const f3 dt = texel_dir(tt % n, tt / n, n);
+            const f3 d = rotate(pp, __ldg(sf + k));
+            const float c = dt.x * d.x + dt.y * d.y + dt.z * d.z;
+            if (irr) {
+                if (c > 0.f) wk = c;
+            } else if (c > pp.depth_cmin && c > 0.f) {
+                wk = __powf(c, pp.depth_sharpness);
+            }
+        }
+        w[(size_t)k * ntp + t] = wk;
     }
+    s_w8[threadIdx.x >> 5][threadIdx.x & 31] = wk;
     __syncthreads();
-    float4* g_irr = v.irr + (size_t)p * ti * ti;
-    float2* g_dep = v.depth + (size_t)p * td * td;
-    const float a = pp.hysteresis;
-    const int nirr = ni * ni, ntot = nirr + nd * nd;
-    for (int k = threadIdx.x; k < ntot; k += blockDim.x) {
-        if (k < nirr) {
-            int i = k % ni, j = k / ni;
-            f3 dt = texel_dir(i, j, ni);
-            float sw = 0.f;
-            f3 sl = {0.f, 0.f, 0.f};
-            for (int r = 0; r < R; ++r) {
-                float4 d = s_dir[r];
-                float c = dt.x * d.x + dt.y * d.y + dt.z * d.z;
-                if (c > 0.f) {
-                    float4 L = s_ray[r];
-                    sw += c;
-                    sl = sl + f3{L.x, L.y, L.z} * c;
-                }
-            }
-            int idx = (j + 1) * ti + (i + 1);
-            float4 old = g_irr[idx];
-            if (sw > 0.f) {
-                float s = DDGI_PI / sw;
-                old.x = a * old.x + (1.f - a) * (sl.x * s);
-                old.y = a * old.y + (1.f - a) * (sl.y * s);
-                old.z = a * old.z + (1.f - a) * (sl.z * s);
-            }
-            s_irr[idx] = old;
-        } else {
-            int kk = k - nirr;
-            int i = kk % nd, j = kk / nd;
-            f3 dt = texel_dir(i, j, nd);
-            float sw = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int r = 0; r < R; ++r) {
-                float4 d = s_dir[r];
-                float c = dt.x * d.x + dt.y * d.y + dt.z * d.z;
-                // weights below 2^-40 are skipped (no change at fp32 resolution);
-                // a warp's texels face nearby directions, so whole warps skip most rays
-                if (c > pp.depth_cmin && c > 0.f) {
-                    float wr = __powf(c, pp.depth_sharpness);
-                    float t = fminf(fabsf(s_ray[r].w), pp.depth_tmax);
-                    sw += wr;
-                    s1 += wr * t;
-                    s2 += wr * t * t;
-                }
-            }
-            int idx = (j + 1) * td + (i + 1);
-            float2 old = g_dep[idx];
-            if (sw > 0.f) {
-                old.x = a * old.x + (1.f - a) * (s1 / sw);
-                old.y = a * old.y + (1.f - a) * (s2 / sw);
-            }
-            s_dep[idx] = old;
+    if (threadIdx.x < 32 && t < ntp) {
+        float sum = 0.f;
+        for (int j = 0; j < 8; ++j) sum += s_w8[j][threadIdx.x];
+        w[(size_t)R * ntp + (size_t)blockIdx.y * ntp + t] = sum;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Blend of G probes per CTA, one slice (blockIdx.y) of the products' warps
+// per CTA.  The probes' ray data sit in shared memory, one row per ray
+// (distance: d, d^2 of each probe, d = min(|t|, tmax); irradiance: L.rgb of
+// each probe, padded); the weights stream through shared memory in chunks of
+// bs.kc rays (cp.async, double-buffered), and each texel's weight sum adds
+// the partial sums in ray order.  Each thread owns one 4 x 4 output tile (4
+// texels x 4 columns: distance columns are (probe, moment), irradiance
+// columns (probe, channel)) and sums it over the rays in order; a warp holds
+// 8 row tiles x 4 column tiles, so one ray costs it one shared-memory
+// wavefront of weights and one of ray data for 512 FMAs.  Epilogue: normalise by the texel's weight sum
+// and mix with the old value by the hysteresis (texels whose weights sum to 0
+// keep it).  With one slice per probe group the padded tiles are staged over
+// the operands and written with their border texels; with several, the
+// interior texels go straight to memory and k_probe_gutter refreshes the
+// borders.
+__global__ void __launch_bounds__(1024) k_probe_blend(VolumeView v, ProbeParams pp, BlendShape bs,
+                                                      const float* __restrict__ w, const float4* __restrict__ rays,
+                                                      int P) {
+    extern __shared__ float4 smem4[];
+    const int R = (int)pp.rays, G = bs.G;
+    const int ni = v.irr_n, nd = v.depth_n, ni2 = ni * ni, nd2 = nd * nd;
+    const int ti = ni + 2, td = nd + 2, ntp = bs.nip + bs.ndp;
+    float* s_sum = reinterpret_cast<float*>(smem4);  // [ntp] weight sums
+    float* s_bd = s_sum + ntp;                       // [R][2G]
+    float* s_bi = s_bd + (size_t)R * 2 * G;          // [R][ci]
+    float* s_w = s_bi + (size_t)R * bs.ci;           // [2][kc][ntp]
+    const int p0 = blockIdx.x * G;
+    const int tid = threadIdx.x;
+    auto stage = [&](int c) {
+        const int k0 = c * bs.kc, kc = min(bs.kc, R - k0);
+        const float4* src = reinterpret_cast<const float4*>(w + (size_t)k0 * ntp);
+        float4* dst = reinterpret_cast<float4*>(s_w + (size_t)(c & 1) * bs.kc * ntp);
+        for (int i = tid; i < kc * ntp / 4; i += blockDim.x) cp_async16(dst + i, src + i);
+        cp_async_commit();
+    };
+    stage(0);
+    {
+        const float* part = w + (size_t)R * ntp;
+        const int nparts = (R + 7) / 8;
+        for (int t = tid; t < ntp; t += blockDim.x) {
+            float sum = 0.f;
+            for (int j = 0; j < nparts; ++j) sum += __ldg(part + (size_t)j * ntp + t);
+            s_sum[t] = sum;
         }
     }
-    __syncthreads();
-    // write the padded tiles, border texels repeating their fold partner
-    for (int k = threadIdx.x; k < ti * ti; k += blockDim.x) {
-        int X = k % ti, Y = k / ti;
-        g_irr[k] = s_irr[border_source(X, Y, ni)];
+    for (int i = tid; i < R * G; i += blockDim.x) {
+        const int g = i / R, k = i - g * R;
+        float4 ray = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p0 + g < P) ray = __ldg(rays + (size_t)(p0 + g) * R + k);
+        const float d = fminf(fabsf(ray.w), pp.depth_tmax);
+        s_bd[k * 2 * G + 2 * g] = d;
+        s_bd[k * 2 * G + 2 * g + 1] = d * d;
+        s_bi[k * bs.ci + 3 * g] = ray.x;
+        s_bi[k * bs.ci + 3 * g + 1] = ray.y;
+        s_bi[k * bs.ci + 3 * g + 2] = ray.z;
     }
-    for (int k = threadIdx.x; k < td * td; k += blockDim.x) {
-        int X = k % td, Y = k / td;
-        g_dep[k] = s_dep[border_source(X, Y, nd)];
+    for (int i = tid; i < R * (bs.ci - 3 * G); i += blockDim.x) {   // pad columns
+        const int k = i / (bs.ci - 3 * G), c = i - k * (bs.ci - 3 * G);
+        s_bi[k * bs.ci + 3 * G + c] = 0.f;
+    }
+    // this thread's tile
+    const int wg = blockIdx.y * bs.warps + (tid >> 5), lane = tid & 31;
+    const int nwd = bs.rg_d * bs.cg_d, nwi = bs.rg_i * bs.cg_i;
+    const bool is_d = wg < nwd, is_i = !is_d && wg < nwd + nwi;
+    int rt = 0, ct = 0, nrt = 1, nct = 1;
+    if (is_d) {
+        rt = (wg % bs.rg_d) * 8 + (lane & 7);
+        ct = (wg / bs.rg_d) * 4 + (lane >> 3);
+        nrt = bs.ndp / 4;
+        nct = 2 * G / 4;
+    } else if (is_i) {
+        const int wi = wg - nwd;
+        rt = (wi % bs.rg_i) * 8 + (lane & 7);
+        ct = (wi / bs.rg_i) * 4 + (lane >> 3);
+        nrt = bs.nip / 4;
+        nct = bs.ci / 4;
+    }
+    const bool live = (is_d || is_i) && rt < nrt && ct < nct;
+    // clamped tile for lanes past the edge (their sums are not stored)
+    const int wrow = (is_d ? bs.nip : 0) + 4 * min(rt, nrt - 1);
+    const int col = 4 * min(ct, nct - 1);
+    const float* bbase = is_d ? s_bd : s_bi;
+    const int bstride = is_d ? 2 * G : bs.ci;
+    float acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    const int nchunk = (R + bs.kc - 1) / bs.kc;
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) {
+            stage(c + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (is_d || is_i) {
+            const float* wr = s_w + (size_t)(c & 1) * bs.kc * ntp + wrow;
+            const int k0 = c * bs.kc, kc = min(bs.kc, R - k0);
+            const float* br = bbase + (size_t)k0 * bstride + col;
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) {
+                const float4 wv = *reinterpret_cast<const float4*>(wr + kk * ntp);
+                const float4 bv = *reinterpret_cast<const float4*>(br + kk * bstride);
+                const float wa[4] = {wv.x, wv.y, wv.z, wv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[4 * r + q] = fmaf(wa[r], ba[q], acc[4 * r + q]);
+            }
+        }
+        __syncthreads();   // the buffer is refilled two chunks on
+    }
+    const float a = pp.hysteresis;
+    const bool staged = bs.slices == 1;
+    // padded tiles staged over the operands (after s_sum): [G][ti*ti] float4, [G][td*td] float2
+    float4* s_irr = reinterpret_cast<float4*>(s_sum + (ntp + 3) / 4 * 4);
+    float2* s_dep = reinterpret_cast<float2*>(s_irr + (size_t)G * ti * ti);
+    if (live && is_d) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int t = wrow - bs.nip + r;
+            if (t >= nd2) break;
+            const float sw = s_sum[wrow + r];
+            const int idx = (t / nd + 1) * td + (t % nd + 1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int g = col / 2 + h;
+                if (g >= G || p0 + g >= P) break;
+                float2* o = v.depth + (size_t)(p0 + g) * td * td + idx;
+                float2 old = *o;
+                if (sw > 0.f) {
+                    old.x = a * old.x + (1.f - a) * (acc[4 * r + 2 * h] / sw);
+                    old.y = a * old.y + (1.f - a) * (acc[4 * r + 2 * h + 1] / sw);
+                }
+                if (staged)
+                    s_dep[g * td * td + idx] = old;
+                else
+                    *o = old;
+            }
+        }
+    } else if (live) {
+        const float* g_irr_f = reinterpret_cast<const float*>(v.irr);
+        float* s_irr_f = reinterpret_cast<float*>(s_irr);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int t = wrow + r;
+            if (t >= ni2) break;
+            const float sw = s_sum[t];
+            const int idx = (t / ni + 1) * ti + (t % ni + 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cc = col + q, g = cc / 3, ch = cc - 3 * g;
+                if (g >= G || p0 + g >= P) break;
+                const size_t o = ((size_t)(p0 + g) * ti * ti + idx) * 4;
+                float old = g_irr_f[o + ch];
+                if (sw > 0.f) old = a * old + (1.f - a) * (acc[4 * r + q] * (DDGI_PI / sw));
+                if (staged) {
+                    s_irr_f[((size_t)g * ti * ti + idx) * 4 + ch] = old;
+                    if (ch == 0) s_irr_f[((size_t)g * ti * ti + idx) * 4 + 3] = g_irr_f[o + 3];
+                } else {
+                    reinterpret_cast<float*>(v.irr)[o + ch] = old;
+                }
+            }
+        }
+    }
+    if (!staged) return;
+    __syncthreads();
+    // the padded tiles, border texels repeating their fold partner
+    const int gn = min(G, P - p0);
+    for (int i = tid; i < gn * ti * ti; i += blockDim.x) {
+        const int g = i / (ti * ti), k = i - g * ti * ti;
+        v.irr[(size_t)(p0 + g) * ti * ti + k] = s_irr[g * ti * ti + border_source(k % ti, k / ti, ni)];
+    }
+    for (int i = tid; i < gn * td * td; i += blockDim.x) {
+        const int g = i / (td * td), k = i - g * td * td;
+        v.depth[(size_t)(p0 + g) * td * td + k] = s_dep[g * td * td + border_source(k % td, k / td, nd)];
+    }
+}
+
+// border texels of every probe's padded tiles repeat their fold partner
+// (after a blend whose CTAs each covered part of a probe's texels)
+__global__ void __launch_bounds__(256) k_probe_gutter(VolumeView v, int P) {
+    const int ni = v.irr_n, nd = v.depth_n, ti = ni + 2, td = nd + 2;
+    const int bi = 4 * (ti - 1), bd = 4 * (td - 1);   // border texels per tile
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * (bi + bd)) return;
+    const int p = i / (bi + bd), j = i - p * (bi + bd);
+    const bool irr = j < bi;
+    const int jj = irr ? j : j - bi, w = irr ? ti : td, n = irr ? ni : nd;
+    // border walk: top row, bottom row, then the left and right columns
+    int X, Y;
+    if (jj < w) {
+        X = jj, Y = 0;
+    } else if (jj < 2 * w) {
+        X = jj - w, Y = w - 1;
+    } else {
+        const int m = jj - 2 * w;
+        X = (m & 1) ? w - 1 : 0;
+        Y = 1 + (m >> 1);
+    }
+    const int src = border_source(X, Y, n);
+    if (irr) {
+        float4* tile = v.irr + (size_t)p * ti * ti;
+        tile[Y * ti + X] = tile[src];
+    } else {
+        float2* tile = v.depth + (size_t)p * td * td;
+        tile[Y * td + X] = tile[src];
     }
 }
 
@@ -277,25 +462,84 @@ cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const Pr
     return cudaGetLastError();
 }
 
-size_t probe_blend_smem(const VolumeView& v, uint32_t rays) {
-    int ti = v.irr_n + 2, td = v.depth_n + 2;
-    return sizeof(float4) * (2 * (size_t)rays + ti * ti) + sizeof(float2) * td * td;
+namespace {
+
+BlendShape blend_shape(const VolumeView& v, int G) {
+    BlendShape b;
+    b.G = G;
+    b.nip = (v.irr_n * v.irr_n + 3) / 4 * 4;
+    b.ndp = (v.depth_n * v.depth_n + 3) / 4 * 4;
+    b.ci = (3 * G + 3) / 4 * 4;
+    b.rg_d = (b.ndp / 4 + 7) / 8;
+    b.cg_d = (2 * G / 4 + 3) / 4;
+    b.rg_i = (b.nip / 4 + 7) / 8;
+    b.cg_i = (b.ci / 4 + 3) / 4;
+    const int total = b.rg_d * b.cg_d + b.rg_i * b.cg_i;
+    b.slices = (total + 31) / 32;   // <= 32 warps per CTA
+    b.warps = (total + b.slices - 1) / b.slices;
+    b.kc = std::max(1, std::min(16, 8192 / (b.nip + b.ndp)));
+    return b;
 }
 
-cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays,
-                               cudaStream_t st) {
-    int P = v.counts.x * v.counts.y * v.counts.z;
-    if (P == 0) return cudaSuccess;
-    size_t smem = probe_blend_smem(v, p.rays);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_probe_blend, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+// shared memory of the blend: weight sums, the probes' ray rows and two
+// weight chunks; with one slice, also room for the padded tiles staged
+// after the sums
+size_t blend_smem(const VolumeView& v, uint32_t rays, const BlendShape& b) {
+    const size_t ntp = b.nip + b.ndp, ti = v.irr_n + 2, td = v.depth_n + 2;
+    const size_t ops = sizeof(float) * (ntp + (size_t)rays * (2 * b.G + b.ci) + 2ull * b.kc * ntp);
+    const size_t tiles = sizeof(float) * ((ntp + 3) / 4 * 4) +
+                         b.G * (sizeof(float4) * ti * ti + sizeof(float2) * td * td);
+    return b.slices == 1 && tiles > ops ? tiles : ops;
+}
+
+// probes per CTA: even, at most 16, the CTAs no more than the SMs where
+// possible, <= 160 KB of shared memory
+BlendShape pick_blend(const VolumeView& v, uint32_t rays, int P) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
     }
-    // one thread per texel of both maps when they fit one CTA (320 for 8x8 +
-    // 16x16), so that the texel loop runs once
-    const int texels = v.irr_n * v.irr_n + v.depth_n * v.depth_n;
-    const int threads = std::min(512, (texels + 31) / 32 * 32);
-    k_probe_blend<<<P, threads, smem, st>>>(v, p, p.sf, rays);
+    int G = (P + sms - 1) / sms;
+    G = std::max(2, std::min(16, (G + 1) / 2 * 2));
+    for (; G > 2; G -= 2)
+        if (blend_smem(v, rays, blend_shape(v, G)) <= 160 * 1024) break;
+    return blend_shape(v, G);
+}
+
+}  // namespace
+
+size_t probe_blend_weights_size(const VolumeView& v, uint32_t rays) {
+    const BlendShape b = blend_shape(v, 2);
+    return (size_t)(b.nip + b.ndp) * (rays + (rays + 7) / 8);
+}
+
+size_t probe_blend_smem(const VolumeView& v, uint32_t rays) {
+    const int P = v.counts.x * v.counts.y * v.counts.z;
+    return blend_smem(v, rays, pick_blend(v, rays, P));
+}
+
+cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays, float* weights,
+                               cudaStream_t st) {
+    const int P = v.counts.x * v.counts.y * v.counts.z;
+    if (P == 0) return cudaSuccess;
+    const BlendShape b = pick_blend(v, p.rays, P);
+    k_blend_weights<<<dim3((b.nip + b.ndp + 31) / 32, (p.rays + 7) / 8), 256, 0, st>>>(v, p, b, p.sf, weights);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = blend_smem(v, p.rays, b);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        e = cudaFuncSetAttribute(k_probe_blend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k_probe_blend<<<dim3((P + b.G - 1) / b.G, b.slices), 32 * b.warps, smem, st>>>(v, p, b, weights, rays, P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || b.slices == 1) return e;
+    const int borders = P * (4 * (v.irr_n + 1) + 4 * (v.depth_n + 1));
+    k_probe_gutter<<<(borders + 255) / 256, 256, 0, st>>>(v, P);
     return cudaGetLastError();
 }
