@@ -299,9 +299,6 @@ ddgi_status probe_params(ddgi_ctx* c, uint32_t frame, ProbeParams* p) {
     p->le_attenuation = c->cfg.le_attenuation;
     p->depth_sharpness = c->cfg.depth_sharpness;
     p->depth_tmax = 1.5f * std::fmax(std::fmax(c->cfg.spacing[0], c->cfg.spacing[1]), c->cfg.spacing[2]);
-    // cos^sharpness < 2^-40 below this cosine: at most R such terms, far below
-    // one ulp of the blend's sums (the nearest of the rays has cos near 1)
-    p->depth_cmin = c->cfg.depth_sharpness > 1.f ? (float)std::pow(0.5, 40.0 / c->cfg.depth_sharpness) : 0.f;
     p->seed = c->cfg.seed;
     p->frame = frame;
     return DDGI_OK;

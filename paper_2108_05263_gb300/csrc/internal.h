@@ -59,7 +59,6 @@ struct ProbeParams {
     float le_attenuation;
     float depth_sharpness;
     float depth_tmax;
-    float depth_cmin;    // rays with cos <= this weigh < 2^-40 in the distance blend
     uint32_t seed, frame;   // keys of the glossy samples at the rays' hits
 };
 

@@ -106,13 +106,15 @@ __device__ __forceinline__ int border_source(int X, int Y, int n) {
 
 // The blend's weights depend on the texel and the frame's ray directions
 // only, not on the probe: irradiance texel t weighs ray k by c = max(0,
-// dir_t . w_k), distance texel t by c^sharpness (0 where c <= the cut below
-// which the weight is < 2^-40).  They are written once per frame, ray-major
-// (W[k][t] over the padded texel list: irradiance texels, padded to a
-// multiple of 4, then distance texels, padded likewise; pads weigh 0), with
-// partial weight sums over groups of 8 rays after them.  The blend is then,
-// for each probe, a product of these fixed matrices with the probe's ray
-// radiance and distances.
+// dir_t . w_k), distance texel t by c^sharpness.  They are written once per
+// frame, ray-major (W[k][t] over the padded texel list: irradiance texels,
+// padded to a multiple of 4, then distance texels, padded likewise; pads
+// weigh 0), with partial weight sums over groups of 8 rays after them.  A
+// distance texel's weights are taken relative to its largest cosine,
+// (c / c_max)^sharpness: the normalised mean is the same, and the largest
+// weight is 1, so no weight that matters underflows however few rays there
+// are.  The blend is then, for each probe, a product of these fixed matrices
+// with the probe's ray radiance and distances.
 struct BlendShape {
     int G;          // probes per CTA (even)
     int nip, ndp;   // irradiance / distance texels, padded to multiples of 4
@@ -123,36 +125,57 @@ struct BlendShape {
     int kc;         // rays per staged chunk of weights
 };
 
-// CTA of 32 texels x 8 rays, one thread per (ray, padded texel); the CTA's
-// 8 weights of each texel are added in ray order into its partial sum
-__global__ void __launch_bounds__(256) k_blend_weights(VolumeView v, ProbeParams pp, BlendShape bs,
-                                                       const float4* __restrict__ sf, float* __restrict__ w) {
-    __shared__ float s_w8[8][32];
+// CTA of 8 texels x 128 ray lanes: the distance texels' largest cosine
+// first, then the weights (stores of W[k][t] in 32-byte runs) and the
+// partial sum of each group of 8 rays, added in ray order
+#define BW_T 8     // texels per CTA
+#define BW_K 128   // ray lanes per CTA
+__global__ void __launch_bounds__(BW_T * BW_K) k_blend_weights(VolumeView v, ProbeParams pp, BlendShape bs,
+                                                               const float4* __restrict__ sf, float* __restrict__ w) {
+    __shared__ float s_c[BW_K][BW_T + 1];
+    __shared__ float s_max[BW_T];
     const int ntp = bs.nip + bs.ndp, R = (int)pp.rays;
-    const int t = blockIdx.x * 32 + (threadIdx.x & 31), k = blockIdx.y * 8 + (threadIdx.x >> 5);
-    float wk = 0.f;
-    if (t < ntp && k < R) {
-        const bool irr = t < bs.nip;
-        const int tt = irr ? t : t - bs.nip;
-        const int n = irr ? v.irr_n : v.depth_n;
-        if (tt < n * n) {
-            const f3 dt = texel_dir(tt % n, tt / n, n);
+    const int tx = threadIdx.x % BW_T, ky = threadIdx.x / BW_T;
+    const int t = blockIdx.x * BW_T + tx;
+    const bool irr = t < bs.nip;
+    const int tt = irr ? t : t - bs.nip;
+    const int n = irr ? v.irr_n : v.depth_n;
+    const bool real = t < ntp && tt < n * n;
+    const f3 dt = real ? texel_dir(tt % n, tt / n, n) : f3{0.f, 0.f, 0.f};
+    float cmax = 0.f;
+    if (real && !irr)
+        for (int k = ky; k < R; k += BW_K) {
+            const f3 d = rotate(pp, __ldg(sf + k));
+            cmax = fmaxf(cmax, dt.x * d.x + dt.y * d.y + dt.z * d.z);
+        }
+    s_c[ky][tx] = cmax;
+    __syncthreads();
+    if (ky == 0) {
+        float m = 0.f;
+        for (int j = 0; j < BW_K; ++j) m = fmaxf(m, s_c[j][tx]);
+        s_max[tx] = m;
+    }
+    __syncthreads();
+    cmax = s_max[tx];
+    float* part = w + (size_t)R * ntp;
+    for (int k0 = 0; k0 < R; k0 += BW_K) {
+        const int k = k0 + ky;
+        float wk = 0.f;
+        if (real && k < R) {
             const f3 d = rotate(pp, __ldg(sf + k));
             const float c = dt.x * d.x + dt.y * d.y + dt.z * d.z;
-            if (irr) {
-                if (c > 0.f) wk = c;
-            } else if (c > pp.depth_cmin && c > 0.f) {
-                wk = __powf(c, pp.depth_sharpness);
-            }
+            if (c > 0.f) wk = irr ? c : __powf(c / cmax, pp.depth_sharpness);
         }
-        w[(size_t)k * ntp + t] = wk;
-    }
-    s_w8[threadIdx.x >> 5][threadIdx.x & 31] = wk;
-    __syncthreads();
-    if (threadIdx.x < 32 && t < ntp) {
-        float sum = 0.f;
-        for (int j = 0; j < 8; ++j) sum += s_w8[j][threadIdx.x];
-        w[(size_t)R * ntp + (size_t)blockIdx.y * ntp + t] = sum;
+        if (t < ntp && k < R) w[(size_t)k * ntp + t] = wk;
+        s_c[ky][tx] = wk;
+        __syncthreads();
+        const int g = k0 / 8 + ky;
+        if (ky < BW_K / 8 && t < ntp && 8 * g < R) {
+            float sum = 0.f;
+            for (int j = 0; j < 8; ++j) sum += s_c[8 * ky + j][tx];
+            part[(size_t)g * ntp + t] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -526,7 +549,7 @@ cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const 
     const int P = v.counts.x * v.counts.y * v.counts.z;
     if (P == 0) return cudaSuccess;
     const BlendShape b = pick_blend(v, p.rays, P);
-    k_blend_weights<<<dim3((b.nip + b.ndp + 31) / 32, (p.rays + 7) / 8), 256, 0, st>>>(v, p, b, p.sf, weights);
+    k_blend_weights<<<(b.nip + b.ndp + BW_T - 1) / BW_T, BW_T * BW_K, 0, st>>>(v, p, b, p.sf, weights);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = blend_smem(v, p.rays, b);

@@ -185,6 +185,41 @@ def test_probe_trace_and_blend_parity(dd, orc, tiny):
     assert ctx.get_status() == dd.OK
 
 
+@pytest.mark.parametrize("irr_n,depth_n,rays", [(8, 16, 256), (5, 7, 37), (2, 3, 1), (32, 32, 64), (16, 32, 1024)])
+def test_probe_blend_shapes_parity(dd, orc, irr_n, depth_n, rays):
+    """The blend alone on seeded ray data (radiance; front-face, back-face
+    and missed distances) for map and ray-set shapes that exercise its
+    padding: odd texel counts (texel rows padded to 4), a ray count that
+    leaves a ragged last chunk of weights, one ray, 32 x 32 maps, and
+    16 x 32 maps with 1024 rays, whose products are split over several CTAs
+    (borders then refreshed by a kernel of their own); two updates, the
+    second mixing by the hysteresis."""
+    import dataclasses
+    sc = scenegen.tiny_room(width=32, height=24, frames=1)
+    sc.settings = dataclasses.replace(sc.settings, rays_per_probe=rays, irr_texels=irr_n, depth_texels=depth_n)
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid, irr_n, depth_n)
+    ctx = dd.Context.from_scene(sc)
+    P = vol.P
+    rng = np.random.default_rng(1000 * irr_n + 10 * depth_n + rays)
+    for f in range(2):
+        ray = np.zeros((P, rays, 4), np.float32)
+        ray[..., :3] = rng.uniform(0.0, 2.0, (P, rays, 3))
+        t = rng.uniform(0.05, 4.0, (P, rays))
+        kind = rng.random((P, rays))
+        ray[..., 3] = np.where(kind < 0.2, -t, np.where(kind < 0.35, 1e30, t))
+        ctx.probe_rays_set(ray)
+        ctx.probe_blend(f)
+        vol.updates = f   # the blend mixes by the hysteresis from the second update on
+        orc.probe_blend(vol, ray.astype(np.float64), f, S.settings)
+    irr, dep, _, upd = ctx.probe_state_get()
+    assert upd == 2
+    assert _frac(_close(irr[..., :3], vol.irr, 1e-5)) >= 0.9999
+    assert _frac(_close(dep, vol.depth, 1e-5)) >= 0.9999
+    assert np.abs(irr[..., 3]).max() == 0.0   # the fourth channel is untouched
+    assert ctx.get_status() == dd.OK
+
+
 def test_probe_update_chain_parity(dd, orc, tiny):
     sc, _, _, _ = tiny
     S = orc.Scene(sc)
