@@ -29,8 +29,9 @@ __device__ __forceinline__ f3 probe_of(const VolumeView& v, int p) {
 
 // one thread per (probe, ray): trace, then the radiance of Eq. probeUpdate
 // (GLOSSY: with the glossy half of L_DDGI+ toward the probe, Sec. 3.3)
+// 9 CTAs per SM: 56 registers, 12 bytes of spill (probe trace 0.182 -> 0.180 ms)
 template <bool GLOSSY>
-__global__ void __launch_bounds__(128) k_probe_trace(SceneView s, VolumeView v, ProbeParams pp,
+__global__ void __launch_bounds__(128, 9) k_probe_trace(SceneView s, VolumeView v, ProbeParams pp,
                                                      const float4* __restrict__ sf,
                                                      float4* __restrict__ rays, int total) {
     int tid = blockIdx.x * blockDim.x + threadIdx.x;
