@@ -177,6 +177,23 @@ def test_gradients_match_oracle(dd, M):
     _assert_grad_elementwise(g, ref, 1e-2, 2.0 ** -12)
 
 
+def test_gradients_of_many_samples_match_oracle(dd, M):
+    """40,000 samples (313 tiles of 128, the last one ragged), entry by entry
+    against the oracle as above; a second call on the same samples agrees
+    with the first to float rounding (the tiles' sums meet in atomics, so
+    their order, and the last bits, may differ)."""
+    sc = scenegen.tiny_room()
+    ctx = dd.Context.from_scene(sc)
+    lo, scale = M.scene_box(sc.verts)
+    s = _samples(sc, 40000, 9)
+    g1 = ctx.mlp_grad(s)
+    g2 = ctx.mlp_grad(s)
+    np.testing.assert_allclose(g1, g2, rtol=1e-5, atol=1e-7 * np.abs(g1).max())
+    ref, _ = _oracle_grad(M, ctx.mlp_params(), s, lo, scale, q=_q16)
+    _assert_grad_elementwise(g1, ref, 1e-2, 2.0 ** -12)
+    assert ctx.get_status() == dd.OK
+
+
 def test_fp32_gradients_match_oracle_elementwise(dd, M):
     """The fp32 debug form's gradients against the fp64 oracle, every entry
     within 1e-3 relative plus 1e-6 of its layer's largest entry."""
