@@ -46,8 +46,8 @@ struct BNode {
 constexpr int kBins = 128;
 constexpr int kMaxLeaf = 4;
 constexpr int kSweepMax = 4096;   // nodes up to this size: exact SAH sweep over sorted centroids
-constexpr int kSplitDepth = 2;    // early split clipping: at most 2^kSplitDepth references per triangle
-constexpr double kSplitAreaFactor = 2.0;   // split boxes larger than this x the mean triangle box
+constexpr int kSplitDepth = 4;    // early split clipping: at most 2^kSplitDepth references per triangle
+constexpr double kSplitAreaFactor = 1.0;   // split boxes larger than this x the mean triangle box
 
 struct Builder {
     const float* verts;
