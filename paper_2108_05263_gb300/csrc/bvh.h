@@ -23,7 +23,8 @@ inline void bvh_leaf_range(int32_t entry, int32_t* first, int32_t* count) {
 }
 
 // Builds an SAH binary BVH over `num_tris` triangles (9 floats each) and
-// collapses it to 4-wide nodes.  split_large: triangles with large boxes
-// enter as several clipped references (a triangle then fills several slots of
-// `tris`); off for scenes whose boxes are refitted from whole triangles.
+// collapses it to 4-wide nodes.  split_large: spatial splits, so that a
+// triangle may be entered as several clipped references (it then fills
+// several slots of `tris`); off for scenes whose boxes are refitted from
+// whole triangles.
 void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* out);

@@ -1,8 +1,10 @@
-// Host BVH construction: surface-area-heuristic binary BVH (binned for large
-// nodes, an exact sweep over sorted centroids for the rest), collapsed
-// into 4-wide nodes whose children boxes are stored as SoA float4 rows, with
-// each slot's entry code (bvh.h) precomputed, so that one node is six box rows
-// and one entry row of 16 bytes on the device.
+// Host BVH construction: a surface-area-heuristic binary BVH -- with spatial
+// splits where triangles may be referenced more than once, else with object
+// splits only (binned for large nodes, an exact sweep over sorted centroids
+// for the rest) -- collapsed into 4-wide nodes whose children boxes are
+// stored as SoA float4 rows, with each slot's entry code (bvh.h)
+// precomputed, so that one node is six box rows and one entry row of 16
+// bytes on the device.
 #include <algorithm>
 #include <array>
 #include <cfloat>
@@ -46,8 +48,6 @@ struct BNode {
 constexpr int kBins = 128;
 constexpr int kMaxLeaf = 4;
 constexpr int kSweepMax = 4096;   // nodes up to this size: exact SAH sweep over sorted centroids
-constexpr int kSplitDepth = 4;    // early split clipping: at most 2^kSplitDepth references per triangle
-constexpr double kSplitAreaFactor = 1.0;   // split boxes larger than this x the mean triangle box
 
 struct Builder {
     const float* verts;
@@ -223,93 +223,285 @@ int clip_poly(const float (*in)[3], int n, int axis, float c, bool below, float 
     return m;
 }
 
-struct SplitRef {
+struct Ref {
     int tri;
     Box box;
 };
 
-// Early split clipping (Ernst & Greiner 2007): a triangle whose box is large
-// is entered as several references, each with the box of the part of the
-// triangle inside one half of its parent box (halved along the longest axis)
-void split_refs(int tri, const float (*poly)[3], int n, const Box& box, int depth, float area_limit,
-                std::vector<SplitRef>& out) {
-    float ext[3];
-    for (int a = 0; a < 3; ++a) ext[a] = box.hi[a] - box.lo[a];
-    if (depth >= kSplitDepth || box.area() <= area_limit || n < 3) {
-        out.push_back({tri, box});
-        return;
-    }
-    const int axis = ext[0] >= ext[1] && ext[0] >= ext[2] ? 0 : (ext[1] >= ext[2] ? 1 : 2);
-    const float c = 0.5f * (box.lo[axis] + box.hi[axis]);
-    for (int side = 0; side < 2; ++side) {
-        float part[16][3];
-        const int m = clip_poly(poly, n, axis, c, side == 0, part);
-        if (m < 3) continue;
-        Box pb;
-        for (int i = 0; i < m; ++i) pb.grow(part[i]);
-        for (int a = 0; a < 3; ++a) {   // stay inside the parent box
-            pb.lo[a] = std::max(pb.lo[a], box.lo[a]);
-            pb.hi[a] = std::min(pb.hi[a], box.hi[a]);
+// the box of the part of triangle `tri` inside `clip` (invalid if none)
+Box clip_tri_box(const float* verts, int tri, const Box& clip) {
+    float poly[16][3], tmp[16][3];
+    const float* v = verts + 9 * (size_t)tri;
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) poly[k][a] = v[3 * k + a];
+    int n = 3;
+    for (int a = 0; a < 3 && n >= 3; ++a)
+        for (int side = 0; side < 2 && n >= 3; ++side) {
+            n = clip_poly(poly, n, a, side == 0 ? clip.lo[a] : clip.hi[a], side == 1, tmp);
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 3; ++c) poly[i][c] = tmp[i][c];
         }
-        if (!pb.valid()) continue;
-        split_refs(tri, part, m, pb, depth + 1, area_limit, out);
+    Box b;
+    if (n < 3) return b;
+    for (int i = 0; i < n; ++i) b.grow(poly[i]);
+    for (int a = 0; a < 3; ++a) {   // stay inside the clip box
+        b.lo[a] = std::max(b.lo[a], clip.lo[a]);
+        b.hi[a] = std::min(b.hi[a], clip.hi[a]);
     }
+    return b;
+}
+
+float overlap_area(const Box& a, const Box& b) {
+    Box o;
+    for (int k = 0; k < 3; ++k) {
+        o.lo[k] = std::max(a.lo[k], b.lo[k]);
+        o.hi[k] = std::min(a.hi[k], b.hi[k]);
+        if (o.lo[k] > o.hi[k]) return 0.f;
+    }
+    return o.area();
+}
+
+// Spatial-split SAH build (Stich, Friedrich and Dietrich 2009): at each node
+// the binned object split over the references' box centres is compared with
+// the best of kSpatialBins spatial splits per axis, for which each reference
+// is clipped to every bin it spans (its triangle clipped to the reference's
+// box within the bin); spatial splits are tried only where the object
+// split's children overlap by more than kSpatialAlpha of the root's surface
+// area.  A reference that straddles the chosen plane continues on both
+// sides with the boxes of its two parts.  Leaves list triangle ids in leaf
+// order (a triangle once per reference).
+constexpr float kSpatialAlpha = 1e-3f;
+constexpr int kSpatialBins = 32;
+
+int build_spatial(const float* verts, int T, std::vector<BNode>& nodes, std::vector<int>& leaf_tri) {
+    struct Item {
+        std::vector<Ref> refs;
+        int parent, side, depth;
+    };
+    std::vector<Ref> init(T);
+    Box rootb;
+    for (int t = 0; t < T; ++t) {
+        init[t].tri = t;
+        for (int k = 0; k < 3; ++k) init[t].box.grow(verts + 9 * (size_t)t + 3 * k);
+        rootb.grow(init[t].box);
+    }
+    const float root_area = rootb.area();
+    size_t total = (size_t)T;   // references so far
+    std::vector<Item> work;
+    work.push_back({std::move(init), -1, 0, 0});
+    int root = -1;
+    while (!work.empty()) {
+        Item it = std::move(work.back());
+        work.pop_back();
+        const std::vector<Ref>& refs = it.refs;
+        const int n = (int)refs.size();
+        Box b, cb;
+        for (const Ref& r : refs) {
+            b.grow(r.box);
+            float c[3];
+            for (int a = 0; a < 3; ++a) c[a] = 0.5f * (r.box.lo[a] + r.box.hi[a]);
+            cb.grow(c);
+        }
+        // object split: binned SAH over the box centres
+        float best_o = FLT_MAX;
+        int oa = -1, obin = -1;
+        Box oL, oR;
+        for (int a = 0; a < 3 && n > 1; ++a) {
+            const float ext = cb.hi[a] - cb.lo[a];
+            if (!(ext > 0.f)) continue;
+            Box bb[kBins];
+            int bc[kBins] = {0};
+            const float scale = kBins / ext;
+            for (const Ref& r : refs) {
+                const int bi = std::min(kBins - 1, (int)((0.5f * (r.box.lo[a] + r.box.hi[a]) - cb.lo[a]) * scale));
+                bc[bi]++;
+                bb[bi].grow(r.box);
+            }
+            Box lb[kBins], rb[kBins];
+            int lc[kBins], rc[kBins];
+            Box acc;
+            int m = 0;
+            for (int i = 0; i < kBins; ++i) {
+                acc.grow(bb[i]);
+                m += bc[i];
+                lb[i] = acc;
+                lc[i] = m;
+            }
+            acc = Box();
+            m = 0;
+            for (int i = kBins - 1; i >= 0; --i) {
+                acc.grow(bb[i]);
+                m += bc[i];
+                rb[i] = acc;
+                rc[i] = m;
+            }
+            for (int i = 0; i + 1 < kBins; ++i) {
+                if (lc[i] == 0 || rc[i + 1] == 0) continue;
+                const float c = lb[i].area() * lc[i] + rb[i + 1].area() * rc[i + 1];
+                if (c < best_o) {
+                    best_o = c;
+                    oa = a;
+                    obin = i;
+                    oL = lb[i];
+                    oR = rb[i + 1];
+                }
+            }
+        }
+        // spatial split where the object split's children overlap
+        float best_s = FLT_MAX, splane = 0.f;
+        int sa = -1;
+        if (n > 1 && oa >= 0 && it.depth < 64 && total < 4 * (size_t)T &&
+            overlap_area(oL, oR) > kSpatialAlpha * root_area) {
+            for (int a = 0; a < 3; ++a) {
+                const float ext = b.hi[a] - b.lo[a];
+                if (!(ext > 0.f)) continue;
+                const float w = ext / kSpatialBins;
+                Box bb[kSpatialBins];
+                int ent[kSpatialBins] = {0}, ex[kSpatialBins] = {0};
+                for (const Ref& r : refs) {
+                    const int b0 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.lo[a] - b.lo[a]) / w)));
+                    const int b1 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.hi[a] - b.lo[a]) / w)));
+                    ent[b0]++;
+                    ex[b1]++;
+                    if (b0 == b1) {
+                        bb[b0].grow(r.box);
+                        continue;
+                    }
+                    for (int k = b0; k <= b1; ++k) {
+                        Box cl = r.box;
+                        cl.lo[a] = std::max(cl.lo[a], b.lo[a] + k * w);
+                        cl.hi[a] = std::min(cl.hi[a], k == kSpatialBins - 1 ? b.hi[a] : b.lo[a] + (k + 1) * w);
+                        const Box pb = clip_tri_box(verts, r.tri, cl);
+                        if (pb.valid()) bb[k].grow(pb);
+                    }
+                }
+                Box lb[kSpatialBins], rb[kSpatialBins];
+                int lc[kSpatialBins], rc[kSpatialBins];
+                Box acc;
+                int m = 0;
+                for (int i = 0; i < kSpatialBins; ++i) {
+                    acc.grow(bb[i]);
+                    m += ent[i];
+                    lb[i] = acc;
+                    lc[i] = m;
+                }
+                acc = Box();
+                m = 0;
+                for (int i = kSpatialBins - 1; i >= 0; --i) {
+                    acc.grow(bb[i]);
+                    m += ex[i];
+                    rb[i] = acc;
+                    rc[i] = m;
+                }
+                for (int i = 0; i + 1 < kSpatialBins; ++i) {
+                    if (lc[i] == 0 || rc[i + 1] == 0 || lc[i] >= n || rc[i + 1] >= n) continue;
+                    const float c = lb[i].area() * lc[i] + rb[i + 1].area() * rc[i + 1];
+                    if (c < best_s) {
+                        best_s = c;
+                        sa = a;
+                        splane = b.lo[a] + (i + 1) * w;
+                    }
+                }
+            }
+        }
+        const float best = std::min(best_o, best_s);
+        const float sah = 0.5f * b.area() + best;   // traversal cost of one node
+        const bool nosplit = oa < 0 && sa < 0;
+        const bool leaf = n <= 2 || (n <= kMaxLeaf && (nosplit || sah >= (float)n * b.area()));
+        BNode nd;
+        nd.box = b;
+        int self;
+        if (leaf) {
+            nd.first = (int)leaf_tri.size();
+            nd.count = n;
+            for (const Ref& r : refs) leaf_tri.push_back(r.tri);
+            nodes.push_back(nd);
+            self = (int)nodes.size() - 1;
+        } else {
+            std::vector<Ref> L, R;
+            if (sa >= 0 && best_s < best_o) {
+                for (const Ref& r : refs) {
+                    if (r.box.hi[sa] <= splane) {
+                        L.push_back(r);
+                    } else if (r.box.lo[sa] >= splane) {
+                        R.push_back(r);
+                    } else {
+                        Box cl = r.box, cr = r.box;
+                        cl.hi[sa] = splane;
+                        cr.lo[sa] = splane;
+                        const Box pl = clip_tri_box(verts, r.tri, cl), pr = clip_tri_box(verts, r.tri, cr);
+                        if (pl.valid()) L.push_back({r.tri, pl});
+                        if (pr.valid()) R.push_back({r.tri, pr});
+                        if (!pl.valid() && !pr.valid()) L.push_back(r);   // never drop a triangle
+                    }
+                }
+                if (L.empty() || R.empty() || (int)L.size() >= n || (int)R.size() >= n) {
+                    L.clear();
+                    R.clear();
+                }
+            }
+            if (L.empty() && oa >= 0) {
+                const float scale = kBins / (cb.hi[oa] - cb.lo[oa]);
+                for (const Ref& r : refs) {
+                    const int bi =
+                        std::min(kBins - 1, (int)((0.5f * (r.box.lo[oa] + r.box.hi[oa]) - cb.lo[oa]) * scale));
+                    (bi <= obin ? L : R).push_back(r);
+                }
+            }
+            if (L.empty() || R.empty()) {   // degenerate: split by position
+                L.assign(refs.begin(), refs.begin() + n / 2);
+                R.assign(refs.begin() + n / 2, refs.end());
+            }
+            total += L.size() + R.size() - (size_t)n;
+            nodes.push_back(nd);
+            self = (int)nodes.size() - 1;
+            work.push_back({std::move(R), self, 1, it.depth + 1});
+            work.push_back({std::move(L), self, 0, it.depth + 1});
+        }
+        if (it.parent < 0)
+            root = self;
+        else if (it.side == 0)
+            nodes[it.parent].left = self;
+        else
+            nodes[it.parent].right = self;
+    }
+    return root;
 }
 
 }  // namespace
 
 void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* out) {
+    const int T = (int)num_tris;
+    // the binary tree and its leaves' triangles in leaf order
     Builder b;
-    b.verts = verts;
-    int T = (int)num_tris;
-    // references: one per triangle, several for triangles with large boxes
-    std::vector<SplitRef> refs;
-    refs.reserve((size_t)T + T / 4);
-    std::vector<Box> tb(T);
-    double mean_area = 0.0;
-    for (int t = 0; t < T; ++t) {
-        const float* v = verts + 9 * (size_t)t;
-        for (int k = 0; k < 3; ++k) tb[t].grow(v + 3 * k);
-        mean_area += tb[t].area();
-    }
-    mean_area = T > 0 ? mean_area / T : 0.0;
-    const float area_limit = (float)(kSplitAreaFactor * mean_area);
-    std::vector<char> was_split(T, 0);
-    for (int t = 0; t < T; ++t) {
-        const float* v = verts + 9 * (size_t)t;
-        if (split_large && kSplitDepth > 0 && tb[t].area() > area_limit) {
-            float poly[3][3];
-            for (int k = 0; k < 3; ++k)
-                for (int a = 0; a < 3; ++a) poly[k][a] = v[3 * k + a];
-            const size_t before = refs.size();
-            split_refs(t, poly, 3, tb[t], 0, area_limit, refs);
-            was_split[t] = refs.size() - before > 1;
-            if (refs.size() == before) refs.push_back({t, tb[t]});
-        } else {
-            refs.push_back({t, tb[t]});
+    std::vector<int> leaf_tri;
+    int root = -1;
+    if (T > 0 && split_large) {
+        b.nodes.reserve(4 * (size_t)T);
+        root = build_spatial(verts, T, b.nodes, leaf_tri);
+    } else if (T > 0) {
+        // one reference per triangle (scenes whose boxes are refitted from
+        // whole triangles)
+        b.verts = verts;
+        b.tbox.resize(T);
+        b.cent.resize(3 * (size_t)T);
+        b.idx.resize(T);
+        for (int t = 0; t < T; ++t) {
+            const float* v = verts + 9 * (size_t)t;
+            for (int k = 0; k < 3; ++k) b.tbox[t].grow(v + 3 * k);
+            for (int a = 0; a < 3; ++a) b.cent[3 * t + a] = (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
+            b.idx[t] = t;
         }
+        b.nodes.reserve(2 * (size_t)T + 1);
+        root = b.build(T);
+        leaf_tri = b.idx;   // leaf-ordered
     }
-    const int S = (int)refs.size();
-    b.tbox.resize(S);
-    b.cent.resize(3 * (size_t)S);
-    b.idx.resize(S);
-    for (int r = 0; r < S; ++r) {
-        const int t = refs[r].tri;
-        const float* v = verts + 9 * (size_t)t;
-        b.tbox[r] = refs[r].box;
-        for (int a = 0; a < 3; ++a)
-            b.cent[3 * r + a] = was_split[t] ? 0.5f * (refs[r].box.lo[a] + refs[r].box.hi[a])
-                                         : (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
-        b.idx[r] = r;
-    }
-    b.nodes.reserve(2 * (size_t)S + 1);
-    int root = S > 0 ? b.build(S) : -1;
+    const int S = (int)leaf_tri.size();
 
-    // triangles in leaf order (the index array is already leaf-ordered); a
-    // split triangle appears once per reference
+    // triangle slots in leaf order: (v0, original index bits), e1, e2
     out->tris.assign(12 * (size_t)S, 0.f);
     for (int k = 0; k < S; ++k) {
-        int t = refs[b.idx[k]].tri;
+        const int t = leaf_tri[k];
         const float* v = verts + 9 * (size_t)t;
         float* o = &out->tris[12 * (size_t)k];
         uint32_t tid = (uint32_t)t;
