@@ -7,6 +7,7 @@
 struct Bvh4 {
     std::vector<float> nodes;   // 32 floats per node (layout in trace.cuh)
     std::vector<float> tris;    // 12 floats per triangle slot, leaf order
+    std::vector<float> slot_box;  // 6 floats per slot: its reference's box (lo, hi), clipped where split
     uint32_t num_nodes = 0;
     uint32_t depth = 0;
 };
@@ -22,9 +23,9 @@ inline void bvh_leaf_range(int32_t entry, int32_t* first, int32_t* count) {
     *count = (v & 7) + 1;
 }
 
-// Builds an SAH binary BVH over `num_tris` triangles (9 floats each) and
-// collapses it to 4-wide nodes.  split_large: spatial splits, so that a
-// triangle may be entered as several clipped references (it then fills
-// several slots of `tris`); off for scenes whose boxes are refitted from
-// whole triangles.
-void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* out);
+// Builds an SAH binary BVH with spatial splits over `num_tris` triangles (9
+// floats each) and collapses it to 4-wide nodes: a triangle may be entered as
+// several clipped references (it then fills several slots of `tris`), except
+// the triangles with fixed[t] != 0, whose slot boxes are refitted from whole
+// triangles (moving instances); fixed may be null (every triangle may split).
+void build_bvh4(const float* verts, uint32_t num_tris, const uint8_t* fixed, Bvh4* out);

@@ -1,7 +1,6 @@
-// Host BVH construction: a surface-area-heuristic binary BVH -- with spatial
-// splits where triangles may be referenced more than once, else with object
-// splits only (binned for large nodes, an exact sweep over sorted centroids
-// for the rest) -- collapsed into 4-wide nodes whose children boxes are
+// Host BVH construction: a surface-area-heuristic binary BVH with spatial
+// splits (triangles marked fixed are never split) collapsed into 4-wide
+// nodes whose children boxes are
 // stored as SoA float4 rows, with each slot's entry code (bvh.h)
 // precomputed, so that one node is six box rows and one entry row of 16
 // bytes on the device.
@@ -47,158 +46,6 @@ struct BNode {
 
 constexpr int kBins = 128;
 constexpr int kMaxLeaf = 4;
-constexpr int kSweepMax = 4096;   // nodes up to this size: exact SAH sweep over sorted centroids
-
-struct Builder {
-    const float* verts;
-    std::vector<Box> tbox;
-    std::vector<float> cent;     // 3 per triangle
-    std::vector<int> idx;
-    std::vector<BNode> nodes;
-    std::vector<int> ord;        // sweep scratch
-    std::vector<float> rarea;
-
-    int make_leaf(int first, int count, const Box& b) {
-        BNode n;
-        n.box = b;
-        n.first = first;
-        n.count = count;
-        nodes.push_back(n);
-        return (int)nodes.size() - 1;
-    }
-
-    // iterative top-down build; returns root index
-    int build(int T) {
-        struct Item {
-            int first, count, parent, side;
-        };
-        std::vector<Item> work;
-        work.push_back({0, T, -1, 0});
-        int root = -1;
-        while (!work.empty()) {
-            Item it = work.back();
-            work.pop_back();
-            Box b, cb;
-            for (int k = it.first; k < it.first + it.count; ++k) {
-                b.grow(tbox[idx[k]]);
-                cb.grow(&cent[3 * idx[k]]);
-            }
-            int self;
-            int split_axis = -1, split_bin = -1, sweep_pos = -1;
-            if (it.count > 2 && it.count <= kSweepMax) {
-                // every split position along each axis, centroids sorted
-                // (ties by triangle index, so the order is deterministic)
-                float best = FLT_MAX;
-                ord.assign(idx.begin() + it.first, idx.begin() + it.first + it.count);
-                rarea.resize(it.count);
-                for (int a = 0; a < 3; ++a) {
-                    std::sort(ord.begin(), ord.end(), [&](int x, int y) {
-                        return cent[3 * x + a] < cent[3 * y + a] || (cent[3 * x + a] == cent[3 * y + a] && x < y);
-                    });
-                    Box acc;
-                    for (int i = it.count - 1; i >= 1; --i) {
-                        acc.grow(tbox[ord[i]]);
-                        rarea[i] = acc.area();
-                    }
-                    acc = Box();
-                    for (int i = 0; i + 1 < it.count; ++i) {
-                        acc.grow(tbox[ord[i]]);
-                        float c = acc.area() * (i + 1) + rarea[i + 1] * (it.count - i - 1);
-                        if (c < best) {
-                            best = c;
-                            split_axis = a;
-                            sweep_pos = i;
-                        }
-                    }
-                }
-                float leaf_cost = b.area() * it.count;
-                float sah = 0.5f * b.area() + best;   // traversal cost of one node
-                if (split_axis >= 0 && it.count <= kMaxLeaf && sah >= leaf_cost) split_axis = -1;
-            } else if (it.count > 2) {
-                float best = FLT_MAX;
-                for (int a = 0; a < 3; ++a) {
-                    float ext = cb.hi[a] - cb.lo[a];
-                    if (!(ext > 0.f)) continue;
-                    Box bb[kBins];
-                    int bc[kBins] = {0};
-                    float scale = kBins / ext;
-                    for (int k = it.first; k < it.first + it.count; ++k) {
-                        int t = idx[k];
-                        int bi = std::min(kBins - 1, (int)((cent[3 * t + a] - cb.lo[a]) * scale));
-                        bc[bi]++;
-                        bb[bi].grow(tbox[t]);
-                    }
-                    float la[kBins], ra[kBins];
-                    int lc[kBins], rc[kBins];
-                    Box acc;
-                    int n = 0;
-                    for (int i = 0; i < kBins; ++i) {
-                        acc.grow(bb[i]);
-                        n += bc[i];
-                        la[i] = acc.area();
-                        lc[i] = n;
-                    }
-                    acc = Box();
-                    n = 0;
-                    for (int i = kBins - 1; i >= 0; --i) {
-                        acc.grow(bb[i]);
-                        n += bc[i];
-                        ra[i] = acc.area();
-                        rc[i] = n;
-                    }
-                    for (int i = 0; i < kBins - 1; ++i) {
-                        if (lc[i] == 0 || rc[i + 1] == 0) continue;
-                        float c = la[i] * lc[i] + ra[i + 1] * rc[i + 1];
-                        if (c < best) {
-                            best = c;
-                            split_axis = a;
-                            split_bin = i;
-                        }
-                    }
-                }
-                float leaf_cost = b.area() * it.count;
-                float sah = 0.5f * b.area() + best;   // traversal cost of one node
-                if (split_axis >= 0 && it.count <= kMaxLeaf && sah >= leaf_cost) split_axis = -1;
-            }
-            int mid = -1;
-            if (split_axis >= 0 && sweep_pos >= 0) {
-                const int a = split_axis;
-                std::sort(idx.begin() + it.first, idx.begin() + it.first + it.count, [&](int x, int y) {
-                    return cent[3 * x + a] < cent[3 * y + a] || (cent[3 * x + a] == cent[3 * y + a] && x < y);
-                });
-                mid = it.first + sweep_pos + 1;
-            } else if (split_axis >= 0) {
-                float ext = cb.hi[split_axis] - cb.lo[split_axis];
-                float scale = kBins / ext;
-                auto beg = idx.begin() + it.first, end = beg + it.count;
-                auto m = std::partition(beg, end, [&](int t) {
-                    int bi = std::min(kBins - 1, (int)((cent[3 * t + split_axis] - cb.lo[split_axis]) * scale));
-                    return bi <= split_bin;
-                });
-                mid = (int)(m - idx.begin());
-            } else if (it.count > kMaxLeaf) {
-                mid = it.first + it.count / 2;   // degenerate centroids: split by position
-            }
-            if (mid < 0) {
-                self = make_leaf(it.first, it.count, b);
-            } else {
-                BNode n;
-                n.box = b;
-                nodes.push_back(n);
-                self = (int)nodes.size() - 1;
-                work.push_back({mid, it.first + it.count - mid, self, 1});
-                work.push_back({it.first, mid - it.first, self, 0});
-            }
-            if (it.parent < 0)
-                root = self;
-            else if (it.side == 0)
-                nodes[it.parent].left = self;
-            else
-                nodes[it.parent].right = self;
-        }
-        return root;
-    }
-};
 
 // Sutherland-Hodgman clip of a convex polygon against one axis-aligned
 // half-space (keep side <= c when `below`, else >= c)
@@ -268,12 +115,15 @@ float overlap_area(const Box& a, const Box& b) {
 // box within the bin); spatial splits are tried only where the object
 // split's children overlap by more than kSpatialAlpha of the root's surface
 // area.  A reference that straddles the chosen plane continues on both
-// sides with the boxes of its two parts.  Leaves list triangle ids in leaf
-// order (a triangle once per reference).
+// sides with the boxes of its two parts.  Triangles marked `fixed` are never
+// split: they count whole in the bin of their box's centre and go to the
+// side of it (their slots' boxes are refitted from whole triangles).  Leaves
+// list triangle ids in leaf order (a triangle once per reference).
 constexpr float kSpatialAlpha = 1e-3f;
 constexpr int kSpatialBins = 32;
 
-int build_spatial(const float* verts, int T, std::vector<BNode>& nodes, std::vector<int>& leaf_tri) {
+int build_spatial(const float* verts, int T, const uint8_t* fixed, std::vector<BNode>& nodes,
+                  std::vector<int>& leaf_tri, std::vector<Box>& leaf_box) {
     struct Item {
         std::vector<Ref> refs;
         int parent, side, depth;
@@ -359,8 +209,11 @@ int build_spatial(const float* verts, int T, std::vector<BNode>& nodes, std::vec
                 Box bb[kSpatialBins];
                 int ent[kSpatialBins] = {0}, ex[kSpatialBins] = {0};
                 for (const Ref& r : refs) {
-                    const int b0 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.lo[a] - b.lo[a]) / w)));
-                    const int b1 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.hi[a] - b.lo[a]) / w)));
+                    int b0 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.lo[a] - b.lo[a]) / w)));
+                    int b1 = std::min(kSpatialBins - 1, std::max(0, (int)((r.box.hi[a] - b.lo[a]) / w)));
+                    if (fixed && fixed[r.tri])   // whole, in the bin of its centre
+                        b0 = b1 = std::min(kSpatialBins - 1,
+                                           std::max(0, (int)((0.5f * (r.box.lo[a] + r.box.hi[a]) - b.lo[a]) / w)));
                     ent[b0]++;
                     ex[b1]++;
                     if (b0 == b1) {
@@ -414,14 +267,19 @@ int build_spatial(const float* verts, int T, std::vector<BNode>& nodes, std::vec
         if (leaf) {
             nd.first = (int)leaf_tri.size();
             nd.count = n;
-            for (const Ref& r : refs) leaf_tri.push_back(r.tri);
+            for (const Ref& r : refs) {
+                leaf_tri.push_back(r.tri);
+                leaf_box.push_back(r.box);
+            }
             nodes.push_back(nd);
             self = (int)nodes.size() - 1;
         } else {
             std::vector<Ref> L, R;
             if (sa >= 0 && best_s < best_o) {
                 for (const Ref& r : refs) {
-                    if (r.box.hi[sa] <= splane) {
+                    if (fixed && fixed[r.tri]) {
+                        (0.5f * (r.box.lo[sa] + r.box.hi[sa]) < splane ? L : R).push_back(r);
+                    } else if (r.box.hi[sa] <= splane) {
                         L.push_back(r);
                     } else if (r.box.lo[sa] >= splane) {
                         R.push_back(r);
@@ -470,33 +328,21 @@ int build_spatial(const float* verts, int T, std::vector<BNode>& nodes, std::vec
 
 }  // namespace
 
-void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* out) {
+void build_bvh4(const float* verts, uint32_t num_tris, const uint8_t* fixed, Bvh4* out) {
     const int T = (int)num_tris;
     // the binary tree and its leaves' triangles in leaf order
-    Builder b;
+    std::vector<BNode> nodes;
     std::vector<int> leaf_tri;
-    int root = -1;
-    if (T > 0 && split_large) {
-        b.nodes.reserve(4 * (size_t)T);
-        root = build_spatial(verts, T, b.nodes, leaf_tri);
-    } else if (T > 0) {
-        // one reference per triangle (scenes whose boxes are refitted from
-        // whole triangles)
-        b.verts = verts;
-        b.tbox.resize(T);
-        b.cent.resize(3 * (size_t)T);
-        b.idx.resize(T);
-        for (int t = 0; t < T; ++t) {
-            const float* v = verts + 9 * (size_t)t;
-            for (int k = 0; k < 3; ++k) b.tbox[t].grow(v + 3 * k);
-            for (int a = 0; a < 3; ++a) b.cent[3 * t + a] = (v[a] + v[3 + a] + v[6 + a]) * (1.f / 3.f);
-            b.idx[t] = t;
-        }
-        b.nodes.reserve(2 * (size_t)T + 1);
-        root = b.build(T);
-        leaf_tri = b.idx;   // leaf-ordered
-    }
+    std::vector<Box> leaf_box;
+    nodes.reserve(4 * (size_t)T);
+    const int root = T > 0 ? build_spatial(verts, T, fixed, nodes, leaf_tri, leaf_box) : -1;
     const int S = (int)leaf_tri.size();
+    out->slot_box.resize(6 * (size_t)S);
+    for (int k = 0; k < S; ++k)
+        for (int a = 0; a < 3; ++a) {
+            out->slot_box[6 * (size_t)k + a] = leaf_box[k].lo[a];
+            out->slot_box[6 * (size_t)k + 3 + a] = leaf_box[k].hi[a];
+        }
 
     // triangle slots in leaf order: (v0, original index bits), e1, e2
     out->tris.assign(12 * (size_t)S, 0.f);
@@ -536,7 +382,7 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
     // inner node costs its area x kNodeCost plus its own children's best
     // spread over 4 slots, a leaf its area x triangles x kTriCost
     constexpr double kNodeCost = 1.0, kTriCost = 0.4;
-    const size_t BN = b.nodes.size();
+    const size_t BN = nodes.size();
     std::vector<std::array<double, 5>> cost(BN);
     std::vector<std::array<signed char, 5>> split(BN);   // k1 of the best spread over exactly k slots, 0: fewer
     {
@@ -547,14 +393,14 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
             int n = st.back();
             st.pop_back();
             post.push_back(n);
-            if (b.nodes[n].left >= 0) {
-                st.push_back(b.nodes[n].left);
-                st.push_back(b.nodes[n].right);
+            if (nodes[n].left >= 0) {
+                st.push_back(nodes[n].left);
+                st.push_back(nodes[n].right);
             }
         }
         for (auto it = post.rbegin(); it != post.rend(); ++it) {
             const int n = *it;
-            const BNode& bn = b.nodes[n];
+            const BNode& bn = nodes[n];
             const double A = bn.box.area();
             if (bn.left < 0) {
                 for (int k = 1; k <= 4; ++k) {
@@ -597,13 +443,13 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
             auto [m, km] = st.back();
             st.pop_back();
             while (km > 1 && split[m][km] == 0) --km;
-            if (km <= 1 || b.nodes[m].left < 0) {
+            if (km <= 1 || nodes[m].left < 0) {
                 out.push_back(m);
                 continue;
             }
             const int k1 = split[m][km];
-            st.push_back({b.nodes[m].right, km - k1});
-            st.push_back({b.nodes[m].left, k1});
+            st.push_back({nodes[m].right, km - k1});
+            st.push_back({nodes[m].left, k1});
         }
     };
     queue.push_back({root, 1});
@@ -611,25 +457,25 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
     for (size_t qi = 0; qi < queue.size(); ++qi) {
         int bn = queue[qi].bnode;
         std::vector<int> ch;
-        if (b.nodes[bn].left < 0) {
+        if (nodes[bn].left < 0) {
             ch.push_back(bn);   // a leaf root: one leaf slot
         } else {
             // the node's children: its two binary children spread over 4 slots
             double bestc = 1e300;
             int bk1 = 1;
             for (int k1 = 1; k1 < 4; ++k1) {
-                double c = cost[b.nodes[bn].left][k1] + cost[b.nodes[bn].right][4 - k1];
+                double c = cost[nodes[bn].left][k1] + cost[nodes[bn].right][4 - k1];
                 if (c < bestc) {
                     bestc = c;
                     bk1 = k1;
                 }
             }
-            collect(b.nodes[bn].left, bk1, ch);
-            collect(b.nodes[bn].right, 4 - bk1, ch);
+            collect(nodes[bn].left, bk1, ch);
+            collect(nodes[bn].right, 4 - bk1, ch);
         }
         slots.push_back(ch);
         for (int c : ch)
-            if (b.nodes[c].left >= 0) queue.push_back({c, queue[qi].depth + 1});
+            if (nodes[c].left >= 0) queue.push_back({c, queue[qi].depth + 1});
         max_depth = std::max(max_depth, (uint32_t)queue[qi].depth);
     }
     // queue order is node order; assign indices of inner children
@@ -644,7 +490,7 @@ void build_bvh4(const float* verts, uint32_t num_tris, bool split_large, Bvh4* o
             int32_t entry = 0;
             float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
             if (c < (int)ch.size()) {
-                const BNode& cn = b.nodes[ch[c]];
+                const BNode& cn = nodes[ch[c]];
                 for (int a = 0; a < 3; ++a) {
                     lo[a] = cn.box.lo[a];
                     hi[a] = cn.box.hi[a];

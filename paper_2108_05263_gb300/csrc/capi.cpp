@@ -74,6 +74,7 @@ struct ddgi_ctx {
     float4* inst_delta = nullptr;    // [3 I] rows of M_prev M_cur^-1
     uint32_t* refit_list = nullptr;  // nodes over instanced triangles, deepest depth first
     std::vector<uint32_t> refit_levels;
+    float* refit_static = nullptr;   // per listed node and slot: the box of the slot's unmoved references
     std::vector<double> xf_cur, xf_prev;   // [12 I] host copies
     float* le_stage = nullptr;       // [3 E] staged emitter radiance
     // page-locked host staging of ddgi_scene_update ([12 I] transforms,
@@ -465,6 +466,30 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
             if (dirty[n] && depth[n] == d) list.push_back(n);
         c->refit_levels.push_back((uint32_t)list.size());
     }
+    // the unmoved references of each listed node's leaf slots keep the boxes
+    // they were built with (clipped where a spatial split cut their triangle);
+    // the refit adds the moving triangles' current boxes to them
+    std::vector<float> stat(24 * list.size());
+    for (size_t i = 0; i < list.size(); ++i)
+        for (int sl = 0; sl < 4; ++sl) {
+            float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+            int32_t en, first, cnt;
+            std::memcpy(&en, &bvh.nodes[32ull * list[i] + 24 + sl], 4);
+            if (en < 0) {
+                bvh_leaf_range(en, &first, &cnt);
+                for (int k = first; k < first + cnt; ++k) {
+                    if (slot_moving[k]) continue;
+                    for (int a = 0; a < 3; ++a) {
+                        lo[a] = std::min(lo[a], bvh.slot_box[6ull * k + a]);
+                        hi[a] = std::max(hi[a], bvh.slot_box[6ull * k + 3 + a]);
+                    }
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                stat[24 * i + 6 * sl + a] = lo[a];
+                stat[24 * i + 6 * sl + 3 + a] = hi[a];
+            }
+        }
     std::vector<int32_t> ti(scene->tri_instance, scene->tri_instance + c->T);
     c->I = I;
     c->NI = (uint32_t)map.size();
@@ -483,6 +508,7 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
     if (e == cudaSuccess) e = dalloc(c, &c->inst_xf, 3ull * I);
     if (e == cudaSuccess) e = dalloc(c, &c->inst_delta, 3ull * I);
     if (e == cudaSuccess) e = dalloc(c, &c->refit_list, list.size());
+    if (e == cudaSuccess) e = dalloc(c, &c->refit_static, stat.size());
     auto up = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
@@ -492,6 +518,7 @@ cudaError_t setup_instances(ddgi_ctx* c, const ddgi_scene* scene, const Bvh4& bv
     up(c->inst_xf, ident.data(), ident.size() * sizeof(float4));
     up(c->inst_delta, ident.data(), ident.size() * sizeof(float4));
     up(c->refit_list, list.data(), list.size() * sizeof(uint32_t));
+    up(c->refit_static, stat.data(), stat.size() * sizeof(float));
     return e;
 }
 
@@ -606,7 +633,12 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     // scene tables (host), fp64 geometry for normals / areas
     Bvh4 bvh;
     // instanced scenes refit slot boxes from whole triangles: no split references
-    build_bvh4(scene->vertices, T, scene->num_instances == 0, &bvh);
+    std::vector<uint8_t> fixed;
+    if (scene->tri_instance) {   // moving triangles: never split (refitted from whole triangles)
+        fixed.resize(T);
+        for (uint32_t t = 0; t < T; ++t) fixed[t] = scene->tri_instance[t] >= 0 ? 1 : 0;
+    }
+    build_bvh4(scene->vertices, T, fixed.empty() ? nullptr : fixed.data(), &bvh);
     ctx->bvh_nodes = bvh.num_nodes;
     ctx->bvh_depth = bvh.depth;
     std::vector<float4> nrm(T), alb(T), emi(T);
@@ -908,7 +940,8 @@ ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const 
         CK(cudaMemcpyAsync(ctx->inst_delta, sd, 12ull * n * sizeof(float), cudaMemcpyHostToDevice, st));
         staged = true;
         CK(launch_instance_update(ctx->inst_obj, ctx->inst_map, ctx->NI, ctx->inst_xf, ctx->tris, ctx->nrm,
-                                  ctx->nodes, ctx->refit_list, ctx->refit_levels, st));
+                                  ctx->nodes, ctx->refit_list, ctx->refit_static, ctx->tri_inst, ctx->refit_levels,
+                                  st));
         ctx->xf_prev = ctx->xf_cur;
         ctx->xf_cur = cur;
     }

@@ -40,10 +40,13 @@ __global__ void __launch_bounds__(128) k_instance_tris(const float4* __restrict_
 }
 
 // one thread per listed node of one depth: each occupied slot's box is the
-// union of its leaf triangles' corners (v0, v0 + e1, v0 + e2, the points the
-// intersection test spans) or of its child node's slot boxes
+// union of its child node's slot boxes, or for a leaf slot the box of its
+// unmoved references as built (static, clipped where the build split their
+// triangles) and its moving triangles' corners (v0, v0 + e1, v0 + e2, the
+// points the intersection test spans)
 __global__ void __launch_bounds__(128) k_refit(float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                               const uint32_t* __restrict__ list, uint32_t n) {
+                                               const uint32_t* __restrict__ list, const float* __restrict__ stat,
+                                               const int32_t* __restrict__ tri_inst, uint32_t n) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float* nd = reinterpret_cast<float*>(nodes + 8 * (size_t)list[i]);
@@ -53,8 +56,12 @@ __global__ void __launch_bounds__(128) k_refit(float4* __restrict__ nodes, const
         if (entry == 0) continue;
         f3 lo = {FLT_MAX, FLT_MAX, FLT_MAX}, hi = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
         if (entry < 0) {
+            const float* sb = stat + 24 * (size_t)i + 6 * c;
+            lo = {sb[0], sb[1], sb[2]};
+            hi = {sb[3], sb[4], sb[5]};
             const int v = -1 - entry, first = v >> 3, cnt = (v & 7) + 1;
             for (int k = first; k < first + cnt; ++k) {
+                if (tri_inst[__float_as_uint(tris[3 * (size_t)k].w)] < 0) continue;   // unmoved: in the static box
                 const f3 v0 = xyz(tris[3 * (size_t)k]);
                 const f3 p1 = v0 + xyz(tris[3 * (size_t)k + 1]), p2 = v0 + xyz(tris[3 * (size_t)k + 2]);
                 lo = {fminf(lo.x, fminf(v0.x, fminf(p1.x, p2.x))), fminf(lo.y, fminf(v0.y, fminf(p1.y, p2.y))),
@@ -97,8 +104,9 @@ __global__ void k_emitter_radiance(const float* __restrict__ le, const uint32_t*
 }  // namespace
 
 cudaError_t launch_instance_update(const float4* obj, const uint4* map, uint32_t n, const float4* xf, float4* tris,
-                                   float4* nrm, float4* nodes, const uint32_t* refit_list,
-                                   const std::vector<uint32_t>& level_offsets, cudaStream_t st) {
+                                   float4* nrm, float4* nodes, const uint32_t* refit_list, const float* refit_static,
+                                   const int32_t* tri_inst, const std::vector<uint32_t>& level_offsets,
+                                   cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     k_instance_tris<<<(n + 127) / 128, 128, 0, st>>>(obj, map, xf, tris, nrm, n);
     cudaError_t e = cudaGetLastError();
@@ -106,7 +114,8 @@ cudaError_t launch_instance_update(const float4* obj, const uint4* map, uint32_t
     for (size_t d = 0; e == cudaSuccess && d + 1 < level_offsets.size(); ++d) {
         const uint32_t a = level_offsets[d], b = level_offsets[d + 1];
         if (b == a) continue;
-        k_refit<<<(b - a + 127) / 128, 128, 0, st>>>(nodes, tris, refit_list + a, b - a);
+        k_refit<<<(b - a + 127) / 128, 128, 0, st>>>(nodes, tris, refit_list + a, refit_static + 24 * (size_t)a,
+                                                      tri_inst, b - a);
         e = cudaGetLastError();
     }
     return e;

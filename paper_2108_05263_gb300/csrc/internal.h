@@ -66,8 +66,9 @@ struct ProbeParams {
 cudaError_t launch_probe_trace(const SceneView& s, const VolumeView& v, const ProbeParams& p,
                                float4* rays, float2* hits, uint32_t* counter, cudaStream_t st);
 cudaError_t launch_instance_update(const float4* obj, const uint4* map, uint32_t n, const float4* xf, float4* tris,
-                                   float4* nrm, float4* nodes, const uint32_t* refit_list,
-                                   const std::vector<uint32_t>& level_offsets, cudaStream_t st);
+                                   float4* nrm, float4* nodes, const uint32_t* refit_list, const float* refit_static,
+                                   const int32_t* tri_inst, const std::vector<uint32_t>& level_offsets,
+                                   cudaStream_t st);
 cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float4* emi, float4* evert, uint32_t E,
                                     cudaStream_t st);
 cudaError_t launch_probe_relocate(const VolumeView& v, const ProbeParams& p, const float4* rays, float4* offset,

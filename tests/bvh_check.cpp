@@ -71,7 +71,9 @@ int main(int argc, char** argv) {
     const bool split = std::atoi(argv[2]) != 0;
     const uint32_t T = (uint32_t)(v.size() / 9);
     Bvh4 b;
-    build_bvh4(v.data(), T, split, &b);
+    // unsplit: every triangle fixed (whole references only)
+    std::vector<uint8_t> all_fixed(T, 1);
+    build_bvh4(v.data(), T, split ? nullptr : all_fixed.data(), &b);
     const uint32_t S = (uint32_t)(b.tris.size() / 12);
     long bad_child = 0, bad_box = 0, missing = 0, dup = 0, orphan = 0, bad_tri = 0;
     std::vector<int> seen(T, 0), reached(b.num_nodes, 0);
