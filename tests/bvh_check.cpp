@@ -1,12 +1,14 @@
 // Host check of the BVH4 builder (compiled by tests/test_bvh_cpu.py together
 // with csrc/bvh_build.cpp; no GPU).  Reads float32 triangles [T][3][3] from
-// argv[1], builds with split references on or off (argv[2] = 1 / 0) and
+// argv[1], builds with spatial splits for every triangle, for none or for
+// every other pair of triangles (argv[2] = 1 / 0 / 2: the others fixed) and
 // checks the structure and the geometry:
 //   - every inner child index is a node other than the root, reached once;
 //     empty slots carry the inverted box, and row 7 is zero;
 //   - every triangle is referenced by some leaf (exactly once without split
 //     references), and each child box contains its child node's boxes;
-//   - without split references, each leaf box contains its triangles;
+//   - without split references, each leaf box contains its triangles; a
+//     fixed triangle has exactly one slot, with its whole triangle's box;
 //   - closest hits of random rays traced through the tree (fp64 slab and
 //     Moller-Trumbore tests, the slab test widened by 1e-9 of the scene size)
 //     equal brute force over all triangles: a box that lost part of its
@@ -68,12 +70,34 @@ int main(int argc, char** argv) {
     float buf[9];
     while (std::fread(buf, 4, 9, f) == 9) v.insert(v.end(), buf, buf + 9);
     std::fclose(f);
-    const bool split = std::atoi(argv[2]) != 0;
+    // 0: every triangle fixed (unsplit), 1: none fixed, 2: every other pair fixed
+    const int mode = std::atoi(argv[2]);
+    const bool split = mode != 0;
     const uint32_t T = (uint32_t)(v.size() / 9);
     Bvh4 b;
-    // unsplit: every triangle fixed (whole references only)
-    std::vector<uint8_t> all_fixed(T, 1);
-    build_bvh4(v.data(), T, split ? nullptr : all_fixed.data(), &b);
+    std::vector<uint8_t> fixed(T, 1);
+    for (uint32_t t = 0; t < T; ++t) fixed[t] = mode == 0 || (mode == 2 && (t / 2) % 2 == 0);
+    build_bvh4(v.data(), T, mode == 1 ? nullptr : fixed.data(), &b);
+    // a fixed triangle: exactly one slot, whose reference box is the whole
+    // triangle's box (moving triangles' slots are refitted from whole triangles)
+    long bad_fixed = 0;
+    {
+        std::vector<int> refs(T, 0);
+        for (uint32_t k = 0; k < (uint32_t)(b.tris.size() / 12); ++k) {
+            uint32_t orig;
+            std::memcpy(&orig, &b.tris[12 * (size_t)k + 3], 4);
+            if (orig >= T || !fixed[orig] || mode == 1) continue;
+            refs[orig]++;
+            const float* w = &v[9 * (size_t)orig];
+            for (int a = 0; a < 3; ++a) {
+                const float lo = std::min(w[a], std::min(w[3 + a], w[6 + a]));
+                const float hi = std::max(w[a], std::max(w[3 + a], w[6 + a]));
+                if (b.slot_box[6 * (size_t)k + a] != lo || b.slot_box[6 * (size_t)k + 3 + a] != hi) bad_fixed++;
+            }
+        }
+        for (uint32_t t = 0; t < T; ++t)
+            if (mode != 1 && fixed[t] && refs[t] != 1) bad_fixed++;
+    }
     const uint32_t S = (uint32_t)(b.tris.size() / 12);
     long bad_child = 0, bad_box = 0, missing = 0, dup = 0, orphan = 0, bad_tri = 0;
     std::vector<int> seen(T, 0), reached(b.num_nodes, 0);
@@ -194,7 +218,8 @@ int main(int argc, char** argv) {
         if (!(best == best_brute || (std::isinf(best) && std::isinf(best_brute)))) ray_mismatch++;
     }
     std::printf("triangles %u slots %u nodes %u depth %u missing %ld dup %ld bad_box %ld bad_child %ld orphan %ld "
-                "bad_tri %ld ray_mismatch %ld of %d\n",
-                T, S, b.num_nodes, b.depth, missing, dup, bad_box, bad_child, orphan, bad_tri, ray_mismatch, rays);
-    return (missing || dup || bad_box || bad_child || orphan || bad_tri || ray_mismatch) ? 1 : 0;
+                "bad_tri %ld bad_fixed %ld ray_mismatch %ld of %d\n",
+                T, S, b.num_nodes, b.depth, missing, dup, bad_box, bad_child, orphan, bad_tri, bad_fixed, ray_mismatch,
+                rays);
+    return (missing || dup || bad_box || bad_child || orphan || bad_tri || bad_fixed || ray_mismatch) ? 1 : 0;
 }

@@ -27,9 +27,12 @@ def checker(tmp_path_factory):
 
 
 def _run(checker, tmp_path, verts, split, rays=1500):
+    """split: False (every triangle fixed), True (none) or "half" (every other
+    pair of triangles fixed: moving quads among static ones)."""
     path = str(tmp_path / "tris.bin")
     np.ascontiguousarray(verts, np.float32).tofile(path)
-    r = subprocess.run([checker, path, "1" if split else "0", str(rays)], capture_output=True, text=True)
+    mode = "2" if split == "half" else ("1" if split else "0")
+    r = subprocess.run([checker, path, mode, str(rays)], capture_output=True, text=True)
     return r.returncode, r.stdout
 
 
@@ -54,11 +57,11 @@ def test_tiny_room(checker, tmp_path, split):
     assert rc == 0, out
 
 
-@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("split", [False, True, "half"])
 def test_big_and_small_triangles(checker, tmp_path, split):
     rc, out = _run(checker, tmp_path, _big_and_small(), split)
     assert rc == 0, out
-    if split:   # the large quads were entered as several references
+    if split:   # the large (free) quads were entered as several references
         slots = int(out.split("slots ")[1].split()[0])
         assert slots > 3012
 
