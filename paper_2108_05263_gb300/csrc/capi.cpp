@@ -32,6 +32,8 @@ struct ddgi_ctx {
     float area_total = 0.f;
     float4* irr = nullptr;
     float2* depth = nullptr;
+    float4* irr_q = nullptr;       // the query's 2x2 tap blocks of irr / depth (VolumeView)
+    float4* depth_q = nullptr;
     float4* offset = nullptr;
     float4* rays = nullptr;
     float* blend_w = nullptr;      // the probe blend's per-frame weight tables
@@ -182,6 +184,8 @@ VolumeView volume_view(ddgi_ctx* c) {
     VolumeView v;
     v.irr = c->irr;
     v.depth = c->depth;
+    v.irr_q = c->irr_q;
+    v.depth_q = c->depth_q;
     v.offset = c->offset;
     v.has_offset = c->offsets_used ? 1 : 0;
     v.origin = make_float3(c->cfg.origin[0], c->cfg.origin[1], c->cfg.origin[2]);
@@ -756,6 +760,8 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(etri, ctx->E)
     ALLOC(irr, P * ti * ti)
     ALLOC(depth, P * td * td)
+    ALLOC(irr_q, P * (ti - 1) * (ti - 1) * 4)
+    ALLOC(depth_q, P * (td - 1) * (td - 1) * 2)
     ALLOC(offset, P)
     ALLOC(rays, P * R)
     ALLOC(blend_w, probe_blend_weights_size(volume_view(ctx), R))
@@ -795,6 +801,8 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     if (e == cudaSuccess && scene->tri_instance) e = setup_instances(ctx, scene, bvh);
     if (e == cudaSuccess) e = cudaMemset(ctx->irr, 0, P * ti * ti * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->depth, 0, P * td * td * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(ctx->irr_q, 0, P * (ti - 1) * (ti - 1) * 4 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(ctx->depth_q, 0, P * (td - 1) * (td - 1) * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->offset, 0, P * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->rays, 0, P * R * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, 4 * sizeof(uint32_t));
@@ -997,6 +1005,7 @@ ddgi_status ddgi_probe_state_set(ddgi_ctx* ctx, const float* irr, const float* d
     const size_t P = ctx->P, ti = ctx->cfg.irr_texels + 2, td = ctx->cfg.depth_texels + 2;
     if (irr) CK(cudaMemcpyAsync(ctx->irr, irr, P * ti * ti * sizeof(float4), cudaMemcpyDefault, st));
     if (depth) CK(cudaMemcpyAsync(ctx->depth, depth, P * td * td * sizeof(float2), cudaMemcpyDefault, st));
+    if (irr || depth) CK(launch_probe_quads(volume_view(ctx), st));
     if (offsets) {
         CK(cudaMemcpyAsync(ctx->offset, offsets, P * sizeof(float4), cudaMemcpyDefault, st));
         ctx->offsets_used = true;
@@ -1084,6 +1093,7 @@ ddgi_status ddgi_state_load(ddgi_ctx* ctx, const void* host_buf, size_t bytes, v
     }
     CK(cudaMemcpyAsync(ctx->irr, b + L.irr, L.dep - L.irr, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->depth, b + L.dep, L.off - L.dep, cudaMemcpyHostToDevice, st));
+    CK(launch_probe_quads(volume_view(ctx), st));
     CK(cudaMemcpyAsync(ctx->offset, b + L.off, L.xf - L.off, cudaMemcpyHostToDevice, st));
     ctx->offsets_used = true;
     if (ctx->cfg.learned_target) {

@@ -119,6 +119,13 @@ __device__ __forceinline__ f3 prev_position(const SceneView& s, uint32_t tri, f3
 struct VolumeView {
     float4* irr;             // [P][ti*ti] rgb, 0
     float2* depth;           // [P][td*td] mean, mean square
+    // the query's copies: for each 2x2 block of a padded tile (top-left
+    // texel (x0, y0), 0 <= x0, y0 <= n, block y0 * (n + 1) + x0) its four
+    // bilinear taps (x0, y0), (x0 + 1, y0), (x0, y0 + 1), (x0 + 1, y0 + 1),
+    // so that a probe's taps are one 32-byte (distance) and two 32-byte
+    // (irradiance) loads; rebuilt from irr / depth whenever those change
+    float4* irr_q;           // [P][(irr_n + 1)^2][4] rgb, 0
+    float4* depth_q;         // [P][(depth_n + 1)^2][2] (mean, mean square) x 2 per float4
     const float4* offset;    // [P] xyz, 0
     int has_offset;          // 0 while every offset is zero (they are then not read)
     float3 origin, spacing;
@@ -126,6 +133,27 @@ struct VolumeView {
     int irr_n, depth_n;      // interior texels per side
     float min_spacing, max_spacing;
 };
+
+// 32-byte (256-bit) accesses: one L1 sector access per record half
+__device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// the same from L2 only (scattered neighbour records: L1 seldom hits), issued
+// where written so that the loads start before the arithmetic that follows
+__device__ __forceinline__ void ld32_l2(const float4* p, float4& a, float4& b) {
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
+__device__ __forceinline__ void st32(float4* p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
+                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // octahedral maps with a one-texel border
@@ -162,6 +190,7 @@ __device__ __forceinline__ f3 texel_dir(int i, int j, int n) {
 // bilinear taps of a padded (n+2)^2 tile in direction d
 struct Taps {
     int i00;   // index of the top-left tap within the tile
+    int q00;   // index of the 2x2 block it starts (y0 * (n + 1) + x0)
     float ax, ay;
 };
 __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
@@ -178,7 +207,16 @@ __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
     if (x0 > n) { x0 = n; t.ax = 1.f; }
     if (y0 > n) { y0 = n; t.ay = 1.f; }
     t.i00 = y0 * (n + 2) + x0;
+    t.q00 = y0 * (n + 1) + x0;
     return t;
+}
+
+// bilinear blend of the four taps (a, b: row y0; c, e: row y0 + 1)
+__device__ __forceinline__ float2 bilerp2(const Taps& t, float2 a, float2 b, float2 c, float2 e) {
+    float w00 = (1.f - t.ax) * (1.f - t.ay), w10 = t.ax * (1.f - t.ay);
+    float w01 = (1.f - t.ax) * t.ay, w11 = t.ax * t.ay;
+    return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * e.x,
+                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y);
 }
 
 __device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) {
@@ -186,10 +224,16 @@ __device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) 
     int w = n + 2;
     float2 a = __ldg(tile + t.i00), b = __ldg(tile + t.i00 + 1);
     float2 c = __ldg(tile + t.i00 + w), e = __ldg(tile + t.i00 + w + 1);
-    float w00 = (1.f - t.ax) * (1.f - t.ay), w10 = t.ax * (1.f - t.ay);
-    float w01 = (1.f - t.ax) * t.ay, w11 = t.ax * t.ay;
-    return make_float2(w00 * a.x + w10 * b.x + w01 * c.x + w11 * e.x,
-                       w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y);
+    return bilerp2(t, a, b, c, e);
+}
+
+// the same from the blocks of a probe (depth_q + p * (n + 1)^2 * 2): one load
+__device__ __forceinline__ float2 sample_depth_q(const float4* blocks, int n, f3 d) {
+    Taps t = oct_taps(d, n);
+    float4 ab, ce;
+    ld32(blocks + 2 * (size_t)t.q00, ab, ce);
+    return bilerp2(t, make_float2(ab.x, ab.y), make_float2(ab.z, ab.w), make_float2(ce.x, ce.y),
+                   make_float2(ce.z, ce.w));
 }
 
 __device__ __forceinline__ f3 probe_pos(const VolumeView& v, int i, int j, int k, int p) {
@@ -219,7 +263,7 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
         base[a] = b;
         al[a] = cnt[a] > 1 ? fminf(fmaxf(g[a] - (float)b, 0.f), 1.f) : 0.f;
     }
-    const int ti = v.irr_n + 2, td = v.depth_n + 2;
+    const int qi = (v.irr_n + 1) * (v.irr_n + 1), qd = (v.depth_n + 1) * (v.depth_n + 1);
     // the irradiance taps depend on n only: one set for the 8 probes
     const Taps tn = oct_taps(n, v.irr_n);
     const float n00 = (1.f - tn.ax) * (1.f - tn.ay), n10 = tn.ax * (1.f - tn.ay);
@@ -241,7 +285,7 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
         dir = r > 0.f ? dir * (1.f / r) : n;
         float wrap = 0.5f * (dot(dir, n) + 1.f);
         float w = wrap * wrap + 0.2f;
-        float2 mom = sample_depth(v.depth + (size_t)p * td * td, v.depth_n, -dir);
+        float2 mom = sample_depth_q(v.depth_q + (size_t)p * qd * 2, v.depth_n, -dir);
         if (r > mom.x) {
             float var = fabsf(mom.y - mom.x * mom.x);
             float dd = r - mom.x;
@@ -251,8 +295,10 @@ __device__ __forceinline__ f3 ddgi_irradiance(const VolumeView& v, f3 q, f3 n) {
         w = fmaxf(w, 1e-6f);
         if (w < 0.2f) w = w * w * w * 25.f;
         w *= tri;
-        const float4* tile = v.irr + (size_t)p * ti * ti + tn.i00;
-        const float4 a = __ldg(tile), b = __ldg(tile + 1), cc = __ldg(tile + ti), d = __ldg(tile + ti + 1);
+        const float4* blk = v.irr_q + ((size_t)p * qi + tn.q00) * 4;
+        float4 a, b, cc, d;
+        ld32(blk, a, b);
+        ld32(blk + 2, cc, d);
         const f3 e = {n00 * a.x + n10 * b.x + n01 * cc.x + n11 * d.x, n00 * a.y + n10 * b.y + n01 * cc.y + n11 * d.y,
                       n00 * a.z + n10 * b.z + n01 * cc.z + n11 * d.z};
         se = se + e * w;
@@ -425,27 +471,6 @@ __device__ __forceinline__ uint32_t sample_emitter_smem(const float* cdf, const 
 struct Rec {
     float4 q0, q1, q2, q3;
 };
-
-// 32-byte (256-bit) accesses: one L1 sector access per record half
-__device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-}
-
-// the same from L2 only (scattered neighbour records: L1 seldom hits), issued
-// where written so that the loads start before the arithmetic that follows
-__device__ __forceinline__ void ld32_l2(const float4* p, float4& a, float4& b) {
-    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-                 : "l"(p));
-}
-
-__device__ __forceinline__ void st32(float4* p, float4 a, float4 b) {
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
-                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
-                 : "memory");
-}
 
 // words 12..15: triangle of y, tag, y's normal (octahedral, 0 0 without a sample)
 __device__ __forceinline__ float4 rec_tail(uint32_t tri, uint32_t tag, float2 ny) {

@@ -79,6 +79,9 @@ size_t probe_blend_smem(const VolumeView& v, uint32_t rays);
 size_t probe_blend_weights_size(const VolumeView& v, uint32_t rays);
 cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const float4* rays, float* weights,
                                cudaStream_t st);
+// rebuilds the query's 2x2 tap blocks from the padded maps (after the maps
+// were written other than by launch_probe_blend, which keeps them current)
+cudaError_t launch_probe_quads(const VolumeView& v, cudaStream_t st);
 cudaError_t launch_gbuffer(const SceneView& s, const CamView& cam, const CamView* prev,
                            const GBufView& g, float2* hits, uint32_t* counter, cudaStream_t st);
 cudaError_t launch_restir_initial(const SceneView& s, const VolumeView& v, const RestirParams& rp,

@@ -365,6 +365,22 @@ __global__ void __launch_bounds__(1024) k_probe_blend(VolumeView v, ProbeParams 
         const int g = i / (td * td), k = i - g * td * td;
         v.depth[(size_t)(p0 + g) * td * td + k] = s_dep[g * td * td + border_source(k % td, k / td, nd)];
     }
+    // the query's 2x2 tap blocks of the same tiles
+    const int qi = (ni + 1) * (ni + 1), qd = (nd + 1) * (nd + 1);
+    for (int i = tid; i < gn * qi; i += blockDim.x) {
+        const int g = i / qi, j = i - g * qi, x0 = j % (ni + 1), y0 = j / (ni + 1);
+        const float4* t = s_irr + (size_t)g * ti * ti;
+        float4* o = v.irr_q + ((size_t)p0 * qi + i) * 4;
+        st32(o, t[border_source(x0, y0, ni)], t[border_source(x0 + 1, y0, ni)]);
+        st32(o + 2, t[border_source(x0, y0 + 1, ni)], t[border_source(x0 + 1, y0 + 1, ni)]);
+    }
+    for (int i = tid; i < gn * qd; i += blockDim.x) {
+        const int g = i / qd, j = i - g * qd, x0 = j % (nd + 1), y0 = j / (nd + 1);
+        const float2* t = s_dep + (size_t)g * td * td;
+        const float2 a = t[border_source(x0, y0, nd)], b = t[border_source(x0 + 1, y0, nd)];
+        const float2 c = t[border_source(x0, y0 + 1, nd)], e = t[border_source(x0 + 1, y0 + 1, nd)];
+        st32(v.depth_q + ((size_t)p0 * qd + i) * 2, make_float4(a.x, a.y, b.x, b.y), make_float4(c.x, c.y, e.x, e.y));
+    }
 }
 
 // border texels of every probe's padded tiles repeat their fold partner
@@ -395,6 +411,29 @@ __global__ void __launch_bounds__(256) k_probe_gutter(VolumeView v, int P) {
     } else {
         float2* tile = v.depth + (size_t)p * td * td;
         tile[Y * td + X] = tile[src];
+    }
+}
+
+// the query's 2x2 tap blocks (VolumeView::irr_q / depth_q) of every probe,
+// read from the padded tiles (borders included); one thread per block
+__global__ void __launch_bounds__(256) k_probe_quads(VolumeView v, int P) {
+    const int ni = v.irr_n, nd = v.depth_n, ti = ni + 2, td = nd + 2;
+    const int qi = (ni + 1) * (ni + 1), qd = (nd + 1) * (nd + 1);
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t ni_all = (size_t)P * qi;
+    if (i >= (size_t)P * (qi + qd)) return;
+    if (i < ni_all) {
+        const size_t p = i / qi;
+        const int j = (int)(i - p * qi), x0 = j % (ni + 1), y0 = j / (ni + 1);
+        const float4* t = v.irr + p * ti * ti + y0 * ti + x0;
+        st32(v.irr_q + i * 4, t[0], t[1]);
+        st32(v.irr_q + i * 4 + 2, t[ti], t[ti + 1]);
+    } else {
+        const size_t k = i - ni_all, p = k / qd;
+        const int j = (int)(k - p * qd), x0 = j % (nd + 1), y0 = j / (nd + 1);
+        const float2* t = v.depth + p * td * td + y0 * td + x0;
+        st32(v.depth_q + k * 2, make_float4(t[0].x, t[0].y, t[1].x, t[1].y),
+             make_float4(t[td].x, t[td].y, t[td + 1].x, t[td + 1].y));
     }
 }
 
@@ -565,5 +604,15 @@ cudaError_t launch_probe_blend(const VolumeView& v, const ProbeParams& p, const 
     if (e != cudaSuccess || b.slices == 1) return e;
     const int borders = P * (4 * (v.irr_n + 1) + 4 * (v.depth_n + 1));
     k_probe_gutter<<<(borders + 255) / 256, 256, 0, st>>>(v, P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_probe_quads(v, st);
+}
+
+cudaError_t launch_probe_quads(const VolumeView& v, cudaStream_t st) {
+    const int P = v.counts.x * v.counts.y * v.counts.z;
+    if (P == 0) return cudaSuccess;
+    const size_t n = (size_t)P * ((v.irr_n + 1) * (v.irr_n + 1) + (v.depth_n + 1) * (v.depth_n + 1));
+    k_probe_quads<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, P);
     return cudaGetLastError();
 }
