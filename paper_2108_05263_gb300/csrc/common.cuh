@@ -201,11 +201,10 @@ __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
     Taps t;
     t.ax = fx - x0f;
     t.ay = fy - y0f;
-    int x0 = (int)x0f, y0 = (int)y0f;
-    if (x0 < 0) { x0 = 0; t.ax = 0.f; }
-    if (y0 < 0) { y0 = 0; t.ay = 0.f; }
-    if (x0 > n) { x0 = n; t.ax = 1.f; }
-    if (y0 > n) { y0 = n; t.ay = 1.f; }
+    // |u| + |v| <= 1 puts fx and fy in [0.5, n + 0.5] (a fast reciprocal in
+    // oct_encode can pass 1 by an ulp, which moves neither floor): the clamps
+    // only keep the taps of a NaN direction inside the tile
+    const int x0 = min(max((int)x0f, 0), n), y0 = min(max((int)y0f, 0), n);
     t.i00 = y0 * (n + 2) + x0;
     t.q00 = y0 * (n + 1) + x0;
     return t;

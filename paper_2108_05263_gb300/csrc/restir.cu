@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         } else if constexpr (GLOSSY) {
             L = radiance_at_glossy<4>(s, v, y, tri, x, u01(rng_u32_dim(cp, 4)), u01(rng_u32_dim(cp, 5)));
         } else {
-            L = radiance_at<4>(s, v, y, tri, x);
+            L = radiance_at<2>(s, v, y, tri, x);
         }
         if (cx > 0.f) {
             float G = cx * fabsf(cyn) / d2;
