@@ -187,10 +187,10 @@ __device__ __forceinline__ f3 texel_dir(int i, int j, int n) {
     return oct_decode(2.f * (i + 0.5f) / n - 1.f, 2.f * (j + 0.5f) / n - 1.f);
 }
 
-// bilinear taps of a padded (n+2)^2 tile in direction d
+// bilinear taps of a padded (n+2)^2 tile in direction d: the 2x2 block of
+// the query's copy (VolumeView) and the weights within it
 struct Taps {
-    int i00;   // index of the top-left tap within the tile
-    int q00;   // index of the 2x2 block it starts (y0 * (n + 1) + x0)
+    int q00;   // index of the 2x2 tap block (top-left tap (x0, y0): y0 * (n + 1) + x0)
     float ax, ay;
 };
 __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
@@ -205,7 +205,6 @@ __device__ __forceinline__ Taps oct_taps(f3 d, int n) {
     // oct_encode can pass 1 by an ulp, which moves neither floor): the clamps
     // only keep the taps of a NaN direction inside the tile
     const int x0 = min(max((int)x0f, 0), n), y0 = min(max((int)y0f, 0), n);
-    t.i00 = y0 * (n + 2) + x0;
     t.q00 = y0 * (n + 1) + x0;
     return t;
 }
@@ -218,15 +217,8 @@ __device__ __forceinline__ float2 bilerp2(const Taps& t, float2 a, float2 b, flo
                        w00 * a.y + w10 * b.y + w01 * c.y + w11 * e.y);
 }
 
-__device__ __forceinline__ float2 sample_depth(const float2* tile, int n, f3 d) {
-    Taps t = oct_taps(d, n);
-    int w = n + 2;
-    float2 a = __ldg(tile + t.i00), b = __ldg(tile + t.i00 + 1);
-    float2 c = __ldg(tile + t.i00 + w), e = __ldg(tile + t.i00 + w + 1);
-    return bilerp2(t, a, b, c, e);
-}
-
-// the same from the blocks of a probe (depth_q + p * (n + 1)^2 * 2): one load
+// distance moments in direction d from a probe's 2x2 tap blocks
+// (depth_q + p * (n + 1)^2 * 2): one 32-byte load
 __device__ __forceinline__ float2 sample_depth_q(const float4* blocks, int n, f3 d) {
     Taps t = oct_taps(d, n);
     float4 ab, ce;

@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(128, 9) k_probe_trace(SceneView s, VolumeView 
             out.w = h.t;
             float att = 1.f;
             if (pp.le_attenuation > 0.f) {
-                const int td = v.depth_n + 2;
-                float mu = sample_depth(v.depth + (size_t)p * td * td, v.depth_n, -w).x;
+                const int qd = (v.depth_n + 1) * (v.depth_n + 1);
+                float mu = sample_depth_q(v.depth_q + (size_t)p * qd * 2, v.depth_n, -w).x;
                 float db = fminf(mu, cell_exit(v, -w));
                 float f = h.t / (h.t + pp.le_attenuation * db);
                 att = f * f;
