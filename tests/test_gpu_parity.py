@@ -193,7 +193,10 @@ def test_probe_blend_shapes_parity(dd, orc, irr_n, depth_n, rays):
     leaves a ragged last chunk of weights, one ray, 32 x 32 maps, and
     16 x 32 maps with 1024 rays, whose products are split over several CTAs
     (borders then refreshed by a kernel of their own); two updates, the
-    second mixing by the hysteresis."""
+    second mixing by the hysteresis.  Then a probe trace, whose hits query
+    the blended maps through the query's 2x2 tap blocks (written by the
+    blend, or rebuilt after the border kernel when the products were
+    split)."""
     import dataclasses
     sc = scenegen.tiny_room(width=32, height=24, frames=1)
     sc.settings = dataclasses.replace(sc.settings, rays_per_probe=rays, irr_texels=irr_n, depth_texels=depth_n)
@@ -217,6 +220,12 @@ def test_probe_blend_shapes_parity(dd, orc, irr_n, depth_n, rays):
     assert _frac(_close(irr[..., :3], vol.irr, 1e-5)) >= 0.9999
     assert _frac(_close(dep, vol.depth, 1e-5)) >= 0.9999
     assert np.abs(irr[..., 3]).max() == 0.0   # the fourth channel is untouched
+    ctx.probe_trace(2)
+    rays2 = ctx.probe_rays_get()
+    ref2 = orc.probe_trace(S, vol, 2)
+    same = np.sign(rays2[..., 3]) == np.sign(ref2[..., 3])
+    assert _frac(same) >= 0.999
+    assert _frac(_close(rays2[..., :3][same], ref2[..., :3][same], 1e-5).all(-1)) >= 0.999
     assert ctx.get_status() == dd.OK
 
 
