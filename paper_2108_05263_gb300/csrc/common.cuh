@@ -141,6 +141,14 @@ __device__ __forceinline__ void ld32(const float4* p, float4& a, float4& b) {
         : "l"(p));
 }
 
+// the same, issued where written (a load whose result the next loop
+// iteration consumes: the request goes out before this iteration's work)
+__device__ __forceinline__ void ld32_issue(const float4* p, float4& a, float4& b) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 // the same from L2 only (scattered neighbour records: L1 seldom hits), issued
 // where written so that the loads start before the arithmetic that follows
 __device__ __forceinline__ void ld32_l2(const float4* p, float4& a, float4& b) {

@@ -183,10 +183,13 @@ __device__ __forceinline__ bool emitter_candidate(const SceneView& s, const Volu
 // candidate's point and radiance and continues the stream with the BSDF rays
 // (it overwrites the slot with the residual); the split keeps this loop free
 // of the probe query's registers (REFLECT: some emitter also reflects, so its
-// candidates need the query too).  SMEM: the emitter records, cumulative
-// areas and guide table are read from shared memory (e_cdf, e_guide,
-// e_vert), else from the scene tables.
-template <bool REFLECT, bool SMEM>
+// candidates need the query too).  MODE 0: every emitter table from global
+// memory; 1: the records, cumulative areas and guide table from shared
+// memory (e_vert, e_cdf, e_guide); 2: the cumulative areas and guide table
+// from shared memory and the records from global memory, each candidate's
+// record requested before the candidate ahead of it is evaluated (tables
+// too large for shared memory: the record loads are L2 round trips).
+template <bool REFLECT, int MODE>
 __device__ __forceinline__ void emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                                    const GBufView& g, float4* __restrict__ state, uint32_t frame,
                                                    uint32_t pix, const float4* e_vert, const float* e_cdf,
@@ -209,11 +212,35 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
     const uint32_t prefix = rng_prefix(rp.seed, pix, frame, PASS_INITIAL);
     const float inv_area = 1.f / s.area_total;
     uint32_t esel = 0u;
-    for (uint32_t c = 0; c < cs.NL; ++c) {
-        const uint32_t cp = rng_cand(prefix, c);
-        EmitterCand ec;
-        if (!emitter_candidate<REFLECT, SMEM>(s, v, x, nx, cp, e_vert, e_cdf, e_guide, ec)) continue;
-        if (cs.add(c, cp, ec.y, ec.L, ec.tri, ec.d2, ec.cx, ec.cy, inv_area)) esel = ec.e;
+    if (MODE == 2) {
+        // candidate c + 1's emitter and record, requested a candidate ahead
+        const uint32_t E = s.num_emitters;
+        uint32_t cp_n = 0u, e_n = 0u;
+        float4 n0, n1, n2, n3;
+        auto fetch = [&](uint32_t c) {
+            cp_n = rng_cand(prefix, c);
+            e_n = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u01(rng_u32_dim(cp_n, 0)));
+            const float4* er = s.evert + 4 * (size_t)e_n;
+            ld32_issue(er, n0, n1);
+            ld32_issue(er + 2, n2, n3);
+        };
+        if (cs.NL > 0) fetch(0);
+        for (uint32_t c = 0; c < cs.NL; ++c) {
+            const uint32_t cp = cp_n;
+            EmitterCand ec;
+            ec.e = e_n;
+            const float4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
+            if (c + 1 < cs.NL) fetch(c + 1);
+            if (!emitter_point<REFLECT>(s, v, x, nx, cp, q0, q1, q2, q3, ec)) continue;
+            if (cs.add(c, cp, ec.y, ec.L, ec.tri, ec.d2, ec.cx, ec.cy, inv_area)) esel = ec.e;
+        }
+    } else {
+        for (uint32_t c = 0; c < cs.NL; ++c) {
+            const uint32_t cp = rng_cand(prefix, c);
+            EmitterCand ec;
+            if (!emitter_candidate<REFLECT, MODE == 1>(s, v, x, nx, cp, e_vert, e_cdf, e_guide, ec)) continue;
+            if (cs.add(c, cp, ec.y, ec.L, ec.tri, ec.d2, ec.cx, ec.cy, inv_area)) esel = ec.e;
+        }
     }
     // the selected candidate's index (tag = pixel * 64 + candidate) or none,
     // and its emitter
@@ -229,25 +256,28 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
     int px = blockIdx.x * blockDim.x + threadIdx.x;
     int py = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (px >= g.width || py >= g.height) return;
-    emitter_candidates<REFLECT, false>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, nullptr, nullptr,
-                                       nullptr);
+    emitter_candidates<REFLECT, 0>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, nullptr, nullptr,
+                                   nullptr);
 }
 
 // Persistent variant for emitter tables that fit in shared memory: each CTA
 // copies the records, cumulative areas and guide table once, then walks
 // 64 x 8 pixel tiles (bottom row of tiles first); the 32-byte record reads
 // of the candidates then come from shared memory instead of the L1 that the
-// per-pixel kernel saturates.
+// per-pixel kernel saturates.  RECORDS false: the records are too many for
+// shared memory and only the search tables are staged (MODE 2 above; 71
+// registers, one CTA per SM: a cap at two CTAs spills and ran 4% slower).
 constexpr int kEmitTileW = 64, kEmitTileH = 8;   // measured best (32 x 16, 128 x 4, 16 x 32 slower)
-template <bool REFLECT>
+template <bool REFLECT, bool RECORDS>
 __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
                                                               float4* __restrict__ state, uint32_t frame) {
     extern __shared__ float4 e_smem[];
     const uint32_t E = s.num_emitters, G = s.guide_size;
     float4* e_vert = e_smem;
-    float* e_cdf = reinterpret_cast<float*>(e_smem + 4 * (size_t)E);
+    float* e_cdf = reinterpret_cast<float*>(e_smem + (RECORDS ? 4 * (size_t)E : 0));
     uint32_t* e_guide = reinterpret_cast<uint32_t*>(e_cdf + E);
-    for (uint32_t i = threadIdx.x; i < 4 * E; i += blockDim.x) e_vert[(i & 3u) * E + (i >> 2)] = __ldg(s.evert + i);
+    if (RECORDS)
+        for (uint32_t i = threadIdx.x; i < 4 * E; i += blockDim.x) e_vert[(i & 3u) * E + (i >> 2)] = __ldg(s.evert + i);
     for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) e_cdf[i] = __ldg(s.cdf + i);
     for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) e_guide[i] = __ldg(s.guide + i);
     __syncthreads();
@@ -258,8 +288,8 @@ __global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, Volum
         const int bx = t % tiles_x, by = tiles_y - 1 - t / tiles_x;
         const int px = bx * kEmitTileW + tx, py = by * kEmitTileH + ty;
         if (px >= g.width || py >= g.height) continue;
-        emitter_candidates<REFLECT, true>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, e_vert, e_cdf,
-                                          e_guide);
+        emitter_candidates<REFLECT, RECORDS ? 1 : 2>(s, v, rp, g, state, frame, (uint32_t)py * g.width + px, e_vert,
+                                                     e_cdf, e_guide);
     }
 }
 
@@ -587,11 +617,12 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 }  // namespace
 
 // the emitter-candidate pass: the shared-memory kernel when the emitter
-// tables fit beside enough resident threads, else the per-pixel kernel
+// tables fit beside enough resident threads (all of them, else the search
+// tables alone), else the per-pixel kernel
 cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                       const GBufView& g, float4* state, uint32_t frame, cudaStream_t st) {
-    const size_t smem = sizeof(float4) * 4 * (size_t)s.num_emitters +
-                        sizeof(float) * (size_t)s.num_emitters + sizeof(uint32_t) * (size_t)s.guide_size;
+    const size_t tables = sizeof(float) * (size_t)s.num_emitters + sizeof(uint32_t) * (size_t)s.guide_size;
+    const size_t full = sizeof(float4) * 4 * (size_t)s.num_emitters + tables;
     static int dev_sms = 0, max_smem = 0;
     if (dev_sms == 0) {
         int dev = 0;
@@ -599,8 +630,13 @@ cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, c
         cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
+    const bool records = full <= 96 * 1024 && (int)full <= max_smem;
+    const size_t smem = records ? full : tables;
     if (smem <= 96 * 1024 && (int)smem <= max_smem) {
-        auto kern = s.emitters_reflect ? k_restir_emitters_smem<true> : k_restir_emitters_smem<false>;
+        auto kern = records ? (s.emitters_reflect ? k_restir_emitters_smem<true, true>
+                                                  : k_restir_emitters_smem<false, true>)
+                            : (s.emitters_reflect ? k_restir_emitters_smem<true, false>
+                                                  : k_restir_emitters_smem<false, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
