@@ -24,6 +24,7 @@ struct ddgi_ctx {
     float4* emi = nullptr;
     float4* spec = nullptr;        // glossy lobe per triangle (k_s.rgb, alpha); null: a diffuse scene
     float4* evert = nullptr;
+    float4* evert3 = nullptr;      // 48-byte emitter records: (v0, Le.b), (e1, Le.r), (e2, Le.g)
     float* cdf = nullptr;
     uint32_t* etri = nullptr;
     uint32_t* guide = nullptr;
@@ -166,6 +167,7 @@ SceneView scene_view(ddgi_ctx* c) {
     s.cdf = c->cdf;
     s.etri = c->etri;
     s.evert = c->evert;
+    s.evert3 = c->evert3;
     s.guide = c->guide;
     s.guide_size = c->G;
     s.emitters_reflect = c->emitters_reflect;
@@ -755,6 +757,7 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     ALLOC(alb, T)
     ALLOC(emi, T)
     ALLOC(evert, 4ull * ctx->E)
+    ALLOC(evert3, 3ull * ctx->E)
     ALLOC(guide, ctx->G)
     ALLOC(cdf, ctx->E)
     ALLOC(etri, ctx->E)
@@ -792,6 +795,16 @@ ddgi_status ddgi_create(const ddgi_scene* scene, const ddgi_config* cfg, ddgi_ct
     up(ctx->alb, alb.data(), T * sizeof(float4));
     up(ctx->emi, emi.data(), T * sizeof(float4));
     up(ctx->evert, evert.data(), evert.size() * sizeof(float4));
+    {
+        std::vector<float4> ev3(3ull * ctx->E);
+        for (size_t k = 0; k < ctx->E; ++k) {
+            ev3[3 * k] = evert[4 * k];
+            ev3[3 * k].w = evert[4 * k + 3].w;
+            ev3[3 * k + 1] = evert[4 * k + 1];
+            ev3[3 * k + 2] = evert[4 * k + 2];
+        }
+        up(ctx->evert3, ev3.data(), ev3.size() * sizeof(float4));
+    }
     up(ctx->cdf, cdf.data(), cdf.size() * sizeof(float));
     up(ctx->etri, etri.data(), etri.size() * sizeof(uint32_t));
     up(ctx->guide, guide.data(), guide.size() * sizeof(uint32_t));
@@ -959,7 +972,7 @@ ddgi_status ddgi_scene_update(ddgi_ctx* ctx, const float* xf, uint32_t n, const 
         std::memcpy(sl, emitter_radiance, 3ull * ctx->E * sizeof(float));
         CK(cudaMemcpyAsync(ctx->le_stage, sl, 3ull * ctx->E * sizeof(float), cudaMemcpyHostToDevice, st));
         staged = true;
-        CK(launch_emitter_radiance(ctx->le_stage, ctx->etri, ctx->emi, ctx->evert, ctx->E, st));
+        CK(launch_emitter_radiance(ctx->le_stage, ctx->etri, ctx->emi, ctx->evert, ctx->evert3, ctx->E, st));
     }
     if (staged) {
         CK(cudaEventRecord(ctx->pin_ev, st));

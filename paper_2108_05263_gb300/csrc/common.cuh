@@ -86,6 +86,7 @@ struct SceneView {
     const float* cdf;        // cumulative emitter area (float), [num_emitters]
     const uint32_t* etri;    // emitter triangle ids
     const float4* evert;     // per emitter: (v0, tri), (e1, Le.r), (e2, Le.g), (n, Le.b)
+    const float4* evert3;    // the same without the normal and triangle: (v0, Le.b), (e1, Le.r), (e2, Le.g)
     const uint32_t* guide;   // emitter search start per 1/guide_size of the area
     uint32_t guide_size;
     uint32_t emitters_reflect;   // some emitter has albedo > 0
@@ -147,6 +148,9 @@ __device__ __forceinline__ void ld32_issue(const float4* p, float4& a, float4& b
     asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p));
+}
+__device__ __forceinline__ void ld16_issue(const float4* p, float4& a) {
+    asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w) : "l"(p));
 }
 
 // the same from L2 only (scattered neighbour records: L1 seldom hits), issued

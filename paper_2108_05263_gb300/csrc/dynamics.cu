@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(128) k_refit(float4* __restrict__ nodes, const
 // new radiance of emitter e (emitter-list order): the triangle table and the
 // emitter record
 __global__ void k_emitter_radiance(const float* __restrict__ le, const uint32_t* __restrict__ etri,
-                                   float4* __restrict__ emi, float4* __restrict__ evert, uint32_t E) {
+                                   float4* __restrict__ emi, float4* __restrict__ evert, float4* __restrict__ evert3,
+                                   uint32_t E) {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const float r = le[3 * (size_t)e], g = le[3 * (size_t)e + 1], b = le[3 * (size_t)e + 2];
@@ -99,6 +100,9 @@ __global__ void k_emitter_radiance(const float* __restrict__ le, const uint32_t*
     evert[4 * (size_t)e + 1].w = r;
     evert[4 * (size_t)e + 2].w = g;
     evert[4 * (size_t)e + 3].w = b;
+    evert3[3 * (size_t)e].w = b;
+    evert3[3 * (size_t)e + 1].w = r;
+    evert3[3 * (size_t)e + 2].w = g;
 }
 
 }  // namespace
@@ -121,9 +125,9 @@ cudaError_t launch_instance_update(const float4* obj, const uint4* map, uint32_t
     return e;
 }
 
-cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float4* emi, float4* evert, uint32_t E,
-                                    cudaStream_t st) {
+cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float4* emi, float4* evert,
+                                    float4* evert3, uint32_t E, cudaStream_t st) {
     if (E == 0) return cudaSuccess;
-    k_emitter_radiance<<<(E + 127) / 128, 128, 0, st>>>(le, etri, emi, evert, E);
+    k_emitter_radiance<<<(E + 127) / 128, 128, 0, st>>>(le, etri, emi, evert, evert3, E);
     return cudaGetLastError();
 }

@@ -69,8 +69,8 @@ cudaError_t launch_instance_update(const float4* obj, const uint4* map, uint32_t
                                    float4* nrm, float4* nodes, const uint32_t* refit_list, const float* refit_static,
                                    const int32_t* tri_inst, const std::vector<uint32_t>& level_offsets,
                                    cudaStream_t st);
-cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float4* emi, float4* evert, uint32_t E,
-                                    cudaStream_t st);
+cudaError_t launch_emitter_radiance(const float* le, const uint32_t* etri, float4* emi, float4* evert,
+                                    float4* evert3, uint32_t E, cudaStream_t st);
 cudaError_t launch_probe_relocate(const VolumeView& v, const ProbeParams& p, const float4* rays, float4* offset,
                                   cudaStream_t st);
 size_t probe_blend_smem(const VolumeView& v, uint32_t rays);

@@ -188,7 +188,9 @@ __device__ __forceinline__ bool emitter_candidate(const SceneView& s, const Volu
 // memory (e_vert, e_cdf, e_guide); 2: the cumulative areas and guide table
 // from shared memory and the records from global memory, each candidate's
 // record requested before the candidate ahead of it is evaluated (tables
-// too large for shared memory: the record loads are L2 round trips).
+// too large for shared memory: the record loads are L2 round trips); without
+// reflecting emitters the 48-byte records, the normal rebuilt from the edges
+// (a quarter fewer bytes: 4K building 8.93 -> 8.70 ms for restir_initial).
 template <bool REFLECT, int MODE>
 __device__ __forceinline__ void emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                                    const GBufView& g, float4* __restrict__ state, uint32_t frame,
@@ -216,20 +218,34 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
         // candidate c + 1's emitter and record, requested a candidate ahead
         const uint32_t E = s.num_emitters;
         uint32_t cp_n = 0u, e_n = 0u;
-        float4 n0, n1, n2, n3;
+        float4 n0, n1, n2, n3 = make_float4(0.f, 0.f, 0.f, 0.f);
         auto fetch = [&](uint32_t c) {
             cp_n = rng_cand(prefix, c);
             e_n = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u01(rng_u32_dim(cp_n, 0)));
-            const float4* er = s.evert + 4 * (size_t)e_n;
-            ld32_issue(er, n0, n1);
-            ld32_issue(er + 2, n2, n3);
+            if (REFLECT) {   // the query at the point needs the record's triangle
+                const float4* er = s.evert + 4 * (size_t)e_n;
+                ld32_issue(er, n0, n1);
+                ld32_issue(er + 2, n2, n3);
+            } else {
+                // (a 32-byte load on the record's aligned half and a 16-byte
+                // one, chosen by the parity of e, measured 9% slower)
+                const float4* er = s.evert3 + 3 * (size_t)e_n;
+                ld16_issue(er, n0);
+                ld16_issue(er + 1, n1);
+                ld16_issue(er + 2, n2);
+            }
         };
         if (cs.NL > 0) fetch(0);
         for (uint32_t c = 0; c < cs.NL; ++c) {
             const uint32_t cp = cp_n;
             EmitterCand ec;
             ec.e = e_n;
-            const float4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
+            float4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
+            if (!REFLECT) {   // (n, Le.b) of the full record; the triangle is not needed here
+                const f3 cr = cross(xyz(q1), xyz(q2));
+                const f3 nn = cr * rsqrtf(dot(cr, cr));
+                q3 = make_float4(nn.x, nn.y, nn.z, q0.w);
+            }
             if (c + 1 < cs.NL) fetch(c + 1);
             if (!emitter_point<REFLECT>(s, v, x, nx, cp, q0, q1, q2, q3, ec)) continue;
             if (cs.add(c, cp, ec.y, ec.L, ec.tri, ec.d2, ec.cx, ec.cy, inv_area)) esel = ec.e;
@@ -265,11 +281,11 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
 // 64 x 8 pixel tiles (bottom row of tiles first); the 32-byte record reads
 // of the candidates then come from shared memory instead of the L1 that the
 // per-pixel kernel saturates.  RECORDS false: the records are too many for
-// shared memory and only the search tables are staged (MODE 2 above; 71
-// registers, one CTA per SM: a cap at two CTAs spills and ran 4% slower).
+// shared memory and only the search tables are staged (MODE 2 above; 72
+// registers, one CTA per SM: caps at two CTAs spill and ran 2-4% slower).
 constexpr int kEmitTileW = 64, kEmitTileH = 8;   // measured best (32 x 16, 128 x 4, 16 x 32 slower)
 template <bool REFLECT, bool RECORDS>
-__global__ void __launch_bounds__(512) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
+__global__ void __launch_bounds__(512, 1) k_restir_emitters_smem(SceneView s, VolumeView v, RestirParams rp, GBufView g,
                                                               float4* __restrict__ state, uint32_t frame) {
     extern __shared__ float4 e_smem[];
     const uint32_t E = s.num_emitters, G = s.guide_size;
