@@ -241,7 +241,10 @@ __device__ __forceinline__ void emitter_candidates(const SceneView& s, const Vol
             EmitterCand ec;
             ec.e = e_n;
             float4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
-            if (!REFLECT) {   // (n, Le.b) of the full record; the triangle is not needed here
+            if (!REFLECT) {
+                // (n, Le.b) of the full record.  q0.w holds Le.b, so ec.tri
+                // below is no triangle: this pass only tests the selected
+                // one against DDGI_NONE, which no finite radiance matches
                 const f3 cr = cross(xyz(q1), xyz(q2));
                 const f3 nn = cr * rsqrtf(dot(cr, cr));
                 q3 = make_float4(nn.x, nn.y, nn.z, q0.w);
