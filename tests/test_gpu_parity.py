@@ -1030,6 +1030,61 @@ def test_scene_without_emitters(dd, orc):
     assert np.all(dd.Reservoirs.fields(out.numpy())["M"][og.tri >= 0] == 1.0)
 
 
+def _many_emitter_room(reflect: bool):
+    """The tiny room with its emitting half-ceiling cut into 2048 triangles
+    (radiance 10; albedo 0.5 when `reflect`): too many emitter records for
+    shared memory, so the emitter candidates stage only the search tables
+    and read the records from global memory (48-byte copies, or the full
+    records when emitters reflect and need the probe query)."""
+    sc = scenegen.tiny_room(width=48, height=32, frames=1)
+    keep = sc.emission.max(axis=1) == 0
+    tris = []
+    n = 32
+    for i in range(n):
+        for j in range(n):
+            x0, x1 = -1.0 + i / n, -1.0 + (i + 1) / n
+            z0, z1 = -1.0 + 2.0 * j / n, -1.0 + 2.0 * (j + 1) / n
+            a, b, c, d = (x0, 1.0, z0), (x1, 1.0, z0), (x1, 1.0, z1), (x0, 1.0, z1)
+            tris += [[a, b, c], [a, c, d]]   # winding normal -y: into the room
+    grid = np.asarray(tris, np.float32)
+    sc.verts = np.concatenate([sc.verts[keep], grid]).astype(np.float32)
+    sc.albedo = np.concatenate([sc.albedo[keep], np.full((len(grid), 3), 0.5 if reflect else 0.0)]).astype(np.float32)
+    sc.emission = np.concatenate([sc.emission[keep], np.full((len(grid), 3), 10.0)]).astype(np.float32)
+    return sc
+
+
+@pytest.mark.parametrize("reflect", [False, True])
+def test_many_emitters_initial_parity(dd, orc, reflect):
+    """restir_initial with 2048 emitters (the search tables in shared memory,
+    the records from global memory, a candidate ahead) against the oracle."""
+    import torch
+    sc = _many_emitter_room(reflect)
+    ctx = dd.Context.from_scene(sc)
+    assert ctx.info.num_emitters == 2048
+    S = orc.Scene(sc)
+    vol = orc.Volume(sc.grid)
+    vol.set_interior(np.full((64, 8, 8, 3), 0.7), np.full((64, 16, 16, 2), 5.0))
+    _vol_to_gpu(ctx, vol)
+    og = orc.gbuffer(S, sc.cameras[0])
+    ref, resid = orc.restir_initial(S, vol, og, 3)
+    n = og.tri.shape[0]
+    out = dd.Reservoirs(n)
+    rr = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ctx.restir_initial(_gbuf_to_gpu(dd, og), out, rr, 3)
+    _res_compare(out.numpy(), ref, what=f"many-emitter initial (reflect {reflect})")
+    assert _frac(_close(rr.cpu().numpy()[:, :3], resid, 1e-5).all(1)) >= 0.999
+    # new radiance for every emitter (all > 0: the emitter list stays): the
+    # records' copies follow
+    le = (10.0 * (1 + np.arange(2048) % 3))[:, None] * np.array([1.0, 0.8, 0.6])
+    ctx.scene_update(None, le.astype(np.float32))
+    sc.emission[sc.emission.max(axis=1) > 0] = le
+    S2 = orc.Scene(sc)
+    ref2, _ = orc.restir_initial(S2, vol, og, 4)
+    ctx.restir_initial(_gbuf_to_gpu(dd, og), out, rr, 4)
+    _res_compare(out.numpy(), ref2, what=f"many-emitter initial after new radiance (reflect {reflect})")
+    assert ctx.get_status() == dd.OK
+
+
 # ---------------------------------------------------------------------------
 # image metrics (Sec. 4): MSE and MAPE in fp64
 # ---------------------------------------------------------------------------
