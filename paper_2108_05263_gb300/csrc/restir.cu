@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
             const uint32_t qi = pix * NB + (c - NL);
             L = cyn < 0.f ? xyz(__ldg(s.emi + tri)) + xyz(__ldg(ind + qi)) : f3{0.f, 0.f, 0.f};
         } else if constexpr (GLOSSY) {
-            L = radiance_at_glossy<4>(s, v, y, tri, x, u01(rng_u32_dim(cp, 4)), u01(rng_u32_dim(cp, 5)));
+            L = radiance_at_glossy<2>(s, v, y, tri, x, u01(rng_u32_dim(cp, 4)), u01(rng_u32_dim(cp, 5)));
         } else {
             L = radiance_at<2>(s, v, y, tri, x);
         }
