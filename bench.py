@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import dataclasses
+import gc
 import hashlib
 import json
 import os
@@ -557,12 +558,17 @@ def run_ours(args, ws, rank, local):
             pipe.run(k, sc.cameras[k % args.frames], out_host[k % 2], stream)
         pipe.finish(stream)
         torch.cuda.synchronize()
-        # three segments of Ke frames: the median, so that one host-side
-        # stall in a segment (other processes on the host) does not set it
+        # five segments of Ke frames: the median, so that host-side stalls in
+        # two of them (other processes on the host) do not set it; the
+        # interpreter's cyclic garbage collector is held off meanwhile (its
+        # full passes over the scene's objects stalled the host for tens of
+        # ms; the collection still runs, after the timing)
         Ke = max(10, min(K, 50))
         seg = []
         k0 = 3
-        for _ in range(3):
+        gc_was = gc.isenabled()
+        gc.disable()
+        for _ in range(5):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for k in range(k0, k0 + Ke):
@@ -573,12 +579,15 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize()
             seg.append(a.elapsed_time(b) / Ke)
             k0 += Ke   # the uploads run one frame ahead across segments
+        if gc_was:
+            gc.enable()
+        gc.collect()
         out["e2e"] = {"value": round(statistics.median(seg), 4), "unit": "ms/frame",
                       "h2d_bytes_per_step": 48 * N, "d2h_bytes_per_step": 16 * N,
                       "segments_ms": [round(x, 4) for x in seg],
                       "path": "ddgi.HostFramePipeline through the C ABI: pinned host G-buffer in, host radiance "
                               "out, every frame, copies overlapped with the previous / next frame; median of "
-                              f"3 segments of {Ke} frames"}
+                              f"5 segments of {Ke} frames"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and not glossy:
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=12.0)
     if rank == 0 and not args.no_equal_time and ws == 1 and not glossy:
