@@ -345,17 +345,6 @@ def run_ours(args, ws, rank, local):
         ctx.probe_blend(f, stream)
         if ctx.cfg.probe_relocation:
             ctx.probe_relocate(f, stream)
-        if pipelined:
-            fr.ev_maps.record(stream)
-            fr.side.wait_event(fr.ev_maps)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(fr.side)
-            ctx.probe_trace(f + 1, fr.side)
-            b.record(fr.side)
-            fr.ev_trace.record(fr.side)
-            fr.pending = f + 1
-            if evs is not None:
-                side_evs.append((a, b))
         mark()
         init, tmp = fr._free_pair()
         if fz and fr.prev_final is not None:
@@ -375,6 +364,17 @@ def run_ours(args, ws, rank, local):
             ctx.restir_spatial(g, res, nxt, f, i, stream)
             res = nxt
             mark()
+        if pipelined:   # the next frame's probe trace beside this frame's shading (as Frame.render)
+            fr.ev_maps.record(stream)
+            fr.side.wait_event(fr.ev_maps)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(fr.side)
+            ctx.probe_trace(f + 1, fr.side)
+            b.record(fr.side)
+            fr.ev_trace.record(fr.side)
+            fr.pending = f + 1
+            if evs is not None:
+                side_evs.append((a, b))
         ctx.shade(g, res, fr.resid, fr.radiance, stream, frame=f)
         mark()
         fr.prev_final, fr.prev_cam = res, cam
@@ -560,9 +560,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         # five segments of Ke frames: the median, so that host-side stalls in
         # two of them (other processes on the host) do not set it; the
-        # interpreter's cyclic garbage collector is held off meanwhile (its
-        # full passes over the scene's objects stalled the host for tens of
-        # ms; the collection still runs, after the timing)
+        # interpreter's cyclic garbage collector is held off meanwhile, so
+        # that none of its passes lands inside a segment (it runs after)
         Ke = max(10, min(K, 50))
         seg = []
         k0 = 3
