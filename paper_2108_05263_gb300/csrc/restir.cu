@@ -159,23 +159,14 @@ __device__ __forceinline__ bool emitter_candidate(const SceneView& s, const Volu
     const float u0 = u01(rng_u32_dim(cp, 0));
     float4 q0, q1, q2, q3;
     if (SMEM) {
-        // three (four with reflecting emitters) planes of E records each
-        // (SoA: consecutive emitters on consecutive 16-byte bank groups);
-        // without reflection the 48-byte records, the normal rebuilt from the
-        // edges and q0.w holding Le.b (ec.tri is then no triangle: the
-        // emitter pass only tests it against DDGI_NONE)
+        // four planes of E records each (SoA: consecutive emitters on
+        // consecutive 16-byte bank groups)
         const uint32_t E = s.num_emitters;
         ec.e = sample_emitter_smem(e_cdf, e_guide, E, s.guide_size, u0);
         q0 = e_vert[ec.e];
         q1 = e_vert[E + ec.e];
         q2 = e_vert[2 * E + ec.e];
-        if (REFLECT) {
-            q3 = e_vert[3 * E + ec.e];
-        } else {
-            const f3 cr = cross(xyz(q1), xyz(q2));
-            const f3 nn = cr * rsqrtf(dot(cr, cr));
-            q3 = make_float4(nn.x, nn.y, nn.z, q0.w);
-        }
+        q3 = e_vert[3 * E + ec.e];
     } else {
         ec.e = sample_emitter(s, u0);
         const float4* er = s.evert + 4 * (size_t)ec.e;
@@ -289,9 +280,7 @@ __global__ void __launch_bounds__(128) k_restir_emitters(SceneView s, VolumeView
 }
 
 // Persistent variant for emitter tables that fit in shared memory: each CTA
-// copies the records (48-byte ones without reflecting emitters: 1024
-// emitters take 56 KB with the search tables), cumulative areas and guide
-// table once, then walks
+// copies the records, cumulative areas and guide table once, then walks
 // 64 x 8 pixel tiles (bottom row of tiles first); the 32-byte record reads
 // of the candidates then come from shared memory instead of the L1 that the
 // per-pixel kernel saturates.  RECORDS false: the records are too many for
@@ -304,13 +293,10 @@ __global__ void __launch_bounds__(512, 1) k_restir_emitters_smem(SceneView s, Vo
     extern __shared__ float4 e_smem[];
     const uint32_t E = s.num_emitters, G = s.guide_size;
     float4* e_vert = e_smem;
-    constexpr uint32_t PL = REFLECT ? 4u : 3u;
-    float* e_cdf = reinterpret_cast<float*>(e_smem + (RECORDS ? PL * (size_t)E : 0));
+    float* e_cdf = reinterpret_cast<float*>(e_smem + (RECORDS ? 4 * (size_t)E : 0));
     uint32_t* e_guide = reinterpret_cast<uint32_t*>(e_cdf + E);
-    if (RECORDS) {
-        const float4* src = REFLECT ? s.evert : s.evert3;
-        for (uint32_t i = threadIdx.x; i < PL * E; i += blockDim.x) e_vert[(i % PL) * E + i / PL] = __ldg(src + i);
-    }
+    if (RECORDS)
+        for (uint32_t i = threadIdx.x; i < 4 * E; i += blockDim.x) e_vert[(i & 3u) * E + (i >> 2)] = __ldg(s.evert + i);
     for (uint32_t i = threadIdx.x; i < E; i += blockDim.x) e_cdf[i] = __ldg(s.cdf + i);
     for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) e_guide[i] = __ldg(s.guide + i);
     __syncthreads();
@@ -655,7 +641,7 @@ inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (
 cudaError_t launch_emitter_candidates(const SceneView& s, const VolumeView& v, const RestirParams& rp,
                                       const GBufView& g, float4* state, uint32_t frame, cudaStream_t st) {
     const size_t tables = sizeof(float) * (size_t)s.num_emitters + sizeof(uint32_t) * (size_t)s.guide_size;
-    const size_t full = sizeof(float4) * (s.emitters_reflect ? 4 : 3) * (size_t)s.num_emitters + tables;
+    const size_t full = sizeof(float4) * 4 * (size_t)s.num_emitters + tables;
     static int dev_sms = 0, max_smem = 0;
     if (dev_sms == 0) {
         int dev = 0;
