@@ -382,8 +382,13 @@ __device__ __forceinline__ void temporal_merge(const SceneView& s, const RestirP
 // compiler's multiply-add contraction in each kernel (a few ulp).
 // GLOSSY: the radiance at a BSDF hit includes the one-sample glossy half of
 // L_DDGI+ (Sec. 3.3), drawn with dimensions 4 and 5 of the candidate's keys.
+// Diffuse: at most 96 registers (five CTAs per SM, 24 bytes of spill) with
+// the probe query's loop not unrolled: 1.183 -> 1.171 ms for the fused pass
+// against 128 registers (four CTAs) with the loop unrolled 2x or not; the
+// glossy form, whose second query would spill 200 bytes there, keeps 128
+// (four CTAs).
 template <bool FUSE, bool GLOSSY>
-__global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
+__global__ void __launch_bounds__(128, GLOSSY ? 4 : 5) k_restir_initial(SceneView s, VolumeView v, RestirParams rp,
                                                         GBufView g, ResView out,
                                                         float4* __restrict__ resid, uint32_t frame,
                                                         const float2* __restrict__ bsdf_hits,
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(128) k_restir_initial(SceneView s, VolumeView 
         } else if constexpr (GLOSSY) {
             L = radiance_at_glossy<2>(s, v, y, tri, x, u01(rng_u32_dim(cp, 4)), u01(rng_u32_dim(cp, 5)));
         } else {
-            L = radiance_at<2>(s, v, y, tri, x);
+            L = radiance_at<1>(s, v, y, tri, x);
         }
         if (cx > 0.f) {
             float G = cx * fabsf(cyn) / d2;
