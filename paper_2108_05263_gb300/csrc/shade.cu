@@ -175,12 +175,10 @@ __device__ f3 shade_radiance(const SceneView& s, const VolumeView& v, const Shad
 }
 
 template <bool GLOSSY>
-__global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
-                                               const float4* __restrict__ resid,
-                                               float4* __restrict__ radiance,
-                                               const float2* __restrict__ vis,
-                                               const float4* __restrict__ ind,
-                                               const MLPState* __restrict__ mst, ShadeParams sp) {
+__device__ __forceinline__ void shade_pixel(SceneView s, VolumeView v, GBufView g, ResView r,
+                                            const float4* __restrict__ resid, float4* __restrict__ radiance,
+                                            const float2* __restrict__ vis, const float4* __restrict__ ind,
+                                            const MLPState* __restrict__ mst, ShadeParams sp) {
     // rows bottom-up: the shadow-ray pass read the pixels' planes top-down,
     // so its last rows are still in L2
     int px = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,6 +226,24 @@ __global__ void __launch_bounds__(128) k_shade(SceneView s, VolumeView v, GBufVi
     radiance[pix] = make_float4(out.x, out.y, out.z, 1.f);
 }
 
+// Diffuse shading at eight CTAs per SM (64 registers, 4 bytes of spill:
+// -3 us against seven at 72); the glossy form, whose recursion's traversal
+// would spill 256 bytes there (and ran 45 us slower at four CTAs and 122
+// registers), keeps the compiler's choice (96).
+__global__ void __launch_bounds__(128, 8) k_shade(SceneView s, VolumeView v, GBufView g, ResView r,
+                                                  const float4* __restrict__ resid, float4* __restrict__ radiance,
+                                                  const float2* __restrict__ vis, const float4* __restrict__ ind,
+                                                  const MLPState* __restrict__ mst, ShadeParams sp) {
+    shade_pixel<false>(s, v, g, r, resid, radiance, vis, ind, mst, sp);
+}
+__global__ void __launch_bounds__(128) k_shade_glossy(SceneView s, VolumeView v, GBufView g, ResView r,
+                                                      const float4* __restrict__ resid,
+                                                      float4* __restrict__ radiance, const float2* __restrict__ vis,
+                                                      const float4* __restrict__ ind,
+                                                      const MLPState* __restrict__ mst, ShadeParams sp) {
+    shade_pixel<true>(s, v, g, r, resid, radiance, vis, ind, mst, sp);
+}
+
 inline dim3 tile_grid(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
 
 }  // namespace
@@ -254,10 +270,10 @@ cudaError_t launch_shade(const SceneView& s, const VolumeView& v, const GBufView
     }
     dim3 b(32, 4);   // measured best for this kernel (16 x 8 slower)
     if (s.spec)
-        k_shade<true><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
-                                                                     mlp ? mst : nullptr, sp);
-    else
-        k_shade<false><<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
+        k_shade_glossy<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
                                                                       mlp ? mst : nullptr, sp);
+    else
+        k_shade<<<tile_grid(g.width, g.height, b), b, 0, st>>>(s, v, g, r, resid, radiance, hits, ind,
+                                                               mlp ? mst : nullptr, sp);
     return cudaGetLastError();
 }
